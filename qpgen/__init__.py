@@ -1,0 +1,5 @@
+"""Seeded synthetic QP instances shared by the oracle, the tests and the bench."""
+from .instances import (  # noqa: F401
+    QPInstance, QPFamily, SEED_BASE, random_sparse_qp, large_sparse_qp, portfolio_qp,
+    mpc_qp, mpc_batch, family_qp, tiny_qp, diagonal_box_qp,
+)
