@@ -1,0 +1,191 @@
+/*
+ * pdqp.h -- C ABI of a GB300 (sm_103a) solver for convex quadratic programs by
+ * restarted accelerated primal-dual hybrid gradient (rAPDHG).
+ *
+ * The method is Algorithm 1 of Lu & Yang, "A Practical and Optimal First-Order
+ * Method for Large-Scale Convex Quadratic Programming" (Section 2), run with
+ * the practical rules of its Section 6 (PDQP adaptive restart, adaptive step
+ * size, primal weight) and the diagonal preconditioning and relative-KKT
+ * progress metric of its Section 5.
+ *
+ * Problem form.  The paper states eq. (1) as  min 1/2 x'Qx + c'x  s.t. Ax <= b
+ * and notes (footnote to eq. (1)) that its results extend to other QP forms.
+ * This library takes the form
+ *
+ *     min 1/2 x'Qx + c'x   s.t.  A[0:m_eq]  x  = b[0:m_eq]
+ *                                A[m_eq:m] x >= b[m_eq:m]
+ *                                l <= x <= u
+ *
+ * with the saddle function L(x,y) = 1/2 x'Qx + c'x - y'(Ax - b) of eq. (2)
+ * (A' = -A, b' = -b), x in [l,u] and y in R^{m_eq} x R_+^{m-m_eq}.
+ *
+ * Conventions common to every call
+ *   - Sparse matrices are CSR: rowptr int32[rows+1] (rowptr[0] = 0,
+ *     non-decreasing), col int32[nnz] strictly increasing inside each row and in
+ *     [0, cols), values float64[nnz], all finite.  Q is square n x n, symmetric
+ *     positive semidefinite and stored in full (both triangles).
+ *   - `mem_space` says where the caller's pointers live: PDQP_MEM_HOST (0) for
+ *     host memory, PDQP_MEM_DEVICE (1) for device memory of the current CUDA
+ *     device (for example a torch CUDA tensor's data_ptr()).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *     call enqueues its device work on that stream; calls that return results
+ *     to the host synchronise it before returning.
+ *   - The library copies everything it is given; the caller keeps ownership of
+ *     its arrays and may free them once the call returns.  Outputs are written
+ *     into caller-owned buffers.
+ *   - Errors are returned as pdqp_status, never thrown; pdqp_last_error()
+ *     describes the most recent error of a handle.  A handle is not thread
+ *     safe; distinct handles are independent.
+ */
+#ifndef PDQP_H
+#define PDQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdqp_problem *pdqp_handle;
+
+typedef enum {
+  PDQP_OK = 0,
+  PDQP_ERR_INVALID = 1,      /* malformed input (bad CSR, l > u, NaN, m_eq > m, ...) */
+  PDQP_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  PDQP_ERR_OOM = 3,          /* device or host allocation failed */
+  PDQP_ITER_LIMIT = 10,      /* max_iter reached; the best iterate is returned */
+  PDQP_TIME_LIMIT = 11,      /* time_limit reached; the best iterate is returned */
+  PDQP_NUMERICAL = 12,       /* NaN or Inf met in the relative KKT error */
+  PDQP_DEVICE_TIMEOUT = 13   /* a bounded device wait gave up */
+} pdqp_status;
+
+enum { PDQP_MEM_HOST = 0, PDQP_MEM_DEVICE = 1 };
+enum { PDQP_PREC_FP64 = 0, PDQP_PREC_MIXED = 1 };
+enum { PDQP_STEP_ADAPTIVE = 0, PDQP_STEP_THEORY = 1 };
+enum { PDQP_RESTART_PDQP = 0, PDQP_RESTART_HALVING = 1, PDQP_RESTART_FIXED = 2,
+       PDQP_RESTART_NONE = 3 };
+
+typedef struct {
+  /* PDQP_PREC_FP64: every step in float64.  PDQP_PREC_MIXED: float32 matrix
+   * values, vectors and SpMVs in the iteration; float64 relative-KKT
+   * reductions, restart decisions and a float64 residual correction at every
+   * restart (not in the paper). */
+  int32_t precision;
+  /* PDQP_STEP_ADAPTIVE: Section 6 step size eta^{n,k} with primal weight
+   * omega (primal step eta/omega, dual step eta*omega).  PDQP_STEP_THEORY:
+   * Theorem 1's eta_k = (k+1)/(2(||Q||+K||A||)), tau_k = (k+1)/(2K||A||)
+   * with K = fixed_K. */
+  int32_t step_rule;
+  /* PDQP_RESTART_PDQP: Section 6 conditions (i)-(iii).  _HALVING: Section 5
+   * adaptive scheme relKKT(z_bar) <= relKKT(z^{n,0})/2.  _FIXED: after
+   * fixed_K inner iterations (taken at the first check with k >= fixed_K).
+   * _NONE: never restart. */
+  int32_t restart_rule;
+  int32_t accelerate;        /* 0: beta_k = theta_k = 1 (plain PDHG, Section 5 "Algorithms") */
+  int32_t scaling;           /* Section 5 "Preprocessing" on/off */
+  int32_t ruiz_iters;        /* 10 */
+  int32_t l2_scaling;        /* 1 */
+  int32_t pock_chambolle;    /* 1 (alpha = 1) */
+  int32_t fixed_K;           /* restart length for _FIXED and the theory step rule */
+  int32_t check_period;      /* iterations between relKKT checks (even; default 64) */
+  int64_t max_iter;          /* 200000 (Section 5) */
+  double eps;                /* relKKT termination tolerance eq. (terminate); 1e-6 */
+  double time_limit;         /* seconds; 3600 (Section 6.1) */
+  double beta_suff, beta_nec, beta_art;   /* 0.2, 0.8, 0.36 (Section 6) */
+  double pw_theta;           /* 0.2: primal-weight smoothing (Section 6) */
+  double eps_zero;           /* 1e-10 */
+  double norm_A, norm_Q;     /* > 0: use these spectral norms of the SCALED
+                                matrices; <= 0: estimate by power iteration */
+  int32_t power_iters;       /* 500 */
+  double power_tol;          /* 1e-6 relative change of the Rayleigh quotient */
+  int32_t lanes_A, lanes_P;  /* CSR lanes per row for the dual / primal kernels;
+                                0 = chosen by the library */
+} pdqp_options;
+
+typedef struct {
+  int32_t status;            /* pdqp_status of the solve */
+  int64_t iterations;        /* total inner iterations */
+  int64_t restarts;
+  double rel_kkt, r_primal, r_dual, r_gap;   /* of the returned iterate, original problem */
+  double primal_obj, dual_obj;
+  double seconds;            /* wall time of the call */
+  double norm_A, norm_Q;     /* spectral norms used (scaled problem) */
+  double omega;              /* final primal weight */
+} pdqp_info;
+
+/* Fill *opt with the defaults listed above. */
+void pdqp_default_options(pdqp_options *opt);
+
+/* Human-readable name of a status code (static string). */
+const char *pdqp_status_string(int32_t status);
+
+/* Create a problem handle (Section 1 eq. (1) in the form above).
+ * n >= 1 variables, m >= 0 rows of which the first m_eq are equalities.
+ * Q_*: CSR of Q (n rows); A_*: CSR of A (m rows; may be NULL when m = 0).
+ * c, b, l, u: float64[n], [m], [n], [n]; l may hold -INFINITY and u +INFINITY,
+ * l <= u elementwise.  The data are validated, copied to device memory and
+ * the transpose of A is built.  Returns PDQP_ERR_INVALID with *out = NULL on
+ * malformed input. */
+pdqp_status pdqp_create(pdqp_handle *out, int64_t n, int64_t m, int64_t m_eq,
+                        const int32_t *Q_rowptr, const int32_t *Q_col, const double *Q_val,
+                        const int32_t *A_rowptr, const int32_t *A_col, const double *A_val,
+                        const double *c, const double *b, const double *l, const double *u,
+                        int32_t mem_space, void *stream);
+
+/* Add a low-rank term to the objective: Q_total = Q + F F' with F float32,
+ * row-major n x r (1 <= r <= 256), applied as F(F'x) (never formed).  The
+ * low-rank term is left out of the scaling norms; D2 scales F's rows. */
+pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float *F, int32_t mem_space,
+                               void *stream);
+
+/* Solve (Algorithm 1 with the Section 6 rules) from (x0, y0) -- NULL means the
+ * all-zero start of Section 5 -- writing the returned iterate to x_out[n] and
+ * y_out[m] (either may be NULL) and the summary to *info (may be NULL).
+ * x0, y0, x_out, y_out live in `mem_space`.  Returns PDQP_OK when relKKT <= eps,
+ * PDQP_ITER_LIMIT / PDQP_TIME_LIMIT with the best iterate written, or an
+ * error.  Synchronises `stream`. */
+pdqp_status pdqp_solve(pdqp_handle h, const pdqp_options *opt, const double *x0, const double *y0,
+                       double *x_out, double *y_out, pdqp_info *info, int32_t mem_space,
+                       void *stream);
+
+/* Solve `count` independent problems with the same options.  Arrays of
+ * per-problem pointers (host arrays of pointers; the pointed-to vectors live in
+ * `mem_space`); x0/y0/x_out/y_out may be NULL as a whole or per entry.
+ * infos[count] receives one summary per problem.  Returns the worst status. */
+pdqp_status pdqp_solve_batch(int32_t count, const pdqp_handle *hs, const pdqp_options *opt,
+                             const double *const *x0, const double *const *y0,
+                             double *const *x_out, double *const *y_out, pdqp_info *infos,
+                             int32_t mem_space, void *stream);
+
+/* Raw iterate state after the last solve, in original coordinates:
+ * x, x_bar (n) and y, y_bar (m) of Algorithm 1 (any pointer may be NULL). */
+pdqp_status pdqp_get_state(pdqp_handle h, double *x, double *y, double *xbar, double *ybar,
+                           int32_t mem_space, void *stream);
+
+/* Relative KKT error (Section 5 "Progress metric", equality/bound form) of a
+ * caller-given (x, y) on the handle's original problem, computed on the
+ * device in float64.  parts[6] (host) receives r_primal, r_dual, r_gap,
+ * rel_kkt, primal_obj, dual_obj. */
+pdqp_status pdqp_kkt(pdqp_handle h, const double *x, const double *y, double *parts,
+                     int32_t mem_space, void *stream);
+
+/* Sizes of the handle's problem. */
+pdqp_status pdqp_get_sizes(pdqp_handle h, int64_t *n, int64_t *m, int64_t *m_eq,
+                           int64_t *nnz_Q, int64_t *nnz_A);
+
+/* Last error message of a handle ("" if none); pdqp_last_error(NULL) gives the
+ * last error of a failed pdqp_create on this thread. */
+const char *pdqp_last_error(pdqp_handle h);
+
+/* Release all device and host memory of a handle (NULL is a no-op). */
+void pdqp_destroy(pdqp_handle h);
+
+/* Kernel launches the library issued since the process started (for
+ * reporting how much GPU work a call did). */
+int64_t pdqp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDQP_H */

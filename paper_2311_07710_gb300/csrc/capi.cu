@@ -1,0 +1,552 @@
+// C ABI of the rAPDHG solver: input validation, device memory, the host loop
+// over chunks of `check_period` iterations, and result marshalling.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pdqp.h"
+#include "solver.h"
+
+struct pdqp_problem {
+  Work w;
+  std::string err;
+  bool mixed_ready = false;
+  std::vector<void*> allocs;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+struct Fail {
+  pdqp_status st;
+  std::string msg;
+};
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? PDQP_ERR_OOM : PDQP_ERR_CUDA,      \
+                 std::string(#call) + ": " + cudaGetErrorString(e_)};                \
+  } while (0)
+
+template <typename T>
+T* dalloc(pdqp_problem* h, size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, count * sizeof(T)));
+  h->allocs.push_back(p);
+  return (T*)p;
+}
+
+template <typename T>
+void to_device(T* dst, const T* src, size_t count, cudaStream_t s) {
+  if (count) CK(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+// Fetch `count` elements of a caller array (host or device) into a host vector.
+template <typename T>
+std::vector<T> fetch(const T* p, size_t count, int mem, cudaStream_t s) {
+  std::vector<T> v(count);
+  if (count == 0) return v;
+  if (mem == PDQP_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(v.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(v.data(), p, count * sizeof(T));
+  }
+  return v;
+}
+
+void check_space(const void* p, int mem, const char* what) {
+  if (!p) return;
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) { cudaGetLastError(); at.type = cudaMemoryTypeUnregistered; }
+  const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (mem == PDQP_MEM_DEVICE && !dev)
+    throw Fail{PDQP_ERR_INVALID, std::string(what) + " is not device memory but mem_space = PDQP_MEM_DEVICE"};
+  if (mem == PDQP_MEM_HOST && at.type == cudaMemoryTypeDevice)
+    throw Fail{PDQP_ERR_INVALID, std::string(what) + " is device memory but mem_space = PDQP_MEM_HOST"};
+}
+
+void validate_csr(const char* name, int64_t rows, int64_t cols, const std::vector<int32_t>& rp,
+                  const std::vector<int32_t>& col, const std::vector<double>& val) {
+  if (rp.empty() || rp[0] != 0) throw Fail{PDQP_ERR_INVALID, std::string(name) + ": rowptr[0] != 0"};
+  for (int64_t i = 0; i < rows; ++i) {
+    if (rp[i + 1] < rp[i]) throw Fail{PDQP_ERR_INVALID, std::string(name) + ": rowptr decreases"};
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      if (col[k] < 0 || col[k] >= cols)
+        throw Fail{PDQP_ERR_INVALID, std::string(name) + ": column index out of range"};
+      if (k > rp[i] && col[k] <= col[k - 1])
+        throw Fail{PDQP_ERR_INVALID, std::string(name) + ": column indices not strictly increasing in a row"};
+      if (!std::isfinite(val[k])) throw Fail{PDQP_ERR_INVALID, std::string(name) + ": non-finite value"};
+    }
+  }
+}
+
+// Transpose a CSR matrix (rows x cols) by a stable counting sort on the column
+// index, so that the rows of the transpose are sorted.
+void transpose_csr(int64_t rows, int64_t cols, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                   const std::vector<double>& val, std::vector<int32_t>& trp, std::vector<int32_t>& tcol,
+                   std::vector<double>& tval) {
+  const int64_t nnz = rp[rows];
+  trp.assign(cols + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k) trp[col[k] + 1]++;
+  for (int64_t j = 0; j < cols; ++j) trp[j + 1] += trp[j];
+  std::vector<int32_t> cur(trp.begin(), trp.end() - 1);
+  tcol.resize(nnz);
+  tval.resize(nnz);
+  for (int64_t i = 0; i < rows; ++i)
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int32_t p = cur[col[k]]++;
+      tcol[p] = (int32_t)i;
+      tval[p] = val[k];
+    }
+}
+
+void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
+                const std::vector<double>& val, cudaStream_t s) {
+  M.rows = rows;
+  M.nnz = rp[rows];
+  M.rp = dalloc<int>(h, rows + 1);
+  M.col = dalloc<int>(h, M.nnz);
+  M.val = dalloc<double>(h, M.nnz);
+  M.sval = dalloc<double>(h, M.nnz);
+  to_device(M.rp, rp.data(), rows + 1, s);
+  to_device(M.col, col.data(), M.nnz, s);
+  to_device(M.val, val.data(), M.nnz, s);
+}
+
+void alloc_mixed(pdqp_problem* h) {
+  if (h->mixed_ready) return;
+  Work& w = h->w;
+  const int n = w.n, m = w.m;
+  w.Q.sval_f = dalloc<float>(h, w.Q.nnz);
+  w.A.sval_f = dalloc<float>(h, w.A.nnz);
+  w.At.sval_f = dalloc<float>(h, w.At.nnz);
+  w.fx = dalloc<float>(h, n); w.fxbar = dalloc<float>(h, n); w.fxt = dalloc<float>(h, n);
+  w.fxmd[0] = dalloc<float>(h, n); w.fxmd[1] = dalloc<float>(h, n);
+  w.fy = dalloc<float>(h, m); w.fybar = dalloc<float>(h, m);
+  w.fc = dalloc<float>(h, n); w.fl = dalloc<float>(h, n); w.fu = dalloc<float>(h, n);
+  w.fb = dalloc<float>(h, m); w.fylo = dalloc<float>(h, m);
+  w.xhi = dalloc<double>(h, n); w.yhi = dalloc<double>(h, m);
+  w.prodAx = dalloc<double>(h, 2 * (size_t)m);
+  w.prodQx = dalloc<double>(h, 2 * (size_t)n);
+  w.prodATy = dalloc<double>(h, 2 * (size_t)n);
+  h->mixed_ready = true;
+}
+
+SolveParams make_params(const pdqp_options& o) {
+  SolveParams p{};
+  p.step_rule = o.step_rule;
+  p.restart_rule = o.restart_rule;
+  p.accelerate = o.accelerate ? 1 : 0;
+  p.fixed_K = o.fixed_K;
+  p.check_period = o.check_period;
+  p.mixed = o.precision == PDQP_PREC_MIXED;
+  p.max_iter = o.max_iter;
+  p.eps = o.eps;
+  p.beta_suff = o.beta_suff;
+  p.beta_nec = o.beta_nec;
+  p.beta_art = o.beta_art;
+  p.pw_theta = o.pw_theta;
+  p.eps_zero = o.eps_zero;
+  p.power_tol = o.power_tol;
+  p.power_iters = o.power_iters;
+  return p;
+}
+
+void validate_options(const pdqp_options& o) {
+  auto bad = [](const char* m) { throw Fail{PDQP_ERR_INVALID, m}; };
+  if (o.precision != PDQP_PREC_FP64 && o.precision != PDQP_PREC_MIXED) bad("options.precision");
+  if (o.step_rule != PDQP_STEP_ADAPTIVE && o.step_rule != PDQP_STEP_THEORY) bad("options.step_rule");
+  if (o.restart_rule < 0 || o.restart_rule > 3) bad("options.restart_rule");
+  if (o.check_period < 2 || o.check_period > PDQP_MAX_CHECK || (o.check_period & 1))
+    bad("options.check_period must be even and in [2, 4096]");
+  if (o.max_iter < 1) bad("options.max_iter must be >= 1");
+  if (!(o.eps >= 0.0)) bad("options.eps must be >= 0");
+  if ((o.restart_rule == PDQP_RESTART_FIXED || o.step_rule == PDQP_STEP_THEORY) && o.fixed_K < 1)
+    bad("options.fixed_K must be >= 1");
+  if (o.power_iters < 1) bad("options.power_iters must be >= 1");
+  for (int L : {o.lanes_A, o.lanes_P})
+    if (L != 0 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) bad("options.lanes_* must be 0,2,4,8,16,32");
+}
+
+int auto_lanes(long long nnz, long long rows) {
+  const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  int L = 2;
+  while (L < 32 && L < avg) L <<= 1;
+  return L;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void sync_state(pdqp_problem* h, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->w.st_host, h->w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+pdqp_status finish_status(int st) {
+  switch (st) {
+    case ST_OPTIMAL: return PDQP_OK;
+    case ST_ITER_LIMIT: return PDQP_ITER_LIMIT;
+    case ST_NUMERICAL: return PDQP_NUMERICAL;
+    default: return PDQP_ERR_CUDA;
+  }
+}
+
+pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0, const double* y0,
+                       double* x_out, double* y_out, pdqp_info* info, int mem, cudaStream_t s) {
+  const double t0 = now_s();
+  Work& w = h->w;
+  validate_options(o);
+  if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
+  check_space(x0, mem, "x0");
+  check_space(y0, mem, "y0");
+  check_space(x_out, mem, "x_out");
+  check_space(y_out, mem, "y_out");
+  const bool mixed = o.precision == PDQP_PREC_MIXED;
+  if (mixed) throw Fail{PDQP_ERR_INVALID, "mixed precision is not available in this build"};
+  const SolveParams p = make_params(o);
+
+  // start point in device memory
+  const double* dx0 = x0;
+  const double* dy0 = y0;
+  if (mem == PDQP_MEM_HOST) {
+    if (x0) { to_device(w.stage_n, x0, w.n, s); dx0 = w.stage_n; }
+    if (y0) { to_device(w.stage_m, y0, w.m, s); dy0 = w.stage_m; }
+  }
+
+  // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle
+  pdqp::scale_reset(w, s);
+  if (o.scaling) {
+    for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(w, 0, s);
+    if (o.l2_scaling) pdqp::scale_pass(w, 1, s);
+    if (o.pock_chambolle) pdqp::scale_pass(w, 2, s);
+  }
+  pdqp::scale_apply(w, mixed, s);
+
+  // spectral norms of the scaled matrices
+  if (!(o.norm_A > 0.0 && o.norm_Q > 0.0)) {
+    pdqp::power_init(w, s);
+    for (int t = 0; t < o.power_iters; ++t) {
+      pdqp::power_iter(w, t, p, s);
+      if ((t & 15) == 15) {
+        sync_state(h, s);
+        if (w.st_host->pi_done[0] && w.st_host->pi_done[1]) break;
+      }
+    }
+  }
+  pdqp::power_finish(w, o.norm_A, o.norm_Q, s);
+  pdqp::init_iterates(w, dx0, dy0, p, s);
+  pdqp::check(w, p, 0, 0, mixed, s);
+  CK(cudaGetLastError());
+  sync_state(h, s);
+
+  const int lanesA = o.lanes_A ? o.lanes_A : auto_lanes(w.A.nnz, w.m);
+  const int lanesP = o.lanes_P ? o.lanes_P : auto_lanes(w.Q.nnz + w.At.nnz, w.n);
+  long long k_total = 0;
+  pdqp_status result = PDQP_OK;
+  bool timed_out = false;
+  while (w.st_host->status == ST_RUNNING) {
+    const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
+    pdqp::iterate_chunk(w, (int)len, lanesA, lanesP, mixed, s);
+    pdqp::check(w, p, 1, len, mixed, s);
+    CK(cudaGetLastError());
+    k_total += len;
+    sync_state(h, s);
+    if (w.st_host->status == ST_RUNNING && now_s() - t0 > o.time_limit) { timed_out = true; break; }
+  }
+  result = timed_out ? PDQP_TIME_LIMIT : finish_status(w.st_host->status);
+
+  // the returned iterate
+  if (x_out || y_out) {
+    double* ox = x_out;
+    double* oy = y_out;
+    if (mem == PDQP_MEM_HOST) { ox = x_out ? w.stage_n : nullptr; oy = y_out ? w.stage_m : nullptr; }
+    pdqp::write_output(w, ox, oy, mixed, s);
+    if (mem == PDQP_MEM_HOST) {
+      if (x_out) CK(cudaMemcpyAsync(x_out, w.stage_n, w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (y_out && w.m) CK(cudaMemcpyAsync(y_out, w.stage_m, w.m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+  }
+  CK(cudaGetLastError());
+  sync_state(h, s);
+  if (info) {
+    const DevState& S = *w.st_host;
+    info->status = result;
+    info->iterations = S.k_total;
+    info->restarts = S.restarts;
+    info->r_primal = S.out_parts[0];
+    info->r_dual = S.out_parts[1];
+    info->r_gap = S.out_parts[2];
+    info->rel_kkt = S.out_parts[3];
+    info->primal_obj = S.out_parts[4];
+    info->dual_obj = S.out_parts[5];
+    info->norm_A = S.normA;
+    info->norm_Q = S.normQ;
+    info->omega = S.omega;
+    info->seconds = now_s() - t0;
+  }
+  return result;
+}
+
+}  // namespace
+
+// ==========================================================================
+extern "C" {
+
+void pdqp_default_options(pdqp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PDQP_PREC_FP64;
+  o->step_rule = PDQP_STEP_ADAPTIVE;
+  o->restart_rule = PDQP_RESTART_PDQP;
+  o->accelerate = 1;
+  o->scaling = 1;
+  o->ruiz_iters = 10;
+  o->l2_scaling = 1;
+  o->pock_chambolle = 1;
+  o->fixed_K = 64;
+  o->check_period = 64;
+  o->max_iter = 200000;
+  o->eps = 1e-6;
+  o->time_limit = 3600.0;
+  o->beta_suff = 0.2;
+  o->beta_nec = 0.8;
+  o->beta_art = 0.36;
+  o->pw_theta = 0.2;
+  o->eps_zero = 1e-10;
+  o->norm_A = 0.0;
+  o->norm_Q = 0.0;
+  o->power_iters = 500;
+  o->power_tol = 1e-6;
+  o->lanes_A = 0;
+  o->lanes_P = 0;
+}
+
+const char* pdqp_status_string(int32_t st) {
+  switch (st) {
+    case PDQP_OK: return "optimal";
+    case PDQP_ERR_INVALID: return "invalid input";
+    case PDQP_ERR_CUDA: return "CUDA error";
+    case PDQP_ERR_OOM: return "out of memory";
+    case PDQP_ITER_LIMIT: return "iteration limit";
+    case PDQP_TIME_LIMIT: return "time limit";
+    case PDQP_NUMERICAL: return "numerical error";
+    case PDQP_DEVICE_TIMEOUT: return "device timeout";
+    default: return "unknown status";
+  }
+}
+
+pdqp_status pdqp_create(pdqp_handle* out, int64_t n, int64_t m, int64_t m_eq, const int32_t* Q_rowptr,
+                        const int32_t* Q_col, const double* Q_val, const int32_t* A_rowptr, const int32_t* A_col,
+                        const double* A_val, const double* c, const double* b, const double* l, const double* u,
+                        int32_t mem, void* stream) {
+  if (!out) return PDQP_ERR_INVALID;
+  *out = nullptr;
+  pdqp_problem* h = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    if (n < 1 || m < 0 || m_eq < 0 || m_eq > m || n > (1LL << 30) || m > (1LL << 30))
+      throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
+    if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
+    if (!Q_rowptr || !c || !l || !u) throw Fail{PDQP_ERR_INVALID, "null Q_rowptr, c, l or u"};
+    if (m > 0 && (!A_rowptr || !b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
+    for (auto pr : {(const void*)Q_rowptr, (const void*)Q_col, (const void*)Q_val, (const void*)A_rowptr,
+                    (const void*)A_col, (const void*)A_val, (const void*)c, (const void*)b, (const void*)l,
+                    (const void*)u})
+      check_space(pr, mem, "input array");
+    // fetch to host for validation and the transpose of A
+    std::vector<int32_t> qrp = fetch(Q_rowptr, n + 1, mem, s);
+    const int64_t nnzQ = qrp[n];
+    if (nnzQ < 0 || (nnzQ > 0 && (!Q_col || !Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
+    std::vector<int32_t> qcol = fetch(Q_col, nnzQ, mem, s);
+    std::vector<double> qval = fetch(Q_val, nnzQ, mem, s);
+    std::vector<int32_t> arp(m + 1, 0), acol;
+    std::vector<double> aval;
+    if (m > 0) {
+      arp = fetch(A_rowptr, m + 1, mem, s);
+      const int64_t nnzA = arp[m];
+      if (nnzA < 0 || (nnzA > 0 && (!A_col || !A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
+      acol = fetch(A_col, nnzA, mem, s);
+      aval = fetch(A_val, nnzA, mem, s);
+    }
+    std::vector<double> hc = fetch(c, n, mem, s), hl = fetch(l, n, mem, s), hu = fetch(u, n, mem, s);
+    std::vector<double> hb = m > 0 ? fetch(b, m, mem, s) : std::vector<double>();
+    validate_csr("Q", n, n, qrp, qcol, qval);
+    validate_csr("A", m, n, arp, acol, aval);
+    for (int64_t j = 0; j < n; ++j) {
+      if (!std::isfinite(hc[j])) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
+      if (std::isnan(hl[j]) || std::isnan(hu[j]) || hl[j] > hu[j] || hl[j] == INFINITY || hu[j] == -INFINITY)
+        throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
+    }
+    for (int64_t i = 0; i < m; ++i)
+      if (!std::isfinite(hb[i])) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
+    std::vector<int32_t> trp, tcol;
+    std::vector<double> tval;
+    if (m > 0) transpose_csr(m, n, arp, acol, aval, trp, tcol, tval);
+    else trp.assign(n + 1, 0);
+
+    h = new pdqp_problem();
+    Work& w = h->w;
+    w.n = (int)n; w.m = (int)m; w.m_eq = (int)m_eq;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    upload_csr(h, w.Q, (int)n, qrp, qcol, qval, s);
+    upload_csr(h, w.A, (int)m, arp, acol, aval, s);
+    upload_csr(h, w.At, (int)n, trp, tcol, tval, s);
+    const size_t N = (size_t)n, M = (size_t)m;
+    w.c = dalloc<double>(h, N); w.l = dalloc<double>(h, N); w.u = dalloc<double>(h, N); w.b = dalloc<double>(h, M);
+    to_device(w.c, hc.data(), N, s); to_device(w.l, hl.data(), N, s); to_device(w.u, hu.data(), N, s);
+    to_device(w.b, hb.data(), M, s);
+    w.cs = dalloc<double>(h, N); w.ls = dalloc<double>(h, N); w.us = dalloc<double>(h, N); w.bs = dalloc<double>(h, M);
+    w.dsc = dalloc<double>(h, N + M); w.nu = dalloc<double>(h, N + M);
+    w.D2 = w.dsc; w.D1 = w.dsc + N;
+    w.x = dalloc<double>(h, N); w.xbar = dalloc<double>(h, N); w.xt = dalloc<double>(h, N);
+    w.xmd[0] = dalloc<double>(h, N); w.xmd[1] = dalloc<double>(h, N); w.ax = dalloc<double>(h, N);
+    w.y = dalloc<double>(h, M); w.ybar = dalloc<double>(h, M); w.ay = dalloc<double>(h, M);
+    w.pv[0] = dalloc<double>(h, N); w.pv[1] = dalloc<double>(h, N);
+    w.pq[0] = dalloc<double>(h, N); w.pq[1] = dalloc<double>(h, N); w.pw = dalloc<double>(h, M);
+    w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
+    w.tab = dalloc<StepEntry>(h, PDQP_MAX_CHECK);
+    w.st = dalloc<DevState>(h, 1);
+    w.stage_n = dalloc<double>(h, N); w.stage_m = dalloc<double>(h, M);
+    CK(cudaMallocHost(&w.st_host, sizeof(DevState)));
+    CK(cudaMemsetAsync(w.st, 0, sizeof(DevState), s));
+    CK(cudaStreamSynchronize(s));
+    *out = h;
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    g_create_error = f.msg;
+    if (h) pdqp_destroy(h);
+    return f.st;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    if (h) pdqp_destroy(h);
+    return PDQP_ERR_OOM;
+  }
+}
+
+pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t mem, void* stream) {
+  (void)r; (void)F; (void)mem; (void)stream;
+  if (!h) return PDQP_ERR_INVALID;
+  h->err = "low-rank Q is not available in this build";
+  return PDQP_ERR_INVALID;
+}
+
+pdqp_status pdqp_solve(pdqp_handle h, const pdqp_options* opt, const double* x0, const double* y0, double* x_out,
+                       double* y_out, pdqp_info* info, int32_t mem, void* stream) {
+  if (!h) return PDQP_ERR_INVALID;
+  pdqp_options o;
+  if (opt) o = *opt; else pdqp_default_options(&o);
+  try {
+    h->err.clear();
+    return solve_impl(h, o, x0, y0, x_out, y_out, info, mem, (cudaStream_t)stream);
+  } catch (const Fail& f) {
+    h->err = f.msg;
+    if (info) { std::memset(info, 0, sizeof(*info)); info->status = f.st; }
+    return f.st;
+  }
+}
+
+pdqp_status pdqp_solve_batch(int32_t count, const pdqp_handle* hs, const pdqp_options* opt,
+                             const double* const* x0, const double* const* y0, double* const* x_out,
+                             double* const* y_out, pdqp_info* infos, int32_t mem, void* stream) {
+  if (count < 0 || (count > 0 && !hs)) return PDQP_ERR_INVALID;
+  pdqp_status worst = PDQP_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    pdqp_status st = pdqp_solve(hs[i], opt, x0 ? x0[i] : nullptr, y0 ? y0[i] : nullptr,
+                                x_out ? x_out[i] : nullptr, y_out ? y_out[i] : nullptr,
+                                infos ? infos + i : nullptr, mem, stream);
+    if (st > worst) worst = st;
+  }
+  return worst;
+}
+
+pdqp_status pdqp_get_state(pdqp_handle h, double* x, double* y, double* xbar, double* ybar, int32_t mem,
+                           void* stream) {
+  if (!h) return PDQP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  Work& w = h->w;
+  try {
+    for (auto p : {x, y, xbar, ybar}) check_space(p, mem, "state output");
+    if (mem == PDQP_MEM_DEVICE) {
+      pdqp::write_state(w, x, y, xbar, ybar, false, s);
+    } else {
+      double* outs[4] = {x, y, xbar, ybar};
+      for (int k = 0; k < 2; ++k) {
+        double* hx = outs[2 * k];
+        double* hy = outs[2 * k + 1];
+        if (!hx && !hy) continue;
+        if (k == 0) pdqp::write_state(w, w.stage_n, w.stage_m, nullptr, nullptr, false, s);
+        else pdqp::write_state(w, nullptr, nullptr, w.stage_n, w.stage_m, false, s);
+        if (hx) CK(cudaMemcpyAsync(hx, w.stage_n, w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (hy && w.m) CK(cudaMemcpyAsync(hy, w.stage_m, w.m * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      }
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    h->err = f.msg;
+    return f.st;
+  }
+}
+
+pdqp_status pdqp_kkt(pdqp_handle h, const double* x, const double* y, double* parts, int32_t mem, void* stream) {
+  if (!h || !x || !parts || (h->w.m > 0 && !y)) return PDQP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  Work& w = h->w;
+  try {
+    check_space(x, mem, "x");
+    check_space(y, mem, "y");
+    const double* dx = x;
+    const double* dy = y;
+    if (mem == PDQP_MEM_HOST) {
+      to_device(w.stage_n, x, w.n, s);
+      dx = w.stage_n;
+      if (w.m) { to_device(w.stage_m, y, w.m, s); dy = w.stage_m; }
+    }
+    pdqp::eval_kkt_user(w, dx, dy ? dy : w.stage_m, s);
+    CK(cudaGetLastError());
+    sync_state(h, s);
+    for (int k = 0; k < 6; ++k) parts[k] = w.st_host->out_parts[k];
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    h->err = f.msg;
+    return f.st;
+  }
+}
+
+pdqp_status pdqp_get_sizes(pdqp_handle h, int64_t* n, int64_t* m, int64_t* m_eq, int64_t* nnz_Q, int64_t* nnz_A) {
+  if (!h) return PDQP_ERR_INVALID;
+  if (n) *n = h->w.n;
+  if (m) *m = h->w.m;
+  if (m_eq) *m_eq = h->w.m_eq;
+  if (nnz_Q) *nnz_Q = h->w.Q.nnz;
+  if (nnz_A) *nnz_A = h->w.A.nnz;
+  return PDQP_OK;
+}
+
+const char* pdqp_last_error(pdqp_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void pdqp_destroy(pdqp_handle h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->w.st_host) cudaFreeHost(h->w.st_host);
+  delete h;
+}
+
+int64_t pdqp_launch_count(void) { return pdqp::g_launches; }
+
+}  // extern "C"

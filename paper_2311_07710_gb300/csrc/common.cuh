@@ -1,0 +1,112 @@
+// Shared device-side definitions of the rAPDHG kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define PDQP_MAX_CHECK 4096   // longest check period (length of the step table)
+#define PDQP_RED_BLOCKS 304   // partial-sum blocks of the reductions (2 x 152 SMs)
+
+enum { ST_RUNNING = 0, ST_OPTIMAL = 1, ST_ITER_LIMIT = 2, ST_NUMERICAL = 3 };
+
+// Step scalars of one inner iteration, written by the decision kernel for the
+// next chunk of `check_period` iterations (Algorithm 1 with Theorem 1's beta,
+// theta and the Section 6 step size).
+struct StepEntry {
+  double tau_p;          // primal step (eta/omega, or Theorem 1's eta_k)
+  double sigma_d;        // dual step (eta*omega, or Theorem 1's tau_k)
+  double inv_beta;       // 1/beta_k: weight of the new iterate in the averages
+  double inv_beta_next;  // 1/beta_{k+1}: forms x_md of the next iteration
+  double theta_next;     // theta_{k+1}: forms the extrapolated point of the next iteration
+  float tau_p_f, sigma_d_f, inv_beta_f, inv_beta_next_f, theta_next_f;
+};
+
+// Scalar solver state, resident in device memory so that the iteration runs
+// without host round trips.
+struct DevState {
+  double omega;          // primal weight
+  double eta_last;       // eta of the last tabulated iteration
+  double anchor_kkt;     // relKKT(z^{n,0})
+  double prev_cand_kkt;  // candidate relKKT of the previous check in this epoch
+  double normA, normQ;
+  long long k_epoch;     // inner iteration counter k of the current epoch
+  long long k_total;     // total iterations
+  long long restarts;
+  int status;            // ST_*
+  int has_prev;          // prev_cand_kkt is valid
+  int restart;           // the last check restarted
+  int cand_avg;          // the candidate of the last check is the average
+  int out_avg;           // the returned iterate is the average
+  int pad0;
+  double parts[2][6];    // r_primal, r_dual, r_gap, rel_kkt, primal_obj, dual_obj (cur, avg)
+  double out_parts[6];
+  double bnorm_inf, cnorm_inf;   // ||b||_inf, ||c||_inf of the original data
+  // power iteration
+  double pi_lam[2], pi_lam_prev[2], pi_inv_norm[2];
+  int pi_done[2];
+  int pi_iters;
+  int pad1;
+};
+
+// Constant parameters of one solve.
+struct SolveParams {
+  int step_rule, restart_rule, accelerate, fixed_K, check_period, mixed;
+  long long max_iter;
+  double eps, beta_suff, beta_nec, beta_art, pw_theta, eps_zero, power_tol;
+  int power_iters;
+};
+
+// Device view of one CSR matrix.
+template <typename V>
+struct Csr {
+  const int* __restrict__ rp;
+  const int* __restrict__ col;
+  const V* __restrict__ val;
+};
+
+// Sum over an aligned group of L lanes (L a power of two <= 32); every lane
+// of the warp executes it.
+template <int L, typename T>
+__device__ __forceinline__ T group_sum(T s) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, L);
+  return s;
+}
+
+// NaN-propagating max.
+__device__ __forceinline__ double nmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Block reduction of NF fields (sum or NaN-propagating max per field); the
+// result is valid in thread 0.  blockDim.x must be a multiple of 32, <= 1024.
+template <int NF>
+__device__ __forceinline__ void block_reduce(double (&v)[NF], const bool (&is_max)[NF]) {
+  __shared__ double sh[32][NF];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double t = __shfl_xor_sync(0xffffffffu, v[f], o);
+      v[f] = is_max[f] ? nmax(v[f], t) : v[f] + t;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sh[w][f] = v[f];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double t = lane < nw ? sh[lane][f] : (is_max[f] ? 0.0 : 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double s = __shfl_xor_sync(0xffffffffu, t, o);
+        t = is_max[f] ? nmax(t, s) : t + s;
+      }
+      v[f] = t;
+    }
+  }
+  __syncthreads();
+}

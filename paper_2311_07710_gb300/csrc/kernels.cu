@@ -1,0 +1,843 @@
+// Device kernels of the rAPDHG solver (sm_103a).
+//
+// One inner iteration of Algorithm 1 (Section 2) is two fused kernels:
+//   k_dual   : rows of A   -- v = A x_tilde, y+ = proj_Y(y - sigma (v - b)),
+//              y_bar+ = (1 - 1/beta) y_bar + y+/beta
+//   k_primal : rows of Q and of A' -- g = Q x_md + c - A'y+,
+//              x+ = proj_[l,u](x - tau g), x_bar+ = (1 - 1/beta) x_bar + x+/beta,
+//              and the next iteration's x_md and x_tilde
+// Every `check_period` iterations k_kkt_m / k_kkt_n reduce, in float64, the
+// relative KKT error of Section 5 for the current and the averaged iterate,
+// k_decide applies the Section 6 restart rule and tabulates the next step
+// sizes, and k_restart_apply moves the iterate to the restart candidate.
+#include <stdio.h>
+
+#include "solver.h"
+
+namespace pdqp {
+
+long long g_launches = 0;
+
+// Launch a kernel and count it.
+template <typename... KArgs, typename... Args>
+static inline void launch(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                          Args... args) {
+  if (grid <= 0) return;
+  kern<<<grid, block, smem, s>>>(args...);
+  ++g_launches;
+}
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// --------------------------------------------------------------------------
+// CSR row helpers: L lanes of a warp cooperate on one row
+// --------------------------------------------------------------------------
+template <int L, typename V, typename X, typename ACC>
+__device__ __forceinline__ ACC row_dot_partial(const Csr<V>& M, const X* __restrict__ x, int beg,
+                                               int end, int lane) {
+  ACC s = ACC(0);
+  for (int k = beg + lane; k < end; k += L) s = fma((ACC)M.val[k], (ACC)__ldg(x + M.col[k]), s);
+  return s;
+}
+
+// --------------------------------------------------------------------------
+// Preconditioning (Section 5 "Preprocessing"): norms of the rows of
+// D K D with K = [[Q, A'], [A, 0]], then d_j /= sqrt(norm_j)
+// --------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(256) k_scale_norms(Csr<double> Q, Csr<double> At, Csr<double> A,
+                                                     const double* __restrict__ d,
+                                                     double* __restrict__ nu, int n, int m, int kind) {
+  const int rows_per_block = 256 / L;
+  const int row = blockIdx.x * rows_per_block + threadIdx.x / L;
+  const int lane = threadIdx.x % L;
+  const bool valid = row < n + m;
+  double acc = 0.0;
+  if (valid) {
+    const double dr = d[row];
+    auto take = [&](double a) {
+      if (kind == 0) acc = fmax(acc, a);
+      else if (kind == 1) acc += a * a;
+      else acc += a;
+    };
+    if (row < n) {
+      for (int k = Q.rp[row] + lane; k < Q.rp[row + 1]; k += L) take(fabs(Q.val[k]) * dr * d[Q.col[k]]);
+      if (m > 0)
+        for (int k = At.rp[row] + lane; k < At.rp[row + 1]; k += L)
+          take(fabs(At.val[k]) * dr * d[n + At.col[k]]);
+    } else {
+      const int i = row - n;
+      for (int k = A.rp[i] + lane; k < A.rp[i + 1]; k += L) take(fabs(A.val[k]) * dr * d[A.col[k]]);
+    }
+  }
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) {
+    double t = __shfl_xor_sync(0xffffffffu, acc, o, L);
+    acc = (kind == 0) ? fmax(acc, t) : acc + t;
+  }
+  if (valid && lane == 0) nu[row] = (kind == 1) ? sqrt(acc) : acc;
+}
+
+__global__ void k_scale_update(double* __restrict__ d, const double* __restrict__ nu, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    const double v = nu[i];
+    d[i] = d[i] / sqrt(v > 0.0 ? v : 1.0);
+  }
+}
+
+__global__ void k_fill(double* __restrict__ p, double v, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) p[i] = v;
+}
+
+// scaled value = (drow[r] * val) * dcol[c]  (or (dcol[c] * val) * drow[r] when `tr`,
+// which makes the stored A~' bitwise equal to the entries of A~)
+template <int L>
+__global__ void __launch_bounds__(256) k_scale_csr(int rows, Csr<double> M, double* __restrict__ out,
+                                                   float* __restrict__ out_f,
+                                                   const double* __restrict__ drow,
+                                                   const double* __restrict__ dcol, int tr) {
+  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
+  const int lane = threadIdx.x % L;
+  if (row >= rows) return;
+  const double dr = drow[row];
+  for (int k = M.rp[row] + lane; k < M.rp[row + 1]; k += L) {
+    const double dc = dcol[M.col[k]];
+    const double v = tr ? (dc * M.val[k]) * dr : (dr * M.val[k]) * dc;
+    out[k] = v;
+    if (out_f) out_f[k] = (float)v;
+  }
+}
+
+// c~ = D2 c, l~ = l / D2, u~ = u / D2 (n);  b~ = D1 b (m)
+__global__ void k_scale_vectors(int n, int m, const double* __restrict__ D1, const double* __restrict__ D2,
+                                const double* __restrict__ c, const double* __restrict__ b,
+                                const double* __restrict__ l, const double* __restrict__ u,
+                                double* __restrict__ cs, double* __restrict__ bs, double* __restrict__ ls,
+                                double* __restrict__ us) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double d = D2[i];
+    cs[i] = d * c[i];
+    ls[i] = l[i] / d;
+    us[i] = u[i] / d;
+  }
+  if (i < m) bs[i] = D1[i] * b[i];
+}
+
+// --------------------------------------------------------------------------
+// Power iteration for ||A~||_2 (on A~'A~) and ||Q~||_2, both from the
+// normalised all-ones vector; v_t = u_t * inv_norm, stop when the Rayleigh
+// quotient changes by <= tol relative.
+// --------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(256) k_pi_m(Csr<double> A, const double* __restrict__ u,
+                                              double* __restrict__ w, int m, const DevState* __restrict__ st) {
+  if (st->pi_done[0]) return;
+  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
+  const int lane = threadIdx.x % L;
+  const bool valid = row < m;
+  double s = valid ? row_dot_partial<L, double, double, double>(A, u, A.rp[row], A.rp[row + 1], lane) : 0.0;
+  s = group_sum<L>(s);
+  if (valid && lane == 0) w[row] = s * st->pi_inv_norm[0];
+}
+
+// u_new = A~' w ; z_new = Q~ v_Q ; block partials of v.u_new, |u_new|^2, vQ.z_new, |z_new|^2
+template <int L>
+__global__ void __launch_bounds__(256) k_pi_n(Csr<double> At, Csr<double> Q, const double* __restrict__ w,
+                                              const double* __restrict__ u_old, double* __restrict__ u_new,
+                                              const double* __restrict__ q_old, double* __restrict__ q_new,
+                                              int n, int m, const DevState* __restrict__ st,
+                                              double* __restrict__ part) {
+  const bool doA = !st->pi_done[0] && m > 0;
+  const bool doQ = !st->pi_done[1];
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  const int rows_per_block = 256 / L;
+  const int lane = threadIdx.x % L;
+  const double sa = st->pi_inv_norm[0], sq = st->pi_inv_norm[1];
+  for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
+    const int row = base + threadIdx.x / L;
+    const bool valid = row < n;
+    double a = 0.0, q = 0.0;
+    if (valid && doA) a = row_dot_partial<L, double, double, double>(At, w, At.rp[row], At.rp[row + 1], lane);
+    if (valid && doQ) q = row_dot_partial<L, double, double, double>(Q, q_old, Q.rp[row], Q.rp[row + 1], lane);
+    a = group_sum<L>(a);
+    q = group_sum<L>(q);
+    if (valid && lane == 0) {
+      if (doA) {
+        u_new[row] = a;
+        f[0] += (u_old[row] * sa) * a;
+        f[1] += a * a;
+      }
+      if (doQ) {
+        const double z = q * sq;     // Q~ (q_old * sq)
+        q_new[row] = z;
+        f[2] += (q_old[row] * sq) * z;
+        f[3] += z * z;
+      }
+    }
+  }
+  const bool is_max[4] = {false, false, false, false};
+  block_reduce<4>(f, is_max);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) part[blockIdx.x * 32 + k] = f[k];
+}
+
+__global__ void k_pi_update(DevState* __restrict__ st, const double* __restrict__ part, int nblk,
+                            double tol, int have_rows) {
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int k = 0; k < 4; ++k) f[k] += part[b * 32 + k];
+  const bool is_max[4] = {false, false, false, false};
+  block_reduce<4>(f, is_max);
+  if (threadIdx.x != 0) return;
+  st->pi_iters += 1;
+  for (int which = 0; which < 2; ++which) {
+    if (st->pi_done[which]) continue;
+    if (which == 0 && !have_rows) { st->pi_done[0] = 1; st->pi_lam[0] = 0.0; continue; }
+    const double lam = f[2 * which], nw = sqrt(f[2 * which + 1]);
+    st->pi_lam[which] = lam;
+    if (nw == 0.0) { st->pi_lam[which] = 0.0; st->pi_done[which] = 1; continue; }
+    if (fabs(lam - st->pi_lam_prev[which]) <= tol * fabs(lam)) { st->pi_done[which] = 1; continue; }
+    st->pi_lam_prev[which] = lam;
+    st->pi_inv_norm[which] = 1.0 / nw;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Start point: x = proj_X(x0 / D2), y = proj_Y(y0 / D1), zeros by default
+// (Section 5 "Algorithms"); averages, x_md, x_tilde and anchors = start.
+// --------------------------------------------------------------------------
+__global__ void k_init_iterates(int n, int m, int m_eq, const double* __restrict__ x0,
+                                const double* __restrict__ y0, const double* __restrict__ D1,
+                                const double* __restrict__ D2, const double* __restrict__ ls,
+                                const double* __restrict__ us, double* x, double* xbar, double* xmd0,
+                                double* xt, double* ax, double* y, double* ybar, double* ay) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = x0 ? x0[i] / D2[i] : 0.0;
+    v = fmin(fmax(v, ls[i]), us[i]);
+    x[i] = v; xbar[i] = v; xmd0[i] = v; xt[i] = v; ax[i] = v;
+  }
+  if (i < m) {
+    double v = y0 ? y0[i] / D1[i] : 0.0;
+    if (i >= m_eq) v = fmax(v, 0.0);
+    y[i] = v; ybar[i] = v; ay[i] = v;
+  }
+}
+
+// --------------------------------------------------------------------------
+// One inner iteration of Algorithm 1: the dual half-step (rows of A)
+// --------------------------------------------------------------------------
+template <typename V>
+struct DualArgs {
+  Csr<V> A;
+  const V* __restrict__ xt;      // extrapolated primal point x_tilde
+  V* __restrict__ y;
+  V* __restrict__ ybar;
+  const V* __restrict__ b;
+  const V* __restrict__ ylo;     // lower bound of inequality duals (mixed mode shift) or null (0)
+  const StepEntry* __restrict__ tab;
+  int m, m_eq;
+};
+
+template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
+template <> __device__ __forceinline__ double step_sigma<double>(const StepEntry& e) { return e.sigma_d; }
+template <> __device__ __forceinline__ float step_sigma<float>(const StepEntry& e) { return e.sigma_d_f; }
+template <typename V> __device__ __forceinline__ V step_tau(const StepEntry& e);
+template <> __device__ __forceinline__ double step_tau<double>(const StepEntry& e) { return e.tau_p; }
+template <> __device__ __forceinline__ float step_tau<float>(const StepEntry& e) { return e.tau_p_f; }
+template <typename V> __device__ __forceinline__ V step_ib(const StepEntry& e);
+template <> __device__ __forceinline__ double step_ib<double>(const StepEntry& e) { return e.inv_beta; }
+template <> __device__ __forceinline__ float step_ib<float>(const StepEntry& e) { return e.inv_beta_f; }
+template <typename V> __device__ __forceinline__ V step_ibn(const StepEntry& e);
+template <> __device__ __forceinline__ double step_ibn<double>(const StepEntry& e) { return e.inv_beta_next; }
+template <> __device__ __forceinline__ float step_ibn<float>(const StepEntry& e) { return e.inv_beta_next_f; }
+template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
+template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
+template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
+
+template <int L, typename V>
+__global__ void __launch_bounds__(256) k_dual(DualArgs<V> a, int j) {
+  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
+  const int lane = threadIdx.x % L;
+  const bool valid = row < a.m;
+  V s = V(0);
+  if (valid) s = row_dot_partial<L, V, V, V>(a.A, a.xt, a.A.rp[row], a.A.rp[row + 1], lane);
+  s = group_sum<L>(s);
+  if (valid && lane == 0) {
+    const StepEntry& e = a.tab[j];
+    const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
+    V yn = a.y[row] - sigma * (s - a.b[row]);
+    if (row >= a.m_eq) yn = a.ylo ? fmax(yn, a.ylo[row]) : fmax(yn, V(0));
+    a.ybar[row] = (V(1) - ib) * a.ybar[row] + ib * yn;
+    a.y[row] = yn;
+  }
+}
+
+// --------------------------------------------------------------------------
+// One inner iteration of Algorithm 1: the primal half-step (rows of Q and A')
+// --------------------------------------------------------------------------
+template <typename V>
+struct PrimalArgs {
+  Csr<V> Q, At;
+  const V* __restrict__ xmd_in;  // x_md of this iteration
+  V* __restrict__ xmd_out;       // x_md of the next iteration
+  const V* __restrict__ y;       // y^{k+1}
+  V* __restrict__ x;
+  V* __restrict__ xbar;
+  V* __restrict__ xt;            // x_tilde of the next iteration
+  const V* __restrict__ c;
+  const V* __restrict__ l;
+  const V* __restrict__ u;
+  const StepEntry* __restrict__ tab;
+  int n, m;
+};
+
+template <int L, typename V>
+__global__ void __launch_bounds__(256) k_primal(PrimalArgs<V> a, int j) {
+  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
+  const int lane = threadIdx.x % L;
+  const bool valid = row < a.n;
+  V s = V(0);
+  if (valid) {
+    s = row_dot_partial<L, V, V, V>(a.Q, a.xmd_in, a.Q.rp[row], a.Q.rp[row + 1], lane);
+    if (a.m > 0) s -= row_dot_partial<L, V, V, V>(a.At, a.y, a.At.rp[row], a.At.rp[row + 1], lane);
+  }
+  s = group_sum<L>(s);
+  if (valid && lane == 0) {
+    const StepEntry& e = a.tab[j];
+    const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
+    const V xo = a.x[row];
+    const V g = s + a.c[row];
+    const V xn = fmin(fmax(xo - tau * g, a.l[row]), a.u[row]);
+    const V xb = (V(1) - ib) * a.xbar[row] + ib * xn;
+    a.xbar[row] = xb;
+    a.xmd_out[row] = (V(1) - ibn) * xb + ibn * xn;
+    a.xt[row] = xn + thn * (xn - xo);
+    a.x[row] = xn;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Relative KKT error (Section 5 "Progress metric", equality/bound form) in
+// float64, for NIT iterates at once, measured on the original problem:
+// (Ax)_i = (A~ x~)_i / D1_i, (Qx)_j = (Q~ x~)_j / D2_j, (A'y)_j = (A~' y~)_j / D2_j.
+// Partial sums go to part[block][field]; k_decide finishes them.
+// --------------------------------------------------------------------------
+struct KktArgs {
+  Csr<double> A, Q, At;                 // scaled (or original with D = null)
+  const double* x[2];                   // float64 iterates (scaled space)
+  const double* y[2];
+  const float* dx[2];                   // mixed mode: iterate = base + delta
+  const float* dy[2];
+  const double* xhi;
+  const double* yhi;
+  const double* ax;                     // anchors (scaled); null: delta from base (mixed)
+  const double* ay;
+  const double* D1;                     // null = 1
+  const double* D2;
+  const double *b, *c, *l, *u;          // original data
+  double* prodAx[2];                    // optional: store A~x~ etc. (mixed-mode correction)
+  double* prodQx[2];
+  double* prodATy[2];
+  double* part;
+  int n, m, m_eq;
+};
+
+template <bool MIXED>
+__device__ __forceinline__ double it_x(const KktArgs& a, int it, int k) {
+  if (MIXED) return a.xhi[k] + (double)a.dx[it][k];
+  return a.x[it][k];
+}
+template <bool MIXED>
+__device__ __forceinline__ double it_y(const KktArgs& a, int it, int k) {
+  if (MIXED) return a.yhi[k] + (double)a.dy[it][k];
+  return a.y[it][k];
+}
+
+template <int L, int NIT, bool MIXED>
+__global__ void __launch_bounds__(256) k_kkt_m(KktArgs a) {
+  // fields: it*4 + {0 max|viol|, 1 max|Ax|, 2 b'y, 3 |dy|^2}, 8: max|b|
+  double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int rpb = 256 / L, lane = threadIdx.x % L;
+  for (int base = blockIdx.x * rpb; base < a.m; base += gridDim.x * rpb) {
+    const int row = base + threadIdx.x / L;
+    const bool valid = row < a.m;
+    double s[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) s[it] = 0.0;
+    if (valid) {
+      for (int k = a.A.rp[row] + lane; k < a.A.rp[row + 1]; k += L) {
+        const double v = a.A.val[k];
+        const int cidx = a.A.col[k];
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) s[it] = fma(v, it_x<MIXED>(a, it, cidx), s[it]);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) s[it] = group_sum<L>(s[it]);
+    if (valid && lane == 0) {
+      const double d1 = a.D1 ? a.D1[row] : 1.0;
+      const double bi = a.b[row];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (a.prodAx[it]) a.prodAx[it][row] = s[it];
+        const double Ax = s[it] / d1;
+        const double viol = row < a.m_eq ? fabs(Ax - bi) : fmax(bi - Ax, 0.0);
+        f[it * 4 + 0] = nmax(f[it * 4 + 0], viol);
+        f[it * 4 + 1] = nmax(f[it * 4 + 1], fabs(Ax));
+        const double yt = it_y<MIXED>(a, it, row);
+        f[it * 4 + 2] += bi * (d1 * yt);
+        const double dy = MIXED ? (double)a.dy[it][row] : (a.ay ? yt - a.ay[row] : 0.0);
+        f[it * 4 + 3] += dy * dy;
+      }
+      f[8] = nmax(f[8], fabs(bi));
+    }
+  }
+  const bool is_max[9] = {true, true, false, false, true, true, false, false, true};
+  block_reduce<9>(f, is_max);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 9; ++k) a.part[blockIdx.x * 32 + k] = f[k];
+}
+
+template <int L, int NIT, bool MIXED>
+__global__ void __launch_bounds__(256) k_kkt_n(KktArgs a) {
+  // fields (offset 9): it*7 + {0 max|res|, 1 max|Qx|, 2 max|A'y|, 3 x'Qx, 4 c'x,
+  // 5 sum(l lam+ - u lam-), 6 |dx|^2}, 14: max|c|
+  double f[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) f[k] = 0.0;
+  const int rpb = 256 / L, lane = threadIdx.x % L;
+  for (int base = blockIdx.x * rpb; base < a.n; base += gridDim.x * rpb) {
+    const int row = base + threadIdx.x / L;
+    const bool valid = row < a.n;
+    double sq[NIT], sa[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) { sq[it] = 0.0; sa[it] = 0.0; }
+    if (valid) {
+      for (int k = a.Q.rp[row] + lane; k < a.Q.rp[row + 1]; k += L) {
+        const double v = a.Q.val[k];
+        const int cidx = a.Q.col[k];
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) sq[it] = fma(v, it_x<MIXED>(a, it, cidx), sq[it]);
+      }
+      if (a.m > 0)
+        for (int k = a.At.rp[row] + lane; k < a.At.rp[row + 1]; k += L) {
+          const double v = a.At.val[k];
+          const int cidx = a.At.col[k];
+#pragma unroll
+          for (int it = 0; it < NIT; ++it) sa[it] = fma(v, it_y<MIXED>(a, it, cidx), sa[it]);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) { sq[it] = group_sum<L>(sq[it]); sa[it] = group_sum<L>(sa[it]); }
+    if (valid && lane == 0) {
+      const double d2 = a.D2 ? a.D2[row] : 1.0;
+      const double cj = a.c[row], lj = a.l[row], uj = a.u[row];
+      const bool lf = isfinite(lj), uf = isfinite(uj);
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (a.prodQx[it]) { a.prodQx[it][row] = sq[it]; a.prodATy[it][row] = sa[it]; }
+        const double Qx = sq[it] / d2, ATy = sa[it] / d2;
+        const double xt = it_x<MIXED>(a, it, row);
+        const double xj = d2 * xt;
+        const double g = Qx + cj - ATy;
+        const double lam = (lf && uf) ? g : (lf ? fmax(g, 0.0) : (uf ? fmin(g, 0.0) : 0.0));
+        double* fi = f + it * 7;
+        fi[0] = nmax(fi[0], fabs(g - lam));
+        fi[1] = nmax(fi[1], fabs(Qx));
+        fi[2] = nmax(fi[2], fabs(ATy));
+        fi[3] += xj * Qx;
+        fi[4] += cj * xj;
+        fi[5] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+        const double dx = MIXED ? (double)a.dx[it][row] : (a.ax ? xt - a.ax[row] : 0.0);
+        fi[6] += dx * dx;
+      }
+      f[14] = nmax(f[14], fabs(cj));
+    }
+  }
+  const bool is_max[15] = {true, true, true, false, false, false, false,
+                           true, true, true, false, false, false, false, true};
+  block_reduce<15>(f, is_max);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 15; ++k) a.part[blockIdx.x * 32 + 9 + k] = f[k];
+}
+
+// relKKT parts from the reduced fields of iterate `it`
+__device__ void kkt_from_fields(const double* F, int it, double* out) {
+  const double maxviol = F[it * 4 + 0], maxAx = F[it * 4 + 1], by = F[it * 4 + 2];
+  const double maxb = F[8];
+  const double* G = F + 9 + it * 7;
+  const double maxres = G[0], maxQx = G[1], maxATy = G[2], xQx = G[3], cx = G[4], bterm = G[5];
+  const double maxc = F[23];
+  const double rp = maxviol / (1.0 + fmax(maxAx, maxb));
+  const double rd = maxres / (1.0 + fmax(fmax(maxQx, maxATy), maxc));
+  const double pobj = 0.5 * xQx + cx;
+  const double dobj = -0.5 * xQx + by + bterm;
+  const double rg = fabs(pobj - dobj) / (1.0 + fmax(fabs(pobj), fabs(dobj)));
+  double rel = nmax(nmax(rp, rd), rg);
+  if (pobj != pobj || dobj != dobj) rel = pobj - dobj;   // NaN
+  out[0] = rp; out[1] = rd; out[2] = rg; out[3] = rel; out[4] = pobj; out[5] = dobj;
+}
+
+// reduce the partials of k_kkt_m / k_kkt_n (fields 0..23) in thread 0
+__device__ void reduce_kkt_partials(const double* __restrict__ part, int nblk, double* F) {
+  double f[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) f[k] = 0.0;
+  const bool is_max[24] = {true, true, false, false, true, true, false, false, true,
+                           true, true, true, false, false, false, false,
+                           true, true, true, false, false, false, false, true};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 24; ++k) f[k] = is_max[k] ? nmax(f[k], part[b * 32 + k]) : f[k] + part[b * 32 + k];
+  block_reduce<24>(f, is_max);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 24; ++k) F[k] = f[k];
+}
+
+// Section 6 step size eta^{n,k}
+__device__ double pdqp_eta(long long k, double eta_prev, double nQ, double nA, double omega) {
+  const double q = nQ / omega;
+  if (k == 0) return 1.98 / (q + sqrt(4.0 * (nA * nA) + q * q));
+  const double kk = (double)(k + 2);
+  const double bound = 0.99 * kk / (q + sqrt((nA * nA) * (kk * kk) + q * q));
+  return fmin((1.0 + 1.0 / (double)k) * eta_prev, bound);
+}
+
+// Tabulate the step scalars of the next `C` inner iterations, k = k_epoch + j.
+__device__ void fill_steps(DevState& S, const SolveParams& p, StepEntry* tab) {
+  double eta = S.eta_last;
+  const long long k0 = S.k_epoch;
+  for (int j = 0; j < p.check_period; ++j) {
+    const long long k = k0 + j;
+    double beta = 1.0, beta1 = 1.0, theta1 = 1.0;
+    if (p.accelerate) {
+      beta = (double)(k + 2) / 2.0;
+      beta1 = (double)(k + 3) / 2.0;
+      theta1 = (double)(k + 1) / ((double)(k + 1) + 1.0);
+    }
+    double tau, sig;
+    if (p.step_rule == 1) {   // Theorem 1
+      tau = (double)(k + 1) / (2.0 * (S.normQ + p.fixed_K * S.normA));
+      sig = (double)(k + 1) / (2.0 * p.fixed_K * S.normA);
+    } else {
+      eta = pdqp_eta(p.accelerate ? k : 0, eta, S.normQ, S.normA, S.omega);
+      tau = eta / S.omega;
+      sig = eta * S.omega;
+    }
+    StepEntry e;
+    e.tau_p = tau; e.sigma_d = sig; e.inv_beta = 1.0 / beta; e.inv_beta_next = 1.0 / beta1;
+    e.theta_next = theta1;
+    e.tau_p_f = (float)tau; e.sigma_d_f = (float)sig; e.inv_beta_f = (float)e.inv_beta;
+    e.inv_beta_next_f = (float)e.inv_beta_next; e.theta_next_f = (float)theta1;
+    tab[j] = e;
+  }
+  S.eta_last = eta;
+}
+
+// mode 0: evaluate z^{0,0} (anchor, maybe already optimal); mode 1: a check
+// after `chunk_len` more iterations (Section 6 restart rule, termination
+// eq. (terminate), iteration limit).
+__global__ void k_decide(DevState* __restrict__ st, const double* __restrict__ part, int nblk,
+                         StepEntry* __restrict__ tab, SolveParams p, int mode, long long chunk_len) {
+  __shared__ double F[24];
+  reduce_kkt_partials(part, nblk, F);
+  if (threadIdx.x != 0) return;
+  DevState& S = *st;
+  double P[2][6];
+  kkt_from_fields(F, 0, P[0]);
+  kkt_from_fields(F, 1, P[1]);
+  for (int it = 0; it < 2; ++it)
+    for (int k = 0; k < 6; ++k) S.parts[it][k] = P[it][k];
+  S.restart = 0;
+  if (mode == 0) {
+    S.anchor_kkt = P[0][3];
+    S.has_prev = 0;
+    S.k_epoch = 0; S.k_total = 0; S.restarts = 0;
+    S.out_avg = 0;
+    for (int k = 0; k < 6; ++k) S.out_parts[k] = P[0][k];
+    const double r = P[0][3];
+    S.status = (r != r) ? ST_NUMERICAL : (r <= p.eps ? ST_OPTIMAL : ST_RUNNING);
+    fill_steps(S, p, tab);
+    return;
+  }
+  S.k_total += chunk_len;
+  S.k_epoch += chunk_len;
+  const double kc = P[0][3], ka = P[1][3];
+  const int cand_avg = (kc < ka) ? 0 : 1;          // GetRestartCandidate, ties -> average
+  const double cand = cand_avg ? ka : kc;
+  S.out_avg = cand_avg;
+  for (int k = 0; k < 6; ++k) S.out_parts[k] = P[cand_avg][k];
+  if (kc != kc || ka != ka) { S.status = ST_NUMERICAL; return; }
+  if (cand <= p.eps) { S.status = ST_OPTIMAL; return; }
+  if (S.k_total >= p.max_iter) { S.status = ST_ITER_LIMIT; return; }
+  int restart = 0, to_avg = cand_avg;
+  double new_anchor = cand;
+  if (p.restart_rule == 0) {
+    restart = (cand <= p.beta_suff * S.anchor_kkt) ||
+              (cand <= p.beta_nec * S.anchor_kkt && S.has_prev && cand > S.prev_cand_kkt) ||
+              ((double)S.k_epoch >= p.beta_art * (double)S.k_total);
+  } else if (p.restart_rule == 1) {
+    to_avg = 1; new_anchor = ka; restart = ka <= 0.5 * S.anchor_kkt;
+  } else if (p.restart_rule == 2) {
+    to_avg = 1; new_anchor = ka; restart = S.k_epoch >= p.fixed_K;
+  }
+  if (!restart) {
+    S.prev_cand_kkt = (p.restart_rule == 0) ? cand : new_anchor;
+    S.has_prev = 1;
+  } else {
+    const double dx2 = F[9 + to_avg * 7 + 6], dy2 = F[to_avg * 4 + 3];
+    if (p.step_rule == 0) {   // PrimalWeightUpdate
+      const double dx = sqrt(dx2), dy = sqrt(dy2);
+      if (dx > p.eps_zero && dy > p.eps_zero)
+        S.omega = exp(p.pw_theta * log(dy / dx) + (1.0 - p.pw_theta) * log(S.omega));
+    }
+    S.restarts += 1;
+    S.anchor_kkt = new_anchor;
+    S.has_prev = 0;
+    S.k_epoch = 0;
+    S.restart = 1;
+    S.cand_avg = to_avg;
+  }
+  fill_steps(S, p, tab);
+}
+
+// Restart of the outer loop from the candidate: x = x_bar = x_md = x_tilde = x_c,
+// y = y_bar = y_c, anchors = z_c (Algorithm 1 "restart the outer loop").
+__global__ void k_restart_apply(const DevState* __restrict__ st, int n, int m, double* x, double* xbar,
+                                double* xmd0, double* xt, double* ax, double* y, double* ybar, double* ay) {
+  if (st->status != ST_RUNNING || !st->restart) return;
+  const int ca = st->cand_avg;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const double v = ca ? xbar[i] : x[i];
+      x[i] = v; xbar[i] = v; xmd0[i] = v; xt[i] = v; ax[i] = v;
+    }
+    if (i < m) {
+      const double v = ca ? ybar[i] : y[i];
+      y[i] = v; ybar[i] = v; ay[i] = v;
+    }
+  }
+}
+
+// Original-space output of the returned iterate (or of the raw state).
+__global__ void k_unscale_out(int n, int m, const double* __restrict__ D1, const double* __restrict__ D2,
+                              const double* __restrict__ xs0, const double* __restrict__ xs1,
+                              const double* __restrict__ ys0, const double* __restrict__ ys1,
+                              const DevState* __restrict__ st, int pick, double* x_out, double* y_out) {
+  const int sel = pick < 0 ? st->out_avg : pick;
+  const double* xs = sel ? xs1 : xs0;
+  const double* ys = sel ? ys1 : ys0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x_out && i < n) x_out[i] = D2[i] * xs[i];
+  if (y_out && i < m) y_out[i] = D1[i] * ys[i];
+}
+
+// ==========================================================================
+// Host-side launchers
+// ==========================================================================
+static int pick_lanes(long long nnz, long long rows) {
+  const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  int L = 2;
+  while (L < 32 && L < avg) L <<= 1;
+  return L;
+}
+
+#define DISPATCH_L(L, ...)                               \
+  switch (L) {                                           \
+    case 2: { constexpr int LL = 2; __VA_ARGS__; } break;   \
+    case 4: { constexpr int LL = 4; __VA_ARGS__; } break;   \
+    case 8: { constexpr int LL = 8; __VA_ARGS__; } break;   \
+    case 16: { constexpr int LL = 16; __VA_ARGS__; } break; \
+    default: { constexpr int LL = 32; __VA_ARGS__; } break; \
+  }
+
+void scale_reset(Work& w, cudaStream_t s) {
+  const long long N = (long long)w.n + w.m;
+  launch(k_fill, cdiv(N, 256), 256, 0, s, w.dsc, 1.0, N);
+}
+
+void scale_pass(Work& w, int kind, cudaStream_t s) {
+  const int N = w.n + w.m;
+  const int L = pick_lanes(w.Q.nnz + 2 * w.A.nnz, N);
+  DISPATCH_L(L, launch(k_scale_norms<LL>, cdiv(N, 256 / LL), 256, 0, s, w.Q.orig(), w.At.orig(),
+                       w.A.orig(), w.dsc, w.nu, w.n, w.m, kind));
+  launch(k_scale_update, cdiv(N, 256), 256, 0, s, w.dsc, w.nu, N);
+}
+
+void scale_apply(Work& w, bool mixed, cudaStream_t s) {
+  const int LQ = pick_lanes(w.Q.nnz, w.n);
+  DISPATCH_L(LQ, launch(k_scale_csr<LL>, cdiv(w.n, 256 / LL), 256, 0, s, w.n, w.Q.orig(), w.Q.sval,
+                        mixed ? w.Q.sval_f : nullptr, w.D2, w.D2, 0));
+  if (w.m > 0) {
+    const int LA = pick_lanes(w.A.nnz, w.m);
+    DISPATCH_L(LA, launch(k_scale_csr<LL>, cdiv(w.m, 256 / LL), 256, 0, s, w.m, w.A.orig(), w.A.sval,
+                          mixed ? w.A.sval_f : nullptr, w.D1, w.D2, 0));
+    const int LT = pick_lanes(w.At.nnz, w.n);
+    DISPATCH_L(LT, launch(k_scale_csr<LL>, cdiv(w.n, 256 / LL), 256, 0, s, w.n, w.At.orig(), w.At.sval,
+                          mixed ? w.At.sval_f : nullptr, w.D2, w.D1, 1));
+  }
+  const int N = w.n > w.m ? w.n : w.m;
+  launch(k_scale_vectors, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.c, w.b, w.l, w.u, w.cs, w.bs,
+         w.ls, w.us);
+}
+
+__global__ void k_pi_init(DevState* st, int n) {
+  st->pi_done[0] = 0; st->pi_done[1] = 0;
+  st->pi_lam[0] = 0.0; st->pi_lam[1] = 0.0;
+  st->pi_lam_prev[0] = 0.0; st->pi_lam_prev[1] = 0.0;
+  st->pi_inv_norm[0] = 1.0 / sqrt((double)n);
+  st->pi_inv_norm[1] = 1.0 / sqrt((double)n);
+  st->pi_iters = 0;
+}
+
+void power_init(Work& w, cudaStream_t s) {
+  launch(k_fill, cdiv(w.n, 256), 256, 0, s, w.pv[0], 1.0, (long long)w.n);
+  launch(k_fill, cdiv(w.n, 256), 256, 0, s, w.pq[0], 1.0, (long long)w.n);
+  launch(k_pi_init, 1, 1, 0, s, w.st, w.n);
+}
+
+void power_iter(Work& w, int t, const SolveParams& p, cudaStream_t s) {
+  const int cur = t & 1, nxt = cur ^ 1;
+  if (w.m > 0) {
+    const int LA = pick_lanes(w.A.nnz, w.m);
+    DISPATCH_L(LA, launch(k_pi_m<LL>, cdiv(w.m, 256 / LL), 256, 0, s, w.A.scaled(), w.pv[cur], w.pw, w.m, w.st));
+  }
+  const int LN = pick_lanes(w.Q.nnz + w.At.nnz, w.n);
+  DISPATCH_L(LN, launch(k_pi_n<LL>, PDQP_RED_BLOCKS, 256, 0, s, w.At.scaled(), w.Q.scaled(), w.pw, w.pv[cur],
+                        w.pv[nxt], w.pq[cur], w.pq[nxt], w.n, w.m, w.st, w.part));
+  launch(k_pi_update, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, p.power_tol, w.m > 0 ? 1 : 0);
+}
+
+__global__ void k_set_norms(DevState* st, double nA, double nQ) {
+  st->normA = nA > 0.0 ? nA : sqrt(fmax(st->pi_lam[0], 0.0));
+  st->normQ = nQ > 0.0 ? nQ : fmax(st->pi_lam[1], 0.0);
+}
+
+void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
+  launch(k_set_norms, 1, 1, 0, s, w.st, normA_opt, normQ_opt);
+}
+
+// ||c~||, ||b~|| -> InitializePrimalWeight
+__global__ void k_sumsq2(const double* __restrict__ a, int na, const double* __restrict__ b, int nb,
+                         double* __restrict__ part) {
+  double f[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(na, nb); i += gridDim.x * blockDim.x) {
+    if (i < na) f[0] += a[i] * a[i];
+    if (i < nb) f[1] += b[i] * b[i];
+  }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (threadIdx.x == 0) { part[blockIdx.x * 32] = f[0]; part[blockIdx.x * 32 + 1] = f[1]; }
+}
+
+__global__ void k_init_omega(DevState* st, const double* __restrict__ part, int nblk, double eps_zero) {
+  double f[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b * 32]; f[1] += part[b * 32 + 1]; }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (threadIdx.x == 0) {
+    const double nc = sqrt(f[0]), nb = sqrt(f[1]);
+    st->omega = (nc > eps_zero && nb > eps_zero) ? nc / nb : 1.0;
+    st->eta_last = 0.0;
+    st->status = ST_RUNNING;
+  }
+}
+
+void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s) {
+  launch(k_sumsq2, PDQP_RED_BLOCKS, 256, 0, s, w.cs, w.n, w.bs, w.m, w.part);
+  launch(k_init_omega, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, p.eps_zero);
+  const int N = w.n > w.m ? w.n : w.m;
+  launch(k_init_iterates, cdiv(N, 256), 256, 0, s, w.n, w.m, w.m_eq, x0, y0, w.D1, w.D2, w.ls, w.us, w.x,
+         w.xbar, w.xmd[0], w.xt, w.ax, w.y, w.ybar, w.ay);
+}
+
+void iterate_chunk(Work& w, int len, int lanesA, int lanesP, bool mixed, cudaStream_t s) {
+  (void)mixed;
+  DualArgs<double> da{w.A.scaled(), w.xt, w.y, w.ybar, w.bs, nullptr, w.tab, w.m, w.m_eq};
+  PrimalArgs<double> pa{w.Q.scaled(), w.At.scaled(), nullptr, nullptr, w.y, w.x, w.xbar, w.xt,
+                        w.cs, w.ls, w.us, w.tab, w.n, w.m};
+  for (int j = 0; j < len; ++j) {
+    if (w.m > 0) {
+      DISPATCH_L(lanesA, launch(k_dual<LL, double>, cdiv(w.m, 256 / LL), 256, 0, s, da, j));
+    }
+    pa.xmd_in = w.xmd[j & 1];
+    pa.xmd_out = w.xmd[(j + 1) & 1];
+    DISPATCH_L(lanesP, launch(k_primal<LL, double>, cdiv(w.n, 256 / LL), 256, 0, s, pa, j));
+  }
+}
+
+static KktArgs kkt_args_scaled(Work& w) {
+  KktArgs a{};
+  a.A = w.A.scaled(); a.Q = w.Q.scaled(); a.At = w.At.scaled();
+  a.x[0] = w.x; a.x[1] = w.xbar; a.y[0] = w.y; a.y[1] = w.ybar;
+  a.ax = w.ax; a.ay = w.ay;
+  a.D1 = w.D1; a.D2 = w.D2;
+  a.b = w.b; a.c = w.c; a.l = w.l; a.u = w.u;
+  a.part = w.part;
+  a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
+  return a;
+}
+
+static void launch_kkt(Work& w, const KktArgs& a, int nit, cudaStream_t s) {
+  const int LA = pick_lanes(w.A.nnz, w.m);
+  const int LN = pick_lanes(w.Q.nnz + w.At.nnz, w.n);
+  if (nit == 2) {
+    DISPATCH_L(LA, launch(k_kkt_m<LL, 2, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
+    DISPATCH_L(LN, launch(k_kkt_n<LL, 2, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
+  } else {
+    DISPATCH_L(LA, launch(k_kkt_m<LL, 1, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
+    DISPATCH_L(LN, launch(k_kkt_n<LL, 1, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
+  }
+}
+
+void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s) {
+  (void)mixed;
+  KktArgs a = kkt_args_scaled(w);
+  launch_kkt(w, a, 2, s);
+  launch(k_decide, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, w.tab, p, mode, chunk_len);
+  if (mode == 1) {
+    const int N = w.n > w.m ? w.n : w.m;
+    const int grid = cdiv(N, 256) < 4 * w.num_sms ? cdiv(N, 256) : 4 * w.num_sms;
+    launch(k_restart_apply, grid, 256, 0, s, w.st, w.n, w.m, w.x, w.xbar, w.xmd[0], w.xt, w.ax, w.y, w.ybar,
+           w.ay);
+  }
+}
+
+void write_output(Work& w, double* x_out, double* y_out, bool mixed, cudaStream_t s) {
+  (void)mixed;
+  const int N = w.n > w.m ? w.n : w.m;
+  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.x, w.xbar, w.y, w.ybar, w.st, -1,
+         x_out, y_out);
+}
+
+void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, bool mixed, cudaStream_t s) {
+  (void)mixed;
+  const int N = w.n > w.m ? w.n : w.m;
+  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.x, w.xbar, w.y, w.ybar, w.st, 0, x, y);
+  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.x, w.xbar, w.y, w.ybar, w.st, 1, xbar,
+         ybar);
+}
+
+// relKKT of a user (x, y) on the original matrices (D = 1)
+__global__ void k_kkt_finish_user(const double* __restrict__ part, int nblk, DevState* st) {
+  __shared__ double F[24];
+  reduce_kkt_partials(part, nblk, F);
+  if (threadIdx.x == 0) kkt_from_fields(F, 0, st->out_parts);
+}
+
+void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
+  KktArgs a{};
+  a.A = w.A.orig(); a.Q = w.Q.orig(); a.At = w.At.orig();
+  a.x[0] = x; a.x[1] = x; a.y[0] = y; a.y[1] = y;
+  a.b = w.b; a.c = w.c; a.l = w.l; a.u = w.u;
+  a.part = w.part;
+  a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
+  launch_kkt(w, a, 1, s);
+  launch(k_kkt_finish_user, 1, 256, 0, s, w.part, PDQP_RED_BLOCKS, w.st);
+}
+
+}  // namespace pdqp

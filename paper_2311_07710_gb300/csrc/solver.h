@@ -1,0 +1,80 @@
+// Host-side view of the device buffers of one problem and the kernel-launch
+// entry points used by the C ABI driver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+struct DCsr {
+  int rows = 0;
+  long long nnz = 0;
+  int* rp = nullptr;          // [rows+1]
+  int* col = nullptr;         // [nnz]
+  double* val = nullptr;      // original values
+  double* sval = nullptr;     // scaled values, float64
+  float* sval_f = nullptr;    // scaled values, float32 (mixed precision)
+  Csr<double> orig() const { return Csr<double>{rp, col, val}; }
+  Csr<double> scaled() const { return Csr<double>{rp, col, sval}; }
+  Csr<float> scaled_f() const { return Csr<float>{rp, col, sval_f}; }
+};
+
+struct Work {
+  int n = 0, m = 0, m_eq = 0;
+  int num_sms = 152;
+  DCsr Q, A, At;                              // At = transpose of A (n rows)
+  double *c = nullptr, *b = nullptr, *l = nullptr, *u = nullptr;        // original data
+  double *cs = nullptr, *bs = nullptr, *ls = nullptr, *us = nullptr;    // scaled data
+  double *D1 = nullptr, *D2 = nullptr;        // views into dsc: D2 = dsc[0:n], D1 = dsc[n:n+m]
+  double *dsc = nullptr, *nu = nullptr;       // scaling vector and row norms [n+m]
+  double *ones = nullptr;                     // [max(n,m)] of 1.0
+  // float64 iterates (scaled space)
+  double *x = nullptr, *xbar = nullptr, *xt = nullptr, *xmd[2] = {nullptr, nullptr};
+  double *y = nullptr, *ybar = nullptr, *ax = nullptr, *ay = nullptr;
+  // float32 iterates of the mixed mode (deltas from the float64 base xhi, yhi)
+  float *fx = nullptr, *fxbar = nullptr, *fxt = nullptr, *fxmd[2] = {nullptr, nullptr};
+  float *fy = nullptr, *fybar = nullptr;
+  float *fc = nullptr, *fb = nullptr, *fl = nullptr, *fu = nullptr, *fylo = nullptr;  // shifted data
+  double *xhi = nullptr, *yhi = nullptr;
+  double *prodAx = nullptr, *prodQx = nullptr, *prodATy = nullptr;      // [2][m], [2][n], [2][n]
+  // low-rank factor (Q_total = Q + F F'), float32 row-major n x r
+  int r = 0;
+  float* F = nullptr;        // original
+  float* Fs = nullptr;       // row-scaled by D2
+  double* Fd = nullptr;      // float64 copy of Fs (for the float64 paths)
+  double* wlr = nullptr;     // [2][r] F'x partial buffers
+  // power iteration
+  double *pv[2] = {nullptr, nullptr}, *pq[2] = {nullptr, nullptr}, *pw = nullptr;
+  // reductions
+  double *part = nullptr;    // [PDQP_RED_BLOCKS][32]
+  StepEntry* tab = nullptr;  // [PDQP_MAX_CHECK]
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;   // pinned mirror
+  // user-vector staging (float64)
+  double *stage_n = nullptr, *stage_m = nullptr;
+};
+
+namespace pdqp {
+
+extern long long g_launches;
+
+// setup
+void scale_pass(Work& w, int kind, cudaStream_t s);          // kind: 0 inf, 1 l2, 2 l1
+void scale_reset(Work& w, cudaStream_t s);
+void scale_apply(Work& w, bool mixed, cudaStream_t s);
+void power_init(Work& w, cudaStream_t s);
+void power_iter(Work& w, int t, const SolveParams& p, cudaStream_t s);
+void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
+void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
+
+// iteration
+void iterate_chunk(Work& w, int len, int lanesA, int lanesP, bool mixed, cudaStream_t s);
+void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
+
+// results
+void write_output(Work& w, double* x_out, double* y_out, bool mixed, cudaStream_t s);
+void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, bool mixed, cudaStream_t s);
+void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s);
+
+}  // namespace pdqp

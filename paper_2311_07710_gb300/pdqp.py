@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libpdqp.so (include/pdqp.h).
+
+Functions carry the C names and only marshal arguments: numpy arrays are
+passed as host pointers (PDQP_MEM_HOST), torch CUDA tensors as device pointers
+(PDQP_MEM_DEVICE).  Every step of the solver runs in the library's CUDA
+kernels; importing this module fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpdqp.so")
+
+PDQP_OK, PDQP_ERR_INVALID, PDQP_ERR_CUDA, PDQP_ERR_OOM = 0, 1, 2, 3
+PDQP_ITER_LIMIT, PDQP_TIME_LIMIT, PDQP_NUMERICAL, PDQP_DEVICE_TIMEOUT = 10, 11, 12, 13
+PDQP_MEM_HOST, PDQP_MEM_DEVICE = 0, 1
+PDQP_PREC_FP64, PDQP_PREC_MIXED = 0, 1
+PDQP_STEP_ADAPTIVE, PDQP_STEP_THEORY = 0, 1
+PDQP_RESTART_PDQP, PDQP_RESTART_HALVING, PDQP_RESTART_FIXED, PDQP_RESTART_NONE = 0, 1, 2, 3
+
+
+class pdqp_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32), ("step_rule", ctypes.c_int32), ("restart_rule", ctypes.c_int32),
+        ("accelerate", ctypes.c_int32), ("scaling", ctypes.c_int32), ("ruiz_iters", ctypes.c_int32),
+        ("l2_scaling", ctypes.c_int32), ("pock_chambolle", ctypes.c_int32), ("fixed_K", ctypes.c_int32),
+        ("check_period", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("eps", ctypes.c_double),
+        ("time_limit", ctypes.c_double), ("beta_suff", ctypes.c_double), ("beta_nec", ctypes.c_double),
+        ("beta_art", ctypes.c_double), ("pw_theta", ctypes.c_double), ("eps_zero", ctypes.c_double),
+        ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double), ("power_iters", ctypes.c_int32),
+        ("power_tol", ctypes.c_double), ("lanes_A", ctypes.c_int32), ("lanes_P", ctypes.c_int32),
+    ]
+
+
+class pdqp_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("iterations", ctypes.c_int64), ("restarts", ctypes.c_int64),
+        ("rel_kkt", ctypes.c_double), ("r_primal", ctypes.c_double), ("r_dual", ctypes.c_double),
+        ("r_gap", ctypes.c_double), ("primal_obj", ctypes.c_double), ("dual_obj", ctypes.c_double),
+        ("seconds", ctypes.c_double), ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double),
+        ("omega", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PdqpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)} ({status}): {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_lib = None
+
+# exported symbols and their signatures: (restype, argtypes)
+SIGNATURES = {
+    "pdqp_default_options": (None, [ctypes.POINTER(pdqp_options)]),
+    "pdqp_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "pdqp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                   _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_set_lowrank_Q": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "pdqp_solve": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_options), _P, _P, _P, _P,
+                                  ctypes.POINTER(pdqp_info), ctypes.c_int32, _P]),
+    "pdqp_solve_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(pdqp_options),
+                                        ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                        ctypes.POINTER(_P), ctypes.POINTER(pdqp_info), ctypes.c_int32, _P]),
+    "pdqp_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_kkt": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _P]),
+    "pdqp_get_sizes": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int64)] * 5),
+    "pdqp_last_error": (ctypes.c_char_p, [_P]),
+    "pdqp_destroy": (None, [_P]),
+    "pdqp_launch_count": (ctypes.c_int64, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libpdqp.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().pdqp_status_string(int(status)).decode()
+
+
+# ---------------------------------------------------------------------------
+# argument marshalling
+# ---------------------------------------------------------------------------
+def _is_torch_cuda(a) -> bool:
+    return a is not None and type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _ptr(a, dtype):
+    """(pointer, keepalive, mem_space) of an array argument."""
+    if a is None:
+        return None, None, None
+    if _is_torch_cuda(a):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"device array must be a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr()), a, PDQP_MEM_DEVICE
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr, PDQP_MEM_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(status, handle=None):
+    if status not in (PDQP_OK, PDQP_ITER_LIMIT, PDQP_TIME_LIMIT, PDQP_NUMERICAL):
+        msg = load().pdqp_last_error(handle).decode()
+        raise PdqpError(status, msg)
+    return status
+
+
+def _one_space(spaces):
+    s = {x for x in spaces if x is not None}
+    if len(s) > 1:
+        raise TypeError("mix of host (numpy) and device (torch CUDA) arrays in one call")
+    return s.pop() if s else PDQP_MEM_HOST
+
+
+# ---------------------------------------------------------------------------
+# the C functions
+# ---------------------------------------------------------------------------
+def pdqp_default_options(**overrides) -> pdqp_options:
+    o = pdqp_options()
+    load().pdqp_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def pdqp_create(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, l, u, stream=None):
+    args = [_ptr(Q_rowptr, np.int32), _ptr(Q_col, np.int32), _ptr(Q_val, np.float64),
+            _ptr(A_rowptr, np.int32), _ptr(A_col, np.int32), _ptr(A_val, np.float64),
+            _ptr(c, np.float64), _ptr(b, np.float64), _ptr(l, np.float64), _ptr(u, np.float64)]
+    mem = _one_space([a[2] for a in args])
+    h = ctypes.c_void_p()
+    st = load().pdqp_create(ctypes.byref(h), int(n), int(m), int(m_eq), *[a[0] for a in args], mem,
+                            _stream(stream))
+    _check(st, None)
+    return h
+
+
+def pdqp_set_lowrank_Q(h, r, F, stream=None):
+    p, keep, mem = _ptr(F, np.float32)
+    return _check(load().pdqp_set_lowrank_Q(h, int(r), p, mem, _stream(stream)), h)
+
+
+def pdqp_solve(h, opt: Optional[pdqp_options] = None, x0=None, y0=None, x_out=None, y_out=None, stream=None):
+    """Returns (status, pdqp_info).  x_out / y_out (numpy float64 or torch CUDA
+    float64) receive the returned iterate."""
+    args = [_ptr(x0, np.float64), _ptr(y0, np.float64)]
+    outs = [x_out, y_out]
+    for o in outs:
+        if o is not None and not _is_torch_cuda(o):
+            if not (isinstance(o, np.ndarray) and o.dtype == np.float64 and o.flags.c_contiguous):
+                raise TypeError("host outputs must be contiguous float64 numpy arrays")
+    oargs = [_ptr(o, np.float64) for o in outs]
+    mem = _one_space([a[2] for a in args + oargs])
+    info = pdqp_info()
+    opt = opt if opt is not None else pdqp_default_options()
+    st = load().pdqp_solve(h, ctypes.byref(opt), args[0][0], args[1][0], oargs[0][0], oargs[1][0],
+                           ctypes.byref(info), mem, _stream(stream))
+    return _check(st, h), info
+
+
+def pdqp_solve_batch(hs: Sequence, opt: Optional[pdqp_options] = None, x0=None, y0=None, x_out=None,
+                     y_out=None, stream=None):
+    """Solve len(hs) problems.  x0/y0/x_out/y_out are None or per-problem lists."""
+    count = len(hs)
+    keep = []
+
+    def arr_of(lst, writable):
+        if lst is None:
+            return None, []
+        ptrs = []
+        for a in lst:
+            if a is not None and writable and not _is_torch_cuda(a):
+                assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+            p = _ptr(a, np.float64)
+            keep.append(p[1])
+            ptrs.append(p)
+        return (ctypes.c_void_p * count)(*[p[0] for p in ptrs]), [p[2] for p in ptrs]
+
+    a0, s0 = arr_of(x0, False)
+    a1, s1 = arr_of(y0, False)
+    a2, s2 = arr_of(x_out, True)
+    a3, s3 = arr_of(y_out, True)
+    mem = _one_space(s0 + s1 + s2 + s3)
+    hs_arr = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+    infos = (pdqp_info * count)()
+    opt = opt if opt is not None else pdqp_default_options()
+    st = load().pdqp_solve_batch(count, hs_arr, ctypes.byref(opt), a0, a1, a2, a3, infos, mem, _stream(stream))
+    return _check(st, None), list(infos)
+
+
+def pdqp_get_state(h, x=None, y=None, xbar=None, ybar=None, stream=None):
+    args = [_ptr(a, np.float64) for a in (x, y, xbar, ybar)]
+    mem = _one_space([a[2] for a in args])
+    return _check(load().pdqp_get_state(h, *[a[0] for a in args], mem, _stream(stream)), h)
+
+
+def pdqp_kkt(h, x, y, stream=None):
+    """[r_primal, r_dual, r_gap, rel_kkt, primal_obj, dual_obj] of (x, y)."""
+    a, b = _ptr(x, np.float64), _ptr(y, np.float64)
+    mem = _one_space([a[2], b[2]])
+    parts = (ctypes.c_double * 6)()
+    _check(load().pdqp_kkt(h, a[0], b[0], parts, mem, _stream(stream)), h)
+    return list(parts)
+
+
+def pdqp_get_sizes(h):
+    vals = [ctypes.c_int64() for _ in range(5)]
+    _check(load().pdqp_get_sizes(h, *[ctypes.byref(v) for v in vals]), h)
+    return tuple(v.value for v in vals)
+
+
+def pdqp_last_error(h=None) -> str:
+    return load().pdqp_last_error(h).decode()
+
+
+def pdqp_destroy(h):
+    load().pdqp_destroy(h)
+
+
+def pdqp_launch_count() -> int:
+    return int(load().pdqp_launch_count())
+
+
+# ---------------------------------------------------------------------------
+# convenience: a handle from scipy CSR data (marshalling only)
+# ---------------------------------------------------------------------------
+def create_from_csr(n, m, m_eq, Q, A, c, b, l, u, device=False, stream=None):
+    """Q, A: scipy.sparse CSR (int32 indices).  device=True uploads the arrays
+    as torch CUDA tensors first, exercising the PDQP_MEM_DEVICE path."""
+    arrays = [Q.indptr, Q.indices, Q.data, A.indptr, A.indices, A.data, c, b, l, u]
+    dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 4
+    arrays = [np.ascontiguousarray(a, dtype=t) for a, t in zip(arrays, dtypes)]
+    if device:
+        import torch
+        arrays = [torch.from_numpy(a).cuda() for a in arrays]
+        torch.cuda.synchronize()
+    return pdqp_create(n, m, m_eq, *arrays, stream=stream)
