@@ -1,0 +1,325 @@
+"""Benchmark: QP solves/sec to relative KKT 1e-6 on the large sparse QP
+(n = 1e6 variables, m = 5e5 rows, half equalities; A with 10 N(0,1) entries per
+column, Q = diag U(0.1,10) + symmetric sparse part, diagonally dominant).
+
+One step = one pdqp_solve of that QP through the C ABI: preconditioning,
+spectral norms, the rAPDHG iterations with their relKKT checks, and the
+returned (x, y) written to device buffers.  The problem data sit in HBM when
+the timed region starts (they exceed the 129 MB L2, so no flush is needed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Under torchrun every rank solves its own instance (seed + rank); the ranks
+share nothing (replicas, weak scaling).  Rank 0 prints one JSON line.
+"""
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "QP solves/sec to 1e-6 rel KKT vs plain FP64 rAPDHG; SpMV+update HBM GB/s"
+WORKLOAD = "large_sparse_qp n=1e6 m=5e5 (m_eq=2.5e5), A 10 nnz/col N(0,1), Q diag U(0.1,10)+5 nnz/row N(0,0.1^2) sym, l=-10 u=10"
+REF_JSON = os.path.join(ROOT, "tests", "golden", "large_sparse_qp_reference.json")
+PEAKS_JSON = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_TXT = os.path.join(ROOT, "profiles", "traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2311_07710_gb300", "csrc", "kernels.cu")
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal float64 rate (no FP64 tensor path used)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=1_000_000,
+                    help="variables of the workload (m = n/2); smaller only for profiler captures")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        load = [s for s in sm if s > 0.5 * (max(sm) if sm else 1)]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- oracle sample
+def oracle_sample(inst, budget_iters=6, scaling_passes=1, power_steps=2):
+    """Time the CPU oracle on a bounded sample of the workload and extrapolate
+    to one full solve with the oracle's own counts for this instance."""
+    from oracle import rapdhg as R
+    ref = json.load(open(REF_JSON))
+    p = R.problem_from_instance(inst)
+    t = time.perf_counter()
+    R.scaling_factors(p, ruiz_iters=scaling_passes, l2=False, pock_chambolle=False)
+    t_pass = (time.perf_counter() - t) / scaling_passes
+    t = time.perf_counter()
+    R.norm_A(p, max_iter=power_steps, tol=0.0)
+    t_powA = (time.perf_counter() - t) / power_steps
+    t = time.perf_counter()
+    R.norm_Q(p, max_iter=power_steps, tol=0.0)
+    t_powQ = (time.perf_counter() - t) / power_steps
+    base = dict(scaling=False, norm_A=ref["norm_A"], norm_Q=ref["norm_Q"], eps=0.0, check_period=10 ** 9)
+    t = time.perf_counter()
+    R.solve(inst, R.Options(max_iter=1, **base))
+    t1 = time.perf_counter() - t
+    t = time.perf_counter()
+    R.solve(inst, R.Options(max_iter=1 + budget_iters, **base))
+    t2 = time.perf_counter() - t
+    t_iter = (t2 - t1) / budget_iters
+    t_kkt = max(t1 - t_iter, 0.0) / 3.0          # one start evaluation + two at the final check
+    iters = ref["iterations"]
+    checks = math.ceil(iters / 64)
+    t_solve = (12 * t_pass + ref["power_steps_A"] * t_powA + ref["power_steps_Q"] * t_powQ
+               + iters * t_iter + (1 + 2 * checks) * t_kkt)
+    sample = (f"{scaling_passes} scaling pass, {power_steps} power steps per norm, "
+              f"{1 + budget_iters}+1 oracle iterations on the n=1e6 workload, extrapolated to a full solve "
+              f"(12 scaling passes, {ref['power_steps_A']}+{ref['power_steps_Q']} power steps, {iters} iterations, "
+              f"{checks} checks: counts of the oracle's own full solve)")
+    return 1.0 / t_solve, t_solve, sample
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle as it stands, bounded samples."""
+    if rank != 0:
+        return
+    import qpgen
+    inst = qpgen.large_sparse_qp()
+    vals = []
+    for step in range(args.warmup + args.steps):
+        v, t_solve, sample = oracle_sample(inst)
+        if step >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": WORKLOAD, "solver": "CPU oracle (numpy/scipy, float64)"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- ours
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    if not os.path.exists(TRAFFIC_TXT):
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    for line in open(TRAFFIC_TXT):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[3] == sha:
+            return float(parts[2])
+    return None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import qpgen
+    from paper_2311_07710_gb300 import pdqp
+
+    pdqp.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    inst = qpgen.large_sparse_qp(seed=qpgen.SEED_BASE + 1 + rank, n=args.n)
+    prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
+    opts = pdqp.pdqp_default_options(precision=prec)
+
+    # ---- device-resident leg ----
+    h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
+                             device=True)
+    x = torch.zeros(inst.n, dtype=torch.float64, device=dev)
+    y = torch.zeros(inst.m, dtype=torch.float64, device=dev)
+    infos = []
+    for _ in range(args.warmup):
+        st, info = pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream)
+    pdqp.pdqp_profile_enable(h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = pdqp.pdqp_launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st, info = pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream)
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = pdqp.pdqp_launch_count() - l0
+    barrier(world)
+    clk = clocks.stop()
+    prof = pdqp.pdqp_profile_read(h)
+    pdqp.pdqp_profile_enable(h, False)
+    t_ms = ev0.elapsed_time(ev1)
+    t_ms_max = allreduce_max(t_ms, world, dev)
+    value = world * args.steps / (t_ms_max / 1e3)
+    iters = [i.iterations for i in infos]
+    statuses = [i.status for i in infos]
+
+    # ---- end-to-end leg: host buffers, H2D + solve + D2H inside the timed region ----
+    host_arrays = [inst.Q.indptr, inst.Q.indices, inst.Q.data, inst.A.indptr, inst.A.indices, inst.A.data,
+                   inst.c, inst.b, inst.l, inst.u]
+    h2d = int(sum(a.nbytes for a in host_arrays))
+    xh, yh = np.zeros(inst.n), np.zeros(inst.m)
+    d2h = xh.nbytes + yh.nbytes
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        he = pdqp.pdqp_create(inst.n, inst.m, inst.m_eq, *host_arrays, stream=stream)
+        pdqp.pdqp_solve(he, opts, x_out=xh, y_out=yh, stream=stream)
+        pdqp.pdqp_destroy(he)
+    torch.cuda.synchronize(dev)
+    e2e_s = allreduce_max(time.perf_counter() - t0, world, dev)
+    e2e_value = world * args.e2e_steps / e2e_s if args.e2e_steps > 0 else None
+    pdqp.pdqp_destroy(h)
+
+    # ---- roofline of the dominant kernel ----
+    peaks = json.load(open(PEAKS_JSON)) if os.path.exists(PEAKS_JSON) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kinds = {k: v for k, v in prof.items() if k in ("dual", "primal") and v["launches"]}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = prof[dom]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    achieved_gbs = d["bytes"] / avg_s / 1e9
+    kname = {"dual": "k_dual", "primal": "k_primal"}[dom]
+    nnz_rows = (inst.nnz_A, inst.m, 8) if dom == "dual" else (inst.nnz_Q + inst.nnz_A, inst.n, 15)
+    flops = 2.0 * nnz_rows[0] + nnz_rows[2] * nnz_rows[1]
+    if args.precision == "fp64":
+        alu_peak = FP64_NOMINAL_TFLOPS * 1e12
+        frac_alu = flops / avg_s / alu_peak
+        frac_hbm = achieved_gbs / hbm_peak
+        if frac_alu >= frac_hbm:
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": frac_alu, "peak_source": "nominal float64 rate (profiling recipe)"}
+        else:
+            roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": frac_hbm,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        roof["hbm"] = {"achieved_gbs": achieved_gbs, "frac_of_measured": frac_hbm}
+        roof["fp64"] = {"achieved_tflops": flops / avg_s / 1e12, "frac_of_nominal": frac_alu}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof.update({"kernel": kname, "avg_launch_us": avg_s * 1e6, "launches": d["launches"],
+                 "algorithmic_bytes_per_launch": d["bytes"], "traffic": traffic_for(kname)})
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": WORKLOAD if args.n == 1_000_000 else f"large_sparse_qp n={args.n}",
+                       "precision": args.precision, "eps": 1e-6,
+                       "l2": "inputs larger than L2 (matrices >= 200 MB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "iterations_per_solve": iters, "statuses": statuses,
+            "iterations_per_sec": world * sum(iters) / (t_ms_max / 1e3),
+            "rel_kkt": max(i.rel_kkt for i in infos),
+            "setup_ms": 1e3 * infos[-1].setup_seconds, "iterate_ms": 1e3 * infos[-1].iterate_seconds,
+            "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.n == 1_000_000:
+        v, t_solve, sample = oracle_sample(inst)
+        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    args.gpus = world if world > 1 else args.gpus
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -112,7 +112,20 @@ typedef struct {
   double seconds;            /* wall time of the call */
   double norm_A, norm_Q;     /* spectral norms used (scaled problem) */
   double omega;              /* final primal weight */
+  double setup_seconds;      /* device time of scaling + spectral norms (CUDA events) */
+  double iterate_seconds;    /* device time from the first iteration to termination */
+  int32_t power_iters;       /* power-iteration steps taken (0 when norms were given) */
 } pdqp_info;
+
+/* Per-kernel device time of the solver's hot loop, measured with CUDA events
+ * recorded on the solve's stream around every launch while profiling is on.
+ * kind 0 = dual half-step, 1 = primal half-step, 2 = relKKT check + restart,
+ * 3 = everything else (scaling, norms, start point, output). */
+typedef struct {
+  int64_t launches[4];
+  double ms[4];              /* summed device milliseconds */
+  double bytes[4];           /* algorithmic DRAM bytes of one launch (kinds 0, 1) */
+} pdqp_profile;
 
 /* Fill *opt with the defaults listed above. */
 void pdqp_default_options(pdqp_options *opt);
@@ -180,6 +193,12 @@ const char *pdqp_last_error(pdqp_handle h);
 
 /* Release all device and host memory of a handle (NULL is a no-op). */
 void pdqp_destroy(pdqp_handle h);
+
+/* Turn per-kernel event timing on (resetting the counters) or off. */
+pdqp_status pdqp_profile_enable(pdqp_handle h, int32_t on);
+
+/* Read the counters accumulated since profiling was turned on. */
+pdqp_status pdqp_profile_read(pdqp_handle h, pdqp_profile *out);
 
 /* Kernel launches the library issued since the process started (for
  * reporting how much GPU work a call did). */

@@ -206,7 +206,10 @@ def scale_problem(p: Problem, D1: np.ndarray, D2: np.ndarray) -> Problem:
 # ---------------------------------------------------------------------------
 # Spectral norms (R10)
 # ---------------------------------------------------------------------------
-def power_norm(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6) -> float:
+POWER_STEPS = {}   # steps taken by the latest power_norm call of each operator name
+
+
+def power_norm(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6, name: str = "") -> float:
     """Largest eigenvalue of a symmetric PSD operator by power iteration from the
     normalised all-ones vector; stops when the Rayleigh quotient changes by at
     most tol relative."""
@@ -215,7 +218,8 @@ def power_norm(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6) -> f
     v = np.full(dim, 1.0 / math.sqrt(dim))
     lam_prev = 0.0
     lam = 0.0
-    for _ in range(max_iter):
+    for step in range(1, max_iter + 1):
+        POWER_STEPS[name] = step
         w = apply_sym(v)
         lam = float(v @ w)
         nw = float(np.linalg.norm(w))
@@ -231,11 +235,11 @@ def power_norm(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6) -> f
 def norm_A(p: Problem, **kw) -> float:
     if p.m == 0:
         return 0.0
-    return math.sqrt(max(power_norm(lambda v: p.A.T @ (p.A @ v), p.n, **kw), 0.0))
+    return math.sqrt(max(power_norm(lambda v: p.A.T @ (p.A @ v), p.n, name="A", **kw), 0.0))
 
 
 def norm_Q(p: Problem, **kw) -> float:
-    return max(power_norm(p.Qmul, p.n, **kw), 0.0)
+    return max(power_norm(p.Qmul, p.n, name="Q", **kw), 0.0)
 
 
 # ---------------------------------------------------------------------------

@@ -14,6 +14,8 @@ struct pdqp_problem {
   Work w;
   std::string err;
   bool mixed_ready = false;
+  int last_precision = PDQP_PREC_FP64;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // solve start, setup done, loop done
   std::vector<void*> allocs;
 };
 
@@ -191,6 +193,7 @@ double now_s() {
 void sync_state(pdqp_problem* h, cudaStream_t s) {
   CK(cudaMemcpyAsync(h->w.st_host, h->w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (h->w.prof.on) h->w.prof.harvest();
 }
 
 pdqp_status finish_status(int st) {
@@ -213,7 +216,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   check_space(x_out, mem, "x_out");
   check_space(y_out, mem, "y_out");
   const bool mixed = o.precision == PDQP_PREC_MIXED;
-  if (mixed) throw Fail{PDQP_ERR_INVALID, "mixed precision is not available in this build"};
+  if (mixed) alloc_mixed(h);
   const SolveParams p = make_params(o);
 
   // start point in device memory
@@ -224,6 +227,8 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     if (y0) { to_device(w.stage_m, y0, w.m, s); dy0 = w.stage_m; }
   }
 
+  h->last_precision = o.precision;
+  CK(cudaEventRecord(h->ev[0], s));
   // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle
   pdqp::scale_reset(w, s);
   if (o.scaling) {
@@ -234,7 +239,8 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   pdqp::scale_apply(w, mixed, s);
 
   // spectral norms of the scaled matrices
-  if (!(o.norm_A > 0.0 && o.norm_Q > 0.0)) {
+  const bool run_power = !(o.norm_A > 0.0 && o.norm_Q > 0.0);
+  if (run_power) {
     pdqp::power_init(w, s);
     for (int t = 0; t < o.power_iters; ++t) {
       pdqp::power_iter(w, t, p, s);
@@ -245,6 +251,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     }
   }
   pdqp::power_finish(w, o.norm_A, o.norm_Q, s);
+  CK(cudaEventRecord(h->ev[1], s));
   pdqp::init_iterates(w, dx0, dy0, p, s);
   pdqp::check(w, p, 0, 0, mixed, s);
   CK(cudaGetLastError());
@@ -265,6 +272,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     if (w.st_host->status == ST_RUNNING && now_s() - t0 > o.time_limit) { timed_out = true; break; }
   }
   result = timed_out ? PDQP_TIME_LIMIT : finish_status(w.st_host->status);
+  CK(cudaEventRecord(h->ev[2], s));
 
   // the returned iterate
   if (x_out || y_out) {
@@ -293,6 +301,12 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     info->norm_A = S.normA;
     info->norm_Q = S.normQ;
     info->omega = S.omega;
+    float t_setup = 0.f, t_iter = 0.f;
+    CK(cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]));
+    CK(cudaEventElapsedTime(&t_iter, h->ev[1], h->ev[2]));
+    info->setup_seconds = 1e-3 * t_setup;
+    info->iterate_seconds = 1e-3 * t_iter;
+    info->power_iters = run_power ? S.pi_iters : 0;
     info->seconds = now_s() - t0;
   }
   return result;
@@ -421,6 +435,7 @@ pdqp_status pdqp_create(pdqp_handle* out, int64_t n, int64_t m, int64_t m_eq, co
     w.st = dalloc<DevState>(h, 1);
     w.stage_n = dalloc<double>(h, N); w.stage_m = dalloc<double>(h, M);
     CK(cudaMallocHost(&w.st_host, sizeof(DevState)));
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
     CK(cudaMemsetAsync(w.st, 0, sizeof(DevState), s));
     CK(cudaStreamSynchronize(s));
     *out = h;
@@ -544,9 +559,35 @@ void pdqp_destroy(pdqp_handle h) {
   if (!h) return;
   for (void* p : h->allocs) cudaFree(p);
   if (h->w.st_host) cudaFreeHost(h->w.st_host);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 
 int64_t pdqp_launch_count(void) { return pdqp::g_launches; }
+
+pdqp_status pdqp_profile_enable(pdqp_handle h, int32_t on) {
+  if (!h) return PDQP_ERR_INVALID;
+  h->w.prof.reset();
+  h->w.prof.on = on != 0;
+  return PDQP_OK;
+}
+
+pdqp_status pdqp_profile_read(pdqp_handle h, pdqp_profile* out) {
+  if (!h || !out) return PDQP_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  const Work& w = h->w;
+  for (int k = 0; k < 4; ++k) {
+    out->launches[k] = w.prof.launches[k];
+    out->ms[k] = w.prof.ms[k];
+  }
+  // algorithmic bytes: matrix (index + value) streams, row pointers, and each
+  // vector read or written once (the gathered vector counted once)
+  const double sv = h->last_precision == PDQP_PREC_MIXED ? 4.0 : 8.0;
+  const double n = w.n, m = w.m;
+  out->bytes[0] = (double)w.A.nnz * (sv + 4.0) + 4.0 * (m + 1) + sv * (n + 5.0 * m);
+  out->bytes[1] = (double)(w.Q.nnz + w.At.nnz) * (sv + 4.0) + 8.0 * (n + 1) + sv * (10.0 * n + m);
+  return PDQP_OK;
+}
 
 }  // extern "C"

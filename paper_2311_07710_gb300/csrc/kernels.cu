@@ -636,6 +636,82 @@ __global__ void k_unscale_out(int n, int m, const double* __restrict__ D1, const
   if (y_out && i < m) y_out[i] = D1[i] * ys[i];
 }
 
+
+// --------------------------------------------------------------------------
+// Mixed precision (float32 iteration, float64 checks).  The iteration runs on
+// the shifted problem in (dx, dy) = (x - x_hi, y - y_hi) around a float64 base
+// z_hi: c' = c~ + Q~x_hi - A~'y_hi, b' = b~ - A~x_hi, l' = l~ - x_hi,
+// u' = u~ - x_hi and dy_I >= -y_hi,I.  Each check materialises the float64
+// iterates proj(z_hi + dz); each restart moves z_hi to the candidate and
+// recomputes the shifted data from the float64 products of that check (the
+// residual correction).
+// --------------------------------------------------------------------------
+struct MixedArgs {
+  int n, m, m_eq;
+  const double *cs, *bs, *ls, *us, *D1, *D2;
+  double *xhi, *yhi;
+  float *fx, *fxbar, *fxt, *fxmd0, *fy, *fybar;
+  float *fc, *fl, *fu, *fb, *fylo;
+  double *x64[2], *y64[2];               // materialised iterates (current, average)
+  const double *prodAx, *prodQx, *prodATy;   // [2][m], [2][n], [2][n]
+};
+
+__global__ void k_init_mixed(MixedArgs a, const double* __restrict__ x0, const double* __restrict__ y0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) {
+    double v = x0 ? x0[i] / a.D2[i] : 0.0;
+    a.xhi[i] = fmin(fmax(v, a.ls[i]), a.us[i]);
+    a.fx[i] = 0.f; a.fxbar[i] = 0.f; a.fxt[i] = 0.f; a.fxmd0[i] = 0.f;
+  }
+  if (i < a.m) {
+    double v = y0 ? y0[i] / a.D1[i] : 0.0;
+    if (i >= a.m_eq) v = fmax(v, 0.0);
+    a.yhi[i] = v;
+    a.fy[i] = 0.f; a.fybar[i] = 0.f;
+  }
+}
+
+__global__ void k_materialize(MixedArgs a) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(a.n, a.m); i += gridDim.x * blockDim.x) {
+    if (i < a.n) {
+      const double h = a.xhi[i], lo = a.ls[i], hi = a.us[i];
+      a.x64[0][i] = fmin(fmax(h + (double)a.fx[i], lo), hi);
+      a.x64[1][i] = fmin(fmax(h + (double)a.fxbar[i], lo), hi);
+    }
+    if (i < a.m) {
+      const double h = a.yhi[i];
+      double v0 = h + (double)a.fy[i], v1 = h + (double)a.fybar[i];
+      if (i >= a.m_eq) { v0 = fmax(v0, 0.0); v1 = fmax(v1, 0.0); }
+      a.y64[0][i] = v0;
+      a.y64[1][i] = v1;
+    }
+  }
+}
+
+// Move the base to the candidate (or, with force, re-derive the shifted data
+// at the current base) and zero the float32 deltas.
+__global__ void k_mixed_rebase(MixedArgs a, const DevState* __restrict__ st, int force) {
+  if (!force && (st->status != ST_RUNNING || !st->restart)) return;
+  const int ca = force ? 0 : st->cand_avg;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(a.n, a.m); i += gridDim.x * blockDim.x) {
+    if (i < a.n) {
+      const double xh = a.x64[ca][i];
+      a.xhi[i] = xh;
+      a.fc[i] = (float)(a.cs[i] + a.prodQx[(size_t)ca * a.n + i] - a.prodATy[(size_t)ca * a.n + i]);
+      a.fl[i] = (float)(a.ls[i] - xh);
+      a.fu[i] = (float)(a.us[i] - xh);
+      a.fx[i] = 0.f; a.fxbar[i] = 0.f; a.fxt[i] = 0.f; a.fxmd0[i] = 0.f;
+    }
+    if (i < a.m) {
+      const double yh = a.y64[ca][i];
+      a.yhi[i] = yh;
+      a.fb[i] = (float)(a.bs[i] - a.prodAx[(size_t)ca * a.m + i]);
+      a.fylo[i] = (float)(-yh);
+      a.fy[i] = 0.f; a.fybar[i] = 0.f;
+    }
+  }
+}
+
 // ==========================================================================
 // Host-side launchers
 // ==========================================================================
@@ -747,26 +823,69 @@ __global__ void k_init_omega(DevState* st, const double* __restrict__ part, int 
   }
 }
 
+static MixedArgs mixed_args(Work& w) {
+  MixedArgs a{};
+  a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
+  a.cs = w.cs; a.bs = w.bs; a.ls = w.ls; a.us = w.us; a.D1 = w.D1; a.D2 = w.D2;
+  a.xhi = w.xhi; a.yhi = w.yhi;
+  a.fx = w.fx; a.fxbar = w.fxbar; a.fxt = w.fxt; a.fxmd0 = w.fxmd[0]; a.fy = w.fy; a.fybar = w.fybar;
+  a.fc = w.fc; a.fl = w.fl; a.fu = w.fu; a.fb = w.fb; a.fylo = w.fylo;
+  a.x64[0] = w.x; a.x64[1] = w.xbar; a.y64[0] = w.y; a.y64[1] = w.ybar;
+  a.prodAx = w.prodAx; a.prodQx = w.prodQx; a.prodATy = w.prodATy;
+  return a;
+}
+
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s) {
   launch(k_sumsq2, PDQP_RED_BLOCKS, 256, 0, s, w.cs, w.n, w.bs, w.m, w.part);
   launch(k_init_omega, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, p.eps_zero);
   const int N = w.n > w.m ? w.n : w.m;
+  if (p.mixed) {
+    launch(k_init_mixed, cdiv(N, 256), 256, 0, s, mixed_args(w), x0, y0);
+    return;
+  }
   launch(k_init_iterates, cdiv(N, 256), 256, 0, s, w.n, w.m, w.m_eq, x0, y0, w.D1, w.D2, w.ls, w.us, w.x,
          w.xbar, w.xmd[0], w.xt, w.ax, w.y, w.ybar, w.ay);
 }
 
+static void iterate_chunk_mixed(Work& w, int len, int lanesA, int lanesP, cudaStream_t s) {
+  DualArgs<float> da{w.A.scaled_f(), w.fxt, w.fy, w.fybar, w.fb, w.fylo, w.tab, w.m, w.m_eq};
+  PrimalArgs<float> pa{w.Q.scaled_f(), w.At.scaled_f(), nullptr, nullptr, w.fy, w.fx, w.fxbar, w.fxt,
+                       w.fc, w.fl, w.fu, w.tab, w.n, w.m};
+  Profiler& P = w.prof;
+  for (int j = 0; j < len; ++j) {
+    if (w.m > 0) {
+      if (P.on) P.begin(0, s);
+      DISPATCH_L(lanesA, launch(k_dual<LL, float>, cdiv(w.m, 256 / LL), 256, 0, s, da, j));
+      if (P.on) P.end(s);
+    }
+    pa.xmd_in = w.fxmd[j & 1];
+    pa.xmd_out = w.fxmd[(j + 1) & 1];
+    if (P.on) P.begin(1, s);
+    DISPATCH_L(lanesP, launch(k_primal<LL, float>, cdiv(w.n, 256 / LL), 256, 0, s, pa, j));
+    if (P.on) P.end(s);
+  }
+}
+
 void iterate_chunk(Work& w, int len, int lanesA, int lanesP, bool mixed, cudaStream_t s) {
-  (void)mixed;
+  if (mixed) {
+    iterate_chunk_mixed(w, len, lanesA, lanesP, s);
+    return;
+  }
   DualArgs<double> da{w.A.scaled(), w.xt, w.y, w.ybar, w.bs, nullptr, w.tab, w.m, w.m_eq};
   PrimalArgs<double> pa{w.Q.scaled(), w.At.scaled(), nullptr, nullptr, w.y, w.x, w.xbar, w.xt,
                         w.cs, w.ls, w.us, w.tab, w.n, w.m};
+  Profiler& P = w.prof;
   for (int j = 0; j < len; ++j) {
     if (w.m > 0) {
+      if (P.on) P.begin(0, s);
       DISPATCH_L(lanesA, launch(k_dual<LL, double>, cdiv(w.m, 256 / LL), 256, 0, s, da, j));
+      if (P.on) P.end(s);
     }
     pa.xmd_in = w.xmd[j & 1];
     pa.xmd_out = w.xmd[(j + 1) & 1];
+    if (P.on) P.begin(1, s);
     DISPATCH_L(lanesP, launch(k_primal<LL, double>, cdiv(w.n, 256 / LL), 256, 0, s, pa, j));
+    if (P.on) P.end(s);
   }
 }
 
@@ -795,8 +914,25 @@ static void launch_kkt(Work& w, const KktArgs& a, int nit, cudaStream_t s) {
 }
 
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s) {
-  (void)mixed;
+  if (w.prof.on) w.prof.begin(2, s);
+  const int NN = w.n > w.m ? w.n : w.m;
+  const int grid_v = cdiv(NN, 256) < 4 * w.num_sms ? cdiv(NN, 256) : 4 * w.num_sms;
   KktArgs a = kkt_args_scaled(w);
+  if (mixed) {
+    MixedArgs ma = mixed_args(w);
+    launch(k_materialize, grid_v, 256, 0, s, ma);
+    a.ax = w.xhi; a.ay = w.yhi;
+    for (int it = 0; it < 2; ++it) {
+      a.prodAx[it] = w.prodAx + (size_t)it * w.m;
+      a.prodQx[it] = w.prodQx + (size_t)it * w.n;
+      a.prodATy[it] = w.prodATy + (size_t)it * w.n;
+    }
+    launch_kkt(w, a, 2, s);
+    launch(k_decide, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, w.tab, p, mode, chunk_len);
+    launch(k_mixed_rebase, grid_v, 256, 0, s, ma, w.st, mode == 0 ? 1 : 0);
+    if (w.prof.on) w.prof.end(s);
+    return;
+  }
   launch_kkt(w, a, 2, s);
   launch(k_decide, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, w.tab, p, mode, chunk_len);
   if (mode == 1) {
@@ -805,7 +941,9 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     launch(k_restart_apply, grid, 256, 0, s, w.st, w.n, w.m, w.x, w.xbar, w.xmd[0], w.xt, w.ax, w.y, w.ybar,
            w.ay);
   }
+  if (w.prof.on) w.prof.end(s);
 }
+
 
 void write_output(Work& w, double* x_out, double* y_out, bool mixed, cudaStream_t s) {
   (void)mixed;
@@ -841,3 +979,36 @@ void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
 }
 
 }  // namespace pdqp
+
+// ---------------------------------------------------------------- profiler
+void Profiler::begin(int k, cudaStream_t s) {
+  const size_t need = 2 * (kind.size() + 1);
+  while (ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+    ev.push_back(e);
+  }
+  cudaEventRecord(ev[2 * kind.size()], s);
+  kind.push_back(k);
+}
+void Profiler::end(cudaStream_t s) {
+  if (kind.empty()) return;
+  cudaEventRecord(ev[2 * kind.size() - 1], s);
+}
+void Profiler::harvest() {
+  for (size_t i = 0; i < kind.size(); ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+      ms[kind[i]] += t;
+      launches[kind[i]] += 1;
+    }
+  }
+  kind.clear();
+}
+void Profiler::reset() {
+  kind.clear();
+  for (int i = 0; i < 4; ++i) { launches[i] = 0; ms[i] = 0.0; }
+}
+Profiler::~Profiler() {
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+}

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 struct DCsr {
@@ -18,6 +20,20 @@ struct DCsr {
   Csr<double> orig() const { return Csr<double>{rp, col, val}; }
   Csr<double> scaled() const { return Csr<double>{rp, col, sval}; }
   Csr<float> scaled_f() const { return Csr<float>{rp, col, sval_f}; }
+};
+
+// Optional CUDA-event timing of kernel launches (per kind, see pdqp_profile).
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // pool; pairs (begin, end)
+  std::vector<int> kind;         // kind of each pair in flight
+  long long launches[4] = {0, 0, 0, 0};
+  double ms[4] = {0, 0, 0, 0};
+  void begin(int k, cudaStream_t s);
+  void end(cudaStream_t s);
+  void harvest();                // after the stream was synchronised
+  void reset();
+  ~Profiler();
 };
 
 struct Work {
@@ -53,6 +69,7 @@ struct Work {
   DevState* st_host = nullptr;   // pinned mirror
   // user-vector staging (float64)
   double *stage_n = nullptr, *stage_m = nullptr;
+  Profiler prof;
 };
 
 namespace pdqp {

@@ -43,11 +43,16 @@ class pdqp_info(ctypes.Structure):
         ("rel_kkt", ctypes.c_double), ("r_primal", ctypes.c_double), ("r_dual", ctypes.c_double),
         ("r_gap", ctypes.c_double), ("primal_obj", ctypes.c_double), ("dual_obj", ctypes.c_double),
         ("seconds", ctypes.c_double), ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double),
-        ("omega", ctypes.c_double),
+        ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
+        ("iterate_seconds", ctypes.c_double), ("power_iters", ctypes.c_int32),
     ]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pdqp_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4), ("bytes", ctypes.c_double * 4)]
 
 
 class PdqpError(RuntimeError):
@@ -77,6 +82,8 @@ SIGNATURES = {
     "pdqp_last_error": (ctypes.c_char_p, [_P]),
     "pdqp_destroy": (None, [_P]),
     "pdqp_launch_count": (ctypes.c_int64, []),
+    "pdqp_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "pdqp_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_profile)]),
 }
 
 
@@ -253,6 +260,18 @@ def pdqp_destroy(h):
 
 def pdqp_launch_count() -> int:
     return int(load().pdqp_launch_count())
+
+
+def pdqp_profile_enable(h, on=True):
+    return _check(load().pdqp_profile_enable(h, 1 if on else 0), h)
+
+
+def pdqp_profile_read(h) -> dict:
+    pr = pdqp_profile()
+    _check(load().pdqp_profile_read(h, ctypes.byref(pr)), h)
+    names = ("dual", "primal", "check", "other")
+    return {nm: dict(launches=int(pr.launches[k]), ms=float(pr.ms[k]), bytes=float(pr.bytes[k]))
+            for k, nm in enumerate(names)}
 
 
 # ---------------------------------------------------------------------------

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_c(tmp_path, lib):
     from paper_2311_07710_gb300 import pdqp
     import ctypes
-    fields = {"pdqp_options": [f for f, _ in pdqp.pdqp_options._fields_],
+    fields = {"pdqp_options": [f for f, _ in pdqp.pdqp_options._fields_], "pdqp_profile": [f for f, _ in pdqp.pdqp_profile._fields_],
               "pdqp_info": [f for f, _ in pdqp.pdqp_info._fields_]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fs in fields.items():
