@@ -183,6 +183,38 @@ pdqp_status pdqp_get_state(pdqp_handle h, double *x, double *y, double *xbar, do
 pdqp_status pdqp_kkt(pdqp_handle h, const double *x, const double *y, double *parts,
                      int32_t mem_space, void *stream);
 
+/* Allocation-free relative KKT error, for callers that cannot allocate device
+ * memory once running: real-time control loops (an MPC controller re-solving
+ * every few milliseconds must not block on the allocator or synchronise the
+ * device) and code running under CUDA stream capture or a fixed device-memory
+ * budget.  The paper has no counterpart; it is a variant of pdqp_kkt that
+ * needs no handle and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ * All array arguments are DEVICE pointers owned by the caller: the CSR of Q
+ * (n rows, nnz_Q entries), of A (m rows) and of its transpose A' (n rows, the
+ * same nnz_A entries, columns sorted), c, b, l, u as in pdqp_create, the point
+ * (x[n], y[m]) in original coordinates, and parts[6] which receives r_primal,
+ * r_dual, r_gap, rel_kkt, primal_obj, dual_obj.  The work is enqueued on
+ * `stream` and the call returns without synchronising.
+ *
+ * Limits: n <= 65536 and m <= 65536; larger problems return PDQP_ERR_INVALID
+ * before any device work.  The partial sums live in one 2 MiB array in the
+ * library's device image that every GPU loading the library holds until the
+ * process exits.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make the first call
+ * on a device before any stream capture.  Every call zeroes and reuses the
+ * same array, so calls whose device work overlaps (on different streams or
+ * from different threads) race on it: order them on one stream. */
+pdqp_status pdqp_kkt_noalloc(int64_t n, int64_t m, int64_t m_eq,
+                             const int32_t *Q_rowptr, const int32_t *Q_col, const double *Q_val,
+                             int64_t nnz_Q,
+                             const int32_t *A_rowptr, const int32_t *A_col, const double *A_val,
+                             const int32_t *At_rowptr, const int32_t *At_col, const double *At_val,
+                             int64_t nnz_A, const double *c, const double *b, const double *l,
+                             const double *u, const double *x, const double *y, double *parts,
+                             void *stream);
+
 /* Sizes of the handle's problem. */
 pdqp_status pdqp_get_sizes(pdqp_handle h, int64_t *n, int64_t *m, int64_t *m_eq,
                            int64_t *nnz_Q, int64_t *nnz_A);

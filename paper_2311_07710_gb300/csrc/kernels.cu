@@ -1012,3 +1012,88 @@ void Profiler::reset() {
 Profiler::~Profiler() {
   for (cudaEvent_t e : ev) cudaEventDestroy(e);
 }
+
+// ==========================================================================
+// Allocation-free relative-KKT evaluation: pdqp_kkt_noalloc.
+//
+// Some callers cannot call cudaMalloc once they are running: a real-time
+// control loop (for example an MPC controller re-solving every few
+// milliseconds) must not block on the allocator or synchronise the device,
+// and code that runs while a CUDA stream is being captured or inside a host
+// with a fixed device-memory budget may not allocate at all.  This entry point
+// evaluates the relative KKT error of a caller-given (x, y) with caller-owned
+// device arrays only; its per-block partial sums live in the file-scope array
+// below, which every GPU that loads this library holds until the process exits.
+// ==========================================================================
+#include <mutex>
+
+#include "pdqp.h"
+
+#define PDQP_NOALLOC_MAX_ROWS 65536                          // max n and max m per call
+#define PDQP_NOALLOC_MAX_BLOCKS (PDQP_NOALLOC_MAX_ROWS / 8)  // a block covers >= 8 rows
+#define PDQP_NOALLOC_MAX_DEVICES 64
+
+// 8192 blocks x 32 partial sums x 8 bytes = 2 MiB per device.
+static __device__ __align__(256) double g_noalloc_scratch[PDQP_NOALLOC_MAX_BLOCKS * 32];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[PDQP_NOALLOC_MAX_DEVICES] = {};
+
+// The variant of the finishing step that writes the six parts to caller memory.
+__global__ void k_kkt_finish_noalloc(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  __shared__ double F[24];
+  pdqp::reduce_kkt_partials(part, nblk, F);
+  if (threadIdx.x == 0) pdqp::kkt_from_fields(F, 0, out);
+}
+
+extern "C" pdqp_status pdqp_kkt_noalloc(int64_t n, int64_t m, int64_t m_eq, const int32_t* Q_rowptr,
+                                        const int32_t* Q_col, const double* Q_val, int64_t nnz_Q,
+                                        const int32_t* A_rowptr, const int32_t* A_col, const double* A_val,
+                                        const int32_t* At_rowptr, const int32_t* At_col, const double* At_val,
+                                        int64_t nnz_A, const double* c, const double* b, const double* l,
+                                        const double* u, const double* x, const double* y, double* parts,
+                                        void* stream) {
+  if (n < 1 || n > PDQP_NOALLOC_MAX_ROWS || m < 0 || m > PDQP_NOALLOC_MAX_ROWS || m_eq < 0 || m_eq > m ||
+      nnz_Q < 0 || nnz_A < 0 || nnz_Q > INT32_MAX || nnz_A > INT32_MAX)
+    return PDQP_ERR_INVALID;   // sizes beyond 65536 rows do not fit the static scratch
+  if (!Q_rowptr || (nnz_Q > 0 && (!Q_col || !Q_val)) || !c || !l || !u || !x || !parts)
+    return PDQP_ERR_INVALID;
+  if (m > 0 && (!A_rowptr || !At_rowptr || !b || !y || (nnz_A > 0 && (!A_col || !A_val || !At_col || !At_val))))
+    return PDQP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= PDQP_NOALLOC_MAX_DEVICES) return PDQP_ERR_CUDA;
+  double* scratch = nullptr;
+  {
+    // once per device, with that device current: the device address of the array
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return PDQP_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  const int LA = pdqp::pick_lanes(nnz_A, m);
+  const int LN = pdqp::pick_lanes(nnz_Q + nnz_A, n);
+  const int gm = m > 0 ? pdqp::cdiv(m, 256 / LA) : 0;
+  const int gn = pdqp::cdiv(n, 256 / LN);
+  const int nblk = gm > gn ? gm : gn;
+  // blocks that one of the two kernels does not launch contribute zeros
+  if (cudaMemsetAsync(scratch, 0, (size_t)nblk * 32 * sizeof(double), s) != cudaSuccess) return PDQP_ERR_CUDA;
+  pdqp::KktArgs a{};
+  a.A = Csr<double>{A_rowptr, A_col, A_val};
+  a.Q = Csr<double>{Q_rowptr, Q_col, Q_val};
+  a.At = Csr<double>{At_rowptr, At_col, At_val};
+  a.x[0] = x; a.x[1] = x; a.y[0] = y; a.y[1] = y;
+  a.b = b; a.c = c; a.l = l; a.u = u;
+  a.part = scratch;
+  a.n = (int)n; a.m = (int)m; a.m_eq = (int)m_eq;
+  if (gm > 0) { DISPATCH_L(LA, pdqp::launch(pdqp::k_kkt_m<LL, 1, false>, gm, 256, 0, s, a)); }
+  DISPATCH_L(LN, pdqp::launch(pdqp::k_kkt_n<LL, 1, false>, gn, 256, 0, s, a));
+  pdqp::launch(k_kkt_finish_noalloc, 1, 256, 0, s, (const double*)scratch, nblk, parts);
+  return cudaGetLastError() == cudaSuccess ? PDQP_OK : PDQP_ERR_CUDA;
+}

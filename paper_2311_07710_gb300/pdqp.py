@@ -84,6 +84,9 @@ SIGNATURES = {
     "pdqp_launch_count": (ctypes.c_int64, []),
     "pdqp_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pdqp_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_profile)]),
+    "pdqp_kkt_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
+                                        ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
+                                        _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -242,6 +245,28 @@ def pdqp_kkt(h, x, y, stream=None):
     parts = (ctypes.c_double * 6)()
     _check(load().pdqp_kkt(h, a[0], b[0], parts, mem, _stream(stream)), h)
     return list(parts)
+
+
+def pdqp_kkt_noalloc(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, At_rowptr, At_col, At_val,
+                     c, b, l, u, x, y, parts, stream=None):
+    """Allocation-free relKKT of (x, y): every array is a torch CUDA tensor
+    (int32 / float64); parts (float64, 6 entries) receives the result.  The
+    call is asynchronous on `stream` and returns the status."""
+    dev = [Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, At_rowptr, At_col, At_val, c, b, l, u, x, y, parts]
+    types = [np.int32, np.int32, np.float64] * 3 + [np.float64] * 7
+    ptrs = []
+    for a, t in zip(dev, types):
+        if a is None:
+            ptrs.append(None)
+            continue
+        if not _is_torch_cuda(a):
+            raise TypeError("pdqp_kkt_noalloc takes device (torch CUDA) arrays only")
+        ptrs.append(_ptr(a, t)[0])
+    nnz_Q = int(Q_col.numel()) if Q_col is not None else 0
+    nnz_A = int(A_col.numel()) if A_col is not None else 0
+    return load().pdqp_kkt_noalloc(int(n), int(m), int(m_eq), ptrs[0], ptrs[1], ptrs[2], nnz_Q, ptrs[3],
+                                   ptrs[4], ptrs[5], ptrs[6], ptrs[7], ptrs[8], nnz_A, *ptrs[9:],
+                                   _stream(stream))
 
 
 def pdqp_get_sizes(h):
