@@ -99,8 +99,8 @@ typedef struct {
                                 matrices; <= 0: estimate by power iteration */
   int32_t power_iters;       /* 500 */
   double power_tol;          /* 1e-6 relative change of the Rayleigh quotient */
-  int32_t lanes_A, lanes_P;  /* CSR lanes per row for the dual / primal kernels;
-                                0 = chosen by the library */
+  int32_t lanes_A, lanes_P;  /* reserved, must be 0, 2, 4, 8, 16 or 32; ignored
+                                (the kernels work on row blocks) */
 } pdqp_options;
 
 typedef struct {

@@ -111,8 +111,26 @@ void transpose_csr(int64_t rows, int64_t cols, const std::vector<int32_t>& rp, c
     }
 }
 
+// Row blocks of at most BNNZ nonzeros and BROWS rows; a longer row alone.
+std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
+  std::vector<int32_t> blk{0};
+  int64_t s = 0;
+  for (int64_t r = 0; r < rows; ++r) {
+    if (r > s && ((int64_t)rp[r + 1] - rp[s] > BNNZ || r - s >= BROWS)) {
+      blk.push_back((int32_t)r);
+      s = r;
+    }
+    if ((int64_t)rp[r + 1] - rp[r] > BNNZ) {   // r == s here: a block of its own
+      blk.push_back((int32_t)(r + 1));
+      s = r + 1;
+    }
+  }
+  if (blk.back() != rows) blk.push_back((int32_t)rows);
+  return blk;
+}
+
 void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
-                const std::vector<double>& val, cudaStream_t s) {
+                const std::vector<double>& val, const std::vector<int32_t>* split, cudaStream_t s) {
   M.rows = rows;
   M.nnz = rp[rows];
   M.rp = dalloc<int>(h, rows + 1);
@@ -122,18 +140,28 @@ void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& 
   to_device(M.rp, rp.data(), rows + 1, s);
   to_device(M.col, col.data(), M.nnz, s);
   to_device(M.val, val.data(), M.nnz, s);
+  const std::vector<int32_t> blk = row_blocks(rows, rp);
+  M.nblk = (int)blk.size() - 1;
+  M.blk = dalloc<int>(h, blk.size());
+  to_device(M.blk, blk.data(), blk.size(), s);
+  if (split) {
+    M.split = dalloc<int>(h, rows);
+    to_device(M.split, split->data(), rows, s);
+  }
+  CK(cudaStreamSynchronize(s));   // the host vectors die with the caller
 }
 
 void alloc_mixed(pdqp_problem* h) {
   if (h->mixed_ready) return;
   Work& w = h->w;
   const int n = w.n, m = w.m;
-  w.Q.sval_f = dalloc<float>(h, w.Q.nnz);
+  w.P.sval_f = dalloc<float>(h, w.P.nnz);
   w.A.sval_f = dalloc<float>(h, w.A.nnz);
-  w.At.sval_f = dalloc<float>(h, w.At.nnz);
   w.fx = dalloc<float>(h, n); w.fxbar = dalloc<float>(h, n); w.fxt = dalloc<float>(h, n);
-  w.fxmd[0] = dalloc<float>(h, n); w.fxmd[1] = dalloc<float>(h, n);
-  w.fy = dalloc<float>(h, m); w.fybar = dalloc<float>(h, m);
+  w.fZ[0] = dalloc<float>(h, (size_t)n + m); w.fZ[1] = dalloc<float>(h, (size_t)n + m);
+  w.fybar = dalloc<float>(h, m); w.yk = dalloc<double>(h, m);
+  w.fpu[0] = dalloc<float>(h, n); w.fpu[1] = dalloc<float>(h, n);
+  w.fpz[0] = dalloc<float>(h, (size_t)n + m); w.fpz[1] = dalloc<float>(h, (size_t)n + m);
   w.fc = dalloc<float>(h, n); w.fl = dalloc<float>(h, n); w.fu = dalloc<float>(h, n);
   w.fb = dalloc<float>(h, m); w.fylo = dalloc<float>(h, m);
   w.xhi = dalloc<double>(h, n); w.yhi = dalloc<double>(h, m);
@@ -177,13 +205,6 @@ void validate_options(const pdqp_options& o) {
   if (o.power_iters < 1) bad("options.power_iters must be >= 1");
   for (int L : {o.lanes_A, o.lanes_P})
     if (L != 0 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) bad("options.lanes_* must be 0,2,4,8,16,32");
-}
-
-int auto_lanes(long long nnz, long long rows) {
-  const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
-  int L = 2;
-  while (L < 32 && L < avg) L <<= 1;
-  return L;
 }
 
 double now_s() {
@@ -241,9 +262,9 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   // spectral norms of the scaled matrices
   const bool run_power = !(o.norm_A > 0.0 && o.norm_Q > 0.0);
   if (run_power) {
-    pdqp::power_init(w, s);
+    pdqp::power_init(w, mixed, s);
     for (int t = 0; t < o.power_iters; ++t) {
-      pdqp::power_iter(w, t, p, s);
+      pdqp::power_iter(w, t, p, mixed, s);
       if ((t & 15) == 15) {
         sync_state(h, s);
         if (w.st_host->pi_done[0] && w.st_host->pi_done[1]) break;
@@ -257,14 +278,12 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   CK(cudaGetLastError());
   sync_state(h, s);
 
-  const int lanesA = o.lanes_A ? o.lanes_A : auto_lanes(w.A.nnz, w.m);
-  const int lanesP = o.lanes_P ? o.lanes_P : auto_lanes(w.Q.nnz + w.At.nnz, w.n);
   long long k_total = 0;
   pdqp_status result = PDQP_OK;
   bool timed_out = false;
   while (w.st_host->status == ST_RUNNING) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
-    pdqp::iterate_chunk(w, (int)len, lanesA, lanesP, mixed, s);
+    pdqp::iterate_chunk(w, (int)len, mixed, s);
     pdqp::check(w, p, 1, len, mixed, s);
     CK(cudaGetLastError());
     k_total += len;
@@ -279,7 +298,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     double* ox = x_out;
     double* oy = y_out;
     if (mem == PDQP_MEM_HOST) { ox = x_out ? w.stage_n : nullptr; oy = y_out ? w.stage_m : nullptr; }
-    pdqp::write_output(w, ox, oy, mixed, s);
+    pdqp::write_output(w, ox, oy, s);
     if (mem == PDQP_MEM_HOST) {
       if (x_out) CK(cudaMemcpyAsync(x_out, w.stage_n, w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
       if (y_out && w.m) CK(cudaMemcpyAsync(y_out, w.stage_m, w.m * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -408,6 +427,19 @@ pdqp_status pdqp_create(pdqp_handle* out, int64_t n, int64_t m, int64_t m_eq, co
     std::vector<double> tval;
     if (m > 0) transpose_csr(m, n, arp, acol, aval, trp, tcol, tval);
     else trp.assign(n + 1, 0);
+    // P = [Q | -A'] row by row: Q's columns, then A' columns shifted by n
+    std::vector<int32_t> prp(n + 1, 0), pcol, psplit(n);
+    std::vector<double> pval;
+    pcol.reserve((size_t)qrp[n] + trp[n]);
+    pval.reserve((size_t)qrp[n] + trp[n]);
+    for (int64_t j = 0; j < n; ++j) {
+      for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k) { pcol.push_back(qcol[k]); pval.push_back(qval[k]); }
+      psplit[j] = (int32_t)pcol.size();
+      for (int32_t k = trp[j]; k < trp[j + 1]; ++k) { pcol.push_back((int32_t)(n + tcol[k])); pval.push_back(-tval[k]); }
+      if (pcol.size() > (size_t)INT32_MAX) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31-1"};
+      prp[j + 1] = (int32_t)pcol.size();
+    }
+    { std::vector<int32_t>().swap(tcol); std::vector<double>().swap(tval); }
 
     h = new pdqp_problem();
     Work& w = h->w;
@@ -415,22 +447,24 @@ pdqp_status pdqp_create(pdqp_handle* out, int64_t n, int64_t m, int64_t m_eq, co
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    upload_csr(h, w.Q, (int)n, qrp, qcol, qval, s);
-    upload_csr(h, w.A, (int)m, arp, acol, aval, s);
-    upload_csr(h, w.At, (int)n, trp, tcol, tval, s);
+    upload_csr(h, w.P, (int)n, prp, pcol, pval, &psplit, s);
+    upload_csr(h, w.A, (int)m, arp, acol, aval, nullptr, s);
     const size_t N = (size_t)n, M = (size_t)m;
     w.c = dalloc<double>(h, N); w.l = dalloc<double>(h, N); w.u = dalloc<double>(h, N); w.b = dalloc<double>(h, M);
     to_device(w.c, hc.data(), N, s); to_device(w.l, hl.data(), N, s); to_device(w.u, hu.data(), N, s);
     to_device(w.b, hb.data(), M, s);
     w.cs = dalloc<double>(h, N); w.ls = dalloc<double>(h, N); w.us = dalloc<double>(h, N); w.bs = dalloc<double>(h, M);
-    w.dsc = dalloc<double>(h, N + M); w.nu = dalloc<double>(h, N + M);
-    w.D2 = w.dsc; w.D1 = w.dsc + N;
+    w.dsc = dalloc<double>(h, N + M); w.idsc = dalloc<double>(h, N + M); w.nu = dalloc<double>(h, N + M);
+    w.D2 = w.dsc; w.D1 = w.dsc + N; w.iD2 = w.idsc; w.iD1 = w.idsc + N;
     w.x = dalloc<double>(h, N); w.xbar = dalloc<double>(h, N); w.xt = dalloc<double>(h, N);
-    w.xmd[0] = dalloc<double>(h, N); w.xmd[1] = dalloc<double>(h, N); w.ax = dalloc<double>(h, N);
-    w.y = dalloc<double>(h, M); w.ybar = dalloc<double>(h, M); w.ay = dalloc<double>(h, M);
-    w.pv[0] = dalloc<double>(h, N); w.pv[1] = dalloc<double>(h, N);
-    w.pq[0] = dalloc<double>(h, N); w.pq[1] = dalloc<double>(h, N); w.pw = dalloc<double>(h, M);
+    w.Z[0] = dalloc<double>(h, N + M); w.Z[1] = dalloc<double>(h, N + M); w.ax = dalloc<double>(h, N);
+    w.y = w.Z[1] + N;
+    w.ybar = dalloc<double>(h, M); w.ay = dalloc<double>(h, M);
+    w.pu[0] = dalloc<double>(h, N); w.pu[1] = dalloc<double>(h, N);
+    w.pz[0] = dalloc<double>(h, N + M); w.pz[1] = dalloc<double>(h, N + M);
     w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
+    w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
+    w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
     w.tab = dalloc<StepEntry>(h, PDQP_MAX_CHECK);
     w.st = dalloc<DevState>(h, 1);
     w.stage_n = dalloc<double>(h, N); w.stage_m = dalloc<double>(h, M);
@@ -495,15 +529,15 @@ pdqp_status pdqp_get_state(pdqp_handle h, double* x, double* y, double* xbar, do
   try {
     for (auto p : {x, y, xbar, ybar}) check_space(p, mem, "state output");
     if (mem == PDQP_MEM_DEVICE) {
-      pdqp::write_state(w, x, y, xbar, ybar, false, s);
+      pdqp::write_state(w, x, y, xbar, ybar, s);
     } else {
       double* outs[4] = {x, y, xbar, ybar};
       for (int k = 0; k < 2; ++k) {
         double* hx = outs[2 * k];
         double* hy = outs[2 * k + 1];
         if (!hx && !hy) continue;
-        if (k == 0) pdqp::write_state(w, w.stage_n, w.stage_m, nullptr, nullptr, false, s);
-        else pdqp::write_state(w, nullptr, nullptr, w.stage_n, w.stage_m, false, s);
+        if (k == 0) pdqp::write_state(w, w.stage_n, w.stage_m, nullptr, nullptr, s);
+        else pdqp::write_state(w, nullptr, nullptr, w.stage_n, w.stage_m, s);
         if (hx) CK(cudaMemcpyAsync(hx, w.stage_n, w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (hy && w.m) CK(cudaMemcpyAsync(hy, w.stage_m, w.m * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -548,7 +582,7 @@ pdqp_status pdqp_get_sizes(pdqp_handle h, int64_t* n, int64_t* m, int64_t* m_eq,
   if (n) *n = h->w.n;
   if (m) *m = h->w.m;
   if (m_eq) *m_eq = h->w.m_eq;
-  if (nnz_Q) *nnz_Q = h->w.Q.nnz;
+  if (nnz_Q) *nnz_Q = h->w.P.nnz - h->w.A.nnz;
   if (nnz_A) *nnz_A = h->w.A.nnz;
   return PDQP_OK;
 }
@@ -586,7 +620,7 @@ pdqp_status pdqp_profile_read(pdqp_handle h, pdqp_profile* out) {
   const double sv = h->last_precision == PDQP_PREC_MIXED ? 4.0 : 8.0;
   const double n = w.n, m = w.m;
   out->bytes[0] = (double)w.A.nnz * (sv + 4.0) + 4.0 * (m + 1) + sv * (n + 5.0 * m);
-  out->bytes[1] = (double)(w.Q.nnz + w.At.nnz) * (sv + 4.0) + 8.0 * (n + 1) + sv * (10.0 * n + m);
+  out->bytes[1] = (double)w.P.nnz * (sv + 4.0) + 4.0 * (n + 1) + sv * (10.0 * n + m);
   return PDQP_OK;
 }
 

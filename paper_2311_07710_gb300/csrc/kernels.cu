@@ -3,13 +3,19 @@
 // One inner iteration of Algorithm 1 (Section 2) is two fused kernels:
 //   k_dual   : rows of A   -- v = A x_tilde, y+ = proj_Y(y - sigma (v - b)),
 //              y_bar+ = (1 - 1/beta) y_bar + y+/beta
-//   k_primal : rows of Q and of A' -- g = Q x_md + c - A'y+,
+//   k_primal : rows of P = [Q | -A'] gathering [x_md ; y+] -- g = Q x_md + c - A'y+,
 //              x+ = proj_[l,u](x - tau g), x_bar+ = (1 - 1/beta) x_bar + x+/beta,
 //              and the next iteration's x_md and x_tilde
 // Every `check_period` iterations k_kkt_m / k_kkt_n reduce, in float64, the
 // relative KKT error of Section 5 for the current and the averaged iterate,
 // k_decide applies the Section 6 restart rule and tabulates the next step
 // sizes, and k_restart_apply moves the iterate to the restart candidate.
+//
+// All SpMV-shaped kernels work on row blocks (see BCsr): the block's nonzeros
+// are contiguous, so its 256 threads issue their index and value loads
+// together (coalesced, 8 per thread), then the independent gathers, stage the
+// products in shared memory, and finish one row per thread -- a row's update
+// reads and writes consecutive entries of the row-indexed vectors.
 #include <stdio.h>
 
 #include "solver.h"
@@ -29,302 +35,45 @@ static inline void launch(void (*kern)(KArgs...), int grid, int block, size_t sm
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// --------------------------------------------------------------------------
-// CSR row helpers: L lanes of a warp cooperate on one row
-// --------------------------------------------------------------------------
-template <int L, typename V, typename X, typename ACC>
-__device__ __forceinline__ ACC row_dot_partial(const Csr<V>& M, const X* __restrict__ x, int beg,
-                                               int end, int lane) {
-  ACC s = ACC(0);
-  for (int k = beg + lane; k < end; k += L) s = fma((ACC)M.val[k], (ACC)__ldg(x + M.col[k]), s);
-  return s;
+static int pick_lanes(long long nnz, long long rows) {
+  const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  int L = 2;
+  while (L < 32 && L < avg) L <<= 1;
+  return L;
 }
 
-// --------------------------------------------------------------------------
-// Preconditioning (Section 5 "Preprocessing"): norms of the rows of
-// D K D with K = [[Q, A'], [A, 0]], then d_j /= sqrt(norm_j)
-// --------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(256) k_scale_norms(Csr<double> Q, Csr<double> At, Csr<double> A,
-                                                     const double* __restrict__ d,
-                                                     double* __restrict__ nu, int n, int m, int kind) {
-  const int rows_per_block = 256 / L;
-  const int row = blockIdx.x * rows_per_block + threadIdx.x / L;
-  const int lane = threadIdx.x % L;
-  const bool valid = row < n + m;
-  double acc = 0.0;
-  if (valid) {
-    const double dr = d[row];
-    auto take = [&](double a) {
-      if (kind == 0) acc = fmax(acc, a);
-      else if (kind == 1) acc += a * a;
-      else acc += a;
-    };
-    if (row < n) {
-      for (int k = Q.rp[row] + lane; k < Q.rp[row + 1]; k += L) take(fabs(Q.val[k]) * dr * d[Q.col[k]]);
-      if (m > 0)
-        for (int k = At.rp[row] + lane; k < At.rp[row + 1]; k += L)
-          take(fabs(At.val[k]) * dr * d[n + At.col[k]]);
-    } else {
-      const int i = row - n;
-      for (int k = A.rp[i] + lane; k < A.rp[i + 1]; k += L) take(fabs(A.val[k]) * dr * d[A.col[k]]);
-    }
+#define DISPATCH_L(L, ...)                                  \
+  switch (L) {                                              \
+    case 2: { constexpr int LL = 2; __VA_ARGS__; } break;   \
+    case 4: { constexpr int LL = 4; __VA_ARGS__; } break;   \
+    case 8: { constexpr int LL = 8; __VA_ARGS__; } break;   \
+    case 16: { constexpr int LL = 16; __VA_ARGS__; } break; \
+    default: { constexpr int LL = 32; __VA_ARGS__; } break; \
   }
+
+// Deterministic sum over the block (valid in every thread).
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+  __shared__ T sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) {
-    double t = __shfl_xor_sync(0xffffffffu, acc, o, L);
-    acc = (kind == 0) ? fmax(acc, t) : acc + t;
-  }
-  if (valid && lane == 0) nu[row] = (kind == 1) ? sqrt(acc) : acc;
-}
-
-__global__ void k_scale_update(double* __restrict__ d, const double* __restrict__ nu, int N) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    const double v = nu[i];
-    d[i] = d[i] / sqrt(v > 0.0 ? v : 1.0);
-  }
-}
-
-__global__ void k_fill(double* __restrict__ p, double v, long long N) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) p[i] = v;
-}
-
-// scaled value = (drow[r] * val) * dcol[c]  (or (dcol[c] * val) * drow[r] when `tr`,
-// which makes the stored A~' bitwise equal to the entries of A~)
-template <int L>
-__global__ void __launch_bounds__(256) k_scale_csr(int rows, Csr<double> M, double* __restrict__ out,
-                                                   float* __restrict__ out_f,
-                                                   const double* __restrict__ drow,
-                                                   const double* __restrict__ dcol, int tr) {
-  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
-  const int lane = threadIdx.x % L;
-  if (row >= rows) return;
-  const double dr = drow[row];
-  for (int k = M.rp[row] + lane; k < M.rp[row + 1]; k += L) {
-    const double dc = dcol[M.col[k]];
-    const double v = tr ? (dc * M.val[k]) * dr : (dr * M.val[k]) * dc;
-    out[k] = v;
-    if (out_f) out_f[k] = (float)v;
-  }
-}
-
-// c~ = D2 c, l~ = l / D2, u~ = u / D2 (n);  b~ = D1 b (m)
-__global__ void k_scale_vectors(int n, int m, const double* __restrict__ D1, const double* __restrict__ D2,
-                                const double* __restrict__ c, const double* __restrict__ b,
-                                const double* __restrict__ l, const double* __restrict__ u,
-                                double* __restrict__ cs, double* __restrict__ bs, double* __restrict__ ls,
-                                double* __restrict__ us) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const double d = D2[i];
-    cs[i] = d * c[i];
-    ls[i] = l[i] / d;
-    us[i] = u[i] / d;
-  }
-  if (i < m) bs[i] = D1[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  T t = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
 }
 
 // --------------------------------------------------------------------------
-// Power iteration for ||A~||_2 (on A~'A~) and ||Q~||_2, both from the
-// normalised all-ones vector; v_t = u_t * inv_norm, stop when the Rayleigh
-// quotient changes by <= tol relative.
-// --------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(256) k_pi_m(Csr<double> A, const double* __restrict__ u,
-                                              double* __restrict__ w, int m, const DevState* __restrict__ st) {
-  if (st->pi_done[0]) return;
-  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
-  const int lane = threadIdx.x % L;
-  const bool valid = row < m;
-  double s = valid ? row_dot_partial<L, double, double, double>(A, u, A.rp[row], A.rp[row + 1], lane) : 0.0;
-  s = group_sum<L>(s);
-  if (valid && lane == 0) w[row] = s * st->pi_inv_norm[0];
-}
-
-// u_new = A~' w ; z_new = Q~ v_Q ; block partials of v.u_new, |u_new|^2, vQ.z_new, |z_new|^2
-template <int L>
-__global__ void __launch_bounds__(256) k_pi_n(Csr<double> At, Csr<double> Q, const double* __restrict__ w,
-                                              const double* __restrict__ u_old, double* __restrict__ u_new,
-                                              const double* __restrict__ q_old, double* __restrict__ q_new,
-                                              int n, int m, const DevState* __restrict__ st,
-                                              double* __restrict__ part) {
-  const bool doA = !st->pi_done[0] && m > 0;
-  const bool doQ = !st->pi_done[1];
-  double f[4] = {0.0, 0.0, 0.0, 0.0};
-  const int rows_per_block = 256 / L;
-  const int lane = threadIdx.x % L;
-  const double sa = st->pi_inv_norm[0], sq = st->pi_inv_norm[1];
-  for (int base = blockIdx.x * rows_per_block; base < n; base += gridDim.x * rows_per_block) {
-    const int row = base + threadIdx.x / L;
-    const bool valid = row < n;
-    double a = 0.0, q = 0.0;
-    if (valid && doA) a = row_dot_partial<L, double, double, double>(At, w, At.rp[row], At.rp[row + 1], lane);
-    if (valid && doQ) q = row_dot_partial<L, double, double, double>(Q, q_old, Q.rp[row], Q.rp[row + 1], lane);
-    a = group_sum<L>(a);
-    q = group_sum<L>(q);
-    if (valid && lane == 0) {
-      if (doA) {
-        u_new[row] = a;
-        f[0] += (u_old[row] * sa) * a;
-        f[1] += a * a;
-      }
-      if (doQ) {
-        const double z = q * sq;     // Q~ (q_old * sq)
-        q_new[row] = z;
-        f[2] += (q_old[row] * sq) * z;
-        f[3] += z * z;
-      }
-    }
-  }
-  const bool is_max[4] = {false, false, false, false};
-  block_reduce<4>(f, is_max);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 4; ++k) part[blockIdx.x * 32 + k] = f[k];
-}
-
-__global__ void k_pi_update(DevState* __restrict__ st, const double* __restrict__ part, int nblk,
-                            double tol, int have_rows) {
-  double f[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-    for (int k = 0; k < 4; ++k) f[k] += part[b * 32 + k];
-  const bool is_max[4] = {false, false, false, false};
-  block_reduce<4>(f, is_max);
-  if (threadIdx.x != 0) return;
-  st->pi_iters += 1;
-  for (int which = 0; which < 2; ++which) {
-    if (st->pi_done[which]) continue;
-    if (which == 0 && !have_rows) { st->pi_done[0] = 1; st->pi_lam[0] = 0.0; continue; }
-    const double lam = f[2 * which], nw = sqrt(f[2 * which + 1]);
-    st->pi_lam[which] = lam;
-    if (nw == 0.0) { st->pi_lam[which] = 0.0; st->pi_done[which] = 1; continue; }
-    if (fabs(lam - st->pi_lam_prev[which]) <= tol * fabs(lam)) { st->pi_done[which] = 1; continue; }
-    st->pi_lam_prev[which] = lam;
-    st->pi_inv_norm[which] = 1.0 / nw;
-  }
-}
-
-// --------------------------------------------------------------------------
-// Start point: x = proj_X(x0 / D2), y = proj_Y(y0 / D1), zeros by default
-// (Section 5 "Algorithms"); averages, x_md, x_tilde and anchors = start.
-// --------------------------------------------------------------------------
-__global__ void k_init_iterates(int n, int m, int m_eq, const double* __restrict__ x0,
-                                const double* __restrict__ y0, const double* __restrict__ D1,
-                                const double* __restrict__ D2, const double* __restrict__ ls,
-                                const double* __restrict__ us, double* x, double* xbar, double* xmd0,
-                                double* xt, double* ax, double* y, double* ybar, double* ay) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    double v = x0 ? x0[i] / D2[i] : 0.0;
-    v = fmin(fmax(v, ls[i]), us[i]);
-    x[i] = v; xbar[i] = v; xmd0[i] = v; xt[i] = v; ax[i] = v;
-  }
-  if (i < m) {
-    double v = y0 ? y0[i] / D1[i] : 0.0;
-    if (i >= m_eq) v = fmax(v, 0.0);
-    y[i] = v; ybar[i] = v; ay[i] = v;
-  }
-}
-
-// --------------------------------------------------------------------------
-// One inner iteration of Algorithm 1: the dual half-step (rows of A)
-// --------------------------------------------------------------------------
-template <typename V>
-struct DualArgs {
-  Csr<V> A;
-  const V* __restrict__ xt;      // extrapolated primal point x_tilde
-  V* __restrict__ y;
-  V* __restrict__ ybar;
-  const V* __restrict__ b;
-  const V* __restrict__ ylo;     // lower bound of inequality duals (mixed mode shift) or null (0)
-  const StepEntry* __restrict__ tab;
-  int m, m_eq;
-};
-
-template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
-template <> __device__ __forceinline__ double step_sigma<double>(const StepEntry& e) { return e.sigma_d; }
-template <> __device__ __forceinline__ float step_sigma<float>(const StepEntry& e) { return e.sigma_d_f; }
-template <typename V> __device__ __forceinline__ V step_tau(const StepEntry& e);
-template <> __device__ __forceinline__ double step_tau<double>(const StepEntry& e) { return e.tau_p; }
-template <> __device__ __forceinline__ float step_tau<float>(const StepEntry& e) { return e.tau_p_f; }
-template <typename V> __device__ __forceinline__ V step_ib(const StepEntry& e);
-template <> __device__ __forceinline__ double step_ib<double>(const StepEntry& e) { return e.inv_beta; }
-template <> __device__ __forceinline__ float step_ib<float>(const StepEntry& e) { return e.inv_beta_f; }
-template <typename V> __device__ __forceinline__ V step_ibn(const StepEntry& e);
-template <> __device__ __forceinline__ double step_ibn<double>(const StepEntry& e) { return e.inv_beta_next; }
-template <> __device__ __forceinline__ float step_ibn<float>(const StepEntry& e) { return e.inv_beta_next_f; }
-template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
-template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
-template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
-
-template <int L, typename V>
-__global__ void __launch_bounds__(256) k_dual(DualArgs<V> a, int j) {
-  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
-  const int lane = threadIdx.x % L;
-  const bool valid = row < a.m;
-  V s = V(0);
-  if (valid) s = row_dot_partial<L, V, V, V>(a.A, a.xt, a.A.rp[row], a.A.rp[row + 1], lane);
-  s = group_sum<L>(s);
-  if (valid && lane == 0) {
-    const StepEntry& e = a.tab[j];
-    const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
-    V yn = a.y[row] - sigma * (s - a.b[row]);
-    if (row >= a.m_eq) yn = a.ylo ? fmax(yn, a.ylo[row]) : fmax(yn, V(0));
-    a.ybar[row] = (V(1) - ib) * a.ybar[row] + ib * yn;
-    a.y[row] = yn;
-  }
-}
-
-// --------------------------------------------------------------------------
-// One inner iteration of Algorithm 1: the primal half-step (rows of Q and A')
-// --------------------------------------------------------------------------
-template <typename V>
-struct PrimalArgs {
-  Csr<V> Q, At;
-  const V* __restrict__ xmd_in;  // x_md of this iteration
-  V* __restrict__ xmd_out;       // x_md of the next iteration
-  const V* __restrict__ y;       // y^{k+1}
-  V* __restrict__ x;
-  V* __restrict__ xbar;
-  V* __restrict__ xt;            // x_tilde of the next iteration
-  const V* __restrict__ c;
-  const V* __restrict__ l;
-  const V* __restrict__ u;
-  const StepEntry* __restrict__ tab;
-  int n, m;
-};
-
-template <int L, typename V>
-__global__ void __launch_bounds__(256) k_primal(PrimalArgs<V> a, int j) {
-  const int row = blockIdx.x * (256 / L) + threadIdx.x / L;
-  const int lane = threadIdx.x % L;
-  const bool valid = row < a.n;
-  V s = V(0);
-  if (valid) {
-    s = row_dot_partial<L, V, V, V>(a.Q, a.xmd_in, a.Q.rp[row], a.Q.rp[row + 1], lane);
-    if (a.m > 0) s -= row_dot_partial<L, V, V, V>(a.At, a.y, a.At.rp[row], a.At.rp[row + 1], lane);
-  }
-  s = group_sum<L>(s);
-  if (valid && lane == 0) {
-    const StepEntry& e = a.tab[j];
-    const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
-    const V xo = a.x[row];
-    const V g = s + a.c[row];
-    const V xn = fmin(fmax(xo - tau * g, a.l[row]), a.u[row]);
-    const V xb = (V(1) - ib) * a.xbar[row] + ib * xn;
-    a.xbar[row] = xb;
-    a.xmd_out[row] = (V(1) - ibn) * xb + ibn * xn;
-    a.xt[row] = xn + thn * (xn - xo);
-    a.x[row] = xn;
-  }
-}
-
-// --------------------------------------------------------------------------
+// Per-row relative KKT kernels on separate Q, A, A' CSR arrays (used by
+// pdqp_kkt_noalloc, which takes caller-owned arrays).
 // Relative KKT error (Section 5 "Progress metric", equality/bound form) in
 // float64, for NIT iterates at once, measured on the original problem:
 // (Ax)_i = (A~ x~)_i / D1_i, (Qx)_j = (Q~ x~)_j / D2_j, (A'y)_j = (A~' y~)_j / D2_j.
-// Partial sums go to part[block][field]; k_decide finishes them.
+// Partial sums go to part[block][field]; k_kkt_finish_noalloc finishes them.
 // --------------------------------------------------------------------------
 struct KktArgs {
   Csr<double> A, Q, At;                 // scaled (or original with D = null)
@@ -498,6 +247,688 @@ __device__ void reduce_kkt_partials(const double* __restrict__ part, int nblk, d
     for (int k = 0; k < 24; ++k) F[k] = f[k];
 }
 
+// ==========================================================================
+// Row-block staging: the products val[e] * vec[col[e]] of one block's
+// nonzeros go to shared memory prod[0..ne); srp[t] = rp[r0+t] - e0.
+// ==========================================================================
+template <typename V, typename X>
+__device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
+                                               int r0, int nr, V* prod, int* srp) {
+  const int tid = threadIdx.x;
+  int ci[BEPT];
+  V vv[BEPT];
+#pragma unroll
+  for (int k = 0; k < BEPT; ++k) {
+    const int e = tid + k * BNT;
+    if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
+  }
+  for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+#pragma unroll
+  for (int k = 0; k < BEPT; ++k) {
+    const int e = tid + k * BNT;
+    if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
+  }
+}
+
+// --------------------------------------------------------------------------
+// One inner iteration of Algorithm 1: the dual half-step (rows of A)
+// --------------------------------------------------------------------------
+template <typename V>
+struct DualB {
+  BCsr<V> A;
+  const V* __restrict__ xt;      // extrapolated primal point x_tilde
+  const V* __restrict__ yold;    // y^k
+  V* __restrict__ ynew;          // y^{k+1}
+  V* __restrict__ ybar;
+  const V* __restrict__ b;
+  const V* __restrict__ ylo;     // lower bound of inequality duals (mixed-mode shift) or null (0)
+  const StepEntry* __restrict__ tab;
+  int m, m_eq;
+};
+
+template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
+template <> __device__ __forceinline__ double step_sigma<double>(const StepEntry& e) { return e.sigma_d; }
+template <> __device__ __forceinline__ float step_sigma<float>(const StepEntry& e) { return e.sigma_d_f; }
+template <typename V> __device__ __forceinline__ V step_tau(const StepEntry& e);
+template <> __device__ __forceinline__ double step_tau<double>(const StepEntry& e) { return e.tau_p; }
+template <> __device__ __forceinline__ float step_tau<float>(const StepEntry& e) { return e.tau_p_f; }
+template <typename V> __device__ __forceinline__ V step_ib(const StepEntry& e);
+template <> __device__ __forceinline__ double step_ib<double>(const StepEntry& e) { return e.inv_beta; }
+template <> __device__ __forceinline__ float step_ib<float>(const StepEntry& e) { return e.inv_beta_f; }
+template <typename V> __device__ __forceinline__ V step_ibn(const StepEntry& e);
+template <> __device__ __forceinline__ double step_ibn<double>(const StepEntry& e) { return e.inv_beta_next; }
+template <> __device__ __forceinline__ float step_ibn<float>(const StepEntry& e) { return e.inv_beta_next_f; }
+template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
+template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
+template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
+
+template <typename V>
+__device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, int r, V s, V yo, V bi, V yb,
+                                         V lo) {
+  const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
+  V yn = yo - sigma * (s - bi);
+  if (r >= a.m_eq) yn = fmax(yn, lo);
+  a.ybar[r] = (V(1) - ib) * yb + ib * yn;
+  a.ynew[r] = yn;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BNT) k_dual(DualB<V> a, int j) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int r0 = a.A.blk[blockIdx.x], r1 = a.A.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = a.A.rp[r0];
+  const int ne = a.A.rp[r1] - e0;
+  // operands of this thread's first row, fetched before the SpMV
+  V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
+  if (tid < nr) {
+    const int r = r0 + tid;
+    yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+    if (a.ylo && r >= a.m_eq) lo = a.ylo[r];
+  }
+  const StepEntry& es = a.tab[j];
+  if (ne <= BNNZ) {
+    stage_products(a.A, a.xt, e0, ne, r0, nr, prod, srp);
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      V s = V(0);
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
+      const int r = r0 + t;
+      if (t >= BNT) {
+        yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+        lo = (a.ylo && r >= a.m_eq) ? a.ylo[r] : V(0);
+      }
+      dual_row(a, es, r, s, yo, bi, yb, lo);
+    }
+  } else {   // a single row longer than a block
+    V s = V(0);
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
+    s = block_sum(s);
+    if (tid == 0) dual_row(a, es, r0, s, yo, bi, yb, lo);
+  }
+}
+
+// --------------------------------------------------------------------------
+// One inner iteration of Algorithm 1: the primal half-step (rows of P)
+// --------------------------------------------------------------------------
+template <typename V>
+struct PrimalB {
+  BCsr<V> P;
+  const V* __restrict__ zin;     // [x_md ; y^{k+1}] of this iteration
+  V* __restrict__ zout;          // x_md of the next iteration -> zout[0:n]
+  V* __restrict__ x;
+  V* __restrict__ xbar;
+  V* __restrict__ xt;            // x_tilde of the next iteration
+  const V* __restrict__ c;
+  const V* __restrict__ l;
+  const V* __restrict__ u;
+  const StepEntry* __restrict__ tab;
+  int n;
+};
+
+template <typename V>
+__device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry& e, int r, V s, V xo, V xb0,
+                                           V cr, V lr, V ur) {
+  const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
+  const V g = s + cr;
+  const V xn = fmin(fmax(xo - tau * g, lr), ur);
+  const V xb = (V(1) - ib) * xb0 + ib * xn;
+  a.xbar[r] = xb;
+  a.zout[r] = (V(1) - ibn) * xb + ibn * xn;
+  a.xt[r] = xn + thn * (xn - xo);
+  a.x[r] = xn;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BNT) k_primal(PrimalB<V> a, int j) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int r0 = a.P.blk[blockIdx.x], r1 = a.P.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = a.P.rp[r0];
+  const int ne = a.P.rp[r1] - e0;
+  V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
+  if (tid < nr) {
+    const int r = r0 + tid;
+    xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
+  }
+  const StepEntry& es = a.tab[j];
+  if (ne <= BNNZ) {
+    stage_products(a.P, a.zin, e0, ne, r0, nr, prod, srp);
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      V s = V(0);
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
+      const int r = r0 + t;
+      if (t >= BNT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
+      primal_row(a, es, r, s, xo, xb, cr, lr, ur);
+    }
+  } else {
+    V s = V(0);
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
+    s = block_sum(s);
+    if (tid == 0) primal_row(a, es, r0, s, xo, xb, cr, lr, ur);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Relative KKT error (Section 5 "Progress metric", equality/bound form) in
+// float64 for NIT iterates, on the original problem:
+// (Ax)_i = (A~x~)_i / D1_i, (Qx)_j = (Q~x~)_j / D2_j, (A'y)_j = (A~'y~)_j / D2_j.
+// Block partial sums go to part_m[field][block] / part_n[field][block].
+// --------------------------------------------------------------------------
+struct KktB {
+  BCsr<double> A, P;                    // scaled (or original with D = null)
+  const double* x[2];                   // iterates (scaled space), x: [n], y: [m]
+  const double* y[2];
+  const double* ax;                     // anchors for the restart distances (null: none)
+  const double* ay;
+  const double *D1, *D2, *iD1, *iD2;    // null = 1
+  const double *b, *c, *l, *u;          // original data
+  double* prodAx[2];                    // optional: A~x~, Q~x~, A~'y~ per iterate
+  double* prodQx[2];
+  double* prodATy[2];
+  double* part_m;                       // [9][nblk_m]
+  double* part_n;                       // [15][nblk_n]
+  int nblk_m, nblk_n;
+  int n, m, m_eq;
+};
+
+template <int NIT>
+__global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
+  // fields: it*4 + {0 max|viol|, 1 max|Ax|, 2 b'y, 3 |dy|^2}, 8: max|b|
+  __shared__ double prod[NIT][BNNZ];
+  __shared__ int srp[BROWS + 1];
+  double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int tid = threadIdx.x;
+  const int r0 = a.A.blk[blockIdx.x], r1 = a.A.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = a.A.rp[r0];
+  const int ne = a.A.rp[r1] - e0;
+  auto row = [&](int r, const double* s) {
+    const double d1 = a.D1 ? a.D1[r] : 1.0, id1 = a.iD1 ? a.iD1[r] : 1.0;
+    const double bi = a.b[r];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      if (a.prodAx[it]) a.prodAx[it][r] = s[it];
+      const double Ax = s[it] * id1;
+      const double viol = r < a.m_eq ? fabs(Ax - bi) : fmax(bi - Ax, 0.0);
+      f[it * 4 + 0] = nmax(f[it * 4 + 0], viol);
+      f[it * 4 + 1] = nmax(f[it * 4 + 1], fabs(Ax));
+      const double yt = a.y[it][r];
+      f[it * 4 + 2] += bi * (d1 * yt);
+      const double dy = a.ay ? yt - a.ay[r] : 0.0;
+      f[it * 4 + 3] += dy * dy;
+    }
+    f[8] = nmax(f[8], fabs(bi));
+  };
+  if (ne <= BNNZ) {
+    int ci[BEPT];
+    double vv[BEPT];
+#pragma unroll
+    for (int k = 0; k < BEPT; ++k) {
+      const int e = tid + k * BNT;
+      if (e < ne) { ci[k] = a.A.col[e0 + e]; vv[k] = a.A.val[e0 + e]; }
+    }
+    for (int t = tid; t <= nr; t += BNT) srp[t] = a.A.rp[r0 + t] - e0;
+#pragma unroll
+    for (int k = 0; k < BEPT; ++k) {
+      const int e = tid + k * BNT;
+      if (e < ne)
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) prod[it][e] = vv[k] * __ldg(a.x[it] + ci[k]);
+    }
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      double s[NIT];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        s[it] = 0.0;
+        for (int e = srp[t]; e < srp[t + 1]; ++e) s[it] += prod[it][e];
+      }
+      row(r0 + t, s);
+    }
+  } else {
+    double s[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) s[it] = 0.0;
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) {
+      const double v = a.A.val[e];
+      const int c = a.A.col[e];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) s[it] += v * __ldg(a.x[it] + c);
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) s[it] = block_sum(s[it]);
+    if (tid == 0) row(r0, s);
+  }
+  const bool is_max[9] = {true, true, false, false, true, true, false, false, true};
+  block_reduce<9>(f, is_max);
+  if (tid == 0)
+    for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
+}
+
+template <int NIT>
+__global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
+  // fields (offset 9): it*7 + {0 max|res|, 1 max|Qx|, 2 max|A'y|, 3 x'Qx, 4 c'x,
+  // 5 sum(l lam+ - u lam-), 6 |dx|^2}, 14: max|c|
+  __shared__ double prod[NIT][BNNZ];
+  __shared__ int srp[BROWS + 1];
+  __shared__ int ssp[BROWS];
+  double f[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) f[k] = 0.0;
+  const int tid = threadIdx.x;
+  const int r0 = a.P.blk[blockIdx.x], r1 = a.P.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = a.P.rp[r0];
+  const int ne = a.P.rp[r1] - e0;
+  const int n = a.n;
+  auto row = [&](int r, const double* sq, const double* sa) {
+    const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
+    const double cj = a.c[r], lj = a.l[r], uj = a.u[r];
+    const bool lf = isfinite(lj), uf = isfinite(uj);
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      if (a.prodQx[it]) { a.prodQx[it][r] = sq[it]; a.prodATy[it][r] = -sa[it]; }
+      const double Qx = sq[it] * id2, ATy = -sa[it] * id2;
+      const double xt = a.x[it][r];
+      const double xj = d2 * xt;
+      const double g = Qx + cj - ATy;
+      const double lam = (lf && uf) ? g : (lf ? fmax(g, 0.0) : (uf ? fmin(g, 0.0) : 0.0));
+      double* fi = f + it * 7;
+      fi[0] = nmax(fi[0], fabs(g - lam));
+      fi[1] = nmax(fi[1], fabs(Qx));
+      fi[2] = nmax(fi[2], fabs(ATy));
+      fi[3] += xj * Qx;
+      fi[4] += cj * xj;
+      fi[5] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+      const double dx = a.ax ? xt - a.ax[r] : 0.0;
+      fi[6] += dx * dx;
+    }
+    f[14] = nmax(f[14], fabs(cj));
+  };
+  if (ne <= BNNZ) {
+    int ci[BEPT];
+    double vv[BEPT];
+#pragma unroll
+    for (int k = 0; k < BEPT; ++k) {
+      const int e = tid + k * BNT;
+      if (e < ne) { ci[k] = a.P.col[e0 + e]; vv[k] = a.P.val[e0 + e]; }
+    }
+    for (int t = tid; t <= nr; t += BNT) srp[t] = a.P.rp[r0 + t] - e0;
+    for (int t = tid; t < nr; t += BNT) ssp[t] = a.P.split[r0 + t] - e0;
+#pragma unroll
+    for (int k = 0; k < BEPT; ++k) {
+      const int e = tid + k * BNT;
+      if (e < ne) {
+        const int c = ci[k];
+#pragma unroll
+        for (int it = 0; it < NIT; ++it)
+          prod[it][e] = vv[k] * (c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n)));
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      double sq[NIT], sa[NIT];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        sq[it] = 0.0; sa[it] = 0.0;
+        for (int e = srp[t]; e < ssp[t]; ++e) sq[it] += prod[it][e];
+        for (int e = ssp[t]; e < srp[t + 1]; ++e) sa[it] += prod[it][e];
+      }
+      row(r0 + t, sq, sa);
+    }
+  } else {
+    const int sp = a.P.split[r0];
+    double sq[NIT], sa[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) { sq[it] = 0.0; sa[it] = 0.0; }
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) {
+      const double v = a.P.val[e];
+      const int c = a.P.col[e];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (e < sp) sq[it] += v * __ldg(a.x[it] + c);
+        else sa[it] += v * __ldg(a.y[it] + (c - n));
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) { sq[it] = block_sum(sq[it]); sa[it] = block_sum(sa[it]); }
+    if (tid == 0) row(r0, sq, sa);
+  }
+  const bool is_max[15] = {true, true, true, false, false, false, false,
+                           true, true, true, false, false, false, false, true};
+  block_reduce<15>(f, is_max);
+  if (tid == 0)
+    for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
+}
+
+// reduce the field-major partials of k_kkt_m / k_kkt_n into F[0..23] (thread 0)
+__device__ void reduce_kkt_blocks(const double* __restrict__ pm, int nbm, const double* __restrict__ pn,
+                                  int nbn, double* F) {
+  double f[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) f[k] = 0.0;
+  const bool is_max[24] = {true, true, false, false, true, true, false, false, true,
+                           true, true, true, false, false, false, false,
+                           true, true, true, false, false, false, false, true};
+  for (int b = threadIdx.x; b < nbm; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double v = pm[(size_t)k * nbm + b];
+      f[k] = is_max[k] ? nmax(f[k], v) : f[k] + v;
+    }
+  for (int b = threadIdx.x; b < nbn; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const double v = pn[(size_t)k * nbn + b];
+      f[9 + k] = is_max[9 + k] ? nmax(f[9 + k], v) : f[9 + k] + v;
+    }
+  block_reduce<24>(f, is_max);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 24; ++k) F[k] = f[k];
+}
+
+// --------------------------------------------------------------------------
+// Preconditioning (Section 5 "Preprocessing"): norms of the rows of D K D,
+// K = [[Q, A'], [A, 0]] -- the rows of P (index j) and of A (index n+i); the
+// columns of P already index d = (D2, D1).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(BNT) k_scale_norms(BCsr<double> M, const double* __restrict__ d, int doff,
+                                                     int dcol_off, double* __restrict__ nu, int kind) {
+  __shared__ double av[BNNZ];
+  __shared__ double dc[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int r0 = M.blk[blockIdx.x], r1 = M.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = M.rp[r0];
+  const int ne = M.rp[r1] - e0;
+  auto take = [&](double acc, double v) {
+    return kind == 0 ? fmax(acc, v) : (kind == 1 ? acc + v * v : acc + v);
+  };
+  if (ne <= BNNZ) {
+#pragma unroll
+    for (int k = 0; k < BEPT; ++k) {
+      const int e = tid + k * BNT;
+      if (e < ne) { av[e] = fabs(M.val[e0 + e]); dc[e] = d[dcol_off + M.col[e0 + e]]; }
+    }
+    for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      const double dr = d[doff + r0 + t];
+      double acc = 0.0;
+      for (int e = srp[t]; e < srp[t + 1]; ++e) acc = take(acc, (av[e] * dr) * dc[e]);
+      nu[doff + r0 + t] = kind == 1 ? sqrt(acc) : acc;
+    }
+  } else {
+    const double dr = d[doff + r0];
+    double acc = 0.0;
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) acc = take(acc, (fabs(M.val[e]) * dr) * d[dcol_off + M.col[e]]);
+    if (kind == 0) {
+      __shared__ double sh[BNT];
+      sh[tid] = acc;
+      __syncthreads();
+      for (int o = BNT / 2; o > 0; o >>= 1) {
+        if (tid < o) sh[tid] = fmax(sh[tid], sh[tid + o]);
+        __syncthreads();
+      }
+      acc = sh[0];
+    } else {
+      acc = block_sum(acc);
+    }
+    if (tid == 0) nu[doff + r0] = kind == 1 ? sqrt(acc) : acc;
+  }
+}
+
+__global__ void k_scale_update(double* __restrict__ d, const double* __restrict__ nu, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    const double v = nu[i];
+    d[i] = d[i] / sqrt(v > 0.0 ? v : 1.0);
+  }
+}
+
+__global__ void k_fill(double* __restrict__ p, double v, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) p[i] = v;
+}
+
+__global__ void k_inverse(const double* __restrict__ d, double* __restrict__ id, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) id[i] = 1.0 / d[i];
+}
+
+// Scaled values of a row-blocked matrix: (d_row * v) * d_col, or for the A'
+// part of P (entries e >= split) (d_col * v) * d_row, which keeps every entry
+// bitwise equal to the corresponding entry (D1 A D2)_ij.
+__global__ void __launch_bounds__(BNT) k_scale_vals(BCsr<double> M, const double* __restrict__ d, int doff,
+                                                    int dcol_off, double* __restrict__ out,
+                                                    float* __restrict__ out_f) {
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int r0 = M.blk[blockIdx.x], r1 = M.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = M.rp[r0];
+  const int ne = M.rp[r1] - e0;
+  for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+  __syncthreads();
+  for (int e = tid; e < ne; e += BNT) {
+    // row of element e: the last t with srp[t] <= e
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (srp[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int r = r0 + lo;
+    const double dr = d[doff + r], dcv = d[dcol_off + M.col[e0 + e]], v = M.val[e0 + e];
+    const bool tr = M.split && (e0 + e) >= M.split[r];
+    const double sv = tr ? (dcv * v) * dr : (dr * v) * dcv;
+    out[e0 + e] = sv;
+    if (out_f) out_f[e0 + e] = (float)sv;
+  }
+}
+
+// c~ = D2 c, l~ = l / D2, u~ = u / D2 (n);  b~ = D1 b (m)
+__global__ void k_scale_vectors(int n, int m, const double* __restrict__ D1, const double* __restrict__ D2,
+                                const double* __restrict__ c, const double* __restrict__ b,
+                                const double* __restrict__ l, const double* __restrict__ u,
+                                double* __restrict__ cs, double* __restrict__ bs, double* __restrict__ ls,
+                                double* __restrict__ us, float* __restrict__ fcs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double d = D2[i];
+    cs[i] = d * c[i];
+    ls[i] = l[i] / d;
+    us[i] = u[i] / d;
+  }
+  if (i < m) bs[i] = D1[i] * b[i];
+}
+
+// --------------------------------------------------------------------------
+// Power iteration for ||A~||_2 (on A~'A~) and ||Q~||_2, both from the
+// normalised all-ones vector.  v_A = u * sa, v_Q = z * sq (sa, sq the inverse
+// norms of the previous u, z); pz = [z ; w] is the input of the P rows.
+// --------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(BNT) k_pi_m(BCsr<V> A, const V* __restrict__ u, V* __restrict__ pz_w,
+                                              const DevState* __restrict__ st) {
+  if (st->pi_done[0]) return;
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int r0 = A.blk[blockIdx.x], r1 = A.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = A.rp[r0];
+  const int ne = A.rp[r1] - e0;
+  const V sa = (V)st->pi_inv_norm[0];
+  if (ne <= BNNZ) {
+    stage_products(A, u, e0, ne, r0, nr, prod, srp);
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      V s = V(0);
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
+      pz_w[r0 + t] = s * sa;
+    }
+  } else {
+    V s = V(0);
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) s += A.val[e] * __ldg(u + A.col[e]);
+    s = block_sum(s);
+    if (tid == 0) pz_w[r0] = s * sa;
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BNT) k_pi_n(BCsr<V> P, const V* __restrict__ pz_old, V* __restrict__ pz_new,
+                                              const V* __restrict__ u_old, V* __restrict__ u_new,
+                                              const DevState* __restrict__ st, double* __restrict__ part,
+                                              int nblk, int have_rows) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  __shared__ int ssp[BROWS];
+  const bool doA = !st->pi_done[0] && have_rows;
+  const bool doQ = !st->pi_done[1];
+  const double sa = st->pi_inv_norm[0], sq = st->pi_inv_norm[1];
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  const int tid = threadIdx.x;
+  const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
+  const int nr = r1 - r0;
+  const int e0 = P.rp[r0];
+  const int ne = P.rp[r1] - e0;
+  auto row = [&](int r, double sQ, double sA) {
+    if (doA) {
+      const double un = -sA;                 // (A~'w)_r: P holds -A~'
+      u_new[r] = (V)un;
+      f[0] += ((double)u_old[r] * sa) * un;
+      f[1] += un * un;
+    }
+    if (doQ) {
+      const double z = sQ * sq;              // Q~ (z_old sq)
+      pz_new[r] = (V)z;
+      f[2] += ((double)pz_old[r] * sq) * z;
+      f[3] += z * z;
+    }
+  };
+  if (ne <= BNNZ) {
+    stage_products(P, pz_old, e0, ne, r0, nr, prod, srp);
+    for (int t = tid; t < nr; t += BNT) ssp[t] = P.split[r0 + t] - e0;
+    __syncthreads();
+    for (int t = tid; t < nr; t += BNT) {
+      V q = V(0), w = V(0);
+      for (int e = srp[t]; e < ssp[t]; ++e) q += prod[e];
+      for (int e = ssp[t]; e < srp[t + 1]; ++e) w += prod[e];
+      row(r0 + t, (double)q, (double)w);
+    }
+  } else {
+    const int sp = P.split[r0];
+    V q = V(0), w = V(0);
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) {
+      const V v = P.val[e] * __ldg(pz_old + P.col[e]);
+      if (e < sp) q += v; else w += v;
+    }
+    q = block_sum(q);
+    w = block_sum(w);
+    if (tid == 0) row(r0, (double)q, (double)w);
+  }
+  const bool is_max[4] = {false, false, false, false};
+  block_reduce<4>(f, is_max);
+  if (tid == 0)
+    for (int k = 0; k < 4; ++k) part[(size_t)k * nblk + blockIdx.x] = f[k];
+}
+
+__global__ void k_pi_update(DevState* __restrict__ st, const double* __restrict__ part, int nblk, double tol,
+                            int have_rows) {
+  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int k = 0; k < 4; ++k) f[k] += part[(size_t)k * nblk + b];
+  const bool is_max[4] = {false, false, false, false};
+  block_reduce<4>(f, is_max);
+  if (threadIdx.x != 0) return;
+  st->pi_iters += 1;
+  for (int which = 0; which < 2; ++which) {
+    if (st->pi_done[which]) continue;
+    if (which == 0 && !have_rows) { st->pi_done[0] = 1; st->pi_lam[0] = 0.0; continue; }
+    const double lam = f[2 * which], nw = sqrt(f[2 * which + 1]);
+    st->pi_lam[which] = lam;
+    if (nw == 0.0) { st->pi_lam[which] = 0.0; st->pi_done[which] = 1; continue; }
+    if (fabs(lam - st->pi_lam_prev[which]) <= tol * fabs(lam)) { st->pi_done[which] = 1; continue; }
+    st->pi_lam_prev[which] = lam;
+    st->pi_inv_norm[which] = 1.0 / nw;
+  }
+}
+
+__global__ void k_pi_init(DevState* st, int n) {
+  st->pi_done[0] = 0; st->pi_done[1] = 0;
+  st->pi_lam[0] = 0.0; st->pi_lam[1] = 0.0;
+  st->pi_lam_prev[0] = 0.0; st->pi_lam_prev[1] = 0.0;
+  st->pi_inv_norm[0] = 1.0 / sqrt((double)n);
+  st->pi_inv_norm[1] = 1.0 / sqrt((double)n);
+  st->pi_iters = 0;
+}
+
+template <typename V>
+__global__ void k_fill_v(V* __restrict__ p, V v, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) p[i] = v;
+}
+
+__global__ void k_set_norms(DevState* st, double nA, double nQ) {
+  st->normA = nA > 0.0 ? nA : sqrt(fmax(st->pi_lam[0], 0.0));
+  st->normQ = nQ > 0.0 ? nQ : fmax(st->pi_lam[1], 0.0);
+}
+
+// ||c~||, ||b~|| -> InitializePrimalWeight
+__global__ void k_sumsq2(const double* __restrict__ a, int na, const double* __restrict__ b, int nb,
+                         double* __restrict__ part) {
+  double f[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(na, nb); i += gridDim.x * blockDim.x) {
+    if (i < na) f[0] += a[i] * a[i];
+    if (i < nb) f[1] += b[i] * b[i];
+  }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (threadIdx.x == 0) { part[blockIdx.x * 32] = f[0]; part[blockIdx.x * 32 + 1] = f[1]; }
+}
+
+__global__ void k_init_omega(DevState* st, const double* __restrict__ part, int nblk, double eps_zero) {
+  double f[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b * 32]; f[1] += part[b * 32 + 1]; }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (threadIdx.x == 0) {
+    const double nc = sqrt(f[0]), nb = sqrt(f[1]);
+    st->omega = (nc > eps_zero && nb > eps_zero) ? nc / nb : 1.0;
+    st->eta_last = 0.0;
+    st->status = ST_RUNNING;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Start point: x = proj_X(x0 / D2), y = proj_Y(y0 / D1), zeros by default
+// (Section 5 "Algorithms"); averages, x_md, x_tilde and anchors = start.
+// --------------------------------------------------------------------------
+__global__ void k_init_iterates(int n, int m, int m_eq, const double* __restrict__ x0,
+                                const double* __restrict__ y0, const double* __restrict__ D1,
+                                const double* __restrict__ D2, const double* __restrict__ ls,
+                                const double* __restrict__ us, double* x, double* xbar, double* xmd0,
+                                double* xt, double* ax, double* y, double* ybar, double* ay) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = x0 ? x0[i] / D2[i] : 0.0;
+    v = fmin(fmax(v, ls[i]), us[i]);
+    x[i] = v; xbar[i] = v; xmd0[i] = v; xt[i] = v; ax[i] = v;
+  }
+  if (i < m) {
+    double v = y0 ? y0[i] / D1[i] : 0.0;
+    if (i >= m_eq) v = fmax(v, 0.0);
+    y[i] = v; ybar[i] = v; ay[i] = v;
+  }
+}
+
 // Section 6 step size eta^{n,k}
 __device__ double pdqp_eta(long long k, double eta_prev, double nQ, double nA, double omega) {
   const double q = nQ / omega;
@@ -541,10 +972,12 @@ __device__ void fill_steps(DevState& S, const SolveParams& p, StepEntry* tab) {
 // mode 0: evaluate z^{0,0} (anchor, maybe already optimal); mode 1: a check
 // after `chunk_len` more iterations (Section 6 restart rule, termination
 // eq. (terminate), iteration limit).
-__global__ void k_decide(DevState* __restrict__ st, const double* __restrict__ part, int nblk,
-                         StepEntry* __restrict__ tab, SolveParams p, int mode, long long chunk_len) {
+__global__ void __launch_bounds__(1024) k_decide(DevState* __restrict__ st, const double* __restrict__ pm,
+                                                 int nbm, const double* __restrict__ pn, int nbn,
+                                                 StepEntry* __restrict__ tab, SolveParams p, int mode,
+                                                 long long chunk_len) {
   __shared__ double F[24];
-  reduce_kkt_partials(part, nblk, F);
+  reduce_kkt_blocks(pm, nbm, pn, nbn, F);
   if (threadIdx.x != 0) return;
   DevState& S = *st;
   double P[2][6];
@@ -636,7 +1069,6 @@ __global__ void k_unscale_out(int n, int m, const double* __restrict__ D1, const
   if (y_out && i < m) y_out[i] = D1[i] * ys[i];
 }
 
-
 // --------------------------------------------------------------------------
 // Mixed precision (float32 iteration, float64 checks).  The iteration runs on
 // the shifted problem in (dx, dy) = (x - x_hi, y - y_hi) around a float64 base
@@ -715,22 +1147,6 @@ __global__ void k_mixed_rebase(MixedArgs a, const DevState* __restrict__ st, int
 // ==========================================================================
 // Host-side launchers
 // ==========================================================================
-static int pick_lanes(long long nnz, long long rows) {
-  const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
-  int L = 2;
-  while (L < 32 && L < avg) L <<= 1;
-  return L;
-}
-
-#define DISPATCH_L(L, ...)                               \
-  switch (L) {                                           \
-    case 2: { constexpr int LL = 2; __VA_ARGS__; } break;   \
-    case 4: { constexpr int LL = 4; __VA_ARGS__; } break;   \
-    case 8: { constexpr int LL = 8; __VA_ARGS__; } break;   \
-    case 16: { constexpr int LL = 16; __VA_ARGS__; } break; \
-    default: { constexpr int LL = 32; __VA_ARGS__; } break; \
-  }
-
 void scale_reset(Work& w, cudaStream_t s) {
   const long long N = (long long)w.n + w.m;
   launch(k_fill, cdiv(N, 256), 256, 0, s, w.dsc, 1.0, N);
@@ -738,89 +1154,53 @@ void scale_reset(Work& w, cudaStream_t s) {
 
 void scale_pass(Work& w, int kind, cudaStream_t s) {
   const int N = w.n + w.m;
-  const int L = pick_lanes(w.Q.nnz + 2 * w.A.nnz, N);
-  DISPATCH_L(L, launch(k_scale_norms<LL>, cdiv(N, 256 / LL), 256, 0, s, w.Q.orig(), w.At.orig(),
-                       w.A.orig(), w.dsc, w.nu, w.n, w.m, kind));
-  launch(k_scale_update, cdiv(N, 256), 256, 0, s, w.dsc, w.nu, N);
+  launch(k_scale_norms, w.P.nblk, BNT, 0, s, w.P.borig(), (const double*)w.dsc, 0, 0, w.nu, kind);
+  launch(k_scale_norms, w.A.nblk, BNT, 0, s, w.A.borig(), (const double*)w.dsc, w.n, 0, w.nu, kind);
+  launch(k_scale_update, cdiv(N, 256), 256, 0, s, w.dsc, (const double*)w.nu, N);
 }
 
 void scale_apply(Work& w, bool mixed, cudaStream_t s) {
-  const int LQ = pick_lanes(w.Q.nnz, w.n);
-  DISPATCH_L(LQ, launch(k_scale_csr<LL>, cdiv(w.n, 256 / LL), 256, 0, s, w.n, w.Q.orig(), w.Q.sval,
-                        mixed ? w.Q.sval_f : nullptr, w.D2, w.D2, 0));
-  if (w.m > 0) {
-    const int LA = pick_lanes(w.A.nnz, w.m);
-    DISPATCH_L(LA, launch(k_scale_csr<LL>, cdiv(w.m, 256 / LL), 256, 0, s, w.m, w.A.orig(), w.A.sval,
-                          mixed ? w.A.sval_f : nullptr, w.D1, w.D2, 0));
-    const int LT = pick_lanes(w.At.nnz, w.n);
-    DISPATCH_L(LT, launch(k_scale_csr<LL>, cdiv(w.n, 256 / LL), 256, 0, s, w.n, w.At.orig(), w.At.sval,
-                          mixed ? w.At.sval_f : nullptr, w.D2, w.D1, 1));
+  const int N = w.n + w.m;
+  launch(k_inverse, cdiv(N, 256), 256, 0, s, (const double*)w.dsc, w.idsc, N);
+  launch(k_scale_vals, w.P.nblk, BNT, 0, s, w.P.borig(), (const double*)w.dsc, 0, 0, w.P.sval,
+         mixed ? w.P.sval_f : (float*)nullptr);
+  launch(k_scale_vals, w.A.nblk, BNT, 0, s, w.A.borig(), (const double*)w.dsc, w.n, 0, w.A.sval,
+         mixed ? w.A.sval_f : (float*)nullptr);
+  const int NN = w.n > w.m ? w.n : w.m;
+  launch(k_scale_vectors, cdiv(NN, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
+         (const double*)w.c, (const double*)w.b, (const double*)w.l, (const double*)w.u, w.cs, w.bs, w.ls, w.us,
+         (float*)nullptr);
+}
+
+void power_init(Work& w, bool mixed, cudaStream_t s) {
+  const long long N = w.n;
+  if (mixed) {
+    launch(k_fill_v<float>, cdiv(N, 256), 256, 0, s, w.fpu[0], 1.0f, N);
+    launch(k_fill_v<float>, cdiv(N, 256), 256, 0, s, w.fpz[0], 1.0f, N);
+  } else {
+    launch(k_fill_v<double>, cdiv(N, 256), 256, 0, s, w.pu[0], 1.0, N);
+    launch(k_fill_v<double>, cdiv(N, 256), 256, 0, s, w.pz[0], 1.0, N);
   }
-  const int N = w.n > w.m ? w.n : w.m;
-  launch(k_scale_vectors, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.c, w.b, w.l, w.u, w.cs, w.bs,
-         w.ls, w.us);
-}
-
-__global__ void k_pi_init(DevState* st, int n) {
-  st->pi_done[0] = 0; st->pi_done[1] = 0;
-  st->pi_lam[0] = 0.0; st->pi_lam[1] = 0.0;
-  st->pi_lam_prev[0] = 0.0; st->pi_lam_prev[1] = 0.0;
-  st->pi_inv_norm[0] = 1.0 / sqrt((double)n);
-  st->pi_inv_norm[1] = 1.0 / sqrt((double)n);
-  st->pi_iters = 0;
-}
-
-void power_init(Work& w, cudaStream_t s) {
-  launch(k_fill, cdiv(w.n, 256), 256, 0, s, w.pv[0], 1.0, (long long)w.n);
-  launch(k_fill, cdiv(w.n, 256), 256, 0, s, w.pq[0], 1.0, (long long)w.n);
   launch(k_pi_init, 1, 1, 0, s, w.st, w.n);
 }
 
-void power_iter(Work& w, int t, const SolveParams& p, cudaStream_t s) {
+template <typename V>
+static void power_iter_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr<V> P, V* const* pu, V* const* pz,
+                         cudaStream_t s) {
   const int cur = t & 1, nxt = cur ^ 1;
-  if (w.m > 0) {
-    const int LA = pick_lanes(w.A.nnz, w.m);
-    DISPATCH_L(LA, launch(k_pi_m<LL>, cdiv(w.m, 256 / LL), 256, 0, s, w.A.scaled(), w.pv[cur], w.pw, w.m, w.st));
-  }
-  const int LN = pick_lanes(w.Q.nnz + w.At.nnz, w.n);
-  DISPATCH_L(LN, launch(k_pi_n<LL>, PDQP_RED_BLOCKS, 256, 0, s, w.At.scaled(), w.Q.scaled(), w.pw, w.pv[cur],
-                        w.pv[nxt], w.pq[cur], w.pq[nxt], w.n, w.m, w.st, w.part));
-  launch(k_pi_update, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, p.power_tol, w.m > 0 ? 1 : 0);
+  if (w.m > 0) launch(k_pi_m<V>, w.A.nblk, BNT, 0, s, A, (const V*)pu[cur], pz[cur] + w.n, (const DevState*)w.st);
+  launch(k_pi_n<V>, w.P.nblk, BNT, 0, s, P, (const V*)pz[cur], pz[nxt], (const V*)pu[cur], pu[nxt],
+         (const DevState*)w.st, w.part_n, w.P.nblk, w.m > 0 ? 1 : 0);
+  launch(k_pi_update, 1, 1024, 0, s, w.st, (const double*)w.part_n, w.P.nblk, p.power_tol, w.m > 0 ? 1 : 0);
 }
 
-__global__ void k_set_norms(DevState* st, double nA, double nQ) {
-  st->normA = nA > 0.0 ? nA : sqrt(fmax(st->pi_lam[0], 0.0));
-  st->normQ = nQ > 0.0 ? nQ : fmax(st->pi_lam[1], 0.0);
+void power_iter(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s) {
+  if (mixed) power_iter_t<float>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, s);
+  else power_iter_t<double>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, s);
 }
 
 void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
   launch(k_set_norms, 1, 1, 0, s, w.st, normA_opt, normQ_opt);
-}
-
-// ||c~||, ||b~|| -> InitializePrimalWeight
-__global__ void k_sumsq2(const double* __restrict__ a, int na, const double* __restrict__ b, int nb,
-                         double* __restrict__ part) {
-  double f[2] = {0.0, 0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(na, nb); i += gridDim.x * blockDim.x) {
-    if (i < na) f[0] += a[i] * a[i];
-    if (i < nb) f[1] += b[i] * b[i];
-  }
-  const bool is_max[2] = {false, false};
-  block_reduce<2>(f, is_max);
-  if (threadIdx.x == 0) { part[blockIdx.x * 32] = f[0]; part[blockIdx.x * 32 + 1] = f[1]; }
-}
-
-__global__ void k_init_omega(DevState* st, const double* __restrict__ part, int nblk, double eps_zero) {
-  double f[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b * 32]; f[1] += part[b * 32 + 1]; }
-  const bool is_max[2] = {false, false};
-  block_reduce<2>(f, is_max);
-  if (threadIdx.x == 0) {
-    const double nc = sqrt(f[0]), nb = sqrt(f[1]);
-    st->omega = (nc > eps_zero && nb > eps_zero) ? nc / nb : 1.0;
-    st->eta_last = 0.0;
-    st->status = ST_RUNNING;
-  }
 }
 
 static MixedArgs mixed_args(Work& w) {
@@ -828,154 +1208,140 @@ static MixedArgs mixed_args(Work& w) {
   a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
   a.cs = w.cs; a.bs = w.bs; a.ls = w.ls; a.us = w.us; a.D1 = w.D1; a.D2 = w.D2;
   a.xhi = w.xhi; a.yhi = w.yhi;
-  a.fx = w.fx; a.fxbar = w.fxbar; a.fxt = w.fxt; a.fxmd0 = w.fxmd[0]; a.fy = w.fy; a.fybar = w.fybar;
+  a.fx = w.fx; a.fxbar = w.fxbar; a.fxt = w.fxt; a.fxmd0 = w.fZ[0]; a.fy = w.fy; a.fybar = w.fybar;
   a.fc = w.fc; a.fl = w.fl; a.fu = w.fu; a.fb = w.fb; a.fylo = w.fylo;
-  a.x64[0] = w.x; a.x64[1] = w.xbar; a.y64[0] = w.y; a.y64[1] = w.ybar;
+  a.x64[0] = w.x; a.x64[1] = w.xbar; a.y64[0] = w.yk; a.y64[1] = w.ybar;
   a.prodAx = w.prodAx; a.prodQx = w.prodQx; a.prodATy = w.prodATy;
   return a;
 }
 
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s) {
-  launch(k_sumsq2, PDQP_RED_BLOCKS, 256, 0, s, w.cs, w.n, w.bs, w.m, w.part);
-  launch(k_init_omega, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, p.eps_zero);
+  launch(k_sumsq2, PDQP_RED_BLOCKS, 256, 0, s, (const double*)w.cs, w.n, (const double*)w.bs, w.m, w.part);
+  launch(k_init_omega, 1, 256, 0, s, w.st, (const double*)w.part, PDQP_RED_BLOCKS, p.eps_zero);
   const int N = w.n > w.m ? w.n : w.m;
   if (p.mixed) {
+    w.fy = w.fZ[1] + w.n;
+    w.y = w.yk;
     launch(k_init_mixed, cdiv(N, 256), 256, 0, s, mixed_args(w), x0, y0);
     return;
   }
-  launch(k_init_iterates, cdiv(N, 256), 256, 0, s, w.n, w.m, w.m_eq, x0, y0, w.D1, w.D2, w.ls, w.us, w.x,
-         w.xbar, w.xmd[0], w.xt, w.ax, w.y, w.ybar, w.ay);
+  w.y = w.Z[1] + w.n;
+  launch(k_init_iterates, cdiv(N, 256), 256, 0, s, w.n, w.m, w.m_eq, x0, y0, (const double*)w.D1,
+         (const double*)w.D2, (const double*)w.ls, (const double*)w.us, w.x, w.xbar, w.Z[0], w.xt, w.ax, w.y,
+         w.ybar, w.ay);
 }
 
-static void iterate_chunk_mixed(Work& w, int len, int lanesA, int lanesP, cudaStream_t s) {
-  DualArgs<float> da{w.A.scaled_f(), w.fxt, w.fy, w.fybar, w.fb, w.fylo, w.tab, w.m, w.m_eq};
-  PrimalArgs<float> pa{w.Q.scaled_f(), w.At.scaled_f(), nullptr, nullptr, w.fy, w.fx, w.fxbar, w.fxt,
-                       w.fc, w.fl, w.fu, w.tab, w.n, w.m};
-  Profiler& P = w.prof;
+template <typename V>
+static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
+                      const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
+  Profiler& Pr = w.prof;
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.m, w.m_eq};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.n};
   for (int j = 0; j < len; ++j) {
     if (w.m > 0) {
-      if (P.on) P.begin(0, s);
-      DISPATCH_L(lanesA, launch(k_dual<LL, float>, cdiv(w.m, 256 / LL), 256, 0, s, da, j));
-      if (P.on) P.end(s);
+      da.yold = Z[(j + 1) & 1] + w.n;
+      da.ynew = Z[j & 1] + w.n;
+      if (Pr.on) Pr.begin(0, s);
+      launch(k_dual<V>, w.A.nblk, BNT, 0, s, da, j);
+      if (Pr.on) Pr.end(s);
     }
-    pa.xmd_in = w.fxmd[j & 1];
-    pa.xmd_out = w.fxmd[(j + 1) & 1];
-    if (P.on) P.begin(1, s);
-    DISPATCH_L(lanesP, launch(k_primal<LL, float>, cdiv(w.n, 256 / LL), 256, 0, s, pa, j));
-    if (P.on) P.end(s);
+    pa.zin = Z[j & 1];
+    pa.zout = Z[(j + 1) & 1];
+    if (Pr.on) Pr.begin(1, s);
+    launch(k_primal<V>, w.P.nblk, BNT, 0, s, pa, j);
+    if (Pr.on) Pr.end(s);
   }
 }
 
-void iterate_chunk(Work& w, int len, int lanesA, int lanesP, bool mixed, cudaStream_t s) {
+void iterate_chunk(Work& w, int len, bool mixed, cudaStream_t s) {
   if (mixed) {
-    iterate_chunk_mixed(w, len, lanesA, lanesP, s);
-    return;
-  }
-  DualArgs<double> da{w.A.scaled(), w.xt, w.y, w.ybar, w.bs, nullptr, w.tab, w.m, w.m_eq};
-  PrimalArgs<double> pa{w.Q.scaled(), w.At.scaled(), nullptr, nullptr, w.y, w.x, w.xbar, w.xt,
-                        w.cs, w.ls, w.us, w.tab, w.n, w.m};
-  Profiler& P = w.prof;
-  for (int j = 0; j < len; ++j) {
-    if (w.m > 0) {
-      if (P.on) P.begin(0, s);
-      DISPATCH_L(lanesA, launch(k_dual<LL, double>, cdiv(w.m, 256 / LL), 256, 0, s, da, j));
-      if (P.on) P.end(s);
-    }
-    pa.xmd_in = w.xmd[j & 1];
-    pa.xmd_out = w.xmd[(j + 1) & 1];
-    if (P.on) P.begin(1, s);
-    DISPATCH_L(lanesP, launch(k_primal<LL, double>, cdiv(w.n, 256 / LL), 256, 0, s, pa, j));
-    if (P.on) P.end(s);
+    run_chunk<float>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx, w.fxbar,
+                     w.fc, w.fl, w.fu, s);
+    w.fy = w.fZ[(len - 1) & 1] + w.n;
+  } else {
+    run_chunk<double>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar, w.cs,
+                      w.ls, w.us, s);
+    w.y = w.Z[(len - 1) & 1] + w.n;
   }
 }
 
-static KktArgs kkt_args_scaled(Work& w) {
-  KktArgs a{};
-  a.A = w.A.scaled(); a.Q = w.Q.scaled(); a.At = w.At.scaled();
+static KktB kkt_args(Work& w, bool scaled) {
+  KktB a{};
+  a.A = scaled ? w.A.bscaled() : w.A.borig();
+  a.P = scaled ? w.P.bscaled() : w.P.borig();
   a.x[0] = w.x; a.x[1] = w.xbar; a.y[0] = w.y; a.y[1] = w.ybar;
   a.ax = w.ax; a.ay = w.ay;
-  a.D1 = w.D1; a.D2 = w.D2;
+  if (scaled) { a.D1 = w.D1; a.D2 = w.D2; a.iD1 = w.iD1; a.iD2 = w.iD2; }
   a.b = w.b; a.c = w.c; a.l = w.l; a.u = w.u;
-  a.part = w.part;
+  a.part_m = w.part_m; a.part_n = w.part_n;
+  a.nblk_m = w.A.nblk; a.nblk_n = w.P.nblk;
   a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
   return a;
-}
-
-static void launch_kkt(Work& w, const KktArgs& a, int nit, cudaStream_t s) {
-  const int LA = pick_lanes(w.A.nnz, w.m);
-  const int LN = pick_lanes(w.Q.nnz + w.At.nnz, w.n);
-  if (nit == 2) {
-    DISPATCH_L(LA, launch(k_kkt_m<LL, 2, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
-    DISPATCH_L(LN, launch(k_kkt_n<LL, 2, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
-  } else {
-    DISPATCH_L(LA, launch(k_kkt_m<LL, 1, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
-    DISPATCH_L(LN, launch(k_kkt_n<LL, 1, false>, PDQP_RED_BLOCKS, 256, 0, s, a));
-  }
 }
 
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s) {
   if (w.prof.on) w.prof.begin(2, s);
   const int NN = w.n > w.m ? w.n : w.m;
   const int grid_v = cdiv(NN, 256) < 4 * w.num_sms ? cdiv(NN, 256) : 4 * w.num_sms;
-  KktArgs a = kkt_args_scaled(w);
   if (mixed) {
     MixedArgs ma = mixed_args(w);
     launch(k_materialize, grid_v, 256, 0, s, ma);
+  }
+  KktB a = kkt_args(w, true);
+  if (mixed) {
     a.ax = w.xhi; a.ay = w.yhi;
     for (int it = 0; it < 2; ++it) {
       a.prodAx[it] = w.prodAx + (size_t)it * w.m;
       a.prodQx[it] = w.prodQx + (size_t)it * w.n;
       a.prodATy[it] = w.prodATy + (size_t)it * w.n;
     }
-    launch_kkt(w, a, 2, s);
-    launch(k_decide, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, w.tab, p, mode, chunk_len);
-    launch(k_mixed_rebase, grid_v, 256, 0, s, ma, w.st, mode == 0 ? 1 : 0);
-    if (w.prof.on) w.prof.end(s);
-    return;
   }
-  launch_kkt(w, a, 2, s);
-  launch(k_decide, 1, 256, 0, s, w.st, w.part, PDQP_RED_BLOCKS, w.tab, p, mode, chunk_len);
-  if (mode == 1) {
-    const int N = w.n > w.m ? w.n : w.m;
-    const int grid = cdiv(N, 256) < 4 * w.num_sms ? cdiv(N, 256) : 4 * w.num_sms;
-    launch(k_restart_apply, grid, 256, 0, s, w.st, w.n, w.m, w.x, w.xbar, w.xmd[0], w.xt, w.ax, w.y, w.ybar,
-           w.ay);
+  if (w.m > 0) launch(k_kkt_m<2>, w.A.nblk, BNT, 0, s, a);
+  launch(k_kkt_n<2>, w.P.nblk, BNT, 0, s, a);
+  launch(k_decide, 1, 1024, 0, s, w.st, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,
+         (const double*)w.part_n, w.P.nblk, w.tab, p, mode, chunk_len);
+  if (mixed) {
+    launch(k_mixed_rebase, grid_v, 256, 0, s, mixed_args(w), (const DevState*)w.st, mode == 0 ? 1 : 0);
+  } else if (mode == 1) {
+    launch(k_restart_apply, grid_v, 256, 0, s, (const DevState*)w.st, w.n, w.m, w.x, w.xbar, w.Z[0], w.xt, w.ax,
+           w.y, w.ybar, w.ay);
   }
   if (w.prof.on) w.prof.end(s);
 }
 
-
-void write_output(Work& w, double* x_out, double* y_out, bool mixed, cudaStream_t s) {
-  (void)mixed;
+void write_output(Work& w, double* x_out, double* y_out, cudaStream_t s) {
   const int N = w.n > w.m ? w.n : w.m;
-  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.x, w.xbar, w.y, w.ybar, w.st, -1,
-         x_out, y_out);
+  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
+         (const double*)w.x, (const double*)w.xbar, (const double*)w.y, (const double*)w.ybar,
+         (const DevState*)w.st, -1, x_out, y_out);
 }
 
-void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, bool mixed, cudaStream_t s) {
-  (void)mixed;
+void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, cudaStream_t s) {
   const int N = w.n > w.m ? w.n : w.m;
-  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.x, w.xbar, w.y, w.ybar, w.st, 0, x, y);
-  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, w.D1, w.D2, w.x, w.xbar, w.y, w.ybar, w.st, 1, xbar,
-         ybar);
+  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
+         (const double*)w.x, (const double*)w.xbar, (const double*)w.y, (const double*)w.ybar,
+         (const DevState*)w.st, 0, x, y);
+  launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
+         (const double*)w.x, (const double*)w.xbar, (const double*)w.y, (const double*)w.ybar,
+         (const DevState*)w.st, 1, xbar, ybar);
 }
 
 // relKKT of a user (x, y) on the original matrices (D = 1)
-__global__ void k_kkt_finish_user(const double* __restrict__ part, int nblk, DevState* st) {
+__global__ void __launch_bounds__(1024) k_kkt_finish_user(const double* __restrict__ pm, int nbm,
+                                                          const double* __restrict__ pn, int nbn, DevState* st) {
   __shared__ double F[24];
-  reduce_kkt_partials(part, nblk, F);
+  reduce_kkt_blocks(pm, nbm, pn, nbn, F);
   if (threadIdx.x == 0) kkt_from_fields(F, 0, st->out_parts);
 }
 
 void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
-  KktArgs a{};
-  a.A = w.A.orig(); a.Q = w.Q.orig(); a.At = w.At.orig();
+  KktB a = kkt_args(w, false);
   a.x[0] = x; a.x[1] = x; a.y[0] = y; a.y[1] = y;
-  a.b = w.b; a.c = w.c; a.l = w.l; a.u = w.u;
-  a.part = w.part;
-  a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
-  launch_kkt(w, a, 1, s);
-  launch(k_kkt_finish_user, 1, 256, 0, s, w.part, PDQP_RED_BLOCKS, w.st);
+  a.ax = nullptr; a.ay = nullptr;
+  if (w.m > 0) launch(k_kkt_m<1>, w.A.nblk, BNT, 0, s, a);
+  launch(k_kkt_n<1>, w.P.nblk, BNT, 0, s, a);
+  launch(k_kkt_finish_user, 1, 1024, 0, s, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,
+         (const double*)w.part_n, w.P.nblk, w.st);
 }
 
 }  // namespace pdqp

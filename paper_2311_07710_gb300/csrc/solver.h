@@ -9,17 +9,40 @@
 
 #include "common.cuh"
 
+// Row blocks: every CUDA block of the SpMV kernels takes whole rows
+// [blk[b], blk[b+1]) holding at most BNNZ nonzeros and BROWS rows; a row longer
+// than BNNZ forms a block of its own.
+constexpr int BNT = 256;            // threads per block
+constexpr int BEPT = 8;             // nonzeros staged per thread
+constexpr int BNNZ = BNT * BEPT;    // nonzeros per row block
+constexpr int BROWS = 512;          // rows per row block
+
+template <typename V>
+struct BCsr {
+  const int* __restrict__ rp;
+  const int* __restrict__ col;
+  const V* __restrict__ val;
+  const int* __restrict__ blk;     // row-block starts [nblk+1]
+  const int* __restrict__ split;   // P only: first index of the A' part of each row
+};
+
 struct DCsr {
   int rows = 0;
   long long nnz = 0;
+  int nblk = 0;
   int* rp = nullptr;          // [rows+1]
   int* col = nullptr;         // [nnz]
+  int* blk = nullptr;         // [nblk+1]
+  int* split = nullptr;       // [rows] (P only)
   double* val = nullptr;      // original values
   double* sval = nullptr;     // scaled values, float64
   float* sval_f = nullptr;    // scaled values, float32 (mixed precision)
   Csr<double> orig() const { return Csr<double>{rp, col, val}; }
   Csr<double> scaled() const { return Csr<double>{rp, col, sval}; }
   Csr<float> scaled_f() const { return Csr<float>{rp, col, sval_f}; }
+  BCsr<double> borig() const { return BCsr<double>{rp, col, val, blk, split}; }
+  BCsr<double> bscaled() const { return BCsr<double>{rp, col, sval, blk, split}; }
+  BCsr<float> bscaled_f() const { return BCsr<float>{rp, col, sval_f, blk, split}; }
 };
 
 // Optional CUDA-event timing of kernel launches (per kind, see pdqp_profile).
@@ -39,17 +62,22 @@ struct Profiler {
 struct Work {
   int n = 0, m = 0, m_eq = 0;
   int num_sms = 152;
-  DCsr Q, A, At;                              // At = transpose of A (n rows)
+  DCsr P, A;   // P = [Q | -A'] (n rows, columns n+i for the A' part), A (m rows)
   double *c = nullptr, *b = nullptr, *l = nullptr, *u = nullptr;        // original data
   double *cs = nullptr, *bs = nullptr, *ls = nullptr, *us = nullptr;    // scaled data
   double *D1 = nullptr, *D2 = nullptr;        // views into dsc: D2 = dsc[0:n], D1 = dsc[n:n+m]
-  double *dsc = nullptr, *nu = nullptr;       // scaling vector and row norms [n+m]
+  double *iD1 = nullptr, *iD2 = nullptr;      // views into idsc = 1 / dsc
+  double *dsc = nullptr, *idsc = nullptr, *nu = nullptr;   // scaling vector, inverse, row norms [n+m]
   double *ones = nullptr;                     // [max(n,m)] of 1.0
-  // float64 iterates (scaled space)
-  double *x = nullptr, *xbar = nullptr, *xt = nullptr, *xmd[2] = {nullptr, nullptr};
-  double *y = nullptr, *ybar = nullptr, *ax = nullptr, *ay = nullptr;
+  // float64 iterates (scaled space).  Z[p] = [x_md ; y] (n+m): the primal
+  // kernel of inner iteration j gathers Z[j&1] and writes the next x_md to
+  // Z[(j+1)&1]; the dual kernel reads y from Z[(j+1)&1] and writes y+ to Z[j&1].
+  double *x = nullptr, *xbar = nullptr, *xt = nullptr, *Z[2] = {nullptr, nullptr};
+  double *ybar = nullptr, *ax = nullptr, *ay = nullptr;
+  double *y = nullptr;         // the current y: Z[(len-1)&1] + n after a chunk of len iterations
+  double *yk = nullptr;        // mixed mode: float64 materialised current y [m]
   // float32 iterates of the mixed mode (deltas from the float64 base xhi, yhi)
-  float *fx = nullptr, *fxbar = nullptr, *fxt = nullptr, *fxmd[2] = {nullptr, nullptr};
+  float *fx = nullptr, *fxbar = nullptr, *fxt = nullptr, *fZ[2] = {nullptr, nullptr};
   float *fy = nullptr, *fybar = nullptr;
   float *fc = nullptr, *fb = nullptr, *fl = nullptr, *fu = nullptr, *fylo = nullptr;  // shifted data
   double *xhi = nullptr, *yhi = nullptr;
@@ -60,10 +88,13 @@ struct Work {
   float* Fs = nullptr;       // row-scaled by D2
   double* Fd = nullptr;      // float64 copy of Fs (for the float64 paths)
   double* wlr = nullptr;     // [2][r] F'x partial buffers
-  // power iteration
-  double *pv[2] = {nullptr, nullptr}, *pq[2] = {nullptr, nullptr}, *pw = nullptr;
+  // power iteration: pu[p] (n) holds u = A~'w, pz[p] = [z ; w] (n+m) the P input
+  double *pu[2] = {nullptr, nullptr}, *pz[2] = {nullptr, nullptr};
+  float *fpu[2] = {nullptr, nullptr}, *fpz[2] = {nullptr, nullptr};
   // reductions
-  double *part = nullptr;    // [PDQP_RED_BLOCKS][32]
+  double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
+  double *part_m = nullptr;  // [9][A.nblk]  field-major partial sums of the row-block kernels
+  double *part_n = nullptr;  // [15][P.nblk]
   StepEntry* tab = nullptr;  // [PDQP_MAX_CHECK]
   DevState* st = nullptr;
   DevState* st_host = nullptr;   // pinned mirror
@@ -80,18 +111,18 @@ extern long long g_launches;
 void scale_pass(Work& w, int kind, cudaStream_t s);          // kind: 0 inf, 1 l2, 2 l1
 void scale_reset(Work& w, cudaStream_t s);
 void scale_apply(Work& w, bool mixed, cudaStream_t s);
-void power_init(Work& w, cudaStream_t s);
-void power_iter(Work& w, int t, const SolveParams& p, cudaStream_t s);
+void power_init(Work& w, bool mixed, cudaStream_t s);
+void power_iter(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s);
 void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 
 // iteration
-void iterate_chunk(Work& w, int len, int lanesA, int lanesP, bool mixed, cudaStream_t s);
+void iterate_chunk(Work& w, int len, bool mixed, cudaStream_t s);
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
 
 // results
-void write_output(Work& w, double* x_out, double* y_out, bool mixed, cudaStream_t s);
-void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, bool mixed, cudaStream_t s);
+void write_output(Work& w, double* x_out, double* y_out, cudaStream_t s);
+void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, cudaStream_t s);
 void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s);
 
 }  // namespace pdqp
