@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 256, 512])
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="variables of the workload (m = n/2); smaller only for profiler captures")
     return ap.parse_args()
@@ -203,7 +204,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     inst = qpgen.large_sparse_qp(seed=qpgen.SEED_BASE + 1 + rank, n=args.n)
     prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
-    opts = pdqp.pdqp_default_options(precision=prec)
+    opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=args.spmv_threads)
 
     # ---- device-resident leg ----
     h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,

@@ -99,8 +99,10 @@ typedef struct {
                                 matrices; <= 0: estimate by power iteration */
   int32_t power_iters;       /* 500 */
   double power_tol;          /* 1e-6 relative change of the Rayleigh quotient */
-  int32_t lanes_A, lanes_P;  /* reserved, must be 0, 2, 4, 8, 16 or 32; ignored
-                                (the kernels work on row blocks) */
+  int32_t spmv_threads;      /* iteration-kernel variant: 256 or 512 threads per row
+                                block, 1 = pipelined persistent (cp.async prefetch of
+                                the next row block), 0 = library choice (256) */
+  int32_t reserved;          /* must be 0 */
 } pdqp_options;
 
 typedef struct {

@@ -133,10 +133,15 @@ void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& 
                 const std::vector<double>& val, const std::vector<int32_t>* split, cudaStream_t s) {
   M.rows = rows;
   M.nnz = rp[rows];
-  M.rp = dalloc<int>(h, rows + 1);
-  M.col = dalloc<int>(h, M.nnz);
-  M.val = dalloc<double>(h, M.nnz);
-  M.sval = dalloc<double>(h, M.nnz);
+  // 8 elements of padding: the pipelined kernels copy 16-byte aligned supersets
+  M.rp = dalloc<int>(h, rows + 1 + 8);
+  M.col = dalloc<int>(h, M.nnz + 8);
+  M.val = dalloc<double>(h, M.nnz + 8);
+  M.sval = dalloc<double>(h, M.nnz + 8);
+  CK(cudaMemsetAsync(M.rp, 0, (rows + 1 + 8) * sizeof(int), s));
+  CK(cudaMemsetAsync(M.col, 0, (M.nnz + 8) * sizeof(int), s));
+  CK(cudaMemsetAsync(M.val, 0, (M.nnz + 8) * sizeof(double), s));
+  CK(cudaMemsetAsync(M.sval, 0, (M.nnz + 8) * sizeof(double), s));
   to_device(M.rp, rp.data(), rows + 1, s);
   to_device(M.col, col.data(), M.nnz, s);
   to_device(M.val, val.data(), M.nnz, s);
@@ -144,6 +149,15 @@ void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& 
   M.nblk = (int)blk.size() - 1;
   M.blk = dalloc<int>(h, blk.size());
   to_device(M.blk, blk.data(), blk.size(), s);
+  std::vector<int32_t> meta(4 * (size_t)(M.nblk > 0 ? M.nblk : 1), 0);
+  for (int b = 0; b < M.nblk; ++b) {
+    meta[4 * b + 0] = blk[b];
+    meta[4 * b + 1] = blk[b + 1];
+    meta[4 * b + 2] = rp[blk[b]];
+    meta[4 * b + 3] = rp[blk[b + 1]];
+  }
+  M.meta = dalloc<int>(h, meta.size());
+  to_device(M.meta, meta.data(), meta.size(), s);
   if (split) {
     M.split = dalloc<int>(h, rows);
     to_device(M.split, split->data(), rows, s);
@@ -155,8 +169,10 @@ void alloc_mixed(pdqp_problem* h) {
   if (h->mixed_ready) return;
   Work& w = h->w;
   const int n = w.n, m = w.m;
-  w.P.sval_f = dalloc<float>(h, w.P.nnz);
-  w.A.sval_f = dalloc<float>(h, w.A.nnz);
+  w.P.sval_f = dalloc<float>(h, w.P.nnz + 8);
+  w.A.sval_f = dalloc<float>(h, w.A.nnz + 8);
+  CK(cudaMemset(w.P.sval_f, 0, (w.P.nnz + 8) * sizeof(float)));
+  CK(cudaMemset(w.A.sval_f, 0, (w.A.nnz + 8) * sizeof(float)));
   w.fx = dalloc<float>(h, n); w.fxbar = dalloc<float>(h, n); w.fxt = dalloc<float>(h, n);
   w.fZ[0] = dalloc<float>(h, (size_t)n + m); w.fZ[1] = dalloc<float>(h, (size_t)n + m);
   w.fybar = dalloc<float>(h, m); w.yk = dalloc<double>(h, m);
@@ -188,6 +204,7 @@ SolveParams make_params(const pdqp_options& o) {
   p.eps_zero = o.eps_zero;
   p.power_tol = o.power_tol;
   p.power_iters = o.power_iters;
+  p.spmv_threads = o.spmv_threads;
   return p;
 }
 
@@ -203,8 +220,8 @@ void validate_options(const pdqp_options& o) {
   if ((o.restart_rule == PDQP_RESTART_FIXED || o.step_rule == PDQP_STEP_THEORY) && o.fixed_K < 1)
     bad("options.fixed_K must be >= 1");
   if (o.power_iters < 1) bad("options.power_iters must be >= 1");
-  for (int L : {o.lanes_A, o.lanes_P})
-    if (L != 0 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) bad("options.lanes_* must be 0,2,4,8,16,32");
+  if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 256 && o.spmv_threads != 512)
+    bad("options.spmv_threads must be 0, 1, 256 or 512");
 }
 
 double now_s() {
@@ -283,7 +300,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   bool timed_out = false;
   while (w.st_host->status == ST_RUNNING) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
-    pdqp::iterate_chunk(w, (int)len, mixed, s);
+    pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s);
     pdqp::check(w, p, 1, len, mixed, s);
     CK(cudaGetLastError());
     k_total += len;
@@ -361,8 +378,8 @@ void pdqp_default_options(pdqp_options* o) {
   o->norm_Q = 0.0;
   o->power_iters = 500;
   o->power_tol = 1e-6;
-  o->lanes_A = 0;
-  o->lanes_P = 0;
+  o->spmv_threads = 0;
+  o->reserved = 0;
 }
 
 const char* pdqp_status_string(int32_t st) {

@@ -55,6 +55,7 @@ struct SolveParams {
   long long max_iter;
   double eps, beta_suff, beta_nec, beta_art, pw_theta, eps_zero, power_tol;
   int power_iters;
+  int spmv_threads;     // threads per row block of the iteration kernels (256 or 512)
 };
 
 // Device view of one CSR matrix.

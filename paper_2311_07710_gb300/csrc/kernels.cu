@@ -18,6 +18,8 @@
 // reads and writes consecutive entries of the row-indexed vectors.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "solver.h"
 
 namespace pdqp {
@@ -251,24 +253,30 @@ __device__ void reduce_kkt_partials(const double* __restrict__ part, int nblk, d
 // Row-block staging: the products val[e] * vec[col[e]] of one block's
 // nonzeros go to shared memory prod[0..ne); srp[t] = rp[r0+t] - e0.
 // ==========================================================================
-template <typename V, typename X>
+template <int NT, typename V, typename X>
 __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
                                                int r0, int nr, V* prod, int* srp) {
+  constexpr int EPT = BNNZ / NT;
   const int tid = threadIdx.x;
-  int ci[BEPT];
-  V vv[BEPT];
+  int ci[EPT];
+  V vv[EPT];
 #pragma unroll
-  for (int k = 0; k < BEPT; ++k) {
-    const int e = tid + k * BNT;
+  for (int k = 0; k < EPT; ++k) {
+    const int e = tid + k * NT;
     if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
   }
-  for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+  for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
 #pragma unroll
-  for (int k = 0; k < BEPT; ++k) {
-    const int e = tid + k * BNT;
+  for (int k = 0; k < EPT; ++k) {
+    const int e = tid + k * NT;
     if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
   }
 }
+
+// Occupancy target of the iteration kernels: NT = 512 threads with at most 32
+// registers (4 blocks, 2048 threads per SM), NT = 256 with at most 64 (4 blocks).
+template <int NT> struct MinBlocks { static constexpr int value = 4; };
+template <> struct MinBlocks<512> { static constexpr int value = 4; };
 
 // --------------------------------------------------------------------------
 // One inner iteration of Algorithm 1: the dual half-step (rows of A)
@@ -312,8 +320,8 @@ __device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, 
   a.ynew[r] = yn;
 }
 
-template <typename V>
-__global__ void __launch_bounds__(BNT) k_dual(DualB<V> a, int j) {
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_dual(DualB<V> a, int j) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -330,9 +338,9 @@ __global__ void __launch_bounds__(BNT) k_dual(DualB<V> a, int j) {
   }
   const StepEntry& es = a.tab[j];
   if (ne <= BNNZ) {
-    stage_products(a.A, a.xt, e0, ne, r0, nr, prod, srp);
+    stage_products<NT>(a.A, a.xt, e0, ne, r0, nr, prod, srp);
     __syncthreads();
-    for (int t = tid; t < nr; t += BNT) {
+    for (int t = tid; t < nr; t += NT) {
       V s = V(0);
       for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
       const int r = r0 + t;
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(BNT) k_dual(DualB<V> a, int j) {
     }
   } else {   // a single row longer than a block
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
     s = block_sum(s);
     if (tid == 0) dual_row(a, es, r0, s, yo, bi, yb, lo);
   }
@@ -381,8 +389,8 @@ __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry&
   a.x[r] = xn;
 }
 
-template <typename V>
-__global__ void __launch_bounds__(BNT) k_primal(PrimalB<V> a, int j) {
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_primal(PrimalB<V> a, int j) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -397,9 +405,9 @@ __global__ void __launch_bounds__(BNT) k_primal(PrimalB<V> a, int j) {
   }
   const StepEntry& es = a.tab[j];
   if (ne <= BNNZ) {
-    stage_products(a.P, a.zin, e0, ne, r0, nr, prod, srp);
+    stage_products<NT>(a.P, a.zin, e0, ne, r0, nr, prod, srp);
     __syncthreads();
-    for (int t = tid; t < nr; t += BNT) {
+    for (int t = tid; t < nr; t += NT) {
       V s = V(0);
       for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
       const int r = r0 + t;
@@ -408,9 +416,154 @@ __global__ void __launch_bounds__(BNT) k_primal(PrimalB<V> a, int j) {
     }
   } else {
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
     s = block_sum(s);
     if (tid == 0) primal_row(a, es, r0, s, xo, xb, cr, lr, ur);
+  }
+}
+
+
+// ==========================================================================
+// Pipelined persistent variants of the two half-steps.  Each CUDA block loops
+// over row blocks b = blockIdx.x, blockIdx.x + gridDim.x, ...; while it
+// gathers and finishes block b, the index, value and row-pointer ranges of its
+// next block stream into the other shared-memory stage with cp.async (16-byte
+// copies of the 16-byte aligned superset of each range).  Block bounds come
+// from one int4 {r0, r1, e0, e1} per block.  Global index/value/rowptr arrays
+// carry 8 elements of padding so the aligned superset never leaves them.
+// ==========================================================================
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <typename V>
+struct PipeSmem {
+  int col[2][BNNZ + 8];
+  V val[2][BNNZ + 8];
+  int rp[2][BROWS + 8];
+  V prod[BNNZ];
+};
+
+// Queue the copies of block m = {r0, r1, e0, e1} into stage s (no copy for a long row).
+template <int NT, typename V>
+__device__ __forceinline__ void pipe_issue(PipeSmem<V>& sm, int s, const int4 m, const int* __restrict__ col,
+                                           const V* __restrict__ val, const int* __restrict__ rp) {
+  const int tid = threadIdx.x;
+  if (m.w - m.z <= BNNZ) {
+    const int a0 = m.z & ~3, a1 = (m.w + 3) & ~3;
+    for (int c = tid; c < (a1 - a0) >> 2; c += NT) cp_async16(&sm.col[s][c << 2], col + a0 + (c << 2));
+    constexpr int PER = 16 / sizeof(V);
+    for (int c = tid; c < (a1 - a0) / PER; c += NT) cp_async16(&sm.val[s][c * PER], val + a0 + c * PER);
+    const int q0 = m.x & ~3, q1 = (m.y + 1 + 3) & ~3;
+    for (int c = tid; c < (q1 - q0) >> 2; c += NT) cp_async16(&sm.rp[s][c << 2], rp + q0 + (c << 2));
+  }
+  cp_async_commit();
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __restrict__ meta, int nblk, int j) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
+  const int tid = threadIdx.x;
+  const StepEntry& es = a.tab[j];
+  int b = blockIdx.x;
+  if (b >= nblk) return;
+  int4 mc = meta[b];
+  pipe_issue<NT>(sm, 0, mc, a.A.col, a.A.val, a.A.rp);
+  for (int s = 0; b < nblk; b += gridDim.x, s ^= 1) {
+    const int bn = b + gridDim.x;
+    int4 mn = make_int4(0, 0, 0, 0);
+    if (bn < nblk) mn = meta[bn];
+    pipe_issue<NT>(sm, s ^ 1, mn, a.A.col, a.A.val, a.A.rp);
+    const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
+    V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
+    if (tid < nr) {
+      const int r = r0 + tid;
+      yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+      if (a.ylo && r >= a.m_eq) lo = a.ylo[r];
+    }
+    cp_async_wait1();
+    __syncthreads();
+    if (ne <= BNNZ) {
+      const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
+#pragma unroll
+      for (int k = 0; k < BNNZ / NT; ++k) {
+        const int e = tid + k * NT;
+        if (e < ne) sm.prod[e] = sm.val[s][e + off] * __ldg(a.xt + sm.col[s][e + off]);
+      }
+      __syncthreads();
+      for (int t = tid; t < nr; t += NT) {
+        V acc = V(0);
+        const int eb = sm.rp[s][t + roff] - e0, ee = sm.rp[s][t + 1 + roff] - e0;
+        for (int e = eb; e < ee; ++e) acc += sm.prod[e];
+        const int r = r0 + t;
+        if (t >= NT) {
+          yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+          lo = (a.ylo && r >= a.m_eq) ? a.ylo[r] : V(0);
+        }
+        dual_row(a, es, r, acc, yo, bi, yb, lo);
+      }
+    } else {
+      V acc = V(0);
+      for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
+      acc = block_sum(acc);
+      if (tid == 0) dual_row(a, es, r0, acc, yo, bi, yb, lo);
+    }
+    __syncthreads();
+    mc = mn;
+  }
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __restrict__ meta, int nblk, int j) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
+  const int tid = threadIdx.x;
+  const StepEntry& es = a.tab[j];
+  int b = blockIdx.x;
+  if (b >= nblk) return;
+  int4 mc = meta[b];
+  pipe_issue<NT>(sm, 0, mc, a.P.col, a.P.val, a.P.rp);
+  for (int s = 0; b < nblk; b += gridDim.x, s ^= 1) {
+    const int bn = b + gridDim.x;
+    int4 mn = make_int4(0, 0, 0, 0);
+    if (bn < nblk) mn = meta[bn];
+    pipe_issue<NT>(sm, s ^ 1, mn, a.P.col, a.P.val, a.P.rp);
+    const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
+    V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
+    if (tid < nr) {
+      const int r = r0 + tid;
+      xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
+    }
+    cp_async_wait1();
+    __syncthreads();
+    if (ne <= BNNZ) {
+      const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
+#pragma unroll
+      for (int k = 0; k < BNNZ / NT; ++k) {
+        const int e = tid + k * NT;
+        if (e < ne) sm.prod[e] = sm.val[s][e + off] * __ldg(a.zin + sm.col[s][e + off]);
+      }
+      __syncthreads();
+      for (int t = tid; t < nr; t += NT) {
+        V acc = V(0);
+        const int eb = sm.rp[s][t + roff] - e0, ee = sm.rp[s][t + 1 + roff] - e0;
+        for (int e = eb; e < ee; ++e) acc += sm.prod[e];
+        const int r = r0 + t;
+        if (t >= NT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
+        primal_row(a, es, r, acc, xo, xb, cr, lr, ur);
+      }
+    } else {
+      V acc = V(0);
+      for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
+      acc = block_sum(acc);
+      if (tid == 0) primal_row(a, es, r0, acc, xo, xb, cr, lr, ur);
+    }
+    __syncthreads();
+    mc = mn;
   }
 }
 
@@ -754,8 +907,8 @@ __global__ void k_scale_vectors(int n, int m, const double* __restrict__ D1, con
 // normalised all-ones vector.  v_A = u * sa, v_Q = z * sq (sa, sq the inverse
 // norms of the previous u, z); pz = [z ; w] is the input of the P rows.
 // --------------------------------------------------------------------------
-template <typename V>
-__global__ void __launch_bounds__(BNT) k_pi_m(BCsr<V> A, const V* __restrict__ u, V* __restrict__ pz_w,
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_pi_m(BCsr<V> A, const V* __restrict__ u, V* __restrict__ pz_w,
                                               const DevState* __restrict__ st) {
   if (st->pi_done[0]) return;
   __shared__ V prod[BNNZ];
@@ -767,23 +920,23 @@ __global__ void __launch_bounds__(BNT) k_pi_m(BCsr<V> A, const V* __restrict__ u
   const int ne = A.rp[r1] - e0;
   const V sa = (V)st->pi_inv_norm[0];
   if (ne <= BNNZ) {
-    stage_products(A, u, e0, ne, r0, nr, prod, srp);
+    stage_products<NT>(A, u, e0, ne, r0, nr, prod, srp);
     __syncthreads();
-    for (int t = tid; t < nr; t += BNT) {
+    for (int t = tid; t < nr; t += NT) {
       V s = V(0);
       for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
       pz_w[r0 + t] = s * sa;
     }
   } else {
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) s += A.val[e] * __ldg(u + A.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += A.val[e] * __ldg(u + A.col[e]);
     s = block_sum(s);
     if (tid == 0) pz_w[r0] = s * sa;
   }
 }
 
-template <typename V>
-__global__ void __launch_bounds__(BNT) k_pi_n(BCsr<V> P, const V* __restrict__ pz_old, V* __restrict__ pz_new,
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_pi_n(BCsr<V> P, const V* __restrict__ pz_old, V* __restrict__ pz_new,
                                               const V* __restrict__ u_old, V* __restrict__ u_new,
                                               const DevState* __restrict__ st, double* __restrict__ part,
                                               int nblk, int have_rows) {
@@ -814,10 +967,10 @@ __global__ void __launch_bounds__(BNT) k_pi_n(BCsr<V> P, const V* __restrict__ p
     }
   };
   if (ne <= BNNZ) {
-    stage_products(P, pz_old, e0, ne, r0, nr, prod, srp);
-    for (int t = tid; t < nr; t += BNT) ssp[t] = P.split[r0 + t] - e0;
+    stage_products<NT>(P, pz_old, e0, ne, r0, nr, prod, srp);
+    for (int t = tid; t < nr; t += NT) ssp[t] = P.split[r0 + t] - e0;
     __syncthreads();
-    for (int t = tid; t < nr; t += BNT) {
+    for (int t = tid; t < nr; t += NT) {
       V q = V(0), w = V(0);
       for (int e = srp[t]; e < ssp[t]; ++e) q += prod[e];
       for (int e = ssp[t]; e < srp[t + 1]; ++e) w += prod[e];
@@ -826,7 +979,7 @@ __global__ void __launch_bounds__(BNT) k_pi_n(BCsr<V> P, const V* __restrict__ p
   } else {
     const int sp = P.split[r0];
     V q = V(0), w = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) {
+    for (int e = e0 + tid; e < e0 + ne; e += NT) {
       const V v = P.val[e] * __ldg(pz_old + P.col[e]);
       if (e < sp) q += v; else w += v;
     }
@@ -1184,19 +1337,25 @@ void power_init(Work& w, bool mixed, cudaStream_t s) {
   launch(k_pi_init, 1, 1, 0, s, w.st, w.n);
 }
 
-template <typename V>
+template <typename V, int NT>
 static void power_iter_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr<V> P, V* const* pu, V* const* pz,
                          cudaStream_t s) {
   const int cur = t & 1, nxt = cur ^ 1;
-  if (w.m > 0) launch(k_pi_m<V>, w.A.nblk, BNT, 0, s, A, (const V*)pu[cur], pz[cur] + w.n, (const DevState*)w.st);
-  launch(k_pi_n<V>, w.P.nblk, BNT, 0, s, P, (const V*)pz[cur], pz[nxt], (const V*)pu[cur], pu[nxt],
+  if (w.m > 0)
+    launch(k_pi_m<V, NT>, w.A.nblk, NT, 0, s, A, (const V*)pu[cur], pz[cur] + w.n, (const DevState*)w.st);
+  launch(k_pi_n<V, NT>, w.P.nblk, NT, 0, s, P, (const V*)pz[cur], pz[nxt], (const V*)pu[cur], pu[nxt],
          (const DevState*)w.st, w.part_n, w.P.nblk, w.m > 0 ? 1 : 0);
   launch(k_pi_update, 1, 1024, 0, s, w.st, (const double*)w.part_n, w.P.nblk, p.power_tol, w.m > 0 ? 1 : 0);
 }
 
 void power_iter(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s) {
-  if (mixed) power_iter_t<float>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, s);
-  else power_iter_t<double>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, s);
+  if (p.spmv_threads != 512) {
+    if (mixed) power_iter_t<float, 256>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, s);
+    else power_iter_t<double, 256>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, s);
+  } else {
+    if (mixed) power_iter_t<float, 512>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, s);
+    else power_iter_t<double, 512>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, s);
+  }
 }
 
 void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
@@ -1231,7 +1390,55 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
          w.ybar, w.ay);
 }
 
-template <typename V>
+template <typename V, int NT>
+static int pipe_grid(void (*kern)(DualB<V>, const int4*, int, int)) {
+  static int blocks = -1;
+  if (blocks < 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
+    blocks = per_sm > 0 ? per_sm : 1;
+  }
+  return blocks;
+}
+template <typename V, int NT>
+static int pipe_grid_p(void (*kern)(PrimalB<V>, const int4*, int, int)) {
+  static int blocks = -1;
+  if (blocks < 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
+    blocks = per_sm > 0 ? per_sm : 1;
+  }
+  return blocks;
+}
+
+template <typename V, int NT>
+static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
+                           const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
+  Profiler& Pr = w.prof;
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.m, w.m_eq};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.n};
+  const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
+  const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
+  const size_t smem = sizeof(PipeSmem<V>);
+  for (int j = 0; j < len; ++j) {
+    if (w.m > 0) {
+      da.yold = Z[(j + 1) & 1] + w.n;
+      da.ynew = Z[j & 1] + w.n;
+      if (Pr.on) Pr.begin(0, s);
+      launch(k_dual_pipe<V, NT>, gd, NT, smem, s, da, (const int4*)w.A.meta, w.A.nblk, j);
+      if (Pr.on) Pr.end(s);
+    }
+    pa.zin = Z[j & 1];
+    pa.zout = Z[(j + 1) & 1];
+    if (Pr.on) Pr.begin(1, s);
+    launch(k_primal_pipe<V, NT>, gp, NT, smem, s, pa, (const int4*)w.P.meta, w.P.nblk, j);
+    if (Pr.on) Pr.end(s);
+  }
+}
+
+template <typename V, int NT>
 static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
                       const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
@@ -1242,25 +1449,45 @@ static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
       if (Pr.on) Pr.begin(0, s);
-      launch(k_dual<V>, w.A.nblk, BNT, 0, s, da, j);
+      launch(k_dual<V, NT>, w.A.nblk, NT, 0, s, da, j);
       if (Pr.on) Pr.end(s);
     }
     pa.zin = Z[j & 1];
     pa.zout = Z[(j + 1) & 1];
     if (Pr.on) Pr.begin(1, s);
-    launch(k_primal<V>, w.P.nblk, BNT, 0, s, pa, j);
+    launch(k_primal<V, NT>, w.P.nblk, NT, 0, s, pa, j);
     if (Pr.on) Pr.end(s);
   }
 }
 
-void iterate_chunk(Work& w, int len, bool mixed, cudaStream_t s) {
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s) {
+  if (nt == 1) {   // pipelined persistent kernels, 256 threads
+    if (mixed) {
+      run_chunk_pipe<float, 256>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+                                 w.fxbar, w.fc, w.fl, w.fu, s);
+      w.fy = w.fZ[(len - 1) & 1] + w.n;
+    } else {
+      run_chunk_pipe<double, 256>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x,
+                                  w.xbar, w.cs, w.ls, w.us, s);
+      w.y = w.Z[(len - 1) & 1] + w.n;
+    }
+    return;
+  }
   if (mixed) {
-    run_chunk<float>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx, w.fxbar,
-                     w.fc, w.fl, w.fu, s);
+    if (nt != 512)
+      run_chunk<float, 256>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+                            w.fxbar, w.fc, w.fl, w.fu, s);
+    else
+      run_chunk<float, 512>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+                            w.fxbar, w.fc, w.fl, w.fu, s);
     w.fy = w.fZ[(len - 1) & 1] + w.n;
   } else {
-    run_chunk<double>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar, w.cs,
-                      w.ls, w.us, s);
+    if (nt != 512)
+      run_chunk<double, 256>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
+                             w.cs, w.ls, w.us, s);
+    else
+      run_chunk<double, 512>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
+                             w.cs, w.ls, w.us, s);
     w.y = w.Z[(len - 1) & 1] + w.n;
   }
 }

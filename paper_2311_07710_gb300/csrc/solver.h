@@ -34,6 +34,7 @@ struct DCsr {
   int* col = nullptr;         // [nnz]
   int* blk = nullptr;         // [nblk+1]
   int* split = nullptr;       // [rows] (P only)
+  int* meta = nullptr;        // int4 {r0, r1, e0, e1} per row block
   double* val = nullptr;      // original values
   double* sval = nullptr;     // scaled values, float64
   float* sval_f = nullptr;    // scaled values, float32 (mixed precision)
@@ -117,7 +118,7 @@ void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 
 // iteration
-void iterate_chunk(Work& w, int len, bool mixed, cudaStream_t s);
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s);
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
 
 // results
