@@ -121,7 +121,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle sample
-def oracle_sample(inst, budget_iters=6, scaling_passes=1, power_steps=2):
+def oracle_sample(inst, budget_iters=6, scaling_passes=1, norm_steps=2):
     """Time the CPU oracle on a bounded sample of the workload and extrapolate
     to one full solve with the oracle's own counts for this instance."""
     from oracle import rapdhg as R
@@ -131,11 +131,11 @@ def oracle_sample(inst, budget_iters=6, scaling_passes=1, power_steps=2):
     R.scaling_factors(p, ruiz_iters=scaling_passes, l2=False, pock_chambolle=False)
     t_pass = (time.perf_counter() - t) / scaling_passes
     t = time.perf_counter()
-    R.norm_A(p, max_iter=power_steps, tol=0.0)
-    t_powA = (time.perf_counter() - t) / power_steps
+    R.norm_A(p, max_iter=norm_steps, tol=0.0)
+    t_normA = (time.perf_counter() - t) / norm_steps
     t = time.perf_counter()
-    R.norm_Q(p, max_iter=power_steps, tol=0.0)
-    t_powQ = (time.perf_counter() - t) / power_steps
+    R.norm_Q(p, max_iter=norm_steps, tol=0.0)
+    t_normQ = (time.perf_counter() - t) / norm_steps
     base = dict(scaling=False, norm_A=ref["norm_A"], norm_Q=ref["norm_Q"], eps=0.0, check_period=10 ** 9)
     t = time.perf_counter()
     R.solve(inst, R.Options(max_iter=1, **base))
@@ -147,11 +147,11 @@ def oracle_sample(inst, budget_iters=6, scaling_passes=1, power_steps=2):
     t_kkt = max(t1 - t_iter, 0.0) / 3.0          # one start evaluation + two at the final check
     iters = ref["iterations"]
     checks = math.ceil(iters / 64)
-    t_solve = (12 * t_pass + ref["power_steps_A"] * t_powA + ref["power_steps_Q"] * t_powQ
+    t_solve = (12 * t_pass + ref["norm_steps_A"] * t_normA + ref["norm_steps_Q"] * t_normQ
                + iters * t_iter + (1 + 2 * checks) * t_kkt)
-    sample = (f"{scaling_passes} scaling pass, {power_steps} power steps per norm, "
+    sample = (f"{scaling_passes} scaling pass, {norm_steps} Lanczos steps per norm, "
               f"{1 + budget_iters}+1 oracle iterations on the n=1e6 workload, extrapolated to a full solve "
-              f"(12 scaling passes, {ref['power_steps_A']}+{ref['power_steps_Q']} power steps, {iters} iterations, "
+              f"(12 scaling passes, {ref['norm_steps_A']}+{ref['norm_steps_Q']} Lanczos steps, {iters} iterations, "
               f"{checks} checks: counts of the oracle's own full solve)")
     return 1.0 / t_solve, t_solve, sample
 

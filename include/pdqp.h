@@ -96,9 +96,10 @@ typedef struct {
   double pw_theta;           /* 0.2: primal-weight smoothing (Section 6) */
   double eps_zero;           /* 1e-10 */
   double norm_A, norm_Q;     /* > 0: use these spectral norms of the SCALED
-                                matrices; <= 0: estimate by power iteration */
-  int32_t power_iters;       /* 500 */
-  double power_tol;          /* 1e-6 relative change of the Rayleigh quotient */
+                                matrices; <= 0: estimate them by the Lanczos method */
+  int32_t norm_iters;        /* Lanczos step limit, 1..512 (default 500) */
+  double norm_tol;           /* stop when the largest Ritz value changes by <= this
+                                relative (default 1e-6) */
   int32_t spmv_threads;      /* iteration-kernel variant: 256 or 512 threads per row
                                 block, 1 = pipelined persistent (cp.async prefetch of
                                 the next row block), 0 = library choice (256) */
@@ -116,7 +117,7 @@ typedef struct {
   double omega;              /* final primal weight */
   double setup_seconds;      /* device time of scaling + spectral norms (CUDA events) */
   double iterate_seconds;    /* device time from the first iteration to termination */
-  int32_t power_iters;       /* power-iteration steps taken (0 when norms were given) */
+  int32_t norm_iters;        /* Lanczos steps taken (0 when the norms were given) */
 } pdqp_info;
 
 /* Per-kernel device time of the solver's hot loop, measured with CUDA events

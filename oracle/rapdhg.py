@@ -47,7 +47,8 @@ the design notes of the repository):
      the same epoch and is false at the first check of an epoch.
   R8 condition (iii): t = iterations of the current epoch, k = total iterations.
   R9 eps_zero = 1e-10.
-  R10 ||A||_2, ||Q||_2 by power iteration from the all-ones vector.
+  R10 ||A||_2, ||Q||_2 by the Lanczos method (largest Ritz value) from the
+      all-ones vector; the paper does not say how the norms are obtained.
   R11 scaling passes divide every index j of the symmetric K by
       sqrt(norm of row j of the current scaled K) (inf-norm for Ruiz, 2-norm
       for the l2 pass, 1-norm for Pock-Chambolle with alpha = 1); zero
@@ -206,40 +207,49 @@ def scale_problem(p: Problem, D1: np.ndarray, D2: np.ndarray) -> Problem:
 # ---------------------------------------------------------------------------
 # Spectral norms (R10)
 # ---------------------------------------------------------------------------
-POWER_STEPS = {}   # steps taken by the latest power_norm call of each operator name
+NORM_STEPS = {}   # Lanczos steps taken by the latest call for each operator name
 
 
-def power_norm(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6, name: str = "") -> float:
-    """Largest eigenvalue of a symmetric PSD operator by power iteration from the
-    normalised all-ones vector; stops when the Rayleigh quotient changes by at
-    most tol relative."""
+def lanczos_max_eig(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6, name: str = "") -> float:
+    """Largest eigenvalue of a symmetric PSD operator: the largest Ritz value of
+    the Lanczos tridiagonal T_k (plain three-term recurrence, no
+    reorthogonalisation) started from the normalised all-ones vector.  Stops
+    when that value changes by at most tol relative, when beta_k <= 1e-12 theta_k
+    (an invariant subspace: the value is exact), or after max_iter steps."""
     if dim == 0:
         return 0.0
     v = np.full(dim, 1.0 / math.sqrt(dim))
-    lam_prev = 0.0
-    lam = 0.0
+    v_prev = np.zeros(dim)
+    beta_prev = 0.0
+    alphas, betas = [], []
+    theta_prev = 0.0
+    theta = 0.0
     for step in range(1, max_iter + 1):
-        POWER_STEPS[name] = step
+        NORM_STEPS[name] = step
         w = apply_sym(v)
-        lam = float(v @ w)
-        nw = float(np.linalg.norm(w))
-        if nw == 0.0:
-            return 0.0
-        v = w / nw
-        if abs(lam - lam_prev) <= tol * abs(lam):
+        alpha = float(v @ w)
+        w = w - alpha * v - beta_prev * v_prev
+        beta = float(np.linalg.norm(w))
+        alphas.append(alpha)
+        T = np.diag(alphas) + np.diag(betas, 1) + np.diag(betas, -1)
+        theta = float(np.linalg.eigvalsh(T)[-1])
+        if abs(theta - theta_prev) <= tol * abs(theta) or beta <= 1e-12 * abs(theta):
             break
-        lam_prev = lam
-    return lam
+        betas.append(beta)
+        v_prev, v = v, w / beta
+        beta_prev = beta
+        theta_prev = theta
+    return theta
 
 
 def norm_A(p: Problem, **kw) -> float:
     if p.m == 0:
         return 0.0
-    return math.sqrt(max(power_norm(lambda v: p.A.T @ (p.A @ v), p.n, name="A", **kw), 0.0))
+    return math.sqrt(max(lanczos_max_eig(lambda v: p.A.T @ (p.A @ v), p.n, name="A", **kw), 0.0))
 
 
 def norm_Q(p: Problem, **kw) -> float:
-    return max(power_norm(p.Qmul, p.n, name="Q", **kw), 0.0)
+    return max(lanczos_max_eig(p.Qmul, p.n, name="Q", **kw), 0.0)
 
 
 # ---------------------------------------------------------------------------
@@ -332,10 +342,10 @@ class Options:
     beta_art: float = 0.36
     pw_theta: float = 0.2
     eps_zero: float = 1e-10
-    norm_A: float = 0.0               # <= 0: power iteration (R10)
+    norm_A: float = 0.0               # <= 0: Lanczos estimate (R10)
     norm_Q: float = 0.0
-    power_iters: int = 500
-    power_tol: float = 1e-6
+    norm_iters: int = 500
+    norm_tol: float = 1e-6
 
 
 @dataclasses.dataclass
@@ -370,8 +380,8 @@ def solve(inst_or_problem, opts: Optional[Options] = None, x0=None, y0=None,
     else:
         D1, D2 = np.ones(m), np.ones(n)
     ps = scale_problem(p, D1, D2)
-    nA = opts.norm_A if opts.norm_A > 0 else norm_A(ps, max_iter=opts.power_iters, tol=opts.power_tol)
-    nQ = opts.norm_Q if opts.norm_Q > 0 else norm_Q(ps, max_iter=opts.power_iters, tol=opts.power_tol)
+    nA = opts.norm_A if opts.norm_A > 0 else norm_A(ps, max_iter=opts.norm_iters, tol=opts.norm_tol)
+    nQ = opts.norm_Q if opts.norm_Q > 0 else norm_Q(ps, max_iter=opts.norm_iters, tol=opts.norm_tol)
 
     unscale = lambda xs, ys: (D2 * xs, D1 * ys)
 

@@ -178,6 +178,7 @@ void alloc_mixed(pdqp_problem* h) {
   w.fybar = dalloc<float>(h, m); w.yk = dalloc<double>(h, m);
   w.fpu[0] = dalloc<float>(h, n); w.fpu[1] = dalloc<float>(h, n);
   w.fpz[0] = dalloc<float>(h, (size_t)n + m); w.fpz[1] = dalloc<float>(h, (size_t)n + m);
+  w.flw[0] = dalloc<float>(h, n); w.flw[1] = dalloc<float>(h, n);
   w.fc = dalloc<float>(h, n); w.fl = dalloc<float>(h, n); w.fu = dalloc<float>(h, n);
   w.fb = dalloc<float>(h, m); w.fylo = dalloc<float>(h, m);
   w.xhi = dalloc<double>(h, n); w.yhi = dalloc<double>(h, m);
@@ -202,8 +203,8 @@ SolveParams make_params(const pdqp_options& o) {
   p.beta_art = o.beta_art;
   p.pw_theta = o.pw_theta;
   p.eps_zero = o.eps_zero;
-  p.power_tol = o.power_tol;
-  p.power_iters = o.power_iters;
+  p.norm_tol = o.norm_tol;
+  p.norm_iters = o.norm_iters;
   p.spmv_threads = o.spmv_threads;
   return p;
 }
@@ -219,7 +220,7 @@ void validate_options(const pdqp_options& o) {
   if (!(o.eps >= 0.0)) bad("options.eps must be >= 0");
   if ((o.restart_rule == PDQP_RESTART_FIXED || o.step_rule == PDQP_STEP_THEORY) && o.fixed_K < 1)
     bad("options.fixed_K must be >= 1");
-  if (o.power_iters < 1) bad("options.power_iters must be >= 1");
+  if (o.norm_iters < 1 || o.norm_iters > 512) bad("options.norm_iters must be in [1, 512]");
   if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 256 && o.spmv_threads != 512)
     bad("options.spmv_threads must be 0, 1, 256 or 512");
 }
@@ -277,18 +278,18 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   pdqp::scale_apply(w, mixed, s);
 
   // spectral norms of the scaled matrices
-  const bool run_power = !(o.norm_A > 0.0 && o.norm_Q > 0.0);
-  if (run_power) {
-    pdqp::power_init(w, mixed, s);
-    for (int t = 0; t < o.power_iters; ++t) {
-      pdqp::power_iter(w, t, p, mixed, s);
-      if ((t & 15) == 15) {
+  const bool run_lanczos = !(o.norm_A > 0.0 && o.norm_Q > 0.0);
+  if (run_lanczos) {
+    pdqp::lanczos_init(w, mixed, s);
+    for (int t = 0; t < o.norm_iters; ++t) {
+      pdqp::lanczos_step(w, t, p, mixed, s);
+      if ((t & 7) == 7) {
         sync_state(h, s);
         if (w.st_host->pi_done[0] && w.st_host->pi_done[1]) break;
       }
     }
   }
-  pdqp::power_finish(w, o.norm_A, o.norm_Q, s);
+  pdqp::norms_finish(w, o.norm_A, o.norm_Q, s);
   CK(cudaEventRecord(h->ev[1], s));
   pdqp::init_iterates(w, dx0, dy0, p, s);
   pdqp::check(w, p, 0, 0, mixed, s);
@@ -342,7 +343,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     CK(cudaEventElapsedTime(&t_iter, h->ev[1], h->ev[2]));
     info->setup_seconds = 1e-3 * t_setup;
     info->iterate_seconds = 1e-3 * t_iter;
-    info->power_iters = run_power ? S.pi_iters : 0;
+    info->norm_iters = run_lanczos ? S.pi_iters : 0;
     info->seconds = now_s() - t0;
   }
   return result;
@@ -376,8 +377,8 @@ void pdqp_default_options(pdqp_options* o) {
   o->eps_zero = 1e-10;
   o->norm_A = 0.0;
   o->norm_Q = 0.0;
-  o->power_iters = 500;
-  o->power_tol = 1e-6;
+  o->norm_iters = 500;
+  o->norm_tol = 1e-6;
   o->spmv_threads = 0;
   o->reserved = 0;
 }
@@ -479,6 +480,8 @@ pdqp_status pdqp_create(pdqp_handle* out, int64_t n, int64_t m, int64_t m_eq, co
     w.ybar = dalloc<double>(h, M); w.ay = dalloc<double>(h, M);
     w.pu[0] = dalloc<double>(h, N); w.pu[1] = dalloc<double>(h, N);
     w.pz[0] = dalloc<double>(h, N + M); w.pz[1] = dalloc<double>(h, N + M);
+    w.lw[0] = dalloc<double>(h, N); w.lw[1] = dalloc<double>(h, N);
+    w.lz_al = dalloc<double>(h, 2 * 512); w.lz_be = dalloc<double>(h, 2 * 512);
     w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
     w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
     w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));

@@ -53,8 +53,8 @@ struct DevState {
 struct SolveParams {
   int step_rule, restart_rule, accelerate, fixed_K, check_period, mixed;
   long long max_iter;
-  double eps, beta_suff, beta_nec, beta_art, pw_theta, eps_zero, power_tol;
-  int power_iters;
+  double eps, beta_suff, beta_nec, beta_art, pw_theta, eps_zero, norm_tol;
+  int norm_iters;
   int spmv_threads;     // threads per row block of the iteration kernels (256 or 512)
 };
 

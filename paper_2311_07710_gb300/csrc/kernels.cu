@@ -903,13 +903,27 @@ __global__ void k_scale_vectors(int n, int m, const double* __restrict__ D1, con
 }
 
 // --------------------------------------------------------------------------
-// Power iteration for ||A~||_2 (on A~'A~) and ||Q~||_2, both from the
-// normalised all-ones vector.  v_A = u * sa, v_Q = z * sq (sa, sq the inverse
-// norms of the previous u, z); pz = [z ; w] is the input of the P rows.
+// Spectral norms ||A~||_2 = sqrt(lambda_max(A~'A~)) and ||Q~||_2 by the Lanczos
+// method: the largest Ritz value of the tridiagonal T_k built by the plain
+// three-term recurrence from the normalised all-ones vector, for both
+// operators at once.  Per step: w = Op v (two SpMV kernels), alpha = v'w,
+// r = w - alpha v - beta_prev v_prev, beta = |r|, theta = lambda_max(T_k),
+// v_next = r / beta.  Stop when theta changes by <= tol relative, when
+// beta <= 1e-12 theta (invariant subspace) or after the step limit.
 // --------------------------------------------------------------------------
+constexpr int LZ_MAX = 512;
+
+struct LzArgs {
+  int n, m, have_rows;
+  double* al;        // [2][LZ_MAX] alphas of A'A and Q
+  double* be;        // [2][LZ_MAX] betas
+  DevState* st;
+};
+
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_pi_m(BCsr<V> A, const V* __restrict__ u, V* __restrict__ pz_w,
-                                              const DevState* __restrict__ st) {
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, const V* __restrict__ vA,
+                                                                   V* __restrict__ wm,
+                                                                   const DevState* __restrict__ st) {
   if (st->pi_done[0]) return;
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
@@ -918,109 +932,219 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_pi_m(BCsr<V> A, co
   const int nr = r1 - r0;
   const int e0 = A.rp[r0];
   const int ne = A.rp[r1] - e0;
-  const V sa = (V)st->pi_inv_norm[0];
   if (ne <= BNNZ) {
-    stage_products<NT>(A, u, e0, ne, r0, nr, prod, srp);
+    stage_products<NT>(A, vA, e0, ne, r0, nr, prod, srp);
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
       V s = V(0);
       for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
-      pz_w[r0 + t] = s * sa;
+      wm[r0 + t] = s;
     }
   } else {
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += NT) s += A.val[e] * __ldg(u + A.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += A.val[e] * __ldg(vA + A.col[e]);
     s = block_sum(s);
-    if (tid == 0) pz_w[r0] = s * sa;
+    if (tid == 0) wm[r0] = s;
   }
 }
 
+// rows of P with input [v_Q ; w_m]: wA = A~'w_m, wQ = Q~ v_Q; partial v'w per block
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_pi_n(BCsr<V> P, const V* __restrict__ pz_old, V* __restrict__ pz_new,
-                                              const V* __restrict__ u_old, V* __restrict__ u_new,
-                                              const DevState* __restrict__ st, double* __restrict__ part,
-                                              int nblk, int have_rows) {
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, const V* __restrict__ zin,
+                                                                   const V* __restrict__ vA, V* __restrict__ wA,
+                                                                   V* __restrict__ wQ, const DevState* __restrict__ st,
+                                                                   double* __restrict__ part, int nblk,
+                                                                   int have_rows) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
   const bool doA = !st->pi_done[0] && have_rows;
   const bool doQ = !st->pi_done[1];
-  const double sa = st->pi_inv_norm[0], sq = st->pi_inv_norm[1];
-  double f[4] = {0.0, 0.0, 0.0, 0.0};
+  if (!doA && !doQ) return;                    // k_lz_alpha reads no partials then
+  double f[2] = {0.0, 0.0};
   const int tid = threadIdx.x;
   const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = P.rp[r0];
   const int ne = P.rp[r1] - e0;
-  auto row = [&](int r, double sQ, double sA) {
-    if (doA) {
-      const double un = -sA;                 // (A~'w)_r: P holds -A~'
-      u_new[r] = (V)un;
-      f[0] += ((double)u_old[r] * sa) * un;
-      f[1] += un * un;
-    }
-    if (doQ) {
-      const double z = sQ * sq;              // Q~ (z_old sq)
-      pz_new[r] = (V)z;
-      f[2] += ((double)pz_old[r] * sq) * z;
-      f[3] += z * z;
-    }
+  auto row = [&](int r, V sQ, V sA) {
+    if (doA) { const V u = -sA; wA[r] = u; f[0] += (double)vA[r] * (double)u; }
+    if (doQ) { wQ[r] = sQ; f[1] += (double)zin[r] * (double)sQ; }
   };
   if (ne <= BNNZ) {
-    stage_products<NT>(P, pz_old, e0, ne, r0, nr, prod, srp);
+    stage_products<NT>(P, zin, e0, ne, r0, nr, prod, srp);
     for (int t = tid; t < nr; t += NT) ssp[t] = P.split[r0 + t] - e0;
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
       V q = V(0), w = V(0);
       for (int e = srp[t]; e < ssp[t]; ++e) q += prod[e];
       for (int e = ssp[t]; e < srp[t + 1]; ++e) w += prod[e];
-      row(r0 + t, (double)q, (double)w);
+      row(r0 + t, q, w);
     }
   } else {
     const int sp = P.split[r0];
     V q = V(0), w = V(0);
     for (int e = e0 + tid; e < e0 + ne; e += NT) {
-      const V v = P.val[e] * __ldg(pz_old + P.col[e]);
+      const V v = P.val[e] * __ldg(zin + P.col[e]);
       if (e < sp) q += v; else w += v;
     }
     q = block_sum(q);
     w = block_sum(w);
-    if (tid == 0) row(r0, (double)q, (double)w);
+    if (tid == 0) row(r0, q, w);
   }
-  const bool is_max[4] = {false, false, false, false};
-  block_reduce<4>(f, is_max);
-  if (tid == 0)
-    for (int k = 0; k < 4; ++k) part[(size_t)k * nblk + blockIdx.x] = f[k];
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)nblk + blockIdx.x] = f[1]; }
 }
 
-__global__ void k_pi_update(DevState* __restrict__ st, const double* __restrict__ part, int nblk, double tol,
-                            int have_rows) {
-  double f[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-    for (int k = 0; k < 4; ++k) f[k] += part[(size_t)k * nblk + b];
-  const bool is_max[4] = {false, false, false, false};
-  block_reduce<4>(f, is_max);
-  if (threadIdx.x != 0) return;
-  st->pi_iters += 1;
-  for (int which = 0; which < 2; ++which) {
-    if (st->pi_done[which]) continue;
-    if (which == 0 && !have_rows) { st->pi_done[0] = 1; st->pi_lam[0] = 0.0; continue; }
-    const double lam = f[2 * which], nw = sqrt(f[2 * which + 1]);
-    st->pi_lam[which] = lam;
-    if (nw == 0.0) { st->pi_lam[which] = 0.0; st->pi_done[which] = 1; continue; }
-    if (fabs(lam - st->pi_lam_prev[which]) <= tol * fabs(lam)) { st->pi_done[which] = 1; continue; }
-    st->pi_lam_prev[which] = lam;
-    st->pi_inv_norm[which] = 1.0 / nw;
+__global__ void __launch_bounds__(1024) k_lz_alpha(LzArgs a, const double* __restrict__ part, int nblk) {
+  double f[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b]; f[1] += part[(size_t)nblk + b]; }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (threadIdx.x == 0) {
+    const int k = a.st->pi_iters;
+    for (int o = 0; o < 2; ++o)
+      if (!a.st->pi_done[o]) a.al[o * LZ_MAX + k] = f[o];
   }
 }
 
-__global__ void k_pi_init(DevState* st, int n) {
-  st->pi_done[0] = 0; st->pi_done[1] = 0;
-  st->pi_lam[0] = 0.0; st->pi_lam[1] = 0.0;
-  st->pi_lam_prev[0] = 0.0; st->pi_lam_prev[1] = 0.0;
-  st->pi_inv_norm[0] = 1.0 / sqrt((double)n);
-  st->pi_inv_norm[1] = 1.0 / sqrt((double)n);
-  st->pi_iters = 0;
+// r = w - alpha v - beta_prev v_prev, written over v_prev; partial |r|^2
+template <typename V>
+__global__ void k_lz_orth(LzArgs a, const V* __restrict__ wA, const V* __restrict__ wQ, const V* __restrict__ vA,
+                          V* __restrict__ vA_prev, const V* __restrict__ vQ, V* __restrict__ vQ_prev,
+                          double* __restrict__ part) {
+  const DevState* st = a.st;
+  const int k = st->pi_iters;
+  const bool doA = !st->pi_done[0] && a.have_rows, doQ = !st->pi_done[1];
+  if (!doA && !doQ) return;
+  const double alA = doA ? a.al[k] : 0.0, alQ = doQ ? a.al[LZ_MAX + k] : 0.0;
+  const double bpA = (doA && k > 0) ? a.be[k - 1] : 0.0, bpQ = (doQ && k > 0) ? a.be[LZ_MAX + k - 1] : 0.0;
+  double f[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    if (doA) {
+      const double r = (double)wA[i] - alA * (double)vA[i] - bpA * (double)vA_prev[i];
+      vA_prev[i] = (V)r;
+      f[0] += r * r;
+    }
+    if (doQ) {
+      const double r = (double)wQ[i] - alQ * (double)vQ[i] - bpQ * (double)vQ_prev[i];
+      vQ_prev[i] = (V)r;
+      f[1] += r * r;
+    }
+  }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  if (threadIdx.x == 0) { part[blockIdx.x * 32] = f[0]; part[blockIdx.x * 32 + 1] = f[1]; }
+}
+
+// Number of eigenvalues of the k x k tridiagonal (al, be) below x: the sign
+// changes of the Sturm sequence p_0 = 1, p_i = (al_i - x) p_{i-1} - be_{i-1}^2 p_{i-2}
+// (p_i = det(T_i - x I)), rescaled to stay in range; a zero p_i counts as a
+// change.  Division free.
+__device__ int sturm_count(const double* __restrict__ al, const double* __restrict__ be, int k, double x) {
+  double pm = 1.0, pc = al[0] - x;
+  if (pc == 0.0) pc = -1e-300;
+  int c = pc < 0.0 ? 1 : 0;
+  for (int i = 1; i < k; ++i) {
+    double pn = (al[i] - x) * pc - (be[i - 1] * be[i - 1]) * pm;
+    if (pn == 0.0) pn = pc > 0.0 ? -1e-300 : 1e-300;
+    if ((pn < 0.0) != (pc < 0.0)) ++c;
+    pm = pc;
+    pc = pn;
+    const double a = fabs(pc);
+    if (a > 1e150) { pc *= 1e-150; pm *= 1e-150; }
+    else if (a < 1e-150) { pc *= 1e150; pm *= 1e150; }
+  }
+  return c;
+}
+
+// lambda_max of the tridiagonal by 32-point multisection within one warp
+__device__ double tridiag_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be, int k) {
+  const int lane = threadIdx.x & 31;
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < k - 1 ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - r);
+    hi = fmax(hi, al[i] + r);
+  }
+  hi += 1e-300 + fabs(hi) * 1e-15;
+  for (int round = 0; round < 12; ++round) {
+    const double step = (hi - lo) / 33.0;
+    const double x = lo + step * (double)(lane + 1);
+    const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be, k, x) < k);   // lambda_max >= x
+    if (ge == 0u) {
+      hi = lo + step;
+    } else {
+      const int t = 31 - __clz(ge);
+      const double nlo = lo + step * (double)(t + 1);
+      hi = t == 31 ? hi : lo + step * (double)(t + 2);
+      lo = nlo;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// beta and theta = lambda_max(T_k) (warp 0: A'A, warp 1: Q), stop test
+__global__ void __launch_bounds__(1024) k_lz_beta(LzArgs a, const double* __restrict__ part, int nblk,
+                                                  double tol, int max_steps) {
+  double f[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b * 32]; f[1] += part[b * 32 + 1]; }
+  const bool is_max[2] = {false, false};
+  block_reduce<2>(f, is_max);
+  __shared__ double beta[2];
+  if (threadIdx.x == 0) { beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]); }
+  __syncthreads();
+  DevState* st = a.st;
+  if (st->pi_done[0] && st->pi_done[1]) return;   // uniform: nothing left to do
+  const int k = st->pi_iters + 1;                 // alphas 0..k-1, betas 0..k-2 form T_k
+  const int o = threadIdx.x >> 5;
+  if (o < 2 && !st->pi_done[o]) {                 // warp-uniform
+    const double theta = tridiag_max_eig_warp(a.al + o * LZ_MAX, a.be + o * LZ_MAX, k);
+    if ((threadIdx.x & 31) == 0) {
+      const double b = beta[o];
+      st->pi_lam[o] = theta;
+      if (fabs(theta - st->pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
+        st->pi_done[o] = 1;
+      } else {
+        a.be[o * LZ_MAX + k - 1] = b;
+        st->pi_lam_prev[o] = theta;
+        st->pi_inv_norm[o] = 1.0 / b;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st->pi_iters = k;
+}
+
+// v_next = r / beta (in the buffer that held v_prev)
+template <typename V>
+__global__ void k_lz_norm(LzArgs a, V* __restrict__ vA_next, V* __restrict__ vQ_next) {
+  const DevState* st = a.st;
+  const bool doA = !st->pi_done[0] && a.have_rows, doQ = !st->pi_done[1];
+  const double sA = st->pi_inv_norm[0], sQ = st->pi_inv_norm[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    if (doA) vA_next[i] = (V)((double)vA_next[i] * sA);
+    if (doQ) vQ_next[i] = (V)((double)vQ_next[i] * sQ);
+  }
+}
+
+template <typename V>
+__global__ void k_lz_init(LzArgs a, V* __restrict__ vA0, V* __restrict__ vA1, V* __restrict__ vQ0,
+                          V* __restrict__ vQ1) {
+  const V v = (V)(1.0 / sqrt((double)a.n));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    vA0[i] = v; vQ0[i] = v; vA1[i] = V(0); vQ1[i] = V(0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevState* st = a.st;
+    st->pi_done[0] = a.have_rows ? 0 : 1;
+    st->pi_done[1] = 0;
+    st->pi_lam[0] = 0.0; st->pi_lam[1] = 0.0;
+    st->pi_lam_prev[0] = 0.0; st->pi_lam_prev[1] = 0.0;
+    st->pi_inv_norm[0] = 1.0; st->pi_inv_norm[1] = 1.0;
+    st->pi_iters = 0;
+  }
 }
 
 template <typename V>
@@ -1082,45 +1206,54 @@ __global__ void k_init_iterates(int n, int m, int m_eq, const double* __restrict
   }
 }
 
-// Section 6 step size eta^{n,k}
-__device__ double pdqp_eta(long long k, double eta_prev, double nQ, double nA, double omega) {
-  const double q = nQ / omega;
+
+// Section 6 bound 0.99 (k+2) / (q + sqrt(|A|^2 (k+2)^2 + q^2)), q = |Q|/omega
+// (its k = 0 value is the k = 0 step 1.98 / (q + sqrt(4|A|^2 + q^2))).
+__device__ __forceinline__ double pdqp_bound(long long k, double q, double nA) {
   if (k == 0) return 1.98 / (q + sqrt(4.0 * (nA * nA) + q * q));
   const double kk = (double)(k + 2);
-  const double bound = 0.99 * kk / (q + sqrt((nA * nA) * (kk * kk) + q * q));
-  return fmin((1.0 + 1.0 / (double)k) * eta_prev, bound);
+  return 0.99 * kk / (q + sqrt((nA * nA) * (kk * kk) + q * q));
 }
 
-// Tabulate the step scalars of the next `C` inner iterations, k = k_epoch + j.
-__device__ void fill_steps(DevState& S, const SolveParams& p, StepEntry* tab) {
-  double eta = S.eta_last;
-  const long long k0 = S.k_epoch;
-  for (int j = 0; j < p.check_period; ++j) {
-    const long long k = k0 + j;
-    double beta = 1.0, beta1 = 1.0, theta1 = 1.0;
-    if (p.accelerate) {
-      beta = (double)(k + 2) / 2.0;
-      beta1 = (double)(k + 3) / 2.0;
-      theta1 = (double)(k + 1) / ((double)(k + 1) + 1.0);
-    }
-    double tau, sig;
-    if (p.step_rule == 1) {   // Theorem 1
-      tau = (double)(k + 1) / (2.0 * (S.normQ + p.fixed_K * S.normA));
-      sig = (double)(k + 1) / (2.0 * p.fixed_K * S.normA);
-    } else {
-      eta = pdqp_eta(p.accelerate ? k : 0, eta, S.normQ, S.normA, S.omega);
-      tau = eta / S.omega;
-      sig = eta * S.omega;
-    }
-    StepEntry e;
-    e.tau_p = tau; e.sigma_d = sig; e.inv_beta = 1.0 / beta; e.inv_beta_next = 1.0 / beta1;
-    e.theta_next = theta1;
-    e.tau_p_f = (float)tau; e.sigma_d_f = (float)sig; e.inv_beta_f = (float)e.inv_beta;
-    e.inv_beta_next_f = (float)e.inv_beta_next; e.theta_next_f = (float)theta1;
-    tab[j] = e;
+// Step scalars of inner iteration k.  Within an epoch omega is fixed and the
+// recurrence eta_k = min((1 + 1/k) eta_{k-1}, bound_k) started at eta_0 =
+// bound_0 always picks bound_k, because bound_k / bound_{k-1} <= (k+2)/(k+1) <
+// (k+1)/k; so each entry evaluates min((1 + 1/k) bound_{k-1}, bound_k) on its
+// own, which reproduces the recurrence value for value.
+__device__ StepEntry make_step(long long k, const DevState& S, const SolveParams& p) {
+  double beta = 1.0, beta1 = 1.0, theta1 = 1.0;
+  if (p.accelerate) {
+    beta = (double)(k + 2) / 2.0;
+    beta1 = (double)(k + 3) / 2.0;
+    theta1 = (double)(k + 1) / ((double)(k + 1) + 1.0);
   }
-  S.eta_last = eta;
+  double tau, sig;
+  if (p.step_rule == 1) {   // Theorem 1
+    tau = (double)(k + 1) / (2.0 * (S.normQ + p.fixed_K * S.normA));
+    sig = (double)(k + 1) / (2.0 * p.fixed_K * S.normA);
+  } else {
+    const double q = S.normQ / S.omega;
+    double eta;
+    if (!p.accelerate || k == 0) eta = pdqp_bound(0, q, S.normA);
+    else eta = fmin((1.0 + 1.0 / (double)k) * pdqp_bound(k - 1, q, S.normA), pdqp_bound(k, q, S.normA));
+    tau = eta / S.omega;
+    sig = eta * S.omega;
+  }
+  StepEntry e;
+  e.tau_p = tau; e.sigma_d = sig; e.inv_beta = 1.0 / beta; e.inv_beta_next = 1.0 / beta1;
+  e.theta_next = theta1;
+  e.tau_p_f = (float)tau; e.sigma_d_f = (float)sig; e.inv_beta_f = (float)e.inv_beta;
+  e.inv_beta_next_f = (float)e.inv_beta_next; e.theta_next_f = (float)theta1;
+  return e;
 }
+
+// Tabulate the next `check_period` entries (k = k_epoch + j), all threads.
+__device__ void fill_steps_block(const DevState& S, const SolveParams& p, StepEntry* tab) {
+  for (int j = threadIdx.x; j < p.check_period; j += blockDim.x) tab[j] = make_step(S.k_epoch + j, S, p);
+}
+
+__device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
+                               long long chunk_len);
 
 // mode 0: evaluate z^{0,0} (anchor, maybe already optimal); mode 1: a check
 // after `chunk_len` more iterations (Section 6 restart rule, termination
@@ -1131,7 +1264,13 @@ __global__ void __launch_bounds__(1024) k_decide(DevState* __restrict__ st, cons
                                                  long long chunk_len) {
   __shared__ double F[24];
   reduce_kkt_blocks(pm, nbm, pn, nbn, F);
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x == 0) decide_thread0(st, F, p, mode, chunk_len);
+  __syncthreads();
+  if (st->status == ST_RUNNING) fill_steps_block(*st, p, tab);
+}
+
+__device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
+                               long long chunk_len) {
   DevState& S = *st;
   double P[2][6];
   kkt_from_fields(F, 0, P[0]);
@@ -1147,7 +1286,6 @@ __global__ void __launch_bounds__(1024) k_decide(DevState* __restrict__ st, cons
     for (int k = 0; k < 6; ++k) S.out_parts[k] = P[0][k];
     const double r = P[0][3];
     S.status = (r != r) ? ST_NUMERICAL : (r <= p.eps ? ST_OPTIMAL : ST_RUNNING);
-    fill_steps(S, p, tab);
     return;
   }
   S.k_total += chunk_len;
@@ -1188,7 +1326,6 @@ __global__ void __launch_bounds__(1024) k_decide(DevState* __restrict__ st, cons
     S.restart = 1;
     S.cand_avg = to_avg;
   }
-  fill_steps(S, p, tab);
 }
 
 // Restart of the outer loop from the candidate: x = x_bar = x_md = x_tilde = x_c,
@@ -1325,40 +1462,46 @@ void scale_apply(Work& w, bool mixed, cudaStream_t s) {
          (float*)nullptr);
 }
 
-void power_init(Work& w, bool mixed, cudaStream_t s) {
-  const long long N = w.n;
-  if (mixed) {
-    launch(k_fill_v<float>, cdiv(N, 256), 256, 0, s, w.fpu[0], 1.0f, N);
-    launch(k_fill_v<float>, cdiv(N, 256), 256, 0, s, w.fpz[0], 1.0f, N);
-  } else {
-    launch(k_fill_v<double>, cdiv(N, 256), 256, 0, s, w.pu[0], 1.0, N);
-    launch(k_fill_v<double>, cdiv(N, 256), 256, 0, s, w.pz[0], 1.0, N);
-  }
-  launch(k_pi_init, 1, 1, 0, s, w.st, w.n);
+template <typename V>
+static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) {
+  LzArgs la{w.n, w.m, w.m > 0 ? 1 : 0, w.lz_al, w.lz_be, w.st};
+  const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
+  launch(k_lz_init<V>, grid, 256, 0, s, la, pu[0], pu[1], pz[0], pz[1]);
+}
+
+void lanczos_init(Work& w, bool mixed, cudaStream_t s) {
+  if (mixed) lanczos_init_t<float>(w, w.fpu, w.fpz, s);
+  else lanczos_init_t<double>(w, w.pu, w.pz, s);
 }
 
 template <typename V, int NT>
-static void power_iter_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr<V> P, V* const* pu, V* const* pz,
-                         cudaStream_t s) {
-  const int cur = t & 1, nxt = cur ^ 1;
-  if (w.m > 0)
-    launch(k_pi_m<V, NT>, w.A.nblk, NT, 0, s, A, (const V*)pu[cur], pz[cur] + w.n, (const DevState*)w.st);
-  launch(k_pi_n<V, NT>, w.P.nblk, NT, 0, s, P, (const V*)pz[cur], pz[nxt], (const V*)pu[cur], pu[nxt],
+static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr<V> P, V* const* pu, V* const* pz,
+                           V* const* lw, cudaStream_t s) {
+  const int cur = t & 1, prv = cur ^ 1;
+  LzArgs la{w.n, w.m, w.m > 0 ? 1 : 0, w.lz_al, w.lz_be, w.st};
+  if (w.m > 0) launch(k_lz_m<V, NT>, w.A.nblk, NT, 0, s, A, (const V*)pu[cur], pz[cur] + w.n, (const DevState*)w.st);
+  launch(k_lz_n<V, NT>, w.P.nblk, NT, 0, s, P, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
          (const DevState*)w.st, w.part_n, w.P.nblk, w.m > 0 ? 1 : 0);
-  launch(k_pi_update, 1, 1024, 0, s, w.st, (const double*)w.part_n, w.P.nblk, p.power_tol, w.m > 0 ? 1 : 0);
+  launch(k_lz_alpha, 1, 1024, 0, s, la, (const double*)w.part_n, w.P.nblk);
+  const int grid = std::min(cdiv(w.n, 256), (int)PDQP_RED_BLOCKS);
+  launch(k_lz_orth<V>, grid, 256, 0, s, la, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
+         (const V*)pz[cur], pz[prv], w.part);
+  launch(k_lz_beta, 1, 1024, 0, s, la, (const double*)w.part, grid, p.norm_tol,
+         p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
+  launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
 }
 
-void power_iter(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s) {
-  if (p.spmv_threads != 512) {
-    if (mixed) power_iter_t<float, 256>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, s);
-    else power_iter_t<double, 256>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, s);
+void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s) {
+  if (p.spmv_threads == 512) {
+    if (mixed) lanczos_step_t<float, 512>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, w.flw, s);
+    else lanczos_step_t<double, 512>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, w.lw, s);
   } else {
-    if (mixed) power_iter_t<float, 512>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, s);
-    else power_iter_t<double, 512>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, s);
+    if (mixed) lanczos_step_t<float, 256>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, w.flw, s);
+    else lanczos_step_t<double, 256>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, w.lw, s);
   }
 }
 
-void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
+void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
   launch(k_set_norms, 1, 1, 0, s, w.st, normA_opt, normQ_opt);
 }
 

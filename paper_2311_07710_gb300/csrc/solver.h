@@ -89,9 +89,12 @@ struct Work {
   float* Fs = nullptr;       // row-scaled by D2
   double* Fd = nullptr;      // float64 copy of Fs (for the float64 paths)
   double* wlr = nullptr;     // [2][r] F'x partial buffers
-  // power iteration: pu[p] (n) holds u = A~'w, pz[p] = [z ; w] (n+m) the P input
+  // Lanczos vectors: pu[p] (n) for A~'A~, pz[p] = [v_Q ; A~v_A] (n+m) the P input
   double *pu[2] = {nullptr, nullptr}, *pz[2] = {nullptr, nullptr};
   float *fpu[2] = {nullptr, nullptr}, *fpz[2] = {nullptr, nullptr};
+  double *lw[2] = {nullptr, nullptr};    // Lanczos products A~'A~v and Q~v [n]
+  float *flw[2] = {nullptr, nullptr};
+  double *lz_al = nullptr, *lz_be = nullptr;   // [2][512] Lanczos coefficients
   // reductions
   double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
   double *part_m = nullptr;  // [9][A.nblk]  field-major partial sums of the row-block kernels
@@ -112,9 +115,9 @@ extern long long g_launches;
 void scale_pass(Work& w, int kind, cudaStream_t s);          // kind: 0 inf, 1 l2, 2 l1
 void scale_reset(Work& w, cudaStream_t s);
 void scale_apply(Work& w, bool mixed, cudaStream_t s);
-void power_init(Work& w, bool mixed, cudaStream_t s);
-void power_iter(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s);
-void power_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
+void lanczos_init(Work& w, bool mixed, cudaStream_t s);
+void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s);
+void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 
 // iteration

@@ -32,8 +32,8 @@ class pdqp_options(ctypes.Structure):
         ("check_period", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("eps", ctypes.c_double),
         ("time_limit", ctypes.c_double), ("beta_suff", ctypes.c_double), ("beta_nec", ctypes.c_double),
         ("beta_art", ctypes.c_double), ("pw_theta", ctypes.c_double), ("eps_zero", ctypes.c_double),
-        ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double), ("power_iters", ctypes.c_int32),
-        ("power_tol", ctypes.c_double), ("spmv_threads", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double), ("norm_iters", ctypes.c_int32),
+        ("norm_tol", ctypes.c_double), ("spmv_threads", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -44,7 +44,7 @@ class pdqp_info(ctypes.Structure):
         ("r_gap", ctypes.c_double), ("primal_obj", ctypes.c_double), ("dual_obj", ctypes.c_double),
         ("seconds", ctypes.c_double), ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double),
         ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
-        ("iterate_seconds", ctypes.c_double), ("power_iters", ctypes.c_int32),
+        ("iterate_seconds", ctypes.c_double), ("norm_iters", ctypes.c_int32),
     ]
 
     def as_dict(self):

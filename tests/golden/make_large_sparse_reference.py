@@ -1,5 +1,5 @@
 """Solve the n=1e6 large sparse QP once with the CPU oracle and store what the
-tests and the bench need: iteration / restart / power-iteration counts, the
+tests and the bench need: iteration / restart / Lanczos step counts, the
 spectral norms, objective values, relKKT parts and the optimal x*, y* at a
 fixed sample of indices.  Calls only the oracle (and the seeded generator).
 
@@ -32,7 +32,7 @@ def main():
     rec = dict(
         what="CPU oracle solve of qpgen.large_sparse_qp() (n=1e6, m=5e5, seed 2311077101), default options",
         status=res.status, iterations=res.iterations, restarts=res.restarts,
-        power_steps_A=R.POWER_STEPS.get("A"), power_steps_Q=R.POWER_STEPS.get("Q"),
+        norm_steps_A=R.NORM_STEPS.get("A"), norm_steps_Q=R.NORM_STEPS.get("Q"),
         norm_A=res.norm_A, norm_Q=res.norm_Q, omega=res.omega, kkt=res.kkt,
         x_index=xi.tolist(), x_value=res.x[xi].tolist(), y_index=yi.tolist(), y_value=res.y[yi].tolist(),
         oracle_seconds=secs)

@@ -39,6 +39,7 @@ MUTATIONS = {
                       "return Problem(Qs, As, p.c / D2, D1 * p.b, p.l / D2, p.u / D2, p.m_eq, F)"),
     "scale_bounds_wrong": ("return Problem(Qs, As, D2 * p.c, D1 * p.b, p.l / D2, p.u / D2, p.m_eq, F)",
                            "return Problem(Qs, As, D2 * p.c, D1 * p.b, p.l * D2, p.u * D2, p.m_eq, F)"),
+    "lanczos_sign": ("w = w - alpha * v - beta_prev * v_prev", "w = w - alpha * v + beta_prev * v_prev"),
     "unscale_wrong": ("unscale = lambda xs, ys: (D2 * xs, D1 * ys)", "unscale = lambda xs, ys: (xs / D2, ys / D1)"),
 }
 
@@ -83,6 +84,12 @@ def _pins_pass(R):
             for key in ("r_primal", "r_dual", "r_gap", "primal_obj", "dual_obj"):
                 if abs(parts[key] - float(Fraction(case[key]))) > 1e-12:
                     return False
+        inst = qpgen.tiny_qp(41, n=12, m=7, m_eq=2, bounds="box")
+        p = R.problem_from_instance(inst)
+        if abs(R.norm_A(p, tol=0.0) - np.linalg.norm(p.A.toarray(), 2)) > 1e-9:
+            return False
+        if abs(R.norm_Q(p, tol=0.0) - np.linalg.eigvalsh(p.Q.toarray()).max()) > 1e-9:
+            return False
         for seed, n, m, m_eq, bounds in [(21, 4, 3, 1, "box"), (22, 5, 4, 2, "mixed")]:
             inst = qpgen.tiny_qp(seed, n=n, m=m, m_eq=m_eq, bounds=bounds)
             inst.A = sp.csr_matrix(inst.A.toarray() * np.linspace(0.5, 3.0, m)[:, None])
@@ -93,7 +100,7 @@ def _pins_pass(R):
             if res.status != "optimal" or np.max(np.abs(res.x - truth[0])) > 1e-5:
                 return False
         return True
-    except (FloatingPointError, ValueError, ZeroDivisionError, OverflowError, IndexError):
+    except (FloatingPointError, ValueError, ZeroDivisionError, OverflowError, IndexError, np.linalg.LinAlgError):
         return False
 
 

@@ -234,11 +234,29 @@ def test_primal_weight_rules():
 
 
 # --------------------------------------------------------------------------- preprocessing / norms
-def test_power_norms_match_dense_linear_algebra():
+def test_lanczos_norms_match_dense_linear_algebra():
+    """On a 12-variable problem Lanczos reaches an invariant subspace within 12
+    steps, so the Ritz value is the exact top eigenvalue."""
     inst = qpgen.tiny_qp(41, n=12, m=7, m_eq=2, bounds="box")
     p = R.problem_from_instance(inst)
-    assert R.norm_A(p, max_iter=20000, tol=1e-14) == pytest.approx(np.linalg.norm(p.A.toarray(), 2), rel=1e-6)
-    assert R.norm_Q(p, max_iter=20000, tol=1e-14) == pytest.approx(np.linalg.eigvalsh(p.Q.toarray()).max(), rel=1e-6)
+    assert R.norm_A(p, tol=0.0) == pytest.approx(np.linalg.norm(p.A.toarray(), 2), rel=1e-10)
+    assert R.norm_Q(p, tol=0.0) == pytest.approx(np.linalg.eigvalsh(p.Q.toarray()).max(), rel=1e-10)
+
+
+def test_lanczos_on_the_n1000_workload():
+    """Against a dense eigen-solve of the scaled n=1000 operators, at the default
+    tolerance: Ritz values are lower bounds of the top eigenvalue and the
+    default stopping rule leaves them within 1e-5 of it."""
+    inst = qpgen.random_sparse_qp()
+    p = R.problem_from_instance(inst)
+    D1, D2 = R.scaling_factors(p)
+    ps = R.scale_problem(p, D1, D2)
+    A, Q = ps.A.toarray(), ps.Q.toarray()
+    truth_A, truth_Q = np.linalg.norm(A, 2), np.linalg.eigvalsh(Q).max()
+    nA, nQ = R.norm_A(ps), R.norm_Q(ps)
+    assert nA == pytest.approx(truth_A, rel=1e-5) and nA <= truth_A * (1 + 1e-12)
+    assert nQ == pytest.approx(truth_Q, rel=1e-5) and nQ <= truth_Q * (1 + 1e-12)
+    assert R.NORM_STEPS["A"] < 100 and R.NORM_STEPS["Q"] < 100
 
 
 def test_ruiz_equilibrates_and_scaling_is_symmetric():
