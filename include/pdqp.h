@@ -103,7 +103,9 @@ typedef struct {
   int32_t spmv_threads;      /* iteration-kernel variant: 256 or 512 threads per row
                                 block, 1 = pipelined persistent (cp.async prefetch of
                                 the next row block), 0 = library choice (256) */
-  int32_t reserved;          /* must be 0 */
+  int32_t no_graphs;         /* 0: replay each full chunk of check_period iterations
+                                and its check as one captured CUDA graph; 1: launch
+                                every kernel directly */
 } pdqp_options;
 
 typedef struct {

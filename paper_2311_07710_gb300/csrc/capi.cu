@@ -10,12 +10,23 @@
 #include "pdqp.h"
 #include "solver.h"
 
+// One chunk (check_period iterations + the check) captured as a CUDA graph,
+// keyed by the solve parameters.
+struct ChunkGraph {
+  bool valid = false;
+  SolveParams key{};
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;       // kernel nodes in the graph (counted per replay)
+};
+
 struct pdqp_problem {
   Work w;
   std::string err;
   bool mixed_ready = false;
   int last_precision = PDQP_PREC_FP64;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // solve start, setup done, loop done
+  cudaStream_t cap = nullptr;                         // private stream for graph capture
+  ChunkGraph graph;
   std::vector<void*> allocs;
 };
 
@@ -235,6 +246,32 @@ void sync_state(pdqp_problem* h, cudaStream_t s) {
   if (h->w.prof.on) h->w.prof.harvest();
 }
 
+// Launch one full chunk through the cached graph (capturing it first if needed).
+void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
+  Work& w = h->w;
+  ChunkGraph& g = h->graph;
+  if (!g.valid || std::memcmp(&g.key, &p, sizeof(SolveParams)) != 0) {
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    g.valid = false;
+    if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    const long long before = pdqp::g_launches;
+    pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap);
+    pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
+    g.kernels = pdqp::g_launches - before;
+    pdqp::g_launches = before;   // captured, not launched
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(h->cap, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    g.key = p;
+    g.valid = true;
+  }
+  CK(cudaGraphLaunch(g.exec, s));
+  pdqp::g_launches += g.kernels;
+}
+
 pdqp_status finish_status(int st) {
   switch (st) {
     case ST_OPTIMAL: return PDQP_OK;
@@ -301,8 +338,14 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   bool timed_out = false;
   while (w.st_host->status == ST_RUNNING) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
-    pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s);
-    pdqp::check(w, p, 1, len, mixed, s);
+    // per-kernel event timing needs direct launches (events recorded by graph
+    // nodes cannot be timed), so profiling bypasses the graph
+    if (len == o.check_period && !o.no_graphs && !w.prof.on) {
+      launch_chunk_graph(h, p, mixed, s);
+    } else {
+      pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s);
+      pdqp::check(w, p, 1, len, mixed, s);
+    }
     CK(cudaGetLastError());
     k_total += len;
     sync_state(h, s);
@@ -380,7 +423,7 @@ void pdqp_default_options(pdqp_options* o) {
   o->norm_iters = 500;
   o->norm_tol = 1e-6;
   o->spmv_threads = 0;
-  o->reserved = 0;
+  o->no_graphs = 0;
 }
 
 const char* pdqp_status_string(int32_t st) {
@@ -615,6 +658,8 @@ void pdqp_destroy(pdqp_handle h) {
   if (h->w.st_host) cudaFreeHost(h->w.st_host);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
 }
 

@@ -1737,6 +1737,8 @@ void Profiler::harvest() {
     if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
       ms[kind[i]] += t;
       launches[kind[i]] += 1;
+    } else {
+      cudaGetLastError();   // a failed timing query must not surface as a later error
     }
   }
   kind.clear();

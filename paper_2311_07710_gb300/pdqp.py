@@ -33,7 +33,7 @@ class pdqp_options(ctypes.Structure):
         ("time_limit", ctypes.c_double), ("beta_suff", ctypes.c_double), ("beta_nec", ctypes.c_double),
         ("beta_art", ctypes.c_double), ("pw_theta", ctypes.c_double), ("eps_zero", ctypes.c_double),
         ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double), ("norm_iters", ctypes.c_int32),
-        ("norm_tol", ctypes.c_double), ("spmv_threads", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("norm_tol", ctypes.c_double), ("spmv_threads", ctypes.c_int32), ("no_graphs", ctypes.c_int32),
     ]
 
 

@@ -223,3 +223,14 @@ def test_invalid_inputs(pdqp):
             pdqp.pdqp_solve(h, pdqp.pdqp_default_options(check_period=3))
     finally:
         pdqp.pdqp_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(pdqp, cfg0, precision):
+    """A chunk replayed from its captured CUDA graph computes exactly what the
+    direct launches compute."""
+    a = G.solve(cfg0, precision=precision, no_graphs=0)
+    b = G.solve(cfg0, precision=precision, no_graphs=1)
+    assert a[1].iterations == b[1].iterations
+    np.testing.assert_array_equal(a[2], b[2])
+    np.testing.assert_array_equal(a[3], b[3])
