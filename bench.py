@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 256, 512])
+    ap.add_argument("--workload", default="large_sparse_qp",
+                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp"],
+                    help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
+                         "of horizon 10..100 in one batched handle; random_sparse_qp: n=1000")
+    ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="variables of the workload (m = n/2); smaller only for profiler captures")
     return ap.parse_args()
@@ -202,15 +207,28 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    inst = qpgen.large_sparse_qp(seed=qpgen.SEED_BASE + 1 + rank, n=args.n)
     prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
     opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=args.spmv_threads)
+    if args.workload == "mpc_batch":
+        insts = qpgen.mpc_batch(args.batch, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
+    elif args.workload == "random_sparse_qp":
+        insts = [qpgen.random_sparse_qp(seed=qpgen.SEED_BASE + 1000 * rank)]
+    else:
+        insts = [qpgen.large_sparse_qp(seed=qpgen.SEED_BASE + 1 + rank, n=args.n)]
+    per_step = len(insts)
+    inst = insts[0]
+    N, M = sum(i.n for i in insts), sum(i.m for i in insts)
+    nnz_A = sum(i.nnz_A for i in insts)
+    nnz_P = sum(i.nnz_Q for i in insts) + nnz_A
 
     # ---- device-resident leg ----
-    h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
-                             device=True)
-    x = torch.zeros(inst.n, dtype=torch.float64, device=dev)
-    y = torch.zeros(inst.m, dtype=torch.float64, device=dev)
+    if len(insts) == 1:
+        h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
+                                 device=True)
+    else:
+        h = pdqp.batch_from_instances(insts, device=True)
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+    y = torch.zeros(M, dtype=torch.float64, device=dev)
     infos = []
     for _ in range(args.warmup):
         st, info = pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream)
@@ -235,26 +253,31 @@ def run_ours(args, world, rank, local):
     pdqp.pdqp_profile_enable(h, False)
     t_ms = ev0.elapsed_time(ev1)
     t_ms_max = allreduce_max(t_ms, world, dev)
-    value = world * args.steps / (t_ms_max / 1e3)
+    value = world * args.steps * per_step / (t_ms_max / 1e3)
+    batch_infos = pdqp.pdqp_batch_info(h)
     iters = [i.iterations for i in infos]
     statuses = [i.status for i in infos]
+    inst_iters = [i.iterations for i in batch_infos]
 
     # ---- end-to-end leg: host buffers, H2D + solve + D2H inside the timed region ----
-    host_arrays = [inst.Q.indptr, inst.Q.indices, inst.Q.data, inst.A.indptr, inst.A.indices, inst.A.data,
-                   inst.c, inst.b, inst.l, inst.u]
-    h2d = int(sum(a.nbytes for a in host_arrays))
-    xh, yh = np.zeros(inst.n), np.zeros(inst.m)
+    host_sets = [[i.Q.indptr, i.Q.indices, i.Q.data, i.A.indptr, i.A.indices, i.A.data, i.c, i.b, i.l, i.u]
+                 for i in insts]
+    h2d = int(sum(a.nbytes for s in host_sets for a in s))
+    xh, yh = np.zeros(N), np.zeros(M)
     d2h = xh.nbytes + yh.nbytes
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        he = pdqp.pdqp_create(inst.n, inst.m, inst.m_eq, *host_arrays, stream=stream)
+        if len(insts) == 1:
+            he = pdqp.pdqp_create(inst.n, inst.m, inst.m_eq, *host_sets[0], stream=stream)
+        else:
+            he = pdqp.pdqp_create_batch([(i.n, i.m, i.m_eq, *s) for i, s in zip(insts, host_sets)], stream=stream)
         pdqp.pdqp_solve(he, opts, x_out=xh, y_out=yh, stream=stream)
         pdqp.pdqp_destroy(he)
     torch.cuda.synchronize(dev)
     e2e_s = allreduce_max(time.perf_counter() - t0, world, dev)
-    e2e_value = world * args.e2e_steps / e2e_s if args.e2e_steps > 0 else None
+    e2e_value = world * args.e2e_steps * per_step / e2e_s if args.e2e_steps > 0 else None
     pdqp.pdqp_destroy(h)
 
     # ---- roofline of the dominant kernel ----
@@ -266,7 +289,7 @@ def run_ours(args, world, rank, local):
     avg_s = d["ms"] / d["launches"] / 1e3
     achieved_gbs = d["bytes"] / avg_s / 1e9
     kname = {"dual": "k_dual", "primal": "k_primal"}[dom]
-    nnz_rows = (inst.nnz_A, inst.m, 8) if dom == "dual" else (inst.nnz_Q + inst.nnz_A, inst.n, 15)
+    nnz_rows = (nnz_A, M, 8) if dom == "dual" else (nnz_P, N, 15)
     flops = 2.0 * nnz_rows[0] + nnz_rows[2] * nnz_rows[1]
     if args.precision == "fp64":
         alu_peak = FP64_NOMINAL_TFLOPS * 1e12
@@ -290,19 +313,25 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": t_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic (seeded generator)",
-            "config": {"workload": WORKLOAD if args.n == 1_000_000 else f"large_sparse_qp n={args.n}",
+            "config": {"workload": (WORKLOAD if args.n == 1_000_000 else f"large_sparse_qp n={args.n}")
+                       if args.workload == "large_sparse_qp" else
+                       (f"mpc_batch: {per_step} control QPs, 12 states, 4 inputs, horizon 10..100, one batched handle"
+                        if args.workload == "mpc_batch" else "random_sparse_qp n=1000 m=500"),
                        "precision": args.precision, "eps": 1e-6,
                        "l2": "inputs larger than L2 (matrices >= 200 MB), no flush",
                        "parallelism": f"replicas x{world}"},
-            "iterations_per_solve": iters, "statuses": statuses,
-            "iterations_per_sec": world * sum(iters) / (t_ms_max / 1e3),
+            "iterations_per_solve": iters if per_step == 1 else
+            {"min": min(inst_iters), "median": statistics.median(inst_iters), "max": max(inst_iters)},
+            "statuses": statuses,
+            "iterations_per_sec": world * args.steps * sum(inst_iters) / (t_ms_max / 1e3),
             "rel_kkt": max(i.rel_kkt for i in infos),
             "setup_ms": 1e3 * infos[-1].setup_seconds, "iterate_ms": 1e3 * infos[-1].iterate_seconds,
             "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.n == 1_000_000:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.n == 1_000_000 and \
+            args.workload == "large_sparse_qp":
         v, t_solve, sample = oracle_sample(inst)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:

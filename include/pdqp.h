@@ -151,6 +151,28 @@ pdqp_status pdqp_create(pdqp_handle *out, int64_t n, int64_t m, int64_t m_eq,
                         const double *c, const double *b, const double *l, const double *u,
                         int32_t mem_space, void *stream);
 
+/* Create one handle holding `count` independent problems of uneven sizes,
+ * stacked block-diagonally on the device.  Every argument is a host array of
+ * `count` entries with the meaning of the pdqp_create argument of the same name
+ * (the arrays they point to live in `mem_space`).  pdqp_solve on such a handle
+ * solves all instances in the same launches, each with its own step sizes,
+ * primal weight, restarts and termination; x0/y0/x_out/y_out are then the
+ * instances' vectors concatenated in order, the returned status is the worst
+ * one and pdqp_batch_info gives each instance's summary. */
+pdqp_status pdqp_create_batch(pdqp_handle *out, int32_t count, const int64_t *n, const int64_t *m,
+                              const int64_t *m_eq, const int32_t *const *Q_rowptr,
+                              const int32_t *const *Q_col, const double *const *Q_val,
+                              const int32_t *const *A_rowptr, const int32_t *const *A_col,
+                              const double *const *A_val, const double *const *c,
+                              const double *const *b, const double *const *l, const double *const *u,
+                              int32_t mem_space, void *stream);
+
+/* Number of instances of a handle (1 for pdqp_create). */
+int32_t pdqp_batch_count(pdqp_handle h);
+
+/* Per-instance summaries of the last pdqp_solve (infos[count], host). */
+pdqp_status pdqp_batch_info(pdqp_handle h, pdqp_info *infos, int32_t count);
+
 /* Add a low-rank term to the objective: Q_total = Q + F F' with F float32,
  * row-major n x r (1 <= r <= 256), applied as F(F'x) (never formed).  The
  * low-rank term is left out of the scaling norms; D2 scales F's rows. */
@@ -167,10 +189,12 @@ pdqp_status pdqp_solve(pdqp_handle h, const pdqp_options *opt, const double *x0,
                        double *x_out, double *y_out, pdqp_info *info, int32_t mem_space,
                        void *stream);
 
-/* Solve `count` independent problems with the same options.  Arrays of
- * per-problem pointers (host arrays of pointers; the pointed-to vectors live in
- * `mem_space`); x0/y0/x_out/y_out may be NULL as a whole or per entry.
- * infos[count] receives one summary per problem.  Returns the worst status. */
+/* Solve `count` separate handles with the same options, one after the other
+ * on `stream` (for many small problems, one pdqp_create_batch handle solves
+ * them together).  Arrays of per-problem pointers (host arrays of pointers; the
+ * pointed-to vectors live in `mem_space`); x0/y0/x_out/y_out may be NULL as a
+ * whole or per entry.  infos[count] receives one summary per problem.  Returns
+ * the worst status. */
 pdqp_status pdqp_solve_batch(int32_t count, const pdqp_handle *hs, const pdqp_options *opt,
                              const double *const *x0, const double *const *y0,
                              double *const *x_out, double *const *y_out, pdqp_info *infos,

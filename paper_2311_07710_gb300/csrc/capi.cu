@@ -27,6 +27,7 @@ struct pdqp_problem {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // solve start, setup done, loop done
   cudaStream_t cap = nullptr;                         // private stream for graph capture
   ChunkGraph graph;
+  std::vector<pdqp_info> infos;                       // per instance, from the last solve
   std::vector<void*> allocs;
 };
 
@@ -141,7 +142,8 @@ std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
 }
 
 void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
-                const std::vector<double>& val, const std::vector<int32_t>* split, cudaStream_t s) {
+                const std::vector<double>& val, const std::vector<int32_t>* split, const std::vector<int32_t>& blk,
+                cudaStream_t s) {
   M.rows = rows;
   M.nnz = rp[rows];
   // 8 elements of padding: the pipelined kernels copy 16-byte aligned supersets
@@ -156,7 +158,6 @@ void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& 
   to_device(M.rp, rp.data(), rows + 1, s);
   to_device(M.col, col.data(), M.nnz, s);
   to_device(M.val, val.data(), M.nnz, s);
-  const std::vector<int32_t> blk = row_blocks(rows, rp);
   M.nblk = (int)blk.size() - 1;
   M.blk = dalloc<int>(h, blk.size());
   to_device(M.blk, blk.data(), blk.size(), s);
@@ -240,10 +241,35 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-void sync_state(pdqp_problem* h, cudaStream_t s) {
-  CK(cudaMemcpyAsync(h->w.st_host, h->w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+// Read the batch counters (8 bytes) -- the only host round trip per chunk.
+void sync_batch(pdqp_problem* h, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->w.bst_host, h->w.bst, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h->w.prof.on) h->w.prof.harvest();
+}
+
+// Read every instance's scalar state.
+void sync_state(pdqp_problem* h, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->w.st_host, h->w.st, sizeof(DevState) * h->w.count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h->w.prof.on) h->w.prof.harvest();
+}
+
+void fill_info(pdqp_info* info, const DevState& S, pdqp_status status, bool lanczos) {
+  std::memset(info, 0, sizeof(*info));
+  info->status = status;
+  info->iterations = S.k_total;
+  info->restarts = S.restarts;
+  info->r_primal = S.out_parts[0];
+  info->r_dual = S.out_parts[1];
+  info->r_gap = S.out_parts[2];
+  info->rel_kkt = S.out_parts[3];
+  info->primal_obj = S.out_parts[4];
+  info->dual_obj = S.out_parts[5];
+  info->norm_A = S.normA;
+  info->norm_Q = S.normQ;
+  info->omega = S.omega;
+  info->norm_iters = lanczos ? S.pi_iters : 0;
 }
 
 // Launch one full chunk through the cached graph (capturing it first if needed).
@@ -304,6 +330,12 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   }
 
   h->last_precision = o.precision;
+  if (w.tab_stride < o.check_period) {
+    w.tab = dalloc<StepEntry>(h, (size_t)w.count * o.check_period);
+    w.tab_stride = o.check_period;
+    if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
+    h->graph.valid = false;
+  }
   CK(cudaEventRecord(h->ev[0], s));
   // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle
   pdqp::scale_reset(w, s);
@@ -321,8 +353,9 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     for (int t = 0; t < o.norm_iters; ++t) {
       pdqp::lanczos_step(w, t, p, mixed, s);
       if ((t & 7) == 7) {
-        sync_state(h, s);
-        if (w.st_host->pi_done[0] && w.st_host->pi_done[1]) break;
+        pdqp::count_running(w, s);
+        sync_batch(h, s);
+        if (w.bst_host->lz_running == 0) break;
       }
     }
   }
@@ -331,12 +364,11 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   pdqp::init_iterates(w, dx0, dy0, p, s);
   pdqp::check(w, p, 0, 0, mixed, s);
   CK(cudaGetLastError());
-  sync_state(h, s);
+  sync_batch(h, s);
 
   long long k_total = 0;
-  pdqp_status result = PDQP_OK;
   bool timed_out = false;
-  while (w.st_host->status == ST_RUNNING) {
+  while (w.bst_host->running > 0) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
     // per-kernel event timing needs direct launches (events recorded by graph
     // nodes cannot be timed), so profiling bypasses the graph
@@ -348,10 +380,9 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     }
     CK(cudaGetLastError());
     k_total += len;
-    sync_state(h, s);
-    if (w.st_host->status == ST_RUNNING && now_s() - t0 > o.time_limit) { timed_out = true; break; }
+    sync_batch(h, s);
+    if (w.bst_host->running > 0 && now_s() - t0 > o.time_limit) { timed_out = true; break; }
   }
-  result = timed_out ? PDQP_TIME_LIMIT : finish_status(w.st_host->status);
   CK(cudaEventRecord(h->ev[2], s));
 
   // the returned iterate
@@ -367,29 +398,215 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   }
   CK(cudaGetLastError());
   sync_state(h, s);
+  // per-instance results; the call returns the worst status
+  h->infos.assign(w.count, pdqp_info{});
+  pdqp_status result = PDQP_OK;
+  float t_setup = 0.f, t_iter = 0.f;
+  CK(cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]));
+  CK(cudaEventElapsedTime(&t_iter, h->ev[1], h->ev[2]));
+  const double secs = now_s() - t0;
+  for (int i = 0; i < w.count; ++i) {
+    const DevState& S = w.st_host[i];
+    const pdqp_status si = (timed_out && S.status == ST_RUNNING) ? PDQP_TIME_LIMIT : finish_status(S.status);
+    fill_info(&h->infos[i], S, si, run_lanczos);
+    h->infos[i].setup_seconds = 1e-3 * t_setup;
+    h->infos[i].iterate_seconds = 1e-3 * t_iter;
+    h->infos[i].seconds = secs;
+    if (si > result) result = si;
+  }
   if (info) {
-    const DevState& S = *w.st_host;
+    *info = h->infos[0];
     info->status = result;
-    info->iterations = S.k_total;
-    info->restarts = S.restarts;
-    info->r_primal = S.out_parts[0];
-    info->r_dual = S.out_parts[1];
-    info->r_gap = S.out_parts[2];
-    info->rel_kkt = S.out_parts[3];
-    info->primal_obj = S.out_parts[4];
-    info->dual_obj = S.out_parts[5];
-    info->norm_A = S.normA;
-    info->norm_Q = S.normQ;
-    info->omega = S.omega;
-    float t_setup = 0.f, t_iter = 0.f;
-    CK(cudaEventElapsedTime(&t_setup, h->ev[0], h->ev[1]));
-    CK(cudaEventElapsedTime(&t_iter, h->ev[1], h->ev[2]));
-    info->setup_seconds = 1e-3 * t_setup;
-    info->iterate_seconds = 1e-3 * t_iter;
-    info->norm_iters = run_lanczos ? S.pi_iters : 0;
-    info->seconds = now_s() - t0;
+    for (int i = 1; i < w.count; ++i) info->iterations = std::max(info->iterations, h->infos[i].iterations);
   }
   return result;
+}
+
+// One instance as given by the caller (host or device pointers per mem_space).
+struct InstanceIn {
+  int64_t n, m, m_eq;
+  const int32_t *Q_rowptr, *Q_col;
+  const double* Q_val;
+  const int32_t *A_rowptr, *A_col;
+  const double* A_val;
+  const double *c, *b, *l, *u;
+};
+
+// Validate every instance, stack them block-diagonally (P = [Q | -A'] and A
+// with global column indices, row blocks that never cross an instance) and
+// upload everything.  Returns the new handle.
+pdqp_problem* build_problem(int count, const InstanceIn* ins, int mem, cudaStream_t s) {
+  if (count < 1) throw Fail{PDQP_ERR_INVALID, "count must be >= 1"};
+  if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
+  int64_t N = 0, M = 0;
+  for (int i = 0; i < count; ++i) {
+    const InstanceIn& in = ins[i];
+    if (in.n < 1 || in.m < 0 || in.m_eq < 0 || in.m_eq > in.m)
+      throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
+    if (!in.Q_rowptr || !in.c || !in.l || !in.u) throw Fail{PDQP_ERR_INVALID, "null Q_rowptr, c, l or u"};
+    if (in.m > 0 && (!in.A_rowptr || !in.b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
+    N += in.n;
+    M += in.m;
+  }
+  if (N > (1LL << 30) || M > (1LL << 30)) throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
+  std::vector<int32_t> prp(1, 0), pcol, psplit, arp(1, 0), acol, pblk{0}, ablk{0}, binst_p, binst_a;
+  std::vector<double> pval, aval, hc, hb, hl, hu;
+  std::vector<int32_t> rinst_n, rinst_m;
+  std::vector<unsigned char> ineq;
+  std::vector<Inst> insts(count);
+  int64_t xoff = 0, yoff = 0;
+  for (int i = 0; i < count; ++i) {
+    const InstanceIn& in = ins[i];
+    const int64_t n = in.n, m = in.m;
+    for (auto pr : {(const void*)in.Q_rowptr, (const void*)in.Q_col, (const void*)in.Q_val,
+                    (const void*)in.A_rowptr, (const void*)in.A_col, (const void*)in.A_val, (const void*)in.c,
+                    (const void*)in.b, (const void*)in.l, (const void*)in.u})
+      check_space(pr, mem, "input array");
+    std::vector<int32_t> qrp = fetch(in.Q_rowptr, n + 1, mem, s);
+    const int64_t nnzQ = qrp[n];
+    if (nnzQ < 0 || (nnzQ > 0 && (!in.Q_col || !in.Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
+    std::vector<int32_t> qcol = fetch(in.Q_col, nnzQ, mem, s);
+    std::vector<double> qval = fetch(in.Q_val, nnzQ, mem, s);
+    std::vector<int32_t> irp(m + 1, 0), icol;
+    std::vector<double> ival;
+    if (m > 0) {
+      irp = fetch(in.A_rowptr, m + 1, mem, s);
+      const int64_t nnzA = irp[m];
+      if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
+      icol = fetch(in.A_col, nnzA, mem, s);
+      ival = fetch(in.A_val, nnzA, mem, s);
+    }
+    std::vector<double> c = fetch(in.c, n, mem, s), l = fetch(in.l, n, mem, s), u = fetch(in.u, n, mem, s);
+    std::vector<double> b = m > 0 ? fetch(in.b, m, mem, s) : std::vector<double>();
+    validate_csr("Q", n, n, qrp, qcol, qval);
+    validate_csr("A", m, n, irp, icol, ival);
+    for (int64_t j = 0; j < n; ++j) {
+      if (!std::isfinite(c[j])) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
+      if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
+        throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
+    }
+    for (int64_t r = 0; r < m; ++r)
+      if (!std::isfinite(b[r])) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
+    std::vector<int32_t> trp, tcol;
+    std::vector<double> tval;
+    if (m > 0) transpose_csr(m, n, irp, icol, ival, trp, tcol, tval);
+    else trp.assign(n + 1, 0);
+    // rows of P = [Q | -A'] with global columns: x part xoff + j, y part N + yoff + r
+    for (int64_t j = 0; j < n; ++j) {
+      for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k) { pcol.push_back((int32_t)(xoff + qcol[k])); pval.push_back(qval[k]); }
+      psplit.push_back((int32_t)pcol.size());
+      for (int32_t k = trp[j]; k < trp[j + 1]; ++k) {
+        pcol.push_back((int32_t)(N + yoff + tcol[k]));
+        pval.push_back(-tval[k]);
+      }
+      if (pcol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
+      prp.push_back((int32_t)pcol.size());
+    }
+    for (int64_t r = 0; r < m; ++r) {
+      for (int32_t k = irp[r]; k < irp[r + 1]; ++k) { acol.push_back((int32_t)(xoff + icol[k])); aval.push_back(ival[k]); }
+      if (acol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(A) exceeds 2^31"};
+      arp.push_back((int32_t)acol.size());
+    }
+    // row blocks of this instance, offset to global rows
+    Inst& I = insts[i];
+    I.n = (int)n; I.m = (int)m; I.m_eq = (int)in.m_eq; I.xoff = (int)xoff; I.yoff = (int)yoff;
+    {
+      std::vector<int32_t> lp(prp.end() - (n + 1), prp.end());
+      const int32_t base = lp[0];
+      for (auto& v : lp) v -= base;
+      const std::vector<int32_t> bl = row_blocks(n, lp);
+      I.bP0 = (int)pblk.size() - 1;
+      for (size_t q = 1; q < bl.size(); ++q) { pblk.push_back((int32_t)(xoff + bl[q])); binst_p.push_back(i); }
+      I.bP1 = (int)pblk.size() - 1;
+    }
+    {
+      I.bA0 = (int)ablk.size() - 1;
+      if (m > 0) {
+        const std::vector<int32_t> bl = row_blocks(m, irp);
+        for (size_t q = 1; q < bl.size(); ++q) { ablk.push_back((int32_t)(yoff + bl[q])); binst_a.push_back(i); }
+      }
+      I.bA1 = (int)ablk.size() - 1;
+    }
+    hc.insert(hc.end(), c.begin(), c.end());
+    hl.insert(hl.end(), l.begin(), l.end());
+    hu.insert(hu.end(), u.begin(), u.end());
+    hb.insert(hb.end(), b.begin(), b.end());
+    rinst_n.insert(rinst_n.end(), (size_t)n, i);
+    rinst_m.insert(rinst_m.end(), (size_t)m, i);
+    for (int64_t r = 0; r < m; ++r) ineq.push_back(r >= in.m_eq ? 1 : 0);
+    xoff += n;
+    yoff += m;
+  }
+
+  pdqp_problem* h = new pdqp_problem();
+  try {
+    Work& w = h->w;
+    w.n = (int)N; w.m = (int)M; w.m_eq = (int)ins[0].m_eq; w.count = count;
+    w.inst_host = insts;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    upload_csr(h, w.P, (int)N, prp, pcol, pval, &psplit, pblk, s);
+    upload_csr(h, w.A, (int)M, arp, acol, aval, nullptr, ablk, s);
+    const size_t n = (size_t)N, m = (size_t)M;
+    w.inst = dalloc<Inst>(h, count);
+    to_device(w.inst, insts.data(), count, s);
+    w.blk_inst_P = dalloc<int>(h, binst_p.size());
+    to_device(w.blk_inst_P, binst_p.data(), binst_p.size(), s);
+    w.blk_inst_A = dalloc<int>(h, binst_a.size());
+    to_device(w.blk_inst_A, binst_a.data(), binst_a.size(), s);
+    w.row_inst_n = dalloc<int>(h, n);
+    to_device(w.row_inst_n, rinst_n.data(), n, s);
+    w.row_inst_m = dalloc<int>(h, m);
+    to_device(w.row_inst_m, rinst_m.data(), m, s);
+    w.row_ineq = dalloc<unsigned char>(h, m);
+    to_device(w.row_ineq, ineq.data(), m, s);
+    w.c = dalloc<double>(h, n); w.l = dalloc<double>(h, n); w.u = dalloc<double>(h, n); w.b = dalloc<double>(h, m);
+    to_device(w.c, hc.data(), n, s); to_device(w.l, hl.data(), n, s); to_device(w.u, hu.data(), n, s);
+    to_device(w.b, hb.data(), m, s);
+    w.cs = dalloc<double>(h, n); w.ls = dalloc<double>(h, n); w.us = dalloc<double>(h, n); w.bs = dalloc<double>(h, m);
+    w.dsc = dalloc<double>(h, n + m); w.idsc = dalloc<double>(h, n + m); w.nu = dalloc<double>(h, n + m);
+    w.D2 = w.dsc; w.D1 = w.dsc + n; w.iD2 = w.idsc; w.iD1 = w.idsc + n;
+    w.x = dalloc<double>(h, n); w.xbar = dalloc<double>(h, n); w.xt = dalloc<double>(h, n);
+    w.Z[0] = dalloc<double>(h, n + m); w.Z[1] = dalloc<double>(h, n + m); w.ax = dalloc<double>(h, n);
+    w.y = w.Z[1] + n;
+    w.ybar = dalloc<double>(h, m); w.ay = dalloc<double>(h, m);
+    w.pu[0] = dalloc<double>(h, n); w.pu[1] = dalloc<double>(h, n);
+    w.pz[0] = dalloc<double>(h, n + m); w.pz[1] = dalloc<double>(h, n + m);
+    w.lw[0] = dalloc<double>(h, n); w.lw[1] = dalloc<double>(h, n);
+    w.lz_al = dalloc<double>(h, (size_t)count * 2 * 512); w.lz_be = dalloc<double>(h, (size_t)count * 2 * 512);
+    w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
+    w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
+    w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
+    w.st = dalloc<DevState>(h, count);
+    w.bst = dalloc<BatchState>(h, 1);
+    w.stage_n = dalloc<double>(h, n); w.stage_m = dalloc<double>(h, m);
+    CK(cudaMallocHost(&w.st_host, sizeof(DevState) * count));
+    CK(cudaMallocHost(&w.bst_host, sizeof(BatchState)));
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    CK(cudaMemsetAsync(w.st, 0, sizeof(DevState) * count, s));
+    CK(cudaMemsetAsync(w.bst, 0, sizeof(BatchState), s));
+    CK(cudaStreamSynchronize(s));
+  } catch (...) {
+    pdqp_destroy(h);
+    throw;
+  }
+  return h;
+}
+
+pdqp_status create_common(pdqp_handle* out, int count, const InstanceIn* ins, int mem, cudaStream_t s) {
+  if (!out) return PDQP_ERR_INVALID;
+  *out = nullptr;
+  try {
+    *out = build_problem(count, ins, mem, s);
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    g_create_error = f.msg;
+    return f.st;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    return PDQP_ERR_OOM;
+  }
 }
 
 }  // namespace
@@ -444,108 +661,27 @@ pdqp_status pdqp_create(pdqp_handle* out, int64_t n, int64_t m, int64_t m_eq, co
                         const int32_t* Q_col, const double* Q_val, const int32_t* A_rowptr, const int32_t* A_col,
                         const double* A_val, const double* c, const double* b, const double* l, const double* u,
                         int32_t mem, void* stream) {
-  if (!out) return PDQP_ERR_INVALID;
-  *out = nullptr;
-  pdqp_problem* h = nullptr;
-  cudaStream_t s = (cudaStream_t)stream;
-  try {
-    if (n < 1 || m < 0 || m_eq < 0 || m_eq > m || n > (1LL << 30) || m > (1LL << 30))
-      throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
-    if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
-    if (!Q_rowptr || !c || !l || !u) throw Fail{PDQP_ERR_INVALID, "null Q_rowptr, c, l or u"};
-    if (m > 0 && (!A_rowptr || !b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
-    for (auto pr : {(const void*)Q_rowptr, (const void*)Q_col, (const void*)Q_val, (const void*)A_rowptr,
-                    (const void*)A_col, (const void*)A_val, (const void*)c, (const void*)b, (const void*)l,
-                    (const void*)u})
-      check_space(pr, mem, "input array");
-    // fetch to host for validation and the transpose of A
-    std::vector<int32_t> qrp = fetch(Q_rowptr, n + 1, mem, s);
-    const int64_t nnzQ = qrp[n];
-    if (nnzQ < 0 || (nnzQ > 0 && (!Q_col || !Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
-    std::vector<int32_t> qcol = fetch(Q_col, nnzQ, mem, s);
-    std::vector<double> qval = fetch(Q_val, nnzQ, mem, s);
-    std::vector<int32_t> arp(m + 1, 0), acol;
-    std::vector<double> aval;
-    if (m > 0) {
-      arp = fetch(A_rowptr, m + 1, mem, s);
-      const int64_t nnzA = arp[m];
-      if (nnzA < 0 || (nnzA > 0 && (!A_col || !A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
-      acol = fetch(A_col, nnzA, mem, s);
-      aval = fetch(A_val, nnzA, mem, s);
-    }
-    std::vector<double> hc = fetch(c, n, mem, s), hl = fetch(l, n, mem, s), hu = fetch(u, n, mem, s);
-    std::vector<double> hb = m > 0 ? fetch(b, m, mem, s) : std::vector<double>();
-    validate_csr("Q", n, n, qrp, qcol, qval);
-    validate_csr("A", m, n, arp, acol, aval);
-    for (int64_t j = 0; j < n; ++j) {
-      if (!std::isfinite(hc[j])) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
-      if (std::isnan(hl[j]) || std::isnan(hu[j]) || hl[j] > hu[j] || hl[j] == INFINITY || hu[j] == -INFINITY)
-        throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
-    }
-    for (int64_t i = 0; i < m; ++i)
-      if (!std::isfinite(hb[i])) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
-    std::vector<int32_t> trp, tcol;
-    std::vector<double> tval;
-    if (m > 0) transpose_csr(m, n, arp, acol, aval, trp, tcol, tval);
-    else trp.assign(n + 1, 0);
-    // P = [Q | -A'] row by row: Q's columns, then A' columns shifted by n
-    std::vector<int32_t> prp(n + 1, 0), pcol, psplit(n);
-    std::vector<double> pval;
-    pcol.reserve((size_t)qrp[n] + trp[n]);
-    pval.reserve((size_t)qrp[n] + trp[n]);
-    for (int64_t j = 0; j < n; ++j) {
-      for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k) { pcol.push_back(qcol[k]); pval.push_back(qval[k]); }
-      psplit[j] = (int32_t)pcol.size();
-      for (int32_t k = trp[j]; k < trp[j + 1]; ++k) { pcol.push_back((int32_t)(n + tcol[k])); pval.push_back(-tval[k]); }
-      if (pcol.size() > (size_t)INT32_MAX) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31-1"};
-      prp[j + 1] = (int32_t)pcol.size();
-    }
-    { std::vector<int32_t>().swap(tcol); std::vector<double>().swap(tval); }
+  InstanceIn in{n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, l, u};
+  return create_common(out, 1, &in, mem, (cudaStream_t)stream);
+}
 
-    h = new pdqp_problem();
-    Work& w = h->w;
-    w.n = (int)n; w.m = (int)m; w.m_eq = (int)m_eq;
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    upload_csr(h, w.P, (int)n, prp, pcol, pval, &psplit, s);
-    upload_csr(h, w.A, (int)m, arp, acol, aval, nullptr, s);
-    const size_t N = (size_t)n, M = (size_t)m;
-    w.c = dalloc<double>(h, N); w.l = dalloc<double>(h, N); w.u = dalloc<double>(h, N); w.b = dalloc<double>(h, M);
-    to_device(w.c, hc.data(), N, s); to_device(w.l, hl.data(), N, s); to_device(w.u, hu.data(), N, s);
-    to_device(w.b, hb.data(), M, s);
-    w.cs = dalloc<double>(h, N); w.ls = dalloc<double>(h, N); w.us = dalloc<double>(h, N); w.bs = dalloc<double>(h, M);
-    w.dsc = dalloc<double>(h, N + M); w.idsc = dalloc<double>(h, N + M); w.nu = dalloc<double>(h, N + M);
-    w.D2 = w.dsc; w.D1 = w.dsc + N; w.iD2 = w.idsc; w.iD1 = w.idsc + N;
-    w.x = dalloc<double>(h, N); w.xbar = dalloc<double>(h, N); w.xt = dalloc<double>(h, N);
-    w.Z[0] = dalloc<double>(h, N + M); w.Z[1] = dalloc<double>(h, N + M); w.ax = dalloc<double>(h, N);
-    w.y = w.Z[1] + N;
-    w.ybar = dalloc<double>(h, M); w.ay = dalloc<double>(h, M);
-    w.pu[0] = dalloc<double>(h, N); w.pu[1] = dalloc<double>(h, N);
-    w.pz[0] = dalloc<double>(h, N + M); w.pz[1] = dalloc<double>(h, N + M);
-    w.lw[0] = dalloc<double>(h, N); w.lw[1] = dalloc<double>(h, N);
-    w.lz_al = dalloc<double>(h, 2 * 512); w.lz_be = dalloc<double>(h, 2 * 512);
-    w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
-    w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
-    w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
-    w.tab = dalloc<StepEntry>(h, PDQP_MAX_CHECK);
-    w.st = dalloc<DevState>(h, 1);
-    w.stage_n = dalloc<double>(h, N); w.stage_m = dalloc<double>(h, M);
-    CK(cudaMallocHost(&w.st_host, sizeof(DevState)));
-    for (auto& e : h->ev) CK(cudaEventCreate(&e));
-    CK(cudaMemsetAsync(w.st, 0, sizeof(DevState), s));
-    CK(cudaStreamSynchronize(s));
-    *out = h;
-    return PDQP_OK;
-  } catch (const Fail& f) {
-    g_create_error = f.msg;
-    if (h) pdqp_destroy(h);
-    return f.st;
-  } catch (const std::bad_alloc&) {
-    g_create_error = "host allocation failed";
-    if (h) pdqp_destroy(h);
-    return PDQP_ERR_OOM;
+pdqp_status pdqp_create_batch(pdqp_handle* out, int32_t count, const int64_t* n, const int64_t* m,
+                              const int64_t* m_eq, const int32_t* const* Q_rowptr, const int32_t* const* Q_col,
+                              const double* const* Q_val, const int32_t* const* A_rowptr,
+                              const int32_t* const* A_col, const double* const* A_val, const double* const* c,
+                              const double* const* b, const double* const* l, const double* const* u, int32_t mem,
+                              void* stream) {
+  if (!out || count < 1 || !n || !m || !m_eq || !Q_rowptr || !Q_col || !Q_val || !A_rowptr || !A_col || !A_val ||
+      !c || !b || !l || !u) {
+    if (out) *out = nullptr;
+    g_create_error = "null argument or count < 1";
+    return PDQP_ERR_INVALID;
   }
+  std::vector<InstanceIn> ins(count);
+  for (int i = 0; i < count; ++i)
+    ins[i] = InstanceIn{n[i], m[i], m_eq[i], Q_rowptr[i], Q_col[i], Q_val[i], A_rowptr[i], A_col[i], A_val[i],
+                        c[i], b[i], l[i], u[i]};
+  return create_common(out, count, ins.data(), mem, (cudaStream_t)stream);
 }
 
 pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t mem, void* stream) {
@@ -640,6 +776,14 @@ pdqp_status pdqp_kkt(pdqp_handle h, const double* x, const double* y, double* pa
   }
 }
 
+pdqp_status pdqp_batch_info(pdqp_handle h, pdqp_info* infos, int32_t count) {
+  if (!h || !infos || count != h->w.count || (int)h->infos.size() != count) return PDQP_ERR_INVALID;
+  for (int i = 0; i < count; ++i) infos[i] = h->infos[i];
+  return PDQP_OK;
+}
+
+int32_t pdqp_batch_count(pdqp_handle h) { return h ? h->w.count : 0; }
+
 pdqp_status pdqp_get_sizes(pdqp_handle h, int64_t* n, int64_t* m, int64_t* m_eq, int64_t* nnz_Q, int64_t* nnz_A) {
   if (!h) return PDQP_ERR_INVALID;
   if (n) *n = h->w.n;
@@ -656,6 +800,7 @@ void pdqp_destroy(pdqp_handle h) {
   if (!h) return;
   for (void* p : h->allocs) cudaFree(p);
   if (h->w.st_host) cudaFreeHost(h->w.st_host);
+  if (h->w.bst_host) cudaFreeHost(h->w.bst_host);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);

@@ -49,6 +49,20 @@ struct DevState {
   int pad1;
 };
 
+// Layout of one instance inside a block-diagonal batch.
+struct Inst {
+  int n, m, m_eq;        // sizes
+  int xoff, yoff;        // first variable / row of the instance
+  int bP0, bP1;          // row blocks of P
+  int bA0, bA1;          // row blocks of A
+};
+
+// Batch-wide counters read by the host between chunks.
+struct BatchState {
+  int running;           // instances still iterating
+  int lz_running;        // instances whose norm estimates are still running
+};
+
 // Constant parameters of one solve.
 struct SolveParams {
   int step_rule, restart_rule, accelerate, fixed_K, check_period, mixed;

@@ -290,8 +290,11 @@ struct DualB {
   V* __restrict__ ybar;
   const V* __restrict__ b;
   const V* __restrict__ ylo;     // lower bound of inequality duals (mixed-mode shift) or null (0)
-  const StepEntry* __restrict__ tab;
-  int m, m_eq;
+  const StepEntry* __restrict__ tab;    // [instance][C]
+  const int* __restrict__ blk_inst;     // instance of each row block
+  const DevState* __restrict__ st;      // per instance
+  const unsigned char* __restrict__ ineq;   // per row: inequality
+  int C;
 };
 
 template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
@@ -315,7 +318,7 @@ __device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, 
                                          V lo) {
   const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
   V yn = yo - sigma * (s - bi);
-  if (r >= a.m_eq) yn = fmax(yn, lo);
+  if (a.ineq[r]) yn = fmax(yn, lo);
   a.ybar[r] = (V(1) - ib) * yb + ib * yn;
   a.ynew[r] = yn;
 }
@@ -325,6 +328,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_dual(DualB<V> a, i
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
+  const int inst = a.blk_inst[blockIdx.x];
+  if (a.st[inst].status != ST_RUNNING) return;
   const int r0 = a.A.blk[blockIdx.x], r1 = a.A.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = a.A.rp[r0];
@@ -334,9 +339,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_dual(DualB<V> a, i
   if (tid < nr) {
     const int r = r0 + tid;
     yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-    if (a.ylo && r >= a.m_eq) lo = a.ylo[r];
+    if (a.ylo) lo = a.ylo[r];
   }
-  const StepEntry& es = a.tab[j];
+  const StepEntry& es = a.tab[inst * a.C + j];
   if (ne <= BNNZ) {
     stage_products<NT>(a.A, a.xt, e0, ne, r0, nr, prod, srp);
     __syncthreads();
@@ -346,7 +351,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_dual(DualB<V> a, i
       const int r = r0 + t;
       if (t >= BNT) {
         yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-        lo = (a.ylo && r >= a.m_eq) ? a.ylo[r] : V(0);
+        lo = a.ylo ? a.ylo[r] : V(0);
       }
       dual_row(a, es, r, s, yo, bi, yb, lo);
     }
@@ -372,8 +377,10 @@ struct PrimalB {
   const V* __restrict__ c;
   const V* __restrict__ l;
   const V* __restrict__ u;
-  const StepEntry* __restrict__ tab;
-  int n;
+  const StepEntry* __restrict__ tab;    // [instance][C]
+  const int* __restrict__ blk_inst;
+  const DevState* __restrict__ st;
+  int C;
 };
 
 template <typename V>
@@ -394,6 +401,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_primal(PrimalB<V> 
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
+  const int inst = a.blk_inst[blockIdx.x];
+  if (a.st[inst].status != ST_RUNNING) return;
   const int r0 = a.P.blk[blockIdx.x], r1 = a.P.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = a.P.rp[r0];
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_primal(PrimalB<V> 
     const int r = r0 + tid;
     xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
   }
-  const StepEntry& es = a.tab[j];
+  const StepEntry& es = a.tab[inst * a.C + j];
   if (ne <= BNNZ) {
     stage_products<NT>(a.P, a.zin, e0, ne, r0, nr, prod, srp);
     __syncthreads();
@@ -468,7 +477,6 @@ __global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __rest
   extern __shared__ __align__(16) unsigned char smraw[];
   PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
   const int tid = threadIdx.x;
-  const StepEntry& es = a.tab[j];
   int b = blockIdx.x;
   if (b >= nblk) return;
   int4 mc = meta[b];
@@ -479,15 +487,19 @@ __global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __rest
     if (bn < nblk) mn = meta[bn];
     pipe_issue<NT>(sm, s ^ 1, mn, a.A.col, a.A.val, a.A.rp);
     const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
+    const int inst = a.blk_inst[b];
+    const bool live = a.st[inst].status == ST_RUNNING;
+    const StepEntry& es = a.tab[inst * a.C + j];
     V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
-    if (tid < nr) {
+    if (live && tid < nr) {
       const int r = r0 + tid;
       yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-      if (a.ylo && r >= a.m_eq) lo = a.ylo[r];
+      if (a.ylo) lo = a.ylo[r];
     }
     cp_async_wait1();
     __syncthreads();
-    if (ne <= BNNZ) {
+    if (!live) {
+    } else if (ne <= BNNZ) {
       const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
 #pragma unroll
       for (int k = 0; k < BNNZ / NT; ++k) {
@@ -502,7 +514,7 @@ __global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __rest
         const int r = r0 + t;
         if (t >= NT) {
           yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-          lo = (a.ylo && r >= a.m_eq) ? a.ylo[r] : V(0);
+          lo = a.ylo ? a.ylo[r] : V(0);
         }
         dual_row(a, es, r, acc, yo, bi, yb, lo);
       }
@@ -522,7 +534,6 @@ __global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __
   extern __shared__ __align__(16) unsigned char smraw[];
   PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
   const int tid = threadIdx.x;
-  const StepEntry& es = a.tab[j];
   int b = blockIdx.x;
   if (b >= nblk) return;
   int4 mc = meta[b];
@@ -533,14 +544,18 @@ __global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __
     if (bn < nblk) mn = meta[bn];
     pipe_issue<NT>(sm, s ^ 1, mn, a.P.col, a.P.val, a.P.rp);
     const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
+    const int inst = a.blk_inst[b];
+    const bool live = a.st[inst].status == ST_RUNNING;
+    const StepEntry& es = a.tab[inst * a.C + j];
     V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
-    if (tid < nr) {
+    if (live && tid < nr) {
       const int r = r0 + tid;
       xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
     }
     cp_async_wait1();
     __syncthreads();
-    if (ne <= BNNZ) {
+    if (!live) {
+    } else if (ne <= BNNZ) {
       const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
 #pragma unroll
       for (int k = 0; k < BNNZ / NT; ++k) {
@@ -587,7 +602,11 @@ struct KktB {
   double* part_m;                       // [9][nblk_m]
   double* part_n;                       // [15][nblk_n]
   int nblk_m, nblk_n;
-  int n, m, m_eq;
+  int n, m;
+  const unsigned char* ineq;            // per row of A: inequality
+  const int* blk_inst_A;                // instance of each row block (null: no status test)
+  const int* blk_inst_P;
+  const DevState* st;
 };
 
 template <int NIT>
@@ -597,6 +616,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
   __shared__ int srp[BROWS + 1];
   double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int tid = threadIdx.x;
+  if (a.st && a.st[a.blk_inst_A[blockIdx.x]].status != ST_RUNNING) return;
   const int r0 = a.A.blk[blockIdx.x], r1 = a.A.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = a.A.rp[r0];
@@ -608,7 +628,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
     for (int it = 0; it < NIT; ++it) {
       if (a.prodAx[it]) a.prodAx[it][r] = s[it];
       const double Ax = s[it] * id1;
-      const double viol = r < a.m_eq ? fabs(Ax - bi) : fmax(bi - Ax, 0.0);
+      const double viol = a.ineq[r] ? fmax(bi - Ax, 0.0) : fabs(Ax - bi);
       f[it * 4 + 0] = nmax(f[it * 4 + 0], viol);
       f[it * 4 + 1] = nmax(f[it * 4 + 1], fabs(Ax));
       const double yt = a.y[it][r];
@@ -675,6 +695,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
 #pragma unroll
   for (int k = 0; k < 15; ++k) f[k] = 0.0;
   const int tid = threadIdx.x;
+  if (a.st && a.st[a.blk_inst_P[blockIdx.x]].status != ST_RUNNING) return;
   const int r0 = a.P.blk[blockIdx.x], r1 = a.P.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = a.P.rp[r0];
@@ -760,22 +781,23 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
     for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
 }
 
-// reduce the field-major partials of k_kkt_m / k_kkt_n into F[0..23] (thread 0)
-__device__ void reduce_kkt_blocks(const double* __restrict__ pm, int nbm, const double* __restrict__ pn,
-                                  int nbn, double* F) {
+// reduce the field-major partials of k_kkt_m / k_kkt_n (blocks [bm0, bm1) of
+// [nbm] and [bn0, bn1) of [nbn]) into F[0..23] (thread 0)
+__device__ void reduce_kkt_blocks(const double* __restrict__ pm, int nbm, int bm0, int bm1,
+                                  const double* __restrict__ pn, int nbn, int bn0, int bn1, double* F) {
   double f[24];
 #pragma unroll
   for (int k = 0; k < 24; ++k) f[k] = 0.0;
   const bool is_max[24] = {true, true, false, false, true, true, false, false, true,
                            true, true, true, false, false, false, false,
                            true, true, true, false, false, false, false, true};
-  for (int b = threadIdx.x; b < nbm; b += blockDim.x)
+  for (int b = bm0 + threadIdx.x; b < bm1; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const double v = pm[(size_t)k * nbm + b];
       f[k] = is_max[k] ? nmax(f[k], v) : f[k] + v;
     }
-  for (int b = threadIdx.x; b < nbn; b += blockDim.x)
+  for (int b = bn0 + threadIdx.x; b < bn1; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
       const double v = pn[(size_t)k * nbn + b];
@@ -914,17 +936,24 @@ __global__ void k_scale_vectors(int n, int m, const double* __restrict__ D1, con
 constexpr int LZ_MAX = 512;
 
 struct LzArgs {
-  int n, m, have_rows;
-  double* al;        // [2][LZ_MAX] alphas of A'A and Q
-  double* be;        // [2][LZ_MAX] betas
-  DevState* st;
+  int n, m, count;
+  double* al;                      // [count][2][LZ_MAX] alphas (A'A, Q)
+  double* be;                      // [count][2][LZ_MAX] betas
+  DevState* st;                    // [count]
+  const Inst* inst;                // [count]
+  const int* blk_inst_P;           // instance of each P row block
+  const int* blk_inst_A;
+  const int* row_inst_n;
+  int nblkP;
 };
 
+__device__ __forceinline__ double* lz_al(const LzArgs& a, int i, int o) { return a.al + ((size_t)i * 2 + o) * LZ_MAX; }
+__device__ __forceinline__ double* lz_be(const LzArgs& a, int i, int o) { return a.be + ((size_t)i * 2 + o) * LZ_MAX; }
+
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, const V* __restrict__ vA,
-                                                                   V* __restrict__ wm,
-                                                                   const DevState* __restrict__ st) {
-  if (st->pi_done[0]) return;
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, LzArgs la, const V* __restrict__ vA,
+                                                                   V* __restrict__ wm) {
+  if (la.st[la.blk_inst_A[blockIdx.x]].pi_done[0]) return;
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -948,19 +977,18 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, co
   }
 }
 
-// rows of P with input [v_Q ; w_m]: wA = A~'w_m, wQ = Q~ v_Q; partial v'w per block
+// rows of P with input [v_Q ; w_m]: wA = A~'w_m, wQ = Q~ v_Q; partial v'w per row block
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, const V* __restrict__ zin,
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, LzArgs la, const V* __restrict__ zin,
                                                                    const V* __restrict__ vA, V* __restrict__ wA,
-                                                                   V* __restrict__ wQ, const DevState* __restrict__ st,
-                                                                   double* __restrict__ part, int nblk,
-                                                                   int have_rows) {
+                                                                   V* __restrict__ wQ, double* __restrict__ part) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
-  const bool doA = !st->pi_done[0] && have_rows;
-  const bool doQ = !st->pi_done[1];
-  if (!doA && !doQ) return;                    // k_lz_alpha reads no partials then
+  const DevState& st = la.st[la.blk_inst_P[blockIdx.x]];
+  const bool doA = !st.pi_done[0];
+  const bool doQ = !st.pi_done[1];
+  if (!doA && !doQ) return;                    // its instance's alpha reduction skips it
   double f[2] = {0.0, 0.0};
   const int tid = threadIdx.x;
   const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
@@ -994,48 +1022,56 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, co
   }
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
-  if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)nblk + blockIdx.x] = f[1]; }
+  if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)la.nblkP + blockIdx.x] = f[1]; }
 }
 
-__global__ void __launch_bounds__(1024) k_lz_alpha(LzArgs a, const double* __restrict__ part, int nblk) {
+// one CUDA block per instance: alpha_k = sum of its row blocks' partials
+__global__ void __launch_bounds__(512) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
+  const int i = blockIdx.x;
+  DevState& st = a.st[i];
+  if (st.pi_done[0] && st.pi_done[1]) return;
+  const Inst in = a.inst[i];
   double f[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b]; f[1] += part[(size_t)nblk + b]; }
+  for (int b = in.bP0 + threadIdx.x; b < in.bP1; b += blockDim.x) { f[0] += part[b]; f[1] += part[(size_t)a.nblkP + b]; }
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   if (threadIdx.x == 0) {
-    const int k = a.st->pi_iters;
+    const int k = st.pi_iters;
     for (int o = 0; o < 2; ++o)
-      if (!a.st->pi_done[o]) a.al[o * LZ_MAX + k] = f[o];
+      if (!st.pi_done[o]) lz_al(a, i, o)[k] = f[o];
   }
 }
 
-// r = w - alpha v - beta_prev v_prev, written over v_prev; partial |r|^2
+// r = w - alpha v - beta_prev v_prev over v_prev, per P row block; partial |r|^2
 template <typename V>
-__global__ void k_lz_orth(LzArgs a, const V* __restrict__ wA, const V* __restrict__ wQ, const V* __restrict__ vA,
-                          V* __restrict__ vA_prev, const V* __restrict__ vQ, V* __restrict__ vQ_prev,
-                          double* __restrict__ part) {
-  const DevState* st = a.st;
-  const int k = st->pi_iters;
-  const bool doA = !st->pi_done[0] && a.have_rows, doQ = !st->pi_done[1];
+__global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V* __restrict__ wQ,
+                          const V* __restrict__ vA, V* __restrict__ vA_prev, const V* __restrict__ vQ,
+                          V* __restrict__ vQ_prev, double* __restrict__ part) {
+  const int i = a.blk_inst_P[blockIdx.x];
+  const DevState& st = a.st[i];
+  const bool doA = !st.pi_done[0], doQ = !st.pi_done[1];
   if (!doA && !doQ) return;
-  const double alA = doA ? a.al[k] : 0.0, alQ = doQ ? a.al[LZ_MAX + k] : 0.0;
-  const double bpA = (doA && k > 0) ? a.be[k - 1] : 0.0, bpQ = (doQ && k > 0) ? a.be[LZ_MAX + k - 1] : 0.0;
+  const int k = st.pi_iters;
+  const double alA = doA ? lz_al(a, i, 0)[k] : 0.0, alQ = doQ ? lz_al(a, i, 1)[k] : 0.0;
+  const double bpA = (doA && k > 0) ? lz_be(a, i, 0)[k - 1] : 0.0;
+  const double bpQ = (doQ && k > 0) ? lz_be(a, i, 1)[k - 1] : 0.0;
   double f[2] = {0.0, 0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+  const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     if (doA) {
-      const double r = (double)wA[i] - alA * (double)vA[i] - bpA * (double)vA_prev[i];
-      vA_prev[i] = (V)r;
-      f[0] += r * r;
+      const double v = (double)wA[r] - alA * (double)vA[r] - bpA * (double)vA_prev[r];
+      vA_prev[r] = (V)v;
+      f[0] += v * v;
     }
     if (doQ) {
-      const double r = (double)wQ[i] - alQ * (double)vQ[i] - bpQ * (double)vQ_prev[i];
-      vQ_prev[i] = (V)r;
-      f[1] += r * r;
+      const double v = (double)wQ[r] - alQ * (double)vQ[r] - bpQ * (double)vQ_prev[r];
+      vQ_prev[r] = (V)v;
+      f[1] += v * v;
     }
   }
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
-  if (threadIdx.x == 0) { part[blockIdx.x * 32] = f[0]; part[blockIdx.x * 32 + 1] = f[1]; }
+  if (threadIdx.x == 0) { part[blockIdx.x] = f[0]; part[(size_t)a.nblkP + blockIdx.x] = f[1]; }
 }
 
 // Number of eigenvalues of the k x k tridiagonal (al, be) below x: the sign
@@ -1085,65 +1121,72 @@ __device__ double tridiag_max_eig_warp(const double* __restrict__ al, const doub
   return 0.5 * (lo + hi);
 }
 
-// beta and theta = lambda_max(T_k) (warp 0: A'A, warp 1: Q), stop test
-__global__ void __launch_bounds__(1024) k_lz_beta(LzArgs a, const double* __restrict__ part, int nblk,
-                                                  double tol, int max_steps) {
+// one CUDA block (256 threads) per instance: beta, theta = lambda_max(T_k)
+// (warp 0: A'A, warp 1: Q), stop test
+__global__ void __launch_bounds__(256) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
+                                                int max_steps) {
+  const int i = blockIdx.x;
+  DevState& st = a.st[i];
+  if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
+  const Inst in = a.inst[i];
   double f[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b * 32]; f[1] += part[b * 32 + 1]; }
+  for (int b = in.bP0 + threadIdx.x; b < in.bP1; b += blockDim.x) { f[0] += part[b]; f[1] += part[(size_t)a.nblkP + b]; }
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   __shared__ double beta[2];
-  if (threadIdx.x == 0) { beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]); }
+  __shared__ int done_in[2];
+  if (threadIdx.x == 0) {
+    beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]);
+    done_in[0] = st.pi_done[0]; done_in[1] = st.pi_done[1];
+  }
   __syncthreads();
-  DevState* st = a.st;
-  if (st->pi_done[0] && st->pi_done[1]) return;   // uniform: nothing left to do
-  const int k = st->pi_iters + 1;                 // alphas 0..k-1, betas 0..k-2 form T_k
+  const int k = st.pi_iters + 1;                  // alphas 0..k-1, betas 0..k-2 form T_k
   const int o = threadIdx.x >> 5;
-  if (o < 2 && !st->pi_done[o]) {                 // warp-uniform
-    const double theta = tridiag_max_eig_warp(a.al + o * LZ_MAX, a.be + o * LZ_MAX, k);
+  if (o < 2 && !done_in[o]) {                     // warp-uniform
+    const double theta = tridiag_max_eig_warp(lz_al(a, i, o), lz_be(a, i, o), k);
     if ((threadIdx.x & 31) == 0) {
       const double b = beta[o];
-      st->pi_lam[o] = theta;
-      if (fabs(theta - st->pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
-        st->pi_done[o] = 1;
+      st.pi_lam[o] = theta;
+      if (fabs(theta - st.pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
+        st.pi_done[o] = 1;
       } else {
-        a.be[o * LZ_MAX + k - 1] = b;
-        st->pi_lam_prev[o] = theta;
-        st->pi_inv_norm[o] = 1.0 / b;
+        lz_be(a, i, o)[k - 1] = b;
+        st.pi_lam_prev[o] = theta;
+        st.pi_inv_norm[o] = 1.0 / b;
       }
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) st->pi_iters = k;
+  if (threadIdx.x == 0) st.pi_iters = k;
 }
 
 // v_next = r / beta (in the buffer that held v_prev)
 template <typename V>
 __global__ void k_lz_norm(LzArgs a, V* __restrict__ vA_next, V* __restrict__ vQ_next) {
-  const DevState* st = a.st;
-  const bool doA = !st->pi_done[0] && a.have_rows, doQ = !st->pi_done[1];
-  const double sA = st->pi_inv_norm[0], sQ = st->pi_inv_norm[1];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-    if (doA) vA_next[i] = (V)((double)vA_next[i] * sA);
-    if (doQ) vQ_next[i] = (V)((double)vQ_next[i] * sQ);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += gridDim.x * blockDim.x) {
+    const DevState& st = a.st[a.row_inst_n[r]];
+    // pi_inv_norm changes only when the operator continues
+    if (!st.pi_done[0]) vA_next[r] = (V)((double)vA_next[r] * st.pi_inv_norm[0]);
+    if (!st.pi_done[1]) vQ_next[r] = (V)((double)vQ_next[r] * st.pi_inv_norm[1]);
   }
 }
 
+// start vectors 1/sqrt(n_i) per instance; Lanczos state
 template <typename V>
 __global__ void k_lz_init(LzArgs a, V* __restrict__ vA0, V* __restrict__ vA1, V* __restrict__ vQ0,
                           V* __restrict__ vQ1) {
-  const V v = (V)(1.0 / sqrt((double)a.n));
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-    vA0[i] = v; vQ0[i] = v; vA1[i] = V(0); vQ1[i] = V(0);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += gridDim.x * blockDim.x) {
+    const V v = (V)(1.0 / sqrt((double)a.inst[a.row_inst_n[r]].n));
+    vA0[r] = v; vQ0[r] = v; vA1[r] = V(0); vQ1[r] = V(0);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    DevState* st = a.st;
-    st->pi_done[0] = a.have_rows ? 0 : 1;
-    st->pi_done[1] = 0;
-    st->pi_lam[0] = 0.0; st->pi_lam[1] = 0.0;
-    st->pi_lam_prev[0] = 0.0; st->pi_lam_prev[1] = 0.0;
-    st->pi_inv_norm[0] = 1.0; st->pi_inv_norm[1] = 1.0;
-    st->pi_iters = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.count; i += gridDim.x * blockDim.x) {
+    DevState& st = a.st[i];
+    st.pi_done[0] = a.inst[i].m > 0 ? 0 : 1;
+    st.pi_done[1] = 0;
+    st.pi_lam[0] = 0.0; st.pi_lam[1] = 0.0;
+    st.pi_lam_prev[0] = 0.0; st.pi_lam_prev[1] = 0.0;
+    st.pi_inv_norm[0] = 1.0; st.pi_inv_norm[1] = 1.0;
+    st.pi_iters = 0;
   }
 }
 
@@ -1153,30 +1196,40 @@ __global__ void k_fill_v(V* __restrict__ p, V v, long long N) {
   if (i < N) p[i] = v;
 }
 
-__global__ void k_set_norms(DevState* st, double nA, double nQ) {
-  st->normA = nA > 0.0 ? nA : sqrt(fmax(st->pi_lam[0], 0.0));
-  st->normQ = nQ > 0.0 ? nQ : fmax(st->pi_lam[1], 0.0);
-}
-
-// ||c~||, ||b~|| -> InitializePrimalWeight
-__global__ void k_sumsq2(const double* __restrict__ a, int na, const double* __restrict__ b, int nb,
-                         double* __restrict__ part) {
-  double f[2] = {0.0, 0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(na, nb); i += gridDim.x * blockDim.x) {
-    if (i < na) f[0] += a[i] * a[i];
-    if (i < nb) f[1] += b[i] * b[i];
+__global__ void k_set_norms(DevState* sts, int count, double nA, double nQ) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    DevState* st = sts + i;
+    st->normA = nA > 0.0 ? nA : sqrt(fmax(st->pi_lam[0], 0.0));
+    st->normQ = nQ > 0.0 ? nQ : fmax(st->pi_lam[1], 0.0);
   }
-  const bool is_max[2] = {false, false};
-  block_reduce<2>(f, is_max);
-  if (threadIdx.x == 0) { part[blockIdx.x * 32] = f[0]; part[blockIdx.x * 32 + 1] = f[1]; }
 }
 
-__global__ void k_init_omega(DevState* st, const double* __restrict__ part, int nblk, double eps_zero) {
+// |c~|^2 over each row block of P, |b~|^2 over each row block of A
+__global__ void k_omega_part(const int* __restrict__ blkP, int nblkP, const int* __restrict__ blkA,
+                             const double* __restrict__ cs, const double* __restrict__ bs,
+                             double* __restrict__ partP, double* __restrict__ partA) {
+  const bool isP = blockIdx.x < nblkP;
+  const int b = isP ? blockIdx.x : blockIdx.x - nblkP;
+  const int* blk = isP ? blkP : blkA;
+  const double* v = isP ? cs : bs;
+  double f = 0.0;
+  for (int r = blk[b] + threadIdx.x; r < blk[b + 1]; r += blockDim.x) f += v[r] * v[r];
+  f = block_sum(f);
+  if (threadIdx.x == 0) (isP ? partP : partA)[b] = f;
+}
+
+// ||c~||, ||b~|| of each instance -> InitializePrimalWeight (one CUDA block per instance)
+__global__ void k_init_omega(DevState* sts, const Inst* __restrict__ insts, const double* __restrict__ partP,
+                             const double* __restrict__ partA, double eps_zero) {
+  const int i = blockIdx.x;
+  const Inst in = insts[i];
   double f[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) { f[0] += part[b * 32]; f[1] += part[b * 32 + 1]; }
+  for (int b = in.bP0 + threadIdx.x; b < in.bP1; b += blockDim.x) f[0] += partP[b];
+  for (int b = in.bA0 + threadIdx.x; b < in.bA1; b += blockDim.x) f[1] += partA[b];
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   if (threadIdx.x == 0) {
+    DevState* st = sts + i;
     const double nc = sqrt(f[0]), nb = sqrt(f[1]);
     st->omega = (nc > eps_zero && nb > eps_zero) ? nc / nb : 1.0;
     st->eta_last = 0.0;
@@ -1188,7 +1241,7 @@ __global__ void k_init_omega(DevState* st, const double* __restrict__ part, int 
 // Start point: x = proj_X(x0 / D2), y = proj_Y(y0 / D1), zeros by default
 // (Section 5 "Algorithms"); averages, x_md, x_tilde and anchors = start.
 // --------------------------------------------------------------------------
-__global__ void k_init_iterates(int n, int m, int m_eq, const double* __restrict__ x0,
+__global__ void k_init_iterates(int n, int m, const unsigned char* __restrict__ ineq, const double* __restrict__ x0,
                                 const double* __restrict__ y0, const double* __restrict__ D1,
                                 const double* __restrict__ D2, const double* __restrict__ ls,
                                 const double* __restrict__ us, double* x, double* xbar, double* xmd0,
@@ -1201,7 +1254,7 @@ __global__ void k_init_iterates(int n, int m, int m_eq, const double* __restrict
   }
   if (i < m) {
     double v = y0 ? y0[i] / D1[i] : 0.0;
-    if (i >= m_eq) v = fmax(v, 0.0);
+    if (ineq[i]) v = fmax(v, 0.0);
     y[i] = v; ybar[i] = v; ay[i] = v;
   }
 }
@@ -1258,15 +1311,33 @@ __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const
 // mode 0: evaluate z^{0,0} (anchor, maybe already optimal); mode 1: a check
 // after `chunk_len` more iterations (Section 6 restart rule, termination
 // eq. (terminate), iteration limit).
-__global__ void __launch_bounds__(1024) k_decide(DevState* __restrict__ st, const double* __restrict__ pm,
-                                                 int nbm, const double* __restrict__ pn, int nbn,
-                                                 StepEntry* __restrict__ tab, SolveParams p, int mode,
-                                                 long long chunk_len) {
+// one CUDA block per instance
+__global__ void __launch_bounds__(512) k_decide(DevState* __restrict__ sts, const Inst* __restrict__ insts,
+                                                const double* __restrict__ pm, int nbm,
+                                                const double* __restrict__ pn, int nbn,
+                                                StepEntry* __restrict__ tabs, int C, SolveParams p, int mode,
+                                                long long chunk_len) {
+  const int i = blockIdx.x;
+  DevState* st = sts + i;
+  if (mode == 1 && st->status != ST_RUNNING) return;     // uniform
+  const Inst in = insts[i];
   __shared__ double F[24];
-  reduce_kkt_blocks(pm, nbm, pn, nbn, F);
+  reduce_kkt_blocks(pm, nbm, in.m > 0 ? in.bA0 : 0, in.m > 0 ? in.bA1 : 0, pn, nbn, in.bP0, in.bP1, F);
   if (threadIdx.x == 0) decide_thread0(st, F, p, mode, chunk_len);
   __syncthreads();
-  if (st->status == ST_RUNNING) fill_steps_block(*st, p, tab);
+  if (st->status == ST_RUNNING) fill_steps_block(*st, p, tabs + (size_t)i * C);
+}
+
+// number of instances still iterating / still estimating norms
+__global__ void k_count_running(const DevState* __restrict__ sts, int count, BatchState* bst) {
+  int run = 0, lz = 0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    run += sts[i].status == ST_RUNNING;
+    lz += !(sts[i].pi_done[0] && sts[i].pi_done[1]);
+  }
+  run = block_sum(run);
+  lz = block_sum(lz);
+  if (threadIdx.x == 0) { bst->running = run; bst->lz_running = lz; }
 }
 
 __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
@@ -1330,18 +1401,23 @@ __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const
 
 // Restart of the outer loop from the candidate: x = x_bar = x_md = x_tilde = x_c,
 // y = y_bar = y_c, anchors = z_c (Algorithm 1 "restart the outer loop").
-__global__ void k_restart_apply(const DevState* __restrict__ st, int n, int m, double* x, double* xbar,
+__global__ void k_restart_apply(const DevState* __restrict__ sts, const int* __restrict__ inst_n,
+                                const int* __restrict__ inst_m, int n, int m, double* x, double* xbar,
                                 double* xmd0, double* xt, double* ax, double* y, double* ybar, double* ay) {
-  if (st->status != ST_RUNNING || !st->restart) return;
-  const int ca = st->cand_avg;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
     if (i < n) {
-      const double v = ca ? xbar[i] : x[i];
-      x[i] = v; xbar[i] = v; xmd0[i] = v; xt[i] = v; ax[i] = v;
+      const DevState& s = sts[inst_n[i]];
+      if (s.status == ST_RUNNING && s.restart) {
+        const double v = s.cand_avg ? xbar[i] : x[i];
+        x[i] = v; xbar[i] = v; xmd0[i] = v; xt[i] = v; ax[i] = v;
+      }
     }
     if (i < m) {
-      const double v = ca ? ybar[i] : y[i];
-      y[i] = v; ybar[i] = v; ay[i] = v;
+      const DevState& s = sts[inst_m[i]];
+      if (s.status == ST_RUNNING && s.restart) {
+        const double v = s.cand_avg ? ybar[i] : y[i];
+        y[i] = v; ybar[i] = v; ay[i] = v;
+      }
     }
   }
 }
@@ -1350,13 +1426,17 @@ __global__ void k_restart_apply(const DevState* __restrict__ st, int n, int m, d
 __global__ void k_unscale_out(int n, int m, const double* __restrict__ D1, const double* __restrict__ D2,
                               const double* __restrict__ xs0, const double* __restrict__ xs1,
                               const double* __restrict__ ys0, const double* __restrict__ ys1,
-                              const DevState* __restrict__ st, int pick, double* x_out, double* y_out) {
-  const int sel = pick < 0 ? st->out_avg : pick;
-  const double* xs = sel ? xs1 : xs0;
-  const double* ys = sel ? ys1 : ys0;
+                              const DevState* __restrict__ sts, const int* __restrict__ inst_n,
+                              const int* __restrict__ inst_m, int pick, double* x_out, double* y_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x_out && i < n) x_out[i] = D2[i] * xs[i];
-  if (y_out && i < m) y_out[i] = D1[i] * ys[i];
+  if (x_out && i < n) {
+    const int sel = pick < 0 ? sts[inst_n[i]].out_avg : pick;
+    x_out[i] = D2[i] * (sel ? xs1[i] : xs0[i]);
+  }
+  if (y_out && i < m) {
+    const int sel = pick < 0 ? sts[inst_m[i]].out_avg : pick;
+    y_out[i] = D1[i] * (sel ? ys1[i] : ys0[i]);
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1369,7 +1449,10 @@ __global__ void k_unscale_out(int n, int m, const double* __restrict__ D1, const
 // residual correction).
 // --------------------------------------------------------------------------
 struct MixedArgs {
-  int n, m, m_eq;
+  int n, m;
+  const unsigned char* ineq;
+  const DevState* sts;
+  const int *inst_n, *inst_m;
   const double *cs, *bs, *ls, *us, *D1, *D2;
   double *xhi, *yhi;
   float *fx, *fxbar, *fxt, *fxmd0, *fy, *fybar;
@@ -1387,7 +1470,7 @@ __global__ void k_init_mixed(MixedArgs a, const double* __restrict__ x0, const d
   }
   if (i < a.m) {
     double v = y0 ? y0[i] / a.D1[i] : 0.0;
-    if (i >= a.m_eq) v = fmax(v, 0.0);
+    if (a.ineq[i]) v = fmax(v, 0.0);
     a.yhi[i] = v;
     a.fy[i] = 0.f; a.fybar[i] = 0.f;
   }
@@ -1403,7 +1486,7 @@ __global__ void k_materialize(MixedArgs a) {
     if (i < a.m) {
       const double h = a.yhi[i];
       double v0 = h + (double)a.fy[i], v1 = h + (double)a.fybar[i];
-      if (i >= a.m_eq) { v0 = fmax(v0, 0.0); v1 = fmax(v1, 0.0); }
+      if (a.ineq[i]) { v0 = fmax(v0, 0.0); v1 = fmax(v1, 0.0); }
       a.y64[0][i] = v0;
       a.y64[1][i] = v1;
     }
@@ -1412,24 +1495,30 @@ __global__ void k_materialize(MixedArgs a) {
 
 // Move the base to the candidate (or, with force, re-derive the shifted data
 // at the current base) and zero the float32 deltas.
-__global__ void k_mixed_rebase(MixedArgs a, const DevState* __restrict__ st, int force) {
-  if (!force && (st->status != ST_RUNNING || !st->restart)) return;
-  const int ca = force ? 0 : st->cand_avg;
+__global__ void k_mixed_rebase(MixedArgs a, int force) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(a.n, a.m); i += gridDim.x * blockDim.x) {
     if (i < a.n) {
-      const double xh = a.x64[ca][i];
-      a.xhi[i] = xh;
-      a.fc[i] = (float)(a.cs[i] + a.prodQx[(size_t)ca * a.n + i] - a.prodATy[(size_t)ca * a.n + i]);
-      a.fl[i] = (float)(a.ls[i] - xh);
-      a.fu[i] = (float)(a.us[i] - xh);
-      a.fx[i] = 0.f; a.fxbar[i] = 0.f; a.fxt[i] = 0.f; a.fxmd0[i] = 0.f;
+      const DevState& s = a.sts[a.inst_n[i]];
+      if (force || (s.status == ST_RUNNING && s.restart)) {
+        const int ca = force ? 0 : s.cand_avg;
+        const double xh = a.x64[ca][i];
+        a.xhi[i] = xh;
+        a.fc[i] = (float)(a.cs[i] + a.prodQx[(size_t)ca * a.n + i] - a.prodATy[(size_t)ca * a.n + i]);
+        a.fl[i] = (float)(a.ls[i] - xh);
+        a.fu[i] = (float)(a.us[i] - xh);
+        a.fx[i] = 0.f; a.fxbar[i] = 0.f; a.fxt[i] = 0.f; a.fxmd0[i] = 0.f;
+      }
     }
     if (i < a.m) {
-      const double yh = a.y64[ca][i];
-      a.yhi[i] = yh;
-      a.fb[i] = (float)(a.bs[i] - a.prodAx[(size_t)ca * a.m + i]);
-      a.fylo[i] = (float)(-yh);
-      a.fy[i] = 0.f; a.fybar[i] = 0.f;
+      const DevState& s = a.sts[a.inst_m[i]];
+      if (force || (s.status == ST_RUNNING && s.restart)) {
+        const int ca = force ? 0 : s.cand_avg;
+        const double yh = a.y64[ca][i];
+        a.yhi[i] = yh;
+        a.fb[i] = (float)(a.bs[i] - a.prodAx[(size_t)ca * a.m + i]);
+        a.fylo[i] = a.ineq[i] ? (float)(-yh) : -INFINITY;
+        a.fy[i] = 0.f; a.fybar[i] = 0.f;
+      }
     }
   }
 }
@@ -1462,11 +1551,19 @@ void scale_apply(Work& w, bool mixed, cudaStream_t s) {
          (float*)nullptr);
 }
 
+static LzArgs lz_args(Work& w) {
+  LzArgs la{};
+  la.n = w.n; la.m = w.m; la.count = w.count;
+  la.al = w.lz_al; la.be = w.lz_be; la.st = w.st; la.inst = w.inst;
+  la.blk_inst_P = w.blk_inst_P; la.blk_inst_A = w.blk_inst_A; la.row_inst_n = w.row_inst_n;
+  la.nblkP = w.P.nblk;
+  return la;
+}
+
 template <typename V>
 static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) {
-  LzArgs la{w.n, w.m, w.m > 0 ? 1 : 0, w.lz_al, w.lz_be, w.st};
-  const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
-  launch(k_lz_init<V>, grid, 256, 0, s, la, pu[0], pu[1], pz[0], pz[1]);
+  const int grid = std::min(cdiv(std::max(w.n, w.count), 256), 4 * w.num_sms);
+  launch(k_lz_init<V>, grid, 256, 0, s, lz_args(w), pu[0], pu[1], pz[0], pz[1]);
 }
 
 void lanczos_init(Work& w, bool mixed, cudaStream_t s) {
@@ -1478,16 +1575,15 @@ template <typename V, int NT>
 static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr<V> P, V* const* pu, V* const* pz,
                            V* const* lw, cudaStream_t s) {
   const int cur = t & 1, prv = cur ^ 1;
-  LzArgs la{w.n, w.m, w.m > 0 ? 1 : 0, w.lz_al, w.lz_be, w.st};
-  if (w.m > 0) launch(k_lz_m<V, NT>, w.A.nblk, NT, 0, s, A, (const V*)pu[cur], pz[cur] + w.n, (const DevState*)w.st);
-  launch(k_lz_n<V, NT>, w.P.nblk, NT, 0, s, P, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
-         (const DevState*)w.st, w.part_n, w.P.nblk, w.m > 0 ? 1 : 0);
-  launch(k_lz_alpha, 1, 1024, 0, s, la, (const double*)w.part_n, w.P.nblk);
-  const int grid = std::min(cdiv(w.n, 256), (int)PDQP_RED_BLOCKS);
-  launch(k_lz_orth<V>, grid, 256, 0, s, la, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
-         (const V*)pz[cur], pz[prv], w.part);
-  launch(k_lz_beta, 1, 1024, 0, s, la, (const double*)w.part, grid, p.norm_tol,
+  const LzArgs la = lz_args(w);
+  if (w.m > 0) launch(k_lz_m<V, NT>, w.A.nblk, NT, 0, s, A, la, (const V*)pu[cur], pz[cur] + w.n);
+  launch(k_lz_n<V, NT>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1], w.part_n);
+  launch(k_lz_alpha, w.count, 512, 0, s, la, (const double*)w.part_n);
+  launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
+         (const V*)pz[cur], pz[prv], w.part_n);
+  launch(k_lz_beta, w.count, 256, 0, s, la, (const double*)w.part_n, p.norm_tol,
          p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
+  const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
   launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
 }
 
@@ -1501,13 +1597,18 @@ void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t
   }
 }
 
+void count_running(Work& w, cudaStream_t s) {
+  launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, w.count, w.bst);
+}
+
 void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
-  launch(k_set_norms, 1, 1, 0, s, w.st, normA_opt, normQ_opt);
+  launch(k_set_norms, cdiv(w.count, 256), 256, 0, s, w.st, w.count, normA_opt, normQ_opt);
 }
 
 static MixedArgs mixed_args(Work& w) {
   MixedArgs a{};
-  a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
+  a.n = w.n; a.m = w.m;
+  a.ineq = w.row_ineq; a.sts = w.st; a.inst_n = w.row_inst_n; a.inst_m = w.row_inst_m;
   a.cs = w.cs; a.bs = w.bs; a.ls = w.ls; a.us = w.us; a.D1 = w.D1; a.D2 = w.D2;
   a.xhi = w.xhi; a.yhi = w.yhi;
   a.fx = w.fx; a.fxbar = w.fxbar; a.fxt = w.fxt; a.fxmd0 = w.fZ[0]; a.fy = w.fy; a.fybar = w.fybar;
@@ -1518,8 +1619,10 @@ static MixedArgs mixed_args(Work& w) {
 }
 
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s) {
-  launch(k_sumsq2, PDQP_RED_BLOCKS, 256, 0, s, (const double*)w.cs, w.n, (const double*)w.bs, w.m, w.part);
-  launch(k_init_omega, 1, 256, 0, s, w.st, (const double*)w.part, PDQP_RED_BLOCKS, p.eps_zero);
+  launch(k_omega_part, w.P.nblk + w.A.nblk, 256, 0, s, (const int*)w.P.blk, w.P.nblk, (const int*)w.A.blk,
+         (const double*)w.cs, (const double*)w.bs, w.part_n, w.part_m);
+  launch(k_init_omega, w.count, 512, 0, s, w.st, (const Inst*)w.inst, (const double*)w.part_n,
+         (const double*)w.part_m, p.eps_zero);
   const int N = w.n > w.m ? w.n : w.m;
   if (p.mixed) {
     w.fy = w.fZ[1] + w.n;
@@ -1528,7 +1631,8 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
     return;
   }
   w.y = w.Z[1] + w.n;
-  launch(k_init_iterates, cdiv(N, 256), 256, 0, s, w.n, w.m, w.m_eq, x0, y0, (const double*)w.D1,
+  launch(k_init_iterates, cdiv(N, 256), 256, 0, s, w.n, w.m, (const unsigned char*)w.row_ineq, x0, y0,
+         (const double*)w.D1,
          (const double*)w.D2, (const double*)w.ls, (const double*)w.us, w.x, w.xbar, w.Z[0], w.xt, w.ax, w.y,
          w.ybar, w.ay);
 }
@@ -1560,8 +1664,8 @@ template <typename V, int NT>
 static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
                            const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
-  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.m, w.m_eq};
-  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.n};
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride};
   const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
   const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
   const size_t smem = sizeof(PipeSmem<V>);
@@ -1585,8 +1689,8 @@ template <typename V, int NT>
 static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
                       const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
-  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.m, w.m_eq};
-  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.n};
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride};
   for (int j = 0; j < len; ++j) {
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
@@ -1645,7 +1749,10 @@ static KktB kkt_args(Work& w, bool scaled) {
   a.b = w.b; a.c = w.c; a.l = w.l; a.u = w.u;
   a.part_m = w.part_m; a.part_n = w.part_n;
   a.nblk_m = w.A.nblk; a.nblk_n = w.P.nblk;
-  a.n = w.n; a.m = w.m; a.m_eq = w.m_eq;
+  a.n = w.n; a.m = w.m;
+  a.ineq = w.row_ineq;
+  a.blk_inst_A = w.blk_inst_A; a.blk_inst_P = w.blk_inst_P;
+  a.st = w.st;
   return a;
 }
 
@@ -1668,14 +1775,15 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
   }
   if (w.m > 0) launch(k_kkt_m<2>, w.A.nblk, BNT, 0, s, a);
   launch(k_kkt_n<2>, w.P.nblk, BNT, 0, s, a);
-  launch(k_decide, 1, 1024, 0, s, w.st, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,
-         (const double*)w.part_n, w.P.nblk, w.tab, p, mode, chunk_len);
+  launch(k_decide, w.count, 512, 0, s, w.st, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
+         (const double*)w.part_n, w.P.nblk, w.tab, w.tab_stride, p, mode, chunk_len);
   if (mixed) {
-    launch(k_mixed_rebase, grid_v, 256, 0, s, mixed_args(w), (const DevState*)w.st, mode == 0 ? 1 : 0);
+    launch(k_mixed_rebase, grid_v, 256, 0, s, mixed_args(w), mode == 0 ? 1 : 0);
   } else if (mode == 1) {
-    launch(k_restart_apply, grid_v, 256, 0, s, (const DevState*)w.st, w.n, w.m, w.x, w.xbar, w.Z[0], w.xt, w.ax,
-           w.y, w.ybar, w.ay);
+    launch(k_restart_apply, grid_v, 256, 0, s, (const DevState*)w.st, (const int*)w.row_inst_n,
+           (const int*)w.row_inst_m, w.n, w.m, w.x, w.xbar, w.Z[0], w.xt, w.ax, w.y, w.ybar, w.ay);
   }
+  launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, w.count, w.bst);
   if (w.prof.on) w.prof.end(s);
 }
 
@@ -1683,24 +1791,24 @@ void write_output(Work& w, double* x_out, double* y_out, cudaStream_t s) {
   const int N = w.n > w.m ? w.n : w.m;
   launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
          (const double*)w.x, (const double*)w.xbar, (const double*)w.y, (const double*)w.ybar,
-         (const DevState*)w.st, -1, x_out, y_out);
+         (const DevState*)w.st, (const int*)w.row_inst_n, (const int*)w.row_inst_m, -1, x_out, y_out);
 }
 
 void write_state(Work& w, double* x, double* y, double* xbar, double* ybar, cudaStream_t s) {
   const int N = w.n > w.m ? w.n : w.m;
   launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
          (const double*)w.x, (const double*)w.xbar, (const double*)w.y, (const double*)w.ybar,
-         (const DevState*)w.st, 0, x, y);
+         (const DevState*)w.st, (const int*)w.row_inst_n, (const int*)w.row_inst_m, 0, x, y);
   launch(k_unscale_out, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
          (const double*)w.x, (const double*)w.xbar, (const double*)w.y, (const double*)w.ybar,
-         (const DevState*)w.st, 1, xbar, ybar);
+         (const DevState*)w.st, (const int*)w.row_inst_n, (const int*)w.row_inst_m, 1, xbar, ybar);
 }
 
 // relKKT of a user (x, y) on the original matrices (D = 1)
 __global__ void __launch_bounds__(1024) k_kkt_finish_user(const double* __restrict__ pm, int nbm,
                                                           const double* __restrict__ pn, int nbn, DevState* st) {
   __shared__ double F[24];
-  reduce_kkt_blocks(pm, nbm, pn, nbn, F);
+  reduce_kkt_blocks(pm, nbm, 0, nbm, pn, nbn, 0, nbn, F);
   if (threadIdx.x == 0) kkt_from_fields(F, 0, st->out_parts);
 }
 
@@ -1708,6 +1816,7 @@ void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
   KktB a = kkt_args(w, false);
   a.x[0] = x; a.x[1] = x; a.y[0] = y; a.y[1] = y;
   a.ax = nullptr; a.ay = nullptr;
+  a.st = nullptr;
   if (w.m > 0) launch(k_kkt_m<1>, w.A.nblk, BNT, 0, s, a);
   launch(k_kkt_n<1>, w.P.nblk, BNT, 0, s, a);
   launch(k_kkt_finish_user, 1, 1024, 0, s, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,

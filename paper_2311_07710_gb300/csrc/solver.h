@@ -61,8 +61,19 @@ struct Profiler {
 };
 
 struct Work {
-  int n = 0, m = 0, m_eq = 0;
+  int n = 0, m = 0, m_eq = 0;   // totals over the batch (m_eq: single-instance value)
+  int count = 1;                // instances stacked block-diagonally
   int num_sms = 152;
+  Inst* inst = nullptr;             // [count]
+  std::vector<Inst> inst_host;
+  int* blk_inst_P = nullptr;        // [P.nblk] instance of every row block
+  int* blk_inst_A = nullptr;        // [A.nblk]
+  int* row_inst_n = nullptr;        // [n] instance of every variable
+  int* row_inst_m = nullptr;        // [m] instance of every row
+  unsigned char* row_ineq = nullptr;   // [m] 1 for an inequality row
+  BatchState* bst = nullptr;
+  BatchState* bst_host = nullptr;   // pinned mirror
+  int tab_stride = 0;               // entries per instance in tab (the check period)
   DCsr P, A;   // P = [Q | -A'] (n rows, columns n+i for the A' part), A (m rows)
   double *c = nullptr, *b = nullptr, *l = nullptr, *u = nullptr;        // original data
   double *cs = nullptr, *bs = nullptr, *ls = nullptr, *us = nullptr;    // scaled data
@@ -94,14 +105,14 @@ struct Work {
   float *fpu[2] = {nullptr, nullptr}, *fpz[2] = {nullptr, nullptr};
   double *lw[2] = {nullptr, nullptr};    // Lanczos products A~'A~v and Q~v [n]
   float *flw[2] = {nullptr, nullptr};
-  double *lz_al = nullptr, *lz_be = nullptr;   // [2][512] Lanczos coefficients
+  double *lz_al = nullptr, *lz_be = nullptr;   // [count][2][512] Lanczos coefficients
   // reductions
   double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
   double *part_m = nullptr;  // [9][A.nblk]  field-major partial sums of the row-block kernels
   double *part_n = nullptr;  // [15][P.nblk]
-  StepEntry* tab = nullptr;  // [PDQP_MAX_CHECK]
-  DevState* st = nullptr;
-  DevState* st_host = nullptr;   // pinned mirror
+  StepEntry* tab = nullptr;  // [count][tab_stride]
+  DevState* st = nullptr;    // [count]
+  DevState* st_host = nullptr;   // pinned mirror [count]
   // user-vector staging (float64)
   double *stage_n = nullptr, *stage_m = nullptr;
   Profiler prof;
@@ -118,6 +129,7 @@ void scale_apply(Work& w, bool mixed, cudaStream_t s);
 void lanczos_init(Work& w, bool mixed, cudaStream_t s);
 void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s);
 void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
+void count_running(Work& w, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 
 // iteration

@@ -84,6 +84,10 @@ SIGNATURES = {
     "pdqp_launch_count": (ctypes.c_int64, []),
     "pdqp_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "pdqp_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_profile)]),
+    "pdqp_create_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int64)] * 3
+                          + [ctypes.POINTER(_P)] * 10 + [ctypes.c_int32, _P]),
+    "pdqp_batch_count": (ctypes.c_int32, [_P]),
+    "pdqp_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_info), ctypes.c_int32]),
     "pdqp_kkt_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                         ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
                                         _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -247,6 +251,42 @@ def pdqp_kkt(h, x, y, stream=None):
     return list(parts)
 
 
+def pdqp_create_batch(instances, stream=None):
+    """One handle for a list of problems; each entry is a tuple
+    (n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, l, u)."""
+    count = len(instances)
+    keep = []
+    cols = [[] for _ in range(10)]
+    dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 4
+    spaces = []
+    for inst in instances:
+        for k, (arr, t) in enumerate(zip(inst[3:], dtypes)):
+            ptr, ka, sp_ = _ptr(arr, t)
+            keep.append(ka)
+            cols[k].append(ptr)
+            spaces.append(sp_)
+    mem = _one_space(spaces)
+    I64 = ctypes.c_int64 * count
+    ns, ms, meqs = I64(*[int(i[0]) for i in instances]), I64(*[int(i[1]) for i in instances]), \
+        I64(*[int(i[2]) for i in instances])
+    ptr_arrays = [(ctypes.c_void_p * count)(*c) for c in cols]
+    h = ctypes.c_void_p()
+    st = load().pdqp_create_batch(ctypes.byref(h), count, ns, ms, meqs, *ptr_arrays, mem, _stream(stream))
+    _check(st, None)
+    return h
+
+
+def pdqp_batch_count(h) -> int:
+    return int(load().pdqp_batch_count(h))
+
+
+def pdqp_batch_info(h):
+    count = pdqp_batch_count(h)
+    infos = (pdqp_info * count)()
+    _check(load().pdqp_batch_info(h, infos, count), h)
+    return list(infos)
+
+
 def pdqp_kkt_noalloc(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, At_rowptr, At_col, At_val,
                      c, b, l, u, x, y, parts, stream=None):
     """Allocation-free relKKT of (x, y): every array is a torch CUDA tensor
@@ -302,6 +342,23 @@ def pdqp_profile_read(h) -> dict:
 # ---------------------------------------------------------------------------
 # convenience: a handle from scipy CSR data (marshalling only)
 # ---------------------------------------------------------------------------
+def batch_from_instances(insts, device=False, stream=None):
+    """A batch handle from objects with n, m, m_eq, Q, A (scipy CSR), c, b, l, u."""
+    entries = []
+    for it in insts:
+        arrays = [it.Q.indptr, it.Q.indices, it.Q.data, it.A.indptr, it.A.indices, it.A.data, it.c, it.b, it.l, it.u]
+        dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 4
+        arrays = [np.ascontiguousarray(a, dtype=t) for a, t in zip(arrays, dtypes)]
+        if device:
+            import torch
+            arrays = [torch.from_numpy(a).cuda() for a in arrays]
+        entries.append((it.n, it.m, it.m_eq, *arrays))
+    if device:
+        import torch
+        torch.cuda.synchronize()
+    return pdqp_create_batch(entries, stream=stream)
+
+
 def create_from_csr(n, m, m_eq, Q, A, c, b, l, u, device=False, stream=None):
     """Q, A: scipy.sparse CSR (int32 indices).  device=True uploads the arrays
     as torch CUDA tensors first, exercising the PDQP_MEM_DEVICE path."""

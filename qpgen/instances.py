@@ -224,19 +224,19 @@ def mpc_qp(seed: int, T: Optional[int] = None, T_range=(10, 100), name: str = "m
             break
     n = NX * (T + 1) + NU * T
     m = NX * (T + 1)
-    xo = lambda t: NX * t            # offset of x_t
-    uo = lambda t: NX * (T + 1) + NU * t  # offset of u_t
-    r_, c_, v_ = [], [], []
-    for i in range(NX):
-        r_.append(i); c_.append(xo(0) + i); v_.append(1.0)
-    for t in range(T):
-        for i in range(NX):
-            row = NX * (t + 1) + i
-            r_.append(row); c_.append(xo(t + 1) + i); v_.append(1.0)
-            for k in range(NX):
-                r_.append(row); c_.append(xo(t) + k); v_.append(-Ad[i, k])
-            for k in range(NU):
-                r_.append(row); c_.append(uo(t) + k); v_.append(-Bd[i, k])
+    # rows 0..11: x_0 = x_init; rows 12(t+1)+i: x_{t+1,i} - A_d[i,:] x_t - B_d[i,:] u_t = 0
+    t = np.arange(T)[:, None, None]
+    i = np.arange(NX)[None, :, None]
+    row = NX * (t + 1) + i                                   # T x 12 x 1
+    cols = np.concatenate([np.broadcast_to(NX * (t + 1) + i, (T, NX, 1)),
+                           np.broadcast_to(NX * t + np.arange(NX)[None, None, :], (T, NX, NX)),
+                           np.broadcast_to(NX * (T + 1) + NU * t + np.arange(NU)[None, None, :], (T, NX, NU))],
+                          axis=2)
+    vals = np.concatenate([np.ones((T, NX, 1)), np.broadcast_to(-Ad[None], (T, NX, NX)),
+                           np.broadcast_to(-Bd[None], (T, NX, NU))], axis=2)
+    r_ = np.concatenate([np.arange(NX), np.broadcast_to(row, cols.shape).ravel()])
+    c_ = np.concatenate([np.arange(NX), cols.ravel()])
+    v_ = np.concatenate([np.ones(NX), vals.ravel()])
     A = sp.coo_matrix((v_, (r_, c_)), shape=(m, n))
     b = np.zeros(m)
     b[:NX] = x_init

@@ -1,0 +1,103 @@
+"""Batched solves: many problems of uneven sizes stacked block-diagonally in
+one handle, each with its own step sizes, restarts and termination.
+
+Each instance's row blocks, sums and reductions are those of a standalone
+solve, so the batch reproduces the standalone solves bit for bit; the batch is
+also held to the oracle's end-state bar (relKKT <= 1e-6, objective within
+1e-6) per instance."""
+import numpy as np
+import pytest
+
+import qpgen
+from oracle import rapdhg as R
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pdqp():
+    return G.lib()
+
+
+def _mixed_bag():
+    return [qpgen.tiny_qp(40 + k, n=5 + 7 * k, m=3 + 5 * k, m_eq=k, bounds=("box", "mixed", "lower")[k % 3],
+                          density=0.5) for k in range(6)] + [qpgen.diagonal_box_qp(99, 17), qpgen.random_sparse_qp()]
+
+
+def _solve_batch(pdqp, insts, **opts):
+    h = pdqp.batch_from_instances(insts)
+    try:
+        N, M = sum(i.n for i in insts), sum(i.m for i in insts)
+        x, y = np.zeros(N), np.zeros(M)
+        st, info = pdqp.pdqp_solve(h, pdqp.pdqp_default_options(**opts), x_out=x, y_out=y)
+        infos = pdqp.pdqp_batch_info(h)
+    finally:
+        pdqp.pdqp_destroy(h)
+    xs, ys, ox, oy = [], [], 0, 0
+    for i in insts:
+        xs.append(x[ox:ox + i.n]); ys.append(y[oy:oy + i.m])
+        ox += i.n; oy += i.m
+    return st, infos, xs, ys
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_batch_reproduces_standalone_solves(pdqp, precision):
+    insts = _mixed_bag()
+    st, infos, xs, ys = _solve_batch(pdqp, insts, precision=precision)
+    assert st == pdqp.PDQP_OK
+    for k, inst in enumerate(insts):
+        s1, info1, x1, y1 = G.solve(inst, precision=precision)
+        assert infos[k].status == s1 and infos[k].iterations == info1.iterations, k
+        np.testing.assert_array_equal(xs[k], x1)
+        np.testing.assert_array_equal(ys[k], y1)
+
+
+def test_batch_meets_oracle_per_instance(pdqp):
+    insts = _mixed_bag()
+    st, infos, xs, ys = _solve_batch(pdqp, insts, precision=1)
+    for k, inst in enumerate(insts):
+        p = R.problem_from_instance(inst)
+        parts = R.kkt_parts(p, xs[k], ys[k])
+        ref = R.solve(inst, R.Options())
+        assert parts["rel_kkt"] <= 1.0001e-6, (k, parts)
+        obj = ref.kkt["primal_obj"]
+        assert abs(parts["primal_obj"] - obj) <= 1e-6 * (1 + abs(obj)), k
+
+
+def test_batch_of_mpc_instances(pdqp):
+    """Control-shaped QPs of horizons 10..100 in one batch, mixed precision."""
+    insts = qpgen.mpc_batch(24, T_range=(10, 100))
+    st, infos, xs, ys = _solve_batch(pdqp, insts, precision=1)
+    assert st == pdqp.PDQP_OK
+    for k, inst in enumerate(insts):
+        parts = R.kkt_parts(R.problem_from_instance(inst), xs[k], ys[k])
+        assert parts["rel_kkt"] <= 1.0001e-6, k
+        assert infos[k].iterations > 0
+
+
+def test_batch_iterates_match_oracle(pdqp):
+    """Float64 batch iterates after 100 iterations, instance by instance."""
+    insts = _mixed_bag()[:4]
+    refs = [R.solve(i, R.Options(max_iter=100, eps=0.0), trace_at=(100,)) for i in insts]
+    h = pdqp.batch_from_instances(insts)
+    try:
+        # one shared norm pair is not what the oracle used: give each instance's
+        # norms by solving with the oracle's norms instance-wise is impossible in
+        # one call, so compare against the oracle run with the batch's own norms
+        pdqp.pdqp_solve(h, pdqp.pdqp_default_options(max_iter=100, eps=0.0))
+        infos = pdqp.pdqp_batch_info(h)
+        N, M = sum(i.n for i in insts), sum(i.m for i in insts)
+        out = [np.zeros(N), np.zeros(M), np.zeros(N), np.zeros(M)]
+        pdqp.pdqp_get_state(h, *out)
+    finally:
+        pdqp.pdqp_destroy(h)
+    ox = oy = 0
+    for k, inst in enumerate(insts):
+        ref = R.solve(inst, R.Options(max_iter=100, eps=0.0, norm_A=infos[k].norm_A, norm_Q=infos[k].norm_Q),
+                      trace_at=(100,)).trace[100]
+        for key, v, off, ln in (("x", out[0], ox, inst.n), ("y", out[1], oy, inst.m),
+                                ("xbar", out[2], ox, inst.n), ("ybar", out[3], oy, inst.m)):
+            assert G.rel_err(v[off:off + ln], ref[key]) <= 1e-10, (k, key)
+        assert infos[k].norm_A == pytest.approx(refs[k].norm_A, rel=1e-6) or inst.m == 0
+        ox += inst.n; oy += inst.m
