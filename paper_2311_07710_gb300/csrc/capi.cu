@@ -685,10 +685,37 @@ pdqp_status pdqp_create_batch(pdqp_handle* out, int32_t count, const int64_t* n,
 }
 
 pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t mem, void* stream) {
-  (void)r; (void)F; (void)mem; (void)stream;
   if (!h) return PDQP_ERR_INVALID;
-  h->err = "low-rank Q is not available in this build";
-  return PDQP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  Work& w = h->w;
+  try {
+    if (r < 1 || r > 256) throw Fail{PDQP_ERR_INVALID, "low-rank: need 1 <= r <= 256"};
+    if (!F) throw Fail{PDQP_ERR_INVALID, "low-rank: null F"};
+    if (w.count != 1) throw Fail{PDQP_ERR_INVALID, "low-rank: only for single-problem handles"};
+    if (w.r != 0) throw Fail{PDQP_ERR_INVALID, "low-rank: already set"};
+    check_space(F, mem, "F");
+    const size_t N = (size_t)w.n * r;
+    std::vector<float> hf = fetch(F, N, mem, s);
+    for (float v : hf)
+      if (!std::isfinite(v)) throw Fail{PDQP_ERR_INVALID, "low-rank: non-finite entry of F"};
+    std::vector<double> hd(hf.begin(), hf.end());
+    w.F = dalloc<float>(h, N);
+    w.Fo = dalloc<double>(h, N);
+    w.Fs = dalloc<float>(h, N);
+    w.Fd = dalloc<double>(h, N);
+    w.wlr = dalloc<double>(h, 2 * (size_t)r);
+    w.lr_part = dalloc<double>(h, (size_t)((w.n + 1023) / 1024) * 2 * r);
+    to_device(w.F, hf.data(), N, s);
+    to_device(w.Fo, hd.data(), N, s);
+    CK(cudaStreamSynchronize(s));
+    w.r = r;
+    if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
+    h->graph.valid = false;
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    h->err = f.msg;
+    return f.st;
+  }
 }
 
 pdqp_status pdqp_solve(pdqp_handle h, const pdqp_options* opt, const double* x0, const double* y0, double* x_out,

@@ -278,6 +278,76 @@ __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __rest
 template <int NT> struct MinBlocks { static constexpr int value = 4; };
 template <> struct MinBlocks<512> { static constexpr int value = 4; };
 
+
+// ==========================================================================
+// Low-rank term of Q: Q_total = Q + F F' with F (n x r, row-major) applied as
+// F (F' v) and never formed.  w = F~' v is a two-stage reduction (row tiles
+// then one reduce); the row term F~_j . w is added where Q v appears.
+// ==========================================================================
+constexpr int LR_ROWS = 1024;   // rows per tile of the F' v reduction
+
+// F~ = D2 F (float64 and float32 copies)
+__global__ void k_lr_scale(const float* __restrict__ F, const double* __restrict__ D2, int n, int r,
+                           double* __restrict__ Fd, float* __restrict__ Ff) {
+  const long long N = (long long)n * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    const double v = D2[e / r] * (double)F[e];
+    Fd[e] = v;
+    if (Ff) Ff[e] = (float)v;
+  }
+}
+
+// partial F~' v over a tile of rows for NV vectors v (thread (g, k): column k,
+// rows of the tile with index = g mod G); part[tile][vec][k]
+template <typename FV, typename X, int NV>
+__global__ void k_lr_ft(const FV* __restrict__ F, int n, int r, const X* __restrict__ v0, const X* __restrict__ v1,
+                        double* __restrict__ part) {
+  const int G = blockDim.x / r;
+  const int g = threadIdx.x / r, kk = threadIdx.x % r;
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  const int j0 = blockIdx.x * LR_ROWS, j1 = min(n, j0 + LR_ROWS);
+  if (g < G) {
+    for (int j = j0 + g; j < j1; j += G) {
+      const double f = (double)F[(size_t)j * r + kk];
+      acc[0] += f * (double)v0[j];
+      if (NV > 1) acc[NV - 1] += f * (double)v1[j];
+    }
+  }
+  __shared__ double sh[2][256];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < r) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int gg = 0; gg < G; ++gg) s += sh[q][gg * r + threadIdx.x];
+      part[((size_t)blockIdx.x * NV + q) * r + threadIdx.x] = s;
+    }
+  }
+}
+
+// w[vec][k] = sum over tiles
+__global__ void k_lr_reduce(const double* __restrict__ part, int ntiles, int r, int nv, double* __restrict__ w) {
+  const int t = threadIdx.x;
+  if (t >= r * nv) return;
+  const int q = t / r, kk = t % r;
+  double s = 0.0;
+  for (int b = 0; b < ntiles; ++b) s += part[((size_t)b * nv + q) * r + kk];
+  w[q * r + kk] = s;
+}
+
+// the row term F~_j . w
+template <typename FV, typename V>
+__device__ __forceinline__ V lr_row(const FV* __restrict__ F, const double* __restrict__ w, int r, int j) {
+  V s = V(0);
+  const FV* f = F + (size_t)j * r;
+  for (int kk = 0; kk < r; ++kk) s += (V)f[kk] * (V)w[kk];
+  return s;
+}
+
 // --------------------------------------------------------------------------
 // One inner iteration of Algorithm 1: the dual half-step (rows of A)
 // --------------------------------------------------------------------------
@@ -381,13 +451,16 @@ struct PrimalB {
   const int* __restrict__ blk_inst;
   const DevState* __restrict__ st;
   int C;
+  const V* __restrict__ F;              // low-rank factor F~ (null: none)
+  const double* __restrict__ wlr;       // F~' x_md of this iteration
+  int r;
 };
 
 template <typename V>
 __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry& e, int r, V s, V xo, V xb0,
                                            V cr, V lr, V ur) {
   const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
-  const V g = s + cr;
+  const V g = s + cr + (a.F ? lr_row<V, V>(a.F, a.wlr, a.r, r) : V(0));
   const V xn = fmin(fmax(xo - tau * g, lr), ur);
   const V xb = (V(1) - ib) * xb0 + ib * xn;
   a.xbar[r] = xb;
@@ -607,6 +680,9 @@ struct KktB {
   const int* blk_inst_A;                // instance of each row block (null: no status test)
   const int* blk_inst_P;
   const DevState* st;
+  const double* F;                      // low-rank factor F~ (null: none)
+  const double* wlr;                    // [2][r]: F~' x per iterate
+  int r;
 };
 
 template <int NIT>
@@ -707,8 +783,9 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
     const bool lf = isfinite(lj), uf = isfinite(uj);
 #pragma unroll
     for (int it = 0; it < NIT; ++it) {
-      if (a.prodQx[it]) { a.prodQx[it][r] = sq[it]; a.prodATy[it][r] = -sa[it]; }
-      const double Qx = sq[it] * id2, ATy = -sa[it] * id2;
+      const double sqt = sq[it] + (a.F ? lr_row<double, double>(a.F, a.wlr + it * a.r, a.r, r) : 0.0);
+      if (a.prodQx[it]) { a.prodQx[it][r] = sqt; a.prodATy[it][r] = -sa[it]; }
+      const double Qx = sqt * id2, ATy = -sa[it] * id2;
       const double xt = a.x[it][r];
       const double xj = d2 * xt;
       const double g = Qx + cj - ATy;
@@ -981,7 +1058,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, Lz
 template <typename V, int NT>
 __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, LzArgs la, const V* __restrict__ zin,
                                                                    const V* __restrict__ vA, V* __restrict__ wA,
-                                                                   V* __restrict__ wQ, double* __restrict__ part) {
+                                                                   V* __restrict__ wQ, double* __restrict__ part,
+                                                                   const V* __restrict__ F,
+                                                                   const double* __restrict__ wlr, int rk) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
@@ -997,7 +1076,11 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, Lz
   const int ne = P.rp[r1] - e0;
   auto row = [&](int r, V sQ, V sA) {
     if (doA) { const V u = -sA; wA[r] = u; f[0] += (double)vA[r] * (double)u; }
-    if (doQ) { wQ[r] = sQ; f[1] += (double)zin[r] * (double)sQ; }
+    if (doQ) {
+      if (F) sQ += lr_row<V, V>(F, wlr, rk, r);
+      wQ[r] = sQ;
+      f[1] += (double)zin[r] * (double)sQ;
+    }
   };
   if (ne <= BNNZ) {
     stage_products<NT>(P, zin, e0, ne, r0, nr, prod, srp);
@@ -1546,9 +1629,21 @@ void scale_apply(Work& w, bool mixed, cudaStream_t s) {
   launch(k_scale_vals, w.A.nblk, BNT, 0, s, w.A.borig(), (const double*)w.dsc, w.n, 0, w.A.sval,
          mixed ? w.A.sval_f : (float*)nullptr);
   const int NN = w.n > w.m ? w.n : w.m;
+  if (w.r > 0)
+    launch(k_lr_scale, std::min(cdiv((long long)w.n * w.r, 256), 8 * w.num_sms), 256, 0, s, (const float*)w.F,
+           (const double*)w.D2, w.n, w.r, w.Fd, mixed ? w.Fs : (float*)nullptr);
   launch(k_scale_vectors, cdiv(NN, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
          (const double*)w.c, (const double*)w.b, (const double*)w.l, (const double*)w.u, w.cs, w.bs, w.ls, w.us,
          (float*)nullptr);
+}
+
+// w = F' v (nv = 1) or F' [v0, v1] (nv = 2) into w.wlr
+template <typename FV, typename X>
+static void lowrank_ft(Work& w, const FV* F, const X* v0, const X* v1, cudaStream_t s) {
+  const int tiles = cdiv(w.n, LR_ROWS);
+  if (v1) launch(k_lr_ft<FV, X, 2>, tiles, 256, 0, s, F, w.n, w.r, v0, v1, w.lr_part);
+  else launch(k_lr_ft<FV, X, 1>, tiles, 256, 0, s, F, w.n, w.r, v0, v1, w.lr_part);
+  launch(k_lr_reduce, 1, 512, 0, s, (const double*)w.lr_part, tiles, w.r, v1 ? 2 : 1, w.wlr);
 }
 
 static LzArgs lz_args(Work& w) {
@@ -1559,6 +1654,10 @@ static LzArgs lz_args(Work& w) {
   la.nblkP = w.P.nblk;
   return la;
 }
+
+template <typename V> static const V* lr_factor(Work& w);
+template <> const double* lr_factor<double>(Work& w) { return w.Fd; }
+template <> const float* lr_factor<float>(Work& w) { return w.Fs; }
 
 template <typename V>
 static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) {
@@ -1577,7 +1676,13 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   const int cur = t & 1, prv = cur ^ 1;
   const LzArgs la = lz_args(w);
   if (w.m > 0) launch(k_lz_m<V, NT>, w.A.nblk, NT, 0, s, A, la, (const V*)pu[cur], pz[cur] + w.n);
-  launch(k_lz_n<V, NT>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1], w.part_n);
+  const V* F = nullptr;
+  if (w.r > 0) {
+    F = lr_factor<V>(w);
+    lowrank_ft<V, V>(w, F, (const V*)pz[cur], (const V*)nullptr, s);
+  }
+  launch(k_lz_n<V, NT>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1], w.part_n, F,
+         (const double*)w.wlr, w.r);
   launch(k_lz_alpha, w.count, 512, 0, s, la, (const double*)w.part_n);
   launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
          (const V*)pz[cur], pz[prv], w.part_n);
@@ -1665,11 +1770,13 @@ static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* con
                            const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
-  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
+                w.r > 0 ? lr_factor<V>(w) : nullptr, w.wlr, w.r};
   const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
   const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
   const size_t smem = sizeof(PipeSmem<V>);
   for (int j = 0; j < len; ++j) {
+    if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
@@ -1690,8 +1797,10 @@ static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z
                       const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
-  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
+                w.r > 0 ? lr_factor<V>(w) : nullptr, w.wlr, w.r};
   for (int j = 0; j < len; ++j) {
+    if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
@@ -1773,6 +1882,10 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
       a.prodATy[it] = w.prodATy + (size_t)it * w.n;
     }
   }
+  if (w.r > 0) {
+    lowrank_ft<double, double>(w, w.Fd, a.x[0], a.x[1], s);
+    a.F = w.Fd; a.wlr = w.wlr; a.r = w.r;
+  }
   if (w.m > 0) launch(k_kkt_m<2>, w.A.nblk, BNT, 0, s, a);
   launch(k_kkt_n<2>, w.P.nblk, BNT, 0, s, a);
   launch(k_decide, w.count, 512, 0, s, w.st, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
@@ -1817,6 +1930,10 @@ void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
   a.x[0] = x; a.x[1] = x; a.y[0] = y; a.y[1] = y;
   a.ax = nullptr; a.ay = nullptr;
   a.st = nullptr;
+  if (w.r > 0) {
+    lowrank_ft<double, double>(w, w.Fo, x, (const double*)nullptr, s);
+    a.F = w.Fo; a.wlr = w.wlr; a.r = w.r;
+  }
   if (w.m > 0) launch(k_kkt_m<1>, w.A.nblk, BNT, 0, s, a);
   launch(k_kkt_n<1>, w.P.nblk, BNT, 0, s, a);
   launch(k_kkt_finish_user, 1, 1024, 0, s, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,

@@ -94,12 +94,14 @@ struct Work {
   float *fc = nullptr, *fb = nullptr, *fl = nullptr, *fu = nullptr, *fylo = nullptr;  // shifted data
   double *xhi = nullptr, *yhi = nullptr;
   double *prodAx = nullptr, *prodQx = nullptr, *prodATy = nullptr;      // [2][m], [2][n], [2][n]
-  // low-rank factor (Q_total = Q + F F'), float32 row-major n x r
+  // low-rank factor (Q_total = Q + F F'), row-major n x r
   int r = 0;
-  float* F = nullptr;        // original
-  float* Fs = nullptr;       // row-scaled by D2
-  double* Fd = nullptr;      // float64 copy of Fs (for the float64 paths)
-  double* wlr = nullptr;     // [2][r] F'x partial buffers
+  float* F = nullptr;        // original, float32
+  double* Fo = nullptr;      // original, float64
+  float* Fs = nullptr;       // D2 F, float32
+  double* Fd = nullptr;      // D2 F, float64
+  double* wlr = nullptr;     // [2][r] F~' v of the current products
+  double* lr_part = nullptr; // [tiles][2][r] partial sums
   // Lanczos vectors: pu[p] (n) for A~'A~, pz[p] = [v_Q ; A~v_A] (n+m) the P input
   double *pu[2] = {nullptr, nullptr}, *pz[2] = {nullptr, nullptr};
   float *fpu[2] = {nullptr, nullptr}, *fpz[2] = {nullptr, nullptr};

@@ -19,8 +19,11 @@ def lib():
 
 def handle(inst, device=False):
     from paper_2311_07710_gb300 import pdqp
-    return pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
-                                device=device)
+    h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
+                             device=device)
+    if getattr(inst, "F", None) is not None:
+        pdqp.pdqp_set_lowrank_Q(h, inst.F.shape[1], np.ascontiguousarray(inst.F, dtype=np.float32))
+    return h
 
 
 def solve(inst, device=False, x0=None, y0=None, **opts):
