@@ -55,6 +55,12 @@ class pdqp_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4), ("bytes", ctypes.c_double * 4)]
 
 
+class pdqp_ws_train_options(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
 class PdqpError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{status_string(status)} ({status}): {msg}")
@@ -91,6 +97,26 @@ SIGNATURES = {
     "pdqp_kkt_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
                                         ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int64,
                                         _P, _P, _P, _P, _P, _P, _P, _P]),
+    # include/pdqp_ws.h
+    "pdqp_ws_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
+    "pdqp_ws_destroy": (None, [_P]),
+    "pdqp_ws_last_error": (ctypes.c_char_p, [_P]),
+    "pdqp_ws_set_params": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_ws_get_params": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_ws_set_normalization": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_ws_get_normalization": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_ws_fit": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
+    "pdqp_ws_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.c_int32, _P]),
+    "pdqp_ws_train": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_ws_train_options), _P, _P, _P, _P, ctypes.c_int64,
+                                     _P, ctypes.c_int32, _P]),
+    "pdqp_ws_infer": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_gemm_bf16": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                      ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
+                                      ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P]),
+    "pdqp_gemm_bf16_check": (ctypes.c_int, [_P]),
+    "pdqp_gemm_bf16_splits": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
 }
 
 
@@ -370,3 +396,116 @@ def create_from_csr(n, m, m_eq, Q, A, c, b, l, u, device=False, stream=None):
         arrays = [torch.from_numpy(a).cuda() for a in arrays]
         torch.cuda.synchronize()
     return pdqp_create(n, m, m_eq, *arrays, stream=stream)
+
+
+# ---------------------------------------------------------------------------
+# learned warm start (include/pdqp_ws.h)
+# ---------------------------------------------------------------------------
+def _ws_check(status, w=None):
+    if status != PDQP_OK:
+        raise PdqpError(status, load().pdqp_ws_last_error(w).decode())
+    return status
+
+
+def _ws_arrays(arrays, dtype):
+    args = [_ptr(a, dtype) for a in arrays]
+    return [a[0] for a in args], [a[1] for a in args], _one_space([a[2] for a in args])
+
+
+def pdqp_ws_create(n, m, d=1024, width=1024, depth=3, max_batch=512, stream=None):
+    w = ctypes.c_void_p()
+    _ws_check(load().pdqp_ws_create(ctypes.byref(w), int(n), int(m), int(d), int(width), int(depth),
+                                    int(max_batch), _stream(stream)), None)
+    return w
+
+
+def pdqp_ws_destroy(w):
+    load().pdqp_ws_destroy(w)
+
+
+def pdqp_ws_set_params(w, layer, W, b=None, stream=None):
+    ptrs, keep, mem = _ws_arrays([W, b], np.float32)
+    return _ws_check(load().pdqp_ws_set_params(w, int(layer), ptrs[0], ptrs[1], mem, _stream(stream)), w)
+
+
+def pdqp_ws_get_params(w, layer, what=0, W=None, b=None, stream=None):
+    """Fill W and/or b (float32 numpy arrays or torch CUDA tensors) in place."""
+    for a in (W, b):
+        if a is not None and not _is_torch_cuda(a):
+            assert isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous
+    ptrs, keep, mem = _ws_arrays([W, b], np.float32)
+    return _ws_check(load().pdqp_ws_get_params(w, int(layer), int(what), ptrs[0], ptrs[1], mem, _stream(stream)), w)
+
+
+def pdqp_ws_set_normalization(w, in_mean, in_scale, out_mean, out_std, out_inv, stream=None):
+    ptrs, keep, mem = _ws_arrays([in_mean, in_scale, out_mean, out_std, out_inv], np.float32)
+    return _ws_check(load().pdqp_ws_set_normalization(w, *ptrs, mem, _stream(stream)), w)
+
+
+def pdqp_ws_get_normalization(w, F, stream=None):
+    out = [np.zeros(F, np.float32) for _ in range(5)]
+    ptrs = [ctypes.c_void_p(a.ctypes.data) for a in out]
+    _ws_check(load().pdqp_ws_get_normalization(w, *ptrs, PDQP_MEM_HOST, _stream(stream)), w)
+    return dict(zip(("in_mean", "in_scale", "out_mean", "out_std", "out_inv"), out))
+
+
+def pdqp_ws_fit(w, C, B, X, Y, stream=None):
+    ptrs, keep, mem = _ws_arrays([C, B, X, Y], np.float64)
+    return _ws_check(load().pdqp_ws_fit(w, *ptrs, int(C.shape[0]), mem, _stream(stream)), w)
+
+
+def pdqp_ws_grad(w, C, B, X, Y, stream=None) -> float:
+    ptrs, keep, mem = _ws_arrays([C, B, X, Y], np.float64)
+    loss = ctypes.c_double()
+    _ws_check(load().pdqp_ws_grad(w, *ptrs, int(C.shape[0]), ctypes.byref(loss), mem, _stream(stream)), w)
+    return loss.value
+
+
+def pdqp_ws_train(w, C, B, X, Y, epochs=10, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0,
+                  stream=None):
+    """Returns the mean minibatch loss of every epoch (numpy float64)."""
+    opt = pdqp_ws_train_options(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps),
+                                int(seed))
+    ptrs, keep, mem = _ws_arrays([C, B, X, Y], np.float64)
+    losses = np.zeros(max(int(epochs), 1))
+    _ws_check(load().pdqp_ws_train(w, ctypes.byref(opt), *ptrs, int(C.shape[0]),
+                                   ctypes.c_void_p(losses.ctypes.data), mem, _stream(stream)), w)
+    return losses[:int(epochs)]
+
+
+def pdqp_ws_infer(w, C, B, X0, Y0, stream=None):
+    """Write the predicted warm starts into X0 [count x n] and Y0 [count x m]
+    (float64 numpy arrays or torch CUDA tensors, in place)."""
+    for a in (X0, Y0):
+        if a is not None and not _is_torch_cuda(a):
+            assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+    ptrs, keep, mem = _ws_arrays([C, B, X0, Y0], np.float64)
+    return _ws_check(load().pdqp_ws_infer(w, ptrs[0], ptrs[1], int(C.shape[0]), ptrs[2], ptrs[3], mem,
+                                          _stream(stream)), w)
+
+
+def pdqp_gemm_bf16(A, B, bias=None, relu=False, mask=None, D_f32=None, D_bf16=None, splits=0, workspace=None,
+                   M=None, N=None, K=None, stream=None):
+    """D = A B' on torch CUDA tensors: A (M x lda) and B (N x ldb) bfloat16,
+    bias float32 [N], mask bfloat16 (M x ldm), D_f32 float32 / D_bf16 bfloat16
+    (M x ldd), workspace float32.  M, N, K default to the shapes of A and B."""
+    M = A.shape[0] if M is None else M
+    N = B.shape[0] if N is None else N
+    K = A.shape[1] if K is None else K
+    D = D_f32 if D_f32 is not None else D_bf16
+    p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    st = load().pdqp_gemm_bf16(int(M), int(N), int(K), p(A), int(A.stride(0)), p(B), int(B.stride(0)), p(bias),
+                               int(bool(relu)), p(mask), int(mask.stride(0)) if mask is not None else 0,
+                               p(D_f32), p(D_bf16), int(D.stride(0)), int(splits), p(workspace),
+                               int(workspace.numel() * 4) if workspace is not None else 0, _stream(stream))
+    if st != PDQP_OK:
+        raise PdqpError(st, "pdqp_gemm_bf16 rejected its arguments")
+    return st
+
+
+def pdqp_gemm_bf16_check(stream=None):
+    return int(load().pdqp_gemm_bf16_check(_stream(stream)))
+
+
+def pdqp_gemm_bf16_splits(M, N, K, splits=0):
+    return int(load().pdqp_gemm_bf16_splits(int(M), int(N), int(K), int(splits)))

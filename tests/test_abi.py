@@ -9,6 +9,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "pdqp.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 def _declared_functions(path):
@@ -33,7 +35,8 @@ def test_header_declares_the_boundary():
 
 def test_library_exports_every_declared_symbol(lib):
     from paper_2311_07710_gb300 import pdqp
-    for name in _declared_functions(HEADER):
+    assert len(HEADERS) >= 2
+    for name in sorted({n for h in HEADERS for n in _declared_functions(h)}):
         assert hasattr(lib, name), name
         assert name in pdqp.SIGNATURES, f"binding lacks {name}"
 
@@ -42,8 +45,9 @@ def test_struct_layout_matches_c(tmp_path, lib):
     from paper_2311_07710_gb300 import pdqp
     import ctypes
     fields = {"pdqp_options": [f for f, _ in pdqp.pdqp_options._fields_], "pdqp_profile": [f for f, _ in pdqp.pdqp_profile._fields_],
-              "pdqp_info": [f for f, _ in pdqp.pdqp_info._fields_]}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+              "pdqp_info": [f for f, _ in pdqp.pdqp_info._fields_],
+              "pdqp_ws_train_options": [f for f, _ in pdqp.pdqp_ws_train_options._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>'] + [f'#include "{h}"' for h in HEADERS] + ["int main(void){"]
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
         for f in fs:
