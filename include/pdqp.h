@@ -170,6 +170,18 @@ pdqp_status pdqp_create_batch(pdqp_handle *out, int32_t count, const int64_t *n,
 /* Number of instances of a handle (1 for pdqp_create). */
 int32_t pdqp_batch_count(pdqp_handle h);
 
+/* One handle for `count` members of a parameterised family: every member has
+ * the same Q, A, l, u (given once, as for pdqp_create) and its own objective
+ * and right-hand side, row i of C [count x n] and of B [count x m] (float64,
+ * row-major, in `mem_space`).  The handle is the one pdqp_create_batch would
+ * build from the same instances (same stacking, row blocks and results); it
+ * is built by replicating the shared structure on the device, so its host
+ * cost does not grow with count.  Requires count * (nnz(Q) + nnz(A)) < 2^31. */
+pdqp_status pdqp_create_family(pdqp_handle *out, int32_t count, int64_t n, int64_t m, int64_t m_eq,
+                               const int32_t *Q_rowptr, const int32_t *Q_col, const double *Q_val,
+                               const int32_t *A_rowptr, const int32_t *A_col, const double *A_val, const double *C,
+                               const double *B, const double *l, const double *u, int32_t mem_space, void *stream);
+
 /* Per-instance summaries of the last pdqp_solve (infos[count], host). */
 pdqp_status pdqp_batch_info(pdqp_handle h, pdqp_info *infos, int32_t count);
 

@@ -432,12 +432,24 @@ struct InstanceIn {
   const double *c, *b, *l, *u;
 };
 
-// Validate every instance, stack them block-diagonally (P = [Q | -A'] and A
-// with global column indices, row blocks that never cross an instance) and
-// upload everything.  Returns the new handle.
-pdqp_problem* build_problem(int count, const InstanceIn* ins, int mem, cudaStream_t s) {
+// Host-side stacking of `count` instances: P = [Q | -A'] and A with global
+// columns, row blocks that never cross an instance, per-row / per-block
+// instance tables and the data vectors.
+struct Stack {
+  int64_t N = 0, M = 0;
+  int count = 0;
+  std::vector<int32_t> prp{0}, pcol, psplit, arp{0}, acol, pblk{0}, ablk{0}, binst_p, binst_a, rinst_n, rinst_m;
+  std::vector<double> pval, aval, hc, hb, hl, hu;
+  std::vector<unsigned char> ineq;
+  std::vector<Inst> insts;
+};
+
+// Validate every instance and stack them block-diagonally.
+Stack stack_instances(int count, const InstanceIn* ins, int mem, cudaStream_t s) {
   if (count < 1) throw Fail{PDQP_ERR_INVALID, "count must be >= 1"};
   if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
+  Stack S;
+  S.count = count;
   int64_t N = 0, M = 0;
   for (int i = 0; i < count; ++i) {
     const InstanceIn& in = ins[i];
@@ -449,11 +461,9 @@ pdqp_problem* build_problem(int count, const InstanceIn* ins, int mem, cudaStrea
     M += in.m;
   }
   if (N > (1LL << 30) || M > (1LL << 30)) throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
-  std::vector<int32_t> prp(1, 0), pcol, psplit, arp(1, 0), acol, pblk{0}, ablk{0}, binst_p, binst_a;
-  std::vector<double> pval, aval, hc, hb, hl, hu;
-  std::vector<int32_t> rinst_n, rinst_m;
-  std::vector<unsigned char> ineq;
-  std::vector<Inst> insts(count);
+  S.N = N;
+  S.M = M;
+  S.insts.resize(count);
   int64_t xoff = 0, yoff = 0;
   for (int i = 0; i < count; ++i) {
     const InstanceIn& in = ins[i];
@@ -493,104 +503,326 @@ pdqp_problem* build_problem(int count, const InstanceIn* ins, int mem, cudaStrea
     else trp.assign(n + 1, 0);
     // rows of P = [Q | -A'] with global columns: x part xoff + j, y part N + yoff + r
     for (int64_t j = 0; j < n; ++j) {
-      for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k) { pcol.push_back((int32_t)(xoff + qcol[k])); pval.push_back(qval[k]); }
-      psplit.push_back((int32_t)pcol.size());
-      for (int32_t k = trp[j]; k < trp[j + 1]; ++k) {
-        pcol.push_back((int32_t)(N + yoff + tcol[k]));
-        pval.push_back(-tval[k]);
+      for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k) {
+        S.pcol.push_back((int32_t)(xoff + qcol[k]));
+        S.pval.push_back(qval[k]);
       }
-      if (pcol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
-      prp.push_back((int32_t)pcol.size());
+      S.psplit.push_back((int32_t)S.pcol.size());
+      for (int32_t k = trp[j]; k < trp[j + 1]; ++k) {
+        S.pcol.push_back((int32_t)(N + yoff + tcol[k]));
+        S.pval.push_back(-tval[k]);
+      }
+      if (S.pcol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
+      S.prp.push_back((int32_t)S.pcol.size());
     }
     for (int64_t r = 0; r < m; ++r) {
-      for (int32_t k = irp[r]; k < irp[r + 1]; ++k) { acol.push_back((int32_t)(xoff + icol[k])); aval.push_back(ival[k]); }
-      if (acol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(A) exceeds 2^31"};
-      arp.push_back((int32_t)acol.size());
+      for (int32_t k = irp[r]; k < irp[r + 1]; ++k) {
+        S.acol.push_back((int32_t)(xoff + icol[k]));
+        S.aval.push_back(ival[k]);
+      }
+      if (S.acol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(A) exceeds 2^31"};
+      S.arp.push_back((int32_t)S.acol.size());
     }
     // row blocks of this instance, offset to global rows
-    Inst& I = insts[i];
-    I.n = (int)n; I.m = (int)m; I.m_eq = (int)in.m_eq; I.xoff = (int)xoff; I.yoff = (int)yoff;
+    Inst& I = S.insts[i];
+    I.n = (int)n;
+    I.m = (int)m;
+    I.m_eq = (int)in.m_eq;
+    I.xoff = (int)xoff;
+    I.yoff = (int)yoff;
     {
-      std::vector<int32_t> lp(prp.end() - (n + 1), prp.end());
+      std::vector<int32_t> lp(S.prp.end() - (n + 1), S.prp.end());
       const int32_t base = lp[0];
       for (auto& v : lp) v -= base;
       const std::vector<int32_t> bl = row_blocks(n, lp);
-      I.bP0 = (int)pblk.size() - 1;
-      for (size_t q = 1; q < bl.size(); ++q) { pblk.push_back((int32_t)(xoff + bl[q])); binst_p.push_back(i); }
-      I.bP1 = (int)pblk.size() - 1;
+      I.bP0 = (int)S.pblk.size() - 1;
+      for (size_t q = 1; q < bl.size(); ++q) {
+        S.pblk.push_back((int32_t)(xoff + bl[q]));
+        S.binst_p.push_back(i);
+      }
+      I.bP1 = (int)S.pblk.size() - 1;
     }
     {
-      I.bA0 = (int)ablk.size() - 1;
+      I.bA0 = (int)S.ablk.size() - 1;
       if (m > 0) {
         const std::vector<int32_t> bl = row_blocks(m, irp);
-        for (size_t q = 1; q < bl.size(); ++q) { ablk.push_back((int32_t)(yoff + bl[q])); binst_a.push_back(i); }
+        for (size_t q = 1; q < bl.size(); ++q) {
+          S.ablk.push_back((int32_t)(yoff + bl[q]));
+          S.binst_a.push_back(i);
+        }
       }
-      I.bA1 = (int)ablk.size() - 1;
+      I.bA1 = (int)S.ablk.size() - 1;
     }
-    hc.insert(hc.end(), c.begin(), c.end());
-    hl.insert(hl.end(), l.begin(), l.end());
-    hu.insert(hu.end(), u.begin(), u.end());
-    hb.insert(hb.end(), b.begin(), b.end());
-    rinst_n.insert(rinst_n.end(), (size_t)n, i);
-    rinst_m.insert(rinst_m.end(), (size_t)m, i);
-    for (int64_t r = 0; r < m; ++r) ineq.push_back(r >= in.m_eq ? 1 : 0);
+    S.hc.insert(S.hc.end(), c.begin(), c.end());
+    S.hl.insert(S.hl.end(), l.begin(), l.end());
+    S.hu.insert(S.hu.end(), u.begin(), u.end());
+    S.hb.insert(S.hb.end(), b.begin(), b.end());
+    S.rinst_n.insert(S.rinst_n.end(), (size_t)n, i);
+    S.rinst_m.insert(S.rinst_m.end(), (size_t)m, i);
+    for (int64_t r = 0; r < m; ++r) S.ineq.push_back(r >= in.m_eq ? 1 : 0);
     xoff += n;
     yoff += m;
   }
+  return S;
+}
 
+void begin_work(pdqp_problem* h, int64_t N, int64_t M, int m_eq, int count, const std::vector<Inst>& insts) {
+  Work& w = h->w;
+  w.n = (int)N;
+  w.m = (int)M;
+  w.m_eq = m_eq;
+  w.count = count;
+  w.inst_host = insts;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
+}
+
+// Upload the structure and data of a host stack.
+void upload_stack(pdqp_problem* h, const Stack& S, cudaStream_t s) {
+  Work& w = h->w;
+  const size_t n = (size_t)S.N, m = (size_t)S.M;
+  upload_csr(h, w.P, (int)S.N, S.prp, S.pcol, S.pval, &S.psplit, S.pblk, s);
+  upload_csr(h, w.A, (int)S.M, S.arp, S.acol, S.aval, nullptr, S.ablk, s);
+  w.inst = dalloc<Inst>(h, S.count);
+  to_device(w.inst, S.insts.data(), S.count, s);
+  w.blk_inst_P = dalloc<int>(h, S.binst_p.size());
+  to_device(w.blk_inst_P, S.binst_p.data(), S.binst_p.size(), s);
+  w.blk_inst_A = dalloc<int>(h, S.binst_a.size());
+  to_device(w.blk_inst_A, S.binst_a.data(), S.binst_a.size(), s);
+  w.row_inst_n = dalloc<int>(h, n);
+  to_device(w.row_inst_n, S.rinst_n.data(), n, s);
+  w.row_inst_m = dalloc<int>(h, m);
+  to_device(w.row_inst_m, S.rinst_m.data(), m, s);
+  w.row_ineq = dalloc<unsigned char>(h, m);
+  to_device(w.row_ineq, S.ineq.data(), m, s);
+  w.c = dalloc<double>(h, n);
+  w.l = dalloc<double>(h, n);
+  w.u = dalloc<double>(h, n);
+  w.b = dalloc<double>(h, m);
+  to_device(w.c, S.hc.data(), n, s);
+  to_device(w.l, S.hl.data(), n, s);
+  to_device(w.u, S.hu.data(), n, s);
+  to_device(w.b, S.hb.data(), m, s);
+  CK(cudaStreamSynchronize(s));   // the host vectors die with the caller
+}
+
+// Everything else a handle needs, sized from w.n, w.m, w.count and the blocks.
+void alloc_work(pdqp_problem* h, cudaStream_t s) {
+  Work& w = h->w;
+  const size_t n = (size_t)w.n, m = (size_t)w.m;
+  const int count = w.count;
+  w.cs = dalloc<double>(h, n); w.ls = dalloc<double>(h, n); w.us = dalloc<double>(h, n); w.bs = dalloc<double>(h, m);
+  w.dsc = dalloc<double>(h, n + m); w.idsc = dalloc<double>(h, n + m); w.nu = dalloc<double>(h, n + m);
+  w.D2 = w.dsc; w.D1 = w.dsc + n; w.iD2 = w.idsc; w.iD1 = w.idsc + n;
+  w.x = dalloc<double>(h, n); w.xbar = dalloc<double>(h, n); w.xt = dalloc<double>(h, n);
+  w.Z[0] = dalloc<double>(h, n + m); w.Z[1] = dalloc<double>(h, n + m); w.ax = dalloc<double>(h, n);
+  w.y = w.Z[1] + n;
+  w.ybar = dalloc<double>(h, m); w.ay = dalloc<double>(h, m);
+  w.pu[0] = dalloc<double>(h, n); w.pu[1] = dalloc<double>(h, n);
+  w.pz[0] = dalloc<double>(h, n + m); w.pz[1] = dalloc<double>(h, n + m);
+  w.lw[0] = dalloc<double>(h, n); w.lw[1] = dalloc<double>(h, n);
+  w.lz_al = dalloc<double>(h, (size_t)count * 2 * 512); w.lz_be = dalloc<double>(h, (size_t)count * 2 * 512);
+  w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
+  w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
+  w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
+  w.st = dalloc<DevState>(h, count);
+  w.bst = dalloc<BatchState>(h, 1);
+  w.stage_n = dalloc<double>(h, n); w.stage_m = dalloc<double>(h, m);
+  CK(cudaMallocHost(&w.st_host, sizeof(DevState) * count));
+  CK(cudaMallocHost(&w.bst_host, sizeof(BatchState)));
+  for (auto& e : h->ev) CK(cudaEventCreate(&e));
+  CK(cudaMemsetAsync(w.st, 0, sizeof(DevState) * count, s));
+  CK(cudaMemsetAsync(w.bst, 0, sizeof(BatchState), s));
+  CK(cudaStreamSynchronize(s));
+}
+
+pdqp_problem* build_problem(int count, const InstanceIn* ins, int mem, cudaStream_t s) {
+  const Stack S = stack_instances(count, ins, mem, s);
   pdqp_problem* h = new pdqp_problem();
   try {
-    Work& w = h->w;
-    w.n = (int)N; w.m = (int)M; w.m_eq = (int)ins[0].m_eq; w.count = count;
-    w.inst_host = insts;
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    upload_csr(h, w.P, (int)N, prp, pcol, pval, &psplit, pblk, s);
-    upload_csr(h, w.A, (int)M, arp, acol, aval, nullptr, ablk, s);
-    const size_t n = (size_t)N, m = (size_t)M;
-    w.inst = dalloc<Inst>(h, count);
-    to_device(w.inst, insts.data(), count, s);
-    w.blk_inst_P = dalloc<int>(h, binst_p.size());
-    to_device(w.blk_inst_P, binst_p.data(), binst_p.size(), s);
-    w.blk_inst_A = dalloc<int>(h, binst_a.size());
-    to_device(w.blk_inst_A, binst_a.data(), binst_a.size(), s);
-    w.row_inst_n = dalloc<int>(h, n);
-    to_device(w.row_inst_n, rinst_n.data(), n, s);
-    w.row_inst_m = dalloc<int>(h, m);
-    to_device(w.row_inst_m, rinst_m.data(), m, s);
-    w.row_ineq = dalloc<unsigned char>(h, m);
-    to_device(w.row_ineq, ineq.data(), m, s);
-    w.c = dalloc<double>(h, n); w.l = dalloc<double>(h, n); w.u = dalloc<double>(h, n); w.b = dalloc<double>(h, m);
-    to_device(w.c, hc.data(), n, s); to_device(w.l, hl.data(), n, s); to_device(w.u, hu.data(), n, s);
-    to_device(w.b, hb.data(), m, s);
-    w.cs = dalloc<double>(h, n); w.ls = dalloc<double>(h, n); w.us = dalloc<double>(h, n); w.bs = dalloc<double>(h, m);
-    w.dsc = dalloc<double>(h, n + m); w.idsc = dalloc<double>(h, n + m); w.nu = dalloc<double>(h, n + m);
-    w.D2 = w.dsc; w.D1 = w.dsc + n; w.iD2 = w.idsc; w.iD1 = w.idsc + n;
-    w.x = dalloc<double>(h, n); w.xbar = dalloc<double>(h, n); w.xt = dalloc<double>(h, n);
-    w.Z[0] = dalloc<double>(h, n + m); w.Z[1] = dalloc<double>(h, n + m); w.ax = dalloc<double>(h, n);
-    w.y = w.Z[1] + n;
-    w.ybar = dalloc<double>(h, m); w.ay = dalloc<double>(h, m);
-    w.pu[0] = dalloc<double>(h, n); w.pu[1] = dalloc<double>(h, n);
-    w.pz[0] = dalloc<double>(h, n + m); w.pz[1] = dalloc<double>(h, n + m);
-    w.lw[0] = dalloc<double>(h, n); w.lw[1] = dalloc<double>(h, n);
-    w.lz_al = dalloc<double>(h, (size_t)count * 2 * 512); w.lz_be = dalloc<double>(h, (size_t)count * 2 * 512);
-    w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
-    w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
-    w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
-    w.st = dalloc<DevState>(h, count);
-    w.bst = dalloc<BatchState>(h, 1);
-    w.stage_n = dalloc<double>(h, n); w.stage_m = dalloc<double>(h, m);
-    CK(cudaMallocHost(&w.st_host, sizeof(DevState) * count));
-    CK(cudaMallocHost(&w.bst_host, sizeof(BatchState)));
-    for (auto& e : h->ev) CK(cudaEventCreate(&e));
-    CK(cudaMemsetAsync(w.st, 0, sizeof(DevState) * count, s));
-    CK(cudaMemsetAsync(w.bst, 0, sizeof(BatchState), s));
-    CK(cudaStreamSynchronize(s));
+    begin_work(h, S.N, S.M, (int)ins[0].m_eq, count, S.insts);
+    upload_stack(h, S, s);
+    alloc_work(h, s);
   } catch (...) {
     pdqp_destroy(h);
     throw;
   }
+  return h;
+}
+
+// ---------------------------------------------------------------- families
+// Device-side replication of a one-instance stack into `count` copies.
+__global__ void k_rep_rowptr(const int* __restrict__ trp, int rows_t, long long nnz_t, int count, int* __restrict__ rp) {
+  const long long total = (long long)count * rows_t;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= total; i += (long long)gridDim.x * blockDim.x)
+    rp[i] = i == total ? (int)(count * nnz_t) : (int)((i / rows_t) * nnz_t + trp[i % rows_t]);
+}
+
+// P mode: template columns j < n_t are x columns (instance offset inst * n_t),
+// j >= n_t are y columns (global N + inst * m_t + j - n_t); A mode: x columns.
+__global__ void k_rep_cols(const int* __restrict__ tcol, const double* __restrict__ tval, long long nnz_t, int count,
+                           int n_t, int m_t, long long N, int pmode, int* __restrict__ col, double* __restrict__ val) {
+  const long long total = (long long)count * nnz_t;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+    const long long inst = k / nnz_t, q = k % nnz_t;
+    const int c = tcol[q];
+    col[k] = (pmode && c >= n_t) ? (int)(N + inst * m_t + (c - n_t)) : (int)(inst * n_t + c);
+    val[k] = tval[q];
+  }
+}
+
+__global__ void k_rep_split(const int* __restrict__ tsplit, int n_t, long long nnz_t, int count, int* __restrict__ split) {
+  const long long total = (long long)count * n_t;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    split[i] = (int)((i / n_t) * nnz_t + tsplit[i % n_t]);
+}
+
+// blk[0] = 0, blk[1 + inst*nb + q] = inst*rows_t + tblk[q+1]; meta per block
+__global__ void k_rep_blocks(const int* __restrict__ tblk, int nb, int rows_t, int count, const int* __restrict__ rp,
+                             int* __restrict__ blk, int* __restrict__ binst, int* __restrict__ meta) {
+  const long long total = (long long)count * nb;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < total; b += (long long)gridDim.x * blockDim.x) {
+    const long long inst = b / nb;
+    const int q = (int)(b % nb);
+    const int r0 = (int)(inst * rows_t + tblk[q]), r1 = (int)(inst * rows_t + tblk[q + 1]);
+    if (b == 0) blk[0] = 0;
+    blk[b + 1] = r1;
+    binst[b] = (int)inst;
+    meta[4 * b + 0] = r0;
+    meta[4 * b + 1] = r1;
+    meta[4 * b + 2] = rp[r0];
+    meta[4 * b + 3] = rp[r1];
+  }
+}
+
+__global__ void k_rep_rows(int n_t, int m_t, int m_eq, int count, int* __restrict__ rinst_n, int* __restrict__ rinst_m,
+                           unsigned char* __restrict__ ineq) {
+  const long long tn = (long long)count * n_t, tm = (long long)count * m_t;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tn + tm; i += (long long)gridDim.x * blockDim.x) {
+    if (i < tn) {
+      rinst_n[i] = (int)(i / n_t);
+    } else {
+      const long long r = i - tn;
+      rinst_m[r] = (int)(r / m_t);
+      ineq[r] = (r % m_t) >= m_eq ? 1 : 0;
+    }
+  }
+}
+
+__global__ void k_rep_vec(const double* __restrict__ t, int len, long long total, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    out[i] = t[i % len];
+}
+
+__global__ void k_count_nonfinite(const double* __restrict__ v, long long n, unsigned long long* __restrict__ cnt) {
+  unsigned long long c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c += !isfinite(v[i]);
+  if (c) atomicAdd(cnt, c);
+}
+
+int rep_grid(long long total) { return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 4096)); }
+
+// Replicate a device CSR of one instance (template handle t) `count` times.
+void replicate_csr(pdqp_problem* h, DCsr& M, const DCsr& T, int count, int n_t, int m_t, long long N, bool pmode,
+                   cudaStream_t s) {
+  const long long rows = (long long)count * T.rows, nnz = (long long)count * T.nnz;
+  M.rows = (int)rows;
+  M.nnz = nnz;
+  M.rp = dalloc<int>(h, rows + 1 + 8);
+  M.col = dalloc<int>(h, nnz + 8);
+  M.val = dalloc<double>(h, nnz + 8);
+  M.sval = dalloc<double>(h, nnz + 8);
+  CK(cudaMemsetAsync(M.rp, 0, (rows + 1 + 8) * sizeof(int), s));
+  CK(cudaMemsetAsync(M.col, 0, (nnz + 8) * sizeof(int), s));
+  CK(cudaMemsetAsync(M.val, 0, (nnz + 8) * sizeof(double), s));
+  CK(cudaMemsetAsync(M.sval, 0, (nnz + 8) * sizeof(double), s));
+  if (T.rows > 0) k_rep_rowptr<<<rep_grid(rows + 1), 256, 0, s>>>(T.rp, T.rows, T.nnz, count, M.rp);
+  if (T.nnz > 0)
+    k_rep_cols<<<rep_grid(nnz), 256, 0, s>>>(T.col, T.val, T.nnz, count, n_t, m_t, N, pmode ? 1 : 0, M.col, M.val);
+  M.nblk = count * T.nblk;
+  M.blk = dalloc<int>(h, (size_t)M.nblk + 1);
+  M.meta = dalloc<int>(h, 4 * (size_t)(M.nblk > 0 ? M.nblk : 1));
+  CK(cudaMemsetAsync(M.blk, 0, ((size_t)M.nblk + 1) * sizeof(int), s));
+  int* binst = dalloc<int>(h, (size_t)std::max(M.nblk, 1));
+  if (T.nblk > 0) k_rep_blocks<<<rep_grid(M.nblk), 256, 0, s>>>(T.blk, T.nblk, T.rows, count, M.rp, M.blk, binst, M.meta);
+  if (pmode) {
+    h->w.blk_inst_P = binst;
+    M.split = dalloc<int>(h, rows);
+    if (T.rows > 0) k_rep_split<<<rep_grid(rows), 256, 0, s>>>(T.split, T.rows, T.nnz, count, M.split);
+  } else {
+    h->w.blk_inst_A = binst;
+  }
+  CK(cudaGetLastError());
+}
+
+pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, const double* B, int mem,
+                           cudaStream_t s) {
+  if (count < 1) throw Fail{PDQP_ERR_INVALID, "count must be >= 1"};
+  if (!C || (base.m > 0 && !B)) throw Fail{PDQP_ERR_INVALID, "null C or B"};
+  check_space(C, mem, "C");
+  check_space(B, mem, "B");
+  pdqp_problem* t = build_problem(1, &base, mem, s);   // validates the base problem
+  pdqp_problem* h = nullptr;
+  try {
+    const Work& tw = t->w;
+    const long long n_t = tw.n, m_t = tw.m;
+    if ((long long)count * tw.P.nnz > INT32_MAX - 16 || (long long)count * tw.A.nnz > INT32_MAX - 16)
+      throw Fail{PDQP_ERR_INVALID, "count * nnz exceeds 2^31"};
+    if ((long long)count * n_t > (1LL << 30) || (long long)count * m_t > (1LL << 30))
+      throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
+    std::vector<Inst> insts(count);
+    const Inst& I0 = tw.inst_host[0];
+    const int nbP = tw.P.nblk, nbA = tw.A.nblk;
+    for (int i = 0; i < count; ++i) {
+      Inst& I = insts[i];
+      I = I0;
+      I.xoff = (int)(i * n_t);
+      I.yoff = (int)(i * m_t);
+      I.bP0 = i * nbP;
+      I.bP1 = (i + 1) * nbP;
+      I.bA0 = i * nbA;
+      I.bA1 = (i + 1) * nbA;
+    }
+    h = new pdqp_problem();
+    const long long N = count * n_t, M = count * m_t;
+    begin_work(h, N, M, tw.m_eq, count, insts);
+    Work& w = h->w;
+    replicate_csr(h, w.P, tw.P, count, (int)n_t, (int)m_t, N, true, s);
+    replicate_csr(h, w.A, tw.A, count, (int)n_t, (int)m_t, N, false, s);
+    w.inst = dalloc<Inst>(h, count);
+    to_device(w.inst, insts.data(), count, s);
+    w.row_inst_n = dalloc<int>(h, N);
+    w.row_inst_m = dalloc<int>(h, M);
+    w.row_ineq = dalloc<unsigned char>(h, M);
+    k_rep_rows<<<rep_grid(N + M), 256, 0, s>>>((int)n_t, (int)m_t, tw.m_eq, count, w.row_inst_n, w.row_inst_m,
+                                               w.row_ineq);
+    w.c = dalloc<double>(h, N);
+    w.l = dalloc<double>(h, N);
+    w.u = dalloc<double>(h, N);
+    w.b = dalloc<double>(h, M);
+    const cudaMemcpyKind kind = mem == PDQP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(w.c, C, (size_t)N * sizeof(double), kind, s));
+    if (M > 0) CK(cudaMemcpyAsync(w.b, B, (size_t)M * sizeof(double), kind, s));
+    k_rep_vec<<<rep_grid(N), 256, 0, s>>>(tw.l, (int)n_t, N, w.l);
+    k_rep_vec<<<rep_grid(N), 256, 0, s>>>(tw.u, (int)n_t, N, w.u);
+    unsigned long long* cnt = dalloc<unsigned long long>(h, 1);
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    k_count_nonfinite<<<rep_grid(N), 256, 0, s>>>(w.c, N, cnt);
+    if (M > 0) k_count_nonfinite<<<rep_grid(M), 256, 0, s>>>(w.b, M, cnt);
+    CK(cudaGetLastError());
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, cnt, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) throw Fail{PDQP_ERR_INVALID, "C or B: non-finite entry"};
+    alloc_work(h, s);
+  } catch (...) {
+    if (h) pdqp_destroy(h);
+    pdqp_destroy(t);
+    throw;
+  }
+  pdqp_destroy(t);
   return h;
 }
 
@@ -682,6 +914,26 @@ pdqp_status pdqp_create_batch(pdqp_handle* out, int32_t count, const int64_t* n,
     ins[i] = InstanceIn{n[i], m[i], m_eq[i], Q_rowptr[i], Q_col[i], Q_val[i], A_rowptr[i], A_col[i], A_val[i],
                         c[i], b[i], l[i], u[i]};
   return create_common(out, count, ins.data(), mem, (cudaStream_t)stream);
+}
+
+pdqp_status pdqp_create_family(pdqp_handle* out, int32_t count, int64_t n, int64_t m, int64_t m_eq,
+                               const int32_t* Q_rowptr, const int32_t* Q_col, const double* Q_val,
+                               const int32_t* A_rowptr, const int32_t* A_col, const double* A_val, const double* C,
+                               const double* B, const double* l, const double* u, int32_t mem, void* stream) {
+  if (!out) return PDQP_ERR_INVALID;
+  *out = nullptr;
+  try {
+    if (count < 1) throw Fail{PDQP_ERR_INVALID, "count must be >= 1"};
+    InstanceIn base{n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, C, B, l, u};
+    *out = build_family(base, count, C, B, mem, (cudaStream_t)stream);
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    g_create_error = f.msg;
+    return f.st;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    return PDQP_ERR_OOM;
+  }
 }
 
 pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t mem, void* stream) {

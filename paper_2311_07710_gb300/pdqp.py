@@ -92,6 +92,8 @@ SIGNATURES = {
     "pdqp_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_profile)]),
     "pdqp_create_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int64)] * 3
                           + [ctypes.POINTER(_P)] * 10 + [ctypes.c_int32, _P]),
+    "pdqp_create_family": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "pdqp_batch_count": (ctypes.c_int32, [_P]),
     "pdqp_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_info), ctypes.c_int32]),
     "pdqp_kkt_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P,
@@ -300,6 +302,35 @@ def pdqp_create_batch(instances, stream=None):
     st = load().pdqp_create_batch(ctypes.byref(h), count, ns, ms, meqs, *ptr_arrays, mem, _stream(stream))
     _check(st, None)
     return h
+
+
+def pdqp_create_family(count, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, C, B, l, u,
+                       stream=None):
+    """One handle for `count` family members sharing Q, A, l, u; C [count x n]
+    and B [count x m] hold each member's c and b."""
+    args = [_ptr(Q_rowptr, np.int32), _ptr(Q_col, np.int32), _ptr(Q_val, np.float64),
+            _ptr(A_rowptr, np.int32), _ptr(A_col, np.int32), _ptr(A_val, np.float64),
+            _ptr(C, np.float64), _ptr(B, np.float64), _ptr(l, np.float64), _ptr(u, np.float64)]
+    mem = _one_space([a[2] for a in args])
+    h = ctypes.c_void_p()
+    st = load().pdqp_create_family(ctypes.byref(h), int(count), int(n), int(m), int(m_eq), *[a[0] for a in args],
+                                   mem, _stream(stream))
+    _check(st, None)
+    return h
+
+
+def family_from_base(base, C, B, device=False, stream=None):
+    """A family handle from a base instance (n, m, m_eq, Q, A, l, u; scipy CSR)
+    and per-member rows C [count x n], B [count x m]."""
+    arrays = [base.Q.indptr, base.Q.indices, base.Q.data, base.A.indptr, base.A.indices, base.A.data,
+              C, B, base.l, base.u]
+    dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 4
+    arrays = [np.ascontiguousarray(a, dtype=t) for a, t in zip(arrays, dtypes)]
+    if device:
+        import torch
+        arrays = [torch.from_numpy(a).cuda() for a in arrays]
+        torch.cuda.synchronize()
+    return pdqp_create_family(C.shape[0], base.n, base.m, base.m_eq, *arrays, stream=stream)
 
 
 def pdqp_batch_count(h) -> int:

@@ -101,3 +101,45 @@ def test_batch_iterates_match_oracle(pdqp):
             assert G.rel_err(v[off:off + ln], ref[key]) <= 1e-10, (k, key)
         assert infos[k].norm_A == pytest.approx(refs[k].norm_A, rel=1e-6) or inst.m == 0
         ox += inst.n; oy += inst.m
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_family_handle_reproduces_batch(pdqp, precision):
+    """A family handle (structure replicated on the device) gives the batch
+    handle's results bit for bit, from zero and from a given start."""
+    fam = qpgen.family_qp(n=300, m=150)
+    C, B = fam.params(0, 7)
+    insts = []
+    for k in range(7):
+        it = qpgen.QPInstance("member", fam.base.n, fam.base.m, fam.base.m_eq, fam.base.Q, fam.base.A, C[k], B[k],
+                              fam.base.l, fam.base.u)
+        insts.append(it)
+    N, M = 7 * fam.base.n, 7 * fam.base.m
+    rng = np.random.default_rng(1)
+    starts = [(None, None), (0.1 * rng.standard_normal(N), 0.1 * rng.standard_normal(M))]
+    for x0, y0 in starts:
+        out = []
+        for make in (lambda: pdqp.batch_from_instances(insts), lambda: pdqp.family_from_base(fam.base, C, B)):
+            h = make()
+            try:
+                x, y = np.zeros(N), np.zeros(M)
+                st, _ = pdqp.pdqp_solve(h, pdqp.pdqp_default_options(precision=precision), x0=x0, y0=y0,
+                                        x_out=x, y_out=y)
+                out.append((st, [(i.status, i.iterations) for i in pdqp.pdqp_batch_info(h)], x, y))
+            finally:
+                pdqp.pdqp_destroy(h)
+        assert out[0][0] == out[1][0] == pdqp.PDQP_OK
+        assert out[0][1] == out[1][1]
+        np.testing.assert_array_equal(out[0][2], out[1][2])
+        np.testing.assert_array_equal(out[0][3], out[1][3])
+
+
+def test_family_handle_rejects_bad_input(pdqp):
+    fam = qpgen.family_qp(n=40, m=20)
+    C, B = fam.params(0, 3)
+    C[1, 5] = np.nan
+    with pytest.raises(pdqp.PdqpError):
+        pdqp.family_from_base(fam.base, C, B)
+    C, B = fam.params(0, 3)
+    h = pdqp.family_from_base(fam.base, C, B, device=True)
+    pdqp.pdqp_destroy(h)
