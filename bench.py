@@ -45,15 +45,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-side", action="store_true",
+                    help="skip the side measurement of plain float64 solves")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 256, 512])
     ap.add_argument("--workload", default="large_sparse_qp",
-                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp"],
+                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws"],
                     help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
-                         "of horizon 10..100 in one batched handle; random_sparse_qp: n=1000")
-    ap.add_argument("--batch", type=int, default=4096)
+                         "of horizon 10..100 in one batched handle; random_sparse_qp: n=1000; "
+                         "family_ws: held-out members of the n=2e4 family solved in one handle from the "
+                         "learned warm start (network trained first on --train solver outputs)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="instances per step (mpc_batch: 4096, family_ws: 1024)")
+    ap.add_argument("--train", type=int, default=4096, help="family_ws: training solves")
+    ap.add_argument("--epochs", type=int, default=20, help="family_ws: training epochs")
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="variables of the workload (m = n/2); smaller only for profiler captures")
     return ap.parse_args()
@@ -210,7 +217,7 @@ def run_ours(args, world, rank, local):
     prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
     opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=args.spmv_threads)
     if args.workload == "mpc_batch":
-        insts = qpgen.mpc_batch(args.batch, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
+        insts = qpgen.mpc_batch(args.batch or 4096, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
     elif args.workload == "random_sparse_qp":
         insts = [qpgen.random_sparse_qp(seed=qpgen.SEED_BASE + 1000 * rank)]
     else:
@@ -258,6 +265,25 @@ def run_ours(args, world, rank, local):
     iters = [i.iterations for i in infos]
     statuses = [i.status for i in infos]
     inst_iters = [i.iterations for i in batch_infos]
+
+    # ---- side measurement: plain float64 solves of the same problem ----
+    fp64_side = None
+    if args.precision == "mixed" and not args.no_fp64_side:
+        o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, spmv_threads=args.spmv_threads)
+        pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
+        torch.cuda.synchronize(dev)
+        k64 = 2
+        ev0.record(stream)
+        for _ in range(k64):
+            st64, info64 = pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = allreduce_max(ev0.elapsed_time(ev1), world, dev)
+        fp64_side = {"value": world * k64 * per_step / (t64 / 1e3), "unit": "solves/s", "steps": k64,
+                     "iterations": info64.iterations if per_step == 1 else
+                     max(i.iterations for i in pdqp.pdqp_batch_info(h)),
+                     "rel_kkt": info64.rel_kkt, "status": info64.status,
+                     "speedup_of_value": value / (world * k64 * per_step / (t64 / 1e3))}
 
     # ---- end-to-end leg: host buffers, H2D + solve + D2H inside the timed region ----
     host_sets = [[i.Q.indptr, i.Q.indices, i.Q.data, i.A.indptr, i.A.indices, i.A.data, i.c, i.b, i.l, i.u]
@@ -330,10 +356,188 @@ def run_ours(args, world, rank, local):
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk}
+    if fp64_side is not None:
+        line["plain_fp64"] = fp64_side
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.n == 1_000_000 and \
             args.workload == "large_sparse_qp":
         v, t_solve, sample = oracle_sample(inst)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+FAMILY_WORKLOAD = ("family_qp n=2e4 m=1e4 (m_eq=5e3): the random_sparse_qp pattern scaled (A 10 nnz/row, "
+                   "Q = B'B + 0.01 I with B 5 nnz/row), c = c_bar + 0.1 N(0,1), b = b_bar + 0.1 N(0,1) per member; "
+                   "warm start: projection 3e4 -> 1024 (fixed), 3 x (1024, ReLU), output 3e4, bf16 weights, "
+                   "fp32 accumulation")
+
+
+def _family_solve(pdqp, base, C, B, opts, stream, X0=None, Y0=None, chunk=1024):
+    """Solve members (C, B) in family handles of `chunk`; returns X, Y, infos."""
+    import torch
+    Xs, Ys, infos = [], [], []
+    for s0 in range(0, C.shape[0], chunk):
+        c, b = C[s0:s0 + chunk], B[s0:s0 + chunk]
+        h = pdqp.family_from_base(base, c, b, stream=stream)
+        x = torch.zeros(c.numel() if hasattr(c, "numel") else c.size, dtype=torch.float64, device="cuda")
+        y = torch.zeros(b.numel() if hasattr(b, "numel") else b.size, dtype=torch.float64, device="cuda")
+        x0 = None if X0 is None else X0[s0:s0 + chunk].reshape(-1)
+        y0 = None if Y0 is None else Y0[s0:s0 + chunk].reshape(-1)
+        pdqp.pdqp_solve(h, opts, x0=x0, y0=y0, x_out=x, y_out=y, stream=stream)
+        infos += pdqp.pdqp_batch_info(h)
+        pdqp.pdqp_destroy(h)
+        Xs.append(x.view(c.shape[0], -1))
+        Ys.append(y.view(b.shape[0], -1))
+    return torch.cat(Xs), torch.cat(Ys), infos
+
+
+def run_family_ws(args, world, rank, local):
+    """Configuration 4: train the warm-start network on solver outputs, then
+    time held-out members solved in one family handle from its predictions."""
+    import torch
+
+    import qpgen
+    from paper_2311_07710_gb300 import pdqp
+
+    pdqp.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
+    opts = pdqp.pdqp_default_options(precision=prec)
+    fam = qpgen.family_qp(seed=qpgen.SEED_BASE + 4 + 1000 * rank)
+    n, m = fam.base.n, fam.base.m
+    batch = args.batch or 1024
+
+    # ---- training data from the solver, then the network (untimed) ----
+    t0 = time.perf_counter()
+    Ctr, Btr = fam.params(0, args.train)
+    Ctr_d, Btr_d = torch.from_numpy(Ctr).to(dev), torch.from_numpy(Btr).to(dev)
+    X, Y, info_tr = _family_solve(pdqp, fam.base, Ctr_d, Btr_d, opts, stream)
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t0
+    proj, layers = qpgen.warmstart_params(qpgen.SEED_BASE + 40 + rank, n + m, 1024, 1024, 3)
+    w = pdqp.pdqp_ws_create(n, m, 1024, 1024, 3, 512, stream=stream)
+    pdqp.pdqp_ws_set_params(w, -1, proj, stream=stream)
+    for j, (W, b) in enumerate(layers):
+        pdqp.pdqp_ws_set_params(w, j, W, b, stream=stream)
+    t0 = time.perf_counter()
+    pdqp.pdqp_ws_fit(w, Ctr_d, Btr_d, X, Y, stream=stream)
+    losses = pdqp.pdqp_ws_train(w, Ctr_d, Btr_d, X, Y, epochs=args.epochs, batch=256, lr=1e-3, seed=1,
+                                stream=stream)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    Xmean, Ymean = X.mean(dim=0), Y.mean(dim=0)
+    del X, Y, Ctr_d, Btr_d
+
+    # ---- held-out members, resident in HBM ----
+    Cte, Bte = fam.params(10 ** 7 + 10 ** 5 * rank, batch)
+    C_d, B_d = torch.from_numpy(Cte).to(dev), torch.from_numpy(Bte).to(dev)
+    X0 = torch.zeros((batch, n), dtype=torch.float64, device=dev)
+    Y0 = torch.zeros((batch, m), dtype=torch.float64, device=dev)
+    h = pdqp.family_from_base(fam.base, C_d, B_d, stream=stream)
+    x = torch.zeros(batch * n, dtype=torch.float64, device=dev)
+    y = torch.zeros(batch * m, dtype=torch.float64, device=dev)
+
+    def step(warm):
+        if warm:
+            pdqp.pdqp_ws_infer(w, C_d, B_d, X0, Y0, stream=stream)
+            return pdqp.pdqp_solve(h, opts, x0=X0.view(-1), y0=Y0.view(-1), x_out=x, y_out=y, stream=stream)
+        return pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream)
+
+    for _ in range(args.warmup):
+        step(True)
+    pdqp.pdqp_profile_enable(h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = pdqp.pdqp_launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = pdqp.pdqp_launch_count() - l0
+    barrier(world)
+    clk = clocks.stop()
+    prof = pdqp.pdqp_profile_read(h)
+    pdqp.pdqp_profile_enable(h, False)
+    t_ms = allreduce_max(ev0.elapsed_time(ev1), world, dev)
+    value = world * args.steps * batch / (t_ms / 1e3)
+    warm_infos = pdqp.pdqp_batch_info(h)
+    Xw, Yw = x.view(batch, n).clone(), y.view(batch, m).clone()
+    # cold start and mean-solution start on the same members (one solve each)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    step(False)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    cold_s = ev0.elapsed_time(ev1) / 1e3
+    cold_infos = pdqp.pdqp_batch_info(h)
+    Xc, Yc = x.view(batch, n).clone(), y.view(batch, m).clone()
+    pdqp.pdqp_solve(h, opts, x0=Xmean.repeat(batch), y0=Ymean.repeat(batch), x_out=x, y_out=y, stream=stream)
+    mean_infos = pdqp.pdqp_batch_info(h)
+    rel = lambda P, Q: float(torch.linalg.norm(P - Q) / torch.linalg.norm(Q))
+    pred_err = rel(torch.cat([X0, Y0], 1), torch.cat([Xc, Yc], 1))
+    mean_err = rel(torch.cat([Xmean.expand(batch, n), Ymean.expand(batch, m)], 1), torch.cat([Xc, Yc], 1))
+
+    # ---- end to end: host (C, B) in, handle + inference + solve, host (x, y) out ----
+    xh, yh = np.zeros(batch * n), np.zeros(batch * m)
+    X0h, Y0h = np.zeros((batch, n)), np.zeros((batch, m))
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        he = pdqp.family_from_base(fam.base, Cte, Bte, stream=stream)
+        pdqp.pdqp_ws_infer(w, Cte, Bte, X0h, Y0h, stream=stream)
+        pdqp.pdqp_solve(he, opts, x0=X0h.reshape(-1), y0=Y0h.reshape(-1), x_out=xh, y_out=yh, stream=stream)
+        pdqp.pdqp_destroy(he)
+    torch.cuda.synchronize(dev)
+    e2e_s = allreduce_max(time.perf_counter() - t0, world, dev)
+    e2e_value = world * args.e2e_steps * batch / e2e_s if args.e2e_steps > 0 else None
+    h2d = Cte.nbytes + Bte.nbytes + sum(a.nbytes for a in (fam.base.Q.indptr, fam.base.Q.indices, fam.base.Q.data,
+                                                             fam.base.A.indptr, fam.base.A.indices, fam.base.A.data,
+                                                             fam.base.l, fam.base.u))
+    pdqp.pdqp_destroy(h)
+    pdqp.pdqp_ws_destroy(w)
+
+    peaks = json.load(open(PEAKS_JSON)) if os.path.exists(PEAKS_JSON) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kinds = {k: v for k, v in prof.items() if k in ("dual", "primal") and v["launches"]}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = prof[dom]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    kname = {"dual": "k_dual", "primal": "k_primal"}[dom]
+    roof = {"bound": "hbm", "achieved": d["bytes"] / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": d["bytes"] / avg_s / 1e9 / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "kernel": kname, "avg_launch_us": avg_s * 1e6, "launches": d["launches"],
+            "algorithmic_bytes_per_launch": d["bytes"], "traffic": traffic_for(kname),
+            "note": "algorithmic bytes count every member's rows at every launch; members that finished skip theirs"}
+    it = lambda infos: {"mean": float(np.mean([i.iterations for i in infos])),
+                        "max": int(max(i.iterations for i in infos))}
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": FAMILY_WORKLOAD, "held_out_per_step": batch, "train_solves": args.train,
+                       "epochs": args.epochs, "precision": args.precision, "eps": 1e-6,
+                       "step": "network inference + one family-handle solve of the held-out members from it",
+                       "l2": "inputs larger than L2 (matrices >= 9 GB), no flush", "parallelism": f"replicas x{world}"},
+            "cold_start": {"value": batch / cold_s, "unit": "solves/s", "iterations": it(cold_infos)},
+            "warm_start": {"iterations": it(warm_infos), "prediction_rel_error": pred_err},
+            "mean_solution_start": {"iterations": it(mean_infos), "rel_error": mean_err},
+            "statuses_ok": bool(all(i.status == 0 for i in warm_infos + cold_infos + mean_infos + info_tr)),
+            "rel_kkt_max": max(i.rel_kkt for i in warm_infos),
+            "training": {"data_s": t_data, "train_s": t_train, "loss_first": float(losses[0]),
+                         "loss_last": float(losses[-1])},
+            "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(xh.nbytes + yh.nbytes)},
+            "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -344,6 +548,8 @@ def main():
     args.gpus = world if world > 1 else args.gpus
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "family_ws":
+        run_family_ws(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -321,16 +321,24 @@ def pdqp_create_family(count, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_co
 
 def family_from_base(base, C, B, device=False, stream=None):
     """A family handle from a base instance (n, m, m_eq, Q, A, l, u; scipy CSR)
-    and per-member rows C [count x n], B [count x m]."""
+    and per-member rows C [count x n], B [count x m] (numpy, or torch CUDA
+    float64 tensors, which put the whole call on device pointers)."""
+    device = device or _is_torch_cuda(C)
     arrays = [base.Q.indptr, base.Q.indices, base.Q.data, base.A.indptr, base.A.indices, base.A.data,
-              C, B, base.l, base.u]
-    dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 4
+              base.l, base.u]
+    dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 2
     arrays = [np.ascontiguousarray(a, dtype=t) for a, t in zip(arrays, dtypes)]
     if device:
         import torch
         arrays = [torch.from_numpy(a).cuda() for a in arrays]
+        C = C if _is_torch_cuda(C) else torch.from_numpy(np.ascontiguousarray(C, dtype=np.float64)).cuda()
+        B = B if _is_torch_cuda(B) else torch.from_numpy(np.ascontiguousarray(B, dtype=np.float64)).cuda()
         torch.cuda.synchronize()
-    return pdqp_create_family(C.shape[0], base.n, base.m, base.m_eq, *arrays, stream=stream)
+    else:
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+    return pdqp_create_family(C.shape[0], base.n, base.m, base.m_eq, *arrays[:6], C, B, *arrays[6:],
+                              stream=stream)
 
 
 def pdqp_batch_count(h) -> int:
