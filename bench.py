@@ -52,11 +52,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 256, 512])
     ap.add_argument("--workload", default="large_sparse_qp",
-                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws"],
+                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws", "gemm"],
                     help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
                          "of horizon 10..100 in one batched handle; random_sparse_qp: n=1000; "
                          "family_ws: held-out members of the n=2e4 family solved in one handle from the "
-                         "learned warm start (network trained first on --train solver outputs)")
+                         "learned warm start (network trained first on --train solver outputs); "
+                         "gemm: the tensor-core BF16 GEMM alone, --gemm-size^3 (and the network's shapes)")
+    ap.add_argument("--gemm-size", type=int, default=8192)
     ap.add_argument("--batch", type=int, default=None,
                     help="instances per step (mpc_batch: 4096, family_ws: 1024)")
     ap.add_argument("--train", type=int, default=4096, help="family_ws: training solves")
@@ -191,15 +193,16 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------------- ours
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary for this kernel and
+    workload, if it was taken on the current kernel source; else None."""
     if not os.path.exists(TRAFFIC_TXT):
         return None
     sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
     for line in open(TRAFFIC_TXT):
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[3] == sha:
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload \
+                and parts[3] == sha:
             return float(parts[2])
     return None
 
@@ -333,7 +336,9 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roof.update({"kernel": kname, "avg_launch_us": avg_s * 1e6, "launches": d["launches"],
-                 "algorithmic_bytes_per_launch": d["bytes"], "traffic": traffic_for(kname)})
+                 "algorithmic_bytes_per_launch": d["bytes"],
+                 "traffic": traffic_for(kname, f"large_sparse_qp_n1e6_{args.precision}")
+                 if args.workload == "large_sparse_qp" and args.n == 1_000_000 else None})
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms_max / args.steps, "higher_is_better": True,
@@ -514,7 +519,7 @@ def run_family_ws(args, world, rank, local):
     roof = {"bound": "hbm", "achieved": d["bytes"] / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
             "frac": d["bytes"] / avg_s / 1e9 / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
             "kernel": kname, "avg_launch_us": avg_s * 1e6, "launches": d["launches"],
-            "algorithmic_bytes_per_launch": d["bytes"], "traffic": traffic_for(kname),
+            "algorithmic_bytes_per_launch": d["bytes"], "traffic": None,
             "note": "algorithmic bytes count every member's rows at every launch; members that finished skip theirs"}
     it = lambda infos: {"mean": float(np.mean([i.iterations for i in infos])),
                         "max": int(max(i.iterations for i in infos))}
@@ -542,6 +547,57 @@ def run_family_ws(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_gemm(args, world, rank, local):
+    """The tcgen05 BF16 GEMM alone: D = A B' (float32 out) on resident bf16
+    operands, against the measured cuBLAS bf16 rate."""
+    import torch
+    from paper_2311_07710_gb300 import pdqp
+
+    pdqp.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    peaks = json.load(open(PEAKS_JSON)) if os.path.exists(PEAKS_JSON) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    S = args.gemm_size
+    shapes = [(S, S, S), (512, 30000, 1024), (30000, 1024, 512), (512, 1024, 30000), (1024, 1024, 30000)]
+    g = torch.Generator(device=dev).manual_seed(rank)
+    results = []
+    for (M, N, K) in shapes:
+        A = torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device=dev, generator=g).to(torch.bfloat16)
+        D = torch.empty(M, N, device=dev, dtype=torch.float32)
+        sp = pdqp.pdqp_gemm_bf16_splits(M, N, K, 0)
+        ws = torch.empty(max(sp, 1) * M * N if sp > 1 else 1, device=dev, dtype=torch.float32)
+        for _ in range(args.warmup):
+            pdqp.pdqp_gemm_bf16(A, B, D_f32=D, workspace=ws, stream=stream)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pdqp.pdqp_gemm_bf16(A, B, D_f32=D, workspace=ws, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        assert pdqp.pdqp_gemm_bf16_check(stream) == 0
+        ms = ev0.elapsed_time(ev1) / args.steps
+        tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
+        results.append({"M": M, "N": N, "K": K, "splits": sp, "ms": ms, "tflops": tf, "frac": tf / peak})
+        del A, B, D, ws
+    top = results[0]
+    line = {"metric": "tensor-core BF16 GEMM TFLOP/s (warm-start network kernels)", "value": top["tflops"],
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": top["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 in, f32 accumulate", "data": "synthetic (torch.randn)",
+            "config": {"workload": f"D[{S}x{S}] = A B' with K={S}, float32 output",
+                       "l2": "operands 128 MiB each at 8192, larger than L2 with the output"},
+            "roofline": {"bound": "tensor", "achieved": top["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": top["frac"], "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
+                         "kernel": "k_gemm_tn", "traffic": None},
+            "shapes": results, "gpu_launches": args.steps * sum(1 + (r["splits"] > 1) for r in results)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -550,6 +606,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "family_ws":
         run_family_ws(args, world, rank, local)
+    elif args.workload == "gemm":
+        run_gemm(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
