@@ -553,6 +553,8 @@ Stack stack_instances(int count, const InstanceIn* ins, int mem, cudaStream_t s)
       }
       I.bA1 = (int)S.ablk.size() - 1;
     }
+    I.cP0 = i == 0 ? 0 : S.insts[i - 1].cP0 + kkt_chunks(S.insts[i - 1].bP0, S.insts[i - 1].bP1);
+    I.cA0 = i == 0 ? 0 : S.insts[i - 1].cA0 + kkt_chunks(S.insts[i - 1].bA0, S.insts[i - 1].bA1);
     S.hc.insert(S.hc.end(), c.begin(), c.end());
     S.hl.insert(S.hl.end(), l.begin(), l.end());
     S.hu.insert(S.hu.end(), u.begin(), u.end());
@@ -573,6 +575,14 @@ void begin_work(pdqp_problem* h, int64_t N, int64_t M, int m_eq, int count, cons
   w.m_eq = m_eq;
   w.count = count;
   w.inst_host = insts;
+  w.nchunk_m = w.nchunk_n = w.maxchunk_m = w.maxchunk_n = 0;
+  for (const Inst& I : insts) {
+    const int cn = kkt_chunks(I.bP0, I.bP1), cm = kkt_chunks(I.bA0, I.bA1);
+    w.nchunk_n += cn;
+    w.nchunk_m += cm;
+    w.maxchunk_n = std::max(w.maxchunk_n, cn);
+    w.maxchunk_m = std::max(w.maxchunk_m, cm);
+  }
   int dev = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&w.num_sms, cudaDevAttrMultiProcessorCount, dev));
@@ -626,6 +636,8 @@ void alloc_work(pdqp_problem* h, cudaStream_t s) {
   w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
   w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
   w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
+  w.cpart_m = dalloc<double>(h, (size_t)9 * std::max(w.nchunk_m, 1));
+  w.cpart_n = dalloc<double>(h, (size_t)15 * std::max(w.nchunk_n, 1));
   w.st = dalloc<DevState>(h, count);
   w.bst = dalloc<BatchState>(h, 1);
   w.stage_n = dalloc<double>(h, n); w.stage_m = dalloc<double>(h, m);
@@ -784,6 +796,8 @@ pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, c
       I.bP1 = (i + 1) * nbP;
       I.bA0 = i * nbA;
       I.bA1 = (i + 1) * nbA;
+      I.cP0 = i * kkt_chunks(0, nbP);
+      I.cA0 = i * kkt_chunks(0, nbA);
     }
     h = new pdqp_problem();
     const long long N = count * n_t, M = count * m_t;

@@ -55,7 +55,11 @@ struct Inst {
   int xoff, yoff;        // first variable / row of the instance
   int bP0, bP1;          // row blocks of P
   int bA0, bA1;          // row blocks of A
+  int cP0, cA0;          // first chunk of KKT_CHUNK row blocks (P, A)
 };
+
+constexpr int KKT_CHUNK = 32;   // row blocks per chunk of the relKKT partial sums
+inline __host__ __device__ int kkt_chunks(int b0, int b1) { return (b1 - b0 + KKT_CHUNK - 1) / KKT_CHUNK; }
 
 // Batch-wide counters read by the host between chunks.
 struct BatchState {
@@ -90,7 +94,13 @@ __device__ __forceinline__ T group_sum(T s) {
 }
 
 // NaN-propagating max.
-__device__ __forceinline__ double nmax(double a, double b) { return (b > a || b != b) ? b : a; }
+// Max of two non-negative doubles (NaN-propagating for NaNs with a clear sign
+// bit, as fabs leaves them): for such values the order of the bit patterns as
+// signed 64-bit integers is the order of the doubles, +inf < NaN, so the max
+// runs on the integer pipes instead of the (slow) float64 ones.
+__device__ __forceinline__ double nmax(double a, double b) {
+  return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
 
 // Block reduction of NF fields (sum or NaN-propagating max per field); the
 // result is valid in thread 0.  blockDim.x must be a multiple of 32, <= 1024.

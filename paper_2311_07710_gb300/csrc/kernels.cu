@@ -34,6 +34,12 @@ static inline void launch(void (*kern)(KArgs...), int grid, int block, size_t sm
   kern<<<grid, block, smem, s>>>(args...);
   ++g_launches;
 }
+template <typename... KArgs, typename... Args>
+static inline void launch(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args... args) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+  kern<<<grid, block, smem, s>>>(args...);
+  ++g_launches;
+}
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -892,48 +898,48 @@ __device__ void reduce_kkt_blocks(const double* __restrict__ pm, int nbm, int bm
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(BNT) k_scale_norms(BCsr<double> M, const double* __restrict__ d, int doff,
                                                      int dcol_off, double* __restrict__ nu, int kind) {
-  __shared__ double av[BNNZ];
-  __shared__ double dc[BNNZ];
+  // row norm of (D M D)_r = d_r * norm_j(|m_rj| d_j): the column factor is
+  // applied per nonzero, the row factor once per row
+  __shared__ double pv[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
   const int r0 = M.blk[blockIdx.x], r1 = M.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = M.rp[r0];
   const int ne = M.rp[r1] - e0;
-  auto take = [&](double acc, double v) {
-    return kind == 0 ? fmax(acc, v) : (kind == 1 ? acc + v * v : acc + v);
+  auto take = [&](double acc, double v) {   // v >= 0
+    return kind == 0 ? nmax(acc, v) : (kind == 1 ? fma(v, v, acc) : acc + v);
   };
+  auto finish = [&](double acc, double dr) { return kind == 1 ? sqrt(acc) * dr : acc * dr; };
   if (ne <= BNNZ) {
 #pragma unroll
     for (int k = 0; k < BEPT; ++k) {
       const int e = tid + k * BNT;
-      if (e < ne) { av[e] = fabs(M.val[e0 + e]); dc[e] = d[dcol_off + M.col[e0 + e]]; }
+      if (e < ne) pv[e] = fabs(M.val[e0 + e]) * d[dcol_off + M.col[e0 + e]];
     }
     for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
     __syncthreads();
     for (int t = tid; t < nr; t += BNT) {
-      const double dr = d[doff + r0 + t];
       double acc = 0.0;
-      for (int e = srp[t]; e < srp[t + 1]; ++e) acc = take(acc, (av[e] * dr) * dc[e]);
-      nu[doff + r0 + t] = kind == 1 ? sqrt(acc) : acc;
+      for (int e = srp[t]; e < srp[t + 1]; ++e) acc = take(acc, pv[e]);
+      nu[doff + r0 + t] = finish(acc, d[doff + r0 + t]);
     }
   } else {
-    const double dr = d[doff + r0];
     double acc = 0.0;
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) acc = take(acc, (fabs(M.val[e]) * dr) * d[dcol_off + M.col[e]]);
+    for (int e = e0 + tid; e < e0 + ne; e += BNT) acc = take(acc, fabs(M.val[e]) * d[dcol_off + M.col[e]]);
     if (kind == 0) {
       __shared__ double sh[BNT];
       sh[tid] = acc;
       __syncthreads();
       for (int o = BNT / 2; o > 0; o >>= 1) {
-        if (tid < o) sh[tid] = fmax(sh[tid], sh[tid + o]);
+        if (tid < o) sh[tid] = nmax(sh[tid], sh[tid + o]);
         __syncthreads();
       }
       acc = sh[0];
     } else {
       acc = block_sum(acc);
     }
-    if (tid == 0) nu[doff + r0] = kind == 1 ? sqrt(acc) : acc;
+    if (tid == 0) nu[doff + r0] = finish(acc, d[doff + r0]);
   }
 }
 
@@ -1157,47 +1163,72 @@ __global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V
   if (threadIdx.x == 0) { part[blockIdx.x] = f[0]; part[(size_t)a.nblkP + blockIdx.x] = f[1]; }
 }
 
-// Number of eigenvalues of the k x k tridiagonal (al, be) below x: the sign
-// changes of the Sturm sequence p_0 = 1, p_i = (al_i - x) p_{i-1} - be_{i-1}^2 p_{i-2}
-// (p_i = det(T_i - x I)), rescaled to stay in range; a zero p_i counts as a
-// change.  Division free.
-__device__ int sturm_count(const double* __restrict__ al, const double* __restrict__ be, int k, double x) {
+// Number of eigenvalues of the k x k tridiagonal (al, be2 = squared betas)
+// below x: the sign changes of the Sturm sequence p_0 = 1,
+// p_i = (al_i - x) p_{i-1} - be_{i-1}^2 p_{i-2} (p_i = det(T_i - x I)); a zero p_i
+// takes the sign opposite to p_{i-1}.  Division free, three float64 operations
+// per step: signs, zeros and the range check (rescale both terms by 2^-/+500
+// when |p_i| leaves [2^-500, 2^500]) work on the bits.
+__device__ __forceinline__ int sturm_count(const double* __restrict__ al, const double* __restrict__ be2, int k,
+                                           double x) {
   double pm = 1.0, pc = al[0] - x;
-  if (pc == 0.0) pc = -1e-300;
-  int c = pc < 0.0 ? 1 : 0;
+  long long bc = __double_as_longlong(pc);
+  if ((bc << 1) == 0) { pc = -1e-300; bc = __double_as_longlong(pc); }
+  int c = (int)((unsigned long long)bc >> 63);
   for (int i = 1; i < k; ++i) {
-    double pn = (al[i] - x) * pc - (be[i - 1] * be[i - 1]) * pm;
-    if (pn == 0.0) pn = pc > 0.0 ? -1e-300 : 1e-300;
-    if ((pn < 0.0) != (pc < 0.0)) ++c;
+    double pn = fma(al[i] - x, pc, -be2[i - 1] * pm);
+    long long bn = __double_as_longlong(pn);
+    if ((bn << 1) == 0) {
+      pn = bc < 0 ? 1e-300 : -1e-300;
+      bn = __double_as_longlong(pn);
+    }
+    c += (int)((unsigned long long)(bn ^ bc) >> 63);
     pm = pc;
     pc = pn;
-    const double a = fabs(pc);
-    if (a > 1e150) { pc *= 1e-150; pm *= 1e-150; }
-    else if (a < 1e-150) { pc *= 1e150; pm *= 1e150; }
+    bc = bn;
+    const int ex = (int)((bn >> 52) & 0x7FF);
+    if (ex > 1023 + 500 || ex < 1023 - 500) {
+      const double f = ex > 1023 ? 0x1p-500 : 0x1p500;
+      pc *= f;
+      pm *= f;
+      bc = __double_as_longlong(pc);
+    }
   }
   return c;
 }
 
-// lambda_max of the tridiagonal by 32-point multisection within one warp
-__device__ double tridiag_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be, int k) {
+// lambda_max of the k x k tridiagonal by multisection: the nw warps of the
+// calling group (warp index g in [0, nw)) test 32 nw points of the bracket per
+// round; `ballots` is shared memory for nw words.  All threads of the group get
+// the same result.  Stops when the bracket is within 4e-15 relative.
+__device__ double tridiag_max_eig(const double* __restrict__ al, const double* __restrict__ be,
+                                  const double* __restrict__ be2, int k, int g, int nw, unsigned* ballots, int bar_id,
+                                  int bar_threads) {
   const int lane = threadIdx.x & 31;
-  double lo = 1e300, hi = -1e300;
+  double lo = 1e300, hi = -1e300;   // Gershgorin bracket
   for (int i = 0; i < k; ++i) {
-    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < k - 1 ? fabs(be[i]) : 0.0);
+    const double r = (i > 0 ? be[i - 1] : 0.0) + (i < k - 1 ? be[i] : 0.0);
     lo = fmin(lo, al[i] - r);
     hi = fmax(hi, al[i] + r);
   }
   hi += 1e-300 + fabs(hi) * 1e-15;
-  for (int round = 0; round < 12; ++round) {
-    const double step = (hi - lo) / 33.0;
-    const double x = lo + step * (double)(lane + 1);
-    const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be, k, x) < k);   // lambda_max >= x
-    if (ge == 0u) {
+  const int npts = 32 * nw;
+  for (int round = 0; round < 16 && hi - lo > 4e-15 * fabs(hi); ++round) {
+    const double step = (hi - lo) / (double)(npts + 1);
+    const int pt = g * 32 + lane;
+    const double x = lo + step * (double)(pt + 1);
+    const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be2, k, x) < k);   // lambda_max >= x
+    if (lane == 0) ballots[g] = ge;
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(bar_threads) : "memory");
+    int t = -1;   // largest point with lambda_max >= x
+    for (int w = nw - 1; w >= 0 && t < 0; --w)
+      if (ballots[w]) t = w * 32 + 31 - __clz(ballots[w]);
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(bar_threads) : "memory");
+    if (t < 0) {
       hi = lo + step;
     } else {
-      const int t = 31 - __clz(ge);
       const double nlo = lo + step * (double)(t + 1);
-      hi = t == 31 ? hi : lo + step * (double)(t + 2);
+      hi = t == npts - 1 ? hi : lo + step * (double)(t + 2);
       lo = nlo;
     }
   }
@@ -1205,7 +1236,7 @@ __device__ double tridiag_max_eig_warp(const double* __restrict__ al, const doub
 }
 
 // one CUDA block (256 threads) per instance: beta, theta = lambda_max(T_k)
-// (warp 0: A'A, warp 1: Q), stop test
+// (A'A and Q: four warps each, or all eight when one operator is done), stop test
 __global__ void __launch_bounds__(256) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
                                                 int max_steps) {
   const int i = blockIdx.x;
@@ -1218,25 +1249,38 @@ __global__ void __launch_bounds__(256) k_lz_beta(LzArgs a, const double* __restr
   block_reduce<2>(f, is_max);
   __shared__ double beta[2];
   __shared__ int done_in[2];
+  __shared__ double s_al[2][LZ_MAX], s_be[2][LZ_MAX], s_be2[2][LZ_MAX];
+  __shared__ unsigned ballots[2][8];
+  const int k = st.pi_iters + 1;                  // alphas 0..k-1, betas 0..k-2 form T_k
   if (threadIdx.x == 0) {
     beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]);
     done_in[0] = st.pi_done[0]; done_in[1] = st.pi_done[1];
   }
-  __syncthreads();
-  const int k = st.pi_iters + 1;                  // alphas 0..k-1, betas 0..k-2 form T_k
-  const int o = threadIdx.x >> 5;
-  if (o < 2 && !done_in[o]) {                     // warp-uniform
-    const double theta = tridiag_max_eig_warp(lz_al(a, i, o), lz_be(a, i, o), k);
-    if ((threadIdx.x & 31) == 0) {
-      const double b = beta[o];
-      st.pi_lam[o] = theta;
-      if (fabs(theta - st.pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
-        st.pi_done[o] = 1;
-      } else {
-        lz_be(a, i, o)[k - 1] = b;
-        st.pi_lam_prev[o] = theta;
-        st.pi_inv_norm[o] = 1.0 / b;
+  for (int o = 0; o < 2; ++o)
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      s_al[o][t] = lz_al(a, i, o)[t];
+      if (t < k - 1) {
+        const double bb = lz_be(a, i, o)[t];
+        s_be[o][t] = fabs(bb);
+        s_be2[o][t] = bb * bb;
       }
+    }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  const bool both = !done_in[0] && !done_in[1];
+  // operator of this warp and its group: both active -> warps 0-3 A'A, 4-7 Q
+  const int o = both ? (warp >> 2) : (done_in[0] ? 1 : 0);
+  const int nw = both ? 4 : 8, g = both ? (warp & 3) : warp;
+  const double theta = tridiag_max_eig(s_al[o], s_be[o], s_be2[o], k, g, nw, ballots[o], 1 + o, 32 * nw);
+  if (g == 0 && (threadIdx.x & 31) == 0) {
+    const double b = beta[o];
+    st.pi_lam[o] = theta;
+    if (fabs(theta - st.pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
+      st.pi_done[o] = 1;
+    } else {
+      lz_be(a, i, o)[k - 1] = b;
+      st.pi_lam_prev[o] = theta;
+      st.pi_inv_norm[o] = 1.0 / b;
     }
   }
   __syncthreads();
@@ -1391,6 +1435,50 @@ __device__ void fill_steps_block(const DevState& S, const SolveParams& p, StepEn
 __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
                                long long chunk_len);
 
+// Chunk sums of the relKKT block partials: CUDA block (i, c) reduces chunk c
+// of instance i -- KKT_CHUNK consecutive row blocks from the instance's first
+// -- for every field in a fixed order, so that a batch and a standalone solve
+// sum identically and the decision kernel reads tens of values, not thousands.
+__global__ void __launch_bounds__(32) k_kkt_chunks(const Inst* __restrict__ insts, const double* __restrict__ pm,
+                                                   int nbm, const double* __restrict__ pn, int nbn,
+                                                   double* __restrict__ cm, int ncm, double* __restrict__ cn,
+                                                   int ncn) {
+  const Inst in = insts[blockIdx.x];
+  const int lane = threadIdx.x, c = blockIdx.y;
+  const int bp = in.bP0 + c * KKT_CHUNK;
+  if (bp < in.bP1) {
+    const bool is_max[15] = {true, true, true, false, false, false, false,
+                             true, true, true, false, false, false, false, true};
+    const int b = bp + lane;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      double v = b < in.bP1 ? pn[(size_t)k * nbn + b] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max[k] ? nmax(v, t) : v + t;
+      }
+      if (lane == 0) cn[(size_t)k * ncn + in.cP0 + c] = v;
+    }
+  }
+  const int ba = in.bA0 + c * KKT_CHUNK;
+  if (in.m > 0 && ba < in.bA1) {
+    const bool is_max[9] = {true, true, false, false, true, true, false, false, true};
+    const int b = ba + lane;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double v = b < in.bA1 ? pm[(size_t)k * nbm + b] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max[k] ? nmax(v, t) : v + t;
+      }
+      if (lane == 0) cm[(size_t)k * ncm + in.cA0 + c] = v;
+    }
+  }
+}
+
+
 // mode 0: evaluate z^{0,0} (anchor, maybe already optimal); mode 1: a check
 // after `chunk_len` more iterations (Section 6 restart rule, termination
 // eq. (terminate), iteration limit).
@@ -1405,7 +1493,9 @@ __global__ void __launch_bounds__(512) k_decide(DevState* __restrict__ sts, cons
   if (mode == 1 && st->status != ST_RUNNING) return;     // uniform
   const Inst in = insts[i];
   __shared__ double F[24];
-  reduce_kkt_blocks(pm, nbm, in.m > 0 ? in.bA0 : 0, in.m > 0 ? in.bA1 : 0, pn, nbn, in.bP0, in.bP1, F);
+  // pm / pn hold the chunk sums of k_kkt_chunks
+  reduce_kkt_blocks(pm, nbm, in.cA0, in.m > 0 ? in.cA0 + kkt_chunks(in.bA0, in.bA1) : in.cA0, pn, nbn, in.cP0,
+                    in.cP0 + kkt_chunks(in.bP0, in.bP1), F);
   if (threadIdx.x == 0) decide_thread0(st, F, p, mode, chunk_len);
   __syncthreads();
   if (st->status == ST_RUNNING) fill_steps_block(*st, p, tabs + (size_t)i * C);
@@ -1888,8 +1978,14 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
   }
   if (w.m > 0) launch(k_kkt_m<2>, w.A.nblk, BNT, 0, s, a);
   launch(k_kkt_n<2>, w.P.nblk, BNT, 0, s, a);
-  launch(k_decide, w.count, 512, 0, s, w.st, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
-         (const double*)w.part_n, w.P.nblk, w.tab, w.tab_stride, p, mode, chunk_len);
+  {
+    const dim3 grid(w.count, std::max(w.maxchunk_n, w.maxchunk_m));
+    launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
+           (const double*)w.part_n, w.P.nblk, w.cpart_m, std::max(w.nchunk_m, 1), w.cpart_n, std::max(w.nchunk_n, 1));
+  }
+  launch(k_decide, w.count, 512, 0, s, w.st, (const Inst*)w.inst, (const double*)w.cpart_m,
+         std::max(w.nchunk_m, 1), (const double*)w.cpart_n, std::max(w.nchunk_n, 1), w.tab, w.tab_stride, p, mode,
+         chunk_len);
   if (mixed) {
     launch(k_mixed_rebase, grid_v, 256, 0, s, mixed_args(w), mode == 0 ? 1 : 0);
   } else if (mode == 1) {

@@ -112,6 +112,9 @@ struct Work {
   double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
   double *part_m = nullptr;  // [9][A.nblk]  field-major partial sums of the row-block kernels
   double *part_n = nullptr;  // [15][P.nblk]
+  double *cpart_m = nullptr; // [9][nchunk_m]  chunk sums of part_m (KKT_CHUNK blocks each)
+  double *cpart_n = nullptr; // [15][nchunk_n]
+  int nchunk_m = 0, nchunk_n = 0, maxchunk_m = 0, maxchunk_n = 0;
   StepEntry* tab = nullptr;  // [count][tab_stride]
   DevState* st = nullptr;    // [count]
   DevState* st_host = nullptr;   // pinned mirror [count]
