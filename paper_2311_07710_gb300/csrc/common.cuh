@@ -102,6 +102,41 @@ __device__ __forceinline__ double nmax(double a, double b) {
   return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
 }
 
+// Block reduction of NF per-thread fields through shared-memory scratch `sh`
+// (NF * NT doubles; it may alias data the block no longer reads).  Field f is
+// a max (bit f of max_mask) or a sum.  Warp w folds fields w, w + NT/32, ...:
+// each lane combines the NT/32 values of its column in a fixed order, then a
+// five-level shuffle tree.  The result is valid in thread 0.  This takes far
+// fewer float64 operations than a shuffle tree per warp and field.
+template <int NF, int NT>
+__device__ __forceinline__ void block_reduce_smem(double (&v)[NF], unsigned max_mask, double* sh) {
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < NF; ++f) sh[f * NT + threadIdx.x] = v[f];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int f = threadIdx.x >> 5; f < NF; f += NT / 32) {
+    const bool mx = (max_mask >> f) & 1u;
+    double t = sh[f * NT + lane];
+#pragma unroll
+    for (int k = 1; k < NT / 32; ++k) {
+      const double x = sh[f * NT + lane + 32 * k];
+      t = mx ? nmax(t, x) : t + x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double x = __shfl_xor_sync(0xffffffffu, t, o);
+      t = mx ? nmax(t, x) : t + x;
+    }
+    if (lane == 0) sh[f * NT] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) v[f] = sh[f * NT];
+  }
+}
+
 // Block reduction of NF fields (sum or NaN-propagating max per field); the
 // result is valid in thread 0.  blockDim.x must be a multiple of 32, <= 1024.
 template <int NF>

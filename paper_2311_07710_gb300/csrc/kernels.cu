@@ -691,10 +691,16 @@ struct KktB {
   int r;
 };
 
+// Both kernels split the row phase into (iterate, row) work items so that a
+// block of 256 threads stays busy when it holds fewer than 256 rows, and reduce
+// their fields through the staging buffer once the rows are done.
 template <int NIT>
 __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
   // fields: it*4 + {0 max|viol|, 1 max|Ax|, 2 b'y, 3 |dy|^2}, 8: max|b|
-  __shared__ double prod[NIT][BNNZ];
+  // product staging, reused for the field reduction
+  constexpr int SZ = NIT * BNNZ > 9 * BNT ? NIT * BNNZ : 9 * BNT;
+  __shared__ double stage[SZ];
+  double(*prod)[BNNZ] = reinterpret_cast<double(*)[BNNZ]>(stage);
   __shared__ int srp[BROWS + 1];
   double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int tid = threadIdx.x;
@@ -703,22 +709,18 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
   const int nr = r1 - r0;
   const int e0 = a.A.rp[r0];
   const int ne = a.A.rp[r1] - e0;
-  auto row = [&](int r, const double* s) {
-    const double d1 = a.D1 ? a.D1[r] : 1.0, id1 = a.iD1 ? a.iD1[r] : 1.0;
+  auto row = [&](int r, int it, double s) {
     const double bi = a.b[r];
-#pragma unroll
-    for (int it = 0; it < NIT; ++it) {
-      if (a.prodAx[it]) a.prodAx[it][r] = s[it];
-      const double Ax = s[it] * id1;
-      const double viol = a.ineq[r] ? fmax(bi - Ax, 0.0) : fabs(Ax - bi);
-      f[it * 4 + 0] = nmax(f[it * 4 + 0], viol);
-      f[it * 4 + 1] = nmax(f[it * 4 + 1], fabs(Ax));
-      const double yt = a.y[it][r];
-      f[it * 4 + 2] += bi * (d1 * yt);
-      const double dy = a.ay ? yt - a.ay[r] : 0.0;
-      f[it * 4 + 3] += dy * dy;
-    }
-    f[8] = nmax(f[8], fabs(bi));
+    if (a.prodAx[it]) a.prodAx[it][r] = s;
+    const double Ax = s * (a.iD1 ? a.iD1[r] : 1.0);
+    const double viol = a.ineq[r] ? fmax(bi - Ax, 0.0) : fabs(Ax - bi);
+    f[it * 4 + 0] = nmax(f[it * 4 + 0], viol);
+    f[it * 4 + 1] = nmax(f[it * 4 + 1], fabs(Ax));
+    const double yt = a.y[it][r];
+    f[it * 4 + 2] += bi * ((a.D1 ? a.D1[r] : 1.0) * yt);
+    const double dy = a.ay ? yt - a.ay[r] : 0.0;
+    f[it * 4 + 3] += dy * dy;
+    if (it == 0) f[8] = nmax(f[8], fabs(bi));
   };
   if (ne <= BNNZ) {
     int ci[BEPT];
@@ -737,14 +739,11 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
         for (int it = 0; it < NIT; ++it) prod[it][e] = vv[k] * __ldg(a.x[it] + ci[k]);
     }
     __syncthreads();
-    for (int t = tid; t < nr; t += BNT) {
-      double s[NIT];
-#pragma unroll
-      for (int it = 0; it < NIT; ++it) {
-        s[it] = 0.0;
-        for (int e = srp[t]; e < srp[t + 1]; ++e) s[it] += prod[it][e];
-      }
-      row(r0 + t, s);
+    for (int q = tid; q < nr * NIT; q += BNT) {
+      const int it = q / nr, t = q - it * nr;
+      double s = 0.0;
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[it][e];
+      row(r0 + t, it, s);
     }
   } else {
     double s[NIT];
@@ -758,10 +757,10 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
     }
 #pragma unroll
     for (int it = 0; it < NIT; ++it) s[it] = block_sum(s[it]);
-    if (tid == 0) row(r0, s);
+    if (tid == 0)
+      for (int it = 0; it < NIT; ++it) row(r0, it, s[it]);
   }
-  const bool is_max[9] = {true, true, false, false, true, true, false, false, true};
-  block_reduce<9>(f, is_max);
+  block_reduce_smem<9, BNT>(f, 0x133u, stage);
   if (tid == 0)
     for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
 }
@@ -770,7 +769,10 @@ template <int NIT>
 __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
   // fields (offset 9): it*7 + {0 max|res|, 1 max|Qx|, 2 max|A'y|, 3 x'Qx, 4 c'x,
   // 5 sum(l lam+ - u lam-), 6 |dx|^2}, 14: max|c|
-  __shared__ double prod[NIT][BNNZ];
+  // product staging, reused for the field reduction
+  constexpr int SZ = NIT * BNNZ > 15 * BNT ? NIT * BNNZ : 15 * BNT;
+  __shared__ double stage[SZ];
+  double(*prod)[BNNZ] = reinterpret_cast<double(*)[BNNZ]>(stage);
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
   double f[15];
@@ -783,30 +785,27 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
   const int e0 = a.P.rp[r0];
   const int ne = a.P.rp[r1] - e0;
   const int n = a.n;
-  auto row = [&](int r, const double* sq, const double* sa) {
-    const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
+  auto row = [&](int r, int it, double sq, double sa) {
     const double cj = a.c[r], lj = a.l[r], uj = a.u[r];
+    const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
+    const double sqt = sq + (a.F ? lr_row<double, double>(a.F, a.wlr + it * a.r, a.r, r) : 0.0);
+    if (a.prodQx[it]) { a.prodQx[it][r] = sqt; a.prodATy[it][r] = -sa; }
+    const double Qx = sqt * id2, ATy = -sa * id2;
+    const double xt = a.x[it][r];
+    const double xj = d2 * xt;
+    const double g = Qx + cj - ATy;
     const bool lf = isfinite(lj), uf = isfinite(uj);
-#pragma unroll
-    for (int it = 0; it < NIT; ++it) {
-      const double sqt = sq[it] + (a.F ? lr_row<double, double>(a.F, a.wlr + it * a.r, a.r, r) : 0.0);
-      if (a.prodQx[it]) { a.prodQx[it][r] = sqt; a.prodATy[it][r] = -sa[it]; }
-      const double Qx = sqt * id2, ATy = -sa[it] * id2;
-      const double xt = a.x[it][r];
-      const double xj = d2 * xt;
-      const double g = Qx + cj - ATy;
-      const double lam = (lf && uf) ? g : (lf ? fmax(g, 0.0) : (uf ? fmin(g, 0.0) : 0.0));
-      double* fi = f + it * 7;
-      fi[0] = nmax(fi[0], fabs(g - lam));
-      fi[1] = nmax(fi[1], fabs(Qx));
-      fi[2] = nmax(fi[2], fabs(ATy));
-      fi[3] += xj * Qx;
-      fi[4] += cj * xj;
-      fi[5] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
-      const double dx = a.ax ? xt - a.ax[r] : 0.0;
-      fi[6] += dx * dx;
-    }
-    f[14] = nmax(f[14], fabs(cj));
+    const double lam = (lf && uf) ? g : (lf ? fmax(g, 0.0) : (uf ? fmin(g, 0.0) : 0.0));
+    double* fi = f + it * 7;
+    fi[0] = nmax(fi[0], fabs(g - lam));
+    fi[1] = nmax(fi[1], fabs(Qx));
+    fi[2] = nmax(fi[2], fabs(ATy));
+    fi[3] += xj * Qx;
+    fi[4] += cj * xj;
+    fi[5] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
+    const double dx = a.ax ? xt - a.ax[r] : 0.0;
+    fi[6] += dx * dx;
+    if (it == 0) f[14] = nmax(f[14], fabs(cj));
   };
   if (ne <= BNNZ) {
     int ci[BEPT];
@@ -829,15 +828,12 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
       }
     }
     __syncthreads();
-    for (int t = tid; t < nr; t += BNT) {
-      double sq[NIT], sa[NIT];
-#pragma unroll
-      for (int it = 0; it < NIT; ++it) {
-        sq[it] = 0.0; sa[it] = 0.0;
-        for (int e = srp[t]; e < ssp[t]; ++e) sq[it] += prod[it][e];
-        for (int e = ssp[t]; e < srp[t + 1]; ++e) sa[it] += prod[it][e];
-      }
-      row(r0 + t, sq, sa);
+    for (int q = tid; q < nr * NIT; q += BNT) {
+      const int it = q / nr, t = q - it * nr;
+      double sq = 0.0, sa = 0.0;
+      for (int e = srp[t]; e < ssp[t]; ++e) sq += prod[it][e];
+      for (int e = ssp[t]; e < srp[t + 1]; ++e) sa += prod[it][e];
+      row(r0 + t, it, sq, sa);
     }
   } else {
     const int sp = a.P.split[r0];
@@ -855,11 +851,10 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
     }
 #pragma unroll
     for (int it = 0; it < NIT; ++it) { sq[it] = block_sum(sq[it]); sa[it] = block_sum(sa[it]); }
-    if (tid == 0) row(r0, sq, sa);
+    if (tid == 0)
+      for (int it = 0; it < NIT; ++it) row(r0, it, sq[it], sa[it]);
   }
-  const bool is_max[15] = {true, true, true, false, false, false, false,
-                           true, true, true, false, false, false, false, true};
-  block_reduce<15>(f, is_max);
+  block_reduce_smem<15, BNT>(f, 0x4387u, stage);
   if (tid == 0)
     for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
 }
@@ -1067,7 +1062,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, Lz
                                                                    V* __restrict__ wQ, double* __restrict__ part,
                                                                    const V* __restrict__ F,
                                                                    const double* __restrict__ wlr, int rk) {
-  __shared__ V prod[BNNZ];
+  __shared__ __align__(16) V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
   const DevState& st = la.st[la.blk_inst_P[blockIdx.x]];
@@ -1109,8 +1104,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, Lz
     w = block_sum(w);
     if (tid == 0) row(r0, q, w);
   }
-  const bool is_max[2] = {false, false};
-  block_reduce<2>(f, is_max);
+  static_assert(sizeof(V) * BNNZ >= 2 * NT * sizeof(double), "staging buffer too small for the reduction");
+  block_reduce_smem<2, NT>(f, 0u, reinterpret_cast<double*>(prod));
   if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)la.nblkP + blockIdx.x] = f[1]; }
 }
 
@@ -1158,8 +1153,8 @@ __global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V
       f[1] += v * v;
     }
   }
-  const bool is_max[2] = {false, false};
-  block_reduce<2>(f, is_max);
+  __shared__ double sh[2 * 256];
+  block_reduce_smem<2, 256>(f, 0u, sh);
   if (threadIdx.x == 0) { part[blockIdx.x] = f[0]; part[(size_t)a.nblkP + blockIdx.x] = f[1]; }
 }
 
