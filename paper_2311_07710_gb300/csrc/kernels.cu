@@ -262,27 +262,38 @@ __device__ void reduce_kkt_partials(const double* __restrict__ part, int nblk, d
 template <int NT, typename V, typename X>
 __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
                                                int r0, int nr, V* prod, int* srp) {
+  // two phases of EPT/2 loads and gathers each: half the registers of one
+  // phase of EPT, so that more blocks fit on an SM
   constexpr int EPT = BNNZ / NT;
+  constexpr int H = EPT / 2;
   const int tid = threadIdx.x;
-  int ci[EPT];
-  V vv[EPT];
-#pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int e = tid + k * NT;
-    if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
-  }
   for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int e = tid + k * NT;
-    if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
+  for (int h = 0; h < 2; ++h) {
+    int ci[H];
+    V vv[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int e = tid + (h * H + k) * NT;
+      if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int e = tid + (h * H + k) * NT;
+      if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
+    }
   }
 }
 
-// Occupancy target of the iteration kernels: NT = 512 threads with at most 32
-// registers (4 blocks, 2048 threads per SM), NT = 256 with at most 64 (4 blocks).
-template <int NT> struct MinBlocks { static constexpr int value = 4; };
-template <> struct MinBlocks<512> { static constexpr int value = 4; };
+// Occupancy target of the row-block kernels (blocks per SM).  They wait on
+// dependent gathers, so more resident warps hide more latency: with the
+// two-phase staging above, 256 threads of float data fit 32 registers without
+// spills (8 blocks, the whole SM: k_primal 97 -> 76 us, k_dual 67 -> 51 us at
+// n=1e6 against 4 blocks at 64 registers); the float64 kernels are bound by
+// the float64 pipes and gain nothing from 5 or 6 blocks, so they keep 64
+// registers (4); NT = 512 runs 4 blocks at 32 registers.
+template <typename V, int NT> struct MinBlocks { static constexpr int value = 4; };
+template <> struct MinBlocks<float, 256> { static constexpr int value = 8; };
 
 
 // ==========================================================================
@@ -400,7 +411,7 @@ __device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, 
 }
 
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_dual(DualB<V> a, int j) {
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a, int j) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -476,7 +487,7 @@ __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry&
 }
 
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_primal(PrimalB<V> a, int j) {
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_primal(PrimalB<V> a, int j) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -1029,7 +1040,7 @@ __device__ __forceinline__ double* lz_al(const LzArgs& a, int i, int o) { return
 __device__ __forceinline__ double* lz_be(const LzArgs& a, int i, int o) { return a.be + ((size_t)i * 2 + o) * LZ_MAX; }
 
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, LzArgs la, const V* __restrict__ vA,
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_m(BCsr<V> A, LzArgs la, const V* __restrict__ vA,
                                                                    V* __restrict__ wm) {
   if (la.st[la.blk_inst_A[blockIdx.x]].pi_done[0]) return;
   __shared__ V prod[BNNZ];
@@ -1057,7 +1068,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_m(BCsr<V> A, Lz
 
 // rows of P with input [v_Q ; w_m]: wA = A~'w_m, wQ = Q~ v_Q; partial v'w per row block
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_lz_n(BCsr<V> P, LzArgs la, const V* __restrict__ zin,
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_n(BCsr<V> P, LzArgs la, const V* __restrict__ zin,
                                                                    const V* __restrict__ vA, V* __restrict__ wA,
                                                                    V* __restrict__ wQ, double* __restrict__ part,
                                                                    const V* __restrict__ F,
