@@ -840,11 +840,387 @@ pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, c
   return h;
 }
 
+// ---------------------------------------------------------------- one problem, built on the device
+// pdqp_create of a single problem: the CSR input is copied to the device as
+// given, validated there, A is transposed by a column count, scan, scatter
+// and a per-column sort by row (the same A' as the stable counting sort of
+// the host path), and P = [Q | -A'] is assembled row by row.  Only the greedy
+// row blocks are formed on the host (from the row pointers), so the handle is
+// the one build_problem makes.
+enum : unsigned {
+  VE_RP = 1u, VE_COL = 2u, VE_ORDER = 4u, VE_VAL = 8u, VE_C = 16u, VE_BOUNDS = 32u, VE_B = 64u, VE_LONG = 128u
+};
+
+// (row pointers outside [0, nnz] or decreasing are flagged before any column
+// of their row is read)
+__global__ void k_validate_csr(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                               int rows, int cols, long long nnz, unsigned* __restrict__ err) {
+  unsigned e = 0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int a = rp[r], b = rp[r + 1];
+    if (a < 0 || b < a || b > nnz) { e |= VE_RP; continue; }
+    for (int k = a; k < b; ++k) {
+      const int c = col[k];
+      if (c < 0 || c >= cols) e |= VE_COL;
+      if (k > a && c <= col[k - 1]) e |= VE_ORDER;
+      if (!isfinite(val[k])) e |= VE_VAL;
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_validate_vecs(const double* __restrict__ c, const double* __restrict__ l, const double* __restrict__ u,
+                                int n, const double* __restrict__ b, int m, unsigned* __restrict__ err) {
+  unsigned e = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n || i < m; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (!isfinite(c[i])) e |= VE_C;
+      const double lo = l[i], hi = u[i];
+      if (isnan(lo) || isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY) e |= VE_BOUNDS;
+    }
+    if (i < m && !isfinite(b[i])) e |= VE_B;
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_col_count(const int* __restrict__ col, long long nnz, int* __restrict__ cnt) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[k]], 1);
+}
+
+// exclusive scan of cnt[0..len) into out[0..len] (out[len] = total), three
+// phases: per-block scans of 1024 elements, a one-block scan of the block
+// totals, the offsets added back
+__global__ void __launch_bounds__(1024) k_scan_blocks(const int* __restrict__ in, int len, int* __restrict__ out,
+                                                      int* __restrict__ sums) {
+  __shared__ int sh[1024];
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  const int v = i < len ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < len) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == 1023) sums[blockIdx.x] = sh[1023];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ sums, int nb, int* __restrict__ total) {
+  __shared__ int sh[1024];
+  int carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) sums[i] = carry + sh[threadIdx.x] - v;
+    const int blk_total = sh[1023];
+    __syncthreads();
+    carry += blk_total;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int len, const int* __restrict__ sums, const int* __restrict__ total) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) out[i] += sums[i / 1024];
+  if (i == 0) out[len] = *total;
+}
+
+// scatter A's entries into the column segments of A' (order within a segment
+// decided by the atomics; sorted afterwards)
+__global__ void k_col_scatter(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                              int rows, const int* __restrict__ trp, int* __restrict__ cur, int* __restrict__ tcol,
+                              double* __restrict__ tval) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const int c = col[k];
+      const int p = trp[c] + atomicAdd(&cur[c], 1);
+      tcol[p] = r;
+      tval[p] = val[k];
+    }
+}
+
+// sort each segment of A' by row (insertion sort; segments longer than
+// SEG_MAX are flagged and the problem is built on the host instead)
+constexpr int SEG_MAX = 4096;
+__global__ void k_seg_sort(const int* __restrict__ trp, int segs, int* __restrict__ tcol, double* __restrict__ tval,
+                           unsigned* __restrict__ err) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < segs; j += gridDim.x * blockDim.x) {
+    const int a = trp[j], b = trp[j + 1];
+    if (b - a > SEG_MAX) { atomicOr(err, VE_LONG); continue; }
+    for (int k = a + 1; k < b; ++k) {
+      const int key = tcol[k];
+      const double v = tval[k];
+      int q = k - 1;
+      while (q >= a && tcol[q] > key) {
+        tcol[q + 1] = tcol[q];
+        tval[q + 1] = tval[q];
+        --q;
+      }
+      tcol[q + 1] = key;
+      tval[q + 1] = v;
+    }
+  }
+}
+
+__global__ void k_row_len(const int* __restrict__ qrp, const int* __restrict__ trp, int n, int* __restrict__ len) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) len[j] = (qrp[j + 1] - qrp[j]) + (trp[j + 1] - trp[j]);
+}
+
+// row j of P: Q's row (columns j'), then -A' row (columns n + i)
+__global__ void k_assemble_P(const int* __restrict__ qrp, const int* __restrict__ qcol, const double* __restrict__ qval,
+                             const int* __restrict__ trp, const int* __restrict__ tcol, const double* __restrict__ tval,
+                             int n, const int* __restrict__ prp, int* __restrict__ pcol, double* __restrict__ pval,
+                             int* __restrict__ split) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = warp; j < n; j += nw) {
+    const int p0 = prp[j], q0 = qrp[j], ql = qrp[j + 1] - q0, t0 = trp[j], tl = trp[j + 1] - t0;
+    for (int k = lane; k < ql; k += 32) {
+      pcol[p0 + k] = qcol[q0 + k];
+      pval[p0 + k] = qval[q0 + k];
+    }
+    for (int k = lane; k < tl; k += 32) {
+      pcol[p0 + ql + k] = n + tcol[t0 + k];
+      pval[p0 + ql + k] = -tval[t0 + k];
+    }
+    if (lane == 0) split[j] = p0 + ql;
+  }
+}
+
+__global__ void k_block_meta(const int* __restrict__ blk, int nblk, const int* __restrict__ rp, int* __restrict__ meta,
+                             int* __restrict__ binst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblk) return;
+  const int r0 = blk[b], r1 = blk[b + 1];
+  meta[4 * b + 0] = r0;
+  meta[4 * b + 1] = r1;
+  meta[4 * b + 2] = rp[r0];
+  meta[4 * b + 3] = rp[r1];
+  binst[b] = 0;
+}
+
+__global__ void k_single_rows(int n, int m, int m_eq, int* __restrict__ rinst_n, int* __restrict__ rinst_m,
+                              unsigned char* __restrict__ ineq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n || i < m; i += gridDim.x * blockDim.x) {
+    if (i < n) rinst_n[i] = 0;
+    if (i < m) {
+      rinst_m[i] = 0;
+      ineq[i] = i >= m_eq ? 1 : 0;
+    }
+  }
+}
+
+// device copy of a caller array (or the array itself when it is on the device)
+template <typename T>
+const T* on_device(pdqp_problem* h, const T* p, size_t count, int mem, std::vector<void*>& tmp, cudaStream_t s) {
+  if (mem == PDQP_MEM_DEVICE || count == 0) return p;
+  T* d = nullptr;
+  CK(cudaMalloc(&d, count * sizeof(T)));
+  tmp.push_back(d);
+  CK(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+struct TmpFree {
+  std::vector<void*> v;
+  ~TmpFree() {
+    for (void* p : v) cudaFree(p);
+  }
+};
+
+int grid_of(long long total, int threads = 256) {
+  return (int)std::max<long long>(1, std::min<long long>((total + threads - 1) / threads, 8192));
+}
+
+// exclusive scan on the device: out[0..len] from in[0..len)
+void device_scan(const int* in, int len, int* out, std::vector<void*>& tmp, cudaStream_t s) {
+  const int nb = std::max(1, (len + 1023) / 1024);
+  int *sums = nullptr, *total = nullptr;
+  CK(cudaMalloc(&sums, (size_t)nb * sizeof(int)));
+  tmp.push_back(sums);
+  CK(cudaMalloc(&total, sizeof(int)));
+  tmp.push_back(total);
+  k_scan_blocks<<<nb, 1024, 0, s>>>(in, len, out, sums);
+  k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, total);
+  k_scan_add<<<grid_of(std::max(len, 1)), 256, 0, s>>>(out, len, sums, total);
+  CK(cudaGetLastError());
+}
+
+// Returns nullptr when the problem needs the host path (a column of A longer
+// than SEG_MAX); throws Fail on invalid input.
+pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s) {
+  if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
+  if (in.n < 1 || in.m < 0 || in.m_eq < 0 || in.m_eq > in.m)
+    throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
+  if (!in.Q_rowptr || !in.c || !in.l || !in.u) throw Fail{PDQP_ERR_INVALID, "null Q_rowptr, c, l or u"};
+  if (in.m > 0 && (!in.A_rowptr || !in.b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
+  if (in.n > (1LL << 30) || in.m > (1LL << 30)) throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
+  for (auto pr : {(const void*)in.Q_rowptr, (const void*)in.Q_col, (const void*)in.Q_val, (const void*)in.A_rowptr,
+                  (const void*)in.A_col, (const void*)in.A_val, (const void*)in.c, (const void*)in.b,
+                  (const void*)in.l, (const void*)in.u})
+    check_space(pr, mem, "input array");
+  const int n = (int)in.n, m = (int)in.m;
+  // row pointers on the host (the greedy row blocks are formed there)
+  std::vector<int32_t> qrp = fetch(in.Q_rowptr, (size_t)n + 1, mem, s);
+  std::vector<int32_t> arp = m > 0 ? fetch(in.A_rowptr, (size_t)m + 1, mem, s) : std::vector<int32_t>(1, 0);
+  if (qrp[0] != 0) throw Fail{PDQP_ERR_INVALID, "Q: rowptr[0] != 0"};
+  if (arp[0] != 0) throw Fail{PDQP_ERR_INVALID, "A: rowptr[0] != 0"};
+  const long long nnzQ = qrp[n], nnzA = arp[m];
+  if (nnzQ < 0 || (nnzQ > 0 && (!in.Q_col || !in.Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
+  if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
+  if (nnzQ + nnzA > (long long)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
+  TmpFree tmp;
+  const int* dqrp = on_device(nullptr, in.Q_rowptr, (size_t)n + 1, mem, tmp.v, s);
+  const int* dqcol = on_device(nullptr, in.Q_col, (size_t)nnzQ, mem, tmp.v, s);
+  const double* dqval = on_device(nullptr, in.Q_val, (size_t)nnzQ, mem, tmp.v, s);
+  const int* darp = m > 0 ? on_device(nullptr, in.A_rowptr, (size_t)m + 1, mem, tmp.v, s) : nullptr;
+  const int* dacol = on_device(nullptr, in.A_col, (size_t)nnzA, mem, tmp.v, s);
+  const double* daval = on_device(nullptr, in.A_val, (size_t)nnzA, mem, tmp.v, s);
+  unsigned* derr = nullptr;
+  CK(cudaMalloc(&derr, sizeof(unsigned)));
+  tmp.v.push_back(derr);
+  CK(cudaMemsetAsync(derr, 0, sizeof(unsigned), s));
+
+  pdqp_problem* h = new pdqp_problem();
+  try {
+    Work& w = h->w;
+    // vectors straight into the handle
+    w.c = dalloc<double>(h, n); w.l = dalloc<double>(h, n); w.u = dalloc<double>(h, n); w.b = dalloc<double>(h, m);
+    const cudaMemcpyKind kind = mem == PDQP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(w.c, in.c, (size_t)n * sizeof(double), kind, s));
+    CK(cudaMemcpyAsync(w.l, in.l, (size_t)n * sizeof(double), kind, s));
+    CK(cudaMemcpyAsync(w.u, in.u, (size_t)n * sizeof(double), kind, s));
+    if (m > 0) CK(cudaMemcpyAsync(w.b, in.b, (size_t)m * sizeof(double), kind, s));
+    k_validate_csr<<<grid_of(n), 256, 0, s>>>(dqrp, dqcol, dqval, n, n, nnzQ, derr);
+    if (m > 0) k_validate_csr<<<grid_of(m), 256, 0, s>>>(darp, dacol, daval, m, n, nnzA, derr);
+    k_validate_vecs<<<grid_of(std::max(n, m)), 256, 0, s>>>(w.c, w.l, w.u, n, w.b, m, derr);
+    CK(cudaGetLastError());
+    unsigned herr = 0;
+    CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr & VE_RP) throw Fail{PDQP_ERR_INVALID, "Q or A: rowptr decreases"};
+    if (herr & VE_COL) throw Fail{PDQP_ERR_INVALID, "Q or A: column index out of range"};
+    if (herr & VE_ORDER) throw Fail{PDQP_ERR_INVALID, "Q or A: column indices not strictly increasing in a row"};
+    if (herr & VE_VAL) throw Fail{PDQP_ERR_INVALID, "Q or A: non-finite value"};
+    if (herr & VE_C) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
+    if (herr & VE_BOUNDS) throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
+    if (herr & VE_B) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
+    // A' by column count, scan, scatter, per-column sort
+    int *cnt = nullptr, *trp = nullptr, *cur = nullptr, *tcol = nullptr;
+    double* tval = nullptr;
+    CK(cudaMalloc(&cnt, (size_t)n * sizeof(int))); tmp.v.push_back(cnt);
+    CK(cudaMalloc(&trp, ((size_t)n + 1) * sizeof(int))); tmp.v.push_back(trp);
+    CK(cudaMalloc(&cur, (size_t)n * sizeof(int))); tmp.v.push_back(cur);
+    CK(cudaMalloc(&tcol, std::max<size_t>((size_t)nnzA, 1) * sizeof(int))); tmp.v.push_back(tcol);
+    CK(cudaMalloc(&tval, std::max<size_t>((size_t)nnzA, 1) * sizeof(double))); tmp.v.push_back(tval);
+    CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), s));
+    CK(cudaMemsetAsync(cur, 0, (size_t)n * sizeof(int), s));
+    if (nnzA > 0) k_col_count<<<grid_of(nnzA), 256, 0, s>>>(dacol, nnzA, cnt);
+    device_scan(cnt, n, trp, tmp.v, s);
+    if (nnzA > 0) {
+      k_col_scatter<<<grid_of(m), 256, 0, s>>>(darp, dacol, daval, m, trp, cur, tcol, tval);
+      k_seg_sort<<<grid_of(n), 256, 0, s>>>(trp, n, tcol, tval, derr);
+    }
+    // P = [Q | -A']
+    int* plen = cnt;   // reuse
+    k_row_len<<<grid_of(n), 256, 0, s>>>(dqrp, trp, n, plen);
+    const long long nnzP = nnzQ + nnzA;
+    w.P.rows = n;
+    w.P.nnz = nnzP;
+    w.P.rp = dalloc<int>(h, (size_t)n + 1 + 8);
+    w.P.col = dalloc<int>(h, (size_t)nnzP + 8);
+    w.P.val = dalloc<double>(h, (size_t)nnzP + 8);
+    w.P.sval = dalloc<double>(h, (size_t)nnzP + 8);
+    w.P.split = dalloc<int>(h, n);
+    CK(cudaMemsetAsync(w.P.rp, 0, ((size_t)n + 1 + 8) * sizeof(int), s));
+    CK(cudaMemsetAsync(w.P.col + nnzP, 0, 8 * sizeof(int), s));
+    CK(cudaMemsetAsync(w.P.val + nnzP, 0, 8 * sizeof(double), s));
+    CK(cudaMemsetAsync(w.P.sval, 0, ((size_t)nnzP + 8) * sizeof(double), s));
+    device_scan(plen, n, w.P.rp, tmp.v, s);
+    k_assemble_P<<<grid_of((long long)n * 32), 256, 0, s>>>(dqrp, dqcol, dqval, trp, tcol, tval, n, w.P.rp, w.P.col,
+                                                            w.P.val, w.P.split);
+    // A as given
+    w.A.rows = m;
+    w.A.nnz = nnzA;
+    w.A.rp = dalloc<int>(h, (size_t)m + 1 + 8);
+    w.A.col = dalloc<int>(h, (size_t)nnzA + 8);
+    w.A.val = dalloc<double>(h, (size_t)nnzA + 8);
+    w.A.sval = dalloc<double>(h, (size_t)nnzA + 8);
+    CK(cudaMemsetAsync(w.A.rp, 0, ((size_t)m + 1 + 8) * sizeof(int), s));
+    CK(cudaMemsetAsync(w.A.col, 0, ((size_t)nnzA + 8) * sizeof(int), s));
+    CK(cudaMemsetAsync(w.A.val, 0, ((size_t)nnzA + 8) * sizeof(double), s));
+    CK(cudaMemsetAsync(w.A.sval, 0, ((size_t)nnzA + 8) * sizeof(double), s));
+    if (m > 0) {
+      CK(cudaMemcpyAsync(w.A.rp, darp, ((size_t)m + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+      if (nnzA > 0) {
+        CK(cudaMemcpyAsync(w.A.col, dacol, (size_t)nnzA * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(w.A.val, daval, (size_t)nnzA * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    CK(cudaGetLastError());
+    // greedy row blocks on the host from the row pointers
+    std::vector<int32_t> prp((size_t)n + 1);
+    CK(cudaMemcpyAsync(prp.data(), w.P.rp, ((size_t)n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (herr & VE_LONG) {   // a column of A longer than the device sort handles
+      pdqp_destroy(h);
+      return nullptr;
+    }
+    const std::vector<int32_t> pblk = row_blocks(n, prp);
+    const std::vector<int32_t> ablk = m > 0 ? row_blocks(m, arp) : std::vector<int32_t>{0};
+    std::vector<Inst> insts(1);
+    Inst& I = insts[0];
+    I.n = n; I.m = m; I.m_eq = (int)in.m_eq; I.xoff = 0; I.yoff = 0;
+    I.bP0 = 0; I.bP1 = (int)pblk.size() - 1;
+    I.bA0 = 0; I.bA1 = (int)ablk.size() - 1;
+    I.cP0 = 0; I.cA0 = 0;
+    begin_work(h, n, m, (int)in.m_eq, 1, insts);
+    for (int side = 0; side < 2; ++side) {
+      DCsr& M = side == 0 ? w.P : w.A;
+      const std::vector<int32_t>& blk = side == 0 ? pblk : ablk;
+      M.nblk = (int)blk.size() - 1;
+      M.blk = dalloc<int>(h, blk.size());
+      to_device(M.blk, blk.data(), blk.size(), s);
+      M.meta = dalloc<int>(h, 4 * (size_t)std::max(M.nblk, 1));
+      int* binst = dalloc<int>(h, (size_t)std::max(M.nblk, 1));
+      if (M.nblk > 0) k_block_meta<<<grid_of(M.nblk), 256, 0, s>>>(M.blk, M.nblk, M.rp, M.meta, binst);
+      (side == 0 ? w.blk_inst_P : w.blk_inst_A) = binst;
+    }
+    w.inst = dalloc<Inst>(h, 1);
+    to_device(w.inst, insts.data(), 1, s);
+    w.row_inst_n = dalloc<int>(h, n);
+    w.row_inst_m = dalloc<int>(h, m);
+    w.row_ineq = dalloc<unsigned char>(h, m);
+    k_single_rows<<<grid_of(std::max(n, m)), 256, 0, s>>>(n, m, (int)in.m_eq, w.row_inst_n, w.row_inst_m, w.row_ineq);
+    CK(cudaGetLastError());
+    alloc_work(h, s);
+  } catch (...) {
+    cudaStreamSynchronize(s);
+    pdqp_destroy(h);
+    throw;
+  }
+  return h;
+}
+
 pdqp_status create_common(pdqp_handle* out, int count, const InstanceIn* ins, int mem, cudaStream_t s) {
   if (!out) return PDQP_ERR_INVALID;
   *out = nullptr;
   try {
-    *out = build_problem(count, ins, mem, s);
+    pdqp_problem* h = count == 1 ? build_single_device(ins[0], mem, s) : nullptr;
+    *out = h ? h : build_problem(count, ins, mem, s);
     return PDQP_OK;
   } catch (const Fail& f) {
     g_create_error = f.msg;

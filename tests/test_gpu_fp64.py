@@ -234,3 +234,30 @@ def test_graph_replay_matches_direct_launches(pdqp, cfg0, precision):
     assert a[1].iterations == b[1].iterations
     np.testing.assert_array_equal(a[2], b[2])
     np.testing.assert_array_equal(a[3], b[3])
+
+
+def test_create_rejects_bad_row_pointers_and_handles_long_columns(pdqp):
+    """Row pointers that leave [0, nnz] are rejected before any column is read;
+    a column of A longer than the device sort takes (4096) is built on the
+    host and solves like the rest."""
+    inst = qpgen.tiny_qp(3, n=4, m=2, m_eq=1)
+    bad_rp = np.array([0, 50, 3, 4, 4], np.int32)      # row 0 claims 50 entries of 4
+    with pytest.raises(pdqp.PdqpError) as e:
+        pdqp.pdqp_create(4, 2, 1, bad_rp, inst.Q.indices[:4].copy(), inst.Q.data[:4].copy(), inst.A.indptr,
+                         inst.A.indices, inst.A.data, inst.c, inst.b, inst.l, inst.u)
+    assert e.value.status == pdqp.PDQP_ERR_INVALID
+    rng = np.random.default_rng(5)
+    n, m = 30, 5000
+    A = sp.random(m, n, density=0.05, random_state=5, format="csr")
+    A = sp.csr_matrix(A + sp.csr_matrix((np.ones(m), (np.arange(m), np.zeros(m, int))), shape=(m, n)))
+    A.sort_indices()
+    x0 = rng.uniform(-0.5, 0.5, n)
+    b = A @ x0 - rng.uniform(0, 1, m)
+    Q = sp.identity(n, format="csr")
+    big = qpgen.QPInstance("long_column", n, m, 0, sp.csr_matrix(Q), A, rng.standard_normal(n), b,
+                           -np.ones(n) * 5, np.ones(n) * 5)
+    assert np.diff(A.tocsc().indptr).max() > 4096
+    st, info, x, y = G.solve(big, eps=1e-6)
+    assert st == pdqp.PDQP_OK
+    parts = R.kkt_parts(R.problem_from_instance(big), x, y)
+    assert parts["rel_kkt"] <= 1.0001e-6
