@@ -262,14 +262,16 @@ __device__ void reduce_kkt_partials(const double* __restrict__ part, int nblk, d
 template <int NT, typename V, typename X>
 __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
                                                int r0, int nr, V* prod, int* srp) {
-  // two phases of EPT/2 loads and gathers each: half the registers of one
-  // phase of EPT, so that more blocks fit on an SM
+  // float data: two phases of EPT/2 loads and gathers each, half the
+  // registers of one phase of EPT, so that 8 blocks fit on an SM; float64
+  // data (4 blocks per SM either way) keeps all EPT gathers in flight at once
   constexpr int EPT = BNNZ / NT;
-  constexpr int H = EPT / 2;
+  constexpr int PH = sizeof(V) == 4 ? 2 : 1;
+  constexpr int H = EPT / PH;
   const int tid = threadIdx.x;
   for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < PH; ++h) {
     int ci[H];
     V vv[H];
 #pragma unroll
