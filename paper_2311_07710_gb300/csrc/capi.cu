@@ -141,6 +141,31 @@ std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
   return blk;
 }
 
+// Segments of the long rows (blocks holding a single row of more than BNNZ
+// nonzeros): LSEG nonzeros each, summed by separate CUDA blocks.
+void build_long_segments(pdqp_problem* h, DCsr& M, const std::vector<int32_t>& rp, const std::vector<int32_t>& blk,
+                         cudaStream_t s) {
+  std::vector<int4> seg;
+  std::vector<int2> bseg(blk.size() > 1 ? blk.size() - 1 : 1, make_int2(0, 0));
+  for (size_t b = 0; b + 1 < blk.size(); ++b) {
+    const int r0 = blk[b], r1 = blk[b + 1];
+    const long long e0 = rp[r0], e1 = rp[r1];
+    if (r1 - r0 != 1 || e1 - e0 <= BNNZ) continue;
+    bseg[b] = make_int2((int)seg.size(), (int)((e1 - e0 + LSEG - 1) / LSEG));
+    for (long long e = e0; e < e1; e += LSEG)
+      seg.push_back(make_int4(r0, (int)e, (int)std::min(e1, e + LSEG), (int)b));
+  }
+  M.nlseg = (int)seg.size();
+  if (M.nlseg == 0) return;
+  M.lseg = dalloc<int4>(h, seg.size());
+  to_device(M.lseg, seg.data(), seg.size(), s);
+  M.blk_seg = dalloc<int2>(h, bseg.size());
+  to_device(M.blk_seg, bseg.data(), bseg.size(), s);
+  M.lpart_d = dalloc<double>(h, seg.size());
+  M.lpart_f = dalloc<float>(h, seg.size());
+  CK(cudaStreamSynchronize(s));   // the host vectors die here
+}
+
 void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
                 const std::vector<double>& val, const std::vector<int32_t>* split, const std::vector<int32_t>& blk,
                 cudaStream_t s) {
@@ -174,6 +199,7 @@ void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& 
     M.split = dalloc<int>(h, rows);
     to_device(M.split, split->data(), rows, s);
   }
+  build_long_segments(h, M, rp, blk, s);
   CK(cudaStreamSynchronize(s));   // the host vectors die with the caller
 }
 
@@ -805,6 +831,32 @@ pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, c
     Work& w = h->w;
     replicate_csr(h, w.P, tw.P, count, (int)n_t, (int)m_t, N, true, s);
     replicate_csr(h, w.A, tw.A, count, (int)n_t, (int)m_t, N, false, s);
+    for (int side = 0; side < 2; ++side) {   // long-row segments: the template's, offset per member
+      const DCsr& T = side == 0 ? tw.P : tw.A;
+      DCsr& Mr = side == 0 ? w.P : w.A;
+      if (T.nlseg == 0) continue;
+      std::vector<int4> ts(T.nlseg);
+      std::vector<int2> tb(T.nblk);
+      CK(cudaMemcpy(ts.data(), T.lseg, ts.size() * sizeof(int4), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(tb.data(), T.blk_seg, tb.size() * sizeof(int2), cudaMemcpyDeviceToHost));
+      std::vector<int4> seg;
+      std::vector<int2> bseg((size_t)count * T.nblk);
+      for (int i = 0; i < count; ++i) {
+        for (int b = 0; b < T.nblk; ++b)
+          bseg[(size_t)i * T.nblk + b] = tb[b].y ? make_int2(tb[b].x + i * T.nlseg, tb[b].y) : make_int2(0, 0);
+        for (const int4& q : ts)
+          seg.push_back(make_int4(q.x + i * T.rows, (int)(q.y + (long long)i * T.nnz), (int)(q.z + (long long)i * T.nnz),
+                                  q.w + i * T.nblk));
+      }
+      Mr.nlseg = (int)seg.size();
+      Mr.lseg = dalloc<int4>(h, seg.size());
+      to_device(Mr.lseg, seg.data(), seg.size(), s);
+      Mr.blk_seg = dalloc<int2>(h, bseg.size());
+      to_device(Mr.blk_seg, bseg.data(), bseg.size(), s);
+      Mr.lpart_d = dalloc<double>(h, seg.size());
+      Mr.lpart_f = dalloc<float>(h, seg.size());
+      CK(cudaStreamSynchronize(s));
+    }
     w.inst = dalloc<Inst>(h, count);
     to_device(w.inst, insts.data(), count, s);
     w.row_inst_n = dalloc<int>(h, N);
@@ -851,20 +903,36 @@ enum : unsigned {
   VE_RP = 1u, VE_COL = 2u, VE_ORDER = 4u, VE_VAL = 8u, VE_C = 16u, VE_BOUNDS = 32u, VE_B = 64u, VE_LONG = 128u
 };
 
-// (row pointers outside [0, nnz] or decreasing are flagged before any column
-// of their row is read)
-__global__ void k_validate_csr(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-                               int rows, int cols, long long nnz, unsigned* __restrict__ err) {
+// Row pointers outside [0, nnz] or decreasing are flagged first (thread per
+// row); the entries are then checked per nonzero (its row by binary search), so
+// long rows spread over the grid.
+__global__ void k_validate_rowptr(const int* __restrict__ rp, int rows, long long nnz, unsigned* __restrict__ err) {
   unsigned e = 0;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
     const int a = rp[r], b = rp[r + 1];
-    if (a < 0 || b < a || b > nnz) { e |= VE_RP; continue; }
-    for (int k = a; k < b; ++k) {
-      const int c = col[k];
-      if (c < 0 || c >= cols) e |= VE_COL;
-      if (k > a && c <= col[k - 1]) e |= VE_ORDER;
-      if (!isfinite(val[k])) e |= VE_VAL;
-    }
+    if (a < 0 || b < a || b > nnz) e |= VE_RP;
+  }
+  if (e) atomicOr(err, e);
+}
+
+__device__ __forceinline__ int row_of(const int* __restrict__ rp, int rows, long long k) {
+  int lo = 0, hi = rows - 1;   // last row with rp[row] <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rp[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_validate_entries(const int* __restrict__ rp, const int* __restrict__ col,
+                                   const double* __restrict__ val, int rows, int cols, long long nnz,
+                                   unsigned* __restrict__ err) {
+  unsigned e = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const int c = col[k];
+    if (c < 0 || c >= cols) e |= VE_COL;
+    if (!isfinite(val[k])) e |= VE_VAL;
+    if (k > 0 && rp[row_of(rp, rows, k)] < k && c <= col[k - 1]) e |= VE_ORDER;
   }
   if (e) atomicOr(err, e);
 }
@@ -936,18 +1004,17 @@ __global__ void k_scan_add(int* __restrict__ out, int len, const int* __restrict
   if (i == 0) out[len] = *total;
 }
 
-// scatter A's entries into the column segments of A' (order within a segment
-// decided by the atomics; sorted afterwards)
+// scatter A's entries into the column segments of A' (per nonzero, its row by
+// binary search; order within a segment decided by the atomics, sorted after)
 __global__ void k_col_scatter(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-                              int rows, const int* __restrict__ trp, int* __restrict__ cur, int* __restrict__ tcol,
-                              double* __restrict__ tval) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
-    for (int k = rp[r]; k < rp[r + 1]; ++k) {
-      const int c = col[k];
-      const int p = trp[c] + atomicAdd(&cur[c], 1);
-      tcol[p] = r;
-      tval[p] = val[k];
-    }
+                              int rows, long long nnz, const int* __restrict__ trp, int* __restrict__ cur,
+                              int* __restrict__ tcol, double* __restrict__ tval) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const int c = col[k];
+    const int p = trp[c] + atomicAdd(&cur[c], 1);
+    tcol[p] = row_of(rp, rows, k);
+    tval[p] = val[k];
+  }
 }
 
 // sort each segment of A' by row (insertion sort; segments longer than
@@ -1103,14 +1170,20 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
     CK(cudaMemcpyAsync(w.l, in.l, (size_t)n * sizeof(double), kind, s));
     CK(cudaMemcpyAsync(w.u, in.u, (size_t)n * sizeof(double), kind, s));
     if (m > 0) CK(cudaMemcpyAsync(w.b, in.b, (size_t)m * sizeof(double), kind, s));
-    k_validate_csr<<<grid_of(n), 256, 0, s>>>(dqrp, dqcol, dqval, n, n, nnzQ, derr);
-    if (m > 0) k_validate_csr<<<grid_of(m), 256, 0, s>>>(darp, dacol, daval, m, n, nnzA, derr);
+    k_validate_rowptr<<<grid_of(n), 256, 0, s>>>(dqrp, n, nnzQ, derr);
+    if (m > 0) k_validate_rowptr<<<grid_of(m), 256, 0, s>>>(darp, m, nnzA, derr);
     k_validate_vecs<<<grid_of(std::max(n, m)), 256, 0, s>>>(w.c, w.l, w.u, n, w.b, m, derr);
     CK(cudaGetLastError());
     unsigned herr = 0;
     CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (herr & VE_RP) throw Fail{PDQP_ERR_INVALID, "Q or A: rowptr decreases"};
+    // the row pointers are sound: check the entries
+    if (nnzQ > 0) k_validate_entries<<<grid_of(nnzQ), 256, 0, s>>>(dqrp, dqcol, dqval, n, n, nnzQ, derr);
+    if (nnzA > 0) k_validate_entries<<<grid_of(nnzA), 256, 0, s>>>(darp, dacol, daval, m, n, nnzA, derr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     if (herr & VE_COL) throw Fail{PDQP_ERR_INVALID, "Q or A: column index out of range"};
     if (herr & VE_ORDER) throw Fail{PDQP_ERR_INVALID, "Q or A: column indices not strictly increasing in a row"};
     if (herr & VE_VAL) throw Fail{PDQP_ERR_INVALID, "Q or A: non-finite value"};
@@ -1130,7 +1203,7 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
     if (nnzA > 0) k_col_count<<<grid_of(nnzA), 256, 0, s>>>(dacol, nnzA, cnt);
     device_scan(cnt, n, trp, tmp.v, s);
     if (nnzA > 0) {
-      k_col_scatter<<<grid_of(m), 256, 0, s>>>(darp, dacol, daval, m, trp, cur, tcol, tval);
+      k_col_scatter<<<grid_of(nnzA), 256, 0, s>>>(darp, dacol, daval, m, nnzA, trp, cur, tcol, tval);
       k_seg_sort<<<grid_of(n), 256, 0, s>>>(trp, n, tcol, tval, derr);
     }
     // P = [Q | -A']
@@ -1198,6 +1271,7 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
       int* binst = dalloc<int>(h, (size_t)std::max(M.nblk, 1));
       if (M.nblk > 0) k_block_meta<<<grid_of(M.nblk), 256, 0, s>>>(M.blk, M.nblk, M.rp, M.meta, binst);
       (side == 0 ? w.blk_inst_P : w.blk_inst_A) = binst;
+      build_long_segments(h, M, side == 0 ? prp : arp, blk, s);
     }
     w.inst = dalloc<Inst>(h, 1);
     to_device(w.inst, insts.data(), 1, s);
@@ -1346,7 +1420,8 @@ pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t
     w.Fs = dalloc<float>(h, N);
     w.Fd = dalloc<double>(h, N);
     w.wlr = dalloc<double>(h, 2 * (size_t)r);
-    w.lr_part = dalloc<double>(h, (size_t)((w.n + 1023) / 1024) * 2 * r);
+    w.wlr_f = dalloc<float>(h, 2 * (size_t)r);
+    w.lr_part = dalloc<double>(h, (size_t)((w.n + LR_ROWS - 1) / LR_ROWS) * 2 * r);
     to_device(w.F, hf.data(), N, s);
     to_device(w.Fo, hd.data(), N, s);
     CK(cudaStreamSynchronize(s));

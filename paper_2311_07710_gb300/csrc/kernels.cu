@@ -294,8 +294,8 @@ __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __rest
 // n=1e6 against 4 blocks at 64 registers); the float64 kernels are bound by
 // the float64 pipes and gain nothing from 5 or 6 blocks, so they keep 64
 // registers (4); NT = 512 runs 4 blocks at 32 registers.
-template <typename V, int NT> struct MinBlocks { static constexpr int value = 4; };
-template <> struct MinBlocks<float, 256> { static constexpr int value = 8; };
+template <typename V, int NT, bool LR = false> struct MinBlocks { static constexpr int value = 4; };
+template <> struct MinBlocks<float, 256, false> { static constexpr int value = 8; };
 
 
 // ==========================================================================
@@ -303,7 +303,6 @@ template <> struct MinBlocks<float, 256> { static constexpr int value = 8; };
 // F (F' v) and never formed.  w = F~' v is a two-stage reduction (row tiles
 // then one reduce); the row term F~_j . w is added where Q v appears.
 // ==========================================================================
-constexpr int LR_ROWS = 1024;   // rows per tile of the F' v reduction
 
 // F~ = D2 F (float64 and float32 copies)
 __global__ void k_lr_scale(const float* __restrict__ F, const double* __restrict__ D2, int n, int r,
@@ -316,54 +315,93 @@ __global__ void k_lr_scale(const float* __restrict__ F, const double* __restrict
   }
 }
 
-// partial F~' v over a tile of rows for NV vectors v (thread (g, k): column k,
-// rows of the tile with index = g mod G); part[tile][vec][k]
+// Partial F~' v for NV vectors v: CUDA block b takes a contiguous range of
+// rows; thread (g, k) sums column k over the rows of its range with index =
+// g mod G, in the factor's precision (float32 for the
+// float32 iteration, float64 for the float64 iteration and the checks);
+// part[block][vec][k].
 template <typename FV, typename X, int NV>
 __global__ void k_lr_ft(const FV* __restrict__ F, int n, int r, const X* __restrict__ v0, const X* __restrict__ v1,
                         double* __restrict__ part) {
   const int G = blockDim.x / r;
   const int g = threadIdx.x / r, kk = threadIdx.x % r;
-  double acc[NV];
+  FV acc[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  const int j0 = blockIdx.x * LR_ROWS, j1 = min(n, j0 + LR_ROWS);
+  for (int q = 0; q < NV; ++q) acc[q] = FV(0);
   if (g < G) {
-    for (int j = j0 + g; j < j1; j += G) {
-      const double f = (double)F[(size_t)j * r + kk];
-      acc[0] += f * (double)v0[j];
-      if (NV > 1) acc[NV - 1] += f * (double)v1[j];
+    // a contiguous range of rows per block; eight rows in flight per thread
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int j0 = blockIdx.x * per, j1 = min(n, j0 + per);
+    int j = j0 + g;
+    for (; j + 7 * G < j1; j += 8 * G) {
+      FV f[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) f[u] = F[(size_t)(j + u * G) * r + kk];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc[0] += f[u] * (FV)v0[j + u * G];
+        if (NV > 1) acc[NV - 1] += f[u] * (FV)v1[j + u * G];
+      }
+    }
+    for (; j < j1; j += G) {
+      const FV f = F[(size_t)j * r + kk];
+      acc[0] += f * (FV)v0[j];
+      if (NV > 1) acc[NV - 1] += f * (FV)v1[j];
     }
   }
-  __shared__ double sh[2][256];
+  __shared__ FV sh[2][256];
 #pragma unroll
   for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = acc[q];
   __syncthreads();
   if (threadIdx.x < r) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double s = 0.0;
+      FV s = FV(0);
       for (int gg = 0; gg < G; ++gg) s += sh[q][gg * r + threadIdx.x];
-      part[((size_t)blockIdx.x * NV + q) * r + threadIdx.x] = s;
+      part[((size_t)blockIdx.x * NV + q) * r + threadIdx.x] = (double)s;
     }
   }
 }
 
-// w[vec][k] = sum over tiles
-__global__ void k_lr_reduce(const double* __restrict__ part, int ntiles, int r, int nv, double* __restrict__ w) {
-  const int t = threadIdx.x;
-  if (t >= r * nv) return;
-  const int q = t / r, kk = t % r;
+// w[vec][k] = sum of the block partials: one CUDA block (256 threads) per
+// (vec, k), a fixed-order tree; a float32 copy for the float32 iteration
+__global__ void __launch_bounds__(256) k_lr_reduce(const double* __restrict__ part, int nparts, int r, int nv,
+                                                   double* __restrict__ w, float* __restrict__ wf) {
+  const int q = blockIdx.x / r, kk = blockIdx.x % r;
+  __shared__ double sh[256];
   double s = 0.0;
-  for (int b = 0; b < ntiles; ++b) s += part[((size_t)b * nv + q) * r + kk];
-  w[q * r + kk] = s;
+  for (int b = threadIdx.x; b < nparts; b += 256) s += part[((size_t)b * nv + q) * r + kk];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    w[q * r + kk] = sh[0];
+    if (wf) wf[q * r + kk] = (float)sh[0];
+  }
 }
 
-// the row term F~_j . w
-template <typename FV, typename V>
-__device__ __forceinline__ V lr_row(const FV* __restrict__ F, const double* __restrict__ w, int r, int j) {
+// the row term F~_j . w (16-byte loads of the row when r allows)
+template <typename FV, typename V, typename W>
+__device__ __forceinline__ V lr_row(const FV* __restrict__ F, const W* __restrict__ w, int r, int j) {
   V s = V(0);
   const FV* f = F + (size_t)j * r;
-  for (int kk = 0; kk < r; ++kk) s += (V)f[kk] * (V)w[kk];
+  constexpr int VW = 16 / sizeof(FV);
+  if (r % VW == 0) {
+    for (int kk = 0; kk < r; kk += VW) {
+      if constexpr (VW == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(f + kk);
+        s += (V)q.x * (V)w[kk] + (V)q.y * (V)w[kk + 1] + (V)q.z * (V)w[kk + 2] + (V)q.w * (V)w[kk + 3];
+      } else {
+        const double2 q = *reinterpret_cast<const double2*>(f + kk);
+        s += (V)q.x * (V)w[kk] + (V)q.y * (V)w[kk + 1];
+      }
+    }
+  } else {
+    for (int kk = 0; kk < r; ++kk) s += (V)f[kk] * (V)w[kk];
+  }
   return s;
 }
 
@@ -384,6 +422,8 @@ struct DualB {
   const DevState* __restrict__ st;      // per instance
   const unsigned char* __restrict__ ineq;   // per row: inequality
   int C;
+  const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
+  const V* __restrict__ lpart;          // segment sums of the long rows
 };
 
 template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
@@ -444,6 +484,13 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a
       }
       dual_row(a, es, r, s, yo, bi, yb, lo);
     }
+  } else if (a.blk_seg) {   // a long row: the sum of its segments (k_long_partials), in order
+    if (tid == 0) {
+      const int2 sg = a.blk_seg[blockIdx.x];
+      V s = V(0);
+      for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
+      dual_row(a, es, r0, s, yo, bi, yb, lo);
+    }
   } else {   // a single row longer than a block
     V s = V(0);
     for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
@@ -471,15 +518,17 @@ struct PrimalB {
   const DevState* __restrict__ st;
   int C;
   const V* __restrict__ F;              // low-rank factor F~ (null: none)
-  const double* __restrict__ wlr;       // F~' x_md of this iteration
+  const V* __restrict__ wlr;            // F~' x_md of this iteration
   int r;
+  const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
+  const V* __restrict__ lpart;          // segment sums of the long rows
 };
 
-template <typename V>
+template <typename V, bool LR = false>
 __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry& e, int r, V s, V xo, V xb0,
                                            V cr, V lr, V ur) {
   const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
-  const V g = s + cr + (a.F ? lr_row<V, V>(a.F, a.wlr, a.r, r) : V(0));
+  const V g = s + cr + (LR ? lr_row<V, V, V>(a.F, a.wlr, a.r, r) : V(0));
   const V xn = fmin(fmax(xo - tau * g, lr), ur);
   const V xb = (V(1) - ib) * xb0 + ib * xn;
   a.xbar[r] = xb;
@@ -488,8 +537,10 @@ __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry&
   a.x[r] = xn;
 }
 
-template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_primal(PrimalB<V> a, int j) {
+// LR: the problem has a low-rank term (its row term gets its own instantiation
+// so that the plain kernel keeps its 32 registers)
+template <typename V, int NT, bool LR = false>
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(PrimalB<V> a, int j) {
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -513,14 +564,36 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_primal(PrimalB<
       for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
       const int r = r0 + t;
       if (t >= BNT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
-      primal_row(a, es, r, s, xo, xb, cr, lr, ur);
+      primal_row<V, LR>(a, es, r, s, xo, xb, cr, lr, ur);
+    }
+  } else if (a.blk_seg) {
+    if (tid == 0) {
+      const int2 sg = a.blk_seg[blockIdx.x];
+      V s = V(0);
+      for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
+      primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
     }
   } else {
     V s = V(0);
     for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
     s = block_sum(s);
-    if (tid == 0) primal_row(a, es, r0, s, xo, xb, cr, lr, ur);
+    if (tid == 0) primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
   }
+}
+
+// Segment sums of the long rows: one CUDA block per segment of LSEG nonzeros
+// of M v (skipping instances that stopped); the iteration kernels add a row's
+// segments in order.
+template <typename V>
+__global__ void __launch_bounds__(256) k_long_partials(BCsr<V> M, const V* __restrict__ vec,
+                                                       const int4* __restrict__ lseg, const int* __restrict__ blk_inst,
+                                                       const DevState* __restrict__ st, V* __restrict__ out) {
+  const int4 g = lseg[blockIdx.x];
+  if (st[blk_inst[g.w]].status != ST_RUNNING) return;
+  V s = V(0);
+  for (int e = g.y + threadIdx.x; e < g.z; e += 256) s += M.val[e] * __ldg(vec + M.col[e]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
 
@@ -661,13 +734,17 @@ __global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __
         for (int e = eb; e < ee; ++e) acc += sm.prod[e];
         const int r = r0 + t;
         if (t >= NT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
-        primal_row(a, es, r, acc, xo, xb, cr, lr, ur);
+        if (a.F) primal_row<V, true>(a, es, r, acc, xo, xb, cr, lr, ur);
+        else primal_row<V, false>(a, es, r, acc, xo, xb, cr, lr, ur);
       }
     } else {
       V acc = V(0);
       for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
       acc = block_sum(acc);
-      if (tid == 0) primal_row(a, es, r0, acc, xo, xb, cr, lr, ur);
+      if (tid == 0) {
+        if (a.F) primal_row<V, true>(a, es, r0, acc, xo, xb, cr, lr, ur);
+        else primal_row<V, false>(a, es, r0, acc, xo, xb, cr, lr, ur);
+      }
     }
     __syncthreads();
     mc = mn;
@@ -801,7 +878,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
   auto row = [&](int r, int it, double sq, double sa) {
     const double cj = a.c[r], lj = a.l[r], uj = a.u[r];
     const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
-    const double sqt = sq + (a.F ? lr_row<double, double>(a.F, a.wlr + it * a.r, a.r, r) : 0.0);
+    const double sqt = sq + (a.F ? lr_row<double, double, double>(a.F, a.wlr + it * a.r, a.r, r) : 0.0);
     if (a.prodQx[it]) { a.prodQx[it][r] = sqt; a.prodATy[it][r] = -sa; }
     const double Qx = sqt * id2, ATy = -sa * id2;
     const double xt = a.x[it][r];
@@ -1069,12 +1146,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_m(BCsr<V> A,
 }
 
 // rows of P with input [v_Q ; w_m]: wA = A~'w_m, wQ = Q~ v_Q; partial v'w per row block
-template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_n(BCsr<V> P, LzArgs la, const V* __restrict__ zin,
+template <typename V, int NT, bool LR = false>
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V> P, LzArgs la, const V* __restrict__ zin,
                                                                    const V* __restrict__ vA, V* __restrict__ wA,
                                                                    V* __restrict__ wQ, double* __restrict__ part,
                                                                    const V* __restrict__ F,
-                                                                   const double* __restrict__ wlr, int rk) {
+                                                                   const V* __restrict__ wlr, int rk) {
   __shared__ __align__(16) V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
@@ -1091,7 +1168,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_n(BCsr<V> P,
   auto row = [&](int r, V sQ, V sA) {
     if (doA) { const V u = -sA; wA[r] = u; f[0] += (double)vA[r] * (double)u; }
     if (doQ) {
-      if (F) sQ += lr_row<V, V>(F, wlr, rk, r);
+      if (LR) sQ += lr_row<V, V, V>(F, wlr, rk, r);
       wQ[r] = sQ;
       f[1] += (double)zin[r] * (double)sQ;
     }
@@ -1738,10 +1815,11 @@ void scale_apply(Work& w, bool mixed, cudaStream_t s) {
 // w = F' v (nv = 1) or F' [v0, v1] (nv = 2) into w.wlr
 template <typename FV, typename X>
 static void lowrank_ft(Work& w, const FV* F, const X* v0, const X* v1, cudaStream_t s) {
-  const int tiles = cdiv(w.n, LR_ROWS);
-  if (v1) launch(k_lr_ft<FV, X, 2>, tiles, 256, 0, s, F, w.n, w.r, v0, v1, w.lr_part);
-  else launch(k_lr_ft<FV, X, 1>, tiles, 256, 0, s, F, w.n, w.r, v0, v1, w.lr_part);
-  launch(k_lr_reduce, 1, 512, 0, s, (const double*)w.lr_part, tiles, w.r, v1 ? 2 : 1, w.wlr);
+  const int grid = std::min(cdiv(w.n, LR_ROWS), 4 * w.num_sms);
+  if (v1) launch(k_lr_ft<FV, X, 2>, grid, 256, 0, s, F, w.n, w.r, v0, v1, w.lr_part);
+  else launch(k_lr_ft<FV, X, 1>, grid, 256, 0, s, F, w.n, w.r, v0, v1, w.lr_part);
+  launch(k_lr_reduce, w.r * (v1 ? 2 : 1), 256, 0, s, (const double*)w.lr_part, grid, w.r, v1 ? 2 : 1, w.wlr,
+         w.wlr_f);
 }
 
 static LzArgs lz_args(Work& w) {
@@ -1756,6 +1834,9 @@ static LzArgs lz_args(Work& w) {
 template <typename V> static const V* lr_factor(Work& w);
 template <> const double* lr_factor<double>(Work& w) { return w.Fd; }
 template <> const float* lr_factor<float>(Work& w) { return w.Fs; }
+template <typename V> static const V* lr_weights(Work& w);
+template <> const double* lr_weights<double>(Work& w) { return w.wlr; }
+template <> const float* lr_weights<float>(Work& w) { return w.wlr_f; }
 
 template <typename V>
 static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) {
@@ -1779,8 +1860,12 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
     F = lr_factor<V>(w);
     lowrank_ft<V, V>(w, F, (const V*)pz[cur], (const V*)nullptr, s);
   }
-  launch(k_lz_n<V, NT>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1], w.part_n, F,
-         (const double*)w.wlr, w.r);
+  if (F)
+    launch(k_lz_n<V, NT, true>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
+           w.part_n, F, lr_weights<V>(w), w.r);
+  else
+    launch(k_lz_n<V, NT, false>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
+           w.part_n, F, lr_weights<V>(w), w.r);
   launch(k_lz_alpha, w.count, 512, 0, s, la, (const double*)w.part_n);
   launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
          (const V*)pz[cur], pz[prv], w.part_n);
@@ -1869,7 +1954,7 @@ static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* con
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
   PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
-                w.r > 0 ? lr_factor<V>(w) : nullptr, w.wlr, w.r};
+                w.r > 0 ? lr_factor<V>(w) : nullptr, lr_weights<V>(w), w.r};
   const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
   const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
   const size_t smem = sizeof(PipeSmem<V>);
@@ -1896,20 +1981,32 @@ static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
   PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
-                w.r > 0 ? lr_factor<V>(w) : nullptr, w.wlr, w.r};
+                w.r > 0 ? lr_factor<V>(w) : nullptr, lr_weights<V>(w), w.r};
+  // long rows: segment sums first (float or float64 buffers by V)
+  V* lpA = sizeof(V) == 4 ? (V*)w.A.lpart_f : (V*)w.A.lpart_d;
+  V* lpP = sizeof(V) == 4 ? (V*)w.P.lpart_f : (V*)w.P.lpart_d;
+  if (w.A.nlseg) { da.blk_seg = w.A.blk_seg; da.lpart = lpA; }
+  if (w.P.nlseg) { pa.blk_seg = w.P.blk_seg; pa.lpart = lpP; }
   for (int j = 0; j < len; ++j) {
     if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
       if (Pr.on) Pr.begin(0, s);
+      if (w.A.nlseg)
+        launch(k_long_partials<V>, w.A.nlseg, 256, 0, s, A, (const V*)xt, (const int4*)w.A.lseg,
+               (const int*)w.blk_inst_A, (const DevState*)w.st, lpA);
       launch(k_dual<V, NT>, w.A.nblk, NT, 0, s, da, j);
       if (Pr.on) Pr.end(s);
     }
     pa.zin = Z[j & 1];
     pa.zout = Z[(j + 1) & 1];
     if (Pr.on) Pr.begin(1, s);
-    launch(k_primal<V, NT>, w.P.nblk, NT, 0, s, pa, j);
+    if (w.P.nlseg)
+      launch(k_long_partials<V>, w.P.nlseg, 256, 0, s, P, (const V*)pa.zin, (const int4*)w.P.lseg,
+             (const int*)w.blk_inst_P, (const DevState*)w.st, lpP);
+    if (w.r > 0) launch(k_primal<V, NT, true>, w.P.nblk, NT, 0, s, pa, j);
+    else launch(k_primal<V, NT, false>, w.P.nblk, NT, 0, s, pa, j);
     if (Pr.on) Pr.end(s);
   }
 }

@@ -16,6 +16,8 @@ constexpr int BNT = 256;            // threads per block
 constexpr int BEPT = 8;             // nonzeros staged per thread
 constexpr int BNNZ = BNT * BEPT;    // nonzeros per row block
 constexpr int BROWS = 512;          // rows per row block
+constexpr int LSEG = 2048;          // nonzeros per segment of a long row
+constexpr int LR_ROWS = 256;        // rows per tile of the low-rank F' v reduction
 
 template <typename V>
 struct BCsr {
@@ -38,6 +40,13 @@ struct DCsr {
   double* val = nullptr;      // original values
   double* sval = nullptr;     // scaled values, float64
   float* sval_f = nullptr;    // scaled values, float32 (mixed precision)
+  // rows longer than BNNZ (each a row block of its own) are also cut into
+  // segments of LSEG nonzeros that separate CUDA blocks sum in parallel
+  int nlseg = 0;
+  int4* lseg = nullptr;       // [nlseg] {row, first nonzero, end nonzero, row block}
+  int2* blk_seg = nullptr;    // [nblk] {first segment, segments} of a long-row block
+  double* lpart_d = nullptr;  // [nlseg] segment sums, float64
+  float* lpart_f = nullptr;   // [nlseg] segment sums, float32
   Csr<double> orig() const { return Csr<double>{rp, col, val}; }
   Csr<double> scaled() const { return Csr<double>{rp, col, sval}; }
   Csr<float> scaled_f() const { return Csr<float>{rp, col, sval_f}; }
@@ -101,6 +110,7 @@ struct Work {
   float* Fs = nullptr;       // D2 F, float32
   double* Fd = nullptr;      // D2 F, float64
   double* wlr = nullptr;     // [2][r] F~' v of the current products
+  float* wlr_f = nullptr;    // [2][r] the same in float32 (float32 iteration)
   double* lr_part = nullptr; // [tiles][2][r] partial sums
   // Lanczos vectors: pu[p] (n) for A~'A~, pz[p] = [v_Q ; A~v_A] (n+m) the P input
   double *pu[2] = {nullptr, nullptr}, *pz[2] = {nullptr, nullptr};
