@@ -1282,13 +1282,12 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ al, const 
   return c;
 }
 
-// lambda_max of the k x k tridiagonal by multisection: the nw warps of the
-// calling group (warp index g in [0, nw)) test 32 nw points of the bracket per
-// round; `ballots` is shared memory for nw words.  All threads of the group get
-// the same result.  Stops when the bracket is within 4e-15 relative.
-__device__ double tridiag_max_eig(const double* __restrict__ al, const double* __restrict__ be,
-                                  const double* __restrict__ be2, int k, int g, int nw, unsigned* ballots, int bar_id,
-                                  int bar_threads) {
+// lambda_max of the k x k tridiagonal by 32-point multisection in one warp,
+// down to a bracket of 4e-15 relative.  One warp per operator keeps the
+// float64 work per round low (a batch of thousands of small problems pays it
+// per instance) and gives every operator its own scheduler partition.
+__device__ double tridiag_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be,
+                                       const double* __restrict__ be2, int k) {
   const int lane = threadIdx.x & 31;
   double lo = 1e300, hi = -1e300;   // Gershgorin bracket
   for (int i = 0; i < k; ++i) {
@@ -1297,33 +1296,26 @@ __device__ double tridiag_max_eig(const double* __restrict__ al, const double* _
     hi = fmax(hi, al[i] + r);
   }
   hi += 1e-300 + fabs(hi) * 1e-15;
-  const int npts = 32 * nw;
   for (int round = 0; round < 16 && hi - lo > 4e-15 * fabs(hi); ++round) {
-    const double step = (hi - lo) / (double)(npts + 1);
-    const int pt = g * 32 + lane;
-    const double x = lo + step * (double)(pt + 1);
+    const double step = (hi - lo) / 33.0;
+    const double x = lo + step * (double)(lane + 1);
     const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be2, k, x) < k);   // lambda_max >= x
-    if (lane == 0) ballots[g] = ge;
-    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(bar_threads) : "memory");
-    int t = -1;   // largest point with lambda_max >= x
-    for (int w = nw - 1; w >= 0 && t < 0; --w)
-      if (ballots[w]) t = w * 32 + 31 - __clz(ballots[w]);
-    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(bar_threads) : "memory");
-    if (t < 0) {
+    if (ge == 0u) {
       hi = lo + step;
     } else {
+      const int t = 31 - __clz(ge);
       const double nlo = lo + step * (double)(t + 1);
-      hi = t == npts - 1 ? hi : lo + step * (double)(t + 2);
+      hi = t == 31 ? hi : lo + step * (double)(t + 2);
       lo = nlo;
     }
   }
   return 0.5 * (lo + hi);
 }
 
-// one CUDA block (256 threads) per instance: beta, theta = lambda_max(T_k)
-// (A'A and Q: four warps each, or all eight when one operator is done), stop test
-__global__ void __launch_bounds__(256) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
-                                                int max_steps) {
+// one CUDA block of 64 threads per instance: beta, theta = lambda_max(T_k)
+// (warp 0: A'A, warp 1: Q), stop test
+__global__ void __launch_bounds__(64) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
+                                               int max_steps) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
@@ -1335,7 +1327,6 @@ __global__ void __launch_bounds__(256) k_lz_beta(LzArgs a, const double* __restr
   __shared__ double beta[2];
   __shared__ int done_in[2];
   __shared__ double s_al[2][LZ_MAX], s_be[2][LZ_MAX], s_be2[2][LZ_MAX];
-  __shared__ unsigned ballots[2][8];
   const int k = st.pi_iters + 1;                  // alphas 0..k-1, betas 0..k-2 form T_k
   if (threadIdx.x == 0) {
     beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]);
@@ -1351,21 +1342,19 @@ __global__ void __launch_bounds__(256) k_lz_beta(LzArgs a, const double* __restr
       }
     }
   __syncthreads();
-  const int warp = threadIdx.x >> 5;
-  const bool both = !done_in[0] && !done_in[1];
-  // operator of this warp and its group: both active -> warps 0-3 A'A, 4-7 Q
-  const int o = both ? (warp >> 2) : (done_in[0] ? 1 : 0);
-  const int nw = both ? 4 : 8, g = both ? (warp & 3) : warp;
-  const double theta = tridiag_max_eig(s_al[o], s_be[o], s_be2[o], k, g, nw, ballots[o], 1 + o, 32 * nw);
-  if (g == 0 && (threadIdx.x & 31) == 0) {
-    const double b = beta[o];
-    st.pi_lam[o] = theta;
-    if (fabs(theta - st.pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
-      st.pi_done[o] = 1;
-    } else {
-      lz_be(a, i, o)[k - 1] = b;
-      st.pi_lam_prev[o] = theta;
-      st.pi_inv_norm[o] = 1.0 / b;
+  const int o = threadIdx.x >> 5;
+  if (!done_in[o]) {                              // warp-uniform
+    const double theta = tridiag_max_eig_warp(s_al[o], s_be[o], s_be2[o], k);
+    if ((threadIdx.x & 31) == 0) {
+      const double b = beta[o];
+      st.pi_lam[o] = theta;
+      if (fabs(theta - st.pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
+        st.pi_done[o] = 1;
+      } else {
+        lz_be(a, i, o)[k - 1] = b;
+        st.pi_lam_prev[o] = theta;
+        st.pi_inv_norm[o] = 1.0 / b;
+      }
     }
   }
   __syncthreads();
@@ -1869,7 +1858,7 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   launch(k_lz_alpha, w.count, 512, 0, s, la, (const double*)w.part_n);
   launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
          (const V*)pz[cur], pz[prv], w.part_n);
-  launch(k_lz_beta, w.count, 256, 0, s, la, (const double*)w.part_n, p.norm_tol,
+  launch(k_lz_beta, w.count, 64, 0, s, la, (const double*)w.part_n, p.norm_tol,
          p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
   const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
   launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
