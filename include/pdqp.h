@@ -102,7 +102,10 @@ typedef struct {
                                 relative (default 1e-6) */
   int32_t spmv_threads;      /* iteration-kernel variant: 256 or 512 threads per row
                                 block, 1 = pipelined persistent (cp.async prefetch of
-                                the next row block), 0 = library choice (256) */
+                                the next row block), 0 = autotuned: the first full
+                                chunk of a handle's first solve times 8 iterations of
+                                each variant and the handle keeps the fastest (all
+                                variants give bitwise identical iterates) */
   int32_t no_graphs;         /* 0: replay each full chunk of check_period iterations
                                 and its check as one captured CUDA graph; 1: launch
                                 every kernel directly */
@@ -120,6 +123,7 @@ typedef struct {
   double setup_seconds;      /* device time of scaling + spectral norms (CUDA events) */
   double iterate_seconds;    /* device time from the first iteration to termination */
   int32_t norm_iters;        /* Lanczos steps taken (0 when the norms were given) */
+  int32_t spmv_threads;      /* iteration-kernel variant used after the first chunk */
 } pdqp_info;
 
 /* Per-kernel device time of the solver's hot loop, measured with CUDA events

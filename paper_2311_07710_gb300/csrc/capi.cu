@@ -29,6 +29,8 @@ struct pdqp_problem {
   ChunkGraph graph;
   std::vector<pdqp_info> infos;                       // per instance, from the last solve
   std::vector<void*> allocs;
+  int tuned_nt = 0;                                   // autotuned iteration-kernel variant (0: not yet)
+  cudaEvent_t tune_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 static thread_local std::string g_create_error;
@@ -345,7 +347,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   check_space(y_out, mem, "y_out");
   const bool mixed = o.precision == PDQP_PREC_MIXED;
   if (mixed) alloc_mixed(h);
-  const SolveParams p = make_params(o);
+  SolveParams p = make_params(o);
 
   // start point in device memory
   const double* dx0 = x0;
@@ -394,11 +396,37 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
 
   long long k_total = 0;
   bool timed_out = false;
+  // autotuning of the iteration-kernel variant: the first full chunk runs
+  // TUNE iterations with each candidate (the iterates do not depend on the
+  // variant), the rest with the fastest
+  static const int kCand[3] = {256, 512, 1};
+  constexpr int TUNE = 8;
+  const bool autotune = o.spmv_threads == 0;
+  if (autotune && h->tuned_nt) p.spmv_threads = h->tuned_nt;
   while (w.bst_host->running > 0) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
+    const bool tune_now = autotune && !h->tuned_nt && len == o.check_period && len >= 4 * TUNE;
     // per-kernel event timing needs direct launches (events recorded by graph
     // nodes cannot be timed), so profiling bypasses the graph
-    if (len == o.check_period && !o.no_graphs && !w.prof.on) {
+    if (tune_now) {
+      for (auto& e : h->tune_ev)
+        if (!e) CK(cudaEventCreate(&e));
+      CK(cudaEventRecord(h->tune_ev[0], s));
+      for (int c = 0; c < 3; ++c) {
+        pdqp::iterate_chunk(w, TUNE, mixed, kCand[c], s, c * TUNE);
+        CK(cudaEventRecord(h->tune_ev[c + 1], s));
+      }
+      CK(cudaEventSynchronize(h->tune_ev[3]));
+      float best = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->tune_ev[c], h->tune_ev[c + 1]));
+        if (c == 0 || ms < best) { best = ms; h->tuned_nt = kCand[c]; }
+      }
+      p.spmv_threads = h->tuned_nt;
+      pdqp::iterate_chunk(w, (int)len - 3 * TUNE, mixed, p.spmv_threads, s, 3 * TUNE);
+      pdqp::check(w, p, 1, len, mixed, s);
+    } else if (len == o.check_period && !o.no_graphs && !w.prof.on) {
       launch_chunk_graph(h, p, mixed, s);
     } else {
       pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s);
@@ -438,6 +466,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     h->infos[i].setup_seconds = 1e-3 * t_setup;
     h->infos[i].iterate_seconds = 1e-3 * t_iter;
     h->infos[i].seconds = secs;
+    h->infos[i].spmv_threads = p.spmv_threads == 0 ? 256 : p.spmv_threads;
     if (si > result) result = si;
   }
   if (info) {
@@ -1546,6 +1575,8 @@ void pdqp_destroy(pdqp_handle h) {
   if (h->w.st_host) cudaFreeHost(h->w.st_host);
   if (h->w.bst_host) cudaFreeHost(h->w.bst_host);
   for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->tune_ev)
     if (e) cudaEventDestroy(e);
   if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
   if (h->cap) cudaStreamDestroy(h->cap);

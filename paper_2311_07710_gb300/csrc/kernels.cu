@@ -1938,7 +1938,7 @@ static int pipe_grid_p(void (*kern)(PrimalB<V>, const int4*, int, int)) {
 }
 
 template <typename V, int NT>
-static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
+static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
                            const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
@@ -1947,7 +1947,7 @@ static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* con
   const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
   const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
   const size_t smem = sizeof(PipeSmem<V>);
-  for (int j = 0; j < len; ++j) {
+  for (int j = j0; j < j0 + len; ++j) {
     if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
@@ -1965,7 +1965,7 @@ static void run_chunk_pipe(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* con
 }
 
 template <typename V, int NT>
-static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
+static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
                       const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
@@ -1976,7 +1976,7 @@ static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z
   V* lpP = sizeof(V) == 4 ? (V*)w.P.lpart_f : (V*)w.P.lpart_d;
   if (w.A.nlseg) { da.blk_seg = w.A.blk_seg; da.lpart = lpA; }
   if (w.P.nlseg) { pa.blk_seg = w.P.blk_seg; pa.lpart = lpP; }
-  for (int j = 0; j < len; ++j) {
+  for (int j = j0; j < j0 + len; ++j) {
     if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
@@ -2000,35 +2000,35 @@ static void run_chunk(Work& w, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z
   }
 }
 
-void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s) {
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0) {
   if (nt == 1) {   // pipelined persistent kernels, 256 threads
     if (mixed) {
-      run_chunk_pipe<float, 256>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+      run_chunk_pipe<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
                                  w.fxbar, w.fc, w.fl, w.fu, s);
-      w.fy = w.fZ[(len - 1) & 1] + w.n;
+      w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
     } else {
-      run_chunk_pipe<double, 256>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x,
+      run_chunk_pipe<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x,
                                   w.xbar, w.cs, w.ls, w.us, s);
-      w.y = w.Z[(len - 1) & 1] + w.n;
+      w.y = w.Z[(j0 + len - 1) & 1] + w.n;
     }
     return;
   }
   if (mixed) {
     if (nt != 512)
-      run_chunk<float, 256>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+      run_chunk<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
                             w.fxbar, w.fc, w.fl, w.fu, s);
     else
-      run_chunk<float, 512>(w, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+      run_chunk<float, 512>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
                             w.fxbar, w.fc, w.fl, w.fu, s);
-    w.fy = w.fZ[(len - 1) & 1] + w.n;
+    w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
   } else {
     if (nt != 512)
-      run_chunk<double, 256>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
+      run_chunk<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
                              w.cs, w.ls, w.us, s);
     else
-      run_chunk<double, 512>(w, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
+      run_chunk<double, 512>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
                              w.cs, w.ls, w.us, s);
-    w.y = w.Z[(len - 1) & 1] + w.n;
+    w.y = w.Z[(j0 + len - 1) & 1] + w.n;
   }
 }
 

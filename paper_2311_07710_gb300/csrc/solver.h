@@ -148,7 +148,8 @@ void count_running(Work& w, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 
 // iteration
-void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s);
+// Iterations j0 .. j0+len-1 of a chunk (j indexes the chunk's step table).
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0);
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
 
 // results

@@ -44,7 +44,7 @@ class pdqp_info(ctypes.Structure):
         ("r_gap", ctypes.c_double), ("primal_obj", ctypes.c_double), ("dual_obj", ctypes.c_double),
         ("seconds", ctypes.c_double), ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double),
         ("omega", ctypes.c_double), ("setup_seconds", ctypes.c_double),
-        ("iterate_seconds", ctypes.c_double), ("norm_iters", ctypes.c_int32),
+        ("iterate_seconds", ctypes.c_double), ("norm_iters", ctypes.c_int32), ("spmv_threads", ctypes.c_int32),
     ]
 
     def as_dict(self):

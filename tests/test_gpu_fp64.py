@@ -261,3 +261,20 @@ def test_create_rejects_bad_row_pointers_and_handles_long_columns(pdqp):
     assert st == pdqp.PDQP_OK
     parts = R.kkt_parts(R.problem_from_instance(big), x, y)
     assert parts["rel_kkt"] <= 1.0001e-6
+
+
+def test_autotuned_variant_gives_the_same_iterates(pdqp, cfg0):
+    """The default options autotune the iteration-kernel variant on the first
+    chunk; every variant yields bitwise identical iterates, so the choice
+    never changes the answer."""
+    outs = {}
+    for nt in (0, 256, 512, 1):
+        st, info, x, y = G.solve(cfg0, spmv_threads=nt)
+        outs[nt] = (x, y, info.iterations, info.spmv_threads)
+        assert st == pdqp.PDQP_OK
+    assert outs[0][3] in (256, 512, 1)
+    for nt in (256, 512, 1):
+        assert outs[nt][3] == nt
+        np.testing.assert_array_equal(outs[nt][0], outs[0][0])
+        np.testing.assert_array_equal(outs[nt][1], outs[0][1])
+        assert outs[nt][2] == outs[0][2]
