@@ -42,10 +42,15 @@ typedef __nv_bfloat16 bf16;
 
 namespace mlp {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
-constexpr int TILE_BYTES = BM * BK * 2;                 // 16 KiB per operand tile
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+// Tile: BM = 128 rows of A, BN = 128 or 256 rows of B (the N width of the MMA
+// and of the tensor-memory accumulator), BK = 64 (one 128-byte swizzle row).
+constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;                    // 16 KiB
+template <int BN> struct Tile {
+  static constexpr int B_BYTES = BN * BK * 2;           // 16 or 32 KiB
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
+};
 constexpr uint64_t WAIT_NS = 200000000ULL;            // a wait gives up after 0.2 s without progress
 
 struct Epi {
@@ -137,9 +142,11 @@ __device__ __forceinline__ float epi_value(float r, int row, int col, const Epi&
   return r;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
               int K, int ktps, Epi epi, float* __restrict__ partial, int* err) {
+  constexpr int STAGE_BYTES = Tile<BN>::STAGE_BYTES;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(sm + STAGES * STAGE_BYTES);
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(128, 1)
       unsigned char* a = sm + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_2d(a, &mapA, &full[s], (kt0 + i) * BK, m0);
-      tma_load_2d(a + TILE_BYTES, &mapB, &full[s], (kt0 + i) * BK, n0);
+      tma_load_2d(a + A_BYTES, &mapB, &full[s], (kt0 + i) * BK, n0);
     }
     s_issued = i;
   } else if (warp == 1 && lane == 0) {   // MMA issuer
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(128, 1)
       s_progress = i + 1;
       asm volatile("tcgen05.fence::after_thread_sync;\n");
       const unsigned char* a = sm + s * STAGE_BYTES;
-      const uint64_t da = smem_desc(a), db = smem_desc(a + TILE_BYTES);
+      const uint64_t da = smem_desc(a), db = smem_desc(a + A_BYTES);
 #pragma unroll
       for (int k = 0; k < BK / 16; ++k) {
         const uint64_t step = (uint64_t)((k * 16 * 2) >> 4);   // 32 bytes further along K
@@ -576,15 +583,15 @@ static EncodeTiledFn encode_fn() {
 }
 
 // Tensor map of a row-major rows x cols bf16 matrix with leading dimension ld
-// (elements): boxes of 128 rows x 64 columns, 128-byte swizzle, zero fill
+// (elements): boxes of box_rows rows x 64 columns, 128-byte swizzle, zero fill
 // outside the matrix.
-static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld) {
+static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   if (((uintptr_t)base & 15) || (((size_t)ld * 2) & 15) || cols > ld) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {BK, BM};
+  const cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -602,8 +609,12 @@ static int num_sms() {
   return g_num_sms;
 }
 
+// the B tile width: 256 when N fills it, else 128
+inline int tile_n(int N) { return N >= 256 ? 256 : 128; }
+
 // number of K splits: enough blocks to cover the SMs, at least 4 k-tiles each
 int plan_splits(int M, int N, int K, int requested) {
+  const int BN = tile_n(N);
   const int KT = (K + BK - 1) / BK;
   int splits = requested;
   if (splits <= 0) {
@@ -626,16 +637,23 @@ size_t splitk_floats(int M, int N, int K, int splits) {
 cudaError_t gemm_tn(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& epi, int splits,
                     float* work, size_t work_floats, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  const int BN = tile_n(N);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
+  if (!make_map(&ma, A, M, K, lda, BM) || !make_map(&mb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
   static std::once_flag attr;
-  std::call_once(attr, [] { cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES); });
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_gemm_tn<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<128>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tn<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<256>::SMEM_BYTES);
+  });
   const int KT = (K + BK - 1) / BK;
   int sp = plan_splits(M, N, K, splits);
   if (sp > 1 && (!work || work_floats < (size_t)sp * M * N)) sp = 1;
   const int ktps = (KT + sp - 1) / sp;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, sp);
-  k_gemm_tn<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, epi, sp > 1 ? work : nullptr, err);
+  if (BN == 256)
+    k_gemm_tn<256><<<grid, 128, Tile<256>::SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, epi, sp > 1 ? work : nullptr, err);
+  else
+    k_gemm_tn<128><<<grid, 128, Tile<128>::SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, epi, sp > 1 ? work : nullptr, err);
   if (sp > 1) {
     const long long MN = (long long)M * N;
     const int blocks = (int)std::min<long long>((MN + 255) / 256, 8LL * num_sms());
