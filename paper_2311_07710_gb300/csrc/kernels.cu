@@ -13,9 +13,10 @@
 //
 // All SpMV-shaped kernels work on row blocks (see BCsr): the block's nonzeros
 // are contiguous, so its 256 threads issue their index and value loads
-// together (coalesced, 8 per thread), then the independent gathers, stage the
-// products in shared memory, and finish one row per thread -- a row's update
-// reads and writes consecutive entries of the row-indexed vectors.
+// together (coalesced, 8 per thread; in two phases of 4 for float data), then
+// the independent gathers, stage the products in shared memory, and finish
+// one row per thread -- a row's update reads and writes consecutive entries
+// of the row-indexed vectors.
 #include <stdio.h>
 
 #include <algorithm>
@@ -1200,7 +1201,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
 }
 
 // one CUDA block per instance: alpha_k = sum of its row blocks' partials
-__global__ void __launch_bounds__(512) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
+__global__ void __launch_bounds__(128) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;
@@ -1556,8 +1557,8 @@ __global__ void __launch_bounds__(32) k_kkt_chunks(const Inst* __restrict__ inst
 // mode 0: evaluate z^{0,0} (anchor, maybe already optimal); mode 1: a check
 // after `chunk_len` more iterations (Section 6 restart rule, termination
 // eq. (terminate), iteration limit).
-// one CUDA block per instance
-__global__ void __launch_bounds__(512) k_decide(DevState* __restrict__ sts, const Inst* __restrict__ insts,
+// one CUDA block of 64 threads per instance (one step-table entry per thread)
+__global__ void __launch_bounds__(64) k_decide(DevState* __restrict__ sts, const Inst* __restrict__ insts,
                                                 const double* __restrict__ pm, int nbm,
                                                 const double* __restrict__ pn, int nbn,
                                                 StepEntry* __restrict__ tabs, int C, SolveParams p, int mode,
@@ -1855,7 +1856,7 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   else
     launch(k_lz_n<V, NT, false>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
            w.part_n, F, lr_weights<V>(w), w.r);
-  launch(k_lz_alpha, w.count, 512, 0, s, la, (const double*)w.part_n);
+  launch(k_lz_alpha, w.count, 128, 0, s, la, (const double*)w.part_n);
   launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
          (const V*)pz[cur], pz[prv], w.part_n);
   launch(k_lz_beta, w.count, 64, 0, s, la, (const double*)w.part_n, p.norm_tol,
@@ -2077,7 +2078,7 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
            (const double*)w.part_n, w.P.nblk, w.cpart_m, std::max(w.nchunk_m, 1), w.cpart_n, std::max(w.nchunk_n, 1));
   }
-  launch(k_decide, w.count, 512, 0, s, w.st, (const Inst*)w.inst, (const double*)w.cpart_m,
+  launch(k_decide, w.count, 64, 0, s, w.st, (const Inst*)w.inst, (const double*)w.cpart_m,
          std::max(w.nchunk_m, 1), (const double*)w.cpart_n, std::max(w.nchunk_n, 1), w.tab, w.tab_stride, p, mode,
          chunk_len);
   if (mixed) {
