@@ -301,6 +301,14 @@ void fill_info(pdqp_info* info, const DevState& S, pdqp_status status, bool lanc
 }
 
 // Launch one full chunk through the cached graph (capturing it first if needed).
+// Batches whose running instances hold less than half of the row blocks
+// launch only those blocks (direct launches sized by the last check's counts)
+// instead of replaying the full-grid chunk graph.
+bool compact_now(const Work& w, const SolveParams& p) {
+  if (w.count <= 1 || p.spmv_threads == 1) return false;
+  return 2LL * w.bst_host->act_P < (long long)w.P.nblk;
+}
+
 void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
   Work& w = h->w;
   ChunkGraph& g = h->graph;
@@ -426,10 +434,10 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       p.spmv_threads = h->tuned_nt;
       pdqp::iterate_chunk(w, (int)len - 3 * TUNE, mixed, p.spmv_threads, s, 3 * TUNE);
       pdqp::check(w, p, 1, len, mixed, s);
-    } else if (len == o.check_period && !o.no_graphs && !w.prof.on) {
+    } else if (len == o.check_period && !o.no_graphs && !w.prof.on && !compact_now(w, p)) {
       launch_chunk_graph(h, p, mixed, s);
     } else {
-      pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s);
+      pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s, 0, compact_now(w, p));
       pdqp::check(w, p, 1, len, mixed, s);
     }
     CK(cudaGetLastError());
@@ -691,6 +699,8 @@ void alloc_work(pdqp_problem* h, cudaStream_t s) {
   w.part = dalloc<double>(h, (size_t)PDQP_RED_BLOCKS * 32);
   w.part_m = dalloc<double>(h, (size_t)9 * (w.A.nblk > 0 ? w.A.nblk : 1));
   w.part_n = dalloc<double>(h, (size_t)15 * (w.P.nblk > 0 ? w.P.nblk : 1));
+  w.act_A = dalloc<int>(h, (size_t)std::max(w.A.nblk, 1));
+  w.act_P = dalloc<int>(h, (size_t)std::max(w.P.nblk, 1));
   w.cpart_m = dalloc<double>(h, (size_t)9 * std::max(w.nchunk_m, 1));
   w.cpart_n = dalloc<double>(h, (size_t)15 * std::max(w.nchunk_n, 1));
   w.st = dalloc<DevState>(h, count);

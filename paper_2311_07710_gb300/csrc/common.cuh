@@ -65,6 +65,7 @@ inline __host__ __device__ int kkt_chunks(int b0, int b1) { return (b1 - b0 + KK
 struct BatchState {
   int running;           // instances still iterating
   int lz_running;        // instances whose norm estimates are still running
+  int act_A, act_P;      // batches: row blocks of A / P of the running instances (lists in Work)
 };
 
 // Constant parameters of one solve.

@@ -425,6 +425,7 @@ struct DualB {
   int C;
   const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
   const V* __restrict__ lpart;          // segment sums of the long rows
+  const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
 };
 
 template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
@@ -458,9 +459,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
-  const int inst = a.blk_inst[blockIdx.x];
+  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;   // compacted batches: running blocks only
+  const int inst = a.blk_inst[bk];
   if (a.st[inst].status != ST_RUNNING) return;
-  const int r0 = a.A.blk[blockIdx.x], r1 = a.A.blk[blockIdx.x + 1];
+  const int r0 = a.A.blk[bk], r1 = a.A.blk[bk + 1];
   const int nr = r1 - r0;
   const int e0 = a.A.rp[r0];
   const int ne = a.A.rp[r1] - e0;
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a
     }
   } else if (a.blk_seg) {   // a long row: the sum of its segments (k_long_partials), in order
     if (tid == 0) {
-      const int2 sg = a.blk_seg[blockIdx.x];
+      const int2 sg = a.blk_seg[bk];
       V s = V(0);
       for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
       dual_row(a, es, r0, s, yo, bi, yb, lo);
@@ -523,6 +525,7 @@ struct PrimalB {
   int r;
   const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
   const V* __restrict__ lpart;          // segment sums of the long rows
+  const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
 };
 
 template <typename V, bool LR = false>
@@ -545,9 +548,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(Prim
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
-  const int inst = a.blk_inst[blockIdx.x];
+  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
+  const int inst = a.blk_inst[bk];
   if (a.st[inst].status != ST_RUNNING) return;
-  const int r0 = a.P.blk[blockIdx.x], r1 = a.P.blk[blockIdx.x + 1];
+  const int r0 = a.P.blk[bk], r1 = a.P.blk[bk + 1];
   const int nr = r1 - r0;
   const int e0 = a.P.rp[r0];
   const int ne = a.P.rp[r1] - e0;
@@ -569,7 +573,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(Prim
     }
   } else if (a.blk_seg) {
     if (tid == 0) {
-      const int2 sg = a.blk_seg[blockIdx.x];
+      const int2 sg = a.blk_seg[bk];
       V s = V(0);
       for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
       primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
@@ -1649,6 +1653,15 @@ __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const
 
 // Restart of the outer loop from the candidate: x = x_bar = x_md = x_tilde = x_c,
 // y = y_bar = y_c, anchors = z_c (Algorithm 1 "restart the outer loop").
+// Row blocks of the instances still running (batches): indices in act, their
+// number in *n (in any order: a block's rows do not depend on its place in
+// the grid).
+__global__ void k_compact_blocks(const int* __restrict__ blk_inst, int nblk, const DevState* __restrict__ st,
+                                 int* __restrict__ act, int* __restrict__ n) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
+    if (st[blk_inst[b]].status == ST_RUNNING) act[atomicAdd(n, 1)] = b;
+}
+
 __global__ void k_restart_apply(const DevState* __restrict__ sts, const int* __restrict__ inst_n,
                                 const int* __restrict__ inst_m, int n, int m, double* x, double* xbar,
                                 double* xmd0, double* xt, double* ax, double* y, double* ybar, double* ay) {
@@ -1967,7 +1980,8 @@ static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt
 
 template <typename V, int NT>
 static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
-                      const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
+                      const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s,
+                      bool compact) {
   Profiler& Pr = w.prof;
   DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
   PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
@@ -1977,6 +1991,13 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
   V* lpP = sizeof(V) == 4 ? (V*)w.P.lpart_f : (V*)w.P.lpart_d;
   if (w.A.nlseg) { da.blk_seg = w.A.blk_seg; da.lpart = lpA; }
   if (w.P.nlseg) { pa.blk_seg = w.P.blk_seg; pa.lpart = lpP; }
+  int gA = w.A.nblk, gP = w.P.nblk;
+  if (compact) {   // only the running instances' row blocks (counts of the last check)
+    da.act = w.act_A;
+    pa.act = w.act_P;
+    gA = w.bst_host->act_A;
+    gP = w.bst_host->act_P;
+  }
   for (int j = j0; j < j0 + len; ++j) {
     if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
     if (w.m > 0) {
@@ -1986,7 +2007,7 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
       if (w.A.nlseg)
         launch(k_long_partials<V>, w.A.nlseg, 256, 0, s, A, (const V*)xt, (const int4*)w.A.lseg,
                (const int*)w.blk_inst_A, (const DevState*)w.st, lpA);
-      launch(k_dual<V, NT>, w.A.nblk, NT, 0, s, da, j);
+      launch(k_dual<V, NT>, gA, NT, 0, s, da, j);
       if (Pr.on) Pr.end(s);
     }
     pa.zin = Z[j & 1];
@@ -1995,13 +2016,13 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
     if (w.P.nlseg)
       launch(k_long_partials<V>, w.P.nlseg, 256, 0, s, P, (const V*)pa.zin, (const int4*)w.P.lseg,
              (const int*)w.blk_inst_P, (const DevState*)w.st, lpP);
-    if (w.r > 0) launch(k_primal<V, NT, true>, w.P.nblk, NT, 0, s, pa, j);
-    else launch(k_primal<V, NT, false>, w.P.nblk, NT, 0, s, pa, j);
+    if (w.r > 0) launch(k_primal<V, NT, true>, gP, NT, 0, s, pa, j);
+    else launch(k_primal<V, NT, false>, gP, NT, 0, s, pa, j);
     if (Pr.on) Pr.end(s);
   }
 }
 
-void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0) {
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0, bool compact) {
   if (nt == 1) {   // pipelined persistent kernels, 256 threads
     if (mixed) {
       run_chunk_pipe<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
@@ -2017,18 +2038,18 @@ void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0)
   if (mixed) {
     if (nt != 512)
       run_chunk<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
-                            w.fxbar, w.fc, w.fl, w.fu, s);
+                            w.fxbar, w.fc, w.fl, w.fu, s, compact);
     else
       run_chunk<float, 512>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
-                            w.fxbar, w.fc, w.fl, w.fu, s);
+                            w.fxbar, w.fc, w.fl, w.fu, s, compact);
     w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
   } else {
     if (nt != 512)
       run_chunk<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
-                             w.cs, w.ls, w.us, s);
+                             w.cs, w.ls, w.us, s, compact);
     else
       run_chunk<double, 512>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
-                             w.cs, w.ls, w.us, s);
+                             w.cs, w.ls, w.us, s, compact);
     w.y = w.Z[(j0 + len - 1) & 1] + w.n;
   }
 }
@@ -2088,6 +2109,14 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
            (const int*)w.row_inst_m, w.n, w.m, w.x, w.xbar, w.Z[0], w.xt, w.ax, w.y, w.ybar, w.ay);
   }
   launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, w.count, w.bst);
+  if (w.count > 1) {   // the running instances' row blocks, for compacted launches
+    cudaMemsetAsync(&w.bst->act_A, 0, 2 * sizeof(int), s);
+    if (w.A.nblk > 0)
+      launch(k_compact_blocks, std::min(cdiv(w.A.nblk, 256), 4 * w.num_sms), 256, 0, s, (const int*)w.blk_inst_A,
+             w.A.nblk, (const DevState*)w.st, w.act_A, &w.bst->act_A);
+    launch(k_compact_blocks, std::min(cdiv(w.P.nblk, 256), 4 * w.num_sms), 256, 0, s, (const int*)w.blk_inst_P,
+           w.P.nblk, (const DevState*)w.st, w.act_P, &w.bst->act_P);
+  }
   if (w.prof.on) w.prof.end(s);
 }
 

@@ -125,6 +125,8 @@ struct Work {
   double *cpart_m = nullptr; // [9][nchunk_m]  chunk sums of part_m (KKT_CHUNK blocks each)
   double *cpart_n = nullptr; // [15][nchunk_n]
   int nchunk_m = 0, nchunk_n = 0, maxchunk_m = 0, maxchunk_n = 0;
+  int* act_A = nullptr;      // batches: [A.nblk] row blocks of the running instances (count in bst)
+  int* act_P = nullptr;      // [P.nblk]
   StepEntry* tab = nullptr;  // [count][tab_stride]
   DevState* st = nullptr;    // [count]
   DevState* st_host = nullptr;   // pinned mirror [count]
@@ -149,7 +151,9 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
 
 // iteration
 // Iterations j0 .. j0+len-1 of a chunk (j indexes the chunk's step table).
-void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0);
+// compact: launch only the row blocks of the running instances (batches; the
+// counts of the last check must be in bst_host).
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0, bool compact = false);
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
 
 // results
