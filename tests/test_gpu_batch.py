@@ -143,3 +143,49 @@ def test_family_handle_rejects_bad_input(pdqp):
     C, B = fam.params(0, 3)
     h = pdqp.family_from_base(fam.base, C, B, device=True)
     pdqp.pdqp_destroy(h)
+
+
+def test_full_mpc_batch_sampled(pdqp):
+    """Configuration 3 at full size (4096 MPC QPs, horizons 10..100, one
+    handle, mixed precision): every instance optimal; sampled instances
+    re-checked by the oracle's relKKT and objective."""
+    insts = qpgen.mpc_batch(4096)
+    st, infos, xs, ys = _solve_batch(pdqp, insts, precision=1)
+    assert st == pdqp.PDQP_OK
+    assert all(i.status == pdqp.PDQP_OK for i in infos)
+    rng = np.random.default_rng(3)
+    sample = sorted(rng.choice(len(insts), 12, replace=False))
+    for k in sample:
+        parts = R.kkt_parts(R.problem_from_instance(insts[k]), xs[k], ys[k])
+        assert parts["rel_kkt"] <= 1.0001e-6, (k, parts)
+    for k in sample[:2]:
+        ref = R.solve(insts[k], R.Options())
+        obj = ref.kkt["primal_obj"]
+        got = R.kkt_parts(R.problem_from_instance(insts[k]), xs[k], ys[k])["primal_obj"]
+        assert abs(got - obj) <= 1e-6 * (1 + abs(obj)), k
+
+
+def test_full_size_family_sampled(pdqp):
+    """Configuration 4's family at full size (n = 2e4, m = 1e4): 64 members in
+    one family handle; sampled members re-checked by the oracle."""
+    fam = qpgen.family_qp()
+    C, B = fam.params(5000, 64)
+    h = pdqp.family_from_base(fam.base, C, B)
+    try:
+        n, m = fam.base.n, fam.base.m
+        x, y = np.zeros(64 * n), np.zeros(64 * m)
+        st, _ = pdqp.pdqp_solve(h, pdqp.pdqp_default_options(precision=1), x_out=x, y_out=y)
+        infos = pdqp.pdqp_batch_info(h)
+    finally:
+        pdqp.pdqp_destroy(h)
+    assert st == pdqp.PDQP_OK and all(i.status == pdqp.PDQP_OK for i in infos)
+    X, Y = x.reshape(64, n), y.reshape(64, m)
+    for k in (0, 17, 40, 63):
+        inst = qpgen.QPInstance("member", n, m, fam.base.m_eq, fam.base.Q, fam.base.A, C[k], B[k], fam.base.l,
+                                fam.base.u)
+        parts = R.kkt_parts(R.problem_from_instance(inst), X[k], Y[k])
+        assert parts["rel_kkt"] <= 1.0001e-6, (k, parts)
+        if k == 17:
+            ref = R.solve(inst, R.Options())
+            obj = ref.kkt["primal_obj"]
+            assert abs(parts["primal_obj"] - obj) <= 1e-6 * (1 + abs(obj))
