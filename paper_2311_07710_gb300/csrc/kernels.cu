@@ -1204,6 +1204,28 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
   if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)la.nblkP + blockIdx.x] = f[1]; }
 }
 
+// Per-thread sums of the two fields of row blocks [b0, b1) (stride blockDim):
+// four independent accumulators, combined in a fixed order.
+__device__ __forceinline__ void lz_block_sums(const double* __restrict__ part, int nblkP, int b0, int b1,
+                                              double (&f)[2]) {
+  double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
+  const int st = blockDim.x;
+  int b = b0 + threadIdx.x;
+  for (; b + 3 * st < b1; b += 4 * st) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[0][u] += part[b + u * st];
+      acc[1][u] += part[(size_t)nblkP + b + u * st];
+    }
+  }
+  for (int u = 0; b < b1; b += st, ++u) {
+    acc[0][u] += part[b];
+    acc[1][u] += part[(size_t)nblkP + b];
+  }
+  f[0] = (acc[0][0] + acc[0][1]) + (acc[0][2] + acc[0][3]);
+  f[1] = (acc[1][0] + acc[1][1]) + (acc[1][2] + acc[1][3]);
+}
+
 // one CUDA block per instance: alpha_k = sum of its row blocks' partials
 __global__ void __launch_bounds__(128) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
   const int i = blockIdx.x;
@@ -1211,7 +1233,7 @@ __global__ void __launch_bounds__(128) k_lz_alpha(LzArgs a, const double* __rest
   if (st.pi_done[0] && st.pi_done[1]) return;
   const Inst in = a.inst[i];
   double f[2] = {0.0, 0.0};
-  for (int b = in.bP0 + threadIdx.x; b < in.bP1; b += blockDim.x) { f[0] += part[b]; f[1] += part[(size_t)a.nblkP + b]; }
+  lz_block_sums(part, a.nblkP, in.bP0, in.bP1, f);
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   if (threadIdx.x == 0) {
@@ -1326,7 +1348,7 @@ __global__ void __launch_bounds__(64) k_lz_beta(LzArgs a, const double* __restri
   if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
   const Inst in = a.inst[i];
   double f[2] = {0.0, 0.0};
-  for (int b = in.bP0 + threadIdx.x; b < in.bP1; b += blockDim.x) { f[0] += part[b]; f[1] += part[(size_t)a.nblkP + b]; }
+  lz_block_sums(part, a.nblkP, in.bP0, in.bP1, f);
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   __shared__ double beta[2];
