@@ -354,6 +354,7 @@ def run_ours(args, world, rank, local):
             "iterations_per_solve": iters if per_step == 1 else
             {"min": min(inst_iters), "median": statistics.median(inst_iters), "max": max(inst_iters)},
             "statuses": statuses,
+            "spmv_variant": infos[-1].spmv_threads,
             "iterations_per_sec": world * args.steps * sum(inst_iters) / (t_ms_max / 1e3),
             "rel_kkt": max(i.rel_kkt for i in infos),
             "setup_ms": 1e3 * infos[-1].setup_seconds, "iterate_ms": 1e3 * infos[-1].iterate_seconds,

@@ -405,34 +405,44 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   long long k_total = 0;
   bool timed_out = false;
   // autotuning of the iteration-kernel variant: the first full chunk runs
-  // TUNE iterations with each candidate (the iterates do not depend on the
-  // variant), the rest with the fastest
+  // two rounds of TUNE iterations with each candidate (interleaved, so that no
+  // candidate always runs first on a cold cache), keeps the fastest by its
+  // better round and runs the rest of the chunk with it; the iterates do not
+  // depend on the variant
   static const int kCand[3] = {256, 512, 1};
-  constexpr int TUNE = 8;
+  constexpr int TUNE = 4, ROUNDS = 2;
   const bool autotune = o.spmv_threads == 0;
   if (autotune && h->tuned_nt) p.spmv_threads = h->tuned_nt;
   while (w.bst_host->running > 0) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
-    const bool tune_now = autotune && !h->tuned_nt && len == o.check_period && len >= 4 * TUNE;
+    const bool tune_now = autotune && !h->tuned_nt && len == o.check_period && len >= 2 * 3 * ROUNDS * TUNE;
     // per-kernel event timing needs direct launches (events recorded by graph
     // nodes cannot be timed), so profiling bypasses the graph
     if (tune_now) {
       for (auto& e : h->tune_ev)
         if (!e) CK(cudaEventCreate(&e));
-      CK(cudaEventRecord(h->tune_ev[0], s));
-      for (int c = 0; c < 3; ++c) {
-        pdqp::iterate_chunk(w, TUNE, mixed, kCand[c], s, c * TUNE);
-        CK(cudaEventRecord(h->tune_ev[c + 1], s));
+      float best_ms[3] = {0.f, 0.f, 0.f};
+      int j = 0;
+      for (int r = 0; r < ROUNDS; ++r) {
+        CK(cudaEventRecord(h->tune_ev[0], s));
+        for (int c = 0; c < 3; ++c) {
+          pdqp::iterate_chunk(w, TUNE, mixed, kCand[c], s, j);
+          j += TUNE;
+          CK(cudaEventRecord(h->tune_ev[c + 1], s));
+        }
+        CK(cudaEventSynchronize(h->tune_ev[3]));
+        for (int c = 0; c < 3; ++c) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, h->tune_ev[c], h->tune_ev[c + 1]));
+          if (r == 0 || ms < best_ms[c]) best_ms[c] = ms;
+        }
       }
-      CK(cudaEventSynchronize(h->tune_ev[3]));
-      float best = 0.f;
-      for (int c = 0; c < 3; ++c) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, h->tune_ev[c], h->tune_ev[c + 1]));
-        if (c == 0 || ms < best) { best = ms; h->tuned_nt = kCand[c]; }
-      }
+      int bc = 0;
+      for (int c = 1; c < 3; ++c)
+        if (best_ms[c] < best_ms[bc]) bc = c;
+      h->tuned_nt = kCand[bc];
       p.spmv_threads = h->tuned_nt;
-      pdqp::iterate_chunk(w, (int)len - 3 * TUNE, mixed, p.spmv_threads, s, 3 * TUNE);
+      pdqp::iterate_chunk(w, (int)len - j, mixed, p.spmv_threads, s, j);
       pdqp::check(w, p, 1, len, mixed, s);
     } else if (len == o.check_period && !o.no_graphs && !w.prof.on && !compact_now(w, p)) {
       launch_chunk_graph(h, p, mixed, s);
