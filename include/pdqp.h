@@ -133,7 +133,9 @@ typedef struct {
 typedef struct {
   int64_t launches[4];
   double ms[4];              /* summed device milliseconds */
-  double bytes[4];           /* algorithmic DRAM bytes of one launch (kinds 0, 1) */
+  double bytes[4];           /* algorithmic DRAM bytes of one launch (kinds 0, 1): the mean
+                                over the timed launches of the bytes of the instances that
+                                were running at each launch */
 } pdqp_profile;
 
 /* Fill *opt with the defaults listed above. */

@@ -1620,12 +1620,14 @@ pdqp_status pdqp_profile_read(pdqp_handle h, pdqp_profile* out) {
     out->launches[k] = w.prof.launches[k];
     out->ms[k] = w.prof.ms[k];
   }
-  // algorithmic bytes: matrix (index + value) streams, row pointers, and each
-  // vector read or written once (the gathered vector counted once)
+  // algorithmic bytes per launch: the mean of each timed launch's bytes (the
+  // instances running at that launch); without timed launches, the whole problem
   const double sv = h->last_precision == PDQP_PREC_MIXED ? 4.0 : 8.0;
   const double n = w.n, m = w.m;
-  out->bytes[0] = (double)w.A.nnz * (sv + 4.0) + 4.0 * (m + 1) + sv * (n + 5.0 * m);
-  out->bytes[1] = (double)w.P.nnz * (sv + 4.0) + 4.0 * (n + 1) + sv * (10.0 * n + m);
+  const double full[2] = {(double)w.A.nnz * (sv + 4.0) + 4.0 * (m + 1) + sv * (n + 5.0 * m),
+                          (double)w.P.nnz * (sv + 4.0) + 4.0 * (n + 1) + sv * (10.0 * n + m)};
+  for (int k = 0; k < 2; ++k)
+    out->bytes[k] = w.prof.launches[k] > 0 ? w.prof.bytes[k] / (double)w.prof.launches[k] : full[k];
   return PDQP_OK;
 }
 

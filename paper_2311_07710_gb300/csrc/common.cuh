@@ -44,6 +44,7 @@ struct DevState {
   double bnorm_inf, cnorm_inf;   // ||b||_inf, ||c||_inf of the original data
   // power iteration
   double pi_lam[2], pi_lam_prev[2], pi_inv_norm[2];
+  double pi_hi_prev[2];  // bracket [pi_lam_prev, pi_hi_prev] of the previous Ritz value
   int pi_done[2];
   int pi_iters;
   int pad1;
@@ -66,6 +67,7 @@ struct BatchState {
   int running;           // instances still iterating
   int lz_running;        // instances whose norm estimates are still running
   int act_A, act_P;      // batches: row blocks of A / P of the running instances (lists in Work)
+  double run_n, run_m, run_nnzA, run_nnzP;   // sizes summed over the running instances
 };
 
 // Constant parameters of one solve.

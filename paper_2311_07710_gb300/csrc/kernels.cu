@@ -1309,22 +1309,65 @@ __device__ __forceinline__ int sturm_count(const double* __restrict__ al, const 
   return c;
 }
 
-// lambda_max of the k x k tridiagonal by 32-point multisection in one warp,
-// down to a bracket of 4e-15 relative.  One warp per operator keeps the
-// float64 work per round low (a batch of thousands of small problems pays it
-// per instance) and gives every operator its own scheduler partition.
-__device__ double tridiag_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be,
-                                       const double* __restrict__ be2, int k) {
+// The same count in float32 on the tridiagonal divided by its Gershgorin scale
+// (|al_i| <= 1, be2_i <= 1, |x| <= 1, so a step grows the terms at most 3x):
+// rescale by 2^-/+60 when |p_i| leaves [2^-60, 2^60].  Only a guess: the float64
+// count checks every bracket built from it.
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ al, const float* __restrict__ be2, int k,
+                                               float x) {
+  float pm = 1.f, pc = al[0] - x;
+  int bc = __float_as_int(pc);
+  if ((bc << 1) == 0) { pc = -0x1p-100f; bc = __float_as_int(pc); }
+  int c = (int)((unsigned)bc >> 31);
+  for (int i = 1; i < k; ++i) {
+    float pn = fmaf(al[i] - x, pc, -be2[i - 1] * pm);
+    int bn = __float_as_int(pn);
+    if ((bn << 1) == 0) {
+      pn = bc < 0 ? 0x1p-100f : -0x1p-100f;
+      bn = __float_as_int(pn);
+    }
+    c += (int)((unsigned)(bn ^ bc) >> 31);
+    pm = pc;
+    pc = pn;
+    bc = bn;
+    const int ex = (bn >> 23) & 0xFF;
+    if (ex > 127 + 60 || ex < 127 - 60) {
+      const float f = ex > 127 ? 0x1p-60f : 0x1p60f;
+      pc *= f;
+      pm *= f;
+      bc = __float_as_int(pc);
+    }
+  }
+  return c;
+}
+
+// Gershgorin bracket [lo, hi) of the spectrum of the k x k tridiagonal, one
+// warp: lanes take every 32nd row, then a shuffle tree
+__device__ __forceinline__ void gershgorin_warp(const double* __restrict__ al, const double* __restrict__ be, int k,
+                                                double& lo, double& hi) {
   const int lane = threadIdx.x & 31;
-  double lo = 1e300, hi = -1e300;   // Gershgorin bracket
-  for (int i = 0; i < k; ++i) {
+  lo = 1e300;
+  hi = -1e300;
+  for (int i = lane; i < k; i += 32) {
     const double r = (i > 0 ? be[i - 1] : 0.0) + (i < k - 1 ? be[i] : 0.0);
     lo = fmin(lo, al[i] - r);
     hi = fmax(hi, al[i] + r);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
   hi += 1e-300 + fabs(hi) * 1e-15;
+}
+
+// 32-point multisection of a bracket [lo, hi) of lambda_max in one warp, down
+// to 4e-15 relative; returns its midpoint
+__device__ double refine_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be2, int k,
+                                      double lo, double hi) {
+  const int lane = threadIdx.x & 31;
   for (int round = 0; round < 16 && hi - lo > 4e-15 * fabs(hi); ++round) {
-    const double step = (hi - lo) / 33.0;
+    const double step = (hi - lo) * (1.0 / 33.0);
     const double x = lo + step * (double)(lane + 1);
     const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be2, k, x) < k);   // lambda_max >= x
     if (ge == 0u) {
@@ -1339,10 +1382,63 @@ __device__ double tridiag_max_eig_warp(const double* __restrict__ al, const doub
   return 0.5 * (lo + hi);
 }
 
-// one CUDA block of 64 threads per instance: beta, theta = lambda_max(T_k)
-// (warp 0: A'A, warp 1: Q), stop test
-__global__ void __launch_bounds__(64) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
-                                               int max_steps) {
+// A bracket [lo, hi) of lambda_max of the k x k tridiagonal, about 1e-6 of its
+// Gershgorin scale wide, that float64 Sturm counts at both ends confirm: four
+// float32 multisection rounds (alf, be2f: the tridiagonal divided by the
+// scale, written here), a margin of 2^-16 of the scale on both sides, then one
+// float64 round whose outer lanes sit on the ends.  Falls back to the
+// Gershgorin bracket when the check fails.  One warp.
+__device__ void bracket_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be,
+                                     const double* __restrict__ be2, float* __restrict__ alf,
+                                     float* __restrict__ be2f, int k, double& lo, double& hi) {
+  const int lane = threadIdx.x & 31;
+  double glo, ghi;
+  gershgorin_warp(al, be, k, glo, ghi);
+  lo = glo;
+  hi = ghi;
+  const double G = fmax(fabs(glo), fabs(ghi));
+  if (!(G > 1e-280 && G < 1e280) || ghi - glo <= 1e-5 * G) return;
+  const double iG = 1.0 / G;
+  for (int i = lane; i < k; i += 32) {
+    alf[i] = (float)(al[i] * iG);
+    if (i < k - 1) be2f[i] = (float)(be2[i] * iG * iG);
+  }
+  __syncwarp();
+  float flo = (float)(glo * iG), fhi = (float)(ghi * iG);
+  for (int round = 0; round < 4; ++round) {
+    const float step = (fhi - flo) * (1.f / 33.f);
+    const float x = flo + step * (float)(lane + 1);
+    const unsigned ge = __ballot_sync(0xffffffffu, sturm_count_f32(alf, be2f, k, x) < k);
+    if (ge == 0u) {
+      fhi = flo + step;
+    } else {
+      const int t = 31 - __clz(ge);
+      const float nlo = flo + step * (float)(t + 1);
+      fhi = t == 31 ? fhi : flo + step * (float)(t + 2);
+      flo = nlo;
+    }
+  }
+  const double clo = fmax(glo, ((double)flo - 0x1p-16) * G);
+  const double chi = fmin(ghi, ((double)fhi + 0x1p-16) * G);
+  const double step = (chi - clo) * (1.0 / 31.0);
+  const double x = lane == 31 ? chi : clo + step * (double)lane;
+  const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be2, k, x) < k);
+  if ((ge & 1u) && !(ge >> 31)) {              // lambda_max in [clo, chi)
+    const int t = 31 - __clz(ge);
+    lo = clo + step * (double)t;
+    hi = t == 30 ? chi : clo + step * (double)(t + 1);
+  }
+}
+
+// one CUDA block of 128 threads per instance: beta, theta = lambda_max(T_k) and
+// the stop test for both operators (warps 0, 1: A'A; warps 2, 3: Q).  The stop
+// test |theta_k - theta_{k-1}| <= tol theta_k (or beta_k <= 1e-12 theta_k, or the
+// step limit) needs the precise Ritz values only where the brackets of
+// theta_k and theta_{k-1} cannot decide it: then the first warp of the pair
+// refines theta_k and the second theta_{k-1} from their brackets, and the
+// outcome is the one the precise values give at every step.
+__global__ void __launch_bounds__(128) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
+                                                int max_steps) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
@@ -1351,9 +1447,10 @@ __global__ void __launch_bounds__(64) k_lz_beta(LzArgs a, const double* __restri
   lz_block_sums(part, a.nblkP, in.bP0, in.bP1, f);
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
-  __shared__ double beta[2];
-  __shared__ int done_in[2];
+  __shared__ double beta[2], s_lo[2], s_hi[2], s_theta[2][2];
+  __shared__ int done_in[2], s_precise[2];
   __shared__ double s_al[2][LZ_MAX], s_be[2][LZ_MAX], s_be2[2][LZ_MAX];
+  __shared__ float s_alf[2][LZ_MAX], s_be2f[2][LZ_MAX];
   const int k = st.pi_iters + 1;                  // alphas 0..k-1, betas 0..k-2 form T_k
   if (threadIdx.x == 0) {
     beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]);
@@ -1369,17 +1466,47 @@ __global__ void __launch_bounds__(64) k_lz_beta(LzArgs a, const double* __restri
       }
     }
   __syncthreads();
-  const int o = threadIdx.x >> 5;
-  if (!done_in[o]) {                              // warp-uniform
-    const double theta = tridiag_max_eig_warp(s_al[o], s_be[o], s_be2[o], k);
-    if ((threadIdx.x & 31) == 0) {
-      const double b = beta[o];
+  const int o = threadIdx.x >> 6, second = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+  const double plo = st.pi_lam_prev[o], phi = st.pi_hi_prev[o];   // bracket of theta_{k-1}
+  if (!done_in[o] && !second) {                   // warp-uniform
+    double lo, hi;
+    bracket_max_eig_warp(s_al[o], s_be[o], s_be2[o], s_alf[o], s_be2f[o], k, lo, hi);
+    const double mag = fmax(fabs(lo), fabs(hi));
+    const double gap = fmax(fmax(lo - phi, plo - hi), 0.0);   // least |theta_k - theta_{k-1}|
+    const bool go_on = k < max_steps && beta[o] > 1e-12 * mag && gap > tol * mag;
+    if (lane == 0) {
+      s_lo[o] = lo;
+      s_hi[o] = hi;
+      s_precise[o] = !go_on;
+    }
+  }
+  __syncthreads();
+  if (!done_in[o] && s_precise[o]) {
+    if (!second)
+      s_theta[o][0] = refine_max_eig_warp(s_al[o], s_be2[o], k, s_lo[o], s_hi[o]);
+    else if (plo != phi)
+      s_theta[o][1] = refine_max_eig_warp(s_al[o], s_be2[o], k - 1, plo, phi);
+    else if (lane == 0)
+      s_theta[o][1] = plo;
+  }
+  __syncthreads();
+  if (!done_in[o] && !second && lane == 0) {
+    const double b = beta[o];
+    if (!s_precise[o]) {                          // continues: keep the bracket
+      st.pi_lam[o] = 0.5 * (s_lo[o] + s_hi[o]);
+      st.pi_lam_prev[o] = s_lo[o];
+      st.pi_hi_prev[o] = s_hi[o];
+      lz_be(a, i, o)[k - 1] = b;
+      st.pi_inv_norm[o] = 1.0 / b;
+    } else {
+      const double theta = s_theta[o][0], theta_prev = s_theta[o][1];
       st.pi_lam[o] = theta;
-      if (fabs(theta - st.pi_lam_prev[o]) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
+      if (fabs(theta - theta_prev) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
         st.pi_done[o] = 1;
       } else {
         lz_be(a, i, o)[k - 1] = b;
         st.pi_lam_prev[o] = theta;
+        st.pi_hi_prev[o] = theta;
         st.pi_inv_norm[o] = 1.0 / b;
       }
     }
@@ -1413,6 +1540,7 @@ __global__ void k_lz_init(LzArgs a, V* __restrict__ vA0, V* __restrict__ vA1, V*
     st.pi_done[1] = 0;
     st.pi_lam[0] = 0.0; st.pi_lam[1] = 0.0;
     st.pi_lam_prev[0] = 0.0; st.pi_lam_prev[1] = 0.0;
+    st.pi_hi_prev[0] = 0.0; st.pi_hi_prev[1] = 0.0;
     st.pi_inv_norm[0] = 1.0; st.pi_inv_norm[1] = 1.0;
     st.pi_iters = 0;
   }
@@ -1603,15 +1731,31 @@ __global__ void __launch_bounds__(64) k_decide(DevState* __restrict__ sts, const
 }
 
 // number of instances still iterating / still estimating norms
-__global__ void k_count_running(const DevState* __restrict__ sts, int count, BatchState* bst) {
+__global__ void k_count_running(const DevState* __restrict__ sts, const Inst* __restrict__ inst,
+                                const int* __restrict__ rpA, const int* __restrict__ rpP, int count,
+                                BatchState* bst) {
   int run = 0, lz = 0;
+  double f[4] = {0.0, 0.0, 0.0, 0.0};   // rows of P and A, nonzeros of A and P of the running instances
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    run += sts[i].status == ST_RUNNING;
+    const bool r = sts[i].status == ST_RUNNING;
+    run += r;
     lz += !(sts[i].pi_done[0] && sts[i].pi_done[1]);
+    if (r) {
+      const Inst in = inst[i];
+      f[0] += in.n;
+      f[1] += in.m;
+      if (in.m > 0) f[2] += rpA[in.yoff + in.m] - rpA[in.yoff];
+      f[3] += rpP[in.xoff + in.n] - rpP[in.xoff];
+    }
   }
   run = block_sum(run);
   lz = block_sum(lz);
-  if (threadIdx.x == 0) { bst->running = run; bst->lz_running = lz; }
+  const bool is_max[4] = {false, false, false, false};
+  block_reduce<4>(f, is_max);
+  if (threadIdx.x == 0) {
+    bst->running = run; bst->lz_running = lz;
+    bst->run_n = f[0]; bst->run_m = f[1]; bst->run_nnzA = f[2]; bst->run_nnzP = f[3];
+  }
 }
 
 __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
@@ -1894,7 +2038,7 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   launch(k_lz_alpha, w.count, 128, 0, s, la, (const double*)w.part_n);
   launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
          (const V*)pz[cur], pz[prv], w.part_n);
-  launch(k_lz_beta, w.count, 64, 0, s, la, (const double*)w.part_n, p.norm_tol,
+  launch(k_lz_beta, w.count, 128, 0, s, la, (const double*)w.part_n, p.norm_tol,
          p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
   const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
   launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
@@ -1911,7 +2055,8 @@ void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t
 }
 
 void count_running(Work& w, cudaStream_t s) {
-  launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, w.count, w.bst);
+  launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, (const Inst*)w.inst, (const int*)w.A.rp,
+         (const int*)w.P.rp, w.count, w.bst);
 }
 
 void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
@@ -1973,6 +2118,16 @@ static int pipe_grid_p(void (*kern)(PrimalB<V>, const int4*, int, int)) {
   return blocks;
 }
 
+// Algorithmic bytes of one dual (kind 0) or primal (kind 1) launch over the
+// instances running at the last check: the matrix streams (index + value),
+// the row pointers, each vector read or written once (the gathered vector
+// counted once); sv = bytes per value.
+static double launch_bytes(const Work& w, int kind, double sv) {
+  const BatchState& b = *w.bst_host;
+  if (kind == 0) return b.run_nnzA * (sv + 4.0) + 4.0 * (b.run_m + 1.0) + sv * (b.run_n + 5.0 * b.run_m);
+  return b.run_nnzP * (sv + 4.0) + 4.0 * (b.run_n + 1.0) + sv * (10.0 * b.run_n + b.run_m);
+}
+
 template <typename V, int NT>
 static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
                            const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
@@ -1988,13 +2143,13 @@ static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
-      if (Pr.on) Pr.begin(0, s);
+      if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
       launch(k_dual_pipe<V, NT>, gd, NT, smem, s, da, (const int4*)w.A.meta, w.A.nblk, j);
       if (Pr.on) Pr.end(s);
     }
     pa.zin = Z[j & 1];
     pa.zout = Z[(j + 1) & 1];
-    if (Pr.on) Pr.begin(1, s);
+    if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
     launch(k_primal_pipe<V, NT>, gp, NT, smem, s, pa, (const int4*)w.P.meta, w.P.nblk, j);
     if (Pr.on) Pr.end(s);
   }
@@ -2025,7 +2180,7 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
-      if (Pr.on) Pr.begin(0, s);
+      if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
       if (w.A.nlseg)
         launch(k_long_partials<V>, w.A.nlseg, 256, 0, s, A, (const V*)xt, (const int4*)w.A.lseg,
                (const int*)w.blk_inst_A, (const DevState*)w.st, lpA);
@@ -2034,7 +2189,7 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
     }
     pa.zin = Z[j & 1];
     pa.zout = Z[(j + 1) & 1];
-    if (Pr.on) Pr.begin(1, s);
+    if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
     if (w.P.nlseg)
       launch(k_long_partials<V>, w.P.nlseg, 256, 0, s, P, (const V*)pa.zin, (const int4*)w.P.lseg,
              (const int*)w.blk_inst_P, (const DevState*)w.st, lpP);
@@ -2130,7 +2285,8 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     launch(k_restart_apply, grid_v, 256, 0, s, (const DevState*)w.st, (const int*)w.row_inst_n,
            (const int*)w.row_inst_m, w.n, w.m, w.x, w.xbar, w.Z[0], w.xt, w.ax, w.y, w.ybar, w.ay);
   }
-  launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, w.count, w.bst);
+  launch(k_count_running, 1, 256, 0, s, (const DevState*)w.st, (const Inst*)w.inst, (const int*)w.A.rp,
+         (const int*)w.P.rp, w.count, w.bst);
   if (w.count > 1) {   // the running instances' row blocks, for compacted launches
     cudaMemsetAsync(&w.bst->act_A, 0, 2 * sizeof(int), s);
     if (w.A.nblk > 0)
@@ -2185,7 +2341,7 @@ void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
 }  // namespace pdqp
 
 // ---------------------------------------------------------------- profiler
-void Profiler::begin(int k, cudaStream_t s) {
+void Profiler::begin(int k, cudaStream_t s, double b) {
   const size_t need = 2 * (kind.size() + 1);
   while (ev.size() < need) {
     cudaEvent_t e;
@@ -2194,6 +2350,7 @@ void Profiler::begin(int k, cudaStream_t s) {
   }
   cudaEventRecord(ev[2 * kind.size()], s);
   kind.push_back(k);
+  kbytes.push_back(b);
 }
 void Profiler::end(cudaStream_t s) {
   if (kind.empty()) return;
@@ -2205,15 +2362,18 @@ void Profiler::harvest() {
     if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
       ms[kind[i]] += t;
       launches[kind[i]] += 1;
+      bytes[kind[i]] += kbytes[i];
     } else {
       cudaGetLastError();   // a failed timing query must not surface as a later error
     }
   }
   kind.clear();
+  kbytes.clear();
 }
 void Profiler::reset() {
   kind.clear();
-  for (int i = 0; i < 4; ++i) { launches[i] = 0; ms[i] = 0.0; }
+  kbytes.clear();
+  for (int i = 0; i < 4; ++i) { launches[i] = 0; ms[i] = 0.0; bytes[i] = 0.0; }
 }
 Profiler::~Profiler() {
   for (cudaEvent_t e : ev) cudaEventDestroy(e);

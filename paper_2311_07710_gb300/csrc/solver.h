@@ -60,9 +60,11 @@ struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> ev;   // pool; pairs (begin, end)
   std::vector<int> kind;         // kind of each pair in flight
+  std::vector<double> kbytes;    // algorithmic bytes of each pair in flight
   long long launches[4] = {0, 0, 0, 0};
   double ms[4] = {0, 0, 0, 0};
-  void begin(int k, cudaStream_t s);
+  double bytes[4] = {0, 0, 0, 0};
+  void begin(int k, cudaStream_t s, double b = 0.0);
   void end(cudaStream_t s);
   void harvest();                // after the stream was synchronised
   void reset();
