@@ -35,7 +35,9 @@ WORKLOAD = "large_sparse_qp n=1e6 m=5e5 (m_eq=2.5e5), A 10 nnz/col N(0,1), Q dia
 REF_JSON = os.path.join(ROOT, "tests", "golden", "large_sparse_qp_reference.json")
 PEAKS_JSON = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_TXT = os.path.join(ROOT, "profiles", "traffic.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2311_07710_gb300", "csrc", "kernels.cu")
+# the sources the iteration kernels (k_dual, k_primal) are compiled from
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2311_07710_gb300", "csrc", f)
+               for f in ("iteration.cu", "rowblock.cuh", "common.cuh")]
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal float64 rate (no FP64 tensor path used)
 
 
@@ -193,12 +195,20 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------------- ours
+def kernel_sha():
+    """sha256[:16] over the iteration kernels' sources, in KERNEL_SRCS order."""
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary for this kernel and
     workload, if it was taken on the current kernel source; else None."""
     if not os.path.exists(TRAFFIC_TXT):
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    sha = kernel_sha()
     for line in open(TRAFFIC_TXT):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload \

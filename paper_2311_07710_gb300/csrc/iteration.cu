@@ -1,0 +1,502 @@
+// The inner iteration of Algorithm 1 (Section 2) as two fused row-block
+// kernels per iteration:
+//   k_dual   : rows of A   -- v = A x_tilde, y+ = proj_Y(y - sigma (v - b)),
+//              y_bar+ = (1 - 1/beta) y_bar + y+/beta
+//   k_primal : rows of P = [Q | -A'] gathering [x_md ; y+] -- g = Q x_md + c - A'y+,
+//              x+ = proj_[l,u](x - tau g), x_bar+ = (1 - 1/beta) x_bar + x+/beta,
+//              and the next iteration's x_md and x_tilde
+// with their pipelined persistent variants, the segment sums of long rows,
+// and the host loop that launches a chunk of iterations.
+#include <algorithm>
+
+#include "rowblock.cuh"
+
+namespace pdqp {
+
+// --------------------------------------------------------------------------
+// One inner iteration of Algorithm 1: the dual half-step (rows of A)
+// --------------------------------------------------------------------------
+template <typename V>
+struct DualB {
+  BCsr<V> A;
+  const V* __restrict__ xt;      // extrapolated primal point x_tilde
+  const V* __restrict__ yold;    // y^k
+  V* __restrict__ ynew;          // y^{k+1}
+  V* __restrict__ ybar;
+  const V* __restrict__ b;
+  const V* __restrict__ ylo;     // lower bound of inequality duals (mixed-mode shift) or null (0)
+  const StepEntry* __restrict__ tab;    // [instance][C]
+  const int* __restrict__ blk_inst;     // instance of each row block
+  const DevState* __restrict__ st;      // per instance
+  const unsigned char* __restrict__ ineq;   // per row: inequality
+  int C;
+  const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
+  const V* __restrict__ lpart;          // segment sums of the long rows
+  const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
+};
+
+template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
+template <> __device__ __forceinline__ double step_sigma<double>(const StepEntry& e) { return e.sigma_d; }
+template <> __device__ __forceinline__ float step_sigma<float>(const StepEntry& e) { return e.sigma_d_f; }
+template <typename V> __device__ __forceinline__ V step_tau(const StepEntry& e);
+template <> __device__ __forceinline__ double step_tau<double>(const StepEntry& e) { return e.tau_p; }
+template <> __device__ __forceinline__ float step_tau<float>(const StepEntry& e) { return e.tau_p_f; }
+template <typename V> __device__ __forceinline__ V step_ib(const StepEntry& e);
+template <> __device__ __forceinline__ double step_ib<double>(const StepEntry& e) { return e.inv_beta; }
+template <> __device__ __forceinline__ float step_ib<float>(const StepEntry& e) { return e.inv_beta_f; }
+template <typename V> __device__ __forceinline__ V step_ibn(const StepEntry& e);
+template <> __device__ __forceinline__ double step_ibn<double>(const StepEntry& e) { return e.inv_beta_next; }
+template <> __device__ __forceinline__ float step_ibn<float>(const StepEntry& e) { return e.inv_beta_next_f; }
+template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
+template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
+template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
+
+template <typename V>
+__device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, int r, V s, V yo, V bi, V yb,
+                                         V lo) {
+  const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
+  V yn = yo - sigma * (s - bi);
+  if (a.ineq[r]) yn = fmax(yn, lo);
+  a.ybar[r] = (V(1) - ib) * yb + ib * yn;
+  a.ynew[r] = yn;
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a, int j) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;   // compacted batches: running blocks only
+  const int inst = a.blk_inst[bk];
+  if (a.st[inst].status != ST_RUNNING) return;
+  const int r0 = a.A.blk[bk], r1 = a.A.blk[bk + 1];
+  const int nr = r1 - r0;
+  const int e0 = a.A.rp[r0];
+  const int ne = a.A.rp[r1] - e0;
+  // operands of this thread's first row, fetched before the SpMV
+  V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
+  if (tid < nr) {
+    const int r = r0 + tid;
+    yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+    if (a.ylo) lo = a.ylo[r];
+  }
+  const StepEntry& es = a.tab[inst * a.C + j];
+  if (ne <= BNNZ) {
+    stage_products<NT>(a.A, a.xt, e0, ne, r0, nr, prod, srp);
+    __syncthreads();
+    for (int t = tid; t < nr; t += NT) {
+      V s = V(0);
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
+      const int r = r0 + t;
+      if (t >= BNT) {
+        yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+        lo = a.ylo ? a.ylo[r] : V(0);
+      }
+      dual_row(a, es, r, s, yo, bi, yb, lo);
+    }
+  } else if (a.blk_seg) {   // a long row: the sum of its segments (k_long_partials), in order
+    if (tid == 0) {
+      const int2 sg = a.blk_seg[bk];
+      V s = V(0);
+      for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
+      dual_row(a, es, r0, s, yo, bi, yb, lo);
+    }
+  } else {   // a single row longer than a block
+    V s = V(0);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
+    s = block_sum(s);
+    if (tid == 0) dual_row(a, es, r0, s, yo, bi, yb, lo);
+  }
+}
+
+// --------------------------------------------------------------------------
+// One inner iteration of Algorithm 1: the primal half-step (rows of P)
+// --------------------------------------------------------------------------
+template <typename V>
+struct PrimalB {
+  BCsr<V> P;
+  const V* __restrict__ zin;     // [x_md ; y^{k+1}] of this iteration
+  V* __restrict__ zout;          // x_md of the next iteration -> zout[0:n]
+  V* __restrict__ x;
+  V* __restrict__ xbar;
+  V* __restrict__ xt;            // x_tilde of the next iteration
+  const V* __restrict__ c;
+  const V* __restrict__ l;
+  const V* __restrict__ u;
+  const StepEntry* __restrict__ tab;    // [instance][C]
+  const int* __restrict__ blk_inst;
+  const DevState* __restrict__ st;
+  int C;
+  const V* __restrict__ F;              // low-rank factor F~ (null: none)
+  const V* __restrict__ wlr;            // F~' x_md of this iteration
+  int r;
+  const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
+  const V* __restrict__ lpart;          // segment sums of the long rows
+  const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
+};
+
+template <typename V, bool LR = false>
+__device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry& e, int r, V s, V xo, V xb0,
+                                           V cr, V lr, V ur) {
+  const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
+  const V g = s + cr + (LR ? lr_row<V, V, V>(a.F, a.wlr, a.r, r) : V(0));
+  const V xn = fmin(fmax(xo - tau * g, lr), ur);
+  const V xb = (V(1) - ib) * xb0 + ib * xn;
+  a.xbar[r] = xb;
+  a.zout[r] = (V(1) - ibn) * xb + ibn * xn;
+  a.xt[r] = xn + thn * (xn - xo);
+  a.x[r] = xn;
+}
+
+// LR: the problem has a low-rank term (its row term gets its own instantiation
+// so that the plain kernel keeps its 32 registers)
+template <typename V, int NT, bool LR = false>
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(PrimalB<V> a, int j) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int tid = threadIdx.x;
+  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
+  const int inst = a.blk_inst[bk];
+  if (a.st[inst].status != ST_RUNNING) return;
+  const int r0 = a.P.blk[bk], r1 = a.P.blk[bk + 1];
+  const int nr = r1 - r0;
+  const int e0 = a.P.rp[r0];
+  const int ne = a.P.rp[r1] - e0;
+  V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
+  if (tid < nr) {
+    const int r = r0 + tid;
+    xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
+  }
+  const StepEntry& es = a.tab[inst * a.C + j];
+  if (ne <= BNNZ) {
+    stage_products<NT>(a.P, a.zin, e0, ne, r0, nr, prod, srp);
+    __syncthreads();
+    for (int t = tid; t < nr; t += NT) {
+      V s = V(0);
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
+      const int r = r0 + t;
+      if (t >= BNT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
+      primal_row<V, LR>(a, es, r, s, xo, xb, cr, lr, ur);
+    }
+  } else if (a.blk_seg) {
+    if (tid == 0) {
+      const int2 sg = a.blk_seg[bk];
+      V s = V(0);
+      for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
+      primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
+    }
+  } else {
+    V s = V(0);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
+    s = block_sum(s);
+    if (tid == 0) primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
+  }
+}
+
+// Segment sums of the long rows: one CUDA block per segment of LSEG nonzeros
+// of M v (skipping instances that stopped); the iteration kernels add a row's
+// segments in order.
+template <typename V>
+__global__ void __launch_bounds__(256) k_long_partials(BCsr<V> M, const V* __restrict__ vec,
+                                                       const int4* __restrict__ lseg, const int* __restrict__ blk_inst,
+                                                       const DevState* __restrict__ st, V* __restrict__ out) {
+  const int4 g = lseg[blockIdx.x];
+  if (st[blk_inst[g.w]].status != ST_RUNNING) return;
+  V s = V(0);
+  for (int e = g.y + threadIdx.x; e < g.z; e += 256) s += M.val[e] * __ldg(vec + M.col[e]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+
+// ==========================================================================
+// Pipelined persistent variants of the two half-steps.  Each CUDA block loops
+// over row blocks b = blockIdx.x, blockIdx.x + gridDim.x, ...; while it
+// gathers and finishes block b, the index, value and row-pointer ranges of its
+// next block stream into the other shared-memory stage with cp.async (16-byte
+// copies of the 16-byte aligned superset of each range).  Block bounds come
+// from one int4 {r0, r1, e0, e1} per block.  Global index/value/rowptr arrays
+// carry 8 elements of padding so the aligned superset never leaves them.
+// ==========================================================================
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <typename V>
+struct PipeSmem {
+  int col[2][BNNZ + 8];
+  V val[2][BNNZ + 8];
+  int rp[2][BROWS + 8];
+  V prod[BNNZ];
+};
+
+// Queue the copies of block m = {r0, r1, e0, e1} into stage s (no copy for a long row).
+template <int NT, typename V>
+__device__ __forceinline__ void pipe_issue(PipeSmem<V>& sm, int s, const int4 m, const int* __restrict__ col,
+                                           const V* __restrict__ val, const int* __restrict__ rp) {
+  const int tid = threadIdx.x;
+  if (m.w - m.z <= BNNZ) {
+    const int a0 = m.z & ~3, a1 = (m.w + 3) & ~3;
+    for (int c = tid; c < (a1 - a0) >> 2; c += NT) cp_async16(&sm.col[s][c << 2], col + a0 + (c << 2));
+    constexpr int PER = 16 / sizeof(V);
+    for (int c = tid; c < (a1 - a0) / PER; c += NT) cp_async16(&sm.val[s][c * PER], val + a0 + c * PER);
+    const int q0 = m.x & ~3, q1 = (m.y + 1 + 3) & ~3;
+    for (int c = tid; c < (q1 - q0) >> 2; c += NT) cp_async16(&sm.rp[s][c << 2], rp + q0 + (c << 2));
+  }
+  cp_async_commit();
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __restrict__ meta, int nblk, int j) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
+  const int tid = threadIdx.x;
+  int b = blockIdx.x;
+  if (b >= nblk) return;
+  int4 mc = meta[b];
+  pipe_issue<NT>(sm, 0, mc, a.A.col, a.A.val, a.A.rp);
+  for (int s = 0; b < nblk; b += gridDim.x, s ^= 1) {
+    const int bn = b + gridDim.x;
+    int4 mn = make_int4(0, 0, 0, 0);
+    if (bn < nblk) mn = meta[bn];
+    pipe_issue<NT>(sm, s ^ 1, mn, a.A.col, a.A.val, a.A.rp);
+    const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
+    const int inst = a.blk_inst[b];
+    const bool live = a.st[inst].status == ST_RUNNING;
+    const StepEntry& es = a.tab[inst * a.C + j];
+    V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
+    if (live && tid < nr) {
+      const int r = r0 + tid;
+      yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+      if (a.ylo) lo = a.ylo[r];
+    }
+    cp_async_wait1();
+    __syncthreads();
+    if (!live) {
+    } else if (ne <= BNNZ) {
+      const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
+#pragma unroll
+      for (int k = 0; k < BNNZ / NT; ++k) {
+        const int e = tid + k * NT;
+        if (e < ne) sm.prod[e] = sm.val[s][e + off] * __ldg(a.xt + sm.col[s][e + off]);
+      }
+      __syncthreads();
+      for (int t = tid; t < nr; t += NT) {
+        V acc = V(0);
+        const int eb = sm.rp[s][t + roff] - e0, ee = sm.rp[s][t + 1 + roff] - e0;
+        for (int e = eb; e < ee; ++e) acc += sm.prod[e];
+        const int r = r0 + t;
+        if (t >= NT) {
+          yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+          lo = a.ylo ? a.ylo[r] : V(0);
+        }
+        dual_row(a, es, r, acc, yo, bi, yb, lo);
+      }
+    } else {
+      V acc = V(0);
+      for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
+      acc = block_sum(acc);
+      if (tid == 0) dual_row(a, es, r0, acc, yo, bi, yb, lo);
+    }
+    __syncthreads();
+    mc = mn;
+  }
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __restrict__ meta, int nblk, int j) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
+  const int tid = threadIdx.x;
+  int b = blockIdx.x;
+  if (b >= nblk) return;
+  int4 mc = meta[b];
+  pipe_issue<NT>(sm, 0, mc, a.P.col, a.P.val, a.P.rp);
+  for (int s = 0; b < nblk; b += gridDim.x, s ^= 1) {
+    const int bn = b + gridDim.x;
+    int4 mn = make_int4(0, 0, 0, 0);
+    if (bn < nblk) mn = meta[bn];
+    pipe_issue<NT>(sm, s ^ 1, mn, a.P.col, a.P.val, a.P.rp);
+    const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
+    const int inst = a.blk_inst[b];
+    const bool live = a.st[inst].status == ST_RUNNING;
+    const StepEntry& es = a.tab[inst * a.C + j];
+    V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
+    if (live && tid < nr) {
+      const int r = r0 + tid;
+      xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
+    }
+    cp_async_wait1();
+    __syncthreads();
+    if (!live) {
+    } else if (ne <= BNNZ) {
+      const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
+#pragma unroll
+      for (int k = 0; k < BNNZ / NT; ++k) {
+        const int e = tid + k * NT;
+        if (e < ne) sm.prod[e] = sm.val[s][e + off] * __ldg(a.zin + sm.col[s][e + off]);
+      }
+      __syncthreads();
+      for (int t = tid; t < nr; t += NT) {
+        V acc = V(0);
+        const int eb = sm.rp[s][t + roff] - e0, ee = sm.rp[s][t + 1 + roff] - e0;
+        for (int e = eb; e < ee; ++e) acc += sm.prod[e];
+        const int r = r0 + t;
+        if (t >= NT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
+        if (a.F) primal_row<V, true>(a, es, r, acc, xo, xb, cr, lr, ur);
+        else primal_row<V, false>(a, es, r, acc, xo, xb, cr, lr, ur);
+      }
+    } else {
+      V acc = V(0);
+      for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
+      acc = block_sum(acc);
+      if (tid == 0) {
+        if (a.F) primal_row<V, true>(a, es, r0, acc, xo, xb, cr, lr, ur);
+        else primal_row<V, false>(a, es, r0, acc, xo, xb, cr, lr, ur);
+      }
+    }
+    __syncthreads();
+    mc = mn;
+  }
+}
+
+template <typename V, int NT>
+static int pipe_grid(void (*kern)(DualB<V>, const int4*, int, int)) {
+  static int blocks = -1;
+  if (blocks < 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
+    blocks = per_sm > 0 ? per_sm : 1;
+  }
+  return blocks;
+}
+template <typename V, int NT>
+static int pipe_grid_p(void (*kern)(PrimalB<V>, const int4*, int, int)) {
+  static int blocks = -1;
+  if (blocks < 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
+    blocks = per_sm > 0 ? per_sm : 1;
+  }
+  return blocks;
+}
+
+// Algorithmic bytes of one dual (kind 0) or primal (kind 1) launch over the
+// instances running at the last check: the matrix streams (index + value),
+// the row pointers, each vector read or written once (the gathered vector
+// counted once); sv = bytes per value.
+static double launch_bytes(const Work& w, int kind, double sv) {
+  const BatchState& b = *w.bst_host;
+  if (kind == 0) return b.run_nnzA * (sv + 4.0) + 4.0 * (b.run_m + 1.0) + sv * (b.run_n + 5.0 * b.run_m);
+  return b.run_nnzP * (sv + 4.0) + 4.0 * (b.run_n + 1.0) + sv * (10.0 * b.run_n + b.run_m);
+}
+
+template <typename V, int NT>
+static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
+                           const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
+  Profiler& Pr = w.prof;
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
+                w.r > 0 ? lr_factor<V>(w) : nullptr, lr_weights<V>(w), w.r};
+  const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
+  const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
+  const size_t smem = sizeof(PipeSmem<V>);
+  for (int j = j0; j < j0 + len; ++j) {
+    if (w.r > 0) lowrank_ft1(w, pa.F, (const V*)Z[j & 1], s);
+    if (w.m > 0) {
+      da.yold = Z[(j + 1) & 1] + w.n;
+      da.ynew = Z[j & 1] + w.n;
+      if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
+      launch(k_dual_pipe<V, NT>, gd, NT, smem, s, da, (const int4*)w.A.meta, w.A.nblk, j);
+      if (Pr.on) Pr.end(s);
+    }
+    pa.zin = Z[j & 1];
+    pa.zout = Z[(j + 1) & 1];
+    if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
+    launch(k_primal_pipe<V, NT>, gp, NT, smem, s, pa, (const int4*)w.P.meta, w.P.nblk, j);
+    if (Pr.on) Pr.end(s);
+  }
+}
+
+template <typename V, int NT>
+static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
+                      const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s,
+                      bool compact) {
+  Profiler& Pr = w.prof;
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
+                w.r > 0 ? lr_factor<V>(w) : nullptr, lr_weights<V>(w), w.r};
+  // long rows: segment sums first (float or float64 buffers by V)
+  V* lpA = sizeof(V) == 4 ? (V*)w.A.lpart_f : (V*)w.A.lpart_d;
+  V* lpP = sizeof(V) == 4 ? (V*)w.P.lpart_f : (V*)w.P.lpart_d;
+  if (w.A.nlseg) { da.blk_seg = w.A.blk_seg; da.lpart = lpA; }
+  if (w.P.nlseg) { pa.blk_seg = w.P.blk_seg; pa.lpart = lpP; }
+  int gA = w.A.nblk, gP = w.P.nblk;
+  if (compact) {   // only the running instances' row blocks (counts of the last check)
+    da.act = w.act_A;
+    pa.act = w.act_P;
+    gA = w.bst_host->act_A;
+    gP = w.bst_host->act_P;
+  }
+  for (int j = j0; j < j0 + len; ++j) {
+    if (w.r > 0) lowrank_ft1(w, pa.F, (const V*)Z[j & 1], s);
+    if (w.m > 0) {
+      da.yold = Z[(j + 1) & 1] + w.n;
+      da.ynew = Z[j & 1] + w.n;
+      if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
+      if (w.A.nlseg)
+        launch(k_long_partials<V>, w.A.nlseg, 256, 0, s, A, (const V*)xt, (const int4*)w.A.lseg,
+               (const int*)w.blk_inst_A, (const DevState*)w.st, lpA);
+      launch(k_dual<V, NT>, gA, NT, 0, s, da, j);
+      if (Pr.on) Pr.end(s);
+    }
+    pa.zin = Z[j & 1];
+    pa.zout = Z[(j + 1) & 1];
+    if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
+    if (w.P.nlseg)
+      launch(k_long_partials<V>, w.P.nlseg, 256, 0, s, P, (const V*)pa.zin, (const int4*)w.P.lseg,
+             (const int*)w.blk_inst_P, (const DevState*)w.st, lpP);
+    if (w.r > 0) launch(k_primal<V, NT, true>, gP, NT, 0, s, pa, j);
+    else launch(k_primal<V, NT, false>, gP, NT, 0, s, pa, j);
+    if (Pr.on) Pr.end(s);
+  }
+}
+
+void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0, bool compact) {
+  if (nt == 1) {   // pipelined persistent kernels, 256 threads
+    if (mixed) {
+      run_chunk_pipe<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+                                 w.fxbar, w.fc, w.fl, w.fu, s);
+      w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
+    } else {
+      run_chunk_pipe<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x,
+                                  w.xbar, w.cs, w.ls, w.us, s);
+      w.y = w.Z[(j0 + len - 1) & 1] + w.n;
+    }
+    return;
+  }
+  if (mixed) {
+    if (nt != 512)
+      run_chunk<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+                            w.fxbar, w.fc, w.fl, w.fu, s, compact);
+    else
+      run_chunk<float, 512>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
+                            w.fxbar, w.fc, w.fl, w.fu, s, compact);
+    w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
+  } else {
+    if (nt != 512)
+      run_chunk<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
+                             w.cs, w.ls, w.us, s, compact);
+    else
+      run_chunk<double, 512>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
+                             w.cs, w.ls, w.us, s, compact);
+    w.y = w.Z[(j0 + len - 1) & 1] + w.n;
+  }
+}
+
+}  // namespace pdqp

@@ -1,15 +1,9 @@
-// Device kernels of the rAPDHG solver (sm_103a).
-//
-// One inner iteration of Algorithm 1 (Section 2) is two fused kernels:
-//   k_dual   : rows of A   -- v = A x_tilde, y+ = proj_Y(y - sigma (v - b)),
-//              y_bar+ = (1 - 1/beta) y_bar + y+/beta
-//   k_primal : rows of P = [Q | -A'] gathering [x_md ; y+] -- g = Q x_md + c - A'y+,
-//              x+ = proj_[l,u](x - tau g), x_bar+ = (1 - 1/beta) x_bar + x+/beta,
-//              and the next iteration's x_md and x_tilde
-// Every `check_period` iterations k_kkt_m / k_kkt_n reduce, in float64, the
-// relative KKT error of Section 5 for the current and the averaged iterate,
-// k_decide applies the Section 6 restart rule and tabulates the next step
-// sizes, and k_restart_apply moves the iterate to the restart candidate.
+// Device kernels of the rAPDHG solver (sm_103a) other than the iteration
+// kernels (iteration.cu): scaling, spectral norms, the relative KKT error of
+// Section 5 in float64 for the current and the averaged iterate (k_kkt_m /
+// k_kkt_n, every `check_period` iterations), the Section 6 restart rule and
+// step table (k_decide), restarts (k_restart_apply), mixed-precision rebasing,
+// the low-rank term and the allocation-free KKT entry point.
 //
 // All SpMV-shaped kernels work on row blocks (see BCsr): the block's nonzeros
 // are contiguous, so its 256 threads issue their index and value loads
@@ -21,28 +15,11 @@
 
 #include <algorithm>
 
-#include "solver.h"
+#include "rowblock.cuh"
 
 namespace pdqp {
 
 long long g_launches = 0;
-
-// Launch a kernel and count it.
-template <typename... KArgs, typename... Args>
-static inline void launch(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
-                          Args... args) {
-  if (grid <= 0) return;
-  kern<<<grid, block, smem, s>>>(args...);
-  ++g_launches;
-}
-template <typename... KArgs, typename... Args>
-static inline void launch(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args... args) {
-  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
-  kern<<<grid, block, smem, s>>>(args...);
-  ++g_launches;
-}
-
-static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 static int pick_lanes(long long nnz, long long rows) {
   const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
@@ -59,22 +36,6 @@ static int pick_lanes(long long nnz, long long rows) {
     case 16: { constexpr int LL = 16; __VA_ARGS__; } break; \
     default: { constexpr int LL = 32; __VA_ARGS__; } break; \
   }
-
-// Deterministic sum over the block (valid in every thread).
-template <typename T>
-__device__ __forceinline__ T block_sum(T v) {
-  __shared__ T sh[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  T t = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  return t;
-}
 
 // --------------------------------------------------------------------------
 // Per-row relative KKT kernels on separate Q, A, A' CSR arrays (used by
@@ -257,49 +218,6 @@ __device__ void reduce_kkt_partials(const double* __restrict__ part, int nblk, d
 }
 
 // ==========================================================================
-// Row-block staging: the products val[e] * vec[col[e]] of one block's
-// nonzeros go to shared memory prod[0..ne); srp[t] = rp[r0+t] - e0.
-// ==========================================================================
-template <int NT, typename V, typename X>
-__device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
-                                               int r0, int nr, V* prod, int* srp) {
-  // float data: two phases of EPT/2 loads and gathers each, half the
-  // registers of one phase of EPT, so that 8 blocks fit on an SM; float64
-  // data (4 blocks per SM either way) keeps all EPT gathers in flight at once
-  constexpr int EPT = BNNZ / NT;
-  constexpr int PH = sizeof(V) == 4 ? 2 : 1;
-  constexpr int H = EPT / PH;
-  const int tid = threadIdx.x;
-  for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
-#pragma unroll
-  for (int h = 0; h < PH; ++h) {
-    int ci[H];
-    V vv[H];
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const int e = tid + (h * H + k) * NT;
-      if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
-    }
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const int e = tid + (h * H + k) * NT;
-      if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
-    }
-  }
-}
-
-// Occupancy target of the row-block kernels (blocks per SM).  They wait on
-// dependent gathers, so more resident warps hide more latency: with the
-// two-phase staging above, 256 threads of float data fit 32 registers without
-// spills (8 blocks, the whole SM: k_primal 97 -> 76 us, k_dual 67 -> 51 us at
-// n=1e6 against 4 blocks at 64 registers); the float64 kernels are bound by
-// the float64 pipes and gain nothing from 5 or 6 blocks, so they keep 64
-// registers (4); NT = 512 runs 4 blocks at 32 registers.
-template <typename V, int NT, bool LR = false> struct MinBlocks { static constexpr int value = 4; };
-template <> struct MinBlocks<float, 256, false> { static constexpr int value = 8; };
-
-
-// ==========================================================================
 // Low-rank term of Q: Q_total = Q + F F' with F (n x r, row-major) applied as
 // F (F' v) and never formed.  w = F~' v is a two-stage reduction (row tiles
 // then one reduce); the row term F~_j . w is added where Q v appears.
@@ -381,378 +299,6 @@ __global__ void __launch_bounds__(256) k_lr_reduce(const double* __restrict__ pa
   if (threadIdx.x == 0) {
     w[q * r + kk] = sh[0];
     if (wf) wf[q * r + kk] = (float)sh[0];
-  }
-}
-
-// the row term F~_j . w (16-byte loads of the row when r allows)
-template <typename FV, typename V, typename W>
-__device__ __forceinline__ V lr_row(const FV* __restrict__ F, const W* __restrict__ w, int r, int j) {
-  V s = V(0);
-  const FV* f = F + (size_t)j * r;
-  constexpr int VW = 16 / sizeof(FV);
-  if (r % VW == 0) {
-    for (int kk = 0; kk < r; kk += VW) {
-      if constexpr (VW == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(f + kk);
-        s += (V)q.x * (V)w[kk] + (V)q.y * (V)w[kk + 1] + (V)q.z * (V)w[kk + 2] + (V)q.w * (V)w[kk + 3];
-      } else {
-        const double2 q = *reinterpret_cast<const double2*>(f + kk);
-        s += (V)q.x * (V)w[kk] + (V)q.y * (V)w[kk + 1];
-      }
-    }
-  } else {
-    for (int kk = 0; kk < r; ++kk) s += (V)f[kk] * (V)w[kk];
-  }
-  return s;
-}
-
-// --------------------------------------------------------------------------
-// One inner iteration of Algorithm 1: the dual half-step (rows of A)
-// --------------------------------------------------------------------------
-template <typename V>
-struct DualB {
-  BCsr<V> A;
-  const V* __restrict__ xt;      // extrapolated primal point x_tilde
-  const V* __restrict__ yold;    // y^k
-  V* __restrict__ ynew;          // y^{k+1}
-  V* __restrict__ ybar;
-  const V* __restrict__ b;
-  const V* __restrict__ ylo;     // lower bound of inequality duals (mixed-mode shift) or null (0)
-  const StepEntry* __restrict__ tab;    // [instance][C]
-  const int* __restrict__ blk_inst;     // instance of each row block
-  const DevState* __restrict__ st;      // per instance
-  const unsigned char* __restrict__ ineq;   // per row: inequality
-  int C;
-  const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
-  const V* __restrict__ lpart;          // segment sums of the long rows
-  const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
-};
-
-template <typename V> __device__ __forceinline__ V step_sigma(const StepEntry& e);
-template <> __device__ __forceinline__ double step_sigma<double>(const StepEntry& e) { return e.sigma_d; }
-template <> __device__ __forceinline__ float step_sigma<float>(const StepEntry& e) { return e.sigma_d_f; }
-template <typename V> __device__ __forceinline__ V step_tau(const StepEntry& e);
-template <> __device__ __forceinline__ double step_tau<double>(const StepEntry& e) { return e.tau_p; }
-template <> __device__ __forceinline__ float step_tau<float>(const StepEntry& e) { return e.tau_p_f; }
-template <typename V> __device__ __forceinline__ V step_ib(const StepEntry& e);
-template <> __device__ __forceinline__ double step_ib<double>(const StepEntry& e) { return e.inv_beta; }
-template <> __device__ __forceinline__ float step_ib<float>(const StepEntry& e) { return e.inv_beta_f; }
-template <typename V> __device__ __forceinline__ V step_ibn(const StepEntry& e);
-template <> __device__ __forceinline__ double step_ibn<double>(const StepEntry& e) { return e.inv_beta_next; }
-template <> __device__ __forceinline__ float step_ibn<float>(const StepEntry& e) { return e.inv_beta_next_f; }
-template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
-template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
-template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
-
-template <typename V>
-__device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, int r, V s, V yo, V bi, V yb,
-                                         V lo) {
-  const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
-  V yn = yo - sigma * (s - bi);
-  if (a.ineq[r]) yn = fmax(yn, lo);
-  a.ybar[r] = (V(1) - ib) * yb + ib * yn;
-  a.ynew[r] = yn;
-}
-
-template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a, int j) {
-  __shared__ V prod[BNNZ];
-  __shared__ int srp[BROWS + 1];
-  const int tid = threadIdx.x;
-  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;   // compacted batches: running blocks only
-  const int inst = a.blk_inst[bk];
-  if (a.st[inst].status != ST_RUNNING) return;
-  const int r0 = a.A.blk[bk], r1 = a.A.blk[bk + 1];
-  const int nr = r1 - r0;
-  const int e0 = a.A.rp[r0];
-  const int ne = a.A.rp[r1] - e0;
-  // operands of this thread's first row, fetched before the SpMV
-  V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
-  if (tid < nr) {
-    const int r = r0 + tid;
-    yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-    if (a.ylo) lo = a.ylo[r];
-  }
-  const StepEntry& es = a.tab[inst * a.C + j];
-  if (ne <= BNNZ) {
-    stage_products<NT>(a.A, a.xt, e0, ne, r0, nr, prod, srp);
-    __syncthreads();
-    for (int t = tid; t < nr; t += NT) {
-      V s = V(0);
-      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
-      const int r = r0 + t;
-      if (t >= BNT) {
-        yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-        lo = a.ylo ? a.ylo[r] : V(0);
-      }
-      dual_row(a, es, r, s, yo, bi, yb, lo);
-    }
-  } else if (a.blk_seg) {   // a long row: the sum of its segments (k_long_partials), in order
-    if (tid == 0) {
-      const int2 sg = a.blk_seg[bk];
-      V s = V(0);
-      for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
-      dual_row(a, es, r0, s, yo, bi, yb, lo);
-    }
-  } else {   // a single row longer than a block
-    V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
-    s = block_sum(s);
-    if (tid == 0) dual_row(a, es, r0, s, yo, bi, yb, lo);
-  }
-}
-
-// --------------------------------------------------------------------------
-// One inner iteration of Algorithm 1: the primal half-step (rows of P)
-// --------------------------------------------------------------------------
-template <typename V>
-struct PrimalB {
-  BCsr<V> P;
-  const V* __restrict__ zin;     // [x_md ; y^{k+1}] of this iteration
-  V* __restrict__ zout;          // x_md of the next iteration -> zout[0:n]
-  V* __restrict__ x;
-  V* __restrict__ xbar;
-  V* __restrict__ xt;            // x_tilde of the next iteration
-  const V* __restrict__ c;
-  const V* __restrict__ l;
-  const V* __restrict__ u;
-  const StepEntry* __restrict__ tab;    // [instance][C]
-  const int* __restrict__ blk_inst;
-  const DevState* __restrict__ st;
-  int C;
-  const V* __restrict__ F;              // low-rank factor F~ (null: none)
-  const V* __restrict__ wlr;            // F~' x_md of this iteration
-  int r;
-  const int2* __restrict__ blk_seg;     // long rows: {first segment, segments} per block (null: none)
-  const V* __restrict__ lpart;          // segment sums of the long rows
-  const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
-};
-
-template <typename V, bool LR = false>
-__device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry& e, int r, V s, V xo, V xb0,
-                                           V cr, V lr, V ur) {
-  const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
-  const V g = s + cr + (LR ? lr_row<V, V, V>(a.F, a.wlr, a.r, r) : V(0));
-  const V xn = fmin(fmax(xo - tau * g, lr), ur);
-  const V xb = (V(1) - ib) * xb0 + ib * xn;
-  a.xbar[r] = xb;
-  a.zout[r] = (V(1) - ibn) * xb + ibn * xn;
-  a.xt[r] = xn + thn * (xn - xo);
-  a.x[r] = xn;
-}
-
-// LR: the problem has a low-rank term (its row term gets its own instantiation
-// so that the plain kernel keeps its 32 registers)
-template <typename V, int NT, bool LR = false>
-__global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(PrimalB<V> a, int j) {
-  __shared__ V prod[BNNZ];
-  __shared__ int srp[BROWS + 1];
-  const int tid = threadIdx.x;
-  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
-  const int inst = a.blk_inst[bk];
-  if (a.st[inst].status != ST_RUNNING) return;
-  const int r0 = a.P.blk[bk], r1 = a.P.blk[bk + 1];
-  const int nr = r1 - r0;
-  const int e0 = a.P.rp[r0];
-  const int ne = a.P.rp[r1] - e0;
-  V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
-  if (tid < nr) {
-    const int r = r0 + tid;
-    xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
-  }
-  const StepEntry& es = a.tab[inst * a.C + j];
-  if (ne <= BNNZ) {
-    stage_products<NT>(a.P, a.zin, e0, ne, r0, nr, prod, srp);
-    __syncthreads();
-    for (int t = tid; t < nr; t += NT) {
-      V s = V(0);
-      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[e];
-      const int r = r0 + t;
-      if (t >= BNT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
-      primal_row<V, LR>(a, es, r, s, xo, xb, cr, lr, ur);
-    }
-  } else if (a.blk_seg) {
-    if (tid == 0) {
-      const int2 sg = a.blk_seg[bk];
-      V s = V(0);
-      for (int q = 0; q < sg.y; ++q) s += a.lpart[sg.x + q];
-      primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
-    }
-  } else {
-    V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
-    s = block_sum(s);
-    if (tid == 0) primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
-  }
-}
-
-// Segment sums of the long rows: one CUDA block per segment of LSEG nonzeros
-// of M v (skipping instances that stopped); the iteration kernels add a row's
-// segments in order.
-template <typename V>
-__global__ void __launch_bounds__(256) k_long_partials(BCsr<V> M, const V* __restrict__ vec,
-                                                       const int4* __restrict__ lseg, const int* __restrict__ blk_inst,
-                                                       const DevState* __restrict__ st, V* __restrict__ out) {
-  const int4 g = lseg[blockIdx.x];
-  if (st[blk_inst[g.w]].status != ST_RUNNING) return;
-  V s = V(0);
-  for (int e = g.y + threadIdx.x; e < g.z; e += 256) s += M.val[e] * __ldg(vec + M.col[e]);
-  s = block_sum(s);
-  if (threadIdx.x == 0) out[blockIdx.x] = s;
-}
-
-
-// ==========================================================================
-// Pipelined persistent variants of the two half-steps.  Each CUDA block loops
-// over row blocks b = blockIdx.x, blockIdx.x + gridDim.x, ...; while it
-// gathers and finishes block b, the index, value and row-pointer ranges of its
-// next block stream into the other shared-memory stage with cp.async (16-byte
-// copies of the 16-byte aligned superset of each range).  Block bounds come
-// from one int4 {r0, r1, e0, e1} per block.  Global index/value/rowptr arrays
-// carry 8 elements of padding so the aligned superset never leaves them.
-// ==========================================================================
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-template <typename V>
-struct PipeSmem {
-  int col[2][BNNZ + 8];
-  V val[2][BNNZ + 8];
-  int rp[2][BROWS + 8];
-  V prod[BNNZ];
-};
-
-// Queue the copies of block m = {r0, r1, e0, e1} into stage s (no copy for a long row).
-template <int NT, typename V>
-__device__ __forceinline__ void pipe_issue(PipeSmem<V>& sm, int s, const int4 m, const int* __restrict__ col,
-                                           const V* __restrict__ val, const int* __restrict__ rp) {
-  const int tid = threadIdx.x;
-  if (m.w - m.z <= BNNZ) {
-    const int a0 = m.z & ~3, a1 = (m.w + 3) & ~3;
-    for (int c = tid; c < (a1 - a0) >> 2; c += NT) cp_async16(&sm.col[s][c << 2], col + a0 + (c << 2));
-    constexpr int PER = 16 / sizeof(V);
-    for (int c = tid; c < (a1 - a0) / PER; c += NT) cp_async16(&sm.val[s][c * PER], val + a0 + c * PER);
-    const int q0 = m.x & ~3, q1 = (m.y + 1 + 3) & ~3;
-    for (int c = tid; c < (q1 - q0) >> 2; c += NT) cp_async16(&sm.rp[s][c << 2], rp + q0 + (c << 2));
-  }
-  cp_async_commit();
-}
-
-template <typename V, int NT>
-__global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __restrict__ meta, int nblk, int j) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
-  const int tid = threadIdx.x;
-  int b = blockIdx.x;
-  if (b >= nblk) return;
-  int4 mc = meta[b];
-  pipe_issue<NT>(sm, 0, mc, a.A.col, a.A.val, a.A.rp);
-  for (int s = 0; b < nblk; b += gridDim.x, s ^= 1) {
-    const int bn = b + gridDim.x;
-    int4 mn = make_int4(0, 0, 0, 0);
-    if (bn < nblk) mn = meta[bn];
-    pipe_issue<NT>(sm, s ^ 1, mn, a.A.col, a.A.val, a.A.rp);
-    const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
-    const int inst = a.blk_inst[b];
-    const bool live = a.st[inst].status == ST_RUNNING;
-    const StepEntry& es = a.tab[inst * a.C + j];
-    V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
-    if (live && tid < nr) {
-      const int r = r0 + tid;
-      yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-      if (a.ylo) lo = a.ylo[r];
-    }
-    cp_async_wait1();
-    __syncthreads();
-    if (!live) {
-    } else if (ne <= BNNZ) {
-      const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
-#pragma unroll
-      for (int k = 0; k < BNNZ / NT; ++k) {
-        const int e = tid + k * NT;
-        if (e < ne) sm.prod[e] = sm.val[s][e + off] * __ldg(a.xt + sm.col[s][e + off]);
-      }
-      __syncthreads();
-      for (int t = tid; t < nr; t += NT) {
-        V acc = V(0);
-        const int eb = sm.rp[s][t + roff] - e0, ee = sm.rp[s][t + 1 + roff] - e0;
-        for (int e = eb; e < ee; ++e) acc += sm.prod[e];
-        const int r = r0 + t;
-        if (t >= NT) {
-          yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-          lo = a.ylo ? a.ylo[r] : V(0);
-        }
-        dual_row(a, es, r, acc, yo, bi, yb, lo);
-      }
-    } else {
-      V acc = V(0);
-      for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
-      acc = block_sum(acc);
-      if (tid == 0) dual_row(a, es, r0, acc, yo, bi, yb, lo);
-    }
-    __syncthreads();
-    mc = mn;
-  }
-}
-
-template <typename V, int NT>
-__global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __restrict__ meta, int nblk, int j) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  PipeSmem<V>& sm = *reinterpret_cast<PipeSmem<V>*>(smraw);
-  const int tid = threadIdx.x;
-  int b = blockIdx.x;
-  if (b >= nblk) return;
-  int4 mc = meta[b];
-  pipe_issue<NT>(sm, 0, mc, a.P.col, a.P.val, a.P.rp);
-  for (int s = 0; b < nblk; b += gridDim.x, s ^= 1) {
-    const int bn = b + gridDim.x;
-    int4 mn = make_int4(0, 0, 0, 0);
-    if (bn < nblk) mn = meta[bn];
-    pipe_issue<NT>(sm, s ^ 1, mn, a.P.col, a.P.val, a.P.rp);
-    const int r0 = mc.x, nr = mc.y - mc.x, e0 = mc.z, ne = mc.w - mc.z;
-    const int inst = a.blk_inst[b];
-    const bool live = a.st[inst].status == ST_RUNNING;
-    const StepEntry& es = a.tab[inst * a.C + j];
-    V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
-    if (live && tid < nr) {
-      const int r = r0 + tid;
-      xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
-    }
-    cp_async_wait1();
-    __syncthreads();
-    if (!live) {
-    } else if (ne <= BNNZ) {
-      const int off = e0 - (e0 & ~3), roff = r0 - (r0 & ~3);
-#pragma unroll
-      for (int k = 0; k < BNNZ / NT; ++k) {
-        const int e = tid + k * NT;
-        if (e < ne) sm.prod[e] = sm.val[s][e + off] * __ldg(a.zin + sm.col[s][e + off]);
-      }
-      __syncthreads();
-      for (int t = tid; t < nr; t += NT) {
-        V acc = V(0);
-        const int eb = sm.rp[s][t + roff] - e0, ee = sm.rp[s][t + 1 + roff] - e0;
-        for (int e = eb; e < ee; ++e) acc += sm.prod[e];
-        const int r = r0 + t;
-        if (t >= NT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
-        if (a.F) primal_row<V, true>(a, es, r, acc, xo, xb, cr, lr, ur);
-        else primal_row<V, false>(a, es, r, acc, xo, xb, cr, lr, ur);
-      }
-    } else {
-      V acc = V(0);
-      for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
-      acc = block_sum(acc);
-      if (tid == 0) {
-        if (a.F) primal_row<V, true>(a, es, r0, acc, xo, xb, cr, lr, ur);
-        else primal_row<V, false>(a, es, r0, acc, xo, xb, cr, lr, ur);
-      }
-    }
-    __syncthreads();
-    mc = mn;
   }
 }
 
@@ -1227,7 +773,8 @@ __device__ __forceinline__ void lz_block_sums(const double* __restrict__ part, i
 }
 
 // one CUDA block per instance: alpha_k = sum of its row blocks' partials
-__global__ void __launch_bounds__(128) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;
@@ -1430,15 +977,17 @@ __device__ void bracket_max_eig_warp(const double* __restrict__ al, const double
   }
 }
 
-// one CUDA block of 128 threads per instance: beta, theta = lambda_max(T_k) and
-// the stop test for both operators (warps 0, 1: A'A; warps 2, 3: Q).  The stop
+// one CUDA block of NT >= 128 threads per instance (all of them sum the block
+// partials): beta, theta = lambda_max(T_k) and the stop test for both
+// operators (warps 0, 1: A'A; warps 2, 3: Q).  The stop
 // test |theta_k - theta_{k-1}| <= tol theta_k (or beta_k <= 1e-12 theta_k, or the
 // step limit) needs the precise Ritz values only where the brackets of
 // theta_k and theta_{k-1} cannot decide it: then the first warp of the pair
 // refines theta_k and the second theta_{k-1} from their brackets, and the
 // outcome is the one the precise values give at every step.
-__global__ void __launch_bounds__(128) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
-                                                int max_steps) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
+                                               int max_steps) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
@@ -1466,9 +1015,10 @@ __global__ void __launch_bounds__(128) k_lz_beta(LzArgs a, const double* __restr
       }
     }
   __syncthreads();
-  const int o = threadIdx.x >> 6, second = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+  const bool ritz = threadIdx.x < 128;            // warps 0..3 work on the Ritz values
+  const int o = (threadIdx.x >> 6) & 1, second = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
   const double plo = st.pi_lam_prev[o], phi = st.pi_hi_prev[o];   // bracket of theta_{k-1}
-  if (!done_in[o] && !second) {                   // warp-uniform
+  if (ritz && !done_in[o] && !second) {           // warp-uniform
     double lo, hi;
     bracket_max_eig_warp(s_al[o], s_be[o], s_be2[o], s_alf[o], s_be2f[o], k, lo, hi);
     const double mag = fmax(fabs(lo), fabs(hi));
@@ -1481,7 +1031,7 @@ __global__ void __launch_bounds__(128) k_lz_beta(LzArgs a, const double* __restr
     }
   }
   __syncthreads();
-  if (!done_in[o] && s_precise[o]) {
+  if (ritz && !done_in[o] && s_precise[o]) {
     if (!second)
       s_theta[o][0] = refine_max_eig_warp(s_al[o], s_be2[o], k, s_lo[o], s_hi[o]);
     else if (plo != phi)
@@ -1490,7 +1040,7 @@ __global__ void __launch_bounds__(128) k_lz_beta(LzArgs a, const double* __restr
       s_theta[o][1] = plo;
   }
   __syncthreads();
-  if (!done_in[o] && !second && lane == 0) {
+  if (ritz && !done_in[o] && !second && lane == 0) {
     const double b = beta[o];
     if (!s_precise[o]) {                          // continues: keep the bracket
       st.pi_lam[o] = 0.5 * (s_lo[o] + s_hi[o]);
@@ -1991,6 +1541,13 @@ static void lowrank_ft(Work& w, const FV* F, const X* v0, const X* v1, cudaStrea
          w.wlr_f);
 }
 
+void lowrank_ft1(Work& w, const float* F, const float* v, cudaStream_t s) {
+  lowrank_ft<float, float>(w, F, v, (const float*)nullptr, s);
+}
+void lowrank_ft1(Work& w, const double* F, const double* v, cudaStream_t s) {
+  lowrank_ft<double, double>(w, F, v, (const double*)nullptr, s);
+}
+
 static LzArgs lz_args(Work& w) {
   LzArgs la{};
   la.n = w.n; la.m = w.m; la.count = w.count;
@@ -2000,13 +1557,6 @@ static LzArgs lz_args(Work& w) {
   return la;
 }
 
-template <typename V> static const V* lr_factor(Work& w);
-template <> const double* lr_factor<double>(Work& w) { return w.Fd; }
-template <> const float* lr_factor<float>(Work& w) { return w.Fs; }
-template <typename V> static const V* lr_weights(Work& w);
-template <> const double* lr_weights<double>(Work& w) { return w.wlr; }
-template <> const float* lr_weights<float>(Work& w) { return w.wlr_f; }
-
 template <typename V>
 static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) {
   const int grid = std::min(cdiv(std::max(w.n, w.count), 256), 4 * w.num_sms);
@@ -2014,6 +1564,8 @@ static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) 
 }
 
 void lanczos_init(Work& w, bool mixed, cudaStream_t s) {
+  w.max_inst_blkP = 0;
+  for (const Inst& in : w.inst_host) w.max_inst_blkP = std::max(w.max_inst_blkP, in.bP1 - in.bP0);
   if (mixed) lanczos_init_t<float>(w, w.fpu, w.fpz, s);
   else lanczos_init_t<double>(w, w.pu, w.pz, s);
 }
@@ -2035,10 +1587,16 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   else
     launch(k_lz_n<V, NT, false>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
            w.part_n, F, lr_weights<V>(w), w.r);
-  launch(k_lz_alpha, w.count, 128, 0, s, la, (const double*)w.part_n);
+  // a single large instance sums thousands of block partials: more threads
+  // keep more of its loads in flight; batches of small instances keep 128
+  const bool wide = w.max_inst_blkP > 2048;
+  if (wide) launch(k_lz_alpha<512>, w.count, 512, 0, s, la, (const double*)w.part_n);
+  else launch(k_lz_alpha<128>, w.count, 128, 0, s, la, (const double*)w.part_n);
   launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
          (const V*)pz[cur], pz[prv], w.part_n);
-  launch(k_lz_beta, w.count, 128, 0, s, la, (const double*)w.part_n, p.norm_tol,
+  if (wide) launch(k_lz_beta<512>, w.count, 512, 0, s, la, (const double*)w.part_n, p.norm_tol,
+         p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
+  else launch(k_lz_beta<128>, w.count, 128, 0, s, la, (const double*)w.part_n, p.norm_tol,
          p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
   const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
   launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
@@ -2093,142 +1651,6 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
          (const double*)w.D1,
          (const double*)w.D2, (const double*)w.ls, (const double*)w.us, w.x, w.xbar, w.Z[0], w.xt, w.ax, w.y,
          w.ybar, w.ay);
-}
-
-template <typename V, int NT>
-static int pipe_grid(void (*kern)(DualB<V>, const int4*, int, int)) {
-  static int blocks = -1;
-  if (blocks < 0) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
-    blocks = per_sm > 0 ? per_sm : 1;
-  }
-  return blocks;
-}
-template <typename V, int NT>
-static int pipe_grid_p(void (*kern)(PrimalB<V>, const int4*, int, int)) {
-  static int blocks = -1;
-  if (blocks < 0) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
-    blocks = per_sm > 0 ? per_sm : 1;
-  }
-  return blocks;
-}
-
-// Algorithmic bytes of one dual (kind 0) or primal (kind 1) launch over the
-// instances running at the last check: the matrix streams (index + value),
-// the row pointers, each vector read or written once (the gathered vector
-// counted once); sv = bytes per value.
-static double launch_bytes(const Work& w, int kind, double sv) {
-  const BatchState& b = *w.bst_host;
-  if (kind == 0) return b.run_nnzA * (sv + 4.0) + 4.0 * (b.run_m + 1.0) + sv * (b.run_n + 5.0 * b.run_m);
-  return b.run_nnzP * (sv + 4.0) + 4.0 * (b.run_n + 1.0) + sv * (10.0 * b.run_n + b.run_m);
-}
-
-template <typename V, int NT>
-static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
-                           const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s) {
-  Profiler& Pr = w.prof;
-  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
-  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
-                w.r > 0 ? lr_factor<V>(w) : nullptr, lr_weights<V>(w), w.r};
-  const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
-  const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
-  const size_t smem = sizeof(PipeSmem<V>);
-  for (int j = j0; j < j0 + len; ++j) {
-    if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
-    if (w.m > 0) {
-      da.yold = Z[(j + 1) & 1] + w.n;
-      da.ynew = Z[j & 1] + w.n;
-      if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
-      launch(k_dual_pipe<V, NT>, gd, NT, smem, s, da, (const int4*)w.A.meta, w.A.nblk, j);
-      if (Pr.on) Pr.end(s);
-    }
-    pa.zin = Z[j & 1];
-    pa.zout = Z[(j + 1) & 1];
-    if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
-    launch(k_primal_pipe<V, NT>, gp, NT, smem, s, pa, (const int4*)w.P.meta, w.P.nblk, j);
-    if (Pr.on) Pr.end(s);
-  }
-}
-
-template <typename V, int NT>
-static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar, const V* b,
-                      const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u, cudaStream_t s,
-                      bool compact) {
-  Profiler& Pr = w.prof;
-  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
-  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
-                w.r > 0 ? lr_factor<V>(w) : nullptr, lr_weights<V>(w), w.r};
-  // long rows: segment sums first (float or float64 buffers by V)
-  V* lpA = sizeof(V) == 4 ? (V*)w.A.lpart_f : (V*)w.A.lpart_d;
-  V* lpP = sizeof(V) == 4 ? (V*)w.P.lpart_f : (V*)w.P.lpart_d;
-  if (w.A.nlseg) { da.blk_seg = w.A.blk_seg; da.lpart = lpA; }
-  if (w.P.nlseg) { pa.blk_seg = w.P.blk_seg; pa.lpart = lpP; }
-  int gA = w.A.nblk, gP = w.P.nblk;
-  if (compact) {   // only the running instances' row blocks (counts of the last check)
-    da.act = w.act_A;
-    pa.act = w.act_P;
-    gA = w.bst_host->act_A;
-    gP = w.bst_host->act_P;
-  }
-  for (int j = j0; j < j0 + len; ++j) {
-    if (w.r > 0) lowrank_ft<V, V>(w, pa.F, (const V*)Z[j & 1], (const V*)nullptr, s);
-    if (w.m > 0) {
-      da.yold = Z[(j + 1) & 1] + w.n;
-      da.ynew = Z[j & 1] + w.n;
-      if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
-      if (w.A.nlseg)
-        launch(k_long_partials<V>, w.A.nlseg, 256, 0, s, A, (const V*)xt, (const int4*)w.A.lseg,
-               (const int*)w.blk_inst_A, (const DevState*)w.st, lpA);
-      launch(k_dual<V, NT>, gA, NT, 0, s, da, j);
-      if (Pr.on) Pr.end(s);
-    }
-    pa.zin = Z[j & 1];
-    pa.zout = Z[(j + 1) & 1];
-    if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
-    if (w.P.nlseg)
-      launch(k_long_partials<V>, w.P.nlseg, 256, 0, s, P, (const V*)pa.zin, (const int4*)w.P.lseg,
-             (const int*)w.blk_inst_P, (const DevState*)w.st, lpP);
-    if (w.r > 0) launch(k_primal<V, NT, true>, gP, NT, 0, s, pa, j);
-    else launch(k_primal<V, NT, false>, gP, NT, 0, s, pa, j);
-    if (Pr.on) Pr.end(s);
-  }
-}
-
-void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0, bool compact) {
-  if (nt == 1) {   // pipelined persistent kernels, 256 threads
-    if (mixed) {
-      run_chunk_pipe<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
-                                 w.fxbar, w.fc, w.fl, w.fu, s);
-      w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
-    } else {
-      run_chunk_pipe<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x,
-                                  w.xbar, w.cs, w.ls, w.us, s);
-      w.y = w.Z[(j0 + len - 1) & 1] + w.n;
-    }
-    return;
-  }
-  if (mixed) {
-    if (nt != 512)
-      run_chunk<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
-                            w.fxbar, w.fc, w.fl, w.fu, s, compact);
-    else
-      run_chunk<float, 512>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,
-                            w.fxbar, w.fc, w.fl, w.fu, s, compact);
-    w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
-  } else {
-    if (nt != 512)
-      run_chunk<double, 256>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
-                             w.cs, w.ls, w.us, s, compact);
-    else
-      run_chunk<double, 512>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar,
-                             w.cs, w.ls, w.us, s, compact);
-    w.y = w.Z[(j0 + len - 1) & 1] + w.n;
-  }
 }
 
 static KktB kkt_args(Work& w, bool scaled) {

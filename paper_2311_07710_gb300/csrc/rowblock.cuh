@@ -1,0 +1,120 @@
+// Row-block helpers shared by the iteration kernels (iteration.cu) and the
+// other kernels (kernels.cu): counted launches, block sums, the staging of a
+// row block's products in shared memory, the occupancy targets and the
+// low-rank row term.
+#pragma once
+
+#include "solver.h"
+
+namespace pdqp {
+
+// Launch a kernel and count it.
+template <typename... KArgs, typename... Args>
+static inline void launch(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                          Args... args) {
+  if (grid <= 0) return;
+  kern<<<grid, block, smem, s>>>(args...);
+  ++g_launches;
+}
+template <typename... KArgs, typename... Args>
+static inline void launch(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args... args) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+  kern<<<grid, block, smem, s>>>(args...);
+  ++g_launches;
+}
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Deterministic sum over the block (valid in every thread).
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+  __shared__ T sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  T t = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// ==========================================================================
+// Row-block staging: the products val[e] * vec[col[e]] of one block's
+// nonzeros go to shared memory prod[0..ne); srp[t] = rp[r0+t] - e0.
+// ==========================================================================
+template <int NT, typename V, typename X>
+__device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
+                                               int r0, int nr, V* prod, int* srp) {
+  // float data: two phases of EPT/2 loads and gathers each, half the
+  // registers of one phase of EPT, so that 8 blocks fit on an SM; float64
+  // data (4 blocks per SM either way) keeps all EPT gathers in flight at once
+  constexpr int EPT = BNNZ / NT;
+  constexpr int PH = sizeof(V) == 4 ? 2 : 1;
+  constexpr int H = EPT / PH;
+  const int tid = threadIdx.x;
+  for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
+#pragma unroll
+  for (int h = 0; h < PH; ++h) {
+    int ci[H];
+    V vv[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int e = tid + (h * H + k) * NT;
+      if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int e = tid + (h * H + k) * NT;
+      if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
+    }
+  }
+}
+
+// Occupancy target of the row-block kernels (blocks per SM).  They wait on
+// dependent gathers, so more resident warps hide more latency: with the
+// two-phase staging above, 256 threads of float data fit 32 registers without
+// spills (8 blocks, the whole SM: k_primal 97 -> 76 us, k_dual 67 -> 51 us at
+// n=1e6 against 4 blocks at 64 registers); the float64 kernels are bound by
+// the float64 pipes and gain nothing from 5 or 6 blocks, so they keep 64
+// registers (4); NT = 512 runs 4 blocks at 32 registers.
+template <typename V, int NT, bool LR = false> struct MinBlocks { static constexpr int value = 4; };
+template <> struct MinBlocks<float, 256, false> { static constexpr int value = 8; };
+
+
+// the row term F~_j . w (16-byte loads of the row when r allows)
+template <typename FV, typename V, typename W>
+__device__ __forceinline__ V lr_row(const FV* __restrict__ F, const W* __restrict__ w, int r, int j) {
+  V s = V(0);
+  const FV* f = F + (size_t)j * r;
+  constexpr int VW = 16 / sizeof(FV);
+  if (r % VW == 0) {
+    for (int kk = 0; kk < r; kk += VW) {
+      if constexpr (VW == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(f + kk);
+        s += (V)q.x * (V)w[kk] + (V)q.y * (V)w[kk + 1] + (V)q.z * (V)w[kk + 2] + (V)q.w * (V)w[kk + 3];
+      } else {
+        const double2 q = *reinterpret_cast<const double2*>(f + kk);
+        s += (V)q.x * (V)w[kk] + (V)q.y * (V)w[kk + 1];
+      }
+    }
+  } else {
+    for (int kk = 0; kk < r; ++kk) s += (V)f[kk] * (V)w[kk];
+  }
+  return s;
+}
+
+template <typename V> static const V* lr_factor(Work& w);
+template <> inline const double* lr_factor<double>(Work& w) { return w.Fd; }
+template <> inline const float* lr_factor<float>(Work& w) { return w.Fs; }
+template <typename V> static const V* lr_weights(Work& w);
+template <> inline const double* lr_weights<double>(Work& w) { return w.wlr; }
+template <> inline const float* lr_weights<float>(Work& w) { return w.wlr_f; }
+
+// F~' v into w.wlr / w.wlr_f for one vector (kernels.cu)
+void lowrank_ft1(Work& w, const float* F, const float* v, cudaStream_t s);
+void lowrank_ft1(Work& w, const double* F, const double* v, cudaStream_t s);
+
+}  // namespace pdqp

@@ -127,6 +127,7 @@ struct Work {
   double *cpart_m = nullptr; // [9][nchunk_m]  chunk sums of part_m (KKT_CHUNK blocks each)
   double *cpart_n = nullptr; // [15][nchunk_n]
   int nchunk_m = 0, nchunk_n = 0, maxchunk_m = 0, maxchunk_n = 0;
+  int max_inst_blkP = 0;     // most row blocks of P held by one instance
   int* act_A = nullptr;      // batches: [A.nblk] row blocks of the running instances (count in bst)
   int* act_P = nullptr;      // [P.nblk]
   StepEntry* tab = nullptr;  // [count][tab_stride]
