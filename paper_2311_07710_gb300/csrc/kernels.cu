@@ -332,17 +332,104 @@ struct KktB {
   int r;
 };
 
-// Both kernels split the row phase into (iterate, row) work items so that a
-// block of 256 threads stays busy when it holds fewer than 256 rows, and reduce
-// their fields through the staging buffer once the rows are done.
+// Sign and class tests on the bits (integer instructions: GB300's float64
+// pipe is the bound of these kernels): v > 0, v < 0, v finite.
+__device__ __forceinline__ bool gt0_bits(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool lt0_bits(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7FF) != 0x7FF;
+}
+
+// Dynamic shared memory of the row-block relKKT kernels: the block's values,
+// the gathered vector entries of each iterate, the row pointers (and the
+// Q / A' split); the value and entry area is reused for the field reduction.
+template <int NIT>
+constexpr size_t kkt_smem_bytes() {
+  return (size_t)(NIT + 1) * BNNZ * sizeof(double) + (size_t)(2 * BROWS + 1) * sizeof(int);
+}
+
+// Stage one row block: sval[e] = val[e0+e], sx[it][e] = the iterate's entry at
+// col[e0+e] (gather(it, c)); srp[t] = rp[r0+t] - e0.
+template <int NIT, typename G>
+__device__ __forceinline__ void kkt_stage(const BCsr<double>& M, int e0, int ne, int r0, int nr, double* sval,
+                                          double* sx, int* srp, G gather) {
+  const int tid = threadIdx.x;
+  int ci[BEPT];
+#pragma unroll
+  for (int k = 0; k < BEPT; ++k) {
+    const int e = tid + k * BNT;
+    if (e < ne) { ci[k] = M.col[e0 + e]; sval[e] = M.val[e0 + e]; }
+  }
+  for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+#pragma unroll
+  for (int k = 0; k < BEPT; ++k) {
+    const int e = tid + k * BNT;
+    if (e < ne)
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) sx[it * BNNZ + e] = gather(it, ci[k]);
+  }
+}
+
+// m side of one row and iterate IT: fields IT*4 + {0 max|viol|, 1 max|Ax|,
+// 2 b'y, 3 |dy|^2}, 8: max|b|
+template <int IT>
+__device__ __forceinline__ void kkt_m_row(const KktB& a, double (&f)[9], int r, double s) {
+  const double bi = a.b[r];
+  if (a.prodAx[IT]) a.prodAx[IT][r] = s;
+  const double Ax = s * (a.iD1 ? a.iD1[r] : 1.0);
+  const double v = Ax - bi;                       // bi - Ax = -v exactly
+  const double viol = a.ineq[r] ? (lt0_bits(v) ? -v : 0.0) : fabs(v);
+  f[IT * 4 + 0] = nmax(f[IT * 4 + 0], viol);
+  f[IT * 4 + 1] = nmax(f[IT * 4 + 1], fabs(Ax));
+  const double yt = a.y[IT][r];
+  f[IT * 4 + 2] = fma(bi, (a.D1 ? a.D1[r] : 1.0) * yt, f[IT * 4 + 2]);
+  const double dy = a.ay ? yt - a.ay[r] : 0.0;
+  f[IT * 4 + 3] = fma(dy, dy, f[IT * 4 + 3]);
+  if (IT == 0) f[8] = nmax(f[8], fabs(bi));
+}
+
+// n side of one row and iterate IT: fields IT*7 + {0 max|res|, 1 max|Qx|,
+// 2 max|A'y|, 3 x'Qx, 4 c'x, 5 sum(l lam+ - u lam-), 6 |dx|^2}, 14: max|c|
+template <int IT, bool LR>
+__device__ __forceinline__ void kkt_n_row(const KktB& a, double (&f)[15], int r, double sq, double sa) {
+  const double cj = a.c[r], lj = a.l[r], uj = a.u[r];
+  const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
+  double sqt = sq;
+  if constexpr (LR) sqt += lr_row<double, double, double>(a.F, a.wlr + IT * a.r, a.r, r);
+  if (a.prodQx[IT]) { a.prodQx[IT][r] = sqt; a.prodATy[IT][r] = -sa; }
+  const double Qx = sqt * id2, ATy = -sa * id2;
+  const double xt = a.x[IT][r];
+  const double xj = d2 * xt;
+  const double g = Qx + cj - ATy;
+  // lam = proj of g onto Lambda_j: R (both bounds finite), R+ (only l), R- (only u), {0}
+  const bool lf = finite_bits(lj), uf = finite_bits(uj);
+  const double lam = (lf && uf) ? g : (lf ? (gt0_bits(g) ? g : 0.0) : (uf ? (lt0_bits(g) ? g : 0.0) : 0.0));
+  f[IT * 7 + 0] = nmax(f[IT * 7 + 0], fabs(g - lam));
+  f[IT * 7 + 1] = nmax(f[IT * 7 + 1], fabs(Qx));
+  f[IT * 7 + 2] = nmax(f[IT * 7 + 2], fabs(ATy));
+  f[IT * 7 + 3] = fma(xj, Qx, f[IT * 7 + 3]);
+  f[IT * 7 + 4] = fma(cj, xj, f[IT * 7 + 4]);
+  // l lam+ - u lam-: lam > 0 only with l finite, lam < 0 only with u finite
+  const double bound = gt0_bits(lam) ? lj : (lt0_bits(lam) ? uj : 0.0);
+  f[IT * 7 + 5] = fma(bound, lam, f[IT * 7 + 5]);
+  const double dx = a.ax ? xt - a.ax[r] : 0.0;
+  f[IT * 7 + 6] = fma(dx, dx, f[IT * 7 + 6]);
+  if (IT == 0) f[14] = nmax(f[14], fabs(cj));
+}
+
+// The row phase splits into (iterate, row) work items, so that a block of 256
+// threads stays busy when it holds fewer than 256 rows; a branch on the
+// iterate keeps every field index known at compile time (the fields stay in
+// registers).  Row sums by FMA over the staged values and entries.
 template <int NIT>
 __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
-  // fields: it*4 + {0 max|viol|, 1 max|Ax|, 2 b'y, 3 |dy|^2}, 8: max|b|
-  // product staging, reused for the field reduction
-  constexpr int SZ = NIT * BNNZ > 9 * BNT ? NIT * BNNZ : 9 * BNT;
-  __shared__ double stage[SZ];
-  double(*prod)[BNNZ] = reinterpret_cast<double(*)[BNNZ]>(stage);
-  __shared__ int srp[BROWS + 1];
+  extern __shared__ __align__(16) double kkt_sm[];
+  double* sval = kkt_sm;
+  double* sx = kkt_sm + BNNZ;
+  int* srp = reinterpret_cast<int*>(kkt_sm + (NIT + 1) * BNNZ);
   double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int tid = threadIdx.x;
   if (a.st && a.st[a.blk_inst_A[blockIdx.x]].status != ST_RUNNING) return;
@@ -350,41 +437,16 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
   const int nr = r1 - r0;
   const int e0 = a.A.rp[r0];
   const int ne = a.A.rp[r1] - e0;
-  auto row = [&](int r, int it, double s) {
-    const double bi = a.b[r];
-    if (a.prodAx[it]) a.prodAx[it][r] = s;
-    const double Ax = s * (a.iD1 ? a.iD1[r] : 1.0);
-    const double viol = a.ineq[r] ? fmax(bi - Ax, 0.0) : fabs(Ax - bi);
-    f[it * 4 + 0] = nmax(f[it * 4 + 0], viol);
-    f[it * 4 + 1] = nmax(f[it * 4 + 1], fabs(Ax));
-    const double yt = a.y[it][r];
-    f[it * 4 + 2] += bi * ((a.D1 ? a.D1[r] : 1.0) * yt);
-    const double dy = a.ay ? yt - a.ay[r] : 0.0;
-    f[it * 4 + 3] += dy * dy;
-    if (it == 0) f[8] = nmax(f[8], fabs(bi));
-  };
   if (ne <= BNNZ) {
-    int ci[BEPT];
-    double vv[BEPT];
-#pragma unroll
-    for (int k = 0; k < BEPT; ++k) {
-      const int e = tid + k * BNT;
-      if (e < ne) { ci[k] = a.A.col[e0 + e]; vv[k] = a.A.val[e0 + e]; }
-    }
-    for (int t = tid; t <= nr; t += BNT) srp[t] = a.A.rp[r0 + t] - e0;
-#pragma unroll
-    for (int k = 0; k < BEPT; ++k) {
-      const int e = tid + k * BNT;
-      if (e < ne)
-#pragma unroll
-        for (int it = 0; it < NIT; ++it) prod[it][e] = vv[k] * __ldg(a.x[it] + ci[k]);
-    }
+    kkt_stage<NIT>(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) { return __ldg(a.x[it] + c); });
     __syncthreads();
     for (int q = tid; q < nr * NIT; q += BNT) {
-      const int it = q / nr, t = q - it * nr;
+      const int it = q >= nr ? 1 : 0, t = q - it * nr;
+      const double* xv = sx + it * BNNZ;
       double s = 0.0;
-      for (int e = srp[t]; e < srp[t + 1]; ++e) s += prod[it][e];
-      row(r0 + t, it, s);
+      for (int e = srp[t]; e < srp[t + 1]; ++e) s = fma(sval[e], xv[e], s);
+      if (it == 0) kkt_m_row<0>(a, f, r0 + t, s);
+      else kkt_m_row<NIT - 1>(a, f, r0 + t, s);
     }
   } else {
     double s[NIT];
@@ -394,28 +456,27 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
       const double v = a.A.val[e];
       const int c = a.A.col[e];
 #pragma unroll
-      for (int it = 0; it < NIT; ++it) s[it] += v * __ldg(a.x[it] + c);
+      for (int it = 0; it < NIT; ++it) s[it] = fma(v, __ldg(a.x[it] + c), s[it]);
     }
 #pragma unroll
     for (int it = 0; it < NIT; ++it) s[it] = block_sum(s[it]);
-    if (tid == 0)
-      for (int it = 0; it < NIT; ++it) row(r0, it, s[it]);
+    if (tid == 0) {
+      kkt_m_row<0>(a, f, r0, s[0]);
+      if (NIT > 1) kkt_m_row<NIT - 1>(a, f, r0, s[NIT - 1]);
+    }
   }
-  block_reduce_smem<9, BNT>(f, 0x133u, stage);
+  block_reduce_smem<9, BNT>(f, 0x133u, kkt_sm);
   if (tid == 0)
     for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
 }
 
-template <int NIT>
+template <int NIT, bool LR>
 __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
-  // fields (offset 9): it*7 + {0 max|res|, 1 max|Qx|, 2 max|A'y|, 3 x'Qx, 4 c'x,
-  // 5 sum(l lam+ - u lam-), 6 |dx|^2}, 14: max|c|
-  // product staging, reused for the field reduction
-  constexpr int SZ = NIT * BNNZ > 15 * BNT ? NIT * BNNZ : 15 * BNT;
-  __shared__ double stage[SZ];
-  double(*prod)[BNNZ] = reinterpret_cast<double(*)[BNNZ]>(stage);
-  __shared__ int srp[BROWS + 1];
-  __shared__ int ssp[BROWS];
+  extern __shared__ __align__(16) double kkt_sm[];
+  double* sval = kkt_sm;
+  double* sx = kkt_sm + BNNZ;
+  int* srp = reinterpret_cast<int*>(kkt_sm + (NIT + 1) * BNNZ);
+  int* ssp = srp + BROWS + 1;
   double f[15];
 #pragma unroll
   for (int k = 0; k < 15; ++k) f[k] = 0.0;
@@ -426,55 +487,20 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
   const int e0 = a.P.rp[r0];
   const int ne = a.P.rp[r1] - e0;
   const int n = a.n;
-  auto row = [&](int r, int it, double sq, double sa) {
-    const double cj = a.c[r], lj = a.l[r], uj = a.u[r];
-    const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
-    const double sqt = sq + (a.F ? lr_row<double, double, double>(a.F, a.wlr + it * a.r, a.r, r) : 0.0);
-    if (a.prodQx[it]) { a.prodQx[it][r] = sqt; a.prodATy[it][r] = -sa; }
-    const double Qx = sqt * id2, ATy = -sa * id2;
-    const double xt = a.x[it][r];
-    const double xj = d2 * xt;
-    const double g = Qx + cj - ATy;
-    const bool lf = isfinite(lj), uf = isfinite(uj);
-    const double lam = (lf && uf) ? g : (lf ? fmax(g, 0.0) : (uf ? fmin(g, 0.0) : 0.0));
-    double* fi = f + it * 7;
-    fi[0] = nmax(fi[0], fabs(g - lam));
-    fi[1] = nmax(fi[1], fabs(Qx));
-    fi[2] = nmax(fi[2], fabs(ATy));
-    fi[3] += xj * Qx;
-    fi[4] += cj * xj;
-    fi[5] += (lam > 0.0 ? lj * lam : 0.0) - (lam < 0.0 ? uj * (-lam) : 0.0);
-    const double dx = a.ax ? xt - a.ax[r] : 0.0;
-    fi[6] += dx * dx;
-    if (it == 0) f[14] = nmax(f[14], fabs(cj));
-  };
   if (ne <= BNNZ) {
-    int ci[BEPT];
-    double vv[BEPT];
-#pragma unroll
-    for (int k = 0; k < BEPT; ++k) {
-      const int e = tid + k * BNT;
-      if (e < ne) { ci[k] = a.P.col[e0 + e]; vv[k] = a.P.val[e0 + e]; }
-    }
-    for (int t = tid; t <= nr; t += BNT) srp[t] = a.P.rp[r0 + t] - e0;
+    kkt_stage<NIT>(a.P, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) {
+      return c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n));
+    });
     for (int t = tid; t < nr; t += BNT) ssp[t] = a.P.split[r0 + t] - e0;
-#pragma unroll
-    for (int k = 0; k < BEPT; ++k) {
-      const int e = tid + k * BNT;
-      if (e < ne) {
-        const int c = ci[k];
-#pragma unroll
-        for (int it = 0; it < NIT; ++it)
-          prod[it][e] = vv[k] * (c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n)));
-      }
-    }
     __syncthreads();
     for (int q = tid; q < nr * NIT; q += BNT) {
-      const int it = q / nr, t = q - it * nr;
+      const int it = q >= nr ? 1 : 0, t = q - it * nr;
+      const double* xv = sx + it * BNNZ;
       double sq = 0.0, sa = 0.0;
-      for (int e = srp[t]; e < ssp[t]; ++e) sq += prod[it][e];
-      for (int e = ssp[t]; e < srp[t + 1]; ++e) sa += prod[it][e];
-      row(r0 + t, it, sq, sa);
+      for (int e = srp[t]; e < ssp[t]; ++e) sq = fma(sval[e], xv[e], sq);
+      for (int e = ssp[t]; e < srp[t + 1]; ++e) sa = fma(sval[e], xv[e], sa);
+      if (it == 0) kkt_n_row<0, LR>(a, f, r0 + t, sq, sa);
+      else kkt_n_row<NIT - 1, LR>(a, f, r0 + t, sq, sa);
     }
   } else {
     const int sp = a.P.split[r0];
@@ -486,18 +512,35 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
       const int c = a.P.col[e];
 #pragma unroll
       for (int it = 0; it < NIT; ++it) {
-        if (e < sp) sq[it] += v * __ldg(a.x[it] + c);
-        else sa[it] += v * __ldg(a.y[it] + (c - n));
+        if (e < sp) sq[it] = fma(v, __ldg(a.x[it] + c), sq[it]);
+        else sa[it] = fma(v, __ldg(a.y[it] + (c - n)), sa[it]);
       }
     }
 #pragma unroll
     for (int it = 0; it < NIT; ++it) { sq[it] = block_sum(sq[it]); sa[it] = block_sum(sa[it]); }
-    if (tid == 0)
-      for (int it = 0; it < NIT; ++it) row(r0, it, sq[it], sa[it]);
+    if (tid == 0) {
+      kkt_n_row<0, LR>(a, f, r0, sq[0], sa[0]);
+      if (NIT > 1) kkt_n_row<NIT - 1, LR>(a, f, r0, sq[NIT - 1], sa[NIT - 1]);
+    }
   }
-  block_reduce_smem<15, BNT>(f, 0x4387u, stage);
+  block_reduce_smem<15, BNT>(f, 0x4387u, kkt_sm);
   if (tid == 0)
     for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
+}
+
+// launch both relKKT kernels with their dynamic shared memory
+template <int NIT>
+static void launch_kkt(const Work& w, const KktB& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_kkt_m<NIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
+    cudaFuncSetAttribute(k_kkt_n<NIT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
+    cudaFuncSetAttribute(k_kkt_n<NIT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
+    attr = true;
+  }
+  if (w.m > 0) launch(k_kkt_m<NIT>, w.A.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
+  if (a.F) launch(k_kkt_n<NIT, true>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
+  else launch(k_kkt_n<NIT, false>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
 }
 
 // reduce the field-major partials of k_kkt_m / k_kkt_n (blocks [bm0, bm1) of
@@ -1691,8 +1734,7 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     lowrank_ft<double, double>(w, w.Fd, a.x[0], a.x[1], s);
     a.F = w.Fd; a.wlr = w.wlr; a.r = w.r;
   }
-  if (w.m > 0) launch(k_kkt_m<2>, w.A.nblk, BNT, 0, s, a);
-  launch(k_kkt_n<2>, w.P.nblk, BNT, 0, s, a);
+  launch_kkt<2>(w, a, s);
   {
     const dim3 grid(w.count, std::max(w.maxchunk_n, w.maxchunk_m));
     launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
@@ -1754,8 +1796,7 @@ void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
     lowrank_ft<double, double>(w, w.Fo, x, (const double*)nullptr, s);
     a.F = w.Fo; a.wlr = w.wlr; a.r = w.r;
   }
-  if (w.m > 0) launch(k_kkt_m<1>, w.A.nblk, BNT, 0, s, a);
-  launch(k_kkt_n<1>, w.P.nblk, BNT, 0, s, a);
+  launch_kkt<1>(w, a, s);
   launch(k_kkt_finish_user, 1, 1024, 0, s, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,
          (const double*)w.part_n, w.P.nblk, w.st);
 }
