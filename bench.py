@@ -54,12 +54,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 256, 512])
     ap.add_argument("--workload", default="large_sparse_qp",
-                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws", "gemm"],
+                    choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws", "gemm", "algorithms"],
                     help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
                          "of horizon 10..100 in one batched handle; random_sparse_qp: n=1000; "
                          "family_ws: held-out members of the n=2e4 family solved in one handle from the "
                          "learned warm start (network trained first on --train solver outputs); "
-                         "gemm: the tensor-core BF16 GEMM alone, --gemm-size^3 (and the network's shapes)")
+                         "gemm: the tensor-core BF16 GEMM alone, --gemm-size^3 (and the network's shapes); "
+                         "algorithms: Section 5's comparison of PDHG, accelerated PDHG, restarted PDHG and "
+                         "rAPDHG (iteration SGM10) on a synthetic QP set")
     ap.add_argument("--gemm-size", type=int, default=8192)
     ap.add_argument("--batch", type=int, default=None,
                     help="instances per step (mpc_batch: 4096, family_ws: 1024)")
@@ -624,6 +626,100 @@ def run_gemm(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- algorithms
+# Section 5 compares four algorithms -- PDHG, accelerated PDHG, restarted PDHG and
+# rAPDHG (Algorithm 1) -- from all-zero starts, with the adaptive restart of that
+# section (restart when relKKT of the average has halved since the epoch's
+# start), no restart, and rAPDHG with a fixed restart length from {10, 100,
+# 1000} (the best per instance), at eps = 1e-3 and 1e-6 with a 200000-iteration
+# limit, by the shifted geometric mean of iterations (shift 10, unsolved counted
+# at the limit).  The paper's instance set is not available; a synthetic set of
+# the QP classes the generators cover stands in for it.
+ALGORITHMS = [  # name, accelerate, restart_rule (0 Section 6, 1 halving, 2 fixed K, 3 none), fixed_K
+    ("rAPDHG (Algorithm 1)", 1, 1, 0),
+    ("accelerated PDHG", 1, 3, 0),
+    ("restarted PDHG", 0, 1, 0),
+    ("PDHG", 0, 3, 0),
+    ("rAPDHG, fixed K=10", 1, 2, 10),
+    ("rAPDHG, fixed K=100", 1, 2, 100),
+    ("rAPDHG, fixed K=1000", 1, 2, 1000),
+    ("rAPDHG, Section 6 rules", 1, 0, 0),
+]
+SGM_LIMIT = 200000
+
+
+def sgm10(iters):
+    """Shifted geometric mean with shift 10 (Section 5)."""
+    return float(np.exp(np.mean(np.log(np.asarray(iters, dtype=np.float64) + 10.0))) - 10.0)
+
+
+def algorithm_set(seed0):
+    """The synthetic instance set: random sparse QPs (n = 200..1000), control
+    QPs (horizons from 10 to 100), large sparse QPs (n = 1e4, 2e4)."""
+    import qpgen
+    insts = []
+    for k, n in enumerate((200, 400, 600, 800, 1000)):
+        for r in range(2):
+            insts.append(qpgen.random_sparse_qp(seed=seed0 + 100 + 10 * k + r, n=n, m=n // 2))
+    insts += [qpgen.mpc_qp(seed=seed0 + 200 + r) for r in range(8)]
+    insts += [qpgen.large_sparse_qp(seed=seed0 + 300 + r, n=n) for r, n in enumerate((10_000, 20_000))]
+    return insts
+
+
+def run_algorithms(args, world, rank, local):
+    import torch
+
+    import qpgen
+    from paper_2311_07710_gb300 import pdqp
+
+    pdqp.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    insts = algorithm_set(qpgen.SEED_BASE + 5000 + 1000 * rank)
+    h = pdqp.batch_from_instances(insts, device=True)
+    N, M = sum(i.n for i in insts), sum(i.m for i in insts)
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+    y = torch.zeros(M, dtype=torch.float64, device=dev)
+    table = {}
+    t0 = time.perf_counter()
+    launches0 = pdqp.pdqp_launch_count()
+    for eps in (1e-3, 1e-6):
+        per = {}
+        for name, acc, rule, K in ALGORITHMS:
+            o = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, eps=eps, max_iter=SGM_LIMIT,
+                                          accelerate=acc, restart_rule=rule, fixed_K=max(K, 1))
+            pdqp.pdqp_solve(h, o, x_out=x, y_out=y)
+            infos = pdqp.pdqp_batch_info(h)
+            its = [i.iterations if i.status == pdqp.PDQP_OK else SGM_LIMIT for i in infos]
+            per[name] = {"solved": sum(i.status == pdqp.PDQP_OK for i in infos), "sgm10": sgm10(its),
+                         "iterations": its}
+        best = [min(a, b, c) for a, b, c in zip(*(per[f"rAPDHG, fixed K={K}"]["iterations"] for K in (10, 100, 1000)))]
+        per["rAPDHG, tuned fixed K (best per instance)"] = {"solved": sum(b < SGM_LIMIT for b in best),
+                                                            "sgm10": sgm10(best), "iterations": best}
+        table[f"{eps:g}"] = per
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    launches = pdqp.pdqp_launch_count() - launches0
+    pdqp.pdqp_destroy(h)
+    if rank != 0:
+        return
+    summary = {eps: {k: {"solved": v["solved"], "sgm10": round(v["sgm10"], 2)} for k, v in per.items()}
+               for eps, per in table.items()}
+    line = {"metric": "iterations SGM10 (shift 10, limit 200000) of PDHG-family algorithms, Section 5 protocol",
+            "value": table["1e-06"]["rAPDHG (Algorithm 1)"]["sgm10"], "unit": "iterations",
+            "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": {"workload": f"algorithms: {len(insts)} synthetic QPs (10 random sparse n=200..1000, "
+                                   "8 control horizons 10..100, 2 large sparse n=1e4, 2e4), one batched handle "
+                                   "per algorithm and tolerance",
+                       "instances": len(insts), "eps": [1e-3, 1e-6], "iteration_limit": SGM_LIMIT,
+                       "step_rule": "Section 6 adaptive step (constant eta_0 without acceleration)",
+                       "adaptive_restart": "relKKT(average) <= relKKT(epoch start) / 2",
+                       "parallelism": "replicas x1"},
+            "table": summary, "gpu_launches": launches}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -634,6 +730,8 @@ def main():
         run_family_ws(args, world, rank, local)
     elif args.workload == "gemm":
         run_gemm(args, world, rank, local)
+    elif args.workload == "algorithms":
+        run_algorithms(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
