@@ -655,7 +655,8 @@ def sgm10(iters):
 
 def algorithm_set(seed0):
     """The synthetic instance set: random sparse QPs (n = 200..1000), control
-    QPs (horizons from 10 to 100), large sparse QPs (n = 1e4, 2e4)."""
+    QPs (horizons from 10 to 100), large sparse QPs (n = 1e4, 2e4), and two
+    each of Lasso, Huber fitting and SVM."""
     import qpgen
     insts = []
     for k, n in enumerate((200, 400, 600, 800, 1000)):
@@ -663,6 +664,9 @@ def algorithm_set(seed0):
             insts.append(qpgen.random_sparse_qp(seed=seed0 + 100 + 10 * k + r, n=n, m=n // 2))
     insts += [qpgen.mpc_qp(seed=seed0 + 200 + r) for r in range(8)]
     insts += [qpgen.large_sparse_qp(seed=seed0 + 300 + r, n=n) for r, n in enumerate((10_000, 20_000))]
+    insts += [qpgen.lasso_qp(seed=seed0 + 400, n=200, m=100), qpgen.lasso_qp(seed=seed0 + 401, n=1000, m=500)]
+    insts += [qpgen.huber_qp(seed=seed0 + 500, n=100, m=500), qpgen.huber_qp(seed=seed0 + 501, n=300, m=3000)]
+    insts += [qpgen.svm_qp(seed=seed0 + 600, n=50, m=200), qpgen.svm_qp(seed=seed0 + 601, n=200, m=1000)]
     return insts
 
 
@@ -710,8 +714,8 @@ def run_algorithms(args, world, rank, local):
             "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
             "config": {"workload": f"algorithms: {len(insts)} synthetic QPs (10 random sparse n=200..1000, "
-                                   "8 control horizons 10..100, 2 large sparse n=1e4, 2e4), one batched handle "
-                                   "per algorithm and tolerance",
+                                   "8 control horizons 10..100, 2 large sparse n=1e4, 2e4, 2 Lasso, 2 Huber, "
+                                   "2 SVM), one batched handle per algorithm and tolerance",
                        "instances": len(insts), "eps": [1e-3, 1e-6], "iteration_limit": SGM_LIMIT,
                        "step_rule": "Section 6 adaptive step (constant eta_0 without acceleration)",
                        "adaptive_restart": "relKKT(average) <= relKKT(epoch start) / 2",

@@ -4,3 +4,4 @@ from .instances import (  # noqa: F401
     mpc_qp, mpc_batch, family_qp, tiny_qp, diagonal_box_qp,
 )
 from .weights import warmstart_params  # noqa: F401
+from .classes import lasso_qp, huber_qp, svm_qp  # noqa: F401

@@ -28,5 +28,5 @@ def test_instance_set_is_seeded():
     import qpgen
     a = bench.algorithm_set(qpgen.SEED_BASE + 5000)
     b = bench.algorithm_set(qpgen.SEED_BASE + 5000)
-    assert len(a) == 20
+    assert len(a) == 26
     assert all((x.c == y.c).all() and (x.A != y.A).nnz == 0 for x, y in zip(a, b))
