@@ -102,9 +102,14 @@ typedef struct {
                                 relative (default 1e-6) */
   int32_t spmv_threads;      /* iteration-kernel variant: 256 or 512 threads per row
                                 block, 1 = pipelined persistent (cp.async prefetch of
-                                the next row block), 0 = autotuned: the first full
-                                chunk of a handle's first solve times 8 iterations of
-                                each variant and the handle keeps the fastest (all
+                                the next row block), 2 = a whole chunk of iterations
+                                in one launch of an 8-CTA thread-block cluster with a
+                                cluster barrier after each half-step (problems of at
+                                most 64 row blocks of A and of P, no row longer than a
+                                row block, no low-rank term; else PDQP_ERR_INVALID),
+                                0 = autotuned: the first full chunk of a handle's
+                                first solve times two rounds of 4 iterations of each
+                                eligible variant and the handle keeps the fastest (all
                                 variants give bitwise identical iterates) */
   int32_t no_graphs;         /* 0: replay each full chunk of check_period iterations
                                 and its check as one captured CUDA graph; 1: launch

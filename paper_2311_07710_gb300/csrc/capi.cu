@@ -30,7 +30,7 @@ struct pdqp_problem {
   std::vector<pdqp_info> infos;                       // per instance, from the last solve
   std::vector<void*> allocs;
   int tuned_nt = 0;                                   // autotuned iteration-kernel variant (0: not yet)
-  cudaEvent_t tune_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t tune_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 static thread_local std::string g_create_error;
@@ -261,8 +261,9 @@ void validate_options(const pdqp_options& o) {
   if ((o.restart_rule == PDQP_RESTART_FIXED || o.step_rule == PDQP_STEP_THEORY) && o.fixed_K < 1)
     bad("options.fixed_K must be >= 1");
   if (o.norm_iters < 1 || o.norm_iters > 512) bad("options.norm_iters must be in [1, 512]");
-  if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 256 && o.spmv_threads != 512)
-    bad("options.spmv_threads must be 0, 1, 256 or 512");
+  if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 2 && o.spmv_threads != 256 &&
+      o.spmv_threads != 512)
+    bad("options.spmv_threads must be 0, 1, 2, 256 or 512");
 }
 
 double now_s() {
@@ -305,8 +306,27 @@ void fill_info(pdqp_info* info, const DevState& S, pdqp_status status, bool lanc
 // launch only those blocks (direct launches sized by the last check's counts)
 // instead of replaying the full-grid chunk graph.
 bool compact_now(const Work& w, const SolveParams& p) {
-  if (w.count <= 1 || p.spmv_threads == 1) return false;
+  if (w.count <= 1 || p.spmv_threads == 1 || p.spmv_threads == 2) return false;
   return 2LL * w.bst_host->act_P < (long long)w.P.nblk;
+}
+
+// Iterations j0 .. j0+len-1 with variant nt captured into a graph (for the
+// tuner: each candidate is timed as the solve loop runs it, replayed).
+cudaGraphExec_t capture_iterations(pdqp_problem* h, int len, bool mixed, int nt, int j0, long long* kernels) {
+  Work& w = h->w;
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  const long long before = pdqp::g_launches;
+  pdqp::iterate_chunk(w, len, mixed, nt, h->cap, j0);
+  *kernels = pdqp::g_launches - before;
+  pdqp::g_launches = before;   // captured, not launched
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamEndCapture(h->cap, &graph));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  return exec;
 }
 
 void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
@@ -354,6 +374,11 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   check_space(x_out, mem, "x_out");
   check_space(y_out, mem, "y_out");
   const bool mixed = o.precision == PDQP_PREC_MIXED;
+  const bool cluster_ok = pdqp::chunk_cluster_ok(w, mixed);
+  if (o.spmv_threads == 2 && !cluster_ok)
+    throw Fail{PDQP_ERR_INVALID, "options.spmv_threads = 2 needs at most 64 row blocks of A and of P, no row "
+                                 "longer than a row block, no low-rank term and 3n + 2m values within 200 KB"};
+  if (cluster_ok) pdqp::prepare_chunk_cluster();
   if (mixed) alloc_mixed(h);
   SolveParams p = make_params(o);
 
@@ -408,37 +433,55 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   // two rounds of TUNE iterations with each candidate (interleaved, so that no
   // candidate always runs first on a cold cache), keeps the fastest by its
   // better round and runs the rest of the chunk with it; the iterates do not
-  // depend on the variant
-  static const int kCand[3] = {256, 512, 1};
+  // depend on the variant.  Problems of a few row blocks also try the
+  // one-launch cluster chunk.  Each candidate's iterations are captured into a
+  // graph and replayed, as the solve loop runs them (direct launches would
+  // charge the per-iteration variants launch gaps that graphs do not have);
+  // with the event profiler on, they are launched directly.
+  static const int kCand[4] = {256, 512, 1, 2};
+  const int ncand = cluster_ok ? 4 : 3;
   constexpr int TUNE = 4, ROUNDS = 2;
   const bool autotune = o.spmv_threads == 0;
   if (autotune && h->tuned_nt) p.spmv_threads = h->tuned_nt;
   while (w.bst_host->running > 0) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
-    const bool tune_now = autotune && !h->tuned_nt && len == o.check_period && len >= 2 * 3 * ROUNDS * TUNE;
+    const bool tune_now = autotune && !h->tuned_nt && len == o.check_period && len >= 2 * ncand * ROUNDS * TUNE;
     // per-kernel event timing needs direct launches (events recorded by graph
     // nodes cannot be timed), so profiling bypasses the graph
     if (tune_now) {
       for (auto& e : h->tune_ev)
         if (!e) CK(cudaEventCreate(&e));
-      float best_ms[3] = {0.f, 0.f, 0.f};
+      float best_ms[4] = {0.f, 0.f, 0.f, 0.f};
       int j = 0;
+      const bool replay = !w.prof.on && !o.no_graphs;
+      if (replay) pdqp::iterate_chunk(w, 0, mixed, 1, s, 0);   // one-time setup of the pipelined variant
       for (int r = 0; r < ROUNDS; ++r) {
+        cudaGraphExec_t ex[4] = {nullptr, nullptr, nullptr, nullptr};
+        long long kern[4] = {0, 0, 0, 0};
+        if (replay)
+          for (int c = 0; c < ncand; ++c) ex[c] = capture_iterations(h, TUNE, mixed, kCand[c], j + c * TUNE, &kern[c]);
         CK(cudaEventRecord(h->tune_ev[0], s));
-        for (int c = 0; c < 3; ++c) {
-          pdqp::iterate_chunk(w, TUNE, mixed, kCand[c], s, j);
+        for (int c = 0; c < ncand; ++c) {
+          if (replay) {
+            CK(cudaGraphLaunch(ex[c], s));
+            pdqp::g_launches += kern[c];
+          } else {
+            pdqp::iterate_chunk(w, TUNE, mixed, kCand[c], s, j);
+          }
           j += TUNE;
           CK(cudaEventRecord(h->tune_ev[c + 1], s));
         }
-        CK(cudaEventSynchronize(h->tune_ev[3]));
-        for (int c = 0; c < 3; ++c) {
+        CK(cudaEventSynchronize(h->tune_ev[ncand]));
+        for (int c = 0; c < ncand; ++c)
+          if (ex[c]) cudaGraphExecDestroy(ex[c]);
+        for (int c = 0; c < ncand; ++c) {
           float ms = 0.f;
           CK(cudaEventElapsedTime(&ms, h->tune_ev[c], h->tune_ev[c + 1]));
           if (r == 0 || ms < best_ms[c]) best_ms[c] = ms;
         }
       }
       int bc = 0;
-      for (int c = 1; c < 3; ++c)
+      for (int c = 1; c < ncand; ++c)
         if (best_ms[c] < best_ms[bc]) bc = c;
       h->tuned_nt = kCand[bc];
       p.spmv_threads = h->tuned_nt;

@@ -7,9 +7,13 @@
 //              and the next iteration's x_md and x_tilde
 // with their pipelined persistent variants, the segment sums of long rows,
 // and the host loop that launches a chunk of iterations.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "rowblock.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pdqp {
 
@@ -61,14 +65,13 @@ __device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, 
   a.ynew[r] = yn;
 }
 
-template <typename V, int NT>
-__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a, int j) {
-  __shared__ V prod[BNNZ];
-  __shared__ int srp[BROWS + 1];
+// The dual half-step of row block bk (one CUDA block): prod and srp are the
+// block's staging buffers; GM is how x_tilde is gathered (see stage_products).
+template <typename V, int NT, int GM>
+__device__ __forceinline__ void dual_block(const DualB<V>& a, int bk, int j, V* prod, int* srp) {
   const int tid = threadIdx.x;
-  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;   // compacted batches: running blocks only
   const int inst = a.blk_inst[bk];
-  if (a.st[inst].status != ST_RUNNING) return;
+  if (a.st[inst].status != ST_RUNNING) return;    // uniform over the block
   const int r0 = a.A.blk[bk], r1 = a.A.blk[bk + 1];
   const int nr = r1 - r0;
   const int e0 = a.A.rp[r0];
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a
   }
   const StepEntry& es = a.tab[inst * a.C + j];
   if (ne <= BNNZ) {
-    stage_products<NT>(a.A, a.xt, e0, ne, r0, nr, prod, srp);
+    stage_products<NT, GM>(a.A, a.xt, e0, ne, r0, nr, prod, srp);
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
       V s = V(0);
@@ -103,10 +106,19 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a
     }
   } else {   // a single row longer than a block
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT)
+      s += a.A.val[e] * gather_load<GM>(a.xt + a.A.col[e]);
     s = block_sum(s);
     if (tid == 0) dual_row(a, es, r0, s, yo, bi, yb, lo);
   }
+}
+
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a, int j) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;   // compacted batches: running blocks only
+  dual_block<V, NT, GATHER_LDG>(a, bk, j, prod, srp);
 }
 
 // --------------------------------------------------------------------------
@@ -148,16 +160,12 @@ __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry&
   a.x[r] = xn;
 }
 
-// LR: the problem has a low-rank term (its row term gets its own instantiation
-// so that the plain kernel keeps its 32 registers)
-template <typename V, int NT, bool LR = false>
-__global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(PrimalB<V> a, int j) {
-  __shared__ V prod[BNNZ];
-  __shared__ int srp[BROWS + 1];
+// The primal half-step of row block bk (one CUDA block), as dual_block.
+template <typename V, int NT, bool LR, int GM>
+__device__ __forceinline__ void primal_block(const PrimalB<V>& a, int bk, int j, V* prod, int* srp) {
   const int tid = threadIdx.x;
-  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
   const int inst = a.blk_inst[bk];
-  if (a.st[inst].status != ST_RUNNING) return;
+  if (a.st[inst].status != ST_RUNNING) return;    // uniform over the block
   const int r0 = a.P.blk[bk], r1 = a.P.blk[bk + 1];
   const int nr = r1 - r0;
   const int e0 = a.P.rp[r0];
@@ -169,7 +177,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(Prim
   }
   const StepEntry& es = a.tab[inst * a.C + j];
   if (ne <= BNNZ) {
-    stage_products<NT>(a.P, a.zin, e0, ne, r0, nr, prod, srp);
+    stage_products<NT, GM>(a.P, a.zin, e0, ne, r0, nr, prod, srp);
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
       V s = V(0);
@@ -187,9 +195,114 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(Prim
     }
   } else {
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += NT) s += a.P.val[e] * __ldg(a.zin + a.P.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT)
+      s += a.P.val[e] * gather_load<GM>(a.zin + a.P.col[e]);
     s = block_sum(s);
     if (tid == 0) primal_row<V, LR>(a, es, r0, s, xo, xb, cr, lr, ur);
+  }
+}
+
+// LR: the problem has a low-rank term (its row term gets its own instantiation
+// so that the plain kernel keeps its 32 registers)
+template <typename V, int NT, bool LR = false>
+__global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(PrimalB<V> a, int j) {
+  __shared__ V prod[BNNZ];
+  __shared__ int srp[BROWS + 1];
+  const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
+  primal_block<V, NT, LR, GATHER_LDG>(a, bk, j, prod, srp);
+}
+
+// --------------------------------------------------------------------------
+// A whole chunk of iterations in one launch, for small problems (whose
+// per-iteration kernels are bound by launch and gather latency): one cluster
+// of C = 16 CTAs (8 where 16 cannot be co-scheduled).  Every CTA keeps its own copy of x_tilde and of both
+// [x_md ; y] buffers in shared memory and gathers from it; after each
+// half-step it writes the rows it updated into every CTA's copy (distributed
+// shared memory) and the cluster meets at a barrier (release / acquire).  CTA
+// c takes row blocks c, c + C, ... of A and of P.  The row arithmetic
+// is that of k_dual / k_primal, so the iterates are bitwise theirs, and every
+// result still goes to global memory for the checks.  Every thread of every
+// CTA takes the same 2 * len + 1 barriers: no path leaves the loop early
+// (blocks of an instance that stopped are skipped).  No low-rank term, no
+// long rows, and the copies must fit in shared memory (the host checks).
+// --------------------------------------------------------------------------
+constexpr int CHUNK_NT = 512;
+constexpr int CHUNK_MAX_BLOCKS = 64;               // row blocks of A and of P, each
+constexpr int CHUNK_SMEM_MAX = 200 * 1024;
+
+// every thread of the cluster arrives (release) and waits (acquire); the
+// unaligned form does not need the warp converged at the barrier
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
+}
+
+template <typename V>
+constexpr size_t chunk_head_bytes() {     // staging buffers, rounded to 16 bytes
+  return ((size_t)BNNZ * sizeof(V) + (BROWS + 1) * sizeof(int) + 15) / 16 * 16;
+}
+template <typename V>
+static size_t chunk_smem_bytes(int n, int m) {
+  return chunk_head_bytes<V>() + (size_t)(3 * (size_t)n + 2 * (size_t)m) * sizeof(V);
+}
+
+// write v into slot p of every CTA's copy (p: this CTA's shared address)
+template <typename V>
+__device__ __forceinline__ void broadcast(cg::cluster_group& cl, int ctas, V* p, V v) {
+  for (int q = 0; q < ctas; ++q) *cl.map_shared_rank(p, q) = v;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(CHUNK_NT)
+    k_chunk_cluster(DualB<V> da, PrimalB<V> pa, int nblkA, int nblkP, V* z0, V* z1, int n, int m, int j0,
+                    int len) {
+  extern __shared__ __align__(16) unsigned char chunk_sm[];
+  V* prod = reinterpret_cast<V*>(chunk_sm);
+  int* srp = reinterpret_cast<int*>(prod + BNNZ);
+  V* xs = reinterpret_cast<V*>(chunk_sm + chunk_head_bytes<V>());   // x_tilde
+  V* zs[2] = {xs + n, xs + n + (n + m)};                            // [x_md ; y], both buffers
+  cg::cluster_group cl = cg::this_cluster();
+  const int cta = (int)cl.block_rank(), ctas = (int)cl.num_blocks();   // the grid is one cluster
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += CHUNK_NT) xs[i] = __ldcg(pa.xt + i);
+  for (int i = tid; i < n + m; i += CHUNK_NT) {
+    zs[0][i] = __ldcg(z0 + i);
+    zs[1][i] = __ldcg(z1 + i);
+  }
+  cluster_barrier();                              // every copy is whole before anyone writes into it
+  DualB<V> dl = da;
+  dl.xt = xs;
+  PrimalB<V> pl = pa;
+  for (int j = j0; j < j0 + len; ++j) {
+    V* zj = (j & 1) ? z1 : z0;
+    V* zn = (j & 1) ? z0 : z1;
+    V* zsj = zs[j & 1];
+    V* zsn = zs[(j + 1) & 1];
+    dl.yold = zn + n;
+    dl.ynew = zj + n;
+    for (int bk = cta; bk < nblkA; bk += ctas) {
+      __syncthreads();                            // the previous block's rows are done with prod
+      dual_block<V, CHUNK_NT, GATHER_PLAIN>(dl, bk, j, prod, srp);
+      if (da.st[da.blk_inst[bk]].status == ST_RUNNING) {
+        const int r0 = da.A.blk[bk], nr = da.A.blk[bk + 1] - r0;
+        for (int t = tid; t < nr; t += CHUNK_NT) broadcast(cl, ctas, zsj + n + r0 + t, dl.ynew[r0 + t]);
+      }
+    }
+    cluster_barrier();
+    pl.zin = zsj;
+    pl.zout = zn;
+    for (int bk = cta; bk < nblkP; bk += ctas) {
+      __syncthreads();
+      primal_block<V, CHUNK_NT, false, GATHER_PLAIN>(pl, bk, j, prod, srp);
+      if (pa.st[pa.blk_inst[bk]].status == ST_RUNNING) {
+        const int r0 = pa.P.blk[bk], nr = pa.P.blk[bk + 1] - r0;
+        for (int t = tid; t < nr; t += CHUNK_NT) {
+          broadcast(cl, ctas, zsn + r0 + t, zn[r0 + t]);
+          broadcast(cl, ctas, xs + r0 + t, pl.xt[r0 + t]);
+        }
+      }
+    }
+    cluster_barrier();
   }
 }
 
@@ -467,7 +580,88 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
   }
 }
 
+bool chunk_cluster_ok(const Work& w, bool mixed) {
+  const size_t smem = mixed ? chunk_smem_bytes<float>(w.n, w.m) : chunk_smem_bytes<double>(w.n, w.m);
+  return w.r == 0 && w.A.nlseg == 0 && w.P.nlseg == 0 && w.A.nblk <= CHUNK_MAX_BLOCKS &&
+         w.P.nblk <= CHUNK_MAX_BLOCKS && w.P.nblk > 0 && smem <= (size_t)CHUNK_SMEM_MAX;
+}
+
+// cluster size: 16 CTAs if a 16-CTA cluster of the largest footprint fits, else 8
+static int g_chunk_ctas = 8;
+
+template <typename V>
+static int chunk_cluster_size() {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(CHUNK_NT);
+  cfg.dynamicSmemBytes = CHUNK_SMEM_MAX;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_chunk_cluster<V>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 8;
+  }
+  return clusters >= 1 ? 16 : 8;
+}
+
+void prepare_chunk_cluster() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_chunk_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, CHUNK_SMEM_MAX);
+  cudaFuncSetAttribute(k_chunk_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CHUNK_SMEM_MAX);
+  cudaFuncSetAttribute(k_chunk_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_chunk_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  g_chunk_ctas = std::min(chunk_cluster_size<float>(), chunk_cluster_size<double>());
+  done = true;
+}
+
+template <typename V>
+static void run_chunk_cluster(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* const* Z, V* ybar,
+                              const V* b, const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u,
+                              cudaStream_t s) {
+  Profiler& Pr = w.prof;
+  DualB<V> da{A, xt, nullptr, nullptr, ybar, b, ylo, w.tab, w.blk_inst_A, w.st, w.row_ineq, w.tab_stride};
+  PrimalB<V> pa{P, nullptr, nullptr, x, xbar, xt, c, l, u, w.tab, w.blk_inst_P, w.st, w.tab_stride,
+                nullptr, nullptr, 0};
+  // kind 3: one launch holds both half-steps of `len` iterations
+  if (Pr.on) Pr.begin(3, s, len * (launch_bytes(w, 0, sizeof(V)) + launch_bytes(w, 1, sizeof(V))));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = g_chunk_ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(g_chunk_ctas);               // one cluster
+  cfg.blockDim = dim3(CHUNK_NT);
+  cfg.dynamicSmemBytes = chunk_smem_bytes<V>(w.n, w.m);
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_chunk_cluster<V>, da, pa, w.m > 0 ? w.A.nblk : 0, w.P.nblk, Z[0], Z[1], w.n, w.m, j0,
+                     len);
+  ++g_launches;
+  if (Pr.on) Pr.end(s);
+}
+
 void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0, bool compact) {
+  if (nt == 2) {   // the whole chunk in one cluster launch (small problems)
+    if (mixed) {
+      run_chunk_cluster<float>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo,
+                               w.fx, w.fxbar, w.fc, w.fl, w.fu, s);
+      w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
+    } else {
+      run_chunk_cluster<double>(w, j0, len, w.A.bscaled(), w.P.bscaled(), w.xt, w.Z, w.ybar, w.bs, nullptr, w.x,
+                                w.xbar, w.cs, w.ls, w.us, s);
+      w.y = w.Z[(j0 + len - 1) & 1] + w.n;
+    }
+    return;
+  }
   if (nt == 1) {   // pipelined persistent kernels, 256 threads
     if (mixed) {
       run_chunk_pipe<float, 256>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx,

@@ -45,7 +45,19 @@ __device__ __forceinline__ T block_sum(T v) {
 // Row-block staging: the products val[e] * vec[col[e]] of one block's
 // nonzeros go to shared memory prod[0..ne); srp[t] = rp[r0+t] - e0.
 // ==========================================================================
-template <int NT, typename V, typename X>
+// How the staging gathers the vector: through the read-only path (GATHER_LDG),
+// through L2 (GATHER_CG: vectors that other CTAs of the same launch write), or
+// with plain loads of a generic pointer (GATHER_PLAIN: a copy in shared memory).
+enum { GATHER_LDG = 0, GATHER_CG = 1, GATHER_PLAIN = 2 };
+
+template <int GM, typename X>
+__device__ __forceinline__ X gather_load(const X* p) {
+  if constexpr (GM == GATHER_LDG) return __ldg(p);
+  else if constexpr (GM == GATHER_CG) return __ldcg(p);
+  else return *p;
+}
+
+template <int NT, int GM = GATHER_LDG, typename V, typename X>
 __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
                                                int r0, int nr, V* prod, int* srp) {
   // float data: two phases of EPT/2 loads and gathers each, half the
@@ -68,7 +80,7 @@ __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __rest
 #pragma unroll
     for (int k = 0; k < H; ++k) {
       const int e = tid + (h * H + k) * NT;
-      if (e < ne) prod[e] = vv[k] * (V)__ldg(vec + ci[k]);
+      if (e < ne) prod[e] = vv[k] * (V)gather_load<GM>(vec + ci[k]);
     }
   }
 }

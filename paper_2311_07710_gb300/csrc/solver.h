@@ -156,7 +156,12 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
 // Iterations j0 .. j0+len-1 of a chunk (j indexes the chunk's step table).
 // compact: launch only the row blocks of the running instances (batches; the
 // counts of the last check must be in bst_host).
+// nt: 256 or 512 threads per row block, 1 the pipelined persistent kernels, 2
+// the whole chunk in one cluster launch (only where chunk_cluster_ok).
 void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0, bool compact = false);
+// few row blocks, no long rows, no low-rank term, the vector copies fit in shared memory
+bool chunk_cluster_ok(const Work& w, bool mixed);
+void prepare_chunk_cluster();           // once, outside any stream capture
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
 
 // results
