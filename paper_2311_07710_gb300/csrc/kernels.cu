@@ -833,7 +833,8 @@ __global__ void __launch_bounds__(NT) k_lz_alpha(LzArgs a, const double* __restr
   }
 }
 
-// r = w - alpha v - beta_prev v_prev over v_prev, per P row block; partial |r|^2
+// r = w - alpha v - beta_prev v_prev over v_prev, per P row block; partial |r|^2.
+// The update runs in the vectors' precision (two FMAs), only |r|^2 in float64.
 template <typename V>
 __global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V* __restrict__ wQ,
                           const V* __restrict__ vA, V* __restrict__ vA_prev, const V* __restrict__ vQ,
@@ -843,21 +844,21 @@ __global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V
   const bool doA = !st.pi_done[0], doQ = !st.pi_done[1];
   if (!doA && !doQ) return;
   const int k = st.pi_iters;
-  const double alA = doA ? lz_al(a, i, 0)[k] : 0.0, alQ = doQ ? lz_al(a, i, 1)[k] : 0.0;
-  const double bpA = (doA && k > 0) ? lz_be(a, i, 0)[k - 1] : 0.0;
-  const double bpQ = (doQ && k > 0) ? lz_be(a, i, 1)[k - 1] : 0.0;
+  const V alA = (V)(doA ? lz_al(a, i, 0)[k] : 0.0), alQ = (V)(doQ ? lz_al(a, i, 1)[k] : 0.0);
+  const V bpA = (V)((doA && k > 0) ? lz_be(a, i, 0)[k - 1] : 0.0);
+  const V bpQ = (V)((doQ && k > 0) ? lz_be(a, i, 1)[k - 1] : 0.0);
   double f[2] = {0.0, 0.0};
   const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     if (doA) {
-      const double v = (double)wA[r] - alA * (double)vA[r] - bpA * (double)vA_prev[r];
-      vA_prev[r] = (V)v;
-      f[0] += v * v;
+      const V v = fma(-bpA, vA_prev[r], fma(-alA, vA[r], wA[r]));
+      vA_prev[r] = v;
+      f[0] = fma((double)v, (double)v, f[0]);
     }
     if (doQ) {
-      const double v = (double)wQ[r] - alQ * (double)vQ[r] - bpQ * (double)vQ_prev[r];
-      vQ_prev[r] = (V)v;
-      f[1] += v * v;
+      const V v = fma(-bpQ, vQ_prev[r], fma(-alQ, vQ[r], wQ[r]));
+      vQ_prev[r] = v;
+      f[1] = fma((double)v, (double)v, f[1]);
     }
   }
   __shared__ double sh[2 * 256];
@@ -1113,9 +1114,10 @@ template <typename V>
 __global__ void k_lz_norm(LzArgs a, V* __restrict__ vA_next, V* __restrict__ vQ_next) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += gridDim.x * blockDim.x) {
     const DevState& st = a.st[a.row_inst_n[r]];
-    // pi_inv_norm changes only when the operator continues
-    if (!st.pi_done[0]) vA_next[r] = (V)((double)vA_next[r] * st.pi_inv_norm[0]);
-    if (!st.pi_done[1]) vQ_next[r] = (V)((double)vQ_next[r] * st.pi_inv_norm[1]);
+    // pi_inv_norm changes only when the operator continues; the product in the
+    // vectors' precision
+    if (!st.pi_done[0]) vA_next[r] = vA_next[r] * (V)st.pi_inv_norm[0];
+    if (!st.pi_done[1]) vQ_next[r] = vQ_next[r] * (V)st.pi_inv_norm[1];
   }
 }
 
