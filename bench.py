@@ -621,7 +621,7 @@ def run_gemm(args, world, rank, local):
                        "l2": "operands 128 MiB each at 8192, larger than L2 with the output"},
             "roofline": {"bound": "tensor", "achieved": top["tflops"], "peak": peak, "unit": "TFLOP/s",
                          "frac": top["frac"], "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
-                         "kernel": "k_gemm_tn", "traffic": None},
+                         "kernel": "k_gemm_tn_p", "traffic": None},
             "shapes": results, "gpu_launches": args.steps * sum(1 + (r["splits"] > 1) for r in results)}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -142,154 +142,62 @@ __device__ __forceinline__ float epi_value(float r, int row, int col, const Epi&
   return r;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
-              int K, int ktps, Epi epi, float* __restrict__ partial, int* err) {
-  constexpr int STAGE_BYTES = Tile<BN>::STAGE_BYTES;
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
-  __shared__ int s_fail, s_issued;
-  __shared__ volatile int s_progress;   // stages consumed by the MMA issuer
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int KT = (K + BK - 1) / BK;
-  const int kt0 = blockIdx.z * ktps;
-  const int nk = min(KT, kt0 + ktps) - kt0;   // >= 1 by construction of the grid
-
-  if (threadIdx.x == 0) {
-    s_fail = 0;
-    s_issued = 0;
-    s_progress = 0;
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(done, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  if (warp == 0) {   // tensor-memory accumulator: 128 lanes x 128 float32 columns
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0 && lane == 0) {   // TMA producer
-    int i = 0;
-    for (; i < nk; ++i) {
-      const int s = i % STAGES;
-      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1, err)) {
-        s_fail = 1;
-        break;
-      }
-      unsigned char* a = sm + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(a, &mapA, &full[s], (kt0 + i) * BK, m0);
-      tma_load_2d(a + A_BYTES, &mapB, &full[s], (kt0 + i) * BK, n0);
-    }
-    s_issued = i;
-  } else if (warp == 1 && lane == 0) {   // MMA issuer
-    const uint32_t idesc = instr_desc(BM, BN);
-    for (int i = 0; i < nk; ++i) {
-      const int s = i % STAGES;
-      if (!mbar_wait(&full[s], (i / STAGES) & 1, err)) {
-        s_fail = 1;
-        break;
-      }
-      s_progress = i + 1;
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const unsigned char* a = sm + s * STAGE_BYTES;
-      const uint64_t da = smem_desc(a), db = smem_desc(a + A_BYTES);
+// Epilogue of 32 accumulator columns of one row: the raw float32 split-K
+// partial of split z (ld = N), or the fused epilogue into the outputs.
+__device__ __forceinline__ void store_chunk(const uint32_t (&v)[32], int row, int cb, int z, int M, int N,
+                                            const Epi& epi, float* __restrict__ partial) {
+  if (partial) {   // raw float32 partial of this k range, ld = N
+    float* dst = partial + ((size_t)z * M + row) * N + cb;
+    if (cb + 32 <= N && (N & 3) == 0) {
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        const uint64_t step = (uint64_t)((k * 16 * 2) >> 4);   // 32 bytes further along K
-        const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(da + step), "l"(db + step), "r"(idesc), "r"(acc));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(&empty[s])));
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-        smem_u32(done)));
-  }
-  __syncwarp();
-  __syncthreads();
-  const bool ok = !s_fail && mbar_wait(done, 0, err, &s_progress);
-  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
-
-  const int row = m0 + warp * 32 + lane;
-  for (int c0 = 0; c0 < BN; c0 += 32) {
-    uint32_t v[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    if (!ok || row >= M) continue;
-    const int cb = n0 + c0;
-    if (partial) {   // raw float32 partial of this k range, ld = N
-      float* dst = partial + ((size_t)blockIdx.z * M + row) * N + cb;
-      if (cb + 32 <= N && (N & 3) == 0) {
-#pragma unroll
-        for (int i = 0; i < 32; i += 4)
-          *(float4*)(dst + i) = make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
-                                            __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
-      } else {
-        for (int i = 0; i < 32 && cb + i < N; ++i) dst[i] = __uint_as_float(v[i]);
-      }
-      continue;
-    }
-    float r[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(v[i]);
-    if (cb + 32 <= N) {
-#pragma unroll
-      for (int i = 0; i < 32; ++i) r[i] = epi_value(r[i], row, cb + i, epi);
-      const size_t o = (size_t)row * epi.ldo + cb;
-      if (epi.out_f) {
-        if ((epi.ldo & 3) == 0) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 4) *(float4*)(epi.out_f + o + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
-        } else {
-          for (int i = 0; i < 32; ++i) epi.out_f[o + i] = r[i];
-        }
-      }
-      if (epi.out_b) {
-        if ((epi.ldo & 7) == 0) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 8) {
-            uint4 q;
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(r[i], r[i + 1]), h1 = __floats2bfloat162_rn(r[i + 2], r[i + 3]),
-                           h2 = __floats2bfloat162_rn(r[i + 4], r[i + 5]), h3 = __floats2bfloat162_rn(r[i + 6], r[i + 7]);
-            q.x = *(uint32_t*)&h0;
-            q.y = *(uint32_t*)&h1;
-            q.z = *(uint32_t*)&h2;
-            q.w = *(uint32_t*)&h3;
-            *(uint4*)(epi.out_b + o + i) = q;
-          }
-        } else {
-          for (int i = 0; i < 32; ++i) epi.out_b[o + i] = __float2bfloat16_rn(r[i]);
-        }
-      }
+      for (int i = 0; i < 32; i += 4)
+        *(float4*)(dst + i) = make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
+                                          __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
     } else {
-      for (int i = 0; i < 32 && cb + i < N; ++i) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (cb + i < N) dst[i] = __uint_as_float(v[i]);
+    }
+    return;
+  }
+  float r[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(v[i]);
+  if (cb + 32 <= N) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = epi_value(r[i], row, cb + i, epi);
+    const size_t o = (size_t)row * epi.ldo + cb;
+    if (epi.out_f) {
+      if ((epi.ldo & 3) == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) *(float4*)(epi.out_f + o + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) epi.out_f[o + i] = r[i];
+      }
+    }
+    if (epi.out_b) {
+      if ((epi.ldo & 7) == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) {
+          uint4 q;
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(r[i], r[i + 1]), h1 = __floats2bfloat162_rn(r[i + 2], r[i + 3]),
+                         h2 = __floats2bfloat162_rn(r[i + 4], r[i + 5]), h3 = __floats2bfloat162_rn(r[i + 6], r[i + 7]);
+          q.x = *(uint32_t*)&h0;
+          q.y = *(uint32_t*)&h1;
+          q.z = *(uint32_t*)&h2;
+          q.w = *(uint32_t*)&h3;
+          *(uint4*)(epi.out_b + o + i) = q;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) epi.out_b[o + i] = __float2bfloat16_rn(r[i]);
+      }
+    }
+  } else {   // the ragged last columns: a test per column keeps the indexing static
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (cb + i < N) {
         const float x = epi_value(r[i], row, cb + i, epi);
         const size_t o = (size_t)row * epi.ldo + cb + i;
         if (epi.out_f) epi.out_f[o] = x;
@@ -297,16 +205,179 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
+}
+
+// 32 float32 accumulator columns of this warp's TMEM lanes, from column address taddr
+__device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// D = A B' (bf16 A, B K-major, float32 accumulation in tensor memory), persistent:
+// one CTA per SM takes work units u = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (a unit is one BM x BN tile of one k split;
+// tile columns fastest, so CTAs running together share A tiles in L2).
+// Warp roles: warp 0 lane 0 issues the TMA loads of every unit through the
+// STAGES ring, warp 1 lane 0 the MMAs, warps 2..5 drain the accumulators
+// (warp w reads TMEM lanes 32 (w mod 4) .. +32).  Two accumulators of BN
+// columns: the epilogue of one unit overlaps the main loop of the next.
+// Every wait is bounded (WAIT_NS without progress, or the error flag), after
+// which the roles leave their loops, the copies in flight land, and the TMEM
+// is freed.
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_tn_p(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                int K, int ktps, int splits, Epi epi, float* __restrict__ partial, int* err) {
+  constexpr int STAGE_BYTES = Tile<BN>::STAGE_BYTES;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(sm + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;       // [2]: the MMAs of a unit are done
+  uint64_t* acc_empty = acc_full + 2;        // [2]: the epilogue has read the accumulator
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+  __shared__ volatile int s_fail;
+  __shared__ int s_issued;                   // stage loads issued, for the cleanup
+  __shared__ volatile int s_progress;        // stages consumed by the MMA issuer
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tn = (N + BN - 1) / BN, tm = (M + BM - 1) / BM;
+  const int KT = (K + BK - 1) / BK;
+  const int units = tm * tn * splits;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_issued = 0;
+    s_progress = 0;
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], 4);           // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {   // two accumulators: 128 lanes x 2 BN float32 columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
-  if (!ok && threadIdx.x == 0) {   // let the copies still in flight land before the block exits
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = *tmem_slot;
+
+  auto unit = [&](int u, int& m0, int& n0, int& kt0, int& nk, int& z) {
+    z = u / (tm * tn);
+    const int t = u - z * (tm * tn);
+    m0 = (t / tn) * BM;
+    n0 = (t % tn) * BN;
+    kt0 = z * ktps;
+    nk = min(KT, kt0 + ktps) - kt0;
+  };
+
+  if (warp == 0 && lane == 0) {   // TMA producer
+    int i = 0;
+    for (int u = blockIdx.x; u < units && !s_fail; u += gridDim.x) {
+      int m0, n0, kt0, nk, z;
+      unit(u, m0, n0, kt0, nk, z);
+      for (int k = 0; k < nk; ++k, ++i) {
+        const int q = i % STAGES;
+        if (i >= STAGES && !mbar_wait(&empty[q], ((i / STAGES) - 1) & 1, err, &s_progress)) {
+          s_fail = 1;
+          break;
+        }
+        unsigned char* a = sm + q * STAGE_BYTES;
+        mbar_expect_tx(&full[q], STAGE_BYTES);
+        tma_load_2d(a, &mapA, &full[q], (kt0 + k) * BK, m0);
+        tma_load_2d(a + A_BYTES, &mapB, &full[q], (kt0 + k) * BK, n0);
+        s_issued = i + 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {   // MMA issuer
+    const uint32_t idesc = instr_desc(BM, BN);
+    int i = 0, lt = 0;
+    for (int u = blockIdx.x; u < units && !s_fail; u += gridDim.x, ++lt) {
+      int m0, n0, kt0, nk, z;
+      unit(u, m0, n0, kt0, nk, z);
+      const int buf = lt & 1;
+      // the epilogue has drained this accumulator (its first use passes at once)
+      if (!mbar_wait(&acc_empty[buf], ((lt >> 1) & 1) ^ 1, err)) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const uint32_t acc_tm = tmem + (uint32_t)(buf * BN);
+      for (int k = 0; k < nk; ++k, ++i) {
+        const int q = i % STAGES;
+        if (!mbar_wait(&full[q], (i / STAGES) & 1, err)) {
+          s_fail = 1;
+          break;
+        }
+        s_progress = i + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const unsigned char* a = sm + q * STAGE_BYTES;
+        const uint64_t da = smem_desc(a), db = smem_desc(a + A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t step = (uint64_t)((kk * 16 * 2) >> 4);   // 32 bytes further along K
+          const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tm),
+              "l"(da + step), "l"(db + step), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&empty[q])));
+      }
+      if (s_fail) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&acc_full[buf])));
+    }
+  } else if (warp >= 2) {   // epilogue
+    const int sp = warp & 3;
+    int lt = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++lt) {
+      int m0, n0, kt0, nk, z;
+      unit(u, m0, n0, kt0, nk, z);
+      const int buf = lt & 1;
+      if (s_fail || !mbar_wait(&acc_full[buf], (lt >> 1) & 1, err, &s_progress)) {
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const int row = m0 + sp * 32 + lane;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(v, tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * BN + c0));
+        if (row < M) store_chunk(v, row, n0 + c0, z, M, N, epi, splits > 1 ? partial : nullptr);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0) {   // record the failure; let the copies in flight land
+    atomicExch(err, 1);
     const int issued = s_issued;
     for (int i = max(0, issued - STAGES); i < issued; ++i) {
-      int never = 0;   // wait on the copies themselves, whatever the error flag says
+      int never = 0;
       mbar_wait(&full[i % STAGES], (i / STAGES) & 1, &never);
     }
   }
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * BN));
 }
 
 // Sum of the split-K partials in a fixed order, then the epilogue.
@@ -642,18 +713,19 @@ cudaError_t gemm_tn(const bf16* A, int lda, const bf16* B, int ldb, int M, int N
   if (!make_map(&ma, A, M, K, lda, BM) || !make_map(&mb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
   static std::once_flag attr;
   std::call_once(attr, [] {
-    cudaFuncSetAttribute(k_gemm_tn<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<128>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_gemm_tn<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<256>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tn_p<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<128>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tn_p<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<256>::SMEM_BYTES);
   });
   const int KT = (K + BK - 1) / BK;
   int sp = plan_splits(M, N, K, splits);
   if (sp > 1 && (!work || work_floats < (size_t)sp * M * N)) sp = 1;
   const int ktps = (KT + sp - 1) / sp;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, sp);
+  const long long units = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * sp;
+  const int grid = (int)std::min<long long>(units, num_sms());
   if (BN == 256)
-    k_gemm_tn<256><<<grid, 128, Tile<256>::SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, epi, sp > 1 ? work : nullptr, err);
+    k_gemm_tn_p<256><<<grid, 192, Tile<256>::SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, sp, epi, work, err);
   else
-    k_gemm_tn<128><<<grid, 128, Tile<128>::SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, epi, sp > 1 ? work : nullptr, err);
+    k_gemm_tn_p<128><<<grid, 192, Tile<128>::SMEM_BYTES, s>>>(ma, mb, M, N, K, ktps, sp, epi, work, err);
   if (sp > 1) {
     const long long MN = (long long)M * N;
     const int blocks = (int)std::min<long long>((MN + 255) / 256, 8LL * num_sms());
