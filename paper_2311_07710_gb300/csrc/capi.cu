@@ -4,6 +4,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -22,6 +24,7 @@ struct ChunkGraph {
 struct pdqp_problem {
   Work w;
   std::string err;
+  cudaStream_t alloc_stream = nullptr;   // stream of the call that allocates (create, solve, set_lowrank_Q)
   bool mixed_ready = false;
   int last_precision = PDQP_PREC_FP64;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // solve start, setup done, loop done
@@ -50,11 +53,56 @@ struct Fail {
                  std::string(#call) + ": " + cudaGetErrorString(e_)};                \
   } while (0)
 
+// Device memory of the handles and of their build temporaries comes from a
+// library-owned stream-ordered pool per device that keeps freed blocks (no
+// release threshold), so handles of similar sizes reuse memory instead of
+// paying cudaMalloc / cudaFree, which synchronise the device.
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  CK(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = UINT64_MAX;
+  CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pools[dev] = pool;
+  return pool;
+}
+
+void* pool_alloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, lib_pool(), s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    throw Fail{PDQP_ERR_OOM, "device memory exhausted"};
+  }
+  CK(e);
+  return p;
+}
+
+// frees of a handle being destroyed (its work is done: every call that runs
+// work on it synchronises its stream before returning) go to a stream of the library
+cudaStream_t free_stream() {
+  static cudaStream_t fs = [] {
+    cudaStream_t t = nullptr;
+    cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+    return t;
+  }();
+  return fs;
+}
+
 template <typename T>
 T* dalloc(pdqp_problem* h, size_t count) {
   if (count == 0) count = 1;
-  void* p = nullptr;
-  CK(cudaMalloc(&p, count * sizeof(T)));
+  void* p = pool_alloc(count * sizeof(T), h->alloc_stream);
   h->allocs.push_back(p);
   return (T*)p;
 }
@@ -211,8 +259,8 @@ void alloc_mixed(pdqp_problem* h) {
   const int n = w.n, m = w.m;
   w.P.sval_f = dalloc<float>(h, w.P.nnz + 8);
   w.A.sval_f = dalloc<float>(h, w.A.nnz + 8);
-  CK(cudaMemset(w.P.sval_f, 0, (w.P.nnz + 8) * sizeof(float)));
-  CK(cudaMemset(w.A.sval_f, 0, (w.A.nnz + 8) * sizeof(float)));
+  CK(cudaMemsetAsync(w.P.sval_f, 0, (w.P.nnz + 8) * sizeof(float), h->alloc_stream));
+  CK(cudaMemsetAsync(w.A.sval_f, 0, (w.A.nnz + 8) * sizeof(float), h->alloc_stream));
   w.fx = dalloc<float>(h, n); w.fxbar = dalloc<float>(h, n); w.fxt = dalloc<float>(h, n);
   w.fZ[0] = dalloc<float>(h, (size_t)n + m); w.fZ[1] = dalloc<float>(h, (size_t)n + m);
   w.fybar = dalloc<float>(h, m); w.yk = dalloc<double>(h, m);
@@ -367,6 +415,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
                        double* x_out, double* y_out, pdqp_info* info, int mem, cudaStream_t s) {
   const double t0 = now_s();
   Work& w = h->w;
+  h->alloc_stream = s;   // buffers a solve adds (mixed precision, a longer step table)
   validate_options(o);
   if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
   check_space(x0, mem, "x0");
@@ -770,6 +819,7 @@ void alloc_work(pdqp_problem* h, cudaStream_t s) {
 pdqp_problem* build_problem(int count, const InstanceIn* ins, int mem, cudaStream_t s) {
   const Stack S = stack_instances(count, ins, mem, s);
   pdqp_problem* h = new pdqp_problem();
+  h->alloc_stream = s;
   try {
     begin_work(h, S.N, S.M, (int)ins[0].m_eq, count, S.insts);
     upload_stack(h, S, s);
@@ -918,6 +968,7 @@ pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, c
       I.cA0 = i * kkt_chunks(0, nbA);
     }
     h = new pdqp_problem();
+    h->alloc_stream = s;
     const long long N = count * n_t, M = count * m_t;
     begin_work(h, N, M, tw.m_eq, count, insts);
     Work& w = h->w;
@@ -1185,17 +1236,18 @@ __global__ void k_single_rows(int n, int m, int m_eq, int* __restrict__ rinst_n,
 template <typename T>
 const T* on_device(pdqp_problem* h, const T* p, size_t count, int mem, std::vector<void*>& tmp, cudaStream_t s) {
   if (mem == PDQP_MEM_DEVICE || count == 0) return p;
-  T* d = nullptr;
-  CK(cudaMalloc(&d, count * sizeof(T)));
+  T* d = (T*)pool_alloc(count * sizeof(T), s);
   tmp.push_back(d);
   CK(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
   return d;
 }
 
+// build temporaries, freed in stream order after the kernels that use them
 struct TmpFree {
   std::vector<void*> v;
+  cudaStream_t s = nullptr;
   ~TmpFree() {
-    for (void* p : v) cudaFree(p);
+    for (void* p : v) cudaFreeAsync(p, s);
   }
 };
 
@@ -1206,10 +1258,9 @@ int grid_of(long long total, int threads = 256) {
 // exclusive scan on the device: out[0..len] from in[0..len)
 void device_scan(const int* in, int len, int* out, std::vector<void*>& tmp, cudaStream_t s) {
   const int nb = std::max(1, (len + 1023) / 1024);
-  int *sums = nullptr, *total = nullptr;
-  CK(cudaMalloc(&sums, (size_t)nb * sizeof(int)));
+  int* sums = (int*)pool_alloc((size_t)nb * sizeof(int), s);
   tmp.push_back(sums);
-  CK(cudaMalloc(&total, sizeof(int)));
+  int* total = (int*)pool_alloc(sizeof(int), s);
   tmp.push_back(total);
   k_scan_blocks<<<nb, 1024, 0, s>>>(in, len, out, sums);
   k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, total);
@@ -1241,18 +1292,19 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
   if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
   if (nnzQ + nnzA > (long long)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
   TmpFree tmp;
+  tmp.s = s;
   const int* dqrp = on_device(nullptr, in.Q_rowptr, (size_t)n + 1, mem, tmp.v, s);
   const int* dqcol = on_device(nullptr, in.Q_col, (size_t)nnzQ, mem, tmp.v, s);
   const double* dqval = on_device(nullptr, in.Q_val, (size_t)nnzQ, mem, tmp.v, s);
   const int* darp = m > 0 ? on_device(nullptr, in.A_rowptr, (size_t)m + 1, mem, tmp.v, s) : nullptr;
   const int* dacol = on_device(nullptr, in.A_col, (size_t)nnzA, mem, tmp.v, s);
   const double* daval = on_device(nullptr, in.A_val, (size_t)nnzA, mem, tmp.v, s);
-  unsigned* derr = nullptr;
-  CK(cudaMalloc(&derr, sizeof(unsigned)));
+  unsigned* derr = (unsigned*)pool_alloc(sizeof(unsigned), s);
   tmp.v.push_back(derr);
   CK(cudaMemsetAsync(derr, 0, sizeof(unsigned), s));
 
   pdqp_problem* h = new pdqp_problem();
+  h->alloc_stream = s;
   try {
     Work& w = h->w;
     // vectors straight into the handle
@@ -1283,13 +1335,12 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
     if (herr & VE_BOUNDS) throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
     if (herr & VE_B) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
     // A' by column count, scan, scatter, per-column sort
-    int *cnt = nullptr, *trp = nullptr, *cur = nullptr, *tcol = nullptr;
-    double* tval = nullptr;
-    CK(cudaMalloc(&cnt, (size_t)n * sizeof(int))); tmp.v.push_back(cnt);
-    CK(cudaMalloc(&trp, ((size_t)n + 1) * sizeof(int))); tmp.v.push_back(trp);
-    CK(cudaMalloc(&cur, (size_t)n * sizeof(int))); tmp.v.push_back(cur);
-    CK(cudaMalloc(&tcol, std::max<size_t>((size_t)nnzA, 1) * sizeof(int))); tmp.v.push_back(tcol);
-    CK(cudaMalloc(&tval, std::max<size_t>((size_t)nnzA, 1) * sizeof(double))); tmp.v.push_back(tval);
+    int* cnt = (int*)pool_alloc((size_t)n * sizeof(int), s); tmp.v.push_back(cnt);
+    int* trp = (int*)pool_alloc(((size_t)n + 1) * sizeof(int), s); tmp.v.push_back(trp);
+    int* cur = (int*)pool_alloc((size_t)n * sizeof(int), s); tmp.v.push_back(cur);
+    int* tcol = (int*)pool_alloc(std::max<size_t>((size_t)nnzA, 1) * sizeof(int), s); tmp.v.push_back(tcol);
+    double* tval = (double*)pool_alloc(std::max<size_t>((size_t)nnzA, 1) * sizeof(double), s);
+    tmp.v.push_back(tval);
     CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), s));
     CK(cudaMemsetAsync(cur, 0, (size_t)n * sizeof(int), s));
     if (nnzA > 0) k_col_count<<<grid_of(nnzA), 256, 0, s>>>(dacol, nnzA, cnt);
@@ -1387,6 +1438,9 @@ pdqp_status create_common(pdqp_handle* out, int count, const InstanceIn* ins, in
   try {
     pdqp_problem* h = count == 1 ? build_single_device(ins[0], mem, s) : nullptr;
     *out = h ? h : build_problem(count, ins, mem, s);
+    // the pool allocations are stream-ordered: complete them before the handle
+    // is used on any other stream
+    CK(cudaStreamSynchronize(s));
     return PDQP_OK;
   } catch (const Fail& f) {
     g_create_error = f.msg;
@@ -1482,6 +1536,7 @@ pdqp_status pdqp_create_family(pdqp_handle* out, int32_t count, int64_t n, int64
     if (count < 1) throw Fail{PDQP_ERR_INVALID, "count must be >= 1"};
     InstanceIn base{n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, C, B, l, u};
     *out = build_family(base, count, C, B, mem, (cudaStream_t)stream);
+    CK(cudaStreamSynchronize((cudaStream_t)stream));   // complete the stream-ordered allocations
     return PDQP_OK;
   } catch (const Fail& f) {
     g_create_error = f.msg;
@@ -1496,6 +1551,7 @@ pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t
   if (!h) return PDQP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   Work& w = h->w;
+  h->alloc_stream = s;
   try {
     if (r < 1 || r > 256) throw Fail{PDQP_ERR_INVALID, "low-rank: need 1 <= r <= 256"};
     if (!F) throw Fail{PDQP_ERR_INVALID, "low-rank: null F"};
@@ -1634,7 +1690,10 @@ const char* pdqp_last_error(pdqp_handle h) { return h ? h->err.c_str() : g_creat
 
 void pdqp_destroy(pdqp_handle h) {
   if (!h) return;
-  for (void* p : h->allocs) cudaFree(p);
+  // nothing may still run on the handle's memory (cudaFree used to imply this
+  // wait); the blocks then go back to the pool without a device-wide free
+  cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFreeAsync(p, free_stream());
   if (h->w.st_host) cudaFreeHost(h->w.st_host);
   if (h->w.bst_host) cudaFreeHost(h->w.bst_host);
   for (auto& e : h->ev)
