@@ -175,19 +175,22 @@ void transpose_csr(int64_t rows, int64_t cols, const std::vector<int32_t>& rp, c
 
 // Row blocks of at most BNNZ nonzeros and BROWS rows; a longer row alone.
 std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
+  // each block is the longest run of rows from its first that holds at most
+  // BROWS rows and BNNZ nonzeros (one binary search on the nondecreasing row
+  // pointers per block); a row of more than BNNZ nonzeros is a block of its own
   std::vector<int32_t> blk{0};
   int64_t s = 0;
-  for (int64_t r = 0; r < rows; ++r) {
-    if (r > s && ((int64_t)rp[r + 1] - rp[s] > BNNZ || r - s >= BROWS)) {
-      blk.push_back((int32_t)r);
-      s = r;
+  while (s < rows) {
+    int64_t e = s + 1;
+    if ((int64_t)rp[s + 1] - rp[s] <= BNNZ) {
+      const int64_t hi = std::min<int64_t>(rows, s + BROWS);
+      e = std::upper_bound(rp.begin() + s + 1, rp.begin() + hi + 1, (int64_t)rp[s] + BNNZ,
+                           [](int64_t v, int32_t x) { return v < (int64_t)x; }) -
+          rp.begin() - 1;
     }
-    if ((int64_t)rp[r + 1] - rp[r] > BNNZ) {   // r == s here: a block of its own
-      blk.push_back((int32_t)(r + 1));
-      s = r + 1;
-    }
+    blk.push_back((int32_t)e);
+    s = e;
   }
-  if (blk.back() != rows) blk.push_back((int32_t)rows);
   return blk;
 }
 
