@@ -131,6 +131,14 @@ pdqp_status pdqp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, int32
                            int32_t ldd, int32_t splits, float *workspace, int64_t workspace_bytes, void *stream);
 pdqp_status pdqp_gemm_bf16_check(void *stream);
 
+/* Diagnostic of the failure path: runs, in one thread, the bounded wait the
+ * tensor-core kernels use on an mbarrier that nothing completes.  The wait
+ * gives up after 0.2 s without progress and raises the error flag; the call
+ * then returns what pdqp_gemm_bf16_check reads (PDQP_DEVICE_TIMEOUT, the flag
+ * cleared; PDQP_ERR_CUDA if the launch failed).  Synchronises the stream.
+ * No fault and no hang: the device stays usable. */
+pdqp_status pdqp_gemm_bf16_wait_probe(void *stream);
+
 /* The number of K splits pdqp_gemm_bf16 would use (0 on invalid sizes). */
 int32_t pdqp_gemm_bf16_splits(int32_t M, int32_t N, int32_t K, int32_t splits);
 

@@ -54,9 +54,11 @@ struct Fail {
   } while (0)
 
 // Device memory of the handles and of their build temporaries comes from a
-// library-owned stream-ordered pool per device that keeps freed blocks (no
-// release threshold), so handles of similar sizes reuse memory instead of
-// paying cudaMalloc / cudaFree, which synchronise the device.
+// library-owned stream-ordered pool per device that keeps up to POOL_KEEP bytes
+// of freed blocks (the rest goes back to the device at synchronisation points),
+// so handles of similar sizes reuse memory instead of paying cudaMalloc /
+// cudaFree, which synchronise the device.
+constexpr uint64_t POOL_KEEP = 8ULL << 30;
 cudaMemPool_t lib_pool() {
   static std::mutex mu;
   static std::map<int, cudaMemPool_t> pools;
@@ -71,7 +73,7 @@ cudaMemPool_t lib_pool() {
   props.location.id = dev;
   cudaMemPool_t pool = nullptr;
   CK(cudaMemPoolCreate(&pool, &props));
-  uint64_t keep = UINT64_MAX;
+  uint64_t keep = POOL_KEEP;
   CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
   pools[dev] = pool;
   return pool;

@@ -380,6 +380,20 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * BN));
 }
 
+// The bounded wait of the tensor-core kernels on an mbarrier that nothing
+// completes: it gives up after WAIT_NS and raises the error flag, as a GEMM
+// whose copies or MMAs never landed would (the host then reads
+// PDQP_DEVICE_TIMEOUT and the context stays usable).
+__global__ void k_wait_probe(int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, err)) atomicExch(err, 1);
+}
+
 // Sum of the split-K partials in a fixed order, then the epilogue.
 __global__ void k_splitk_epi(const float* __restrict__ part, int splits, int M, int N, Epi epi) {
   const long long MN = (long long)M * N;
@@ -1428,6 +1442,14 @@ pdqp_status pdqp_gemm_bf16_check(void* stream) {
     return PDQP_DEVICE_TIMEOUT;
   }
   return PDQP_OK;
+}
+
+pdqp_status pdqp_gemm_bf16_wait_probe(void* stream) {
+  int* err = gemm_err_ptr();
+  if (!err) return PDQP_ERR_CUDA;
+  k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(err);
+  if (cudaGetLastError() != cudaSuccess) return PDQP_ERR_CUDA;
+  return pdqp_gemm_bf16_check(stream);
 }
 
 int32_t pdqp_gemm_bf16_splits(int32_t M, int32_t N, int32_t K, int32_t splits) {

@@ -118,6 +118,7 @@ SIGNATURES = {
                                       ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
                                       ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P]),
     "pdqp_gemm_bf16_check": (ctypes.c_int, [_P]),
+    "pdqp_gemm_bf16_wait_probe": (ctypes.c_int, [_P]),
     "pdqp_gemm_bf16_splits": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
 }
 
@@ -544,6 +545,11 @@ def pdqp_gemm_bf16(A, B, bias=None, relu=False, mask=None, D_f32=None, D_bf16=No
 
 def pdqp_gemm_bf16_check(stream=None):
     return int(load().pdqp_gemm_bf16_check(_stream(stream)))
+
+
+def pdqp_gemm_bf16_wait_probe(stream=None):
+    """Status of a bounded device wait that runs out (PDQP_DEVICE_TIMEOUT)."""
+    return int(load().pdqp_gemm_bf16_wait_probe(_stream(stream)))
 
 
 def pdqp_gemm_bf16_splits(M, N, K, splits=0):

@@ -137,3 +137,28 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(pd.PdqpError):
         pd.pdqp_gemm_bf16(Ah, B, D_f32=D, K=16)
     assert pd.pdqp_gemm_bf16_check() == 0
+
+
+def test_a_wait_that_runs_out_reports_device_timeout_and_the_device_stays_usable():
+    """The failure path of the tensor-core kernels, made safely: their bounded
+    wait on an mbarrier that nothing completes gives up after 0.2 s, the host
+    reads PDQP_DEVICE_TIMEOUT, the flag is cleared and the next GEMM is right."""
+    import time
+
+    import torch
+    pd = lib()
+    t = time.perf_counter()
+    st = pd.pdqp_gemm_bf16_wait_probe()
+    dt = time.perf_counter() - t
+    assert st == pd.PDQP_DEVICE_TIMEOUT
+    assert 0.15 <= dt < 10.0
+    assert pd.pdqp_gemm_bf16_check() == pd.PDQP_OK
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(256, 128, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(256, 128, device="cuda", generator=g).to(torch.bfloat16)
+    D = torch.zeros(256, 256, dtype=torch.float32, device="cuda")
+    pd.pdqp_gemm_bf16(A, B, D_f32=D)
+    assert pd.pdqp_gemm_bf16_check() == pd.PDQP_OK
+    ref = A.double() @ B.double().T
+    bound = 4 * 128 * 2.0 ** -24 * (A.double().abs() @ B.double().abs().T)
+    assert bool(((D.double() - ref).abs() <= bound + 1e-30).all())
