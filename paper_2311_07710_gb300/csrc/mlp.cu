@@ -223,7 +223,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
 // D = A B' (bf16 A, B K-major, float32 accumulation in tensor memory), persistent:
 // one CTA per SM takes work units u = blockIdx.x,
 // blockIdx.x + gridDim.x, ... (a unit is one BM x BN tile of one k split;
-// tile columns fastest, so CTAs running together share A tiles in L2).
+// the tiles in bands of tile rows, see `unit`).
 // Warp roles: warp 0 lane 0 issues the TMA loads of every unit through the
 // STAGES ring, warp 1 lane 0 the MMAs, warps 2..5 drain the accumulators
 // (warp w reads TMEM lanes 32 (w mod 4) .. +32).  Two accumulators of BN
@@ -275,11 +275,18 @@ __global__ void __launch_bounds__(192, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = *tmem_slot;
 
+  // tiles in bands of GROUP tile rows, column-major inside a band: the CTAs
+  // running together cover about GROUP rows of A and gridDim / GROUP columns of
+  // B tiles, a working set that stays in L2
+  constexpr int GROUP = 8;
   auto unit = [&](int u, int& m0, int& n0, int& kt0, int& nk, int& z) {
     z = u / (tm * tn);
     const int t = u - z * (tm * tn);
-    m0 = (t / tn) * BM;
-    n0 = (t % tn) * BN;
+    const int band = t / (GROUP * tn), first = band * GROUP;
+    const int rows = min(tm - first, GROUP);
+    const int q = t - band * GROUP * tn;
+    m0 = (first + q % rows) * BM;
+    n0 = (q / rows) * BN;
     kt0 = z * ktps;
     nk = min(KT, kt0 + ktps) - kt0;
   };
