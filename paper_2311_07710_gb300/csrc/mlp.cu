@@ -13,16 +13,18 @@
 // and Adam moments are float32.
 //
 // GEMM: D[M x N] = A[M x K] * B[N x K]^T with A and B row-major bfloat16 (both
-// K-major).  One CUDA block computes a 128 x 128 tile: thread 0 of warp 0
-// streams 128 x 64 tiles of A and B into a 4-stage shared-memory ring with TMA
-// (128-byte swizzle), thread 0 of warp 1 issues tcgen05.mma (M=128, N=128,
-// K=16, kind::f16 with bf16 A and B) on each stage and releases it with
-// tcgen05.commit, and after the last stage the four warps read the
-// accumulator with tcgen05.ld (warp w owns rows 32w..32w+31 = TMEM lanes).
-// Split-K: blockIdx.z takes a range of k-tiles and writes raw float32
+// K-major), persistent: one CUDA block per SM walks 128 x 256 tiles (128 x 128
+// when N < 256) and k splits.  Thread 0 of warp 0 streams 64-wide K slices of
+// A and B into a 4-stage shared-memory ring with TMA (128-byte swizzle),
+// thread 0 of warp 1 issues tcgen05.mma (M=128, N=256, K=16, kind::f16 with
+// bf16 A and B) on each stage into one of two float32 accumulators in tensor
+// memory and releases the stage with tcgen05.commit, and warps 2..5 drain the
+// other accumulator with tcgen05.ld into the fused epilogue (warp w reads TMEM
+// lanes 32 (w mod 4) .. +32), so a tile's epilogue overlaps the next tile's
+// main loop.  Split-K: a unit takes a range of k slices and writes raw float32
 // partials that a second kernel sums in a fixed order.  Every mbarrier wait is
-// bounded; a wait that gives up sets the error flag, waits (bounded) for the
-// copies still in flight, frees the tensor memory and returns.
+// bounded; a wait that gives up sets the error flag, the roles leave their
+// loops, the copies still in flight land (bounded), the tensor memory is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
