@@ -369,10 +369,11 @@ cudaGraphExec_t capture_iterations(pdqp_problem* h, int len, bool mixed, int nt,
   Work& w = h->w;
   if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  const long long before = pdqp::g_launches;
+  pdqp::t_capturing = true;    // captured, not launched
+  pdqp::t_captured = 0;
   pdqp::iterate_chunk(w, len, mixed, nt, h->cap, j0);
-  *kernels = pdqp::g_launches - before;
-  pdqp::g_launches = before;   // captured, not launched
+  pdqp::t_capturing = false;
+  *kernels = pdqp::t_captured;
   cudaGraph_t graph = nullptr;
   CK(cudaStreamEndCapture(h->cap, &graph));
   cudaGraphExec_t exec = nullptr;
@@ -390,11 +391,12 @@ void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaS
     g.valid = false;
     if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    const long long before = pdqp::g_launches;
+    pdqp::t_capturing = true;    // captured, not launched
+    pdqp::t_captured = 0;
     pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap);
     pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
-    g.kernels = pdqp::g_launches - before;
-    pdqp::g_launches = before;   // captured, not launched
+    pdqp::t_capturing = false;
+    g.kernels = pdqp::t_captured;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamEndCapture(h->cap, &graph));
     const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
@@ -1710,7 +1712,7 @@ void pdqp_destroy(pdqp_handle h) {
   delete h;
 }
 
-int64_t pdqp_launch_count(void) { return pdqp::g_launches; }
+int64_t pdqp_launch_count(void) { return pdqp::g_launches.load(std::memory_order_relaxed); }
 
 pdqp_status pdqp_profile_enable(pdqp_handle h, int32_t on) {
   if (!h) return PDQP_ERR_INVALID;

@@ -10,6 +10,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "rowblock.cuh"
 
@@ -476,26 +477,23 @@ __global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __
   }
 }
 
+// resident blocks per SM of a pipelined kernel (its shared-memory limit set
+// once; a function-local static is initialised once, thread-safely)
+template <typename K>
+static int pipe_blocks(K kern, int nt, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
+  return per_sm > 0 ? per_sm : 1;
+}
 template <typename V, int NT>
 static int pipe_grid(void (*kern)(DualB<V>, const int4*, int, int)) {
-  static int blocks = -1;
-  if (blocks < 0) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
-    blocks = per_sm > 0 ? per_sm : 1;
-  }
+  static const int blocks = pipe_blocks(kern, NT, sizeof(PipeSmem<V>));
   return blocks;
 }
 template <typename V, int NT>
 static int pipe_grid_p(void (*kern)(PrimalB<V>, const int4*, int, int)) {
-  static int blocks = -1;
-  if (blocks < 0) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<V>));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sizeof(PipeSmem<V>));
-    blocks = per_sm > 0 ? per_sm : 1;
-  }
+  static const int blocks = pipe_blocks(kern, NT, sizeof(PipeSmem<V>));
   return blocks;
 }
 
@@ -611,14 +609,14 @@ static int chunk_cluster_size() {
 }
 
 void prepare_chunk_cluster() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_chunk_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, CHUNK_SMEM_MAX);
-  cudaFuncSetAttribute(k_chunk_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CHUNK_SMEM_MAX);
-  cudaFuncSetAttribute(k_chunk_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaFuncSetAttribute(k_chunk_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  g_chunk_ctas = std::min(chunk_cluster_size<float>(), chunk_cluster_size<double>());
-  done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_chunk_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, CHUNK_SMEM_MAX);
+    cudaFuncSetAttribute(k_chunk_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CHUNK_SMEM_MAX);
+    cudaFuncSetAttribute(k_chunk_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_chunk_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    g_chunk_ctas = std::min(chunk_cluster_size<float>(), chunk_cluster_size<double>());
+  });
 }
 
 template <typename V>
@@ -645,7 +643,7 @@ static void run_chunk_cluster(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V*
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_chunk_cluster<V>, da, pa, w.m > 0 ? w.A.nblk : 0, w.P.nblk, Z[0], Z[1], w.n, w.m, j0,
                      len);
-  ++g_launches;
+  count_launch();
   if (Pr.on) Pr.end(s);
 }
 

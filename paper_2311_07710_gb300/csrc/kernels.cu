@@ -14,12 +14,15 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "rowblock.cuh"
 
 namespace pdqp {
 
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
+thread_local bool t_capturing = false;
+thread_local long long t_captured = 0;
 
 static int pick_lanes(long long nnz, long long rows) {
   const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
@@ -531,13 +534,12 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
 // launch both relKKT kernels with their dynamic shared memory
 template <int NIT>
 static void launch_kkt(const Work& w, const KktB& a, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_kkt_m<NIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
     cudaFuncSetAttribute(k_kkt_n<NIT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
     cudaFuncSetAttribute(k_kkt_n<NIT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
-    attr = true;
-  }
+  });
   if (w.m > 0) launch(k_kkt_m<NIT>, w.A.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
   if (a.F) launch(k_kkt_n<NIT, true>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
   else launch(k_kkt_n<NIT, false>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);

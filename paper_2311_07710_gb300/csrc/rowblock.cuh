@@ -14,13 +14,13 @@ static inline void launch(void (*kern)(KArgs...), int grid, int block, size_t sm
                           Args... args) {
   if (grid <= 0) return;
   kern<<<grid, block, smem, s>>>(args...);
-  ++g_launches;
+  count_launch();
 }
 template <typename... KArgs, typename... Args>
 static inline void launch(void (*kern)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args... args) {
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
   kern<<<grid, block, smem, s>>>(args...);
-  ++g_launches;
+  count_launch();
 }
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }

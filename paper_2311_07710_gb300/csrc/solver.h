@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -140,7 +141,15 @@ struct Work {
 
 namespace pdqp {
 
-extern long long g_launches;
+// Kernels the library launched (a graph replay counts the kernels it holds).
+// A thread capturing a graph counts its launches in t_captured instead.
+extern std::atomic<long long> g_launches;
+extern thread_local bool t_capturing;
+extern thread_local long long t_captured;
+inline void count_launch() {
+  if (t_capturing) ++t_captured;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 // setup
 void scale_pass(Work& w, int kind, cudaStream_t s);          // kind: 0 inf, 1 l2, 2 l1
