@@ -4,9 +4,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <atomic>
+#include <climits>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pdqp.h"
@@ -616,127 +619,211 @@ struct Stack {
   std::vector<Inst> insts;
 };
 
-// Validate every instance and stack them block-diagonally.
+// One instance's rows of P = [Q | -A'] and of A with global column indices,
+// its row pointers and P's split from 0, its row blocks in local rows.
+struct Piece {
+  std::vector<int32_t> prp, pcol, psplit, arp, acol, pbl, abl;
+  std::vector<double> pval, aval, c, l, u, b;
+};
+
+// Validate and assemble instance i (its first variable xoff, first row yoff,
+// N variables in the whole stack); throws Fail.
+Piece make_piece(const InstanceIn& in, int64_t xoff, int64_t yoff, int64_t N, int mem, cudaStream_t s) {
+  const int64_t n = in.n, m = in.m;
+  for (auto pr : {(const void*)in.Q_rowptr, (const void*)in.Q_col, (const void*)in.Q_val,
+                  (const void*)in.A_rowptr, (const void*)in.A_col, (const void*)in.A_val, (const void*)in.c,
+                  (const void*)in.b, (const void*)in.l, (const void*)in.u})
+    check_space(pr, mem, "input array");
+  std::vector<int32_t> qrp = fetch(in.Q_rowptr, n + 1, mem, s);
+  const int64_t nnzQ = qrp[n];
+  if (nnzQ < 0 || (nnzQ > 0 && (!in.Q_col || !in.Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
+  std::vector<int32_t> qcol = fetch(in.Q_col, nnzQ, mem, s);
+  std::vector<double> qval = fetch(in.Q_val, nnzQ, mem, s);
+  Piece P;
+  std::vector<int32_t> icol;
+  std::vector<double> ival;
+  P.arp.assign(m + 1, 0);
+  if (m > 0) {
+    P.arp = fetch(in.A_rowptr, m + 1, mem, s);
+    const int64_t nnzA = P.arp[m];
+    if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
+    icol = fetch(in.A_col, nnzA, mem, s);
+    ival = fetch(in.A_val, nnzA, mem, s);
+  }
+  P.c = fetch(in.c, n, mem, s);
+  P.l = fetch(in.l, n, mem, s);
+  P.u = fetch(in.u, n, mem, s);
+  if (m > 0) P.b = fetch(in.b, m, mem, s);
+  validate_csr("Q", n, n, qrp, qcol, qval);
+  validate_csr("A", m, n, P.arp, icol, ival);
+  for (int64_t j = 0; j < n; ++j) {
+    if (!std::isfinite(P.c[j])) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
+    if (std::isnan(P.l[j]) || std::isnan(P.u[j]) || P.l[j] > P.u[j] || P.l[j] == INFINITY || P.u[j] == -INFINITY)
+      throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
+  }
+  for (int64_t r = 0; r < m; ++r)
+    if (!std::isfinite(P.b[r])) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
+  std::vector<int32_t> trp, tcol;
+  std::vector<double> tval;
+  if (m > 0) transpose_csr(m, n, P.arp, icol, ival, trp, tcol, tval);
+  else trp.assign(n + 1, 0);
+  // rows of P = [Q | -A'] with global columns: x part xoff + j, y part N + yoff + r
+  const size_t nnzP = (size_t)nnzQ + tcol.size();
+  if (nnzP > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
+  P.pcol.resize(nnzP);
+  P.pval.resize(nnzP);
+  P.prp.resize(n + 1);
+  P.psplit.resize(n);
+  P.prp[0] = 0;
+  size_t e = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k, ++e) {
+      P.pcol[e] = (int32_t)(xoff + qcol[k]);
+      P.pval[e] = qval[k];
+    }
+    P.psplit[j] = (int32_t)e;
+    for (int32_t k = trp[j]; k < trp[j + 1]; ++k, ++e) {
+      P.pcol[e] = (int32_t)(N + yoff + tcol[k]);
+      P.pval[e] = -tval[k];
+    }
+    P.prp[j + 1] = (int32_t)e;
+  }
+  P.acol.resize(icol.size());
+  for (size_t k = 0; k < icol.size(); ++k) P.acol[k] = (int32_t)(xoff + icol[k]);
+  P.aval = std::move(ival);
+  P.pbl = row_blocks(n, P.prp);
+  P.abl = m > 0 ? row_blocks(m, P.arp) : std::vector<int32_t>{0};
+  return P;
+}
+
+// Run fn(i) for i in [0, count) on up to 16 host threads; the Fail of the
+// lowest failing i is rethrown (as a sequential loop would throw it).
+template <class Fn>
+void parallel_instances(int count, Fn fn) {
+  const int nt = std::max(1, std::min<int>({count, 16, (int)std::max(1u, std::thread::hardware_concurrency())}));
+  std::atomic<int> next{0};
+  std::mutex mu;
+  int fail_i = INT_MAX;
+  Fail fail{PDQP_OK, ""};
+  bool other = false;
+  auto body = [&] {
+    for (int i; (i = next.fetch_add(1)) < count;) {
+      try {
+        fn(i);
+      } catch (const Fail& f) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (i < fail_i) { fail_i = i; fail = f; }
+      } catch (...) {
+        std::lock_guard<std::mutex> lock(mu);
+        other = true;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(body);
+  body();
+  for (auto& t : pool) t.join();
+  if (fail_i != INT_MAX) throw fail;
+  if (other) throw std::bad_alloc();
+}
+
+// Validate every instance and stack them block-diagonally: the instances are
+// assembled in parallel, then copied into place after a prefix over sizes.
 Stack stack_instances(int count, const InstanceIn* ins, int mem, cudaStream_t s) {
   if (count < 1) throw Fail{PDQP_ERR_INVALID, "count must be >= 1"};
   if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
   Stack S;
   S.count = count;
   int64_t N = 0, M = 0;
+  std::vector<int64_t> xoff(count), yoff(count);
   for (int i = 0; i < count; ++i) {
     const InstanceIn& in = ins[i];
     if (in.n < 1 || in.m < 0 || in.m_eq < 0 || in.m_eq > in.m)
       throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
     if (!in.Q_rowptr || !in.c || !in.l || !in.u) throw Fail{PDQP_ERR_INVALID, "null Q_rowptr, c, l or u"};
     if (in.m > 0 && (!in.A_rowptr || !in.b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
+    xoff[i] = N;
+    yoff[i] = M;
     N += in.n;
     M += in.m;
   }
   if (N > (1LL << 30) || M > (1LL << 30)) throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
   S.N = N;
   S.M = M;
+  std::vector<Piece> pieces(count);
+  parallel_instances(count, [&](int i) { pieces[i] = make_piece(ins[i], xoff[i], yoff[i], N, mem, s); });
+  // offsets of every instance's nonzeros and row blocks; the instances' records
+  std::vector<int64_t> pe(count + 1, 0), ae(count + 1, 0);
+  std::vector<int> pb(count + 1, 0), ab(count + 1, 0);
   S.insts.resize(count);
-  int64_t xoff = 0, yoff = 0;
   for (int i = 0; i < count; ++i) {
-    const InstanceIn& in = ins[i];
-    const int64_t n = in.n, m = in.m;
-    for (auto pr : {(const void*)in.Q_rowptr, (const void*)in.Q_col, (const void*)in.Q_val,
-                    (const void*)in.A_rowptr, (const void*)in.A_col, (const void*)in.A_val, (const void*)in.c,
-                    (const void*)in.b, (const void*)in.l, (const void*)in.u})
-      check_space(pr, mem, "input array");
-    std::vector<int32_t> qrp = fetch(in.Q_rowptr, n + 1, mem, s);
-    const int64_t nnzQ = qrp[n];
-    if (nnzQ < 0 || (nnzQ > 0 && (!in.Q_col || !in.Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
-    std::vector<int32_t> qcol = fetch(in.Q_col, nnzQ, mem, s);
-    std::vector<double> qval = fetch(in.Q_val, nnzQ, mem, s);
-    std::vector<int32_t> irp(m + 1, 0), icol;
-    std::vector<double> ival;
-    if (m > 0) {
-      irp = fetch(in.A_rowptr, m + 1, mem, s);
-      const int64_t nnzA = irp[m];
-      if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
-      icol = fetch(in.A_col, nnzA, mem, s);
-      ival = fetch(in.A_val, nnzA, mem, s);
-    }
-    std::vector<double> c = fetch(in.c, n, mem, s), l = fetch(in.l, n, mem, s), u = fetch(in.u, n, mem, s);
-    std::vector<double> b = m > 0 ? fetch(in.b, m, mem, s) : std::vector<double>();
-    validate_csr("Q", n, n, qrp, qcol, qval);
-    validate_csr("A", m, n, irp, icol, ival);
-    for (int64_t j = 0; j < n; ++j) {
-      if (!std::isfinite(c[j])) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
-      if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
-        throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
-    }
-    for (int64_t r = 0; r < m; ++r)
-      if (!std::isfinite(b[r])) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
-    std::vector<int32_t> trp, tcol;
-    std::vector<double> tval;
-    if (m > 0) transpose_csr(m, n, irp, icol, ival, trp, tcol, tval);
-    else trp.assign(n + 1, 0);
-    // rows of P = [Q | -A'] with global columns: x part xoff + j, y part N + yoff + r
-    for (int64_t j = 0; j < n; ++j) {
-      for (int32_t k = qrp[j]; k < qrp[j + 1]; ++k) {
-        S.pcol.push_back((int32_t)(xoff + qcol[k]));
-        S.pval.push_back(qval[k]);
-      }
-      S.psplit.push_back((int32_t)S.pcol.size());
-      for (int32_t k = trp[j]; k < trp[j + 1]; ++k) {
-        S.pcol.push_back((int32_t)(N + yoff + tcol[k]));
-        S.pval.push_back(-tval[k]);
-      }
-      if (S.pcol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
-      S.prp.push_back((int32_t)S.pcol.size());
-    }
-    for (int64_t r = 0; r < m; ++r) {
-      for (int32_t k = irp[r]; k < irp[r + 1]; ++k) {
-        S.acol.push_back((int32_t)(xoff + icol[k]));
-        S.aval.push_back(ival[k]);
-      }
-      if (S.acol.size() > (size_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(A) exceeds 2^31"};
-      S.arp.push_back((int32_t)S.acol.size());
-    }
-    // row blocks of this instance, offset to global rows
+    const Piece& P = pieces[i];
+    pe[i + 1] = pe[i] + (int64_t)P.pcol.size();
+    ae[i + 1] = ae[i] + (int64_t)P.acol.size();
+    pb[i + 1] = pb[i] + (int)P.pbl.size() - 1;
+    ab[i + 1] = ab[i] + (int)P.abl.size() - 1;
     Inst& I = S.insts[i];
-    I.n = (int)n;
-    I.m = (int)m;
-    I.m_eq = (int)in.m_eq;
-    I.xoff = (int)xoff;
-    I.yoff = (int)yoff;
-    {
-      std::vector<int32_t> lp(S.prp.end() - (n + 1), S.prp.end());
-      const int32_t base = lp[0];
-      for (auto& v : lp) v -= base;
-      const std::vector<int32_t> bl = row_blocks(n, lp);
-      I.bP0 = (int)S.pblk.size() - 1;
-      for (size_t q = 1; q < bl.size(); ++q) {
-        S.pblk.push_back((int32_t)(xoff + bl[q]));
-        S.binst_p.push_back(i);
-      }
-      I.bP1 = (int)S.pblk.size() - 1;
-    }
-    {
-      I.bA0 = (int)S.ablk.size() - 1;
-      if (m > 0) {
-        const std::vector<int32_t> bl = row_blocks(m, irp);
-        for (size_t q = 1; q < bl.size(); ++q) {
-          S.ablk.push_back((int32_t)(yoff + bl[q]));
-          S.binst_a.push_back(i);
-        }
-      }
-      I.bA1 = (int)S.ablk.size() - 1;
-    }
+    I.n = (int)ins[i].n;
+    I.m = (int)ins[i].m;
+    I.m_eq = (int)ins[i].m_eq;
+    I.xoff = (int)xoff[i];
+    I.yoff = (int)yoff[i];
+    I.bP0 = pb[i];
+    I.bP1 = pb[i + 1];
+    I.bA0 = ab[i];
+    I.bA1 = ab[i + 1];
     I.cP0 = i == 0 ? 0 : S.insts[i - 1].cP0 + kkt_chunks(S.insts[i - 1].bP0, S.insts[i - 1].bP1);
     I.cA0 = i == 0 ? 0 : S.insts[i - 1].cA0 + kkt_chunks(S.insts[i - 1].bA0, S.insts[i - 1].bA1);
-    S.hc.insert(S.hc.end(), c.begin(), c.end());
-    S.hl.insert(S.hl.end(), l.begin(), l.end());
-    S.hu.insert(S.hu.end(), u.begin(), u.end());
-    S.hb.insert(S.hb.end(), b.begin(), b.end());
-    S.rinst_n.insert(S.rinst_n.end(), (size_t)n, i);
-    S.rinst_m.insert(S.rinst_m.end(), (size_t)m, i);
-    for (int64_t r = 0; r < m; ++r) S.ineq.push_back(r >= in.m_eq ? 1 : 0);
-    xoff += n;
-    yoff += m;
   }
+  if (pe[count] > (int64_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
+  if (ae[count] > (int64_t)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(A) exceeds 2^31"};
+  S.prp.assign(N + 1, 0);
+  S.psplit.resize(N);
+  S.pcol.resize(pe[count]);
+  S.pval.resize(pe[count]);
+  S.arp.assign(M + 1, 0);
+  S.acol.resize(ae[count]);
+  S.aval.resize(ae[count]);
+  S.pblk.assign(pb[count] + 1, 0);
+  S.binst_p.resize(pb[count]);
+  S.ablk.assign(ab[count] + 1, 0);
+  S.binst_a.resize(ab[count]);
+  S.hc.resize(N);
+  S.hl.resize(N);
+  S.hu.resize(N);
+  S.hb.resize(M);
+  S.rinst_n.resize(N);
+  S.rinst_m.resize(M);
+  S.ineq.resize(M);
+  parallel_instances(count, [&](int i) {
+    Piece& P = pieces[i];
+    const int64_t x0 = xoff[i], y0 = yoff[i], n = ins[i].n, m = ins[i].m;
+    for (int64_t j = 0; j < n; ++j) {
+      S.prp[x0 + j + 1] = (int32_t)(pe[i] + P.prp[j + 1]);
+      S.psplit[x0 + j] = (int32_t)(pe[i] + P.psplit[j]);
+    }
+    std::copy(P.pcol.begin(), P.pcol.end(), S.pcol.begin() + pe[i]);
+    std::copy(P.pval.begin(), P.pval.end(), S.pval.begin() + pe[i]);
+    for (int64_t r = 0; r < m; ++r) S.arp[y0 + r + 1] = (int32_t)(ae[i] + P.arp[r + 1]);
+    std::copy(P.acol.begin(), P.acol.end(), S.acol.begin() + ae[i]);
+    std::copy(P.aval.begin(), P.aval.end(), S.aval.begin() + ae[i]);
+    for (size_t q = 1; q < P.pbl.size(); ++q) {
+      S.pblk[pb[i] + q] = (int32_t)(x0 + P.pbl[q]);
+      S.binst_p[pb[i] + q - 1] = i;
+    }
+    for (size_t q = 1; q < P.abl.size(); ++q) {
+      S.ablk[ab[i] + q] = (int32_t)(y0 + P.abl[q]);
+      S.binst_a[ab[i] + q - 1] = i;
+    }
+    std::copy(P.c.begin(), P.c.end(), S.hc.begin() + x0);
+    std::copy(P.l.begin(), P.l.end(), S.hl.begin() + x0);
+    std::copy(P.u.begin(), P.u.end(), S.hu.begin() + x0);
+    std::copy(P.b.begin(), P.b.end(), S.hb.begin() + y0);
+    std::fill(S.rinst_n.begin() + x0, S.rinst_n.begin() + x0 + n, i);
+    std::fill(S.rinst_m.begin() + y0, S.rinst_m.begin() + y0 + m, i);
+    for (int64_t r = 0; r < m; ++r) S.ineq[y0 + r] = r >= ins[i].m_eq ? 1 : 0;
+    P = Piece();   // free the piece as soon as it is placed
+  });
   return S;
 }
 
