@@ -334,20 +334,27 @@ def run_ours(args, world, rank, local):
 
     # ---- end-to-end leg: host buffers, H2D + solve + D2H inside the timed region ----
     # the inputs and outputs live in pinned host memory (filled before the timed region)
-    host_sets = [[pinned_copy(a) for a in (i.Q.indptr, i.Q.indices, i.Q.data, i.A.indptr, i.A.indices, i.A.data,
-                                           i.c, i.b, i.l, i.u)] for i in insts]
+    # (a batch as one block-diagonal problem: ten arrays, stacked on the device)
+    if len(insts) == 1:
+        host_sets = [[pinned_copy(a) for a in (inst.Q.indptr, inst.Q.indices, inst.Q.data, inst.A.indptr,
+                                               inst.A.indices, inst.A.data, inst.c, inst.b, inst.l, inst.u)]]
+    else:
+        pk = pdqp.pack_instances(insts)
+        host_sets = [[pinned_copy(pk[k]) for k in ("Q_rowptr", "Q_col", "Q_val", "A_rowptr", "A_col", "A_val",
+                                                   "c", "b", "l", "u")]]
     h2d = int(sum(a.nbytes for s in host_sets for a in s))
     xh, yh = pinned_copy(np.zeros(N)), pinned_copy(np.zeros(M))
     d2h = xh.nbytes + yh.nbytes
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
+    e2e_status = 0
     for _ in range(args.e2e_steps):
         if len(insts) == 1:
             he = pdqp.pdqp_create(inst.n, inst.m, inst.m_eq, *host_sets[0], stream=stream)
         else:
-            he = pdqp.pdqp_create_batch([(i.n, i.m, i.m_eq, *s) for i, s in zip(insts, host_sets)], stream=stream)
-        pdqp.pdqp_solve(he, opts, x_out=xh, y_out=yh, stream=stream)
+            he = pdqp.pdqp_create_batch_packed(pk["n"], pk["m"], pk["m_eq"], *host_sets[0], stream=stream)
+        e2e_status = max(e2e_status, pdqp.pdqp_solve(he, opts, x_out=xh, y_out=yh, stream=stream)[0])
         pdqp.pdqp_destroy(he)
     torch.cuda.synchronize(dev)
     e2e_s = allreduce_max(time.perf_counter() - t0, world, dev)
@@ -406,7 +413,9 @@ def run_ours(args, world, rank, local):
             "setup_ms": 1e3 * infos[-1].setup_seconds, "iterate_ms": 1e3 * infos[-1].iterate_seconds,
             "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
             "roofline": roof,
-            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "calls": ("pdqp_create" if len(insts) == 1 else "pdqp_create_batch_packed")
+                    + " + pdqp_solve + pdqp_destroy, pinned host arrays", "worst_status": e2e_status},
             "gpu_launches": launches, "clocks": clk}
     if fp64_side is not None:
         line["plain_fp64"] = fp64_side
@@ -550,10 +559,12 @@ def run_family_ws(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
+    e2e_status = 0
     for _ in range(args.e2e_steps):
         he = pdqp.family_from_base(pbase, Cp, Bp, stream=stream)
         pdqp.pdqp_ws_infer(w, Cp, Bp, X0h, Y0h, stream=stream)
-        pdqp.pdqp_solve(he, opts, x0=X0h.reshape(-1), y0=Y0h.reshape(-1), x_out=xh, y_out=yh, stream=stream)
+        e2e_status = max(e2e_status, pdqp.pdqp_solve(he, opts, x0=X0h.reshape(-1), y0=Y0h.reshape(-1), x_out=xh,
+                                                     y_out=yh, stream=stream)[0])
         pdqp.pdqp_destroy(he)
     torch.cuda.synchronize(dev)
     e2e_s = allreduce_max(time.perf_counter() - t0, world, dev)
@@ -595,7 +606,7 @@ def run_family_ws(args, world, rank, local):
             "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(xh.nbytes + yh.nbytes)},
+                    "d2h_bytes_per_step": int(xh.nbytes + yh.nbytes), "worst_status": e2e_status},
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)

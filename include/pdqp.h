@@ -178,6 +178,30 @@ pdqp_status pdqp_create_batch(pdqp_handle *out, int32_t count, const int64_t *n,
                               const double *const *b, const double *const *l, const double *const *u,
                               int32_t mem_space, void *stream);
 
+/* The handle pdqp_create_batch builds from the same instances (same stacking,
+ * row blocks and results), from the batch handed over as one block-diagonal
+ * problem: with x_i = n[0] + ... + n[i-1] and y_i = m[0] + ... + m[i-1],
+ * instance i owns the variables [x_i, x_i + n[i]) and the rows
+ * [y_i, y_i + m[i]) of the stack (N = sum n, M = sum m variables and rows).
+ * n, m, m_eq: host arrays of `count` entries, as for pdqp_create_batch.
+ * Q_*: CSR of the stacked Q, N rows; A_*: CSR of the stacked A, M rows (may be
+ * NULL when M = 0); both with global column indices (the block-diagonal
+ * matrix of the instances' matrices), each row's columns inside its own
+ * instance's variables.  c, l, u: float64[N]; b: float64[M]; the instances'
+ * vectors concatenated.  All ten arrays live in `mem_space`; the library
+ * copies them.  Validation, the transpose of A and the stacking run on the
+ * device; the host reads only the row pointers (to form the row blocks), so
+ * the host cost of a call does not grow with the number of nonzeros.  A
+ * column of A with more than 4096 nonzeros sends the call to the host
+ * stacking of pdqp_create_batch (same handle).  PDQP_ERR_INVALID with
+ * *out = NULL on malformed input, a nonzero outside its row's instance
+ * included. */
+pdqp_status pdqp_create_batch_packed(pdqp_handle *out, int32_t count, const int64_t *n, const int64_t *m,
+                                     const int64_t *m_eq, const int32_t *Q_rowptr, const int32_t *Q_col,
+                                     const double *Q_val, const int32_t *A_rowptr, const int32_t *A_col,
+                                     const double *A_val, const double *c, const double *b, const double *l,
+                                     const double *u, int32_t mem_space, void *stream);
+
 /* Number of instances of a handle (1 for pdqp_create). */
 int32_t pdqp_batch_count(pdqp_handle h);
 

@@ -178,17 +178,17 @@ void transpose_csr(int64_t rows, int64_t cols, const std::vector<int32_t>& rp, c
     }
 }
 
-// Row blocks of at most BNNZ nonzeros and BROWS rows; a longer row alone.
-std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
-  // each block is the longest run of rows from its first that holds at most
-  // BROWS rows and BNNZ nonzeros (one binary search on the nondecreasing row
-  // pointers per block); a row of more than BNNZ nonzeros is a block of its own
-  std::vector<int32_t> blk{0};
-  int64_t s = 0;
-  while (s < rows) {
+// Blocks of rows [r0, r1), their ends appended to blk: each block is the
+// longest run of rows from its first that holds at most BROWS rows and BNNZ
+// nonzeros (one binary search on the nondecreasing row pointers per block); a
+// row of more than BNNZ nonzeros is a block of its own.  Only differences of
+// row pointers enter, so a block's rows do not depend on where rp starts.
+void append_row_blocks(int64_t r0, int64_t r1, const std::vector<int32_t>& rp, std::vector<int32_t>& blk) {
+  int64_t s = r0;
+  while (s < r1) {
     int64_t e = s + 1;
     if ((int64_t)rp[s + 1] - rp[s] <= BNNZ) {
-      const int64_t hi = std::min<int64_t>(rows, s + BROWS);
+      const int64_t hi = std::min<int64_t>(r1, s + BROWS);
       e = std::upper_bound(rp.begin() + s + 1, rp.begin() + hi + 1, (int64_t)rp[s] + BNNZ,
                            [](int64_t v, int32_t x) { return v < (int64_t)x; }) -
           rp.begin() - 1;
@@ -196,6 +196,12 @@ std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
     blk.push_back((int32_t)e);
     s = e;
   }
+}
+
+// Row blocks of rows [0, rows), starting with 0.
+std::vector<int32_t> row_blocks(int64_t rows, const std::vector<int32_t>& rp) {
+  std::vector<int32_t> blk{0};
+  append_row_blocks(0, rows, rp, blk);
   return blk;
 }
 
@@ -598,14 +604,35 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
 }
 
 // One instance as given by the caller (host or device pointers per mem_space).
+// rebase: the pointers point into a packed (block-diagonal) batch, so the row
+// pointers are shifted to start at 0 and col_base is taken off every column.
 struct InstanceIn {
-  int64_t n, m, m_eq;
-  const int32_t *Q_rowptr, *Q_col;
-  const double* Q_val;
-  const int32_t *A_rowptr, *A_col;
-  const double* A_val;
-  const double *c, *b, *l, *u;
+  int64_t n = 0, m = 0, m_eq = 0;
+  const int32_t *Q_rowptr = nullptr, *Q_col = nullptr;
+  const double* Q_val = nullptr;
+  const int32_t *A_rowptr = nullptr, *A_col = nullptr;
+  const double* A_val = nullptr;
+  const double *c = nullptr, *b = nullptr, *l = nullptr, *u = nullptr;
+  bool rebase = false;
+  int64_t col_base = 0;
 };
+
+// Row pointers shifted to start at 0, columns shifted by -base; a value that
+// leaves int32 becomes -1, which validation rejects.
+void rebase_rowptr(std::vector<int32_t>& rp) {
+  const int64_t b0 = rp.empty() ? 0 : rp[0];
+  for (auto& v : rp) {
+    const int64_t t = (int64_t)v - b0;
+    v = (t < INT32_MIN || t > INT32_MAX) ? -1 : (int32_t)t;
+  }
+}
+
+void rebase_cols(std::vector<int32_t>& col, int64_t base) {
+  for (auto& v : col) {
+    const int64_t t = (int64_t)v - base;
+    v = (t < 0 || t > INT32_MAX) ? -1 : (int32_t)t;
+  }
+}
 
 // Host-side stacking of `count` instances: P = [Q | -A'] and A with global
 // columns, row blocks that never cross an instance, per-row / per-block
@@ -635,9 +662,11 @@ Piece make_piece(const InstanceIn& in, int64_t xoff, int64_t yoff, int64_t N, in
                   (const void*)in.b, (const void*)in.l, (const void*)in.u})
     check_space(pr, mem, "input array");
   std::vector<int32_t> qrp = fetch(in.Q_rowptr, n + 1, mem, s);
+  if (in.rebase) rebase_rowptr(qrp);
   const int64_t nnzQ = qrp[n];
   if (nnzQ < 0 || (nnzQ > 0 && (!in.Q_col || !in.Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
   std::vector<int32_t> qcol = fetch(in.Q_col, nnzQ, mem, s);
+  if (in.rebase) rebase_cols(qcol, in.col_base);
   std::vector<double> qval = fetch(in.Q_val, nnzQ, mem, s);
   Piece P;
   std::vector<int32_t> icol;
@@ -645,9 +674,11 @@ Piece make_piece(const InstanceIn& in, int64_t xoff, int64_t yoff, int64_t N, in
   P.arp.assign(m + 1, 0);
   if (m > 0) {
     P.arp = fetch(in.A_rowptr, m + 1, mem, s);
+    if (in.rebase) rebase_rowptr(P.arp);
     const int64_t nnzA = P.arp[m];
     if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
     icol = fetch(in.A_col, nnzA, mem, s);
+    if (in.rebase) rebase_cols(icol, in.col_base);
     ival = fetch(in.A_val, nnzA, mem, s);
   }
   P.c = fetch(in.c, n, mem, s);
@@ -1161,15 +1192,20 @@ __device__ __forceinline__ int row_of(const int* __restrict__ rp, int rows, long
   return lo;
 }
 
+// A nonzero of row r belongs to the instance rinst[r]: its column must lie in
+// that instance's variables [ioff[inst], ioff[inst + 1]).
 __global__ void k_validate_entries(const int* __restrict__ rp, const int* __restrict__ col,
-                                   const double* __restrict__ val, int rows, int cols, long long nnz,
+                                   const double* __restrict__ val, int rows, long long nnz,
+                                   const int* __restrict__ rinst, const int* __restrict__ ioff,
                                    unsigned* __restrict__ err) {
   unsigned e = 0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
+    const int r = row_of(rp, rows, k);
+    const int inst = rinst[r];
     const int c = col[k];
-    if (c < 0 || c >= cols) e |= VE_COL;
+    if (c < ioff[inst] || c >= ioff[inst + 1]) e |= VE_COL;
     if (!isfinite(val[k])) e |= VE_VAL;
-    if (k > 0 && rp[row_of(rp, rows, k)] < k && c <= col[k - 1]) e |= VE_ORDER;
+    if (k > rp[r] && c <= col[k - 1]) e |= VE_ORDER;
   }
   if (e) atomicOr(err, e);
 }
@@ -1236,9 +1272,8 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ sums, int 
 }
 
 __global__ void k_scan_add(int* __restrict__ out, int len, const int* __restrict__ sums, const int* __restrict__ total) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < len) out[i] += sums[i / 1024];
-  if (i == 0) out[len] = *total;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) out[i] += sums[i / 1024];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[len] = *total;
 }
 
 // scatter A's entries into the column segments of A' (per nonzero, its row by
@@ -1278,8 +1313,8 @@ __global__ void k_seg_sort(const int* __restrict__ trp, int segs, int* __restric
 }
 
 __global__ void k_row_len(const int* __restrict__ qrp, const int* __restrict__ trp, int n, int* __restrict__ len) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) len[j] = (qrp[j + 1] - qrp[j]) + (trp[j + 1] - trp[j]);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    len[j] = (qrp[j + 1] - qrp[j]) + (trp[j + 1] - trp[j]);
 }
 
 // row j of P: Q's row (columns j'), then -A' row (columns n + i)
@@ -1303,25 +1338,37 @@ __global__ void k_assemble_P(const int* __restrict__ qrp, const int* __restrict_
   }
 }
 
-__global__ void k_block_meta(const int* __restrict__ blk, int nblk, const int* __restrict__ rp, int* __restrict__ meta,
-                             int* __restrict__ binst) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nblk) return;
-  const int r0 = blk[b], r1 = blk[b + 1];
-  meta[4 * b + 0] = r0;
-  meta[4 * b + 1] = r1;
-  meta[4 * b + 2] = rp[r0];
-  meta[4 * b + 3] = rp[r1];
-  binst[b] = 0;
+__global__ void k_block_meta(const int* __restrict__ blk, int nblk, const int* __restrict__ rp, int* __restrict__ meta) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+    const int r0 = blk[b], r1 = blk[b + 1];
+    meta[4 * b + 0] = r0;
+    meta[4 * b + 1] = r1;
+    meta[4 * b + 2] = rp[r0];
+    meta[4 * b + 3] = rp[r1];
+  }
 }
 
-__global__ void k_single_rows(int n, int m, int m_eq, int* __restrict__ rinst_n, int* __restrict__ rinst_m,
-                              unsigned char* __restrict__ ineq) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n || i < m; i += gridDim.x * blockDim.x) {
-    if (i < n) rinst_n[i] = 0;
-    if (i < m) {
-      rinst_m[i] = 0;
-      ineq[i] = i >= m_eq ? 1 : 0;
+// The instance of every variable and row -- the last instance whose first
+// variable (ioff) or first row (joff) is at or before it; instances without
+// rows repeat a joff entry and are passed over -- and the inequality flags.
+__global__ void k_batch_rows(const int* __restrict__ ioff, const int* __restrict__ joff, const int* __restrict__ meq,
+                             int count, int N, int M, int* __restrict__ rinst_n, int* __restrict__ rinst_m,
+                             unsigned char* __restrict__ ineq) {
+  const long long total = (long long)N + M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const bool var = i < N;
+    const int r = var ? (int)i : (int)(i - N);
+    const int* __restrict__ off = var ? ioff : joff;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    if (var) {
+      rinst_n[r] = lo;
+    } else {
+      rinst_m[r] = lo;
+      ineq[r] = r - off[lo] >= meq[lo] ? 1 : 0;
     }
   }
 }
@@ -1345,6 +1392,8 @@ struct TmpFree {
   }
 };
 
+// Grid for `total` items, capped at 8192 blocks: every kernel launched with it
+// loops over its items with the grid's stride.
 int grid_of(long long total, int threads = 256) {
   return (int)std::max<long long>(1, std::min<long long>((total + threads - 1) / threads, 8192));
 }
@@ -1362,118 +1411,196 @@ void device_scan(const int* in, int len, int* out, std::vector<void*>& tmp, cuda
   CK(cudaGetLastError());
 }
 
-// Returns nullptr when the problem needs the host path (a column of A longer
-// than SEG_MAX); throws Fail on invalid input.
-pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s) {
+// A batch handed over as one block-diagonal problem: instance i owns the
+// variables [xoff_i, xoff_i + n_i) and the rows [yoff_i, yoff_i + m_i), in
+// order; Q (N rows) and A (M rows) are CSR over the whole stack with global
+// column indices, and c, l, u (N) and b (M) are the instances' vectors
+// concatenated.  A single problem is the case count = 1.
+struct PackedIn {
+  int count = 0;
+  const int64_t *n = nullptr, *m = nullptr, *m_eq = nullptr;
+  const int32_t *Q_rowptr = nullptr, *Q_col = nullptr;
+  const double* Q_val = nullptr;
+  const int32_t *A_rowptr = nullptr, *A_col = nullptr;
+  const double* A_val = nullptr;
+  const double *c = nullptr, *b = nullptr, *l = nullptr, *u = nullptr;
+};
+
+// The instances of a packed batch as the host path takes them: pointers into
+// the packed arrays, with row pointers and columns rebased to the instance.
+std::vector<InstanceIn> unpack_instances(const PackedIn& in, const std::vector<int64_t>& xoff,
+                                         const std::vector<int64_t>& yoff, const std::vector<int32_t>& qrp,
+                                         const std::vector<int32_t>& arp) {
+  std::vector<InstanceIn> ins(in.count);
+  for (int i = 0; i < in.count; ++i) {
+    const int64_t q0 = qrp[xoff[i]], a0 = arp[yoff[i]];
+    InstanceIn& t = ins[i];
+    t.n = in.n[i];
+    t.m = in.m[i];
+    t.m_eq = in.m_eq[i];
+    t.Q_rowptr = in.Q_rowptr + xoff[i];
+    t.Q_col = in.Q_col ? in.Q_col + q0 : nullptr;
+    t.Q_val = in.Q_val ? in.Q_val + q0 : nullptr;
+    t.A_rowptr = in.A_rowptr ? in.A_rowptr + yoff[i] : nullptr;
+    t.A_col = in.A_col ? in.A_col + a0 : nullptr;
+    t.A_val = in.A_val ? in.A_val + a0 : nullptr;
+    t.c = in.c + xoff[i];
+    t.b = in.b ? in.b + yoff[i] : nullptr;
+    t.l = in.l + xoff[i];
+    t.u = in.u + xoff[i];
+    t.rebase = true;
+    t.col_base = xoff[i];
+  }
+  return ins;
+}
+
+// Build on the device: the packed input is copied as given and validated
+// there, A is transposed by a column count, scan, scatter and a per-column
+// sort by row (the same A' as the stable counting sort of the host path), and
+// P = [Q | -A'] is assembled row by row.  Only the greedy row blocks are formed
+// on the host, per instance, from the row pointers, so the handle is the one
+// build_problem makes from the same instances.  Returns nullptr, with the
+// instances for the host path in *fallback, when a column of A is longer than
+// SEG_MAX; throws Fail on invalid input.
+pdqp_problem* build_device(const PackedIn& in, int mem, cudaStream_t s, std::vector<InstanceIn>* fallback) {
   if (mem != PDQP_MEM_HOST && mem != PDQP_MEM_DEVICE) throw Fail{PDQP_ERR_INVALID, "mem_space"};
-  if (in.n < 1 || in.m < 0 || in.m_eq < 0 || in.m_eq > in.m)
-    throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
+  const int count = in.count;
+  if (count < 1 || !in.n || !in.m || !in.m_eq) throw Fail{PDQP_ERR_INVALID, "null argument or count < 1"};
+  std::vector<int64_t> xoff((size_t)count + 1, 0), yoff((size_t)count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    if (in.n[i] < 1 || in.m[i] < 0 || in.m_eq[i] < 0 || in.m_eq[i] > in.m[i])
+      throw Fail{PDQP_ERR_INVALID, "sizes: need n >= 1, 0 <= m_eq <= m"};
+    if (in.n[i] > (1LL << 30) || in.m[i] > (1LL << 30)) throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
+    xoff[i + 1] = xoff[i] + in.n[i];
+    yoff[i + 1] = yoff[i] + in.m[i];
+    if (xoff[i + 1] > (1LL << 30) || yoff[i + 1] > (1LL << 30))
+      throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
+  }
+  const int N = (int)xoff[count], M = (int)yoff[count];
   if (!in.Q_rowptr || !in.c || !in.l || !in.u) throw Fail{PDQP_ERR_INVALID, "null Q_rowptr, c, l or u"};
-  if (in.m > 0 && (!in.A_rowptr || !in.b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
-  if (in.n > (1LL << 30) || in.m > (1LL << 30)) throw Fail{PDQP_ERR_INVALID, "total n or m exceeds 2^30"};
+  if (M > 0 && (!in.A_rowptr || !in.b)) throw Fail{PDQP_ERR_INVALID, "null A_rowptr or b with m > 0"};
   for (auto pr : {(const void*)in.Q_rowptr, (const void*)in.Q_col, (const void*)in.Q_val, (const void*)in.A_rowptr,
                   (const void*)in.A_col, (const void*)in.A_val, (const void*)in.c, (const void*)in.b,
                   (const void*)in.l, (const void*)in.u})
     check_space(pr, mem, "input array");
-  const int n = (int)in.n, m = (int)in.m;
   // row pointers on the host (the greedy row blocks are formed there)
-  std::vector<int32_t> qrp = fetch(in.Q_rowptr, (size_t)n + 1, mem, s);
-  std::vector<int32_t> arp = m > 0 ? fetch(in.A_rowptr, (size_t)m + 1, mem, s) : std::vector<int32_t>(1, 0);
+  std::vector<int32_t> qrp = fetch(in.Q_rowptr, (size_t)N + 1, mem, s);
+  std::vector<int32_t> arp = M > 0 ? fetch(in.A_rowptr, (size_t)M + 1, mem, s) : std::vector<int32_t>(1, 0);
   if (qrp[0] != 0) throw Fail{PDQP_ERR_INVALID, "Q: rowptr[0] != 0"};
   if (arp[0] != 0) throw Fail{PDQP_ERR_INVALID, "A: rowptr[0] != 0"};
-  const long long nnzQ = qrp[n], nnzA = arp[m];
+  const long long nnzQ = qrp[N], nnzA = arp[M];
   if (nnzQ < 0 || (nnzQ > 0 && (!in.Q_col || !in.Q_val))) throw Fail{PDQP_ERR_INVALID, "Q: bad nnz or null arrays"};
   if (nnzA < 0 || (nnzA > 0 && (!in.A_col || !in.A_val))) throw Fail{PDQP_ERR_INVALID, "A: bad nnz or null arrays"};
   if (nnzQ + nnzA > (long long)INT32_MAX - 16) throw Fail{PDQP_ERR_INVALID, "nnz(Q) + nnz(A) exceeds 2^31"};
   TmpFree tmp;
   tmp.s = s;
-  const int* dqrp = on_device(nullptr, in.Q_rowptr, (size_t)n + 1, mem, tmp.v, s);
+  const int* dqrp = on_device(nullptr, in.Q_rowptr, (size_t)N + 1, mem, tmp.v, s);
   const int* dqcol = on_device(nullptr, in.Q_col, (size_t)nnzQ, mem, tmp.v, s);
   const double* dqval = on_device(nullptr, in.Q_val, (size_t)nnzQ, mem, tmp.v, s);
-  const int* darp = m > 0 ? on_device(nullptr, in.A_rowptr, (size_t)m + 1, mem, tmp.v, s) : nullptr;
+  const int* darp = M > 0 ? on_device(nullptr, in.A_rowptr, (size_t)M + 1, mem, tmp.v, s) : nullptr;
   const int* dacol = on_device(nullptr, in.A_col, (size_t)nnzA, mem, tmp.v, s);
   const double* daval = on_device(nullptr, in.A_val, (size_t)nnzA, mem, tmp.v, s);
   unsigned* derr = (unsigned*)pool_alloc(sizeof(unsigned), s);
   tmp.v.push_back(derr);
   CK(cudaMemsetAsync(derr, 0, sizeof(unsigned), s));
+  // instance tables: first variable and first row of every instance (then
+  // the totals), equality rows per instance
+  std::vector<int32_t> itab(3 * (size_t)count + 2);
+  for (int i = 0; i <= count; ++i) {
+    itab[i] = (int32_t)xoff[i];
+    itab[count + 1 + i] = (int32_t)yoff[i];
+    if (i < count) itab[2 * (size_t)count + 2 + i] = (int32_t)in.m_eq[i];
+  }
+  int* ditab = (int*)pool_alloc(itab.size() * sizeof(int), s);
+  tmp.v.push_back(ditab);
+  to_device(ditab, itab.data(), itab.size(), s);
+  const int *dioff = ditab, *djoff = ditab + count + 1, *dmeq = ditab + 2 * (size_t)count + 2;
 
   pdqp_problem* h = new pdqp_problem();
   h->alloc_stream = s;
   try {
     Work& w = h->w;
     // vectors straight into the handle
-    w.c = dalloc<double>(h, n); w.l = dalloc<double>(h, n); w.u = dalloc<double>(h, n); w.b = dalloc<double>(h, m);
+    w.c = dalloc<double>(h, N); w.l = dalloc<double>(h, N); w.u = dalloc<double>(h, N); w.b = dalloc<double>(h, M);
     const cudaMemcpyKind kind = mem == PDQP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(w.c, in.c, (size_t)n * sizeof(double), kind, s));
-    CK(cudaMemcpyAsync(w.l, in.l, (size_t)n * sizeof(double), kind, s));
-    CK(cudaMemcpyAsync(w.u, in.u, (size_t)n * sizeof(double), kind, s));
-    if (m > 0) CK(cudaMemcpyAsync(w.b, in.b, (size_t)m * sizeof(double), kind, s));
-    k_validate_rowptr<<<grid_of(n), 256, 0, s>>>(dqrp, n, nnzQ, derr);
-    if (m > 0) k_validate_rowptr<<<grid_of(m), 256, 0, s>>>(darp, m, nnzA, derr);
-    k_validate_vecs<<<grid_of(std::max(n, m)), 256, 0, s>>>(w.c, w.l, w.u, n, w.b, m, derr);
+    CK(cudaMemcpyAsync(w.c, in.c, (size_t)N * sizeof(double), kind, s));
+    CK(cudaMemcpyAsync(w.l, in.l, (size_t)N * sizeof(double), kind, s));
+    CK(cudaMemcpyAsync(w.u, in.u, (size_t)N * sizeof(double), kind, s));
+    if (M > 0) CK(cudaMemcpyAsync(w.b, in.b, (size_t)M * sizeof(double), kind, s));
+    w.row_inst_n = dalloc<int>(h, N);
+    w.row_inst_m = dalloc<int>(h, M);
+    w.row_ineq = dalloc<unsigned char>(h, M);
+    k_batch_rows<<<grid_of((long long)N + M), 256, 0, s>>>(dioff, djoff, dmeq, count, N, M, w.row_inst_n,
+                                                           w.row_inst_m, w.row_ineq);
+    k_validate_rowptr<<<grid_of(N), 256, 0, s>>>(dqrp, N, nnzQ, derr);
+    if (M > 0) k_validate_rowptr<<<grid_of(M), 256, 0, s>>>(darp, M, nnzA, derr);
+    k_validate_vecs<<<grid_of(std::max(N, M)), 256, 0, s>>>(w.c, w.l, w.u, N, w.b, M, derr);
     CK(cudaGetLastError());
     unsigned herr = 0;
     CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (herr & VE_RP) throw Fail{PDQP_ERR_INVALID, "Q or A: rowptr decreases"};
     // the row pointers are sound: check the entries
-    if (nnzQ > 0) k_validate_entries<<<grid_of(nnzQ), 256, 0, s>>>(dqrp, dqcol, dqval, n, n, nnzQ, derr);
-    if (nnzA > 0) k_validate_entries<<<grid_of(nnzA), 256, 0, s>>>(darp, dacol, daval, m, n, nnzA, derr);
+    if (nnzQ > 0)
+      k_validate_entries<<<grid_of(nnzQ), 256, 0, s>>>(dqrp, dqcol, dqval, N, nnzQ, w.row_inst_n, dioff, derr);
+    if (nnzA > 0)
+      k_validate_entries<<<grid_of(nnzA), 256, 0, s>>>(darp, dacol, daval, M, nnzA, w.row_inst_m, dioff, derr);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (herr & VE_COL) throw Fail{PDQP_ERR_INVALID, "Q or A: column index out of range"};
+    if (herr & VE_COL) throw Fail{PDQP_ERR_INVALID, "Q or A: column index out of range (of its instance)"};
     if (herr & VE_ORDER) throw Fail{PDQP_ERR_INVALID, "Q or A: column indices not strictly increasing in a row"};
     if (herr & VE_VAL) throw Fail{PDQP_ERR_INVALID, "Q or A: non-finite value"};
     if (herr & VE_C) throw Fail{PDQP_ERR_INVALID, "c: non-finite entry"};
     if (herr & VE_BOUNDS) throw Fail{PDQP_ERR_INVALID, "bounds: need l <= u, l < +inf, u > -inf"};
     if (herr & VE_B) throw Fail{PDQP_ERR_INVALID, "b: non-finite entry"};
-    // A' by column count, scan, scatter, per-column sort
-    int* cnt = (int*)pool_alloc((size_t)n * sizeof(int), s); tmp.v.push_back(cnt);
-    int* trp = (int*)pool_alloc(((size_t)n + 1) * sizeof(int), s); tmp.v.push_back(trp);
-    int* cur = (int*)pool_alloc((size_t)n * sizeof(int), s); tmp.v.push_back(cur);
+    // A' by column count, scan, scatter, per-column sort (A is block-diagonal,
+    // so A' is too, with the instances in the same order)
+    int* cnt = (int*)pool_alloc((size_t)N * sizeof(int), s); tmp.v.push_back(cnt);
+    int* trp = (int*)pool_alloc(((size_t)N + 1) * sizeof(int), s); tmp.v.push_back(trp);
+    int* cur = (int*)pool_alloc((size_t)N * sizeof(int), s); tmp.v.push_back(cur);
     int* tcol = (int*)pool_alloc(std::max<size_t>((size_t)nnzA, 1) * sizeof(int), s); tmp.v.push_back(tcol);
     double* tval = (double*)pool_alloc(std::max<size_t>((size_t)nnzA, 1) * sizeof(double), s);
     tmp.v.push_back(tval);
-    CK(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), s));
-    CK(cudaMemsetAsync(cur, 0, (size_t)n * sizeof(int), s));
+    CK(cudaMemsetAsync(cnt, 0, (size_t)N * sizeof(int), s));
+    CK(cudaMemsetAsync(cur, 0, (size_t)N * sizeof(int), s));
     if (nnzA > 0) k_col_count<<<grid_of(nnzA), 256, 0, s>>>(dacol, nnzA, cnt);
-    device_scan(cnt, n, trp, tmp.v, s);
+    device_scan(cnt, N, trp, tmp.v, s);
     if (nnzA > 0) {
-      k_col_scatter<<<grid_of(nnzA), 256, 0, s>>>(darp, dacol, daval, m, nnzA, trp, cur, tcol, tval);
-      k_seg_sort<<<grid_of(n), 256, 0, s>>>(trp, n, tcol, tval, derr);
+      k_col_scatter<<<grid_of(nnzA), 256, 0, s>>>(darp, dacol, daval, M, nnzA, trp, cur, tcol, tval);
+      k_seg_sort<<<grid_of(N), 256, 0, s>>>(trp, N, tcol, tval, derr);
     }
     // P = [Q | -A']
     int* plen = cnt;   // reuse
-    k_row_len<<<grid_of(n), 256, 0, s>>>(dqrp, trp, n, plen);
+    k_row_len<<<grid_of(N), 256, 0, s>>>(dqrp, trp, N, plen);
     const long long nnzP = nnzQ + nnzA;
-    w.P.rows = n;
+    w.P.rows = N;
     w.P.nnz = nnzP;
-    w.P.rp = dalloc<int>(h, (size_t)n + 1 + 8);
+    w.P.rp = dalloc<int>(h, (size_t)N + 1 + 8);
     w.P.col = dalloc<int>(h, (size_t)nnzP + 8);
     w.P.val = dalloc<double>(h, (size_t)nnzP + 8);
     w.P.sval = dalloc<double>(h, (size_t)nnzP + 8);
-    w.P.split = dalloc<int>(h, n);
-    CK(cudaMemsetAsync(w.P.rp, 0, ((size_t)n + 1 + 8) * sizeof(int), s));
+    w.P.split = dalloc<int>(h, N);
+    CK(cudaMemsetAsync(w.P.rp, 0, ((size_t)N + 1 + 8) * sizeof(int), s));
     CK(cudaMemsetAsync(w.P.col + nnzP, 0, 8 * sizeof(int), s));
     CK(cudaMemsetAsync(w.P.val + nnzP, 0, 8 * sizeof(double), s));
     CK(cudaMemsetAsync(w.P.sval, 0, ((size_t)nnzP + 8) * sizeof(double), s));
-    device_scan(plen, n, w.P.rp, tmp.v, s);
-    k_assemble_P<<<grid_of((long long)n * 32), 256, 0, s>>>(dqrp, dqcol, dqval, trp, tcol, tval, n, w.P.rp, w.P.col,
+    device_scan(plen, N, w.P.rp, tmp.v, s);
+    k_assemble_P<<<grid_of((long long)N * 32), 256, 0, s>>>(dqrp, dqcol, dqval, trp, tcol, tval, N, w.P.rp, w.P.col,
                                                             w.P.val, w.P.split);
     // A as given
-    w.A.rows = m;
+    w.A.rows = M;
     w.A.nnz = nnzA;
-    w.A.rp = dalloc<int>(h, (size_t)m + 1 + 8);
+    w.A.rp = dalloc<int>(h, (size_t)M + 1 + 8);
     w.A.col = dalloc<int>(h, (size_t)nnzA + 8);
     w.A.val = dalloc<double>(h, (size_t)nnzA + 8);
     w.A.sval = dalloc<double>(h, (size_t)nnzA + 8);
-    CK(cudaMemsetAsync(w.A.rp, 0, ((size_t)m + 1 + 8) * sizeof(int), s));
+    CK(cudaMemsetAsync(w.A.rp, 0, ((size_t)M + 1 + 8) * sizeof(int), s));
     CK(cudaMemsetAsync(w.A.col, 0, ((size_t)nnzA + 8) * sizeof(int), s));
     CK(cudaMemsetAsync(w.A.val, 0, ((size_t)nnzA + 8) * sizeof(double), s));
     CK(cudaMemsetAsync(w.A.sval, 0, ((size_t)nnzA + 8) * sizeof(double), s));
-    if (m > 0) {
-      CK(cudaMemcpyAsync(w.A.rp, darp, ((size_t)m + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    if (M > 0) {
+      CK(cudaMemcpyAsync(w.A.rp, darp, ((size_t)M + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
       if (nnzA > 0) {
         CK(cudaMemcpyAsync(w.A.col, dacol, (size_t)nnzA * sizeof(int), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(w.A.val, daval, (size_t)nnzA * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1481,41 +1608,53 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
     }
     CK(cudaGetLastError());
     // greedy row blocks on the host from the row pointers
-    std::vector<int32_t> prp((size_t)n + 1);
-    CK(cudaMemcpyAsync(prp.data(), w.P.rp, ((size_t)n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> prp((size_t)N + 1);
+    CK(cudaMemcpyAsync(prp.data(), w.P.rp, ((size_t)N + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (herr & VE_LONG) {   // a column of A longer than the device sort handles
       pdqp_destroy(h);
+      if (fallback) *fallback = unpack_instances(in, xoff, yoff, qrp, arp);
       return nullptr;
     }
-    const std::vector<int32_t> pblk = row_blocks(n, prp);
-    const std::vector<int32_t> ablk = m > 0 ? row_blocks(m, arp) : std::vector<int32_t>{0};
-    std::vector<Inst> insts(1);
-    Inst& I = insts[0];
-    I.n = n; I.m = m; I.m_eq = (int)in.m_eq; I.xoff = 0; I.yoff = 0;
-    I.bP0 = 0; I.bP1 = (int)pblk.size() - 1;
-    I.bA0 = 0; I.bA1 = (int)ablk.size() - 1;
-    I.cP0 = 0; I.cA0 = 0;
-    begin_work(h, n, m, (int)in.m_eq, 1, insts);
-    for (int side = 0; side < 2; ++side) {
-      DCsr& M = side == 0 ? w.P : w.A;
-      const std::vector<int32_t>& blk = side == 0 ? pblk : ablk;
-      M.nblk = (int)blk.size() - 1;
-      M.blk = dalloc<int>(h, blk.size());
-      to_device(M.blk, blk.data(), blk.size(), s);
-      M.meta = dalloc<int>(h, 4 * (size_t)std::max(M.nblk, 1));
-      int* binst = dalloc<int>(h, (size_t)std::max(M.nblk, 1));
-      if (M.nblk > 0) k_block_meta<<<grid_of(M.nblk), 256, 0, s>>>(M.blk, M.nblk, M.rp, M.meta, binst);
-      (side == 0 ? w.blk_inst_P : w.blk_inst_A) = binst;
-      build_long_segments(h, M, side == 0 ? prp : arp, blk, s);
+    // each instance's blocks in its own rows, as build_problem forms them
+    std::vector<int32_t> pblk{0}, ablk{0}, binst_p, binst_a;
+    std::vector<Inst> insts(count);
+    for (int i = 0; i < count; ++i) {
+      Inst& I = insts[i];
+      I.n = (int)in.n[i];
+      I.m = (int)in.m[i];
+      I.m_eq = (int)in.m_eq[i];
+      I.xoff = (int)xoff[i];
+      I.yoff = (int)yoff[i];
+      I.bP0 = (int)pblk.size() - 1;
+      append_row_blocks(xoff[i], xoff[i + 1], prp, pblk);
+      I.bP1 = (int)pblk.size() - 1;
+      I.bA0 = (int)ablk.size() - 1;
+      append_row_blocks(yoff[i], yoff[i + 1], arp, ablk);
+      I.bA1 = (int)ablk.size() - 1;
+      binst_p.resize(I.bP1, i);
+      binst_a.resize(I.bA1, i);
+      I.cP0 = i == 0 ? 0 : insts[i - 1].cP0 + kkt_chunks(insts[i - 1].bP0, insts[i - 1].bP1);
+      I.cA0 = i == 0 ? 0 : insts[i - 1].cA0 + kkt_chunks(insts[i - 1].bA0, insts[i - 1].bA1);
     }
-    w.inst = dalloc<Inst>(h, 1);
-    to_device(w.inst, insts.data(), 1, s);
-    w.row_inst_n = dalloc<int>(h, n);
-    w.row_inst_m = dalloc<int>(h, m);
-    w.row_ineq = dalloc<unsigned char>(h, m);
-    k_single_rows<<<grid_of(std::max(n, m)), 256, 0, s>>>(n, m, (int)in.m_eq, w.row_inst_n, w.row_inst_m, w.row_ineq);
+    begin_work(h, N, M, (int)in.m_eq[0], count, insts);
+    for (int side = 0; side < 2; ++side) {
+      DCsr& C = side == 0 ? w.P : w.A;
+      const std::vector<int32_t>& blk = side == 0 ? pblk : ablk;
+      const std::vector<int32_t>& bin = side == 0 ? binst_p : binst_a;
+      C.nblk = (int)blk.size() - 1;
+      C.blk = dalloc<int>(h, blk.size());
+      to_device(C.blk, blk.data(), blk.size(), s);
+      C.meta = dalloc<int>(h, 4 * (size_t)std::max(C.nblk, 1));
+      int* binst = dalloc<int>(h, (size_t)std::max(C.nblk, 1));
+      to_device(binst, bin.data(), bin.size(), s);
+      if (C.nblk > 0) k_block_meta<<<grid_of(C.nblk), 256, 0, s>>>(C.blk, C.nblk, C.rp, C.meta);
+      (side == 0 ? w.blk_inst_P : w.blk_inst_A) = binst;
+      build_long_segments(h, C, side == 0 ? prp : arp, blk, s);
+    }
+    w.inst = dalloc<Inst>(h, count);
+    to_device(w.inst, insts.data(), count, s);
     CK(cudaGetLastError());
     alloc_work(h, s);
   } catch (...) {
@@ -1526,14 +1665,42 @@ pdqp_problem* build_single_device(const InstanceIn& in, int mem, cudaStream_t s)
   return h;
 }
 
-pdqp_status create_common(pdqp_handle* out, int count, const InstanceIn* ins, int mem, cudaStream_t s) {
+pdqp_status create_packed(pdqp_handle* out, const PackedIn& in, int mem, cudaStream_t s) {
   if (!out) return PDQP_ERR_INVALID;
   *out = nullptr;
   try {
-    pdqp_problem* h = count == 1 ? build_single_device(ins[0], mem, s) : nullptr;
-    *out = h ? h : build_problem(count, ins, mem, s);
+    std::vector<InstanceIn> fallback;
+    pdqp_problem* h = build_device(in, mem, s, &fallback);
+    *out = h ? h : build_problem((int)fallback.size(), fallback.data(), mem, s);
     // the pool allocations are stream-ordered: complete them before the handle
     // is used on any other stream
+    CK(cudaStreamSynchronize(s));
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    g_create_error = f.msg;
+    return f.st;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    return PDQP_ERR_OOM;
+  }
+}
+
+pdqp_status create_common(pdqp_handle* out, int count, const InstanceIn* ins, int mem, cudaStream_t s) {
+  if (!out) return PDQP_ERR_INVALID;
+  *out = nullptr;
+  if (count == 1) {   // a single problem is built on the device
+    PackedIn p;
+    p.count = 1;
+    p.n = &ins[0].n;
+    p.m = &ins[0].m;
+    p.m_eq = &ins[0].m_eq;
+    p.Q_rowptr = ins[0].Q_rowptr; p.Q_col = ins[0].Q_col; p.Q_val = ins[0].Q_val;
+    p.A_rowptr = ins[0].A_rowptr; p.A_col = ins[0].A_col; p.A_val = ins[0].A_val;
+    p.c = ins[0].c; p.b = ins[0].b; p.l = ins[0].l; p.u = ins[0].u;
+    return create_packed(out, p, mem, s);
+  }
+  try {
+    *out = build_problem(count, ins, mem, s);
     CK(cudaStreamSynchronize(s));
     return PDQP_OK;
   } catch (const Fail& f) {
@@ -1618,6 +1785,20 @@ pdqp_status pdqp_create_batch(pdqp_handle* out, int32_t count, const int64_t* n,
     ins[i] = InstanceIn{n[i], m[i], m_eq[i], Q_rowptr[i], Q_col[i], Q_val[i], A_rowptr[i], A_col[i], A_val[i],
                         c[i], b[i], l[i], u[i]};
   return create_common(out, count, ins.data(), mem, (cudaStream_t)stream);
+}
+
+pdqp_status pdqp_create_batch_packed(pdqp_handle* out, int32_t count, const int64_t* n, const int64_t* m,
+                                     const int64_t* m_eq, const int32_t* Q_rowptr, const int32_t* Q_col,
+                                     const double* Q_val, const int32_t* A_rowptr, const int32_t* A_col,
+                                     const double* A_val, const double* c, const double* b, const double* l,
+                                     const double* u, int32_t mem, void* stream) {
+  PackedIn p;
+  p.count = count;
+  p.n = n; p.m = m; p.m_eq = m_eq;
+  p.Q_rowptr = Q_rowptr; p.Q_col = Q_col; p.Q_val = Q_val;
+  p.A_rowptr = A_rowptr; p.A_col = A_col; p.A_val = A_val;
+  p.c = c; p.b = b; p.l = l; p.u = u;
+  return create_packed(out, p, mem, (cudaStream_t)stream);
 }
 
 pdqp_status pdqp_create_family(pdqp_handle* out, int32_t count, int64_t n, int64_t m, int64_t m_eq,

@@ -92,6 +92,8 @@ SIGNATURES = {
     "pdqp_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(pdqp_profile)]),
     "pdqp_create_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int64)] * 3
                           + [ctypes.POINTER(_P)] * 10 + [ctypes.c_int32, _P]),
+    "pdqp_create_batch_packed": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32]
+                                 + [ctypes.POINTER(ctypes.c_int64)] * 3 + [_P] * 10 + [ctypes.c_int32, _P]),
     "pdqp_create_family": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "pdqp_batch_count": (ctypes.c_int32, [_P]),
@@ -305,6 +307,25 @@ def pdqp_create_batch(instances, stream=None):
     return h
 
 
+def pdqp_create_batch_packed(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, l, u,
+                             stream=None):
+    """One handle for a batch handed over as one block-diagonal problem: n, m,
+    m_eq are the instances' sizes (sequences of count ints); the CSR arrays
+    span the whole stack with global column indices and c, b, l, u are the
+    instances' vectors concatenated (pack_instances builds them)."""
+    count = len(n)
+    I64 = ctypes.c_int64 * count
+    ns, ms, meqs = I64(*[int(v) for v in n]), I64(*[int(v) for v in m]), I64(*[int(v) for v in m_eq])
+    dtypes = [np.int32, np.int32, np.float64] * 2 + [np.float64] * 4
+    args = [_ptr(a, t) for a, t in zip((Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, l, u), dtypes)]
+    mem = _one_space([a[2] for a in args])
+    h = ctypes.c_void_p()
+    st = load().pdqp_create_batch_packed(ctypes.byref(h), count, ns, ms, meqs, *[a[0] for a in args], mem,
+                                         _stream(stream))
+    _check(st, None)
+    return h
+
+
 def pdqp_create_family(count, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, C, B, l, u,
                        stream=None):
     """One handle for `count` family members sharing Q, A, l, u; C [count x n]
@@ -423,6 +444,32 @@ def batch_from_instances(insts, device=False, stream=None):
         import torch
         torch.cuda.synchronize()
     return pdqp_create_batch(entries, stream=stream)
+
+
+def pack_instances(insts):
+    """The block-diagonal form pdqp_create_batch_packed takes, from objects with
+    n, m, m_eq, Q, A (scipy CSR), c, b, l, u: a dict of the sizes (n, m, m_eq)
+    and the ten arrays (int32 row pointers and global columns, float64 values
+    and vectors)."""
+    n = np.array([it.n for it in insts], np.int64)
+    m = np.array([it.m for it in insts], np.int64)
+    xoff = np.concatenate([[0], np.cumsum(n)])
+
+    def stack(mats, rows):
+        nnz = np.array([M.indptr[rows[k]] for k, M in enumerate(mats)], np.int64)
+        eoff = np.concatenate([[0], np.cumsum(nnz)])
+        rp = np.concatenate([[0]] + [M.indptr[1:rows[k] + 1].astype(np.int64) + eoff[k]
+                                     for k, M in enumerate(mats)]).astype(np.int32)
+        col = np.concatenate([np.zeros(0, np.int64)] + [M.indices[:nnz[k]].astype(np.int64) + xoff[k]
+                                                        for k, M in enumerate(mats)]).astype(np.int32)
+        val = np.concatenate([np.zeros(0)] + [np.asarray(M.data[:nnz[k]], np.float64) for k, M in enumerate(mats)])
+        return rp, col, val
+
+    Qrp, Qcol, Qval = stack([it.Q for it in insts], n)
+    Arp, Acol, Aval = stack([it.A for it in insts], m)
+    cat = lambda f: np.concatenate([np.zeros(0)] + [np.asarray(getattr(it, f), np.float64) for it in insts])
+    return dict(n=n, m=m, m_eq=np.array([it.m_eq for it in insts], np.int64), Q_rowptr=Qrp, Q_col=Qcol,
+                Q_val=Qval, A_rowptr=Arp, A_col=Acol, A_val=Aval, c=cat("c"), b=cat("b"), l=cat("l"), u=cat("u"))
 
 
 def create_from_csr(n, m, m_eq, Q, A, c, b, l, u, device=False, stream=None):
