@@ -58,6 +58,12 @@ the design notes of the repository):
   R13 candidate ties pick the average (strict '<' in GetRestartCandidate).
   R14 a low-rank term F F' of Q is applied as F(F'x) and is left out of the
       scaling norms (D2 still scales F).
+  R18 (not in the paper; optional) infeasibility certificates: at every
+      check after the termination and iteration-limit tests, the current and
+      the average iterate's displacement from the epoch's anchor, projected
+      onto the recession cones of X and Y and unscaled, are tested as a
+      Farkas ray y (primal infeasible) and as an unbounded direction d (dual
+      infeasible), each to eps_infeasible relative to its own objective term.
 """
 from __future__ import annotations
 
@@ -322,6 +328,72 @@ def primal_weight_update(z_new, z_old, omega, theta, eps_zero):
     return omega
 
 # ---------------------------------------------------------------------------
+# Infeasibility certificates (R18; not in the paper)
+# ---------------------------------------------------------------------------
+def recession_project(d, l, u):
+    """Projection onto the recession cone of X = [l, u]: {0} where both bounds
+    are finite, [0, inf) where only l is, (-inf, 0] where only u is, R else."""
+    lo, up = np.isfinite(l), np.isfinite(u)
+    return np.where(lo & up, 0.0, np.where(lo, np.maximum(d, 0.0), np.where(up, np.minimum(d, 0.0), d)))
+
+
+def _inf_norm(v) -> float:
+    return float(np.max(np.abs(v))) if v.size else 0.0
+
+
+def dual_ray_value(p: Problem, rho: np.ndarray, eps: float) -> float:
+    """Farkas test for primal infeasibility.  For rho with rho_I >= 0 and every
+    feasible x, b'rho <= rho'Ax <= sigma_X(A'rho) (sigma_X the support function
+    of the box); so b'rho - sigma_X(A'rho) > 0 proves that no x is feasible.
+    With lam = proj_Lambda(-A'rho), b'rho + l'lam+ - u'lam- is that value on the
+    part of -A'rho inside Lambda (where sigma_X is finite) and |-A'rho - lam|_inf
+    is what leaves it.  Returns the value when it is positive and the residual
+    is at most eps times it, else 0."""
+    g = -(p.A.T @ rho)
+    lo, up = np.isfinite(p.l), np.isfinite(p.u)
+    lam = np.where(lo & up, g, np.where(lo, np.maximum(g, 0.0), np.where(up, np.minimum(g, 0.0), 0.0)))
+    lam_pos, lam_neg = np.maximum(lam, 0.0), np.maximum(-lam, 0.0)
+    value = float(p.b @ rho) + float(np.sum(np.where(lam_pos > 0, p.l, 0.0) * lam_pos)
+                                     - np.sum(np.where(lam_neg > 0, p.u, 0.0) * lam_neg))
+    return value if (value > 0 and _inf_norm(g - lam) <= eps * value) else 0.0
+
+
+def primal_ray_value(p: Problem, d: np.ndarray, eps: float) -> float:
+    """Test of d (in the recession cone of X) as a direction of unbounded
+    descent: c'd < 0, Qd = 0, A_E d = 0, A_I d >= 0, the last three to eps
+    times |c'd|.  Returns |c'd| when d passes, else 0."""
+    cd = float(p.c @ d)
+    if not cd < 0:
+        return 0.0
+    Ad = p.A @ d
+    viol = np.abs(Ad)
+    viol[p.m_eq:] = np.maximum(-Ad[p.m_eq:], 0.0)
+    worst = max(_inf_norm(viol), _inf_norm(p.Qmul(d)))
+    return -cd if worst <= eps * (-cd) else 0.0
+
+
+def find_certificate(p: Problem, ps: Problem, D1, D2, iterates, anchor, eps: float):
+    """R18: the rays of the current and the average iterate (in that order),
+    tested for primal infeasibility first.  Returns (status, x, y) with the
+    normalised certificate -- y with b'y - sigma_X(A'y) = 1, or d with c'd = -1
+    -- or None."""
+    rays = []
+    for xs, ys in iterates:
+        d = D2 * recession_project(xs - anchor[0], ps.l, ps.u)
+        rho = D1 * proj_Y(ys - anchor[1], p.m_eq)
+        rays.append((d, rho))
+    for d, rho in rays:
+        v = dual_ray_value(p, rho, eps)
+        if v > 0:
+            return "primal_infeasible", np.zeros(p.n), rho / v
+    for d, rho in rays:
+        v = primal_ray_value(p, d, eps)
+        if v > 0:
+            return "dual_infeasible", d / v, np.zeros(p.m)
+    return None
+
+
+# ---------------------------------------------------------------------------
 # Solver
 # ---------------------------------------------------------------------------
 @dataclasses.dataclass
@@ -346,13 +418,15 @@ class Options:
     norm_Q: float = 0.0
     norm_iters: int = 500
     norm_tol: float = 1e-6
+    detect_infeasibility: bool = False   # R18
+    eps_infeasible: float = 1e-8
 
 
 @dataclasses.dataclass
 class Result:
     x: np.ndarray
     y: np.ndarray
-    status: str                       # "optimal" | "iteration_limit"
+    status: str                       # "optimal" | "iteration_limit" | "primal_infeasible" | "dual_infeasible"
     iterations: int
     restarts: int
     kkt: Dict[str, float]
@@ -451,6 +525,13 @@ def solve(inst_or_problem, opts: Optional[Options] = None, x0=None, y0=None,
             return finish(cx, cy, "optimal")
         if total >= opts.max_iter:
             return finish(cx, cy, "iteration_limit")
+        if opts.detect_infeasibility:
+            cert = find_certificate(p, ps, D1, D2, ((x, y), (xbar, ybar)), (anchor_x, anchor_y),
+                                    opts.eps_infeasible)
+            if cert is not None:
+                rec["infeasible"] = cert[0]
+                return Result(cert[1], cert[2], cert[0], total, restarts, kkt_parts(p, cert[1], cert[2]),
+                              omega, nA, nQ, D1, D2, trace, checks)
 
         cx, cy, cand_kkt, restart = restart_decision(
             opts, (x, y, kkt_cur), (xbar, ybar, kkt_avg), anchor_kkt, prev_cand_kkt, k, total)
