@@ -57,7 +57,16 @@ typedef enum {
   PDQP_ITER_LIMIT = 10,      /* max_iter reached; the best iterate is returned */
   PDQP_TIME_LIMIT = 11,      /* time_limit reached; the best iterate is returned */
   PDQP_NUMERICAL = 12,       /* NaN or Inf met in the relative KKT error */
-  PDQP_DEVICE_TIMEOUT = 13   /* a bounded device wait gave up */
+  PDQP_DEVICE_TIMEOUT = 13,  /* a bounded device wait gave up */
+  /* with options.detect_infeasibility (not in the paper): a certificate was
+   * found and is returned in place of the iterate, unscaled, for the original
+   * problem.  PRIMAL_INFEASIBLE: y_out holds a Farkas ray y, y_I >= 0, with
+   * b'y - sup_{l<=x<=u} (A'y)'x = 1 on the part of A'y the box bounds, the rest
+   * of A'y within eps_infeasible; x_out is 0.  DUAL_INFEASIBLE: x_out holds a
+   * direction d of the box's recession cone with c'd = -1 and Qd, A_E d and
+   * the negative part of A_I d within eps_infeasible; y_out is 0. */
+  PDQP_PRIMAL_INFEASIBLE = 14,
+  PDQP_DUAL_INFEASIBLE = 15
 } pdqp_status;
 
 enum { PDQP_MEM_HOST = 0, PDQP_MEM_DEVICE = 1 };
@@ -103,7 +112,8 @@ typedef struct {
   int32_t spmv_threads;      /* iteration-kernel variant: 256 or 512 threads per row
                                 block, 1 = pipelined persistent (cp.async prefetch of
                                 the next row block), 2 = a whole chunk of iterations
-                                in one launch of an 8-CTA thread-block cluster with a
+                                in one launch of a 16-CTA thread-block cluster (8 where
+                                16 cannot be resident) with a
                                 cluster barrier after each half-step (problems of at
                                 most 64 row blocks of A and of P, no row longer than a
                                 row block, no low-rank term; else PDQP_ERR_INVALID),
@@ -114,6 +124,17 @@ typedef struct {
   int32_t no_graphs;         /* 0: replay each full chunk of check_period iterations
                                 and its check as one captured CUDA graph; 1: launch
                                 every kernel directly */
+  /* 1: at every check, after the termination and iteration-limit tests, the
+   * current and the average iterate's displacement from the epoch's first
+   * iterate (projected onto the recession cones of the box and of the dual
+   * set) are tested as infeasibility certificates, each to eps_infeasible
+   * relative to its own objective term (Farkas value b'y - sup (A'y)'x, or
+   * |c'd|); the first that passes ends the solve with PDQP_PRIMAL_INFEASIBLE
+   * (tested first) or PDQP_DUAL_INFEASIBLE.  Not in the paper; default 0.
+   * Best effort: a problem whose rays do not settle to eps_infeasible ends as
+   * without it (iteration limit or numerical error). */
+  int32_t detect_infeasibility;
+  double eps_infeasible;     /* 1e-8 */
 } pdqp_options;
 
 typedef struct {

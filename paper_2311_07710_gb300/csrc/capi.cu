@@ -20,6 +20,8 @@
 struct ChunkGraph {
   bool valid = false;
   SolveParams key{};
+  int key_detect = 0;          // the certificate tests are part of the captured check
+  double key_eps_inf = 0.0;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;       // kernel nodes in the graph (counted per replay)
 };
@@ -267,6 +269,35 @@ void upload_csr(pdqp_problem* h, DCsr& M, int rows, const std::vector<int32_t>& 
   CK(cudaStreamSynchronize(s));   // the host vectors die with the caller
 }
 
+// Buffers of the certificate tests (first solve that asks for them).
+void alloc_infeas(pdqp_problem* h, cudaStream_t s) {
+  Work& w = h->w;
+  if (w.inf) return;
+  const size_t n = (size_t)w.n, m = (size_t)w.m;
+  w.inf = dalloc<InfState>(h, w.count);
+  for (int k = 0; k < 2; ++k) {
+    w.inf_x[k] = dalloc<double>(h, n);
+    w.inf_y[k] = dalloc<double>(h, m);
+    CK(cudaMemsetAsync(w.inf_x[k], 0, std::max<size_t>(n, 1) * sizeof(double), s));
+    CK(cudaMemsetAsync(w.inf_y[k], 0, std::max<size_t>(m, 1) * sizeof(double), s));
+  }
+  w.inf_zn = dalloc<double>(h, n);
+  w.inf_zm = dalloc<double>(h, m);
+  w.inf_lrec = dalloc<double>(h, n);
+  w.inf_urec = dalloc<double>(h, n);
+  w.inf_part_m = dalloc<double>(h, (size_t)9 * std::max(w.A.nblk, 1));
+  w.inf_part_n = dalloc<double>(h, (size_t)15 * std::max(w.P.nblk, 1));
+  w.inf_cpart_m = dalloc<double>(h, (size_t)9 * std::max(w.nchunk_m, 1));
+  w.inf_cpart_n = dalloc<double>(h, (size_t)15 * std::max(w.nchunk_n, 1));
+  CK(cudaMemsetAsync(w.inf, 0, sizeof(InfState) * w.count, s));
+  CK(cudaMemsetAsync(w.inf_zn, 0, std::max<size_t>(n, 1) * sizeof(double), s));
+  CK(cudaMemsetAsync(w.inf_zm, 0, std::max<size_t>(m, 1) * sizeof(double), s));
+  CK(cudaMemsetAsync(w.inf_part_m, 0, (size_t)9 * std::max(w.A.nblk, 1) * sizeof(double), s));
+  CK(cudaMemsetAsync(w.inf_part_n, 0, (size_t)15 * std::max(w.P.nblk, 1) * sizeof(double), s));
+  pdqp::infeas_prepare(w, s);
+  CK(cudaGetLastError());
+}
+
 void alloc_mixed(pdqp_problem* h) {
   if (h->mixed_ready) return;
   Work& w = h->w;
@@ -326,6 +357,9 @@ void validate_options(const pdqp_options& o) {
   if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 2 && o.spmv_threads != 256 &&
       o.spmv_threads != 512)
     bad("options.spmv_threads must be 0, 1, 2, 256 or 512");
+  if (o.detect_infeasibility != 0 && o.detect_infeasibility != 1) bad("options.detect_infeasibility must be 0 or 1");
+  if (o.detect_infeasibility && !(o.eps_infeasible > 0.0 && o.eps_infeasible < 1.0))
+    bad("options.eps_infeasible must be in (0, 1)");
 }
 
 double now_s() {
@@ -395,7 +429,8 @@ cudaGraphExec_t capture_iterations(pdqp_problem* h, int len, bool mixed, int nt,
 void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
   Work& w = h->w;
   ChunkGraph& g = h->graph;
-  if (!g.valid || std::memcmp(&g.key, &p, sizeof(SolveParams)) != 0) {
+  if (!g.valid || std::memcmp(&g.key, &p, sizeof(SolveParams)) != 0 || g.key_detect != w.detect ||
+      g.key_eps_inf != w.eps_inf) {
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
     g.valid = false;
     if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
@@ -412,6 +447,8 @@ void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaS
     cudaGraphDestroy(graph);
     CK(e);
     g.key = p;
+    g.key_detect = w.detect;
+    g.key_eps_inf = w.eps_inf;
     g.valid = true;
   }
   CK(cudaGraphLaunch(g.exec, s));
@@ -423,6 +460,8 @@ pdqp_status finish_status(int st) {
     case ST_OPTIMAL: return PDQP_OK;
     case ST_ITER_LIMIT: return PDQP_ITER_LIMIT;
     case ST_NUMERICAL: return PDQP_NUMERICAL;
+    case ST_PRIMAL_INF: return PDQP_PRIMAL_INFEASIBLE;
+    case ST_DUAL_INF: return PDQP_DUAL_INFEASIBLE;
     default: return PDQP_ERR_CUDA;
   }
 }
@@ -445,6 +484,9 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
                                  "longer than a row block, no low-rank term and 3n + 2m values within 200 KB"};
   if (cluster_ok) pdqp::prepare_chunk_cluster();
   if (mixed) alloc_mixed(h);
+  w.detect = o.detect_infeasibility ? 1 : 0;
+  w.eps_inf = o.eps_infeasible;
+  if (w.detect) alloc_infeas(h, s);
   SolveParams p = make_params(o);
 
   // start point in device memory
@@ -571,6 +613,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     double* oy = y_out;
     if (mem == PDQP_MEM_HOST) { ox = x_out ? w.stage_n : nullptr; oy = y_out ? w.stage_m : nullptr; }
     pdqp::write_output(w, ox, oy, s);
+    pdqp::write_certificates(w, ox, oy, s);
     if (mem == PDQP_MEM_HOST) {
       if (x_out) CK(cudaMemcpyAsync(x_out, w.stage_n, w.n * sizeof(double), cudaMemcpyDeviceToHost, s));
       if (y_out && w.m) CK(cudaMemcpyAsync(y_out, w.stage_m, w.m * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1744,6 +1787,8 @@ void pdqp_default_options(pdqp_options* o) {
   o->norm_tol = 1e-6;
   o->spmv_threads = 0;
   o->no_graphs = 0;
+  o->detect_infeasibility = 0;
+  o->eps_infeasible = 1e-8;
 }
 
 const char* pdqp_status_string(int32_t st) {
@@ -1756,6 +1801,8 @@ const char* pdqp_status_string(int32_t st) {
     case PDQP_TIME_LIMIT: return "time limit";
     case PDQP_NUMERICAL: return "numerical error";
     case PDQP_DEVICE_TIMEOUT: return "device timeout";
+    case PDQP_PRIMAL_INFEASIBLE: return "primal infeasible";
+    case PDQP_DUAL_INFEASIBLE: return "dual infeasible";
     default: return "unknown status";
   }
 }

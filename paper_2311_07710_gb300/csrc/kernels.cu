@@ -1259,7 +1259,7 @@ __device__ void fill_steps_block(const DevState& S, const SolveParams& p, StepEn
 }
 
 __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
-                               long long chunk_len);
+                               long long chunk_len, int inf_status);
 
 // Chunk sums of the relKKT block partials: CUDA block (i, c) reduces chunk c
 // of instance i -- KKT_CHUNK consecutive row blocks from the instance's first
@@ -1313,7 +1313,7 @@ __global__ void __launch_bounds__(64) k_decide(DevState* __restrict__ sts, const
                                                 const double* __restrict__ pm, int nbm,
                                                 const double* __restrict__ pn, int nbn,
                                                 StepEntry* __restrict__ tabs, int C, SolveParams p, int mode,
-                                                long long chunk_len) {
+                                                long long chunk_len, const InfState* __restrict__ inf) {
   const int i = blockIdx.x;
   DevState* st = sts + i;
   if (mode == 1 && st->status != ST_RUNNING) return;     // uniform
@@ -1322,7 +1322,7 @@ __global__ void __launch_bounds__(64) k_decide(DevState* __restrict__ sts, const
   // pm / pn hold the chunk sums of k_kkt_chunks
   reduce_kkt_blocks(pm, nbm, in.cA0, in.m > 0 ? in.cA0 + kkt_chunks(in.bA0, in.bA1) : in.cA0, pn, nbn, in.cP0,
                     in.cP0 + kkt_chunks(in.bP0, in.bP1), F);
-  if (threadIdx.x == 0) decide_thread0(st, F, p, mode, chunk_len);
+  if (threadIdx.x == 0) decide_thread0(st, F, p, mode, chunk_len, inf ? inf[i].status : 0);
   __syncthreads();
   if (st->status == ST_RUNNING) fill_steps_block(*st, p, tabs + (size_t)i * C);
 }
@@ -1356,7 +1356,7 @@ __global__ void k_count_running(const DevState* __restrict__ sts, const Inst* __
 }
 
 __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
-                               long long chunk_len) {
+                               long long chunk_len, int inf_status) {
   DevState& S = *st;
   double P[2][6];
   kkt_from_fields(F, 0, P[0]);
@@ -1384,6 +1384,7 @@ __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const
   if (kc != kc || ka != ka) { S.status = ST_NUMERICAL; return; }
   if (cand <= p.eps) { S.status = ST_OPTIMAL; return; }
   if (S.k_total >= p.max_iter) { S.status = ST_ITER_LIMIT; return; }
+  if (inf_status) { S.status = inf_status; return; }   // a certificate of this check (optional)
   int restart = 0, to_avg = cand_avg;
   double new_anchor = cand;
   if (p.restart_rule == 0) {
@@ -1717,6 +1718,182 @@ static KktB kkt_args(Work& w, bool scaled) {
   return a;
 }
 
+// ==========================================================================
+// Infeasibility certificates (optional; not in the paper).  The rays are the
+// current and the average iterate's displacement from the anchor the relKKT
+// check measures restart distances from (the epoch's first iterate; in mixed
+// precision the float64 base), projected onto the recession cones of X (0
+// where both bounds are finite, [0, inf) where only l is, (-inf, 0] where
+// only u is) and of Y (y_I >= 0).  Their tests are relKKT quantities of
+// homogeneous problems, so the relKKT kernels evaluate them on the original
+// problem: a primal ray d with b = 0 and the recession cone as the box gives
+// the violation of A d, |Qd|_inf and c'd; a dual ray y with x = 0 and c = 0
+// gives b'y + l'lam+ - u'lam- (lam = proj_Lambda(-A'y)), the Farkas value
+// b'y - sup_{x in X} (A'y)'x where -A'y lies in Lambda, and |-A'y - lam|_inf,
+// what leaves Lambda, as the dual residual.
+// ==========================================================================
+__global__ void k_rec_bounds(int n, const double* __restrict__ l, const double* __restrict__ u,
+                             double* __restrict__ lrec, double* __restrict__ urec) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    lrec[i] = isfinite(l[i]) ? 0.0 : -INFINITY;
+    urec[i] = isfinite(u[i]) ? 0.0 : INFINITY;
+  }
+}
+
+// Rays of the instances still running (the rows of the others keep the
+// certificate they ended with).
+__global__ void k_rays(int n, int m, const DevState* __restrict__ st, const int* __restrict__ inst_n,
+                       const int* __restrict__ inst_m, const unsigned char* __restrict__ ineq,
+                       const double* __restrict__ l, const double* __restrict__ u, const double* __restrict__ x0,
+                       const double* __restrict__ x1, const double* __restrict__ ax, const double* __restrict__ y0,
+                       const double* __restrict__ y1, const double* __restrict__ ay, double* __restrict__ rx0,
+                       double* __restrict__ rx1, double* __restrict__ ry0, double* __restrict__ ry1) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
+    if (i < n && st[inst_n[i]].status == ST_RUNNING) {
+      const bool lo = isfinite(l[i]), up = isfinite(u[i]);
+      double d0 = x0[i] - ax[i], d1 = x1[i] - ax[i];
+      if (lo && up) { d0 = 0.0; d1 = 0.0; }
+      else if (lo) { d0 = fmax(d0, 0.0); d1 = fmax(d1, 0.0); }
+      else if (up) { d0 = fmin(d0, 0.0); d1 = fmin(d1, 0.0); }
+      rx0[i] = d0;
+      rx1[i] = d1;
+    }
+    if (i < m && st[inst_m[i]].status == ST_RUNNING) {
+      double r0 = y0[i] - ay[i], r1 = y1[i] - ay[i];
+      if (ineq[i]) { r0 = fmax(r0, 0.0); r1 = fmax(r1, 0.0); }
+      ry0[i] = r0;
+      ry1[i] = r1;
+    }
+  }
+}
+
+// PASS 0 (primal rays): d passes if c'd < 0 and max(|viol(A d)|_inf,
+// |Qd|_inf) <= eps |c'd|.  PASS 1 (dual rays): y passes if its Farkas value
+// v > 0 and the residual <= eps v; then the instance's status: primal
+// infeasible if a dual ray passed, else dual infeasible if a primal ray did
+// (the current iterate's ray before the average's).
+template <int PASS>
+__global__ void __launch_bounds__(64) k_infeas(InfState* __restrict__ inf, const DevState* __restrict__ sts,
+                                               const Inst* __restrict__ insts, const double* __restrict__ pm,
+                                               int nbm, const double* __restrict__ pn, int nbn, double eps) {
+  const int i = blockIdx.x;
+  if (sts[i].status != ST_RUNNING) return;     // uniform
+  const Inst in = insts[i];
+  __shared__ double F[24];
+  reduce_kkt_blocks(pm, nbm, in.cA0, in.m > 0 ? in.cA0 + kkt_chunks(in.bA0, in.bA1) : in.cA0, pn, nbn, in.cP0,
+                    in.cP0 + kkt_chunks(in.bP0, in.bP1), F);
+  if (threadIdx.x != 0) return;
+  InfState& I = inf[i];
+  if (PASS == 0) {
+    I.dual_it = -1;
+    I.dual_scale = 0.0;
+    for (int it = 0; it < 2; ++it) {
+      const double viol = F[it * 4 + 0], qd = F[9 + it * 7 + 1], cd = F[9 + it * 7 + 4];
+      if (cd < 0.0 && fmax(viol, qd) <= eps * -cd) {
+        I.dual_it = it;
+        I.dual_scale = -cd;
+        break;
+      }
+    }
+  } else {
+    I.status = 0;
+    for (int it = 0; it < 2; ++it) {
+      const double res = F[9 + it * 7 + 0], v = F[it * 4 + 2] + F[9 + it * 7 + 5];
+      if (v > 0.0 && res <= eps * v) {
+        I.status = ST_PRIMAL_INF;
+        I.cert_it = it;
+        I.scale = v;
+        break;
+      }
+    }
+    if (!I.status && I.dual_it >= 0) {
+      I.status = ST_DUAL_INF;
+      I.cert_it = I.dual_it;
+      I.scale = I.dual_scale;
+    }
+  }
+}
+
+// The normalised certificate of every instance that ended infeasible, in
+// original coordinates, over its rows of x_out / y_out (the other vector 0).
+__global__ void k_write_cert(int n, int m, const double* __restrict__ D1, const double* __restrict__ D2,
+                             const DevState* __restrict__ st, const InfState* __restrict__ inf,
+                             const int* __restrict__ inst_n, const int* __restrict__ inst_m,
+                             const double* __restrict__ rx0, const double* __restrict__ rx1,
+                             const double* __restrict__ ry0, const double* __restrict__ ry1,
+                             double* __restrict__ x_out, double* __restrict__ y_out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
+    if (i < n && x_out) {
+      const int k = inst_n[i], s = st[k].status;
+      if (s == ST_PRIMAL_INF) x_out[i] = 0.0;
+      else if (s == ST_DUAL_INF) x_out[i] = D2[i] * (inf[k].cert_it ? rx1 : rx0)[i] / inf[k].scale;
+    }
+    if (i < m && y_out) {
+      const int k = inst_m[i], s = st[k].status;
+      if (s == ST_DUAL_INF) y_out[i] = 0.0;
+      else if (s == ST_PRIMAL_INF) y_out[i] = D1[i] * (inf[k].cert_it ? ry1 : ry0)[i] / inf[k].scale;
+    }
+  }
+}
+
+// Both passes over the rays of the iterates the check's relKKT pass `main`
+// read (and its anchors).
+static void infeas_check(Work& w, const KktB& main, cudaStream_t s) {
+  const int NN = w.n > w.m ? w.n : w.m;
+  const int grid_v = cdiv(NN, 256) < 4 * w.num_sms ? cdiv(NN, 256) : 4 * w.num_sms;
+  launch(k_rays, grid_v, 256, 0, s, w.n, w.m, (const DevState*)w.st, (const int*)w.row_inst_n,
+         (const int*)w.row_inst_m, (const unsigned char*)w.row_ineq, (const double*)w.l, (const double*)w.u,
+         main.x[0], main.x[1], main.ax, main.y[0], main.y[1], main.ay, w.inf_x[0], w.inf_x[1], w.inf_y[0],
+         w.inf_y[1]);
+  const dim3 cgrid(w.count, std::max(w.maxchunk_n, w.maxchunk_m));
+  for (int pass = 0; pass < 2; ++pass) {
+    KktB a = kkt_args(w, true);
+    a.part_m = w.inf_part_m;
+    a.part_n = w.inf_part_n;
+    a.ax = w.inf_zn;
+    a.ay = w.inf_zm;
+    if (pass == 0) {   // primal rays: b = 0, the box's recession cone as the box
+      a.x[0] = w.inf_x[0]; a.x[1] = w.inf_x[1];
+      a.y[0] = w.inf_zm; a.y[1] = w.inf_zm;
+      a.b = w.inf_zm; a.l = w.inf_lrec; a.u = w.inf_urec;
+      if (w.r > 0) {
+        lowrank_ft<double, double>(w, w.Fd, a.x[0], a.x[1], s);
+        a.F = w.Fd; a.wlr = w.wlr; a.r = w.r;
+      }
+    } else {           // dual rays: x = 0, c = 0
+      a.x[0] = w.inf_zn; a.x[1] = w.inf_zn;
+      a.y[0] = w.inf_y[0]; a.y[1] = w.inf_y[1];
+      a.c = w.inf_zn;
+    }
+    launch_kkt<2>(w, a, s);
+    launch(k_kkt_chunks, cgrid, 32, 0, s, (const Inst*)w.inst, (const double*)w.inf_part_m, w.A.nblk,
+           (const double*)w.inf_part_n, w.P.nblk, w.inf_cpart_m, std::max(w.nchunk_m, 1), w.inf_cpart_n,
+           std::max(w.nchunk_n, 1));
+    if (pass == 0)
+      launch(k_infeas<0>, w.count, 64, 0, s, w.inf, (const DevState*)w.st, (const Inst*)w.inst,
+             (const double*)w.inf_cpart_m, std::max(w.nchunk_m, 1), (const double*)w.inf_cpart_n,
+             std::max(w.nchunk_n, 1), w.eps_inf);
+    else
+      launch(k_infeas<1>, w.count, 64, 0, s, w.inf, (const DevState*)w.st, (const Inst*)w.inst,
+             (const double*)w.inf_cpart_m, std::max(w.nchunk_m, 1), (const double*)w.inf_cpart_n,
+             std::max(w.nchunk_n, 1), w.eps_inf);
+  }
+}
+
+void infeas_prepare(Work& w, cudaStream_t s) {
+  launch(k_rec_bounds, cdiv(w.n, 256), 256, 0, s, w.n, (const double*)w.l, (const double*)w.u, w.inf_lrec,
+         w.inf_urec);
+}
+
+void write_certificates(Work& w, double* x_out, double* y_out, cudaStream_t s) {
+  if (!w.detect || !w.inf || (!x_out && !y_out)) return;
+  const int N = w.n > w.m ? w.n : w.m;
+  launch(k_write_cert, cdiv(N, 256), 256, 0, s, w.n, w.m, (const double*)w.D1, (const double*)w.D2,
+         (const DevState*)w.st, (const InfState*)w.inf, (const int*)w.row_inst_n, (const int*)w.row_inst_m,
+         (const double*)w.inf_x[0], (const double*)w.inf_x[1], (const double*)w.inf_y[0],
+         (const double*)w.inf_y[1], x_out, y_out);
+}
+
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s) {
   if (w.prof.on) w.prof.begin(2, s);
   const int NN = w.n > w.m ? w.n : w.m;
@@ -1744,9 +1921,11 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
            (const double*)w.part_n, w.P.nblk, w.cpart_m, std::max(w.nchunk_m, 1), w.cpart_n, std::max(w.nchunk_n, 1));
   }
+  const bool certify = w.detect && w.inf && mode == 1;
+  if (certify) infeas_check(w, a, s);
   launch(k_decide, w.count, 64, 0, s, w.st, (const Inst*)w.inst, (const double*)w.cpart_m,
          std::max(w.nchunk_m, 1), (const double*)w.cpart_n, std::max(w.nchunk_n, 1), w.tab, w.tab_stride, p, mode,
-         chunk_len);
+         chunk_len, certify ? (const InfState*)w.inf : (const InfState*)nullptr);
   if (mixed) {
     launch(k_mixed_rebase, grid_v, 256, 0, s, mixed_args(w), mode == 0 ? 1 : 0);
   } else if (mode == 1) {

@@ -72,6 +72,20 @@ struct Profiler {
   ~Profiler();
 };
 
+// Statuses of an instance beyond the ST_* of the device state: an
+// infeasibility certificate was found (optional detection, not in the paper).
+enum { ST_PRIMAL_INF = 4, ST_DUAL_INF = 5 };
+
+// Per-instance result of the certificate tests of the last check: status
+// ST_PRIMAL_INF / ST_DUAL_INF / 0, the iterate whose ray passed (0 current,
+// 1 average) and the ray's objective term (Farkas value or |c'd|) that
+// normalises it; dual_it / dual_scale hold the unbounded-direction test
+// between the two passes.
+struct InfState {
+  int status, cert_it, dual_it, pad;
+  double scale, dual_scale;
+};
+
 struct Work {
   int n = 0, m = 0, m_eq = 0;   // totals over the batch (m_eq: single-instance value)
   int count = 1;                // instances stacked block-diagonally
@@ -136,6 +150,15 @@ struct Work {
   DevState* st_host = nullptr;   // pinned mirror [count]
   // user-vector staging (float64)
   double *stage_n = nullptr, *stage_m = nullptr;
+  // infeasibility certificates (this solve's options; buffers on first use)
+  int detect = 0;
+  double eps_inf = 1e-8;
+  InfState* inf = nullptr;                   // [count]
+  double *inf_x[2] = {nullptr, nullptr};     // rays of the current / average iterate, scaled [n]
+  double *inf_y[2] = {nullptr, nullptr};     // [m]
+  double *inf_zn = nullptr, *inf_zm = nullptr;       // zeros [n], [m]
+  double *inf_lrec = nullptr, *inf_urec = nullptr;   // the box's recession cone: 0 / -inf / +inf [n]
+  double *inf_part_m = nullptr, *inf_part_n = nullptr, *inf_cpart_m = nullptr, *inf_cpart_n = nullptr;
   Profiler prof;
 };
 
@@ -172,6 +195,12 @@ void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 
 bool chunk_cluster_ok(const Work& w, bool mixed);
 void prepare_chunk_cluster();           // once, outside any stream capture
 void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mixed, cudaStream_t s);
+
+// infeasibility certificates: fill the recession-cone bounds once the
+// buffers exist; after write_output, the certificates of the instances that
+// ended infeasible replace their iterates
+void infeas_prepare(Work& w, cudaStream_t s);
+void write_certificates(Work& w, double* x_out, double* y_out, cudaStream_t s);
 
 // results
 void write_output(Work& w, double* x_out, double* y_out, cudaStream_t s);

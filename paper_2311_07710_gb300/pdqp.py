@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libpdqp.so")
 
 PDQP_OK, PDQP_ERR_INVALID, PDQP_ERR_CUDA, PDQP_ERR_OOM = 0, 1, 2, 3
 PDQP_ITER_LIMIT, PDQP_TIME_LIMIT, PDQP_NUMERICAL, PDQP_DEVICE_TIMEOUT = 10, 11, 12, 13
+PDQP_PRIMAL_INFEASIBLE, PDQP_DUAL_INFEASIBLE = 14, 15
 PDQP_MEM_HOST, PDQP_MEM_DEVICE = 0, 1
 PDQP_PREC_FP64, PDQP_PREC_MIXED = 0, 1
 PDQP_STEP_ADAPTIVE, PDQP_STEP_THEORY = 0, 1
@@ -34,6 +35,7 @@ class pdqp_options(ctypes.Structure):
         ("beta_art", ctypes.c_double), ("pw_theta", ctypes.c_double), ("eps_zero", ctypes.c_double),
         ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double), ("norm_iters", ctypes.c_int32),
         ("norm_tol", ctypes.c_double), ("spmv_threads", ctypes.c_int32), ("no_graphs", ctypes.c_int32),
+        ("detect_infeasibility", ctypes.c_int32), ("eps_infeasible", ctypes.c_double),
     ]
 
 
@@ -176,7 +178,8 @@ def _stream(stream):
 
 
 def _check(status, handle=None):
-    if status not in (PDQP_OK, PDQP_ITER_LIMIT, PDQP_TIME_LIMIT, PDQP_NUMERICAL):
+    if status not in (PDQP_OK, PDQP_ITER_LIMIT, PDQP_TIME_LIMIT, PDQP_NUMERICAL, PDQP_PRIMAL_INFEASIBLE,
+                      PDQP_DUAL_INFEASIBLE):
         msg = load().pdqp_last_error(handle).decode()
         raise PdqpError(status, msg)
     return status
