@@ -48,7 +48,12 @@ the design notes of the repository):
   R8 condition (iii): t = iterations of the current epoch, k = total iterations.
   R9 eps_zero = 1e-10.
   R10 ||A||_2, ||Q||_2 by the Lanczos method (largest Ritz value) from the
-      all-ones vector; the paper does not say how the norms are obtained.
+      sign vector s/sqrt(n), s_j = -1 where the top bit of SplitMix64's
+      finaliser (Steele, Lea & Flood 2014) of the index j is set, else +1; the
+      paper does not say how the norms are obtained.  (Not the all-ones
+      vector: it is an eigenvector of Laplacian-like operators -- of Q = L + cI
+      for its smallest eigenvalue, of A'A in its null space when every row of
+      A sums to zero -- where Lanczos stops at once at the wrong value.)
   R11 scaling passes divide every index j of the symmetric K by
       sqrt(norm of row j of the current scaled K) (inf-norm for Ruiz, 2-norm
       for the l2 pass, 1-norm for Pock-Chambolle with alpha = 1); zero
@@ -216,15 +221,26 @@ def scale_problem(p: Problem, D1: np.ndarray, D2: np.ndarray) -> Problem:
 NORM_STEPS = {}   # Lanczos steps taken by the latest call for each operator name
 
 
+def lanczos_start(dim: int) -> np.ndarray:
+    """R10's start vector: s_j / sqrt(dim), s_j = -1 where the top bit of the
+    SplitMix64 finaliser of j (Steele, Lea & Flood 2014; uint64 arithmetic,
+    which numpy wraps mod 2^64) is set, else +1."""
+    z = np.arange(dim, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    z = z ^ (z >> np.uint64(31))
+    return np.where((z >> np.uint64(63)) == 1, -1.0, 1.0) / math.sqrt(dim)
+
+
 def lanczos_max_eig(apply_sym, dim: int, max_iter: int = 500, tol: float = 1e-6, name: str = "") -> float:
     """Largest eigenvalue of a symmetric PSD operator: the largest Ritz value of
     the Lanczos tridiagonal T_k (plain three-term recurrence, no
-    reorthogonalisation) started from the normalised all-ones vector.  Stops
-    when that value changes by at most tol relative, when beta_k <= 1e-12 theta_k
-    (an invariant subspace: the value is exact), or after max_iter steps."""
+    reorthogonalisation) started from lanczos_start (R10).  Stops when that
+    value changes by at most tol relative, when beta_k <= 1e-12 theta_k (an
+    invariant subspace: the value is exact), or after max_iter steps."""
     if dim == 0:
         return 0.0
-    v = np.full(dim, 1.0 / math.sqrt(dim))
+    v = lanczos_start(dim)
     v_prev = np.zeros(dim)
     beta_prev = 0.0
     alphas, betas = [], []

@@ -1123,12 +1123,27 @@ __global__ void k_lz_norm(LzArgs a, V* __restrict__ vA_next, V* __restrict__ vQ_
   }
 }
 
-// start vectors 1/sqrt(n_i) per instance; Lanczos state
+// Start vector entry of row j (its index within its instance) of an instance
+// of n variables: +-1/sqrt(n), negative where the top bit of the SplitMix64
+// finaliser (Steele, Lea & Flood 2014) of j is set.  Not the all-ones vector,
+// an eigenvector of Laplacian-like operators (of L + cI for its smallest
+// eigenvalue; of A'A in its null space when A's rows sum to zero).
+__device__ __forceinline__ double lz_start(int j, int n) {
+  unsigned long long z = (unsigned long long)j + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  const double v = 1.0 / sqrt((double)n);
+  return (z >> 63) ? -v : v;
+}
+
+// start vectors per instance; Lanczos state
 template <typename V>
 __global__ void k_lz_init(LzArgs a, V* __restrict__ vA0, V* __restrict__ vA1, V* __restrict__ vQ0,
                           V* __restrict__ vQ1) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += gridDim.x * blockDim.x) {
-    const V v = (V)(1.0 / sqrt((double)a.inst[a.row_inst_n[r]].n));
+    const Inst& in = a.inst[a.row_inst_n[r]];
+    const V v = (V)lz_start(r - in.xoff, in.n);
     vA0[r] = v; vQ0[r] = v; vA1[r] = V(0); vQ1[r] = V(0);
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.count; i += gridDim.x * blockDim.x) {
