@@ -174,23 +174,63 @@ def oracle_sample(inst, budget_iters=6, scaling_passes=1, norm_steps=2):
     return 1.0 / t_solve, t_solve, sample
 
 
+def _oracle_solves(insts):
+    """Full oracle solves (default options) of `insts`; solves per second."""
+    from oracle import rapdhg as R
+    t = time.perf_counter()
+    for inst in insts:
+        R.solve(inst, R.Options())
+    return len(insts) / (time.perf_counter() - t)
+
+
 def run_reference(args, world, rank):
-    """--impl reference: the CPU oracle as it stands, bounded samples."""
+    """--impl reference: the CPU oracle as it stands, bounded samples of the
+    workload the GPU arm runs with the same arguments (rank 0 only)."""
     if rank != 0:
         return
+    import dataclasses
     import qpgen
-    inst = qpgen.large_sparse_qp()
+    wl = args.workload
+    if wl in ("gemm", "algorithms"):
+        print(json.dumps({"impl": "reference", "unavailable": f"workload {wl}: not a solve workload (the oracle "
+                          "arm times solves; gemm is measured against cuBLAS, algorithms reports iteration "
+                          "counts)"}), flush=True)
+        return
+    per_step = 1                 # solves in one step of the GPU arm
+    if wl == "large_sparse_qp":
+        inst = qpgen.large_sparse_qp()
+        step, workload = (lambda: oracle_sample(inst)), WORKLOAD
+    elif wl == "random_sparse_qp":
+        inst = qpgen.random_sparse_qp(seed=qpgen.SEED_BASE)
+        step = lambda: (_oracle_solves([inst]), None, "one full oracle solve of the instance per step")
+        workload = "random_sparse_qp n=1000 m=500"
+    elif wl == "mpc_batch":
+        batch = per_step = args.batch or 4096
+        insts = qpgen.mpc_batch(min(64, batch), seed=qpgen.SEED_BASE + 3)
+        step = lambda: (_oracle_solves(insts), None,
+                        f"full oracle solves of the first {len(insts)} of the {batch} control QPs per step")
+        workload = f"mpc_batch: {batch} control QPs, 12 states, 4 inputs, horizon 10..100"
+    else:   # family_ws
+        per_step = args.batch or 1024
+        fam = qpgen.family_qp(seed=qpgen.SEED_BASE + 4)
+        C, B = fam.params(10 ** 7, 8)
+        insts = [dataclasses.replace(fam.base, c=C[i], b=B[i]) for i in range(len(C))]
+        step = lambda: (_oracle_solves(insts), None,
+                        f"full oracle solves of {len(insts)} held-out members per step from the all-zero start "
+                        "(the oracle has no network)")
+        workload = FAMILY_WORKLOAD
     vals = []
-    for step in range(args.warmup + args.steps):
-        v, t_solve, sample = oracle_sample(inst)
-        if step >= args.warmup:
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        v, _, sample = step()
+        if k >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator)",
-            "config": {"workload": WORKLOAD, "solver": "CPU oracle (numpy/scipy, float64)"},
+            "config": {"workload": workload, "solver": "CPU oracle (numpy/scipy, float64)"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -1,0 +1,33 @@
+"""The bench's reference arm (the CPU oracle) on the CPU: one JSON line with
+the contract's keys, for a solve workload, and an explicit line for a
+workload that is not a solve."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*args):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600, check=True).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_line_has_the_contract_keys():
+    d = _run("--steps", "2", "--warmup", "1", "--workload", "random_sparse_qp")
+    assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["ms_per_step"] == 1e3 / d["value"]
+    assert d["config"]["workload"].startswith("random_sparse_qp")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_non_solve_workload_says_so():
+    d = _run("--steps", "1", "--warmup", "0", "--workload", "gemm")
+    assert d["impl"] == "reference" and "unavailable" in d
