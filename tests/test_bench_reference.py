@@ -31,3 +31,19 @@ def test_reference_line_has_the_contract_keys():
 def test_non_solve_workload_says_so():
     d = _run("--steps", "1", "--warmup", "0", "--workload", "gemm")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_roofline_peak_source(tmp_path, monkeypatch):
+    """The roofline denominator is the measured value when MEASURED_PEAKS.json
+    holds it, else the profiling recipe's fallback, and says which."""
+    sys.path.insert(0, ROOT)
+    import bench
+    f = tmp_path / "peaks.json"
+    f.write_text(json.dumps({"hbm_gbs": 6543.2}))
+    monkeypatch.setattr(bench, "PEAKS_JSON", str(f))
+    assert bench.peak_of("hbm_gbs") == (6543.2, "MEASURED_PEAKS.json hbm_gbs (of measured)")
+    v, src = bench.peak_of("bf16_tflops", "burst")
+    assert v == 1900.0 and src.endswith("(burst, of fallback)")
+    monkeypatch.setattr(bench, "PEAKS_JSON", str(tmp_path / "absent.json"))
+    v, src = bench.peak_of("hbm_gbs")
+    assert v == 6800.0 and "of fallback" in src
