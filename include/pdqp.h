@@ -184,13 +184,16 @@ pdqp_status pdqp_create(pdqp_handle *out, int64_t n, int64_t m, int64_t m_eq,
                         int32_t mem_space, void *stream);
 
 /* Create one handle holding `count` independent problems of uneven sizes,
- * stacked block-diagonally on the device.  Every argument is a host array of
+ * stacked block-diagonally (each instance validated and assembled on the host,
+ * on up to 16 threads, then copied to the device; pdqp_create_batch_packed
+ * builds the same handle on the device).  Every argument is a host array of
  * `count` entries with the meaning of the pdqp_create argument of the same name
  * (the arrays they point to live in `mem_space`).  pdqp_solve on such a handle
  * solves all instances in the same launches, each with its own step sizes,
  * primal weight, restarts and termination; x0/y0/x_out/y_out are then the
- * instances' vectors concatenated in order, the returned status is the worst
- * one and pdqp_batch_info gives each instance's summary. */
+ * instances' vectors concatenated in order, the returned status is the largest
+ * status code among the instances and pdqp_batch_info gives each instance's
+ * summary. */
 pdqp_status pdqp_create_batch(pdqp_handle *out, int32_t count, const int64_t *n, const int64_t *m,
                               const int64_t *m_eq, const int32_t *const *Q_rowptr,
                               const int32_t *const *Q_col, const double *const *Q_val,
