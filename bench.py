@@ -194,6 +194,19 @@ def _oracle_solves(insts):
     return len(insts) / (time.perf_counter() - t)
 
 
+def oracle_agreement(ref, x, y, primal_obj):
+    """A solve of the n=1e6 problem against the oracle's stored solve of it:
+    the objective's relative error and max |v - v*| / (1 + |v*|) over the
+    stored sample of x and y entries."""
+    xs, ys = np.asarray(ref["x_value"]), np.asarray(ref["y_value"])
+    ex = float(np.max(np.abs(np.asarray(x)[ref["x_index"]] - xs) / (1.0 + np.abs(xs))))
+    ey = float(np.max(np.abs(np.asarray(y)[ref["y_index"]] - ys) / (1.0 + np.abs(ys))))
+    obj = ref["kkt"]["primal_obj"]
+    return {"obj_rel_err": abs(primal_obj - obj) / (1.0 + abs(obj)), "x_max_rel_err": ex, "y_max_rel_err": ey,
+            "sample": f"{len(xs)} x and {len(ys)} y entries of the oracle's stored solve ({ref['iterations']} "
+                      "iterations, float64)"}
+
+
 def run_reference(args, world, rank):
     """--impl reference: the CPU oracle as it stands, bounded samples of the
     workload the GPU arm runs with the same arguments (rank 0 only)."""
@@ -363,6 +376,12 @@ def run_ours(args, world, rank, local):
     iters = [i.iterations for i in infos]
     statuses = [i.status for i in infos]
     inst_iters = [i.iterations for i in batch_infos]
+    # agreement with the oracle's stored solve of the same problem (x, y hold the
+    # last solve of this arm; the float64 side below overwrites them)
+    vs_oracle = None
+    if args.workload == "large_sparse_qp" and args.n == 1_000_000 and rank == 0:
+        vs_oracle = oracle_agreement(json.load(open(REF_JSON)), x.cpu().numpy(), y.cpu().numpy(),
+                                     infos[-1].primal_obj)
 
     # ---- side measurement: plain float64 solves of the same problem ----
     fp64_side = None
@@ -469,6 +488,8 @@ def run_ours(args, world, rank, local):
             "gpu_launches": launches, "clocks": clk}
     if fp64_side is not None:
         line["plain_fp64"] = fp64_side
+    if vs_oracle is not None:
+        line["vs_oracle"] = vs_oracle
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.n == 1_000_000 and \
             args.workload == "large_sparse_qp":
         v, t_solve, sample = oracle_sample(inst)

@@ -47,3 +47,22 @@ def test_roofline_peak_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PEAKS_JSON", str(tmp_path / "absent.json"))
     v, src = bench.peak_of("hbm_gbs")
     assert v == 6800.0 and "of fallback" in src
+
+
+def test_oracle_agreement_against_the_stored_solve():
+    """The bench's comparison with the oracle's stored n=1e6 solve: zero for
+    the stored values themselves, the planted deviation otherwise."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    ref = json.load(open(bench.REF_JSON))
+    x, y = np.zeros(1_000_000), np.zeros(500_000)
+    x[ref["x_index"]] = ref["x_value"]
+    y[ref["y_index"]] = ref["y_value"]
+    a = bench.oracle_agreement(ref, x, y, ref["kkt"]["primal_obj"])
+    assert a["obj_rel_err"] == 0 and a["x_max_rel_err"] == 0 and a["y_max_rel_err"] == 0
+    k = ref["x_index"][5]
+    x[k] += 1e-3 * (1 + abs(ref["x_value"][5]))
+    a = bench.oracle_agreement(ref, x, y, ref["kkt"]["primal_obj"] * (1 + 1e-7))
+    assert abs(a["x_max_rel_err"] - 1e-3) < 1e-12 and a["y_max_rel_err"] == 0
+    assert 0 < a["obj_rel_err"] < 1e-7
