@@ -153,6 +153,22 @@ def test_detection_leaves_feasible_solves_alone(k):
     np.testing.assert_array_equal(a.y, b.y)
 
 
+CLASSES = [qpgen.random_sparse_qp(seed=qpgen.SEED_BASE), *qpgen.mpc_batch(3, seed=qpgen.SEED_BASE + 3),
+           qpgen.lasso_qp(), qpgen.huber_qp(), qpgen.svm_qp()]
+
+
+@pytest.mark.parametrize("k", range(len(CLASSES)), ids=[i.name for i in CLASSES])
+def test_no_certificate_on_the_feasible_classes(k):
+    """With detection on, the bench's problem classes (random sparse, control,
+    Lasso, Huber, SVM) solve exactly as without it: no ray of theirs passes."""
+    inst = CLASSES[k]
+    a = R.solve(inst, R.Options())
+    b = R.solve(inst, R.Options(detect_infeasibility=True))
+    assert a.status == b.status == "optimal" and a.iterations == b.iterations
+    np.testing.assert_array_equal(a.x, b.x)
+    np.testing.assert_array_equal(a.y, b.y)
+
+
 # ---------------------------------------------------------------------------
 # planted mistakes in the certificate tests
 # ---------------------------------------------------------------------------
