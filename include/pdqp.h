@@ -183,8 +183,10 @@ pdqp_status pdqp_create(pdqp_handle *out, int64_t n, int64_t m, int64_t m_eq,
                         const double *c, const double *b, const double *l, const double *u,
                         int32_t mem_space, void *stream);
 
-/* Create one handle holding `count` independent problems of uneven sizes,
- * stacked block-diagonally (each instance validated and assembled on the host,
+/* Create one handle holding `count` independent problems of uneven sizes
+ * (batching is not in the paper: every instance runs Algorithm 1 with the
+ * Section 6 rules on its own, as a standalone solve would), stacked
+ * block-diagonally (each instance validated and assembled on the host,
  * on up to 16 threads, then copied to the device; pdqp_create_batch_packed
  * builds the same handle on the device).  Every argument is a host array of
  * `count` entries with the meaning of the pdqp_create argument of the same name
@@ -203,8 +205,8 @@ pdqp_status pdqp_create_batch(pdqp_handle *out, int32_t count, const int64_t *n,
                               int32_t mem_space, void *stream);
 
 /* The handle pdqp_create_batch builds from the same instances (same stacking,
- * row blocks and results), from the batch handed over as one block-diagonal
- * problem: with x_i = n[0] + ... + n[i-1] and y_i = m[0] + ... + m[i-1],
+ * row blocks and results; not in the paper), from the batch handed over as one
+ * block-diagonal problem: with x_i = n[0] + ... + n[i-1] and y_i = m[0] + ... + m[i-1],
  * instance i owns the variables [x_i, x_i + n[i]) and the rows
  * [y_i, y_i + m[i]) of the stack (N = sum n, M = sum m variables and rows).
  * n, m, m_eq: host arrays of `count` entries, as for pdqp_create_batch.
@@ -229,7 +231,8 @@ pdqp_status pdqp_create_batch_packed(pdqp_handle *out, int32_t count, const int6
 /* Number of instances of a handle (1 for pdqp_create). */
 int32_t pdqp_batch_count(pdqp_handle h);
 
-/* One handle for `count` members of a parameterised family: every member has
+/* One handle for `count` members of a parameterised family (not in the
+ * paper; a batch whose members share their structure): every member has
  * the same Q, A, l, u (given once, as for pdqp_create) and its own objective
  * and right-hand side, row i of C [count x n] and of B [count x m] (float64,
  * row-major, in `mem_space`).  The handle is the one pdqp_create_batch would
@@ -244,7 +247,8 @@ pdqp_status pdqp_create_family(pdqp_handle *out, int32_t count, int64_t n, int64
 /* Per-instance summaries of the last pdqp_solve (infos[count], host). */
 pdqp_status pdqp_batch_info(pdqp_handle h, pdqp_info *infos, int32_t count);
 
-/* Add a low-rank term to the objective: Q_total = Q + F F' with F float32,
+/* Add a low-rank term to the objective (not in the paper, whose Q is one sparse
+ * matrix): Q_total = Q + F F' with F float32,
  * row-major n x r (1 <= r <= 256), applied as F(F'x) (never formed).  The
  * low-rank term is left out of the scaling norms; D2 scales F's rows. */
 pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float *F, int32_t mem_space,
