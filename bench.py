@@ -27,6 +27,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The CPU oracle's timings (cpu_baseline, --impl reference) are reported as one
+# thread: keep numpy's BLAS on one thread before numpy loads (a caller's own
+# setting wins).
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
 
 import numpy as np  # noqa: E402
 
