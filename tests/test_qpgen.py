@@ -88,3 +88,24 @@ def test_seeds_reproduce():
     np.testing.assert_array_equal(a.b, b.b)
     c = qpgen.random_sparse_qp(seed=6)
     assert not np.array_equal(a.c, c.c)
+
+
+def _sectors_per_warp(insts):
+    """Distinct 32-byte sectors of float32 values touched by each 32 consecutive
+    nonzeros of P = [Q | A'] (what one warp of the primal kernel's staging loop
+    gathers), averaged."""
+    Q = sp.block_diag([i.Q for i in insts], format="csr")
+    A = sp.block_diag([i.A for i in insts], format="csr")
+    P = sp.hstack([Q, sp.csr_matrix(A.T)], format="csr")
+    P.sort_indices()
+    col = P.indices.astype(np.int64)
+    g = np.sort((col[:col.size - col.size % 32] * 4 // 32).reshape(-1, 32), axis=1)
+    return float((1 + (np.diff(g, axis=1) != 0).sum(axis=1)).mean())
+
+
+def test_gather_locality_of_the_workloads():
+    """The random large sparse QP gathers from a new sector for almost every
+    nonzero (the kernels' L2 sector bound); the control QPs' banded structure
+    coalesces about 8 nonzeros per sector."""
+    assert _sectors_per_warp([qpgen.large_sparse_qp(n=100_000)]) > 30.0
+    assert _sectors_per_warp(qpgen.mpc_batch(64, seed=qpgen.SEED_BASE + 3)) < 5.0
