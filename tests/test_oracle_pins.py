@@ -342,3 +342,19 @@ def test_restart_variants_converge_and_rapdhg_beats_pdhg():
         assert res.kkt["primal_obj"] == pytest.approx(truth[2], rel=1e-6, abs=1e-6), name
         iters[name] = res.iterations
     assert iters["rapdhg"] < iters["pdhg"]
+
+
+def test_relkkt_when_the_dual_objective_exceeds_the_primal():
+    """Worked by hand: min 1/2 x^2 s.t. x >= 1 (no bounds) at x = 1/2, y = 3.
+    Primal violation 1 - 1/2 over 1 + max(|Ax|, |b|) = 2: 1/4.  Reduced cost
+    Qx - A'y = -5/2 with Lambda = {0}: dual residual 5/2 over 1 + max(1/2, 3, 0):
+    5/8.  Objectives p = 1/8, d = -1/8 + 3 = 23/8: gap |p - d| / (1 + 23/8) =
+    22/31, the largest, so relKKT = 22/31 (the gap is an absolute value)."""
+    p = R.Problem(sp.csr_matrix(np.array([[1.0]])), sp.csr_matrix(np.array([[1.0]])), np.zeros(1),
+                  np.array([1.0]), np.array([-np.inf]), np.array([np.inf]), 0)
+    k = R.kkt_parts(p, np.array([0.5]), np.array([3.0]))
+    assert k["r_primal"] == pytest.approx(1 / 4, abs=1e-15)
+    assert k["r_dual"] == pytest.approx(5 / 8, abs=1e-15)
+    assert (k["primal_obj"], k["dual_obj"]) == (pytest.approx(1 / 8, abs=1e-15), pytest.approx(23 / 8, abs=1e-15))
+    assert k["r_gap"] == pytest.approx(22 / 31, abs=1e-15)
+    assert k["rel_kkt"] == pytest.approx(22 / 31, abs=1e-15)
