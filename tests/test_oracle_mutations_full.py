@@ -1,0 +1,68 @@
+"""More planted mistakes, each run against the complete oracle pin files: the
+oracle, the generators and the tests are copied to a scratch directory, the
+mistake is planted in the copy of the oracle, and the pin files run there in
+a subprocess (the repository's own oracle is never edited).  Every mistake
+must fail at least one pin.  Not planted: replacing the step-growth cap
+min((1 + 1/k) eta_{k-1}, bound_k) by bound_k, an equivalent change (within an
+epoch the min always picks the bound, since bound_k / bound_{k-1} <=
+(k+2)/(k+1) < (k+1)/k)."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_fixed_point.py", "tests/test_oracle_theorem1.py",
+             "tests/test_oracle_infeasibility.py", "tests/test_oracle_lowrank.py",
+             "tests/test_oracle_lanczos_start.py", "tests/test_oracle_classes.py"]
+
+MUTATIONS = {
+    "primal_weight_inverted": ("math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))",
+                               "math.exp(theta * math.log(dx / dy) + (1.0 - theta) * math.log(omega))"),
+    "primal_weight_theta_swapped": ("math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))",
+                                    "math.exp((1.0 - theta) * math.log(dy / dx) + theta * math.log(omega))"),
+    "initial_weight_inverted": ("return nc / nb if (nc > eps_zero and nb > eps_zero) else 1.0",
+                                "return nb / nc if (nc > eps_zero and nb > eps_zero) else 1.0"),
+    "first_step_halved": ("return 1.98 / (q + math.sqrt(4.0 * normA ** 2 + q ** 2))",
+                          "return 0.99 / (q + math.sqrt(4.0 * normA ** 2 + q ** 2))"),
+    "condition_ii_reversed": ("and cand > prev_cand_kkt)", "and cand < prev_cand_kkt)"),
+    "artificial_restart_constant": ("or k >= opts.beta_art * total)", "or k >= opts.beta_nec * total)"),
+    "halving_factor": ("return ax, ay, akkt, akkt <= 0.5 * anchor_kkt",
+                       "return ax, ay, akkt, akkt <= 0.8 * anchor_kkt"),
+    "xbar_from_old_x": ("xbar = (1.0 - 1.0 / beta) * xbar + x_new / beta",
+                        "xbar = (1.0 - 1.0 / beta) * xbar + x / beta"),
+    "steps_swapped": ("tau_p, sigma_d = eta / omega, eta * omega", "tau_p, sigma_d = eta * omega, eta / omega"),
+    "gap_without_abs": ("r_gap = abs(primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))",
+                        "r_gap = (primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))"),
+}
+
+
+def _scratch(tmp_path):
+    for d in ("oracle", "qpgen", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=shutil.ignore_patterns("__pycache__"))
+    return tmp_path
+
+
+def _run_pins(where):
+    env = {**os.environ, "PYTHONDONTWRITEBYTECODE": "1"}
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PIN_FILES],
+                          cwd=where, env=env, capture_output=True, text=True, timeout=900)
+
+
+def test_unmutated_copy_passes(tmp_path):
+    r = _run_pins(_scratch(tmp_path))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_fails_a_pin(tmp_path, name):
+    where = _scratch(tmp_path)
+    src_path = where / "oracle" / "rapdhg.py"
+    src = src_path.read_text()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, name
+    src_path.write_text(src.replace(old, new))
+    r = _run_pins(where)
+    assert r.returncode != 0, f"{name} passed every pin"
