@@ -16,7 +16,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_fixed_point.py", "tests/test_oracle_theorem1.py",
              "tests/test_oracle_infeasibility.py", "tests/test_oracle_lowrank.py",
-             "tests/test_oracle_lanczos_start.py", "tests/test_oracle_classes.py"]
+             "tests/test_oracle_lanczos_start.py", "tests/test_oracle_classes.py",
+             "tests/test_oracle_restart_bookkeeping.py"]
 
 MUTATIONS = {
     "primal_weight_inverted": ("math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))",
@@ -34,6 +35,14 @@ MUTATIONS = {
     "xbar_from_old_x": ("xbar = (1.0 - 1.0 / beta) * xbar + x_new / beta",
                         "xbar = (1.0 - 1.0 / beta) * xbar + x / beta"),
     "steps_swapped": ("tau_p, sigma_d = eta / omega, eta * omega", "tau_p, sigma_d = eta * omega, eta / omega"),
+    "l2_pass_is_l1": ("nu = np.sqrt(np.asarray(absK.multiply(absK).sum(axis=1)).ravel())",
+                      "nu = np.asarray(absK.sum(axis=1)).ravel()"),
+    "anchor_relkkt_not_reset": ("anchor_x, anchor_y, anchor_kkt = x.copy(), y.copy(), cand_kkt",
+                                "anchor_x, anchor_y = x.copy(), y.copy()"),
+    "previous_candidate_kept": ("        anchor_x, anchor_y, anchor_kkt = x.copy(), y.copy(), cand_kkt\n        prev_cand_kkt = None",
+                                "        anchor_x, anchor_y, anchor_kkt = x.copy(), y.copy(), cand_kkt"),
+    "restart_keeps_x_prev": ("        x_prev, xbar, ybar = x.copy(), x.copy(), y.copy()\n        anchor_x",
+                             "        xbar, ybar = x.copy(), y.copy()\n        anchor_x"),
     "gap_without_abs": ("r_gap = abs(primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))",
                         "r_gap = (primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))"),
 }
