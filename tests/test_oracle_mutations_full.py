@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_fixed_point.py", "tests/test_oracle_theorem1.py",
              "tests/test_oracle_infeasibility.py", "tests/test_oracle_lowrank.py",
              "tests/test_oracle_lanczos_start.py", "tests/test_oracle_classes.py",
-             "tests/test_oracle_restart_bookkeeping.py"]
+             "tests/test_oracle_restart_bookkeeping.py", "tests/test_oracle_invariants.py"]
 
 MUTATIONS = {
     "primal_weight_inverted": ("math.exp(theta * math.log(dy / dx) + (1.0 - theta) * math.log(omega))",
@@ -43,6 +43,14 @@ MUTATIONS = {
                                 "        anchor_x, anchor_y, anchor_kkt = x.copy(), y.copy(), cand_kkt"),
     "restart_keeps_x_prev": ("        x_prev, xbar, ybar = x.copy(), x.copy(), y.copy()\n        anchor_x",
                              "        xbar, ybar = x.copy(), y.copy()\n        anchor_x"),
+    "lanczos_absolute_tolerance": (
+        "if abs(theta - theta_prev) <= tol * abs(theta) or beta <= 1e-12 * abs(theta):",
+        "if abs(theta - theta_prev) <= tol or beta <= 1e-12 * abs(theta):"),
+    "x0_not_projected": ("x = proj_X(np.zeros(n) if x0 is None else np.asarray(x0, np.float64) / D2, ps.l, ps.u)",
+                         "x = np.zeros(n) if x0 is None else np.asarray(x0, np.float64) / D2"),
+    "y0_not_projected": ("y = proj_Y(np.zeros(m) if y0 is None else np.asarray(y0, np.float64) / D1, m_eq)",
+                         "y = np.zeros(m) if y0 is None else np.asarray(y0, np.float64) / D1"),
+    "relkkt_on_scaled_problem": ("kkt_cur = rel_kkt(p, *unscale(x, y))", "kkt_cur = rel_kkt(ps, x, y)"),
     "gap_without_abs": ("r_gap = abs(primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))",
                         "r_gap = (primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))"),
 }
