@@ -153,6 +153,26 @@ def test_detection_leaves_feasible_solves_alone(k):
     np.testing.assert_array_equal(a.y, b.y)
 
 
+@pytest.mark.parametrize("s", [1e-6, 1.0, 1e6])
+def test_certificate_tests_are_scale_free(s):
+    """A ray has no natural length: both tests are positively homogeneous,
+    test(s ray) = s test(ray).  The rays here leave a residual 1e-12 of their
+    objective term, far inside eps = 1e-8 relatively but not absolutely once
+    scaled by 1e6."""
+    free2 = R.Problem(sp.csr_matrix((1, 1)), sp.csr_matrix(np.array([[1.0], [1.0]])), np.zeros(1),
+                      np.array([1.0, 2.0]), np.array([-INF]), np.array([INF]), 2)
+    rho = np.array([-1.0 + 1e-12, 1.0])                  # A'rho = 1e-12, b'rho = 1 + 1e-12
+    v1 = R.dual_ray_value(free2, rho, 1e-8)
+    assert v1 == pytest.approx(1.0, rel=1e-11)
+    assert R.dual_ray_value(free2, s * rho, 1e-8) == pytest.approx(s * v1, rel=1e-12)
+    ray = R.Problem(sp.csr_matrix(np.diag([0.0, 1.0])), sp.csr_matrix((0, 2)), np.array([-1.0, 0.0]),
+                    np.zeros(0), np.array([0.0, -INF]), np.array([INF, INF]), 0)
+    d = np.array([1.0, 1e-12])                           # Qd = 1e-12, c'd = -1
+    w1 = R.primal_ray_value(ray, d, 1e-8)
+    assert w1 == 1.0
+    assert R.primal_ray_value(ray, s * d, 1e-8) == pytest.approx(s * w1, rel=1e-15)
+
+
 CLASSES = [qpgen.random_sparse_qp(seed=qpgen.SEED_BASE), *qpgen.mpc_batch(3, seed=qpgen.SEED_BASE + 3),
            qpgen.lasso_qp(), qpgen.huber_qp(), qpgen.svm_qp()]
 
@@ -178,6 +198,9 @@ MUTATIONS = {
     "no_cone_projection": ("d = D2 * recession_project(xs - anchor[0], ps.l, ps.u)", "d = D2 * (xs - anchor[0])"),
     "ineq_rows_two_sided": ("viol[p.m_eq:] = np.maximum(-Ad[p.m_eq:], 0.0)", "pass"),
     "no_unscaling": ("rho = D1 * proj_Y(ys - anchor[1], p.m_eq)", "rho = proj_Y(ys - anchor[1], p.m_eq)"),
+    "farkas_residual_absolute": ("return value if (value > 0 and _inf_norm(g - lam) <= eps * value) else 0.0",
+                                 "return value if (value > 0 and _inf_norm(g - lam) <= eps) else 0.0"),
+    "ray_residual_absolute": ("return -cd if worst <= eps * (-cd) else 0.0", "return -cd if worst <= eps else 0.0"),
 }
 
 
@@ -203,6 +226,13 @@ def _pins_pass(R_):
             _check_ray(inst, r.x)
         for inst in FEASIBLE:
             assert _solve(R_, inst).status == "optimal"
+        free2 = R_.Problem(sp.csr_matrix((1, 1)), sp.csr_matrix(np.array([[1.0], [1.0]])), np.zeros(1),
+                           np.array([1.0, 2.0]), np.array([-INF]), np.array([INF]), 2)
+        rho = np.array([-1.0 + 1e-12, 1.0])
+        assert R_.dual_ray_value(free2, 1e6 * rho, 1e-8) > 0
+        ray = R_.Problem(sp.csr_matrix(np.diag([0.0, 1.0])), sp.csr_matrix((0, 2)), np.array([-1.0, 0.0]),
+                         np.zeros(0), np.array([0.0, -INF]), np.array([INF, INF]), 0)
+        assert R_.primal_ray_value(ray, 1e6 * np.array([1.0, 1e-12]), 1e-8) > 0
     except (AssertionError, FloatingPointError, ZeroDivisionError, ValueError):
         return False
     return True
