@@ -51,6 +51,19 @@ MUTATIONS = {
     "y0_not_projected": ("y = proj_Y(np.zeros(m) if y0 is None else np.asarray(y0, np.float64) / D1, m_eq)",
                          "y = np.zeros(m) if y0 is None else np.asarray(y0, np.float64) / D1"),
     "relkkt_on_scaled_problem": ("kkt_cur = rel_kkt(p, *unscale(x, y))", "kkt_cur = rel_kkt(ps, x, y)"),
+    "no_check_at_max_iter": ("if total % opts.check_period != 0 and total != opts.max_iter:",
+                             "if total % opts.check_period != 0:"),
+    "termination_strict": ("if cand_kkt <= opts.eps:", "if cand_kkt < opts.eps:"),
+    "certificate_average_first": ("    for xs, ys in iterates:\n", "    for xs, ys in reversed(iterates):\n"),
+    "primal_rays_tested_first": (
+        "    for d, rho in rays:\n        v = dual_ray_value(p, rho, eps)\n        if v > 0:\n"
+        "            return \"primal_infeasible\", np.zeros(p.n), rho / v\n"
+        "    for d, rho in rays:\n        v = primal_ray_value(p, d, eps)\n        if v > 0:\n"
+        "            return \"dual_infeasible\", d / v, np.zeros(p.m)\n",
+        "    for d, rho in rays:\n        v = primal_ray_value(p, d, eps)\n        if v > 0:\n"
+        "            return \"dual_infeasible\", d / v, np.zeros(p.m)\n"
+        "    for d, rho in rays:\n        v = dual_ray_value(p, rho, eps)\n        if v > 0:\n"
+        "            return \"primal_infeasible\", np.zeros(p.n), rho / v\n"),
     "gap_without_abs": ("r_gap = abs(primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))",
                         "r_gap = (primal_obj - dual_obj) / (1.0 + max(abs(primal_obj), abs(dual_obj)))"),
 }
