@@ -63,6 +63,8 @@ the design notes of the repository):
   R13 candidate ties pick the average (strict '<' in GetRestartCandidate).
   R14 a low-rank term F F' of Q is applied as F(F'x) and is left out of the
       scaling norms (D2 still scales F).
+  R15 fixed-frequency restarts (restart_rule "fixed") are taken at the first
+      check with k >= K: restarts happen only at checks.
   R18 (not in the paper; optional) infeasibility certificates: at every
       check after the termination and iteration-limit tests, the current and
       the average iterate's displacement from the epoch's anchor, projected
