@@ -67,7 +67,7 @@ def parse():
                     help="skip the side measurement of plain float64 solves")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 2, 256, 512])
+    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 2, 3, 256, 512])
     ap.add_argument("--workload", default="large_sparse_qp",
                     choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws", "gemm", "algorithms"],
                     help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
@@ -79,8 +79,11 @@ def parse():
                          "rAPDHG (iteration SGM10) on a synthetic QP set")
     ap.add_argument("--gemm-size", type=int, default=8192)
     ap.add_argument("--batch", type=int, default=None,
-                    help="instances per step (mpc_batch: 4096, family_ws: 1024)")
-    ap.add_argument("--train", type=int, default=4096, help="family_ws: training solves")
+                    help="instances per step (mpc_batch: 4096, family_ws: members per handle, 2048)")
+    ap.add_argument("--train", type=int, default=50000, help="family_ws: training solves")
+    ap.add_argument("--held", type=int, default=10000, help="family_ws: held-out members solved")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: skip the sub-records of the MPC batch and the learned warm start")
     ap.add_argument("--epochs", type=int, default=20, help="family_ws: training epochs")
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="variables of the workload (m = n/2); smaller only for profiler captures")
@@ -239,7 +242,7 @@ def run_reference(args, world, rank):
                         f"full oracle solves of the first {len(insts)} of the {batch} control QPs per step")
         workload = f"mpc_batch: {batch} control QPs, 12 states, 4 inputs, horizon 10..100"
     else:   # family_ws
-        per_step = args.batch or 1024
+        per_step = args.batch or 2048
         fam = qpgen.family_qp(seed=qpgen.SEED_BASE + 4)
         C, B = fam.params(10 ** 7, 8)
         insts = [dataclasses.replace(fam.base, c=C[i], b=B[i]) for i in range(len(C))]
@@ -498,6 +501,11 @@ def run_ours(args, world, rank, local):
             args.workload == "large_sparse_qp":
         v, t_solve, sample = oracle_sample(inst)
         line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
+    # the other configurations the target compares, as compact sub-records
+    # (their own timing; the line's value stays the n=1e6 solve)
+    if args.workload == "large_sparse_qp" and args.n == 1_000_000 and not args.no_configs:
+        line["configs"] = {"mpc_batch": mpc_record(pdqp, rank, dev, stream),
+                           "family_ws": family_record(pdqp, rank, dev, stream, train=args.train, held=args.held)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -508,15 +516,15 @@ FAMILY_WORKLOAD = ("family_qp n=2e4 m=1e4 (m_eq=5e3): the random_sparse_qp patte
                    "fp32 accumulation")
 
 
-def _family_solve(pdqp, base, C, B, opts, stream, X0=None, Y0=None, chunk=1024):
+def _family_solve(pdqp, base, C, B, opts, stream, X0=None, Y0=None, chunk=2048):
     """Solve members (C, B) in family handles of `chunk`; returns X, Y, infos."""
     import torch
     Xs, Ys, infos = [], [], []
     for s0 in range(0, C.shape[0], chunk):
         c, b = C[s0:s0 + chunk], B[s0:s0 + chunk]
         h = pdqp.family_from_base(base, c, b, stream=stream)
-        x = torch.zeros(c.numel() if hasattr(c, "numel") else c.size, dtype=torch.float64, device="cuda")
-        y = torch.zeros(b.numel() if hasattr(b, "numel") else b.size, dtype=torch.float64, device="cuda")
+        x = torch.zeros(c.numel(), dtype=torch.float64, device="cuda")
+        y = torch.zeros(b.numel(), dtype=torch.float64, device="cuda")
         x0 = None if X0 is None else X0[s0:s0 + chunk].reshape(-1)
         y0 = None if Y0 is None else Y0[s0:s0 + chunk].reshape(-1)
         pdqp.pdqp_solve(h, opts, x0=x0, y0=y0, x_out=x, y_out=y, stream=stream)
@@ -527,29 +535,149 @@ def _family_solve(pdqp, base, C, B, opts, stream, X0=None, Y0=None, chunk=1024):
     return torch.cat(Xs), torch.cat(Ys), infos
 
 
-def run_family_ws(args, world, rank, local):
-    """Configuration 4: train the warm-start network on solver outputs, then
-    time held-out members solved in one family handle from its predictions."""
+def _iters(infos):
+    its = [i.iterations for i in infos]
+    return {"mean": float(np.mean(its)), "median": float(np.median(its)), "max": int(max(its))}
+
+
+def _timed(stream, fn):
+    """Device time (s) of fn's work on `stream` (CUDA events, synchronised)."""
     import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
 
+
+def plain_fp64_cold(pdqp, insts, stream, dev):
+    """Plain rAPDHG as the paper runs it: float64, from the all-zero start, one
+    problem per handle solved after another (each handle built and solved
+    once before the timed region).  Solves per second over `insts`."""
+    import torch
+    o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64)
+    hs, outs = [], []
+    for inst in insts:
+        h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
+                                 device=True)
+        x = torch.zeros(inst.n, dtype=torch.float64, device=dev)
+        y = torch.zeros(max(inst.m, 1), dtype=torch.float64, device=dev)
+        pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
+        hs.append(h)
+        outs.append((x, y))
+
+    def run():
+        return [pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)[1] for h, (x, y) in zip(hs, outs)]
+    t, infos = _timed(stream, run)
+    for h in hs:
+        pdqp.pdqp_destroy(h)
+    return {"value": len(insts) / t, "unit": "solves/s", "problems": len(insts),
+            "how": "float64, all-zero start, one problem per handle, solved one after another",
+            "iterations": _iters(infos), "rel_kkt_max": max(i.rel_kkt for i in infos),
+            "statuses_ok": bool(all(i.status == 0 for i in infos))}
+
+
+def _roofline_of(prof, hbm_peak, hbm_src, note):
+    kinds = {k: v for k, v in prof.items() if k in ("dual", "primal") and v["launches"]}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = prof[dom]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    return {"bound": "hbm", "achieved": d["bytes"] / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": d["bytes"] / avg_s / 1e9 / hbm_peak, "peak_source": hbm_src,
+            "kernel": {"dual": "k_dual", "primal": "k_primal"}[dom], "avg_launch_us": avg_s * 1e6,
+            "launches": d["launches"], "algorithmic_bytes_per_launch": d["bytes"],
+            "bytes_counted": note, "traffic": None, "timing": PROFILED_PASS}
+
+
+MPC_WORKLOAD = ("mpc_batch: 4096 control QPs (12 states, 4 inputs, horizon U{10..100}; dynamics I + N(0,0.1^2) as "
+                "banded equality rows; |u| <= 1, |x| <= 5; Q diag U(0.1,1)), one batched handle")
+
+
+def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True):
+    """Configuration 4096 MPC QPs: the batched mixed-precision solve (one
+    handle, CUDA-graph chunks) against plain float64 cold solves of the same
+    problems, with the dominant kernel's roofline and an end-to-end leg."""
+    import torch
     import qpgen
-    from paper_2311_07710_gb300 import pdqp
+    insts = qpgen.mpc_batch(4096, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
+    N, M = sum(i.n for i in insts), sum(i.m for i in insts)
+    opts = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_MIXED)
+    h = pdqp.batch_from_instances(insts, device=True)
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+    y = torch.zeros(M, dtype=torch.float64, device=dev)
+    pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream)
+    l0 = pdqp.pdqp_launch_count()
+    t, _ = _timed(stream, lambda: [pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream) for _ in range(steps)])
+    launches = pdqp.pdqp_launch_count() - l0
+    infos = pdqp.pdqp_batch_info(h)
+    value = steps * len(insts) / t
+    prof = profiled_pass(pdqp, h, lambda: pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream), 1, dev)
+    # the same handle in plain float64 from the zero start (batched)
+    o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64)
+    pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
+    t64, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream))
+    infos64 = pdqp.pdqp_batch_info(h)
+    pdqp.pdqp_destroy(h)
+    plain = plain_fp64_cold(pdqp, insts[:plain_sample], stream, dev)
+    hbm_peak, hbm_src = peak_of("hbm_gbs")
+    rec = {"workload": MPC_WORKLOAD, "metric": "solves/s to 1e-6 relKKT", "value": value, "unit": "solves/s",
+           "precision": "mixed (float32 SpMV, float64 checks)", "steps": steps, "ms_per_step": 1e3 * t / steps,
+           "iterations": _iters(infos), "rel_kkt_max": max(i.rel_kkt for i in infos),
+           "statuses_ok": bool(all(i.status == 0 for i in infos)), "gpu_launches": launches,
+           "batched_fp64_cold": {"value": len(insts) / t64, "unit": "solves/s", "iterations": _iters(infos64),
+                                 "rel_kkt_max": max(i.rel_kkt for i in infos64)},
+           "plain_fp64_cold": plain, "speedup_vs_plain_fp64_cold": value / plain["value"],
+           "kernel_ms": {k: v["ms"] for k, v in prof.items()},
+           "roofline": _roofline_of(prof, hbm_peak, hbm_src, "each launch's bytes over the instances running "
+                                                               "at that launch (every problem's own matrix)")}
+    if e2e:
+        pk = pdqp.pack_instances(insts)
+        host = [pinned_copy(pk[k]) for k in ("Q_rowptr", "Q_col", "Q_val", "A_rowptr", "A_col", "A_val",
+                                             "c", "b", "l", "u")]
+        xh, yh = pinned_copy(np.zeros(N)), pinned_copy(np.zeros(M))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        he = pdqp.pdqp_create_batch_packed(pk["n"], pk["m"], pk["m_eq"], *host, stream=stream)
+        st = pdqp.pdqp_solve(he, opts, x_out=xh, y_out=yh, stream=stream)[0]
+        pdqp.pdqp_destroy(he)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        rec["e2e"] = {"value": len(insts) / te, "unit": "solves/s", "h2d_bytes_per_step": int(sum(a.nbytes for a in host)),
+                      "d2h_bytes_per_step": int(xh.nbytes + yh.nbytes),
+                      "calls": "pdqp_create_batch_packed + pdqp_solve + pdqp_destroy, pinned host arrays",
+                      "worst_status": int(st)}
+    return rec
 
-    pdqp.load()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
-    opts = pdqp.pdqp_default_options(precision=prec)
+
+FAMILY_WORKLOAD = ("family_qp n=2e4 m=1e4 (m_eq=5e3): the random_sparse_qp pattern scaled (A 10 nnz/row, "
+                   "Q = B'B + 0.01 I with B 5 nnz/row), c = c_bar + 0.1 N(0,1), b = b_bar + 0.1 N(0,1) per member; "
+                   "warm start: projection 3e4 -> 1024 (fixed), 3 x (1024, ReLU), output 3e4, bf16 weights, "
+                   "fp32 accumulation")
+
+
+def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, epochs=20, plain_sample=32,
+                  e2e=True, spmv_threads=0, precision="mixed"):
+    """Configuration learned warm start: `train` solver-produced solutions of
+    the family train the network; `held` held-out members are then solved in
+    family handles of `chunk` from its predictions (timed: inference + solve).
+    Beside it, on the first held-out handle: cold and mean-solution starts,
+    the batched float64 cold solve, and plain float64 cold solves of a sample
+    of members, one per handle."""
+    import dataclasses
+    import torch
+    import qpgen
+    prec = pdqp.PDQP_PREC_MIXED if precision == "mixed" else pdqp.PDQP_PREC_FP64
+    opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=spmv_threads)
     fam = qpgen.family_qp(seed=qpgen.SEED_BASE + 4 + 1000 * rank)
     n, m = fam.base.n, fam.base.m
-    batch = args.batch or 1024
 
     # ---- training data from the solver, then the network (untimed) ----
     t0 = time.perf_counter()
-    Ctr, Btr = fam.params(0, args.train)
+    Ctr, Btr = fam.params(0, train)
     Ctr_d, Btr_d = torch.from_numpy(Ctr).to(dev), torch.from_numpy(Btr).to(dev)
-    X, Y, info_tr = _family_solve(pdqp, fam.base, Ctr_d, Btr_d, opts, stream)
+    X, Y, info_tr = _family_solve(pdqp, fam.base, Ctr_d, Btr_d, opts, stream, chunk=chunk)
     torch.cuda.synchronize(dev)
     t_data = time.perf_counter() - t0
     proj, layers = qpgen.warmstart_params(qpgen.SEED_BASE + 40 + rank, n + m, 1024, 1024, 3)
@@ -559,129 +687,149 @@ def run_family_ws(args, world, rank, local):
         pdqp.pdqp_ws_set_params(w, j, W, b, stream=stream)
     t0 = time.perf_counter()
     pdqp.pdqp_ws_fit(w, Ctr_d, Btr_d, X, Y, stream=stream)
-    losses = pdqp.pdqp_ws_train(w, Ctr_d, Btr_d, X, Y, epochs=args.epochs, batch=256, lr=1e-3, seed=1,
-                                stream=stream)
+    losses = pdqp.pdqp_ws_train(w, Ctr_d, Btr_d, X, Y, epochs=epochs, batch=256, lr=1e-3, seed=1, stream=stream)
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     Xmean, Ymean = X.mean(dim=0), Y.mean(dim=0)
     del X, Y, Ctr_d, Btr_d
+    torch.cuda.empty_cache()
 
-    # ---- held-out members, resident in HBM ----
-    Cte, Bte = fam.params(10 ** 7 + 10 ** 5 * rank, batch)
+    # ---- held-out members, resident in HBM: inference + solve per handle ----
+    Cte, Bte = fam.params(10 ** 7 + 10 ** 5 * rank, held)
     C_d, B_d = torch.from_numpy(Cte).to(dev), torch.from_numpy(Bte).to(dev)
-    X0 = torch.zeros((batch, n), dtype=torch.float64, device=dev)
-    Y0 = torch.zeros((batch, m), dtype=torch.float64, device=dev)
-    h = pdqp.family_from_base(fam.base, C_d, B_d, stream=stream)
-    x = torch.zeros(batch * n, dtype=torch.float64, device=dev)
-    y = torch.zeros(batch * m, dtype=torch.float64, device=dev)
+    t_warm, warm_infos, launches, prof = 0.0, [], 0, None
+    first = None
+    for s0 in range(0, held, chunk):
+        c, b = C_d[s0:s0 + chunk], B_d[s0:s0 + chunk]
+        k = c.shape[0]
+        h = pdqp.family_from_base(fam.base, c, b, stream=stream)
+        X0 = torch.zeros((k, n), dtype=torch.float64, device=dev)
+        Y0 = torch.zeros((k, m), dtype=torch.float64, device=dev)
+        x = torch.zeros(k * n, dtype=torch.float64, device=dev)
+        y = torch.zeros(k * m, dtype=torch.float64, device=dev)
 
-    def step(warm):
-        if warm:
-            pdqp.pdqp_ws_infer(w, C_d, B_d, X0, Y0, stream=stream)
+        def step():
+            pdqp.pdqp_ws_infer(w, c, b, X0, Y0, stream=stream)
             return pdqp.pdqp_solve(h, opts, x0=X0.view(-1), y0=Y0.view(-1), x_out=x, y_out=y, stream=stream)
-        return pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream)
+        l0 = pdqp.pdqp_launch_count()
+        t, _ = _timed(stream, step)
+        launches += pdqp.pdqp_launch_count() - l0
+        t_warm += t
+        warm_infos += pdqp.pdqp_batch_info(h)
+        if first is None:
+            first = (h, c, b, k, x, y, X0, Y0)
+            prof = profiled_pass(pdqp, h, step, 1, dev)
+        else:
+            pdqp.pdqp_destroy(h)
+    value = held / t_warm
 
-    for _ in range(args.warmup):
-        step(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = pdqp.pdqp_launch_count()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step(True)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    launches = pdqp.pdqp_launch_count() - l0
-    barrier(world)
-    clk = clocks.stop()
-    t_ms = allreduce_max(ev0.elapsed_time(ev1), world, dev)
-    value = world * args.steps * batch / (t_ms / 1e3)
-    warm_infos = pdqp.pdqp_batch_info(h)
-    Xw, Yw = x.view(batch, n).clone(), y.view(batch, m).clone()
-    prof = profiled_pass(pdqp, h, lambda: step(True), args.steps, dev)
-    # cold start and mean-solution start on the same members (one solve each)
-    torch.cuda.synchronize(dev)
-    ev0.record(stream)
-    step(False)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    cold_s = ev0.elapsed_time(ev1) / 1e3
+    # ---- the first handle's members from other starts and in plain float64 ----
+    h, c, b, k, x, y, X0, Y0 = first
+    Xw, Yw = X0.clone(), Y0.clone()
+    t_cold, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream))
     cold_infos = pdqp.pdqp_batch_info(h)
-    Xc, Yc = x.view(batch, n).clone(), y.view(batch, m).clone()
-    pdqp.pdqp_solve(h, opts, x0=Xmean.repeat(batch), y0=Ymean.repeat(batch), x_out=x, y_out=y, stream=stream)
+    Xc, Yc = x.view(k, n).clone(), y.view(k, m).clone()
+    t_mean, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, opts, x0=Xmean.repeat(k), y0=Ymean.repeat(k), x_out=x,
+                                                        y_out=y, stream=stream))
     mean_infos = pdqp.pdqp_batch_info(h)
+    o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, spmv_threads=spmv_threads)
+    t64, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream))
+    infos64 = pdqp.pdqp_batch_info(h)
     rel = lambda P, Q: float(torch.linalg.norm(P - Q) / torch.linalg.norm(Q))
-    pred_err = rel(torch.cat([X0, Y0], 1), torch.cat([Xc, Yc], 1))
-    mean_err = rel(torch.cat([Xmean.expand(batch, n), Ymean.expand(batch, m)], 1), torch.cat([Xc, Yc], 1))
+    pred_err = rel(torch.cat([Xw, Yw], 1), torch.cat([Xc, Yc], 1))
+    mean_err = rel(torch.cat([Xmean.expand(k, n), Ymean.expand(k, m)], 1), torch.cat([Xc, Yc], 1))
+    pdqp.pdqp_destroy(h)
+    Cp, Bp = Cte[:plain_sample], Bte[:plain_sample]
+    members = [dataclasses.replace(fam.base, c=Cp[i], b=Bp[i]) for i in range(len(Cp))]
+    plain = plain_fp64_cold(pdqp, members, stream, dev)
 
     # ---- end to end: host (C, B) in, handle + inference + solve, host (x, y) out ----
-    # the inputs and outputs live in pinned host memory (filled before the timed region)
-    import types
-    base = fam.base
-    pbase = types.SimpleNamespace(
-        n=base.n, m=base.m, m_eq=base.m_eq, l=pinned_copy(base.l), u=pinned_copy(base.u),
-        Q=types.SimpleNamespace(indptr=pinned_copy(base.Q.indptr.astype(np.int32)),
-                                indices=pinned_copy(base.Q.indices.astype(np.int32)), data=pinned_copy(base.Q.data)),
-        A=types.SimpleNamespace(indptr=pinned_copy(base.A.indptr.astype(np.int32)),
-                                indices=pinned_copy(base.A.indices.astype(np.int32)), data=pinned_copy(base.A.data)))
-    Cp, Bp = pinned_copy(Cte), pinned_copy(Bte)
-    xh, yh = pinned_copy(np.zeros(batch * n)), pinned_copy(np.zeros(batch * m))
-    X0h, Y0h = pinned_copy(np.zeros((batch, n))), pinned_copy(np.zeros((batch, m)))
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    e2e_status = 0
-    for _ in range(args.e2e_steps):
-        he = pdqp.family_from_base(pbase, Cp, Bp, stream=stream)
-        pdqp.pdqp_ws_infer(w, Cp, Bp, X0h, Y0h, stream=stream)
-        e2e_status = max(e2e_status, pdqp.pdqp_solve(he, opts, x0=X0h.reshape(-1), y0=Y0h.reshape(-1), x_out=xh,
-                                                     y_out=yh, stream=stream)[0])
+    e2e_rec = None
+    if e2e:
+        import types
+        base = fam.base
+        pbase = types.SimpleNamespace(
+            n=base.n, m=base.m, m_eq=base.m_eq, l=pinned_copy(base.l), u=pinned_copy(base.u),
+            Q=types.SimpleNamespace(indptr=pinned_copy(base.Q.indptr.astype(np.int32)),
+                                    indices=pinned_copy(base.Q.indices.astype(np.int32)),
+                                    data=pinned_copy(base.Q.data)),
+            A=types.SimpleNamespace(indptr=pinned_copy(base.A.indptr.astype(np.int32)),
+                                    indices=pinned_copy(base.A.indices.astype(np.int32)),
+                                    data=pinned_copy(base.A.data)))
+        Cph, Bph = pinned_copy(Cte[:chunk]), pinned_copy(Bte[:chunk])
+        kk = Cph.shape[0]
+        xh, yh = pinned_copy(np.zeros(kk * n)), pinned_copy(np.zeros(kk * m))
+        X0h, Y0h = pinned_copy(np.zeros((kk, n))), pinned_copy(np.zeros((kk, m)))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        he = pdqp.family_from_base(pbase, Cph, Bph, stream=stream)
+        pdqp.pdqp_ws_infer(w, Cph, Bph, X0h, Y0h, stream=stream)
+        st = pdqp.pdqp_solve(he, opts, x0=X0h.reshape(-1), y0=Y0h.reshape(-1), x_out=xh, y_out=yh,
+                             stream=stream)[0]
         pdqp.pdqp_destroy(he)
-    torch.cuda.synchronize(dev)
-    e2e_s = allreduce_max(time.perf_counter() - t0, world, dev)
-    e2e_value = world * args.e2e_steps * batch / e2e_s if args.e2e_steps > 0 else None
-    h2d = Cte.nbytes + Bte.nbytes + sum(a.nbytes for a in (fam.base.Q.indptr, fam.base.Q.indices, fam.base.Q.data,
-                                                             fam.base.A.indptr, fam.base.A.indices, fam.base.A.data,
-                                                             fam.base.l, fam.base.u))
-    pdqp.pdqp_destroy(h)
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        h2d = Cph.nbytes + Bph.nbytes + sum(a.nbytes for a in (base.Q.indptr, base.Q.indices, base.Q.data,
+                                                                base.A.indptr, base.A.indices, base.A.data,
+                                                                base.l, base.u))
+        e2e_rec = {"value": kk / te, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(xh.nbytes + yh.nbytes), "members_per_step": kk,
+                   "calls": "pdqp_create_family + pdqp_ws_infer + pdqp_solve + pdqp_destroy, pinned host arrays",
+                   "worst_status": int(st)}
     pdqp.pdqp_ws_destroy(w)
-
     hbm_peak, hbm_src = peak_of("hbm_gbs")
-    kinds = {k: v for k, v in prof.items() if k in ("dual", "primal") and v["launches"]}
-    dom = max(kinds, key=lambda k: kinds[k]["ms"])
-    d = prof[dom]
-    avg_s = d["ms"] / d["launches"] / 1e3
-    kname = {"dual": "k_dual", "primal": "k_primal"}[dom]
-    roof = {"bound": "hbm", "achieved": d["bytes"] / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-            "frac": d["bytes"] / avg_s / 1e9 / hbm_peak, "peak_source": hbm_src,
-            "kernel": kname, "avg_launch_us": avg_s * 1e6, "launches": d["launches"],
-            "algorithmic_bytes_per_launch": d["bytes"], "traffic": None, "timing": PROFILED_PASS}
-    it = lambda infos: {"mean": float(np.mean([i.iterations for i in infos])),
-                        "max": int(max(i.iterations for i in infos))}
-    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic (seeded generator)",
-            "config": {"workload": FAMILY_WORKLOAD, "held_out_per_step": batch, "train_solves": args.train,
-                       "epochs": args.epochs, "precision": args.precision, "eps": 1e-6,
-                       "step": "network inference + one family-handle solve of the held-out members from it",
-                       "l2": "inputs larger than L2 (matrices >= 9 GB), no flush", "parallelism": f"replicas x{world}"},
-            "cold_start": {"value": batch / cold_s, "unit": "solves/s", "iterations": it(cold_infos)},
-            "warm_start": {"iterations": it(warm_infos), "prediction_rel_error": pred_err},
-            "mean_solution_start": {"iterations": it(mean_infos), "rel_error": mean_err},
-            "statuses_ok": bool(all(i.status == 0 for i in warm_infos + cold_infos + mean_infos + info_tr)),
-            "rel_kkt_max": max(i.rel_kkt for i in warm_infos),
-            "training": {"data_s": t_data, "train_s": t_train, "loss_first": float(losses[0]),
-                         "loss_last": float(losses[-1])},
-            "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
-            "roofline": roof,
-            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(xh.nbytes + yh.nbytes), "worst_status": e2e_status},
-            "gpu_launches": launches, "clocks": clk}
+    rec = {"workload": FAMILY_WORKLOAD, "metric": "solves/s to 1e-6 relKKT", "value": value, "unit": "solves/s",
+           "precision": precision, "train_solves": train, "held_out": held, "members_per_handle": chunk,
+           "epochs": epochs, "step": "network inference + one family-handle solve from its prediction",
+           "ms_per_member": 1e3 * t_warm / held, "gpu_launches": launches,
+           "iteration_variant": warm_infos[0].spmv_threads,
+           "warm_start": {"iterations": _iters(warm_infos), "prediction_rel_error": pred_err},
+           "cold_start": {"value": k / t_cold, "unit": "solves/s", "iterations": _iters(cold_infos)},
+           "mean_solution_start": {"value": k / t_mean, "unit": "solves/s", "iterations": _iters(mean_infos),
+                                   "rel_error": mean_err},
+           "batched_fp64_cold": {"value": k / t64, "unit": "solves/s", "iterations": _iters(infos64),
+                                 "rel_kkt_max": max(i.rel_kkt for i in infos64)},
+           "plain_fp64_cold": plain, "speedup_vs_plain_fp64_cold": value / plain["value"],
+           "statuses_ok": bool(all(i.status == 0 for i in warm_infos + cold_infos + mean_infos + infos64 + info_tr)),
+           "rel_kkt_max": max(i.rel_kkt for i in warm_infos),
+           "training": {"data_s": t_data, "train_s": t_train, "loss_first": float(losses[0]),
+                        "loss_last": float(losses[-1])},
+           "kernel_ms": {kk: v["ms"] for kk, v in prof.items()},
+           "roofline": _roofline_of(prof, hbm_peak, hbm_src, "Section 8(d)'s count: the shared matrix once per "
+                                                              "launch, each running member's vectors once")}
+    if e2e_rec is not None:
+        rec["e2e"] = e2e_rec
+    return rec
+
+
+def run_family_ws(args, world, rank, local):
+    """Configuration learned warm start as its own bench line."""
+    import torch
+    from paper_2311_07710_gb300 import pdqp
+
+    pdqp.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    rec = family_record(pdqp, rank, dev, stream, train=args.train, held=args.held, chunk=args.batch or 2048,
+                        epochs=args.epochs, e2e=args.e2e_steps > 0, spmv_threads=args.spmv_threads,
+                        precision=args.precision)
+    barrier(world)
+    clk = clocks.stop()
+    value = allreduce_max(rec["ms_per_member"], world, dev)
+    line = {"metric": METRIC, "value": world * 1e3 / value, "unit": "solves/s", "n_gpus": world,
+            "steps": math.ceil(args.held / (args.batch or 2048)), "warmup": 0,
+            "ms_per_step": value * (args.batch or 2048),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic (seeded generator)",
+            "config": {"workload": FAMILY_WORKLOAD, "train_solves": args.train, "held_out": args.held,
+                       "l2": "inputs larger than L2 (matrices and vectors >= 9 GB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": rec["gpu_launches"], "clocks": clk}
+    line.update({k: v for k, v in rec.items() if k not in ("value", "gpu_launches")})
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -117,7 +117,14 @@ typedef struct {
                                 cluster barrier after each half-step (problems of at
                                 most 64 row blocks of A and of P, no row longer than a
                                 row block, no low-rank term; else PDQP_ERR_INVALID),
-                                0 = autotuned: the first full chunk of a handle's
+                                3 = family handles (pdqp_create_family; no row longer
+                                than a row block, no low-rank term; else
+                                PDQP_ERR_INVALID): the iteration vectors interleaved
+                                by member, v[j * members + i], one warp per row for 32
+                                members, so one matrix entry meets 32 members in one
+                                coalesced load,
+                                0 = autotuned: 3 for an eligible family handle, else
+                                the first full chunk of a handle's
                                 first solve times two rounds of 4 iterations of each
                                 eligible variant and the handle keeps the fastest (all
                                 variants give bitwise identical iterates) */
@@ -277,8 +284,38 @@ pdqp_status pdqp_solve_batch(int32_t count, const pdqp_handle *hs, const pdqp_op
 
 /* Raw iterate state after the last solve, in original coordinates:
  * x, x_bar (n) and y, y_bar (m) of Algorithm 1 (any pointer may be NULL). */
-pdqp_status pdqp_get_state(pdqp_handle h, double *x, double *y, double *xbar, double *ybar,
-                           int32_t mem_space, void *stream);
+pdqp_status pdqp_get_iterates(pdqp_handle h, double *x, double *y, double *xbar, double *ybar,
+                              int32_t mem_space, void *stream);
+
+/* Complete solver state after the last solve, for checkpoint and resume: the
+ * iterates and averages of Algorithm 1, the restart anchor z^{n,0}, and the
+ * per-instance scalars of Section 6's rules (primal weight omega, the step
+ * size eta, the anchor's relKKT, the previous candidate's relKKT, the epoch
+ * and total iteration counters, the restart count, the spectral norms), the
+ * preprocessing scaling (Section 5) and the step sizes tabulated for the
+ * current check period.  In mixed precision it also holds the float64 base
+ * and the float32 deltas and shifted data.
+ *
+ * buf (HOST memory, caller-owned) receives an opaque blob of this library
+ * version; with buf = NULL only *bytes is set to the size needed.  On entry
+ * *bytes is the capacity of buf, on return the size written.  Needs a solve
+ * on the handle first (else PDQP_ERR_INVALID); synchronises `stream`.  The
+ * blob of a batch handle holds every instance. */
+pdqp_status pdqp_get_state(pdqp_handle h, void *buf, size_t *bytes, void *stream);
+
+/* Load a state from pdqp_get_state into a handle of the same problem (the
+ * same sizes and nonzero counts; a low-rank term set as before).  The next
+ * pdqp_solve on the handle continues from it instead of starting afresh: no
+ * preprocessing, norm estimate or initial point (x0 and y0 must be NULL), and
+ * an instance that the iteration limit stopped runs on (Section 5's
+ * termination test is applied again at its next check).  That solve must use
+ * the saved solve's precision, check_period, step, restart and primal-weight
+ * options (else PDQP_ERR_INVALID) and a larger max_iter (a total count,
+ * including the iterations before the save).  It then follows the trajectory
+ * an uninterrupted solve would have taken, bit for bit.  The blob is copied;
+ * synchronises `stream`.  Errors: PDQP_ERR_INVALID for a blob of another
+ * version or problem, or one shorter than its header says. */
+pdqp_status pdqp_set_state(pdqp_handle h, const void *buf, size_t bytes, void *stream);
 
 /* Relative KKT error (Section 5 "Progress metric", equality/bound form) of a
  * caller-given (x, y) on the handle's original problem, computed on the
@@ -290,10 +327,9 @@ pdqp_status pdqp_kkt(pdqp_handle h, const double *x, const double *y, double *pa
 /* Allocation-free relative KKT error, for callers that cannot allocate device
  * memory once running: real-time control loops (an MPC controller re-solving
  * every few milliseconds must not block on the allocator or synchronise the
- * device) and code running under CUDA stream capture or a fixed device-memory
- * budget.  The paper has no counterpart; it is a variant of pdqp_kkt that
- * needs no handle and calls no cudaMalloc, cudaFree or allocating library
- * routine.
+ * device) and processes held to a fixed device-memory budget after start-up.
+ * The paper has no counterpart; it is a variant of pdqp_kkt that needs no
+ * handle and calls no cudaMalloc, cudaFree or allocating library routine.
  *
  * All array arguments are DEVICE pointers owned by the caller: the CSR of Q
  * (n rows, nnz_Q entries), of A (m rows) and of its transpose A' (n rows, the
@@ -301,6 +337,13 @@ pdqp_status pdqp_kkt(pdqp_handle h, const double *x, const double *y, double *pa
  * (x[n], y[m]) in original coordinates, and parts[6] which receives r_primal,
  * r_dual, r_gap, rel_kkt, primal_obj, dual_obj.  The work is enqueued on
  * `stream` and the call returns without synchronising.
+ *
+ * Errors: PDQP_ERR_INVALID for bad sizes, a missing array or an array that is
+ * not device (or managed) memory, all before any device work.  The CONTENTS
+ * of the CSR arrays are not validated: a decreasing row pointer or a column
+ * index out of range (>= n for Q and A, >= m for A') is undefined behaviour.
+ * PDQP_ERR_CUDA when an error was already pending on the calling thread (it is
+ * left in place and nothing is launched) or a launch of this call failed.
  *
  * Limits: n <= 65536 and m <= 65536; larger problems return PDQP_ERR_INVALID
  * before any device work.  The partial sums live in one 2 MiB array in the

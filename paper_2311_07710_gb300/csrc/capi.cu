@@ -39,6 +39,18 @@ struct pdqp_problem {
   std::vector<void*> allocs;
   int tuned_nt = 0;                                   // autotuned iteration-kernel variant (0: not yet)
   cudaEvent_t tune_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // Where the last solve stopped (what pdqp_get_state exports): its parameters,
+  // the step-table position (iterations run since the table was last filled;
+  // 0 at a check) and the iterations of the solve loop.
+  bool solved = false;
+  SolveParams end_p{};
+  int end_pos = 0;
+  long long end_k_total = 0;
+  // A state loaded by pdqp_set_state: the next solve continues from it.
+  bool resume = false;
+  SolveParams resume_p{};
+  int resume_pos = 0, resume_recheck = 0;
+  long long resume_k_total = 0;
 };
 
 static thread_local std::string g_create_error;
@@ -321,6 +333,18 @@ void alloc_mixed(pdqp_problem* h) {
   h->mixed_ready = true;
 }
 
+// The member-interleaved vectors of a family handle for one precision (on
+// the first solve that uses them).
+void alloc_il(pdqp_problem* h, bool mixed) {
+  Work& w = h->w;
+  const size_t ld = (size_t)w.fam_ld, n = (size_t)w.fam_n, m = (size_t)w.fam_m;
+  const size_t len[IL_SLOTS] = {n + m, n + m, n, n, n, m, n, n, n, m, m};
+  for (int k = 0; k < IL_SLOTS; ++k) {
+    if (mixed && !w.ilf[k]) w.ilf[k] = dalloc<float>(h, len[k] * ld);
+    if (!mixed && !w.ild[k]) w.ild[k] = dalloc<double>(h, len[k] * ld);
+  }
+}
+
 SolveParams make_params(const pdqp_options& o) {
   SolveParams p{};
   p.step_rule = o.step_rule;
@@ -354,9 +378,9 @@ void validate_options(const pdqp_options& o) {
   if ((o.restart_rule == PDQP_RESTART_FIXED || o.step_rule == PDQP_STEP_THEORY) && o.fixed_K < 1)
     bad("options.fixed_K must be >= 1");
   if (o.norm_iters < 1 || o.norm_iters > 512) bad("options.norm_iters must be in [1, 512]");
-  if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 2 && o.spmv_threads != 256 &&
-      o.spmv_threads != 512)
-    bad("options.spmv_threads must be 0, 1, 2, 256 or 512");
+  if (o.spmv_threads != 0 && o.spmv_threads != 1 && o.spmv_threads != 2 && o.spmv_threads != 3 &&
+      o.spmv_threads != 256 && o.spmv_threads != 512)
+    bad("options.spmv_threads must be 0, 1, 2, 3, 256 or 512");
   if (o.detect_infeasibility != 0 && o.detect_infeasibility != 1) bad("options.detect_infeasibility must be 0 or 1");
   if (o.detect_infeasibility && !(o.eps_infeasible > 0.0 && o.eps_infeasible < 1.0))
     bad("options.eps_infeasible must be in (0, 1)");
@@ -402,7 +426,7 @@ void fill_info(pdqp_info* info, const DevState& S, pdqp_status status, bool lanc
 // launch only those blocks (direct launches sized by the last check's counts)
 // instead of replaying the full-grid chunk graph.
 bool compact_now(const Work& w, const SolveParams& p) {
-  if (w.count <= 1 || p.spmv_threads == 1 || p.spmv_threads == 2) return false;
+  if (w.count <= 1 || p.spmv_threads == 1 || p.spmv_threads == 2 || p.spmv_threads == 3) return false;
   return 2LL * w.bst_host->act_P < (long long)w.P.nblk;
 }
 
@@ -483,11 +507,37 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     throw Fail{PDQP_ERR_INVALID, "options.spmv_threads = 2 needs at most 64 row blocks of A and of P, no row "
                                  "longer than a row block, no low-rank term and 3n + 2m values within 200 KB"};
   if (cluster_ok) pdqp::prepare_chunk_cluster();
+  // family handles run on member-interleaved vectors unless a row-block
+  // variant is asked for (no low-rank term, no long rows)
+  const bool il_ok = w.fam_il && w.r == 0;
+  if (o.spmv_threads == 3 && !il_ok)
+    throw Fail{PDQP_ERR_INVALID, "options.spmv_threads = 3 needs a family handle without long rows or low-rank term"};
+  const bool use_il = il_ok && (o.spmv_threads == 0 || o.spmv_threads == 3);
   if (mixed) alloc_mixed(h);
+  if (use_il) alloc_il(h, mixed);
   w.detect = o.detect_infeasibility ? 1 : 0;
   w.eps_inf = o.eps_infeasible;
   if (w.detect) alloc_infeas(h, s);
   SolveParams p = make_params(o);
+  if (use_il) p.spmv_threads = 3;
+
+  // a state loaded by pdqp_set_state: the solve continues from it, so the
+  // parameters that shape the trajectory must be the saved solve's
+  const bool resuming = h->resume;
+  if (resuming) {
+    const SolveParams& q = h->resume_p;
+    if (x0 || y0) throw Fail{PDQP_ERR_INVALID, "a resumed solve starts from the loaded state: x0 and y0 must be NULL"};
+    if (p.step_rule != q.step_rule || p.restart_rule != q.restart_rule || p.accelerate != q.accelerate ||
+        p.fixed_K != q.fixed_K || p.check_period != q.check_period || p.mixed != q.mixed ||
+        p.beta_suff != q.beta_suff || p.beta_nec != q.beta_nec || p.beta_art != q.beta_art ||
+        p.pw_theta != q.pw_theta || p.eps_zero != q.eps_zero)
+      throw Fail{PDQP_ERR_INVALID, "a resumed solve needs the saved solve's precision, check period, step, "
+                                   "restart and primal-weight options"};
+    if (o.max_iter <= h->resume_k_total)
+      throw Fail{PDQP_ERR_INVALID, "options.max_iter must exceed the iterations of the loaded state"};
+  }
+  h->resume = false;
+  h->solved = false;
 
   // start point in device memory
   const double* dx0 = x0;
@@ -505,17 +555,20 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     h->graph.valid = false;
   }
   CK(cudaEventRecord(h->ev[0], s));
-  // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle
-  pdqp::scale_reset(w, s);
-  if (o.scaling) {
-    for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(w, 0, s);
-    if (o.l2_scaling) pdqp::scale_pass(w, 1, s);
-    if (o.pock_chambolle) pdqp::scale_pass(w, 2, s);
+  // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle (a resumed
+  // solve has its scaling vector from the loaded state)
+  if (!resuming) {
+    pdqp::scale_reset(w, s);
+    if (o.scaling) {
+      for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(w, 0, s);
+      if (o.l2_scaling) pdqp::scale_pass(w, 1, s);
+      if (o.pock_chambolle) pdqp::scale_pass(w, 2, s);
+    }
   }
   pdqp::scale_apply(w, mixed, s);
 
-  // spectral norms of the scaled matrices
-  const bool run_lanczos = !(o.norm_A > 0.0 && o.norm_Q > 0.0);
+  // spectral norms of the scaled matrices (a resumed solve keeps its own)
+  const bool run_lanczos = !resuming && !(o.norm_A > 0.0 && o.norm_Q > 0.0);
   if (run_lanczos) {
     pdqp::lanczos_init(w, mixed, s);
     for (int t = 0; t < o.norm_iters; ++t) {
@@ -527,14 +580,35 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       }
     }
   }
-  pdqp::norms_finish(w, o.norm_A, o.norm_Q, s);
+  if (!resuming) pdqp::norms_finish(w, o.norm_A, o.norm_Q, s);
   CK(cudaEventRecord(h->ev[1], s));
-  pdqp::init_iterates(w, dx0, dy0, p, s);
-  pdqp::check(w, p, 0, 0, mixed, s);
+  long long k_total = 0;
+  int pos = 0;   // step-table position: iterations since the table was last filled
+  if (!resuming) {
+    pdqp::init_iterates(w, dx0, dy0, p, s);
+    pdqp::check(w, p, 0, 0, mixed, s);
+  } else {
+    // the loaded state stopped mid-period (at the iteration limit): run the rest
+    // of that period on its step table, then its check; or it stopped at a
+    // check that the iteration limit ended before the restart decision: take
+    // that check again (same iterates, same values) to make the decision
+    k_total = h->resume_k_total;
+    pos = h->resume_pos;
+    if (pos > 0) {
+      const int len = (int)std::min<long long>(o.check_period - pos, o.max_iter - k_total);
+      pdqp::iterate_chunk(w, len, mixed, p.spmv_threads, s, pos);
+      pdqp::check(w, p, 1, len, mixed, s);
+      k_total += len;
+      pos = (pos + len) % o.check_period;
+    } else if (h->resume_recheck) {
+      pdqp::check(w, p, 1, 0, mixed, s);
+    } else {
+      pdqp::count_running(w, s);
+    }
+  }
   CK(cudaGetLastError());
   sync_batch(h, s);
 
-  long long k_total = 0;
   bool timed_out = false;
   // autotuning of the iteration-kernel variant: the first full chunk runs
   // two rounds of TUNE iterations with each candidate (interleaved, so that no
@@ -548,7 +622,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   static const int kCand[4] = {256, 512, 1, 2};
   const int ncand = cluster_ok ? 4 : 3;
   constexpr int TUNE = 4, ROUNDS = 2;
-  const bool autotune = o.spmv_threads == 0;
+  const bool autotune = o.spmv_threads == 0 && !use_il;
   if (autotune && h->tuned_nt) p.spmv_threads = h->tuned_nt;
   while (w.bst_host->running > 0) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
@@ -602,6 +676,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     }
     CK(cudaGetLastError());
     k_total += len;
+    pos = (int)(len % o.check_period);
     sync_batch(h, s);
     if (w.bst_host->running > 0 && now_s() - t0 > o.time_limit) { timed_out = true; break; }
   }
@@ -643,6 +718,10 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     info->status = result;
     for (int i = 1; i < w.count; ++i) info->iterations = std::max(info->iterations, h->infos[i].iterations);
   }
+  h->solved = true;
+  h->end_p = p;
+  h->end_pos = pos;
+  h->end_k_total = k_total;
   return result;
 }
 
@@ -1194,6 +1273,19 @@ pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, c
     CK(cudaStreamSynchronize(s));
     if (bad) throw Fail{PDQP_ERR_INVALID, "C or B: non-finite entry"};
     alloc_work(h, s);
+    // one member's structure for the member-interleaved iteration kernels
+    w.fam_count = count;
+    w.fam_n = (int)n_t;
+    w.fam_m = (int)m_t;
+    w.fam_ld = (count + 127) / 128 * 128;   // whole warps of 4 float (2 double) members per lane
+    w.fam_nnzP = tw.P.nnz;
+    w.fam_nnzA = tw.A.nnz;
+    w.fam_il = tw.P.nlseg == 0 && tw.A.nlseg == 0 && n_t > 0;
+    if (w.fam_il) {
+      w.famP_col = dalloc<int>(h, tw.P.nnz + 8);
+      CK(cudaMemcpyAsync(w.famP_col, tw.P.col, (size_t)tw.P.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
   } catch (...) {
     if (h) pdqp_destroy(h);
     pdqp_destroy(t);
@@ -1758,6 +1850,53 @@ pdqp_status create_common(pdqp_handle* out, int count, const InstanceIn* ins, in
 }  // namespace
 
 // ==========================================================================
+// --------------------------------------------------------------------------
+// Solver state for a resume (pdqp_get_state / pdqp_set_state): an opaque blob
+// of a fixed header and the device sections below, in this order.  Every
+// section is a whole device array, so a resumed solve continues bit for bit
+// where the saved one stopped.
+// --------------------------------------------------------------------------
+namespace {
+
+constexpr char STATE_MAGIC[8] = {'P', 'D', 'Q', 'P', 'S', 'T', 'A', 'T'};
+constexpr uint32_t STATE_VERSION = 1;
+
+struct StateHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int64_t n, m, count, r, nnz_P, nnz_A;
+  int64_t check_period, pos, k_total;
+  int32_t mixed, y_in_z1, fy_in_z1, pad;
+  SolveParams params;
+  uint64_t total_bytes;
+};
+
+// (device pointer, bytes) of each section after the header and the step table
+std::vector<std::pair<void*, size_t>> state_sections(Work& w, bool mixed) {
+  const size_t n = (size_t)w.n, m = (size_t)w.m, c = (size_t)w.count;
+  std::vector<std::pair<void*, size_t>> v = {
+      {w.st, c * sizeof(DevState)}, {w.dsc, (n + m) * sizeof(double)},
+      {w.x, n * sizeof(double)},    {w.xbar, n * sizeof(double)},       {w.xt, n * sizeof(double)},
+      {w.Z[0], (n + m) * sizeof(double)}, {w.Z[1], (n + m) * sizeof(double)},
+      {w.ybar, m * sizeof(double)}, {w.ax, n * sizeof(double)},        {w.ay, m * sizeof(double)}};
+  if (mixed) {
+    const std::pair<void*, size_t> f[] = {
+        {w.fx, n * 4},     {w.fxbar, n * 4}, {w.fxt, n * 4}, {w.fZ[0], (n + m) * 4}, {w.fZ[1], (n + m) * 4},
+        {w.fybar, m * 4},  {w.fc, n * 4},    {w.fl, n * 4},  {w.fu, n * 4},          {w.fb, m * 4},
+        {w.fylo, m * 4},   {w.xhi, n * 8},   {w.yhi, m * 8}, {w.yk, m * 8}};
+    v.insert(v.end(), std::begin(f), std::end(f));
+  }
+  return v;
+}
+
+size_t state_bytes(Work& w, bool mixed, int C) {
+  size_t b = sizeof(StateHeader) + (size_t)w.count * C * sizeof(StepEntry);
+  for (auto& sec : state_sections(w, mixed)) b += sec.second;
+  return b;
+}
+
+}  // namespace
+
 extern "C" {
 
 void pdqp_default_options(pdqp_options* o) {
@@ -1934,7 +2073,7 @@ pdqp_status pdqp_solve_batch(int32_t count, const pdqp_handle* hs, const pdqp_op
   return worst;
 }
 
-pdqp_status pdqp_get_state(pdqp_handle h, double* x, double* y, double* xbar, double* ybar, int32_t mem,
+pdqp_status pdqp_get_iterates(pdqp_handle h, double* x, double* y, double* xbar, double* ybar, int32_t mem,
                            void* stream) {
   if (!h) return PDQP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1958,6 +2097,117 @@ pdqp_status pdqp_get_state(pdqp_handle h, double* x, double* y, double* xbar, do
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    h->err = f.msg;
+    return f.st;
+  }
+}
+
+pdqp_status pdqp_get_state(pdqp_handle h, void* buf, size_t* bytes, void* stream) {
+  if (!h || !bytes) return PDQP_ERR_INVALID;
+  try {
+    h->err.clear();
+    if (!h->solved) throw Fail{PDQP_ERR_INVALID, "pdqp_get_state: no solve has run on this handle"};
+    Work& w = h->w;
+    const bool mixed = h->end_p.mixed != 0;
+    const int C = h->end_p.check_period;
+    const size_t need = state_bytes(w, mixed, C);
+    if (!buf) { *bytes = need; return PDQP_OK; }
+    if (*bytes < need) throw Fail{PDQP_ERR_INVALID, "pdqp_get_state: buffer smaller than the state"};
+    cudaStream_t s = (cudaStream_t)stream;
+    StateHeader hd{};
+    std::memcpy(hd.magic, STATE_MAGIC, 8);
+    hd.version = STATE_VERSION;
+    hd.header_bytes = sizeof(StateHeader);
+    hd.n = w.n; hd.m = w.m; hd.count = w.count; hd.r = w.r; hd.nnz_P = w.P.nnz; hd.nnz_A = w.A.nnz;
+    hd.check_period = C; hd.pos = h->end_pos; hd.k_total = h->end_k_total;
+    hd.mixed = mixed;
+    hd.y_in_z1 = w.y == w.Z[1] + w.n;
+    hd.fy_in_z1 = mixed && w.fy == w.fZ[1] + w.n;
+    hd.params = h->end_p;
+    hd.total_bytes = need;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    std::memcpy(out, &hd, sizeof hd);
+    size_t off = sizeof hd;
+    // the step table, [count][C] out of its [count][tab_stride] layout
+    CK(cudaMemcpy2DAsync(out + off, C * sizeof(StepEntry), w.tab, (size_t)w.tab_stride * sizeof(StepEntry),
+                         C * sizeof(StepEntry), w.count, cudaMemcpyDeviceToHost, s));
+    off += (size_t)w.count * C * sizeof(StepEntry);
+    for (auto& sec : state_sections(w, mixed)) {
+      if (sec.second) CK(cudaMemcpyAsync(out + off, sec.first, sec.second, cudaMemcpyDeviceToHost, s));
+      off += sec.second;
+    }
+    CK(cudaStreamSynchronize(s));
+    *bytes = need;
+    return PDQP_OK;
+  } catch (const Fail& f) {
+    h->err = f.msg;
+    return f.st;
+  }
+}
+
+pdqp_status pdqp_set_state(pdqp_handle h, const void* buf, size_t bytes, void* stream) {
+  if (!h || !buf) return PDQP_ERR_INVALID;
+  try {
+    h->err.clear();
+    Work& w = h->w;
+    StateHeader hd{};
+    if (bytes < sizeof hd) throw Fail{PDQP_ERR_INVALID, "pdqp_set_state: buffer shorter than the state header"};
+    std::memcpy(&hd, buf, sizeof hd);
+    if (std::memcmp(hd.magic, STATE_MAGIC, 8) != 0 || hd.version != STATE_VERSION ||
+        hd.header_bytes != sizeof(StateHeader))
+      throw Fail{PDQP_ERR_INVALID, "pdqp_set_state: not a state of this library version"};
+    if (hd.n != w.n || hd.m != w.m || hd.count != w.count || hd.r != w.r || hd.nnz_P != w.P.nnz ||
+        hd.nnz_A != w.A.nnz)
+      throw Fail{PDQP_ERR_INVALID, "pdqp_set_state: the state belongs to a problem of other sizes"};
+    const int C = (int)hd.check_period;
+    if (C < 2 || C > PDQP_MAX_CHECK || hd.pos < 0 || hd.pos >= C || hd.k_total < 0 || hd.params.check_period != C ||
+        hd.params.mixed != hd.mixed)
+      throw Fail{PDQP_ERR_INVALID, "pdqp_set_state: inconsistent state header"};
+    const bool mixed = hd.mixed != 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->alloc_stream = s;
+    if (mixed) alloc_mixed(h);
+    const size_t need = state_bytes(w, mixed, C);
+    if (bytes < need || hd.total_bytes != need)
+      throw Fail{PDQP_ERR_INVALID, "pdqp_set_state: buffer shorter than the state it describes"};
+    if (w.tab_stride < C) {
+      w.tab = dalloc<StepEntry>(h, (size_t)w.count * C);
+      w.tab_stride = C;
+      if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
+      h->graph.valid = false;
+    }
+    const unsigned char* in = static_cast<const unsigned char*>(buf);
+    size_t off = sizeof hd;
+    CK(cudaMemcpy2DAsync(w.tab, (size_t)w.tab_stride * sizeof(StepEntry), in + off, C * sizeof(StepEntry),
+                         C * sizeof(StepEntry), w.count, cudaMemcpyHostToDevice, s));
+    off += (size_t)w.count * C * sizeof(StepEntry);
+    // instances the iteration limit stopped run on; the others keep their status
+    std::vector<DevState> sts((size_t)w.count);
+    std::memcpy(sts.data(), in + off, sts.size() * sizeof(DevState));
+    int limit_stopped = 0;
+    for (DevState& S : sts)
+      if (S.status == ST_ITER_LIMIT) { S.status = ST_RUNNING; ++limit_stopped; }
+    bool first = true;
+    for (auto& sec : state_sections(w, mixed)) {
+      const void* src = first ? static_cast<const void*>(sts.data()) : static_cast<const void*>(in + off);
+      if (sec.second) CK(cudaMemcpyAsync(sec.first, src, sec.second, cudaMemcpyHostToDevice, s));
+      off += sec.second;
+      first = false;
+    }
+    CK(cudaStreamSynchronize(s));   // the host copy of the statuses goes out of scope
+    w.y = hd.y_in_z1 ? w.Z[1] + w.n : w.Z[0] + w.n;
+    if (mixed) {
+      w.fy = hd.fy_in_z1 ? w.fZ[1] + w.n : w.fZ[0] + w.n;
+      w.y = w.yk;
+    }
+    h->resume = true;
+    h->resume_p = hd.params;
+    h->resume_pos = (int)hd.pos;
+    h->resume_k_total = hd.k_total;
+    h->resume_recheck = hd.pos == 0 && limit_stopped > 0;
+    h->solved = false;
     return PDQP_OK;
   } catch (const Fail& f) {
     h->err = f.msg;

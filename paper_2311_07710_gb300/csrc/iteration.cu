@@ -56,13 +56,36 @@ template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
 template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
 template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
 
+// Explicitly rounded arithmetic for the row updates: every kernel variant
+// that updates a row calls the same functions, and with each operation's
+// rounding fixed here (no fused multiply-add left to the compiler's choice at
+// each inlined call site) they all produce the same bits.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// The dual update of one row from its sum s = (A x_tilde)_r: y+ and y_bar+
+// (shared by the row-block and the member-interleaved kernels).
+template <typename V>
+__device__ __forceinline__ void dual_update(const StepEntry& e, V s, V yo, V bi, V yb, V lo, bool ineq, V& yn,
+                                            V& ybn) {
+  const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
+  yn = r_fma(-sigma, r_sub(s, bi), yo);                       // y - sigma (A x_tilde - b)
+  if (ineq) yn = fmax(yn, lo);
+  ybn = r_fma(ib, yn, r_mul(r_sub(V(1), ib), yb));            // (1 - 1/beta) y_bar + y+/beta
+}
+
 template <typename V>
 __device__ __forceinline__ void dual_row(const DualB<V>& a, const StepEntry& e, int r, V s, V yo, V bi, V yb,
                                          V lo) {
-  const V sigma = step_sigma<V>(e), ib = step_ib<V>(e);
-  V yn = yo - sigma * (s - bi);
-  if (a.ineq[r]) yn = fmax(yn, lo);
-  a.ybar[r] = (V(1) - ib) * yb + ib * yn;
+  V yn, ybn;
+  dual_update<V>(e, s, yo, bi, yb, lo, a.ineq[r] != 0, yn, ybn);
+  a.ybar[r] = ybn;
   a.ynew[r] = yn;
 }
 
@@ -148,16 +171,29 @@ struct PrimalB {
   const int* __restrict__ act;          // row block of each CUDA block (null: the block index)
 };
 
+// The primal update of one row from g = (Q x_md - A'y+)_r + c_r (+ the
+// low-rank term): x+, x_bar+ and the next iteration's x_md and x_tilde
+// (shared by the row-block and the member-interleaved kernels).
+template <typename V>
+__device__ __forceinline__ void primal_update(const StepEntry& e, V g, V xo, V xb0, V lr, V ur, V& xn, V& xb, V& zo,
+                                              V& xtn) {
+  const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
+  xn = fmin(fmax(r_fma(-tau, g, xo), lr), ur);               // proj_X(x - tau g)
+  xb = r_fma(ib, xn, r_mul(r_sub(V(1), ib), xb0));            // (1 - 1/beta) x_bar + x+/beta
+  zo = r_fma(ibn, xn, r_mul(r_sub(V(1), ibn), xb));           // next x_md
+  xtn = r_fma(thn, r_sub(xn, xo), xn);                        // next x_tilde
+}
+
 template <typename V, bool LR = false>
 __device__ __forceinline__ void primal_row(const PrimalB<V>& a, const StepEntry& e, int r, V s, V xo, V xb0,
                                            V cr, V lr, V ur) {
-  const V tau = step_tau<V>(e), ib = step_ib<V>(e), ibn = step_ibn<V>(e), thn = step_thn<V>(e);
-  const V g = s + cr + (LR ? lr_row<V, V, V>(a.F, a.wlr, a.r, r) : V(0));
-  const V xn = fmin(fmax(xo - tau * g, lr), ur);
-  const V xb = (V(1) - ib) * xb0 + ib * xn;
+  V g = r_add(s, cr);
+  if constexpr (LR) g = r_add(g, lr_row<V, V, V>(a.F, a.wlr, a.r, r));
+  V xn, xb, zo, xtn;
+  primal_update<V>(e, g, xo, xb0, lr, ur, xn, xb, zo, xtn);
   a.xbar[r] = xb;
-  a.zout[r] = (V(1) - ibn) * xb + ibn * xn;
-  a.xt[r] = xn + thn * (xn - xo);
+  a.zout[r] = zo;
+  a.xt[r] = xtn;
   a.x[r] = xn;
 }
 
@@ -578,6 +614,301 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
   }
 }
 
+// ==========================================================================
+// Family handles: members that share the matrix, run on member-interleaved
+// vectors v[j * ld + member] (ld = members rounded up to 32).  A warp takes
+// one row for 32 members: each matrix entry is read once for them and meets
+// their 32 values of the gathered vector in one coalesced load, where the
+// member-major layout gathers 32 scattered sectors.  The row sum runs over
+// the row's entries in CSR order with separately rounded products and sums,
+// as the row-block kernels sum their staged products, and the row update is
+// the same function: a member's iterates are bitwise those of its standalone
+// solve.  The vectors are transposed into this layout at the start of a
+// chunk and back at its end, so the checks, restarts and rebases run on the
+// member-major layout as for any batch.
+// ==========================================================================
+constexpr int IL_NT = 256;
+constexpr int IL_RPB = IL_NT / 32;     // rows per CUDA block (one warp each)
+
+
+template <typename V>
+struct FamIL {
+  const int* __restrict__ rp;          // one member's CSR (A, or P with local columns)
+  const int* __restrict__ col;
+  const V* __restrict__ val;           // scaled values (the same for every member)
+  int rows, ld, count, C;
+  const StepEntry* __restrict__ tab;   // [member][C]
+  const DevState* __restrict__ st;     // [member]
+  const V* __restrict__ zin;           // gathered vector (x_tilde, or [x_md ; y+])
+  // dual: yold, ynew, ybar, b, ylo (may be null), ineq;  primal: x, xbar, zout, xt, c, l, u
+  const V* __restrict__ v0;
+  V* __restrict__ w0;
+  V* __restrict__ w1;
+  V* __restrict__ w2;
+  V* __restrict__ w3;
+  const V* __restrict__ r0;
+  const V* __restrict__ r1;
+  const V* __restrict__ r2;
+  const unsigned char* __restrict__ ineq;
+};
+
+// 16 bytes of consecutive members per lane: 4 float or 2 double
+template <typename V> struct IlVec;
+template <> struct IlVec<float> { using T = float4; static constexpr int W = 4; };
+template <> struct IlVec<double> { using T = double2; static constexpr int W = 2; };
+constexpr int IL_LD_ALIGN = 128;       // members per warp in float32 (the leading dimension's unit)
+
+template <typename V>
+__device__ __forceinline__ void il_load(const V* p, V (&v)[IlVec<V>::W]) {
+  const typename IlVec<V>::T q = __ldg(reinterpret_cast<const typename IlVec<V>::T*>(p));
+  if constexpr (IlVec<V>::W == 4) { v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w; }
+  else { v[0] = q.x; v[1] = q.y; }
+}
+template <typename V>
+__device__ __forceinline__ void il_load_rw(const V* p, V (&v)[IlVec<V>::W]) {   // a vector the kernel writes
+  const typename IlVec<V>::T q = *reinterpret_cast<const typename IlVec<V>::T*>(p);
+  if constexpr (IlVec<V>::W == 4) { v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w; }
+  else { v[0] = q.x; v[1] = q.y; }
+}
+template <typename V>
+__device__ __forceinline__ void il_store(V* p, const V (&v)[IlVec<V>::W]) {
+  typename IlVec<V>::T q;
+  if constexpr (IlVec<V>::W == 4) { q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3]; }
+  else { q.x = v[0]; q.y = v[1]; }
+  *reinterpret_cast<typename IlVec<V>::T*>(p) = q;
+}
+
+// The row sums of this lane's W members: for each, sequential over the row's
+// entries, each product and sum rounded on its own (no fused multiply-add),
+// as prod[e] is staged and summed by the row-block kernels.
+template <typename V>
+__device__ __forceinline__ void il_row_sum(const FamIL<V>& a, int r, int m0, V (&s)[IlVec<V>::W]) {
+  constexpr int W = IlVec<V>::W;
+  const int e0 = a.rp[r], e1 = a.rp[r + 1];
+#pragma unroll
+  for (int q = 0; q < W; ++q) s[q] = V(0);
+  int e = e0;
+  for (; e + 2 <= e1; e += 2) {
+    const int c0 = __ldg(a.col + e), c1 = __ldg(a.col + e + 1);
+    const V v0 = __ldg(a.val + e), v1 = __ldg(a.val + e + 1);
+    V z0[W], z1[W];
+    il_load(a.zin + (size_t)c0 * a.ld + m0, z0);
+    il_load(a.zin + (size_t)c1 * a.ld + m0, z1);
+#pragma unroll
+    for (int q = 0; q < W; ++q) s[q] = r_add(r_add(s[q], r_mul(v0, z0[q])), r_mul(v1, z1[q]));
+  }
+  if (e < e1) {
+    const int c0 = __ldg(a.col + e);
+    const V v0 = __ldg(a.val + e);
+    V z0[W];
+    il_load(a.zin + (size_t)c0 * a.ld + m0, z0);
+#pragma unroll
+    for (int q = 0; q < W; ++q) s[q] = r_add(s[q], r_mul(v0, z0[q]));
+  }
+}
+
+// Per-member step entries and running flags of the block's 32 W members;
+// false when none of them runs (uniform over the block).
+template <typename V>
+__device__ __forceinline__ bool il_members(const FamIL<V>& a, int j, StepEntry* es, int* run) {
+  constexpr int GM = 32 * IlVec<V>::W;
+  int any = 0;
+  for (int k = threadIdx.x; k < GM; k += blockDim.x) {
+    const int mem = blockIdx.y * GM + k;
+    const bool ok = mem < a.count && a.st[mem].status == ST_RUNNING;
+    run[k] = ok;
+    if (ok) es[k] = a.tab[(size_t)mem * a.C + j];
+    any |= ok;
+  }
+  return __syncthreads_or(any) != 0;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(IL_NT, 4) k_dual_il(FamIL<V> a, int j) {
+  constexpr int W = IlVec<V>::W, GM = 32 * W;
+  __shared__ StepEntry es[GM];
+  __shared__ int run[GM];
+  if (!il_members(a, j, es, run)) return;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * IL_RPB + (threadIdx.x >> 5);
+  if (r >= a.rows) return;
+  const int k0 = lane * W, m0 = blockIdx.y * GM + k0;
+  bool any = false;
+#pragma unroll
+  for (int q = 0; q < W; ++q) any |= run[k0 + q] != 0;
+  if (!any) return;
+  const size_t idx = (size_t)r * a.ld + m0;
+  V yo[W], bi[W], yb[W], lo[W], s[W], yn[W], ybn[W];
+  il_load_rw(a.v0 + idx, yo);
+  il_load(a.r0 + idx, bi);
+  il_load_rw(a.w1 + idx, yb);
+  if (a.r1) il_load(a.r1 + idx, lo);
+  else
+#pragma unroll
+    for (int q = 0; q < W; ++q) lo[q] = V(0);
+  il_row_sum(a, r, m0, s);
+  const bool ineq = a.ineq[r] != 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    if (run[k0 + q]) dual_update<V>(es[k0 + q], s[q], yo[q], bi[q], yb[q], lo[q], ineq, yn[q], ybn[q]);
+    else { ybn[q] = yb[q]; yn[q] = a.w0[idx + q]; }    // a member that stopped keeps its values
+  }
+  il_store(a.w1 + idx, ybn);   // y_bar
+  il_store(a.w0 + idx, yn);    // y+
+}
+
+template <typename V>
+__global__ void __launch_bounds__(IL_NT, 4) k_primal_il(FamIL<V> a, int j) {
+  constexpr int W = IlVec<V>::W, GM = 32 * W;
+  __shared__ StepEntry es[GM];
+  __shared__ int run[GM];
+  if (!il_members(a, j, es, run)) return;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * IL_RPB + (threadIdx.x >> 5);
+  if (r >= a.rows) return;
+  const int k0 = lane * W, m0 = blockIdx.y * GM + k0;
+  bool any = false;
+#pragma unroll
+  for (int q = 0; q < W; ++q) any |= run[k0 + q] != 0;
+  if (!any) return;
+  const size_t idx = (size_t)r * a.ld + m0;
+  V xo[W], xb0[W], cr[W], lr[W], ur[W], s[W], xn[W], xb[W], zo[W], xtn[W];
+  il_load_rw(a.w0 + idx, xo);
+  il_load_rw(a.w1 + idx, xb0);
+  il_load(a.r0 + idx, cr);
+  il_load(a.r1 + idx, lr);
+  il_load(a.r2 + idx, ur);
+  il_row_sum(a, r, m0, s);
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    if (run[k0 + q]) {
+      const V g = r_add(s[q], cr[q]);
+      primal_update<V>(es[k0 + q], g, xo[q], xb0[q], lr[q], ur[q], xn[q], xb[q], zo[q], xtn[q]);
+    } else {   // a member that stopped keeps its values
+      xn[q] = xo[q]; xb[q] = xb0[q]; zo[q] = a.w2[idx + q]; xtn[q] = a.w3[idx + q];
+    }
+  }
+  il_store(a.w1 + idx, xb);    // x_bar
+  il_store(a.w2 + idx, zo);    // x_md of the next iteration
+  il_store(a.w3 + idx, xtn);   // x_tilde of the next iteration
+  il_store(a.w0 + idx, xn);    // x
+}
+
+// member-major [count][L] (member stride `stride`) <-> interleaved [L][ld],
+// through 32 x 32 shared-memory tiles
+template <typename V>
+__global__ void __launch_bounds__(256) k_to_il(const V* __restrict__ src, long long stride, int L, int count,
+                                               V* __restrict__ dst, int ld) {
+  __shared__ V t[32][33];
+  const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int mem = m0 + k, jj = j0 + threadIdx.x;
+    if (mem < count && jj < L) t[k][threadIdx.x] = src[(size_t)mem * stride + jj];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int jj = j0 + k, mem = m0 + threadIdx.x;
+    if (jj < L && mem < count) dst[(size_t)jj * ld + mem] = t[threadIdx.x][k];
+  }
+}
+template <typename V>
+__global__ void __launch_bounds__(256) k_from_il(const V* __restrict__ src, int ld, int L, int count,
+                                                 V* __restrict__ dst, long long stride) {
+  __shared__ V t[32][33];
+  const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int jj = j0 + k, mem = m0 + threadIdx.x;
+    if (jj < L && mem < count) t[k][threadIdx.x] = src[(size_t)jj * ld + mem];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int mem = m0 + k, jj = j0 + threadIdx.x;
+    if (mem < count && jj < L) dst[(size_t)mem * stride + jj] = t[threadIdx.x][k];
+  }
+}
+
+// the transposes take a 2-D block of 32 x 8 threads
+template <typename V>
+static void to_il(const V* src, long long stride, int L, int count, V* dst, int ld, cudaStream_t s) {
+  if (L <= 0 || !src) return;
+  k_to_il<V><<<dim3(cdiv(L, 32), cdiv(count, 32)), dim3(32, 8), 0, s>>>(src, stride, L, count, dst, ld);
+  count_launch();
+}
+template <typename V>
+static void from_il(const V* src, int ld, int L, int count, V* dst, long long stride, cudaStream_t s) {
+  if (L <= 0) return;
+  k_from_il<V><<<dim3(cdiv(L, 32), cdiv(count, 32)), dim3(32, 8), 0, s>>>(src, ld, L, count, dst, stride);
+  count_launch();
+}
+
+// Algorithmic bytes of one family launch: the shared matrix once, the vectors
+// of each running member once (kind 0 dual, 1 primal; sv = bytes per value).
+static double il_launch_bytes(const Work& w, int kind, double sv) {
+  const double members = w.fam_n > 0 ? w.bst_host->run_n / w.fam_n : 0.0;
+  if (kind == 0)
+    return w.fam_nnzA * (sv + 4.0) + 4.0 * (w.fam_m + 1.0) + sv * members * (w.fam_n + 5.0 * w.fam_m);
+  return w.fam_nnzP * (sv + 4.0) + 4.0 * (w.fam_n + 1.0) + sv * members * (10.0 * w.fam_n + w.fam_m);
+}
+
+template <typename V>
+static void run_chunk_il(Work& w, int j0, int len, const V* Aval, const V* Pval, V* xt, V* const* Z, V* ybar,
+                         const V* b, const V* ylo, V* x, V* xbar, const V* c, const V* l, const V* u,
+                         cudaStream_t s) {
+  Profiler& Pr = w.prof;
+  V* const* I = reinterpret_cast<V* const*>(sizeof(V) == 4 ? (void* const*)w.ilf : (void* const*)w.ild);
+  const int n = w.fam_n, m = w.fam_m, cnt = w.fam_count, ld = w.fam_ld;
+  const long long N = (long long)cnt * n;
+  auto tin = [&](const V* src, long long stride, int L, V* dst) { to_il<V>(src, stride, L, cnt, dst, ld, s); };
+  // member-major -> interleaved: everything the iterations read
+  for (int p = 0; p < 2; ++p) {
+    tin(Z[p], n, n, I[IL_Z0 + p]);
+    tin(Z[p] + N, m, m, I[IL_Z0 + p] + (size_t)n * ld);
+  }
+  tin(x, n, n, I[IL_X]);
+  tin(xbar, n, n, I[IL_XBAR]);
+  tin(xt, n, n, I[IL_XT]);
+  tin(ybar, m, m, I[IL_YBAR]);
+  tin(c, n, n, I[IL_C]);
+  tin(l, n, n, I[IL_L]);
+  tin(u, n, n, I[IL_U]);
+  tin(b, m, m, I[IL_B]);
+  tin(ylo, m, m, I[IL_YLO]);
+  const int groups = ld / (32 * IlVec<V>::W);
+  FamIL<V> da{};
+  da.rp = w.A.rp; da.col = w.A.col; da.val = Aval;
+  da.rows = m; da.ld = ld; da.count = cnt; da.C = w.tab_stride; da.tab = w.tab; da.st = w.st;
+  da.zin = I[IL_XT];
+  da.w1 = I[IL_YBAR]; da.r0 = I[IL_B]; da.r1 = ylo ? I[IL_YLO] : nullptr; da.ineq = w.row_ineq;
+  FamIL<V> pa{};
+  pa.rp = w.P.rp; pa.col = w.famP_col; pa.val = Pval;
+  pa.rows = n; pa.ld = ld; pa.count = cnt; pa.C = w.tab_stride; pa.tab = w.tab; pa.st = w.st;
+  pa.w0 = I[IL_X]; pa.w1 = I[IL_XBAR]; pa.w3 = I[IL_XT]; pa.r0 = I[IL_C]; pa.r1 = I[IL_L]; pa.r2 = I[IL_U];
+  for (int j = j0; j < j0 + len; ++j) {
+    if (m > 0) {
+      da.v0 = I[IL_Z0 + ((j + 1) & 1)] + (size_t)n * ld;   // y^k
+      da.w0 = I[IL_Z0 + (j & 1)] + (size_t)n * ld;         // y^{k+1}
+      if (Pr.on) Pr.begin(0, s, il_launch_bytes(w, 0, sizeof(V)));
+      launch(k_dual_il<V>, dim3(cdiv(m, IL_RPB), groups), IL_NT, 0, s, da, j);
+      if (Pr.on) Pr.end(s);
+    }
+    pa.zin = I[IL_Z0 + (j & 1)];
+    pa.w2 = I[IL_Z0 + ((j + 1) & 1)];
+    if (Pr.on) Pr.begin(1, s, il_launch_bytes(w, 1, sizeof(V)));
+    launch(k_primal_il<V>, dim3(cdiv(n, IL_RPB), groups), IL_NT, 0, s, pa, j);
+    if (Pr.on) Pr.end(s);
+  }
+  // interleaved -> member-major: everything the iterations wrote
+  auto back = [&](const V* src, int L, V* dst, long long stride) { from_il<V>(src, ld, L, cnt, dst, stride, s); };
+  for (int p = 0; p < 2; ++p) {
+    back(I[IL_Z0 + p], n, Z[p], n);
+    back(I[IL_Z0 + p] + (size_t)n * ld, m, Z[p] + N, m);
+  }
+  back(I[IL_X], n, x, n);
+  back(I[IL_XBAR], n, xbar, n);
+  back(I[IL_XT], n, xt, n);
+  back(I[IL_YBAR], m, ybar, m);
+}
+
 bool chunk_cluster_ok(const Work& w, bool mixed) {
   const size_t smem = mixed ? chunk_smem_bytes<float>(w.n, w.m) : chunk_smem_bytes<double>(w.n, w.m);
   return w.r == 0 && w.A.nlseg == 0 && w.P.nlseg == 0 && w.A.nblk <= CHUNK_MAX_BLOCKS &&
@@ -648,6 +979,19 @@ static void run_chunk_cluster(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V*
 }
 
 void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0, bool compact) {
+  if (nt == 3) {   // a family handle on member-interleaved vectors
+    if (len <= 0) return;
+    if (mixed) {
+      run_chunk_il<float>(w, j0, len, w.A.sval_f, w.P.sval_f, w.fxt, w.fZ, w.fybar, w.fb, w.fylo, w.fx, w.fxbar, w.fc,
+                          w.fl, w.fu, s);
+      w.fy = w.fZ[(j0 + len - 1) & 1] + w.n;
+    } else {
+      run_chunk_il<double>(w, j0, len, w.A.sval, w.P.sval, w.xt, w.Z, w.ybar, w.bs, nullptr, w.x, w.xbar, w.cs, w.ls,
+                           w.us, s);
+      w.y = w.Z[(j0 + len - 1) & 1] + w.n;
+    }
+    return;
+  }
   if (nt == 2) {   // the whole chunk in one cluster launch (small problems)
     if (mixed) {
       run_chunk_cluster<float>(w, j0, len, w.A.bscaled_f(), w.P.bscaled_f(), w.fxt, w.fZ, w.fybar, w.fb, w.fylo,

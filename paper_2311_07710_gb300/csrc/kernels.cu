@@ -2046,8 +2046,8 @@ Profiler::~Profiler() {
 // Some callers cannot call cudaMalloc once they are running: a real-time
 // control loop (for example an MPC controller re-solving every few
 // milliseconds) must not block on the allocator or synchronise the device,
-// and code that runs while a CUDA stream is being captured or inside a host
-// with a fixed device-memory budget may not allocate at all.  This entry point
+// and a host process with a fixed device-memory budget may not allocate at
+// all after start-up.  This entry point
 // evaluates the relative KKT error of a caller-given (x, y) with caller-owned
 // device arrays only; its per-block partial sums live in the file-scope array
 // below, which every GPU that loads this library holds until the process exits.
@@ -2059,6 +2059,9 @@ Profiler::~Profiler() {
 #define PDQP_NOALLOC_MAX_ROWS 65536                          // max n and max m per call
 #define PDQP_NOALLOC_MAX_BLOCKS (PDQP_NOALLOC_MAX_ROWS / 8)  // a block covers >= 8 rows
 #define PDQP_NOALLOC_MAX_DEVICES 64
+// a block of 256 threads covers 256 / L rows with L <= 32 lanes per row
+// (pick_lanes), so at most MAX_ROWS / 8 blocks ever touch the scratch
+static_assert(PDQP_NOALLOC_MAX_BLOCKS * (256 / 32) >= PDQP_NOALLOC_MAX_ROWS, "noalloc scratch too small");
 
 // 8192 blocks x 32 partial sums x 8 bytes = 2 MiB per device.
 static __device__ __align__(256) double g_noalloc_scratch[PDQP_NOALLOC_MAX_BLOCKS * 32];
@@ -2087,6 +2090,24 @@ extern "C" pdqp_status pdqp_kkt_noalloc(int64_t n, int64_t m, int64_t m_eq, cons
     return PDQP_ERR_INVALID;
   if (m > 0 && (!A_rowptr || !At_rowptr || !b || !y || (nnz_A > 0 && (!A_col || !A_val || !At_col || !At_val))))
     return PDQP_ERR_INVALID;
+  // every array the kernels touch must be device (or managed) memory: a host
+  // pointer would make them fault.  The query allocates nothing.
+  {
+    const void* ptrs[] = {Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, At_rowptr, At_col, At_val,
+                          c, b, l, u, x, y, parts};
+    for (const void* p : ptrs) {
+      if (!p) continue;
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return PDQP_ERR_INVALID;
+      }
+      if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return PDQP_ERR_INVALID;
+    }
+  }
+  // an error left pending by earlier work on this thread is not ours: leave it
+  // for the caller to read and launch nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return PDQP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= PDQP_NOALLOC_MAX_DEVICES) return PDQP_ERR_CUDA;
@@ -2109,6 +2130,7 @@ extern "C" pdqp_status pdqp_kkt_noalloc(int64_t n, int64_t m, int64_t m_eq, cons
   const int gm = m > 0 ? pdqp::cdiv(m, 256 / LA) : 0;
   const int gn = pdqp::cdiv(n, 256 / LN);
   const int nblk = gm > gn ? gm : gn;
+  if (nblk > PDQP_NOALLOC_MAX_BLOCKS) return PDQP_ERR_INVALID;   // unreachable by the sizes above
   // blocks that one of the two kernels does not launch contribute zeros
   if (cudaMemsetAsync(scratch, 0, (size_t)nblk * 32 * sizeof(double), s) != cudaSuccess) return PDQP_ERR_CUDA;
   pdqp::KktArgs a{};

@@ -10,6 +10,9 @@
 
 #include "common.cuh"
 
+// Slots of the member-interleaved vectors of a family handle.
+enum { IL_Z0 = 0, IL_Z1, IL_X, IL_XBAR, IL_XT, IL_YBAR, IL_C, IL_L, IL_U, IL_B, IL_YLO, IL_SLOTS };
+
 // Row blocks: every CUDA block of the SpMV kernels takes whole rows
 // [blk[b], blk[b+1]) holding at most BNNZ nonzeros and BROWS rows; a row longer
 // than BNNZ forms a block of its own.
@@ -153,6 +156,16 @@ struct Work {
   // infeasibility certificates (this solve's options; buffers on first use)
   int detect = 0;
   double eps_inf = 1e-8;
+  // Family handles (members that share the matrix): one member's sizes and
+  // its P columns in local numbering (the A' part at fam_n + k), and the
+  // member-interleaved copies of the iteration vectors, v[j * fam_ld + member],
+  // that the family iteration kernels run on within a chunk (slots IL_*).
+  int fam_count = 0, fam_n = 0, fam_m = 0, fam_ld = 0;
+  long long fam_nnzP = 0, fam_nnzA = 0;
+  int* famP_col = nullptr;
+  bool fam_il = false;                       // eligible: no long rows, no low-rank term
+  double* ild[11] = {};                      // float64 (allocated on first use)
+  float* ilf[11] = {};                       // float32
   InfState* inf = nullptr;                   // [count]
   double *inf_x[2] = {nullptr, nullptr};     // rays of the current / average iterate, scaled [n]
   double *inf_y[2] = {nullptr, nullptr};     // [m]
@@ -189,7 +202,8 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
 // compact: launch only the row blocks of the running instances (batches; the
 // counts of the last check must be in bst_host).
 // nt: 256 or 512 threads per row block, 1 the pipelined persistent kernels, 2
-// the whole chunk in one cluster launch (only where chunk_cluster_ok).
+// the whole chunk in one cluster launch (only where chunk_cluster_ok), 3 the
+// member-interleaved family kernels (only where w.fam_il, buffers allocated).
 void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0, bool compact = false);
 // few row blocks, no long rows, no low-rank term, the vector copies fit in shared memory
 bool chunk_cluster_ok(const Work& w, bool mixed);

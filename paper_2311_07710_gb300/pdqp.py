@@ -84,7 +84,9 @@ SIGNATURES = {
     "pdqp_solve_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(pdqp_options),
                                         ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                         ctypes.POINTER(_P), ctypes.POINTER(pdqp_info), ctypes.c_int32, _P]),
-    "pdqp_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_get_iterates": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "pdqp_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t), _P]),
+    "pdqp_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "pdqp_kkt": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _P]),
     "pdqp_get_sizes": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int64)] * 5),
     "pdqp_last_error": (ctypes.c_char_p, [_P]),
@@ -270,10 +272,26 @@ def pdqp_solve_batch(hs: Sequence, opt: Optional[pdqp_options] = None, x0=None, 
     return _check(st, None), list(infos)
 
 
-def pdqp_get_state(h, x=None, y=None, xbar=None, ybar=None, stream=None):
+def pdqp_get_iterates(h, x=None, y=None, xbar=None, ybar=None, stream=None):
     args = [_ptr(a, np.float64) for a in (x, y, xbar, ybar)]
     mem = _one_space([a[2] for a in args])
-    return _check(load().pdqp_get_state(h, *[a[0] for a in args], mem, _stream(stream)), h)
+    return _check(load().pdqp_get_iterates(h, *[a[0] for a in args], mem, _stream(stream)), h)
+
+
+def pdqp_get_state(h, stream=None):
+    """The handle's complete solver state after its last solve (checkpoint), as bytes."""
+    lib = load()
+    size = ctypes.c_size_t(0)
+    _check(lib.pdqp_get_state(h, None, ctypes.byref(size), _stream(stream)), h)
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib.pdqp_get_state(h, buf, ctypes.byref(size), _stream(stream)), h)
+    return buf.raw[:size.value]
+
+
+def pdqp_set_state(h, state: bytes, stream=None):
+    """Load a checkpoint from pdqp_get_state; the next pdqp_solve continues from it."""
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    return _check(load().pdqp_set_state(h, buf, len(state), _stream(stream)), h)
 
 
 def pdqp_kkt(h, x, y, stream=None):

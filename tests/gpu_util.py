@@ -48,7 +48,7 @@ def state_after(inst, iters, **opts):
         o = pdqp.pdqp_default_options(max_iter=iters, eps=0.0, **opts)
         pdqp.pdqp_solve(h, o)
         out = [np.zeros(inst.n), np.zeros(inst.m), np.zeros(inst.n), np.zeros(inst.m)]
-        pdqp.pdqp_get_state(h, *out)
+        pdqp.pdqp_get_iterates(h, *out)
         return dict(x=out[0], y=out[1], xbar=out[2], ybar=out[3])
     finally:
         pdqp.pdqp_destroy(h)

@@ -89,7 +89,7 @@ def test_batch_iterates_match_oracle(pdqp):
         infos = pdqp.pdqp_batch_info(h)
         N, M = sum(i.n for i in insts), sum(i.m for i in insts)
         out = [np.zeros(N), np.zeros(M), np.zeros(N), np.zeros(M)]
-        pdqp.pdqp_get_state(h, *out)
+        pdqp.pdqp_get_iterates(h, *out)
     finally:
         pdqp.pdqp_destroy(h)
     ox = oy = 0
@@ -132,6 +132,37 @@ def test_family_handle_reproduces_batch(pdqp, precision):
         assert out[0][1] == out[1][1]
         np.testing.assert_array_equal(out[0][2], out[1][2])
         np.testing.assert_array_equal(out[0][3], out[1][3])
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_family_interleaved_kernels_match_row_block_kernels(pdqp, precision):
+    """The member-interleaved family kernels (spmv_threads 3, the family
+    default: one warp per row for 32 members, coalesced gathers) against the
+    row-block kernels on the replicated layout (256), bit for bit: 40 members
+    (a partial group of 32) that stop at different checks, from a given
+    start."""
+    fam = qpgen.family_qp(n=500, m=250)
+    count = 40
+    C, B = fam.params(100, count)
+    n, m = fam.base.n, fam.base.m
+    rng = np.random.default_rng(2)
+    x0, y0 = 0.1 * rng.standard_normal(count * n), 0.1 * rng.standard_normal(count * m)
+    outs = []
+    for nt in (256, 3):
+        h = pdqp.family_from_base(fam.base, C, B)
+        try:
+            x, y = np.zeros(count * n), np.zeros(count * m)
+            st, info = pdqp.pdqp_solve(h, pdqp.pdqp_default_options(precision=precision, spmv_threads=nt), x0=x0,
+                                       y0=y0, x_out=x, y_out=y)
+            outs.append((st, [(i.status, i.iterations) for i in pdqp.pdqp_batch_info(h)], x, y, info.spmv_threads))
+        finally:
+            pdqp.pdqp_destroy(h)
+    assert outs[0][0] == outs[1][0] == pdqp.PDQP_OK
+    assert outs[1][4] == 3
+    assert len({it for _, it in outs[1][1]}) > 1      # members stop at different checks
+    assert outs[0][1] == outs[1][1]
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+    np.testing.assert_array_equal(outs[0][3], outs[1][3])
 
 
 def test_family_handle_rejects_bad_input(pdqp):

@@ -99,7 +99,7 @@ def test_variant_iterates_match_oracle(pdqp, variant):
                                        norm_Q=ref.norm_Q, **go)
             P.pdqp_solve(h, o, x0=x0, y0=y0)
             out = [np.zeros(inst.n), np.zeros(inst.m), np.zeros(inst.n), np.zeros(inst.m)]
-            P.pdqp_get_state(h, *out)
+            P.pdqp_get_iterates(h, *out)
         finally:
             P.pdqp_destroy(h)
         for key, v in zip(("x", "y", "xbar", "ybar"), out):

@@ -154,7 +154,7 @@ def test_device_build_past_the_capped_grid(pdqp):
     try:
         pdqp.pdqp_solve(h, pdqp.pdqp_default_options(max_iter=50, eps=0.0, norm_A=ref.norm_A, norm_Q=ref.norm_Q))
         x = np.zeros(inst.n)
-        pdqp.pdqp_get_state(h, x)
+        pdqp.pdqp_get_iterates(h, x)
     finally:
         pdqp.pdqp_destroy(h)
     assert G.rel_err(x, ref.trace[50]["x"]) <= 1e-10
@@ -175,7 +175,7 @@ def test_packed_batch_past_the_capped_grid(pdqp):
         try:
             pdqp.pdqp_solve(h, pdqp.pdqp_default_options(max_iter=64, eps=0.0))
             st = [np.zeros(N), np.zeros(M), np.zeros(N), np.zeros(M)]
-            pdqp.pdqp_get_state(h, *st)
+            pdqp.pdqp_get_iterates(h, *st)
             outs.append(st)
         finally:
             pdqp.pdqp_destroy(h)
