@@ -57,30 +57,62 @@ __device__ __forceinline__ X gather_load(const X* p) {
   else return *p;
 }
 
+// Four consecutive entries of an index or value array by one 16-byte load
+// (p 16-byte aligned).
+__device__ __forceinline__ void load4(const int* __restrict__ p, int (&v)[4]) {
+  const int4 q = __ldg(reinterpret_cast<const int4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const float* __restrict__ p, float (&v)[4]) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* __restrict__ p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// The block's index and value streams are read as aligned quads (16-byte
+// loads: a quarter of the load requests of element loads, the requests the
+// gathers compete with); quad q holds entries a0 + 4q .. a0 + 4q + 3 with
+// a0 = e0 rounded down to a multiple of 4 (the arrays carry 8 entries of
+// padding, so the last quad stays inside them), and only the block's own
+// entries are gathered and staged.  The staged products and their order are
+// those of element-wise staging.
 template <int NT, int GM = GATHER_LDG, typename V, typename X>
 __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
                                                int r0, int nr, V* prod, int* srp) {
-  // float data: two phases of EPT/2 loads and gathers each, half the
-  // registers of one phase of EPT, so that 8 blocks fit on an SM; float64
-  // data (4 blocks per SM either way) keeps all EPT gathers in flight at once
-  constexpr int EPT = BNNZ / NT;
-  constexpr int PH = sizeof(V) == 4 ? 2 : 1;
-  constexpr int H = EPT / PH;
+  // float data: one quad (four gathers) per phase, so that 256 threads fit 32
+  // registers and 8 blocks an SM; float64 data (4 blocks per SM either way)
+  // keeps two quads' gathers in flight at once
+  constexpr int QPT = BNNZ / NT / 4 + 1;           // quads per thread, one more for the misalignment
+  constexpr int QPP = sizeof(V) == 4 ? 1 : 2;      // quads per phase
   const int tid = threadIdx.x;
+  const int a0 = e0 & ~3, o = e0 - a0;
+  const int nq = (o + ne + 3) >> 2;
   for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
 #pragma unroll
-  for (int h = 0; h < PH; ++h) {
-    int ci[H];
-    V vv[H];
+  for (int h = 0; h < QPT; h += QPP) {
+    int ci[QPP][4];
+    V vv[QPP][4];
 #pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const int e = tid + (h * H + k) * NT;
-      if (e < ne) { ci[k] = M.col[e0 + e]; vv[k] = M.val[e0 + e]; }
+    for (int k = 0; k < QPP; ++k) {
+      const int q = tid + (h + k) * NT;
+      if (h + k < QPT && q < nq) {
+        load4(M.col + a0 + 4 * q, ci[k]);
+        load4(M.val + a0 + 4 * q, vv[k]);
+      }
     }
 #pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const int e = tid + (h * H + k) * NT;
-      if (e < ne) prod[e] = vv[k] * (V)gather_load<GM>(vec + ci[k]);
+    for (int k = 0; k < QPP; ++k) {
+      const int q = tid + (h + k) * NT;
+      if (h + k < QPT && q < nq) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = 4 * q + i - o;   // the entry's place in the block
+          if (e >= 0 && e < ne) prod[e] = vv[k][i] * (V)gather_load<GM>(vec + ci[k][i]);
+        }
+      }
     }
   }
 }
