@@ -54,6 +54,10 @@ TRAFFIC_TXT = os.path.join(ROOT, "profiles", "traffic.txt")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2311_07710_gb300", "csrc", f)
                for f in ("iteration.cu", "rowblock.cuh", "common.cuh")]
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal float64 rate (no FP64 tensor path used)
+# Random 4-byte gathers (with their int32 index and float32 value streams) into
+# an L2-resident vector, measured on GB300 through the SM's load path, the
+# fastest of the paths measured (profiles/gather_ceiling_gb300.md)
+GATHER_ROOF_PER_S = 2.6e11
 
 
 def parse():
@@ -396,18 +400,23 @@ def run_ours(args, world, rank, local):
         o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, spmv_threads=args.spmv_threads)
         pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
         torch.cuda.synchronize(dev)
-        k64 = 2
+        k64 = args.steps          # the same step count as the mixed-precision leg
         ev0.record(stream)
         for _ in range(k64):
             st64, info64 = pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         t64 = allreduce_max(ev0.elapsed_time(ev1), world, dev)
+        prof64 = profiled_pass(pdqp, h, lambda: pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream), 1, dev)
         fp64_side = {"value": world * k64 * per_step / (t64 / 1e3), "unit": "solves/s", "steps": k64,
+                     "ms_per_step": t64 / k64,
                      "iterations": info64.iterations if per_step == 1 else
                      max(i.iterations for i in pdqp.pdqp_batch_info(h)),
                      "rel_kkt": info64.rel_kkt, "status": info64.status,
-                     "speedup_of_value": value / (world * k64 * per_step / (t64 / 1e3))}
+                     "speedup_of_value": value / (world * k64 * per_step / (t64 / 1e3)),
+                     "setup_ms": 1e3 * info64.setup_seconds, "iterate_ms": 1e3 * info64.iterate_seconds,
+                     "kernel_ms": {k: v["ms"] for k, v in prof64.items()},
+                     "roofline": roofline_fp64(prof64, nnz_A, nnz_P, N, M)}
 
     # ---- end-to-end leg: host buffers, H2D + solve + D2H inside the timed region ----
     # the inputs and outputs live in pinned host memory (filled before the timed region)
@@ -464,6 +473,13 @@ def run_ours(args, world, rank, local):
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}
+    if dom in ("dual", "primal"):
+        # the same launch against the random-gather roof: one gather per nonzero
+        gathers = nnz_rows[0]
+        roof["gather_roof"] = {"gathers_per_launch": gathers, "rate_per_s": GATHER_ROOF_PER_S,
+                               "floor_us": 1e6 * gathers / GATHER_ROOF_PER_S,
+                               "frac": gathers / GATHER_ROOF_PER_S / avg_s,
+                               "source": "profiles/gather_ceiling_gb300.md (measured on GB300)"}
     roof.update({"kernel": kname, "avg_launch_us": avg_s * 1e6, "launches": d["launches"],
                  "algorithmic_bytes_per_launch": d["bytes"], "timing": PROFILED_PASS,
                  "traffic": traffic_for(kname, f"large_sparse_qp_n1e6_{args.precision}")
@@ -504,8 +520,11 @@ def run_ours(args, world, rank, local):
     # the other configurations the target compares, as compact sub-records
     # (their own timing; the line's value stays the n=1e6 solve)
     if args.workload == "large_sparse_qp" and args.n == 1_000_000 and not args.no_configs:
-        line["configs"] = {"mpc_batch": mpc_record(pdqp, rank, dev, stream),
-                           "family_ws": family_record(pdqp, rank, dev, stream, train=args.train, held=args.held)}
+        cores = os.cpu_count() or 1
+        cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+        line["configs"] = {"mpc_batch": mpc_record(pdqp, rank, dev, stream, cpu_sample=4 * cores if cpu else 0),
+                           "family_ws": family_record(pdqp, rank, dev, stream, train=args.train, held=args.held,
+                                                      cpu_sample=cores if cpu else 0)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -552,6 +571,64 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1) / 1e3, out
 
 
+def roofline_fp64(prof, nnz_A, nnz_P, N, M):
+    """Roofline of the dominant iteration kernel of a float64 solve: against
+    HBM by its algorithmic bytes and against the nominal float64 rate by its
+    flops (2 per nonzero and ~15 per row of the update); the larger fraction
+    names the bound."""
+    hbm_peak, hbm_src = peak_of("hbm_gbs")
+    kinds = {k: v for k, v in prof.items() if k in ("dual", "primal") and v["launches"]}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = prof[dom]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    nnz, rows, per_row = (nnz_A, M, 8) if dom == "dual" else (nnz_P, N, 15)
+    flops = 2.0 * nnz + per_row * rows
+    frac_hbm = d["bytes"] / avg_s / 1e9 / hbm_peak
+    frac_alu = flops / avg_s / (FP64_NOMINAL_TFLOPS * 1e12)
+    roof = {"kernel": {"dual": "k_dual", "primal": "k_primal"}[dom], "avg_launch_us": avg_s * 1e6,
+            "launches": d["launches"], "algorithmic_bytes_per_launch": d["bytes"],
+            "hbm": {"achieved_gbs": d["bytes"] / avg_s / 1e9, "peak": hbm_peak, "frac": frac_hbm,
+                    "peak_source": hbm_src},
+            "fp64": {"achieved_tflops": flops / avg_s / 1e12, "peak": FP64_NOMINAL_TFLOPS, "frac": frac_alu,
+                     "peak_source": "nominal float64 rate (profiling recipe)"}}
+    roof["bound"] = "alu" if frac_alu >= frac_hbm else "hbm"
+    roof["frac"] = max(frac_alu, frac_hbm)
+    return roof
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            for key in ("model name", "CPU part", "Hardware"):
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_solve_one(inst):
+    from oracle import rapdhg as R
+    R.solve(inst, R.Options())
+    return 1
+
+
+def oracle_all_cores(insts):
+    """The CPU oracle on every host core: independent problems solved by a
+    pool of processes (started with spawn, so no CUDA state is forked);
+    solves per second, the cores used and the sample."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_solve_one, insts[:cores]))          # workers started and warm
+        t = time.perf_counter()
+        list(ex.map(_oracle_solve_one, insts))
+        dt = time.perf_counter() - t
+    return len(insts) / dt, cores
+
+
 def plain_fp64_cold(pdqp, insts, stream, dev):
     """Plain rAPDHG as the paper runs it: float64, from the all-zero start, one
     problem per handle solved after another (each handle built and solved
@@ -595,7 +672,7 @@ MPC_WORKLOAD = ("mpc_batch: 4096 control QPs (12 states, 4 inputs, horizon U{10.
                 "banded equality rows; |u| <= 1, |x| <= 5; Q diag U(0.1,1)), one batched handle")
 
 
-def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True):
+def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True, cpu_sample=0):
     """Configuration 4096 MPC QPs: the batched mixed-precision solve (one
     handle, CUDA-graph chunks) against plain float64 cold solves of the same
     problems, with the dominant kernel's roofline and an end-to-end leg."""
@@ -622,6 +699,12 @@ def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True):
     pdqp.pdqp_destroy(h)
     plain = plain_fp64_cold(pdqp, insts[:plain_sample], stream, dev)
     hbm_peak, hbm_src = peak_of("hbm_gbs")
+    cpu = None
+    if cpu_sample:
+        v, cores = oracle_all_cores(insts[:cpu_sample])
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+               "sample": f"full oracle solves (float64, default options) of the first {cpu_sample} of the 4096 "
+                         "problems, one process per core"}
     rec = {"workload": MPC_WORKLOAD, "metric": "solves/s to 1e-6 relKKT", "value": value, "unit": "solves/s",
            "precision": "mixed (float32 SpMV, float64 checks)", "steps": steps, "ms_per_step": 1e3 * t / steps,
            "iterations": _iters(infos), "rel_kkt_max": max(i.rel_kkt for i in infos),
@@ -632,6 +715,8 @@ def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True):
            "kernel_ms": {k: v["ms"] for k, v in prof.items()},
            "roofline": _roofline_of(prof, hbm_peak, hbm_src, "each launch's bytes over the instances running "
                                                                "at that launch (every problem's own matrix)")}
+    if cpu is not None:
+        rec["cpu_baseline"] = cpu
     if e2e:
         pk = pdqp.pack_instances(insts)
         host = [pinned_copy(pk[k]) for k in ("Q_rowptr", "Q_col", "Q_val", "A_rowptr", "A_col", "A_val",
@@ -658,7 +743,7 @@ FAMILY_WORKLOAD = ("family_qp n=2e4 m=1e4 (m_eq=5e3): the random_sparse_qp patte
 
 
 def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, epochs=20, plain_sample=32,
-                  e2e=True, spmv_threads=0, precision="mixed"):
+                  e2e=True, spmv_threads=0, precision="mixed", cpu_sample=0):
     """Configuration learned warm start: `train` solver-produced solutions of
     the family train the network; `held` held-out members are then solved in
     family handles of `chunk` from its predictions (timed: inference + solve).
@@ -742,6 +827,12 @@ def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, 
     Cp, Bp = Cte[:plain_sample], Bte[:plain_sample]
     members = [dataclasses.replace(fam.base, c=Cp[i], b=Bp[i]) for i in range(len(Cp))]
     plain = plain_fp64_cold(pdqp, members, stream, dev)
+    cpu = None
+    if cpu_sample:
+        v, cores = oracle_all_cores([dataclasses.replace(fam.base, c=Cte[i], b=Bte[i]) for i in range(cpu_sample)])
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
+               "sample": f"full oracle solves (float64, all-zero start: the oracle has no network) of {cpu_sample} "
+                         "held-out members, one process per core"}
 
     # ---- end to end: host (C, B) in, handle + inference + solve, host (x, y) out ----
     e2e_rec = None
@@ -799,6 +890,8 @@ def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, 
                                                               "launch, each running member's vectors once")}
     if e2e_rec is not None:
         rec["e2e"] = e2e_rec
+    if cpu is not None:
+        rec["cpu_baseline"] = cpu
     return rec
 
 

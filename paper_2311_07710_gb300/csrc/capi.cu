@@ -343,6 +343,13 @@ void alloc_il(pdqp_problem* h, bool mixed) {
     if (mixed && !w.ilf[k]) w.ilf[k] = dalloc<float>(h, len[k] * ld);
     if (!mixed && !w.ild[k]) w.ild[k] = dalloc<double>(h, len[k] * ld);
   }
+  const size_t klen[ILK_SLOTS] = {n, n, m, m, m, m, n, n, n, n};
+  for (int k = 0; k < ILK_SLOTS; ++k)
+    if (!w.ilk[k]) w.ilk[k] = dalloc<double>(h, klen[k] * ld);
+  const size_t cnt = (size_t)w.fam_count;
+  const size_t slen[6] = {m, m, n, n, n, n};
+  for (int k = 0; k < 6; ++k)
+    if (!w.kks[k]) w.kks[k] = dalloc<double>(h, slen[k] * cnt);
 }
 
 SolveParams make_params(const pdqp_options& o) {
@@ -515,6 +522,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   const bool use_il = il_ok && (o.spmv_threads == 0 || o.spmv_threads == 3);
   if (mixed) alloc_mixed(h);
   if (use_il) alloc_il(h, mixed);
+  w.il_active = use_il;
   w.detect = o.detect_infeasibility ? 1 : 0;
   w.eps_inf = o.eps_infeasible;
   if (w.detect) alloc_infeas(h, s);

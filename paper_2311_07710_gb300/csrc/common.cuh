@@ -173,3 +173,18 @@ __device__ __forceinline__ void block_reduce(double (&v)[NF], const bool (&is_ma
   }
   __syncthreads();
 }
+
+// Explicitly rounded arithmetic: kernels that must produce the same bits for
+// the same row (the row updates of every iteration-kernel variant, the relKKT
+// row terms of the row-block and the member-interleaved checks) compute with
+// these, so that every operation's rounding is fixed in the source (no fused
+// multiply-add left to the compiler's choice at each inlined call site).
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+

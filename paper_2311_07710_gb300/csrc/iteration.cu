@@ -56,19 +56,6 @@ template <typename V> __device__ __forceinline__ V step_thn(const StepEntry& e);
 template <> __device__ __forceinline__ double step_thn<double>(const StepEntry& e) { return e.theta_next; }
 template <> __device__ __forceinline__ float step_thn<float>(const StepEntry& e) { return e.theta_next_f; }
 
-// Explicitly rounded arithmetic for the row updates: every kernel variant
-// that updates a row calls the same functions, and with each operation's
-// rounding fixed here (no fused multiply-add left to the compiler's choice at
-// each inlined call site) they all produce the same bits.
-__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-
 // The dual update of one row from its sum s = (A x_tilde)_r: y+ and y_bar+
 // (shared by the row-block and the member-interleaved kernels).
 template <typename V>
@@ -680,30 +667,44 @@ __device__ __forceinline__ void il_store(V* p, const V (&v)[IlVec<V>::W]) {
 
 // The row sums of this lane's W members: for each, sequential over the row's
 // entries, each product and sum rounded on its own (no fused multiply-add),
-// as prod[e] is staged and summed by the row-block kernels.
+// as prod[e] is staged and summed by the row-block kernels.  The warp reads
+// the row's indices and values 32 at a time in one coalesced load and hands
+// each entry to all lanes by shuffle, so that the L1 data pipe (the bound of
+// this kernel) moves only the gathered members' values.  Every lane of the
+// warp runs it (the shuffles need the whole warp).
 template <typename V>
 __device__ __forceinline__ void il_row_sum(const FamIL<V>& a, int r, int m0, V (&s)[IlVec<V>::W]) {
   constexpr int W = IlVec<V>::W;
+  const int lane = threadIdx.x & 31;
   const int e0 = a.rp[r], e1 = a.rp[r + 1];
 #pragma unroll
   for (int q = 0; q < W; ++q) s[q] = V(0);
-  int e = e0;
-  for (; e + 2 <= e1; e += 2) {
-    const int c0 = __ldg(a.col + e), c1 = __ldg(a.col + e + 1);
-    const V v0 = __ldg(a.val + e), v1 = __ldg(a.val + e + 1);
-    V z0[W], z1[W];
-    il_load(a.zin + (size_t)c0 * a.ld + m0, z0);
-    il_load(a.zin + (size_t)c1 * a.ld + m0, z1);
+  for (int base = e0; base < e1; base += 32) {
+    int cl = 0;
+    V vl = V(0);
+    if (base + lane < e1) { cl = __ldg(a.col + base + lane); vl = __ldg(a.val + base + lane); }
+    const int cnt = min(32, e1 - base);
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {
+      int c[4];
+      V v[4], z[4][W];
 #pragma unroll
-    for (int q = 0; q < W; ++q) s[q] = r_add(r_add(s[q], r_mul(v0, z0[q])), r_mul(v1, z1[q]));
-  }
-  if (e < e1) {
-    const int c0 = __ldg(a.col + e);
-    const V v0 = __ldg(a.val + e);
-    V z0[W];
-    il_load(a.zin + (size_t)c0 * a.ld + m0, z0);
+      for (int i = 0; i < 4; ++i) { c[i] = __shfl_sync(0xffffffffu, cl, k + i); v[i] = __shfl_sync(0xffffffffu, vl, k + i); }
 #pragma unroll
-    for (int q = 0; q < W; ++q) s[q] = r_add(s[q], r_mul(v0, z0[q]));
+      for (int i = 0; i < 4; ++i) il_load(a.zin + (size_t)c[i] * a.ld + m0, z[i]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < W; ++q) s[q] = r_add(s[q], r_mul(v[i], z[i][q]));
+    }
+    for (; k < cnt; ++k) {
+      const int c = __shfl_sync(0xffffffffu, cl, k);
+      const V v = __shfl_sync(0xffffffffu, vl, k);
+      V z[W];
+      il_load(a.zin + (size_t)c * a.ld + m0, z);
+#pragma unroll
+      for (int q = 0; q < W; ++q) s[q] = r_add(s[q], r_mul(v, z[q]));
+    }
   }
 }
 
@@ -733,10 +734,6 @@ __global__ void __launch_bounds__(IL_NT, 4) k_dual_il(FamIL<V> a, int j) {
   const int r = blockIdx.x * IL_RPB + (threadIdx.x >> 5);
   if (r >= a.rows) return;
   const int k0 = lane * W, m0 = blockIdx.y * GM + k0;
-  bool any = false;
-#pragma unroll
-  for (int q = 0; q < W; ++q) any |= run[k0 + q] != 0;
-  if (!any) return;
   const size_t idx = (size_t)r * a.ld + m0;
   V yo[W], bi[W], yb[W], lo[W], s[W], yn[W], ybn[W];
   il_load_rw(a.v0 + idx, yo);
@@ -767,10 +764,6 @@ __global__ void __launch_bounds__(IL_NT, 4) k_primal_il(FamIL<V> a, int j) {
   const int r = blockIdx.x * IL_RPB + (threadIdx.x >> 5);
   if (r >= a.rows) return;
   const int k0 = lane * W, m0 = blockIdx.y * GM + k0;
-  bool any = false;
-#pragma unroll
-  for (int q = 0; q < W; ++q) any |= run[k0 + q] != 0;
-  if (!any) return;
   const size_t idx = (size_t)r * a.ld + m0;
   V xo[W], xb0[W], cr[W], lr[W], ur[W], s[W], xn[W], xb[W], zo[W], xtn[W];
   il_load_rw(a.w0 + idx, xo);
@@ -792,53 +785,6 @@ __global__ void __launch_bounds__(IL_NT, 4) k_primal_il(FamIL<V> a, int j) {
   il_store(a.w2 + idx, zo);    // x_md of the next iteration
   il_store(a.w3 + idx, xtn);   // x_tilde of the next iteration
   il_store(a.w0 + idx, xn);    // x
-}
-
-// member-major [count][L] (member stride `stride`) <-> interleaved [L][ld],
-// through 32 x 32 shared-memory tiles
-template <typename V>
-__global__ void __launch_bounds__(256) k_to_il(const V* __restrict__ src, long long stride, int L, int count,
-                                               V* __restrict__ dst, int ld) {
-  __shared__ V t[32][33];
-  const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += 8) {
-    const int mem = m0 + k, jj = j0 + threadIdx.x;
-    if (mem < count && jj < L) t[k][threadIdx.x] = src[(size_t)mem * stride + jj];
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += 8) {
-    const int jj = j0 + k, mem = m0 + threadIdx.x;
-    if (jj < L && mem < count) dst[(size_t)jj * ld + mem] = t[threadIdx.x][k];
-  }
-}
-template <typename V>
-__global__ void __launch_bounds__(256) k_from_il(const V* __restrict__ src, int ld, int L, int count,
-                                                 V* __restrict__ dst, long long stride) {
-  __shared__ V t[32][33];
-  const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += 8) {
-    const int jj = j0 + k, mem = m0 + threadIdx.x;
-    if (jj < L && mem < count) t[k][threadIdx.x] = src[(size_t)jj * ld + mem];
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += 8) {
-    const int mem = m0 + k, jj = j0 + threadIdx.x;
-    if (mem < count && jj < L) dst[(size_t)mem * stride + jj] = t[threadIdx.x][k];
-  }
-}
-
-// the transposes take a 2-D block of 32 x 8 threads
-template <typename V>
-static void to_il(const V* src, long long stride, int L, int count, V* dst, int ld, cudaStream_t s) {
-  if (L <= 0 || !src) return;
-  k_to_il<V><<<dim3(cdiv(L, 32), cdiv(count, 32)), dim3(32, 8), 0, s>>>(src, stride, L, count, dst, ld);
-  count_launch();
-}
-template <typename V>
-static void from_il(const V* src, int ld, int L, int count, V* dst, long long stride, cudaStream_t s) {
-  if (L <= 0) return;
-  k_from_il<V><<<dim3(cdiv(L, 32), cdiv(count, 32)), dim3(32, 8), 0, s>>>(src, ld, L, count, dst, stride);
-  count_launch();
 }
 
 // Algorithmic bytes of one family launch: the shared matrix once, the vectors

@@ -378,19 +378,21 @@ __device__ __forceinline__ void kkt_stage(const BCsr<double>& M, int e0, int ne,
 
 // m side of one row and iterate IT: fields IT*4 + {0 max|viol|, 1 max|Ax|,
 // 2 b'y, 3 |dy|^2}, 8: max|b|
+// (every operation explicitly rounded: the row-block and the member-interleaved
+// checks inline this and must agree bit for bit)
 template <int IT>
 __device__ __forceinline__ void kkt_m_row(const KktB& a, double (&f)[9], int r, double s) {
   const double bi = a.b[r];
   if (a.prodAx[IT]) a.prodAx[IT][r] = s;
-  const double Ax = s * (a.iD1 ? a.iD1[r] : 1.0);
-  const double v = Ax - bi;                       // bi - Ax = -v exactly
+  const double Ax = a.iD1 ? r_mul(s, a.iD1[r]) : s;
+  const double v = r_sub(Ax, bi);                 // bi - Ax = -v exactly
   const double viol = a.ineq[r] ? (lt0_bits(v) ? -v : 0.0) : fabs(v);
   f[IT * 4 + 0] = nmax(f[IT * 4 + 0], viol);
   f[IT * 4 + 1] = nmax(f[IT * 4 + 1], fabs(Ax));
   const double yt = a.y[IT][r];
-  f[IT * 4 + 2] = fma(bi, (a.D1 ? a.D1[r] : 1.0) * yt, f[IT * 4 + 2]);
-  const double dy = a.ay ? yt - a.ay[r] : 0.0;
-  f[IT * 4 + 3] = fma(dy, dy, f[IT * 4 + 3]);
+  f[IT * 4 + 2] = r_fma(bi, a.D1 ? r_mul(a.D1[r], yt) : yt, f[IT * 4 + 2]);
+  const double dy = a.ay ? r_sub(yt, a.ay[r]) : 0.0;
+  f[IT * 4 + 3] = r_fma(dy, dy, f[IT * 4 + 3]);
   if (IT == 0) f[8] = nmax(f[8], fabs(bi));
 }
 
@@ -399,27 +401,26 @@ __device__ __forceinline__ void kkt_m_row(const KktB& a, double (&f)[9], int r, 
 template <int IT, bool LR>
 __device__ __forceinline__ void kkt_n_row(const KktB& a, double (&f)[15], int r, double sq, double sa) {
   const double cj = a.c[r], lj = a.l[r], uj = a.u[r];
-  const double d2 = a.D2 ? a.D2[r] : 1.0, id2 = a.iD2 ? a.iD2[r] : 1.0;
   double sqt = sq;
-  if constexpr (LR) sqt += lr_row<double, double, double>(a.F, a.wlr + IT * a.r, a.r, r);
+  if constexpr (LR) sqt = r_add(sqt, lr_row<double, double, double>(a.F, a.wlr + IT * a.r, a.r, r));
   if (a.prodQx[IT]) { a.prodQx[IT][r] = sqt; a.prodATy[IT][r] = -sa; }
-  const double Qx = sqt * id2, ATy = -sa * id2;
+  const double Qx = a.iD2 ? r_mul(sqt, a.iD2[r]) : sqt, ATy = a.iD2 ? r_mul(-sa, a.iD2[r]) : -sa;
   const double xt = a.x[IT][r];
-  const double xj = d2 * xt;
-  const double g = Qx + cj - ATy;
+  const double xj = a.D2 ? r_mul(a.D2[r], xt) : xt;
+  const double g = r_sub(r_add(Qx, cj), ATy);
   // lam = proj of g onto Lambda_j: R (both bounds finite), R+ (only l), R- (only u), {0}
   const bool lf = finite_bits(lj), uf = finite_bits(uj);
   const double lam = (lf && uf) ? g : (lf ? (gt0_bits(g) ? g : 0.0) : (uf ? (lt0_bits(g) ? g : 0.0) : 0.0));
-  f[IT * 7 + 0] = nmax(f[IT * 7 + 0], fabs(g - lam));
+  f[IT * 7 + 0] = nmax(f[IT * 7 + 0], fabs(r_sub(g, lam)));
   f[IT * 7 + 1] = nmax(f[IT * 7 + 1], fabs(Qx));
   f[IT * 7 + 2] = nmax(f[IT * 7 + 2], fabs(ATy));
-  f[IT * 7 + 3] = fma(xj, Qx, f[IT * 7 + 3]);
-  f[IT * 7 + 4] = fma(cj, xj, f[IT * 7 + 4]);
+  f[IT * 7 + 3] = r_fma(xj, Qx, f[IT * 7 + 3]);
+  f[IT * 7 + 4] = r_fma(cj, xj, f[IT * 7 + 4]);
   // l lam+ - u lam-: lam > 0 only with l finite, lam < 0 only with u finite
   const double bound = gt0_bits(lam) ? lj : (lt0_bits(lam) ? uj : 0.0);
-  f[IT * 7 + 5] = fma(bound, lam, f[IT * 7 + 5]);
-  const double dx = a.ax ? xt - a.ax[r] : 0.0;
-  f[IT * 7 + 6] = fma(dx, dx, f[IT * 7 + 6]);
+  f[IT * 7 + 5] = r_fma(bound, lam, f[IT * 7 + 5]);
+  const double dx = a.ax ? r_sub(xt, a.ax[r]) : 0.0;
+  f[IT * 7 + 6] = r_fma(dx, dx, f[IT * 7 + 6]);
   if (IT == 0) f[14] = nmax(f[14], fabs(cj));
 }
 
@@ -543,6 +544,151 @@ static void launch_kkt(const Work& w, const KktB& a, cudaStream_t s) {
   if (w.m > 0) launch(k_kkt_m<NIT>, w.A.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
   if (a.F) launch(k_kkt_n<NIT, true>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
   else launch(k_kkt_n<NIT, false>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
+}
+
+// --------------------------------------------------------------------------
+// The check of a family handle (members sharing the matrix) on
+// member-interleaved vectors: k_kkt_sums_il forms every member's row sums of
+// A x, Q x and A'y for the current and the average iterate with one warp per
+// row for 64 members (coalesced 16-byte loads of the gathered entries), each
+// sum sequential over the row's entries by FMA as the row-block kernels sum
+// their staged values; the sums go back to the member-major layout and
+// k_kkt_m_sums / k_kkt_n_sums take them through the row terms and the block
+// reduction of k_kkt_m / k_kkt_n, item for item: the partials are bitwise
+// those of the row-block check.
+// --------------------------------------------------------------------------
+struct KktIL {
+  const int *rpA, *colA, *rpP, *colP, *splitP;   // one member's A and P (local columns)
+  const double *valA, *valP;                     // scaled values
+  const double* x[2];                            // interleaved iterates [n x ld], [m x ld]
+  const double* y[2];
+  double* sA[2];                                 // interleaved row sums: A x [m x ld]
+  double* sQ[2];                                 // Q x [n x ld]
+  double* sT[2];                                 // A'y [n x ld] (P's -A' part summed)
+  int n, m, ld, count;
+  const DevState* st;
+};
+
+constexpr int KIL_MEM = 64;   // members per warp (two float64 per lane)
+
+__global__ void __launch_bounds__(256, 4) k_kkt_sums_il(KktIL a, int side) {
+  __shared__ int run_any;
+  const int lane = threadIdx.x & 31, r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int m0 = blockIdx.y * KIL_MEM + 2 * lane;
+  const bool run0 = m0 < a.count && a.st[m0].status == ST_RUNNING;
+  const bool run1 = m0 + 1 < a.count && a.st[m0 + 1].status == ST_RUNNING;
+  if (threadIdx.x == 0) run_any = 0;
+  __syncthreads();
+  if (run0 || run1) run_any = 1;
+  __syncthreads();
+  if (!run_any) return;
+  const int rows = side == 0 ? a.m : a.n;
+  if (r >= rows) return;    // uniform over the warp: every lane stays for the shuffles
+  const size_t ld = (size_t)a.ld;
+  const int lane_ = threadIdx.x & 31;
+  double s[2][2][2] = {};   // [part: Q or A x / A'y][iterate][member]
+  // the row's entries 32 at a time by one coalesced load, handed to every
+  // lane by shuffle; each sum sequential over the entries by FMA
+  auto accum = [&](const int* __restrict__ col, const double* __restrict__ val, int e0, int e1, int part,
+                   const double* const* z, int coff) {
+    for (int base = e0; base < e1; base += 32) {
+      int cl = 0;
+      double vl = 0.0;
+      if (base + lane_ < e1) { cl = __ldg(col + base + lane_); vl = __ldg(val + base + lane_); }
+      const int cnt = min(32, e1 - base);
+      for (int k = 0; k < cnt; ++k) {
+        const double v = __shfl_sync(0xffffffffu, vl, k);
+        const size_t c = (size_t)(__shfl_sync(0xffffffffu, cl, k) - coff) * ld + m0;
+        const double2 z0 = __ldg(reinterpret_cast<const double2*>(z[0] + c));
+        const double2 z1 = __ldg(reinterpret_cast<const double2*>(z[1] + c));
+        s[part][0][0] = r_fma(v, z0.x, s[part][0][0]);
+        s[part][0][1] = r_fma(v, z0.y, s[part][0][1]);
+        s[part][1][0] = r_fma(v, z1.x, s[part][1][0]);
+        s[part][1][1] = r_fma(v, z1.y, s[part][1][1]);
+      }
+    }
+  };
+  const size_t idx = (size_t)r * ld + m0;
+  if (side == 0) {
+    accum(a.colA, a.valA, a.rpA[r], a.rpA[r + 1], 0, a.x, 0);
+    for (int it = 0; it < 2; ++it)
+      *reinterpret_cast<double2*>(a.sA[it] + idx) = make_double2(s[0][it][0], s[0][it][1]);
+  } else {
+    const int sp = a.splitP[r];
+    accum(a.colP, a.valP, a.rpP[r], sp, 0, a.x, 0);
+    accum(a.colP, a.valP, sp, a.rpP[r + 1], 1, a.y, a.n);
+    for (int it = 0; it < 2; ++it) {
+      *reinterpret_cast<double2*>(a.sQ[it] + idx) = make_double2(s[0][it][0], s[0][it][1]);
+      *reinterpret_cast<double2*>(a.sT[it] + idx) = make_double2(s[1][it][0], s[1][it][1]);
+    }
+  }
+}
+
+// k_kkt_m / k_kkt_n on given row sums (member-major; rows of at most one row block)
+__global__ void __launch_bounds__(BNT) k_kkt_m_sums(KktB a, const double* __restrict__ s0,
+                                                     const double* __restrict__ s1) {
+  __shared__ double sh[9 * BNT];
+  double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int tid = threadIdx.x;
+  if (a.st && a.st[a.blk_inst_A[blockIdx.x]].status != ST_RUNNING) return;
+  const int r0 = a.A.blk[blockIdx.x], nr = a.A.blk[blockIdx.x + 1] - r0;
+  for (int q = tid; q < nr * 2; q += BNT) {
+    const int it = q >= nr ? 1 : 0, t = q - it * nr;
+    if (it == 0) kkt_m_row<0>(a, f, r0 + t, s0[r0 + t]);
+    else kkt_m_row<1>(a, f, r0 + t, s1[r0 + t]);
+  }
+  block_reduce_smem<9, BNT>(f, 0x133u, sh);
+  if (tid == 0)
+    for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
+}
+
+__global__ void __launch_bounds__(BNT) k_kkt_n_sums(KktB a, const double* __restrict__ q0,
+                                                     const double* __restrict__ q1, const double* __restrict__ t0,
+                                                     const double* __restrict__ t1) {
+  __shared__ double sh[15 * BNT];
+  double f[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) f[k] = 0.0;
+  const int tid = threadIdx.x;
+  if (a.st && a.st[a.blk_inst_P[blockIdx.x]].status != ST_RUNNING) return;
+  const int r0 = a.P.blk[blockIdx.x], nr = a.P.blk[blockIdx.x + 1] - r0;
+  for (int q = tid; q < nr * 2; q += BNT) {
+    const int it = q >= nr ? 1 : 0, t = q - it * nr;
+    if (it == 0) kkt_n_row<0, false>(a, f, r0 + t, q0[r0 + t], t0[r0 + t]);
+    else kkt_n_row<1, false>(a, f, r0 + t, q1[r0 + t], t1[r0 + t]);
+  }
+  block_reduce_smem<15, BNT>(f, 0x4387u, sh);
+  if (tid == 0)
+    for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
+}
+
+// the check's relKKT partials of a family handle through the interleaved sums
+static void launch_kkt_il(Work& w, const KktB& a, cudaStream_t s) {
+  const int n = w.fam_n, m = w.fam_m, cnt = w.fam_count, ld = w.fam_ld;
+  double* const* I = w.ilk;
+  to_il<double>(a.x[0], n, n, cnt, I[ILK_X0], ld, s);
+  to_il<double>(a.x[1], n, n, cnt, I[ILK_X1], ld, s);
+  to_il<double>(a.y[0], m, m, cnt, I[ILK_Y0], ld, s);
+  to_il<double>(a.y[1], m, m, cnt, I[ILK_Y1], ld, s);
+  KktIL k{};
+  k.rpA = w.A.rp; k.colA = w.A.col; k.valA = w.A.sval;
+  k.rpP = w.P.rp; k.colP = w.famP_col; k.valP = w.P.sval; k.splitP = w.P.split;
+  k.x[0] = I[ILK_X0]; k.x[1] = I[ILK_X1]; k.y[0] = I[ILK_Y0]; k.y[1] = I[ILK_Y1];
+  k.sA[0] = I[ILK_SA0]; k.sA[1] = I[ILK_SA1];
+  k.sQ[0] = I[ILK_SQ0]; k.sQ[1] = I[ILK_SQ1]; k.sT[0] = I[ILK_ST0]; k.sT[1] = I[ILK_ST1];
+  k.n = n; k.m = m; k.ld = ld; k.count = cnt; k.st = w.st;
+  if (m > 0) launch(k_kkt_sums_il, dim3(cdiv(m, 8), ld / KIL_MEM), 256, 0, s, k, 0);
+  launch(k_kkt_sums_il, dim3(cdiv(n, 8), ld / KIL_MEM), 256, 0, s, k, 1);
+  double* const* S = w.kks;
+  from_il<double>(I[ILK_SA0], ld, m, cnt, S[0], m, s);
+  from_il<double>(I[ILK_SA1], ld, m, cnt, S[1], m, s);
+  from_il<double>(I[ILK_SQ0], ld, n, cnt, S[2], n, s);
+  from_il<double>(I[ILK_SQ1], ld, n, cnt, S[3], n, s);
+  from_il<double>(I[ILK_ST0], ld, n, cnt, S[4], n, s);
+  from_il<double>(I[ILK_ST1], ld, n, cnt, S[5], n, s);
+  if (w.m > 0) launch(k_kkt_m_sums, w.A.nblk, BNT, 0, s, a, (const double*)S[0], (const double*)S[1]);
+  launch(k_kkt_n_sums, w.P.nblk, BNT, 0, s, a, (const double*)S[2], (const double*)S[3], (const double*)S[4],
+         (const double*)S[5]);
 }
 
 // reduce the field-major partials of k_kkt_m / k_kkt_n (blocks [bm0, bm1) of
@@ -1930,7 +2076,8 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     lowrank_ft<double, double>(w, w.Fd, a.x[0], a.x[1], s);
     a.F = w.Fd; a.wlr = w.wlr; a.r = w.r;
   }
-  launch_kkt<2>(w, a, s);
+  if (w.il_active) launch_kkt_il(w, a, s);   // a family handle on interleaved vectors (no low-rank term)
+  else launch_kkt<2>(w, a, s);
   {
     const dim3 grid(w.count, std::max(w.maxchunk_n, w.maxchunk_m));
     launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,

@@ -150,6 +150,53 @@ __device__ __forceinline__ V lr_row(const FV* __restrict__ F, const W* __restric
   return s;
 }
 
+// member-major [count][L] (member stride `stride`) <-> interleaved [L][ld],
+// through 32 x 32 shared-memory tiles
+template <typename V>
+__global__ void __launch_bounds__(256) k_to_il(const V* __restrict__ src, long long stride, int L, int count,
+                                               V* __restrict__ dst, int ld) {
+  __shared__ V t[32][33];
+  const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int mem = m0 + k, jj = j0 + threadIdx.x;
+    if (mem < count && jj < L) t[k][threadIdx.x] = src[(size_t)mem * stride + jj];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int jj = j0 + k, mem = m0 + threadIdx.x;
+    if (jj < L && mem < count) dst[(size_t)jj * ld + mem] = t[threadIdx.x][k];
+  }
+}
+template <typename V>
+__global__ void __launch_bounds__(256) k_from_il(const V* __restrict__ src, int ld, int L, int count,
+                                                 V* __restrict__ dst, long long stride) {
+  __shared__ V t[32][33];
+  const int j0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int jj = j0 + k, mem = m0 + threadIdx.x;
+    if (jj < L && mem < count) t[k][threadIdx.x] = src[(size_t)jj * ld + mem];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int mem = m0 + k, jj = j0 + threadIdx.x;
+    if (mem < count && jj < L) dst[(size_t)mem * stride + jj] = t[threadIdx.x][k];
+  }
+}
+
+// the transposes take a 2-D block of 32 x 8 threads
+template <typename V>
+static void to_il(const V* src, long long stride, int L, int count, V* dst, int ld, cudaStream_t s) {
+  if (L <= 0 || !src) return;
+  k_to_il<V><<<dim3(cdiv(L, 32), cdiv(count, 32)), dim3(32, 8), 0, s>>>(src, stride, L, count, dst, ld);
+  count_launch();
+}
+template <typename V>
+static void from_il(const V* src, int ld, int L, int count, V* dst, long long stride, cudaStream_t s) {
+  if (L <= 0) return;
+  k_from_il<V><<<dim3(cdiv(L, 32), cdiv(count, 32)), dim3(32, 8), 0, s>>>(src, ld, L, count, dst, stride);
+  count_launch();
+}
+
 template <typename V> static const V* lr_factor(Work& w);
 template <> inline const double* lr_factor<double>(Work& w) { return w.Fd; }
 template <> inline const float* lr_factor<float>(Work& w) { return w.Fs; }

@@ -12,6 +12,8 @@
 
 // Slots of the member-interleaved vectors of a family handle.
 enum { IL_Z0 = 0, IL_Z1, IL_X, IL_XBAR, IL_XT, IL_YBAR, IL_C, IL_L, IL_U, IL_B, IL_YLO, IL_SLOTS };
+// ... and of the family check (float64): the iterates and the row sums.
+enum { ILK_X0 = 0, ILK_X1, ILK_Y0, ILK_Y1, ILK_SA0, ILK_SA1, ILK_SQ0, ILK_SQ1, ILK_ST0, ILK_ST1, ILK_SLOTS };
 
 // Row blocks: every CUDA block of the SpMV kernels takes whole rows
 // [blk[b], blk[b+1]) holding at most BNNZ nonzeros and BROWS rows; a row longer
@@ -166,6 +168,9 @@ struct Work {
   bool fam_il = false;                       // eligible: no long rows, no low-rank term
   double* ild[11] = {};                      // float64 (allocated on first use)
   float* ilf[11] = {};                       // float32
+  double* ilk[10] = {};                      // the check's interleaved iterates and row sums (ILK_*)
+  double* kks[6] = {};                       // the check's row sums, member-major: A x (2) [m], Q x (2), A'y (2) [n]
+  bool il_active = false;                    // this solve runs the interleaved kernels
   InfState* inf = nullptr;                   // [count]
   double *inf_x[2] = {nullptr, nullptr};     // rays of the current / average iterate, scaled [n]
   double *inf_y[2] = {nullptr, nullptr};     // [m]
