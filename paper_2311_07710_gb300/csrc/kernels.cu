@@ -916,7 +916,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
     }
   };
   if (ne <= BNNZ) {
-    stage_products<NT>(P, zin, e0, ne, r0, nr, prod, srp);
+    // once the instance's ||Q|| has converged only the A' part is gathered
+    stage_products<NT>(P, zin, e0, ne, r0, nr, prod, srp, doQ ? 0 : la.n);
     for (int t = tid; t < nr; t += NT) ssp[t] = P.split[r0 + t] - e0;
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
