@@ -71,7 +71,7 @@ def parse():
                     help="skip the side measurement of plain float64 solves")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 2, 3, 256, 512])
+    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 2, 3, 4, 256, 512])
     ap.add_argument("--workload", default="large_sparse_qp",
                     choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws", "gemm", "algorithms"],
                     help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
@@ -516,7 +516,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.n == 1_000_000 and \
             args.workload == "large_sparse_qp":
         v, t_solve, sample = oracle_sample(inst)
-        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+                                "cores_available": os.cpu_count(), "cpu": cpu_model(),
+                                "note": "one problem: the oracle's CSR products run on one thread; the batch "
+                                        "configurations' sub-records time the oracle on every core"}
     # the other configurations the target compares, as compact sub-records
     # (their own timing; the line's value stays the n=1e6 solve)
     if args.workload == "large_sparse_qp" and args.n == 1_000_000 and not args.no_configs:
@@ -597,6 +600,14 @@ def roofline_fp64(prof, nnz_A, nnz_P, N, M):
 
 
 def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the oracle legs."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             for key in ("model name", "CPU part", "Hardware"):
@@ -610,23 +621,35 @@ def cpu_model():
 
 def _oracle_solve_one(inst):
     from oracle import rapdhg as R
-    R.solve(inst, R.Options())
-    return 1
+    r = R.solve(inst, R.Options())
+    return r.x, r.y, r.kkt["primal_obj"]
 
 
 def oracle_all_cores(insts):
     """The CPU oracle on every host core: independent problems solved by a
     pool of processes (started with spawn, so no CUDA state is forked);
-    solves per second, the cores used and the sample."""
+    solves per second, the cores used and the oracle's solutions."""
     import concurrent.futures as cf
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
         list(ex.map(_oracle_solve_one, insts[:cores]))          # workers started and warm
         t = time.perf_counter()
-        list(ex.map(_oracle_solve_one, insts))
+        sols = list(ex.map(_oracle_solve_one, insts))
         dt = time.perf_counter() - t
-    return len(insts) / dt, cores
+    return len(insts) / dt, cores, sols
+
+
+def agreement(sols, xs, ys, objs):
+    """The GPU's answers against the oracle's for the same problems: the worst
+    objective relative error and max |v - v*| / (1 + |v*|) over x and y."""
+    eo = ex = ey = 0.0
+    for (xo, yo, oo), x, y, o in zip(sols, xs, ys, objs):
+        eo = max(eo, abs(o - oo) / (1.0 + abs(oo)))
+        ex = max(ex, float(np.max(np.abs(x - xo) / (1.0 + np.abs(xo)))))
+        if len(yo):
+            ey = max(ey, float(np.max(np.abs(y - yo) / (1.0 + np.abs(yo)))))
+    return {"obj_rel_err_max": eo, "x_max_rel_err": ex, "y_max_rel_err": ey, "problems": len(sols)}
 
 
 def plain_fp64_cold(pdqp, insts, stream, dev):
@@ -690,6 +713,7 @@ def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True, cpu_
     launches = pdqp.pdqp_launch_count() - l0
     infos = pdqp.pdqp_batch_info(h)
     value = steps * len(insts) / t
+    x_mixed, y_mixed = x.clone(), y.clone()
     prof = profiled_pass(pdqp, h, lambda: pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream), 1, dev)
     # the same handle in plain float64 from the zero start (batched)
     o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64)
@@ -701,10 +725,16 @@ def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True, cpu_
     hbm_peak, hbm_src = peak_of("hbm_gbs")
     cpu = None
     if cpu_sample:
-        v, cores = oracle_all_cores(insts[:cpu_sample])
+        v, cores, sols = oracle_all_cores(insts[:cpu_sample])
+        xo = np.cumsum([0] + [i.n for i in insts[:cpu_sample]])
+        yo = np.cumsum([0] + [i.m for i in insts[:cpu_sample]])
+        xh, yh = x_mixed[:xo[-1]].cpu().numpy(), y_mixed[:yo[-1]].cpu().numpy()
         cpu = {"value": v, "unit": "solves/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                "sample": f"full oracle solves (float64, default options) of the first {cpu_sample} of the 4096 "
-                         "problems, one process per core"}
+                         "problems, one process per core",
+               "vs_oracle": agreement(sols, [xh[xo[k]:xo[k + 1]] for k in range(cpu_sample)],
+                                      [yh[yo[k]:yo[k + 1]] for k in range(cpu_sample)],
+                                      [i.primal_obj for i in infos[:cpu_sample]])}
     rec = {"workload": MPC_WORKLOAD, "metric": "solves/s to 1e-6 relKKT", "value": value, "unit": "solves/s",
            "precision": "mixed (float32 SpMV, float64 checks)", "steps": steps, "ms_per_step": 1e3 * t / steps,
            "iterations": _iters(infos), "rel_kkt_max": max(i.rel_kkt for i in infos),
@@ -811,6 +841,7 @@ def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, 
     # ---- the first handle's members from other starts and in plain float64 ----
     h, c, b, k, x, y, X0, Y0 = first
     Xw, Yw = X0.clone(), Y0.clone()
+    Xw_out, Yw_out = x.view(k, n).clone(), y.view(k, m).clone()   # the first handle's warm-started answers
     t_cold, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream))
     cold_infos = pdqp.pdqp_batch_info(h)
     Xc, Yc = x.view(k, n).clone(), y.view(k, m).clone()
@@ -829,10 +860,13 @@ def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, 
     plain = plain_fp64_cold(pdqp, members, stream, dev)
     cpu = None
     if cpu_sample:
-        v, cores = oracle_all_cores([dataclasses.replace(fam.base, c=Cte[i], b=Bte[i]) for i in range(cpu_sample)])
+        v, cores, sols = oracle_all_cores([dataclasses.replace(fam.base, c=Cte[i], b=Bte[i])
+                                           for i in range(cpu_sample)])
+        Xh, Yh = Xw_out[:cpu_sample].cpu().numpy(), Yw_out[:cpu_sample].cpu().numpy()
         cpu = {"value": v, "unit": "solves/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                "sample": f"full oracle solves (float64, all-zero start: the oracle has no network) of {cpu_sample} "
-                         "held-out members, one process per core"}
+                         "held-out members, one process per core",
+               "vs_oracle": agreement(sols, list(Xh), list(Yh), [i.primal_obj for i in warm_infos[:cpu_sample]])}
 
     # ---- end to end: host (C, B) in, handle + inference + solve, host (x, y) out ----
     e2e_rec = None
