@@ -71,7 +71,7 @@ def parse():
                     help="skip the side measurement of plain float64 solves")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 2, 3, 4, 256, 512])
+    ap.add_argument("--spmv-threads", type=int, default=0, choices=[0, 1, 2, 3, 256, 512])
     ap.add_argument("--workload", default="large_sparse_qp",
                     choices=["large_sparse_qp", "mpc_batch", "random_sparse_qp", "family_ws", "gemm", "algorithms"],
                     help="large_sparse_qp: the n=1e6 QP (default); mpc_batch: 4096 control QPs "
