@@ -121,13 +121,16 @@ typedef struct {
                                 than a row block, no low-rank term; else
                                 PDQP_ERR_INVALID): the iteration vectors interleaved
                                 by member, v[j * members + i], one warp per row for 32
-                                members, so one matrix entry meets 32 members in one
+                                members, so one matrix entry meets 128 members in one
                                 coalesced load,
                                 0 = autotuned: 3 for an eligible family handle, else
-                                the first full chunk of a handle's
-                                first solve times two rounds of 4 iterations of each
-                                eligible variant and the handle keeps the fastest (all
-                                variants give bitwise identical iterates) */
+                                the first full chunk of a handle's first solve in each
+                                precision times two rounds of 3 iterations of each
+                                eligible variant and keeps the fastest for that
+                                precision; the choice is also kept for the process per
+                                problem shape, so later handles of the same sizes,
+                                nonzeros and row blocks start with it (all variants
+                                give bitwise identical iterates) */
   int32_t no_graphs;         /* 0: replay each full chunk of check_period iterations
                                 and its check as one captured CUDA graph; 1: launch
                                 every kernel directly */

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "pdqp.h"
@@ -37,7 +38,7 @@ struct pdqp_problem {
   ChunkGraph graph;
   std::vector<pdqp_info> infos;                       // per instance, from the last solve
   std::vector<void*> allocs;
-  int tuned_nt = 0;                                   // autotuned iteration-kernel variant (0: not yet)
+  int tuned_nt[2] = {0, 0};                           // autotuned variant per precision (0: not yet)
   cudaEvent_t tune_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // Where the last solve stopped (what pdqp_get_state exports): its parameters,
   // the step-table position (iterations run since the table was last filled;
@@ -497,6 +498,35 @@ pdqp_status finish_status(int st) {
   }
 }
 
+// The autotuned iteration-kernel variant of each problem shape (sizes,
+// nonzeros, row blocks, batch count, low-rank rank, precision), kept for the
+// process: a new handle of a shape tuned before starts with its variant
+// instead of timing the candidates again (every variant gives the same bits,
+// so this changes only the time).
+struct TuneKey {
+  long long n, m, nnzP, nnzA;
+  int nblkP, nblkA, nlsegP, nlsegA, count, r, mixed;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, m, nnzP, nnzA, nblkP, nblkA, nlsegP, nlsegA, count, r, mixed) <
+           std::tie(o.n, o.m, o.nnzP, o.nnzA, o.nblkP, o.nblkA, o.nlsegP, o.nlsegA, o.count, o.r, o.mixed);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+TuneKey tune_key(const Work& w, bool mixed) {
+  return TuneKey{w.n, w.m, w.P.nnz, w.A.nnz, w.P.nblk, w.A.nblk, w.P.nlseg, w.A.nlseg, w.count, w.r, mixed ? 1 : 0};
+}
+int tuned_lookup(const Work& w, bool mixed) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(tune_key(w, mixed));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+void tuned_store(const Work& w, bool mixed, int nt) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[tune_key(w, mixed)] = nt;
+}
+
 pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0, const double* y0,
                        double* x_out, double* y_out, pdqp_info* info, int mem, cudaStream_t s) {
   const double t0 = now_s();
@@ -631,10 +661,12 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   const int ncand = cluster_ok ? 4 : 3;
   constexpr int TUNE = 4, ROUNDS = 2;
   const bool autotune = o.spmv_threads == 0 && !use_il;
-  if (autotune && h->tuned_nt) p.spmv_threads = h->tuned_nt;
+  int& tuned = h->tuned_nt[mixed ? 1 : 0];
+  if (autotune && !tuned) tuned = tuned_lookup(w, mixed);   // a handle of the same shape tuned before
+  if (autotune && tuned) p.spmv_threads = tuned;
   while (w.bst_host->running > 0) {
     const long long len = std::min<long long>(o.check_period, o.max_iter - k_total);
-    const bool tune_now = autotune && !h->tuned_nt && len == o.check_period && len >= 2 * ncand * ROUNDS * TUNE;
+    const bool tune_now = autotune && !tuned && len == o.check_period && len >= 2 * ncand * ROUNDS * TUNE;
     // per-kernel event timing needs direct launches (events recorded by graph
     // nodes cannot be timed), so profiling bypasses the graph
     if (tune_now) {
@@ -672,8 +704,9 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       int bc = 0;
       for (int c = 1; c < ncand; ++c)
         if (best_ms[c] < best_ms[bc]) bc = c;
-      h->tuned_nt = kCand[bc];
-      p.spmv_threads = h->tuned_nt;
+      tuned = kCand[bc];
+      tuned_store(w, mixed, tuned);
+      p.spmv_threads = tuned;
       pdqp::iterate_chunk(w, (int)len - j, mixed, p.spmv_threads, s, j);
       pdqp::check(w, p, 1, len, mixed, s);
     } else if (len == o.check_period && !o.no_graphs && !w.prof.on && !compact_now(w, p)) {

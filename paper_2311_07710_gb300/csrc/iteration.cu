@@ -432,6 +432,13 @@ __global__ void __launch_bounds__(NT) k_dual_pipe(DualB<V> a, const int4* __rest
         }
         dual_row(a, es, r, acc, yo, bi, yb, lo);
       }
+    } else if (a.blk_seg) {   // a long row: the sum of its segments (k_long_partials), as k_dual
+      if (tid == 0) {
+        const int2 sg = a.blk_seg[b];
+        V acc = V(0);
+        for (int q = 0; q < sg.y; ++q) acc += a.lpart[sg.x + q];
+        dual_row(a, es, r0, acc, yo, bi, yb, lo);
+      }
     } else {
       V acc = V(0);
       for (int e = e0 + tid; e < e0 + ne; e += NT) acc += a.A.val[e] * __ldg(a.xt + a.A.col[e]);
@@ -485,6 +492,14 @@ __global__ void __launch_bounds__(NT) k_primal_pipe(PrimalB<V> a, const int4* __
         if (t >= NT) { xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r]; }
         if (a.F) primal_row<V, true>(a, es, r, acc, xo, xb, cr, lr, ur);
         else primal_row<V, false>(a, es, r, acc, xo, xb, cr, lr, ur);
+      }
+    } else if (a.blk_seg) {   // a long row: the sum of its segments, as k_primal
+      if (tid == 0) {
+        const int2 sg = a.blk_seg[b];
+        V acc = V(0);
+        for (int q = 0; q < sg.y; ++q) acc += a.lpart[sg.x + q];
+        if (a.F) primal_row<V, true>(a, es, r0, acc, xo, xb, cr, lr, ur);
+        else primal_row<V, false>(a, es, r0, acc, xo, xb, cr, lr, ur);
       }
     } else {
       V acc = V(0);
@@ -540,18 +555,29 @@ static void run_chunk_pipe(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt
   const int gd = std::min(w.A.nblk, w.num_sms * pipe_grid<V, NT>(k_dual_pipe<V, NT>));
   const int gp = std::min(w.P.nblk, w.num_sms * pipe_grid_p<V, NT>(k_primal_pipe<V, NT>));
   const size_t smem = sizeof(PipeSmem<V>);
+  // long rows: segment sums first, the same as the row-block variants
+  V* lpA = sizeof(V) == 4 ? (V*)w.A.lpart_f : (V*)w.A.lpart_d;
+  V* lpP = sizeof(V) == 4 ? (V*)w.P.lpart_f : (V*)w.P.lpart_d;
+  if (w.A.nlseg) { da.blk_seg = w.A.blk_seg; da.lpart = lpA; }
+  if (w.P.nlseg) { pa.blk_seg = w.P.blk_seg; pa.lpart = lpP; }
   for (int j = j0; j < j0 + len; ++j) {
     if (w.r > 0) lowrank_ft1(w, pa.F, (const V*)Z[j & 1], s);
     if (w.m > 0) {
       da.yold = Z[(j + 1) & 1] + w.n;
       da.ynew = Z[j & 1] + w.n;
       if (Pr.on) Pr.begin(0, s, launch_bytes(w, 0, sizeof(V)));
+      if (w.A.nlseg)
+        launch(k_long_partials<V>, w.A.nlseg, 256, 0, s, A, (const V*)xt, (const int4*)w.A.lseg,
+               (const int*)w.blk_inst_A, (const DevState*)w.st, lpA);
       launch(k_dual_pipe<V, NT>, gd, NT, smem, s, da, (const int4*)w.A.meta, w.A.nblk, j);
       if (Pr.on) Pr.end(s);
     }
     pa.zin = Z[j & 1];
     pa.zout = Z[(j + 1) & 1];
     if (Pr.on) Pr.begin(1, s, launch_bytes(w, 1, sizeof(V)));
+    if (w.P.nlseg)
+      launch(k_long_partials<V>, w.P.nlseg, 256, 0, s, P, (const V*)pa.zin, (const int4*)w.P.lseg,
+             (const int*)w.blk_inst_P, (const DevState*)w.st, lpP);
     launch(k_primal_pipe<V, NT>, gp, NT, smem, s, pa, (const int4*)w.P.meta, w.P.nblk, j);
     if (Pr.on) Pr.end(s);
   }
