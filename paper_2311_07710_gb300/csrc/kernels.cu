@@ -1812,14 +1812,12 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
 }
 
+// The norm estimates run at one width whatever the iteration kernels' variant
+// (long rows are summed with the block's stride), so that variant never
+// changes the step sizes.
 void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s) {
-  if (p.spmv_threads == 512) {
-    if (mixed) lanczos_step_t<float, 512>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, w.flw, s);
-    else lanczos_step_t<double, 512>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, w.lw, s);
-  } else {
-    if (mixed) lanczos_step_t<float, 256>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, w.flw, s);
-    else lanczos_step_t<double, 256>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, w.lw, s);
-  }
+  if (mixed) lanczos_step_t<float, 256>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, w.flw, s);
+  else lanczos_step_t<double, 256>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, w.lw, s);
 }
 
 void count_running(Work& w, cudaStream_t s) {

@@ -119,3 +119,20 @@ def test_batch_with_a_member_without_rows():
         np.testing.assert_array_equal(y[yo:yo + inst.m], ys)
         xo += inst.n
         yo += inst.m
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_every_variant_gives_the_same_bits_with_long_rows(precision):
+    """Rows past a row block (2049 and 4096 entries, P's rows of those A'
+    columns) are summed from the same segment sums by every iteration-kernel
+    variant, the pipelined persistent one included, so the autotuner's choice
+    never changes the answer there either."""
+    pd = G.lib()
+    inst = long_rows()
+    runs = {nt: G.solve(inst, precision=precision, spmv_threads=nt) for nt in (256, 512, 1)}
+    for nt, (st, info, x, y) in runs.items():
+        assert st == pd.PDQP_OK and info.spmv_threads == nt
+    for nt in (512, 1):
+        assert runs[nt][1].iterations == runs[256][1].iterations
+        np.testing.assert_array_equal(runs[nt][2], runs[256][2])
+        np.testing.assert_array_equal(runs[nt][3], runs[256][3])
