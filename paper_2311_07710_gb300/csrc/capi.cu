@@ -52,6 +52,9 @@ struct pdqp_problem {
   SolveParams resume_p{};
   int resume_pos = 0, resume_recheck = 0;
   long long resume_k_total = 0;
+  // A family handle's one-member problem: the members share its matrix, so the
+  // scaling and the norm estimates run on it once and are copied to all.
+  pdqp_problem* tmpl = nullptr;
 };
 
 static thread_local std::string g_create_error;
@@ -595,30 +598,47 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   CK(cudaEventRecord(h->ev[0], s));
   // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle (a resumed
   // solve has its scaling vector from the loaded state)
+  // A family handle runs both on its template (one member, the same row
+  // blocks, sums and thread mapping as each member's part of the replicated
+  // matrix, hence the same bits) unless a low-rank term, which the template
+  // lacks, enters the norm of Q.
+  pdqp_problem* const ft = h->tmpl;
+  Work& sw = ft ? ft->w : w;
+  if (ft) ft->alloc_stream = s;
   if (!resuming) {
-    pdqp::scale_reset(w, s);
+    pdqp::scale_reset(sw, s);
     if (o.scaling) {
-      for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(w, 0, s);
-      if (o.l2_scaling) pdqp::scale_pass(w, 1, s);
-      if (o.pock_chambolle) pdqp::scale_pass(w, 2, s);
+      for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(sw, 0, s);
+      if (o.l2_scaling) pdqp::scale_pass(sw, 1, s);
+      if (o.pock_chambolle) pdqp::scale_pass(sw, 2, s);
     }
+    if (ft) pdqp::family_scaling(w, sw, s);
   }
   pdqp::scale_apply(w, mixed, s);
 
   // spectral norms of the scaled matrices (a resumed solve keeps its own)
   const bool run_lanczos = !resuming && !(o.norm_A > 0.0 && o.norm_Q > 0.0);
+  pdqp_problem* const lh = ft && w.r == 0 ? ft : h;
+  Work& lw = lh->w;
   if (run_lanczos) {
-    pdqp::lanczos_init(w, mixed, s);
+    if (lh != h) {
+      if (mixed) alloc_mixed(lh);
+      pdqp::scale_apply(lw, mixed, s);
+    }
+    pdqp::lanczos_init(lw, mixed, s);
     for (int t = 0; t < o.norm_iters; ++t) {
-      pdqp::lanczos_step(w, t, p, mixed, s);
+      pdqp::lanczos_step(lw, t, p, mixed, s);
       if ((t & 7) == 7) {
-        pdqp::count_running(w, s);
-        sync_batch(h, s);
-        if (w.bst_host->lz_running == 0) break;
+        pdqp::count_running(lw, s);
+        sync_batch(lh, s);
+        if (lw.bst_host->lz_running == 0) break;
       }
     }
   }
-  if (!resuming) pdqp::norms_finish(w, o.norm_A, o.norm_Q, s);
+  if (!resuming) {
+    pdqp::norms_finish(lw, o.norm_A, o.norm_Q, s);
+    if (lh != h) pdqp::family_norms(w, lw, s);
+  }
   CK(cudaEventRecord(h->ev[1], s));
   long long k_total = 0;
   int pos = 0;   // step-table position: iterations since the table was last filled
@@ -1332,7 +1352,7 @@ pdqp_problem* build_family(const InstanceIn& base, int count, const double* C, c
     pdqp_destroy(t);
     throw;
   }
-  pdqp_destroy(t);
+  h->tmpl = t;
   return h;
 }
 
@@ -2315,6 +2335,7 @@ void pdqp_destroy(pdqp_handle h) {
     if (e) cudaEventDestroy(e);
   if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->tmpl) pdqp_destroy(h->tmpl);
   delete h;
 }
 

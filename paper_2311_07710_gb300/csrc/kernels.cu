@@ -1829,6 +1829,36 @@ void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s) {
   launch(k_set_norms, cdiv(w.count, 256), 256, 0, s, w.st, w.count, normA_opt, normQ_opt);
 }
 
+// dsc = [D2 of every member ; D1 of every member] from the template's [D2 ; D1]
+__global__ void k_family_scaling(const double* __restrict__ t, int n_t, int m_t, long long N, long long total,
+                                 double* __restrict__ dsc) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    dsc[i] = i < N ? t[i % n_t] : t[n_t + (i - N) % m_t];
+}
+
+__global__ void k_family_norms(const DevState* __restrict__ t, int count, DevState* __restrict__ sts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    DevState* st = sts + i;
+    st->normA = t->normA;
+    st->normQ = t->normQ;
+    st->pi_iters = t->pi_iters;
+    for (int o = 0; o < 2; ++o) {
+      st->pi_lam[o] = t->pi_lam[o];
+      st->pi_done[o] = t->pi_done[o];
+    }
+  }
+}
+
+void family_scaling(Work& w, const Work& t, cudaStream_t s) {
+  const long long N = (long long)w.n, total = N + w.m;
+  launch(k_family_scaling, std::min(cdiv(total, 256), 8 * w.num_sms), 256, 0, s, (const double*)t.dsc, t.n, t.m, N,
+         total, w.dsc);
+}
+
+void family_norms(Work& w, const Work& t, cudaStream_t s) {
+  launch(k_family_norms, cdiv(w.count, 256), 256, 0, s, (const DevState*)t.st, w.count, w.st);
+}
+
 static MixedArgs mixed_args(Work& w) {
   MixedArgs a{};
   a.n = w.n; a.m = w.m;

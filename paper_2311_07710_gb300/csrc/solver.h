@@ -199,6 +199,10 @@ void scale_apply(Work& w, bool mixed, cudaStream_t s);
 void lanczos_init(Work& w, bool mixed, cudaStream_t s);
 void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s);
 void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
+// A family handle's members share the matrix, so its scaling vector and norm
+// estimates are those of its one-member template t: copy them to every member.
+void family_scaling(Work& w, const Work& t, cudaStream_t s);
+void family_norms(Work& w, const Work& t, cudaStream_t s);
 void count_running(Work& w, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 

@@ -105,8 +105,10 @@ def test_batch_iterates_match_oracle(pdqp):
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_family_handle_reproduces_batch(pdqp, precision):
-    """A family handle (structure replicated on the device) gives the batch
-    handle's results bit for bit, from zero and from a given start."""
+    """A family handle (structure replicated on the device; scaling and norm
+    estimates computed once on its one-member template) gives the batch
+    handle's results bit for bit, norms included, from zero and from a given
+    start."""
     fam = qpgen.family_qp(n=300, m=150)
     C, B = fam.params(0, 7)
     insts = []
@@ -125,7 +127,8 @@ def test_family_handle_reproduces_batch(pdqp, precision):
                 x, y = np.zeros(N), np.zeros(M)
                 st, _ = pdqp.pdqp_solve(h, pdqp.pdqp_default_options(precision=precision), x0=x0, y0=y0,
                                         x_out=x, y_out=y)
-                out.append((st, [(i.status, i.iterations) for i in pdqp.pdqp_batch_info(h)], x, y))
+                out.append((st, [(i.status, i.iterations, i.norm_A, i.norm_Q, i.norm_iters)
+                                 for i in pdqp.pdqp_batch_info(h)], x, y))
             finally:
                 pdqp.pdqp_destroy(h)
         assert out[0][0] == out[1][0] == pdqp.PDQP_OK
