@@ -608,9 +608,12 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   if (!resuming) {
     pdqp::scale_reset(sw, s);
     if (o.scaling) {
-      for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(sw, 0, s);
-      if (o.l2_scaling) pdqp::scale_pass(sw, 1, s);
-      if (o.pock_chambolle) pdqp::scale_pass(sw, 2, s);
+      int pass = 0;
+      for (int i = 0; i < o.ruiz_iters; ++i) pdqp::scale_pass(sw, 0, pass++, s);
+      if (o.l2_scaling) pdqp::scale_pass(sw, 1, pass++, s);
+      if (o.pock_chambolle) pdqp::scale_pass(sw, 2, pass++, s);
+      if ((pass & 1) && sw.n + sw.m > 0)   // the factors are in the second buffer
+        CK(cudaMemcpyAsync(sw.dsc, sw.nu, ((size_t)sw.n + sw.m) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     if (ft) pdqp::family_scaling(w, sw, s);
   }

@@ -723,10 +723,15 @@ __device__ void reduce_kkt_blocks(const double* __restrict__ pm, int nbm, int bm
 // K = [[Q, A'], [A, 0]] -- the rows of P (index j) and of A (index n+i); the
 // columns of P already index d = (D2, D1).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(BNT) k_scale_norms(BCsr<double> M, const double* __restrict__ d, int doff,
-                                                     int dcol_off, double* __restrict__ nu, int kind) {
-  // row norm of (D M D)_r = d_r * norm_j(|m_rj| d_j): the column factor is
-  // applied per nonzero, the row factor once per row
+// One pass of the scaling (KIND 0: Ruiz, the inf-norm; 1: l2; 2: Pock-Chambolle,
+// the l1 norm) over the rows of M: the norm nu_r of row r of D K D =
+// d_r * norm_j(|m_rj| d_j) (the column factor per nonzero, the row factor once
+// per row) and the row's new factor d_r / sqrt(nu_r) (nu_r = 0: unchanged),
+// written to dnew, the other of two buffers (every row of K has one writer and
+// the pass reads only d).
+template <int KIND>
+__global__ void __launch_bounds__(BNT) k_scale_pass(BCsr<double> M, const double* __restrict__ d, int doff,
+                                                    int dcol_off, double* __restrict__ dnew) {
   __shared__ double pv[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
@@ -735,26 +740,38 @@ __global__ void __launch_bounds__(BNT) k_scale_norms(BCsr<double> M, const doubl
   const int e0 = M.rp[r0];
   const int ne = M.rp[r1] - e0;
   auto take = [&](double acc, double v) {   // v >= 0
-    return kind == 0 ? nmax(acc, v) : (kind == 1 ? fma(v, v, acc) : acc + v);
+    return KIND == 0 ? nmax(acc, v) : (KIND == 1 ? fma(v, v, acc) : acc + v);
   };
-  auto finish = [&](double acc, double dr) { return kind == 1 ? sqrt(acc) * dr : acc * dr; };
+  auto update = [&](int r, double acc) {
+    const double dr = d[doff + r];
+    const double nu = KIND == 1 ? sqrt(acc) * dr : acc * dr;
+    dnew[doff + r] = dr / sqrt(nu > 0.0 ? nu : 1.0);
+  };
   if (ne <= BNNZ) {
-#pragma unroll
-    for (int k = 0; k < BEPT; ++k) {
-      const int e = tid + k * BNT;
-      if (e < ne) pv[e] = fabs(M.val[e0 + e]) * d[dcol_off + M.col[e0 + e]];
-    }
-    for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+    // m_rj d_j staged from 16-byte loads; |m_rj d_j| = |m_rj| d_j (d > 0;
+    // rounding to nearest is symmetric in the sign)
+    stage_products<BNT>(M, d + dcol_off, e0, ne, r0, nr, pv, srp);
     __syncthreads();
     for (int t = tid; t < nr; t += BNT) {
       double acc = 0.0;
-      for (int e = srp[t]; e < srp[t + 1]; ++e) acc = take(acc, pv[e]);
-      nu[doff + r0 + t] = finish(acc, d[doff + r0 + t]);
+      if constexpr (KIND == 0) {
+        // the largest |m_rj d_j|: non-negative doubles order as their bit
+        // patterns (integer instructions, not the float64 pipe)
+        unsigned long long best = 0;
+        for (int e = srp[t]; e < srp[t + 1]; ++e) {
+          const unsigned long long b = (unsigned long long)__double_as_longlong(pv[e]) & 0x7FFFFFFFFFFFFFFFULL;
+          best = b > best ? b : best;
+        }
+        acc = __longlong_as_double((long long)best);
+      } else {
+        for (int e = srp[t]; e < srp[t + 1]; ++e) acc = take(acc, fabs(pv[e]));
+      }
+      update(r0 + t, acc);
     }
   } else {
     double acc = 0.0;
     for (int e = e0 + tid; e < e0 + ne; e += BNT) acc = take(acc, fabs(M.val[e]) * d[dcol_off + M.col[e]]);
-    if (kind == 0) {
+    if (KIND == 0) {
       __shared__ double sh[BNT];
       sh[tid] = acc;
       __syncthreads();
@@ -766,15 +783,7 @@ __global__ void __launch_bounds__(BNT) k_scale_norms(BCsr<double> M, const doubl
     } else {
       acc = block_sum(acc);
     }
-    if (tid == 0) nu[doff + r0] = finish(acc, d[doff + r0]);
-  }
-}
-
-__global__ void k_scale_update(double* __restrict__ d, const double* __restrict__ nu, int N) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    const double v = nu[i];
-    d[i] = d[i] / sqrt(v > 0.0 ? v : 1.0);
+    if (tid == 0) update(r0, acc);
   }
 }
 
@@ -855,7 +864,18 @@ struct LzArgs {
   const int* blk_inst_A;
   const int* row_inst_n;
   int nblkP;
+  // 1: the new Lanczos vector is stored as r and normalised where it is read
+  // (its readers multiply by pi_inv_norm, k_lz_orth writes v = r / beta back);
+  // 0: k_lz_norm normalises it in place (a low-rank term reads it as well)
+  int lazy;
 };
+
+// the factor that normalises operator o's stored vector (1 when it is stored
+// normalised), in the vectors' precision
+template <typename V>
+__device__ __forceinline__ V lz_scale(const LzArgs& a, const DevState& st, int o) {
+  return a.lazy ? (V)st.pi_inv_norm[o] : V(1);
+}
 
 __device__ __forceinline__ double* lz_al(const LzArgs& a, int i, int o) { return a.al + ((size_t)i * 2 + o) * LZ_MAX; }
 __device__ __forceinline__ double* lz_be(const LzArgs& a, int i, int o) { return a.be + ((size_t)i * 2 + o) * LZ_MAX; }
@@ -863,16 +883,18 @@ __device__ __forceinline__ double* lz_be(const LzArgs& a, int i, int o) { return
 template <typename V, int NT>
 __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_m(BCsr<V> A, LzArgs la, const V* __restrict__ vA,
                                                                    V* __restrict__ wm) {
-  if (la.st[la.blk_inst_A[blockIdx.x]].pi_done[0]) return;
+  const DevState& st = la.st[la.blk_inst_A[blockIdx.x]];
+  if (st.pi_done[0]) return;
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
+  const V gA = lz_scale<V>(la, st, 0);
   const int r0 = A.blk[blockIdx.x], r1 = A.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = A.rp[r0];
   const int ne = A.rp[r1] - e0;
   if (ne <= BNNZ) {
-    stage_products<NT>(A, vA, e0, ne, r0, nr, prod, srp);
+    stage_products<NT, GATHER_LDG, V, V, true>(A, vA, e0, ne, r0, nr, prod, srp, 0, gA, la.n);
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
       V s = V(0);
@@ -881,7 +903,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_m(BCsr<V> A,
     }
   } else {
     V s = V(0);
-    for (int e = e0 + tid; e < e0 + ne; e += NT) s += A.val[e] * __ldg(vA + A.col[e]);
+    for (int e = e0 + tid; e < e0 + ne; e += NT) s += A.val[e] * r_mul(__ldg(vA + A.col[e]), gA);
     s = block_sum(s);
     if (tid == 0) wm[r0] = s;
   }
@@ -903,21 +925,23 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
   if (!doA && !doQ) return;                    // its instance's alpha reduction skips it
   double f[2] = {0.0, 0.0};
   const int tid = threadIdx.x;
+  const V gA = lz_scale<V>(la, st, 0), gQ = lz_scale<V>(la, st, 1);   // v_A, v_Q normalisation
   const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
   const int nr = r1 - r0;
   const int e0 = P.rp[r0];
   const int ne = P.rp[r1] - e0;
   auto row = [&](int r, V sQ, V sA) {
-    if (doA) { const V u = -sA; wA[r] = u; f[0] += (double)vA[r] * (double)u; }
+    if (doA) { const V u = -sA; wA[r] = u; f[0] += (double)r_mul(vA[r], gA) * (double)u; }
     if (doQ) {
       if (LR) sQ += lr_row<V, V, V>(F, wlr, rk, r);
       wQ[r] = sQ;
-      f[1] += (double)zin[r] * (double)sQ;
+      f[1] += (double)r_mul(zin[r], gQ) * (double)sQ;
     }
   };
   if (ne <= BNNZ) {
-    // once the instance's ||Q|| has converged only the A' part is gathered
-    stage_products<NT>(P, zin, e0, ne, r0, nr, prod, srp, doQ ? 0 : la.n);
+    // once the instance's ||Q|| has converged only the A' part is gathered;
+    // the v_Q entries (columns < n) are normalised as they are gathered
+    stage_products<NT, GATHER_LDG, V, V, true>(P, zin, e0, ne, r0, nr, prod, srp, doQ ? 0 : la.n, gQ, la.n);
     for (int t = tid; t < nr; t += NT) ssp[t] = P.split[r0 + t] - e0;
     __syncthreads();
     for (int t = tid; t < nr; t += NT) {
@@ -930,7 +954,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
     const int sp = P.split[r0];
     V q = V(0), w = V(0);
     for (int e = e0 + tid; e < e0 + ne; e += NT) {
-      const V v = P.val[e] * __ldg(zin + P.col[e]);
+      const V x = __ldg(zin + P.col[e]);
+      const V v = P.val[e] * (e < sp ? r_mul(x, gQ) : x);
       if (e < sp) q += v; else w += v;
     }
     q = block_sum(q);
@@ -982,13 +1007,20 @@ __global__ void __launch_bounds__(NT) k_lz_alpha(LzArgs a, const double* __restr
   }
 }
 
-// r = w - alpha v - beta_prev v_prev over v_prev, per P row block; partial |r|^2.
-// The update runs in the vectors' precision (two FMAs), only |r|^2 in float64.
+// r = w - alpha v - beta_prev v_prev over v_prev, one warp per P row block (8
+// per CTA: the per-block prologue of the instance's scalars runs in parallel);
+// partial |r|^2 per row block.  With lazy normalisation v is the stored vector
+// times 1/beta of the last step, written back here as the normalised vector
+// that the next step's three-term update reads as v_prev.  The update runs in
+// the vectors' precision (two FMAs), only |r|^2 in float64.
 template <typename V>
-__global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V* __restrict__ wQ,
-                          const V* __restrict__ vA, V* __restrict__ vA_prev, const V* __restrict__ vQ,
-                          V* __restrict__ vQ_prev, double* __restrict__ part) {
-  const int i = a.blk_inst_P[blockIdx.x];
+__global__ void __launch_bounds__(256) k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA,
+                                                 const V* __restrict__ wQ, V* __restrict__ vA,
+                                                 V* __restrict__ vA_prev, V* __restrict__ vQ,
+                                                 V* __restrict__ vQ_prev, double* __restrict__ part) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= a.nblkP) return;                      // warp-uniform
+  const int i = a.blk_inst_P[b];
   const DevState& st = a.st[i];
   const bool doA = !st.pi_done[0], doQ = !st.pi_done[1];
   if (!doA && !doQ) return;
@@ -996,23 +1028,49 @@ __global__ void k_lz_orth(LzArgs a, BCsr<V> P, const V* __restrict__ wA, const V
   const V alA = (V)(doA ? lz_al(a, i, 0)[k] : 0.0), alQ = (V)(doQ ? lz_al(a, i, 1)[k] : 0.0);
   const V bpA = (V)((doA && k > 0) ? lz_be(a, i, 0)[k - 1] : 0.0);
   const V bpQ = (V)((doQ && k > 0) ? lz_be(a, i, 1)[k - 1] : 0.0);
+  const V gA = lz_scale<V>(a, st, 0), gQ = lz_scale<V>(a, st, 1);
   double f[2] = {0.0, 0.0};
-  const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
-  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    if (doA) {
-      const V v = fma(-bpA, vA_prev[r], fma(-alA, vA[r], wA[r]));
-      vA_prev[r] = v;
-      f[0] = fma((double)v, (double)v, f[0]);
+  const int r0 = P.blk[b], r1 = P.blk[b + 1];
+  // four rows per lane at a time: their loads in flight together; the rows
+  // enter |r|^2 in increasing order
+  constexpr int U = 4;
+  for (int r = r0 + lane; r < r1; r += 32 * U) {
+    V w[2][U], v[2][U], vp[2][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rr = r + 32 * u;
+      if (rr < r1) {
+        if (doA) { w[0][u] = __ldg(wA + rr); v[0][u] = vA[rr]; vp[0][u] = vA_prev[rr]; }
+        if (doQ) { w[1][u] = __ldg(wQ + rr); v[1][u] = vQ[rr]; vp[1][u] = vQ_prev[rr]; }
+      }
     }
-    if (doQ) {
-      const V v = fma(-bpQ, vQ_prev[r], fma(-alQ, vQ[r], wQ[r]));
-      vQ_prev[r] = v;
-      f[1] = fma((double)v, (double)v, f[1]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int rr = r + 32 * u;
+      if (rr < r1) {
+        if (doA) {
+          const V x = r_mul(v[0][u], gA);
+          if (a.lazy) vA[rr] = x;
+          const V t = fma(-bpA, vp[0][u], fma(-alA, x, w[0][u]));
+          vA_prev[rr] = t;
+          f[0] = fma((double)t, (double)t, f[0]);
+        }
+        if (doQ) {
+          const V x = r_mul(v[1][u], gQ);
+          if (a.lazy) vQ[rr] = x;
+          const V t = fma(-bpQ, vp[1][u], fma(-alQ, x, w[1][u]));
+          vQ_prev[rr] = t;
+          f[1] = fma((double)t, (double)t, f[1]);
+        }
+      }
     }
   }
-  __shared__ double sh[2 * 256];
-  block_reduce_smem<2, 256>(f, 0u, sh);
-  if (threadIdx.x == 0) { part[blockIdx.x] = f[0]; part[(size_t)a.nblkP + blockIdx.x] = f[1]; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    f[0] += __shfl_xor_sync(0xffffffffu, f[0], o);
+    f[1] += __shfl_xor_sync(0xffffffffu, f[1], o);
+  }
+  if (lane == 0) { part[b] = f[0]; part[(size_t)a.nblkP + b] = f[1]; }
 }
 
 // Number of eigenvalues of the k x k tridiagonal (al, be2 = squared betas)
@@ -1718,11 +1776,20 @@ void scale_reset(Work& w, cudaStream_t s) {
   launch(k_fill, cdiv(N, 256), 256, 0, s, w.dsc, 1.0, N);
 }
 
-void scale_pass(Work& w, int kind, cudaStream_t s) {
-  const int N = w.n + w.m;
-  launch(k_scale_norms, w.P.nblk, BNT, 0, s, w.P.borig(), (const double*)w.dsc, 0, 0, w.nu, kind);
-  launch(k_scale_norms, w.A.nblk, BNT, 0, s, w.A.borig(), (const double*)w.dsc, w.n, 0, w.nu, kind);
-  launch(k_scale_update, cdiv(N, 256), 256, 0, s, w.dsc, (const double*)w.nu, N);
+// pass `pass` of a sequence reads the factors from dsc (even) or nu (odd) and
+// writes them to the other buffer
+template <int KIND>
+static void scale_pass_t(Work& w, const double* d, double* dn, cudaStream_t s) {
+  launch(k_scale_pass<KIND>, w.P.nblk, BNT, 0, s, w.P.borig(), d, 0, 0, dn);
+  launch(k_scale_pass<KIND>, w.A.nblk, BNT, 0, s, w.A.borig(), d, w.n, 0, dn);
+}
+
+void scale_pass(Work& w, int kind, int pass, cudaStream_t s) {
+  const double* d = (pass & 1) ? w.nu : w.dsc;
+  double* dn = (pass & 1) ? w.dsc : w.nu;
+  if (kind == 0) scale_pass_t<0>(w, d, dn, s);
+  else if (kind == 1) scale_pass_t<1>(w, d, dn, s);
+  else scale_pass_t<2>(w, d, dn, s);
 }
 
 void scale_apply(Work& w, bool mixed, cudaStream_t s) {
@@ -1764,6 +1831,7 @@ static LzArgs lz_args(Work& w) {
   la.al = w.lz_al; la.be = w.lz_be; la.st = w.st; la.inst = w.inst;
   la.blk_inst_P = w.blk_inst_P; la.blk_inst_A = w.blk_inst_A; la.row_inst_n = w.row_inst_n;
   la.nblkP = w.P.nblk;
+  la.lazy = w.r == 0 ? 1 : 0;
   return la;
 }
 
@@ -1802,14 +1870,13 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   const bool wide = w.max_inst_blkP > 2048;
   if (wide) launch(k_lz_alpha<512>, w.count, 512, 0, s, la, (const double*)w.part_n);
   else launch(k_lz_alpha<128>, w.count, 128, 0, s, la, (const double*)w.part_n);
-  launch(k_lz_orth<V>, w.P.nblk, 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], (const V*)pu[cur], pu[prv],
-         (const V*)pz[cur], pz[prv], w.part_n);
+  launch(k_lz_orth<V>, cdiv(w.P.nblk, 8), 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], pu[cur], pu[prv],
+         pz[cur], pz[prv], w.part_n);
   if (wide) launch(k_lz_beta<512>, w.count, 512, 0, s, la, (const double*)w.part_n, p.norm_tol,
          p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
   else launch(k_lz_beta<128>, w.count, 128, 0, s, la, (const double*)w.part_n, p.norm_tol,
          p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
-  const int grid = std::min(cdiv(w.n, 256), 4 * w.num_sms);
-  launch(k_lz_norm<V>, grid, 256, 0, s, la, pu[prv], pz[prv]);
+  if (!la.lazy) launch(k_lz_norm<V>, std::min(cdiv(w.n, 256), 4 * w.num_sms), 256, 0, s, la, pu[prv], pz[prv]);
 }
 
 // The norm estimates run at one width whatever the iteration kernels' variant

@@ -81,9 +81,12 @@ __device__ __forceinline__ void load4(const double* __restrict__ p, double (&v)[
 // those of element-wise staging.
 // cmin: entries whose column is below it are staged as 0 without their gather
 // (a caller that needs only the sums over the columns >= cmin).
-template <int NT, int GM = GATHER_LDG, typename V, typename X>
+// SC: the gathered entries of the columns below csplit are multiplied by sc
+// first (a vector kept unnormalised, normalised where it is read).
+template <int NT, int GM = GATHER_LDG, typename V, typename X, bool SC = false>
 __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __restrict__ vec, int e0, int ne,
-                                               int r0, int nr, V* prod, int* srp, int cmin = 0) {
+                                               int r0, int nr, V* prod, int* srp, int cmin = 0, V sc = V(1),
+                                               int csplit = 0) {
   // float data: one quad (four gathers) per phase, so that 256 threads fit 32
   // registers and 8 blocks an SM; float64 data (4 blocks per SM either way)
   // keeps two quads' gathers in flight at once
@@ -112,7 +115,19 @@ __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __rest
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int e = 4 * q + i - o;   // the entry's place in the block
-          if (e >= 0 && e < ne) prod[e] = ci[k][i] >= cmin ? vv[k][i] * (V)gather_load<GM>(vec + ci[k][i]) : V(0);
+          if constexpr (SC) {
+            if (e >= 0 && e < ne) {
+              const int c = ci[k][i];
+              V p = V(0);
+              if (c >= cmin) {
+                const V x = (V)gather_load<GM>(vec + c);
+                p = vv[k][i] * (c < csplit ? r_mul(x, sc) : x);
+              }
+              prod[e] = p;
+            }
+          } else {
+            if (e >= 0 && e < ne) prod[e] = ci[k][i] >= cmin ? vv[k][i] * (V)gather_load<GM>(vec + ci[k][i]) : V(0);
+          }
         }
       }
     }

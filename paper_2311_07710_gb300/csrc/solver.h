@@ -193,7 +193,9 @@ inline void count_launch() {
 }
 
 // setup
-void scale_pass(Work& w, int kind, cudaStream_t s);          // kind: 0 inf, 1 l2, 2 l1
+// scaling pass number `pass` (kind: 0 inf, 1 l2, 2 l1): reads the factors
+// from w.dsc (even pass) or w.nu (odd), writes them to the other buffer
+void scale_pass(Work& w, int kind, int pass, cudaStream_t s);
 void scale_reset(Work& w, cudaStream_t s);
 void scale_apply(Work& w, bool mixed, cudaStream_t s);
 void lanczos_init(Work& w, bool mixed, cudaStream_t s);

@@ -1,8 +1,8 @@
 """Degenerate and boundary shapes against the oracle: a 1 x 1 problem, only
 equalities, only inequalities, free variables, an empty row of A together
-with a variable that appears in no row and no entry of Q, and rows of exactly
+with a variable that appears in no row and no entry of Q, rows of exactly
 2048, 2049 and 4096 nonzeros (a full row block, one nonzero past it, two
-segments).  float64 iterates match the oracle's (norms injected) at three
+segments), and entries over 24 decades with exact ties and subnormals.  float64 iterates match the oracle's (norms injected) at three
 checkpoints; mixed-precision solves reach the oracle's end state; a batch
 with a member that has no rows reproduces the standalone solves bit for bit."""
 import numpy as np
@@ -65,6 +65,33 @@ def long_rows():
                             np.full(n, 1.0))
 
 
+def wide_magnitudes():
+    """A = S G T with row and column factors spread over 1e-12..1e12 (the
+    Ruiz passes undo them; their row maxima are formed from bit patterns and
+    must be the exact maxima), Q = T Q0 T, c, b, l, u scaled to match; column
+    1 is minus column 0 with the same Q entry, so the two have equal factors
+    and every row's two products tie exactly; two subnormal entries."""
+    rng = np.random.default_rng(7309)
+    n, m, m_eq = 60, 30, 10
+    s = 10.0 ** rng.uniform(-12, 12, m)
+    t = 10.0 ** rng.uniform(-12, 12, n)
+    t[1] = t[0]
+    G0 = sp.random(m, n, density=0.15, random_state=rng, data_rvs=rng.standard_normal).toarray()
+    G0[:, 0] = np.where(G0[:, 0] == 0.0, 1.0, G0[:, 0])
+    G0[:, 1] = -G0[:, 0]
+    A = (s[:, None] * G0) * t[None, :]
+    A[2, 5] = 1e-310
+    A[3, 7] = -2e-310
+    q0 = rng.uniform(1.0, 2.0, n)
+    q0[1] = q0[0]
+    Q = sp.diags(q0 * t * t)
+    x0 = rng.uniform(-0.5, 0.5, n) / t
+    b = A @ x0
+    b[m_eq:] -= 0.5 * s[m_eq:]
+    return qpgen.QPInstance("wide_magnitudes", n, m, m_eq, _canon(Q, (n, n)), _canon(A, (m, n)),
+                            t * rng.standard_normal(n), b, -1.0 / t, 1.0 / t)
+
+
 CASES = {
     "1x1": lambda: qpgen.tiny_qp(seed=qpgen.SEED_BASE + 7302, n=1, m=1, m_eq=0),
     "all_equality": lambda: qpgen.tiny_qp(seed=qpgen.SEED_BASE + 7303, n=12, m=6, m_eq=6),
@@ -72,6 +99,7 @@ CASES = {
     "free_variables": lambda: qpgen.tiny_qp(seed=qpgen.SEED_BASE + 7305, n=10, m=4, m_eq=2, bounds="free"),
     "empty_row_and_column": empty_row_and_column,
     "long_row_boundaries": long_rows,
+    "wide_magnitudes": wide_magnitudes,
 }
 
 
