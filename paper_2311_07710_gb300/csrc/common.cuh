@@ -107,31 +107,54 @@ __device__ __forceinline__ double nmax(double a, double b) {
 
 // Block reduction of NF per-thread fields through shared-memory scratch `sh`
 // (NF * NT doubles; it may alias data the block no longer reads).  Field f is
-// a max (bit f of max_mask) or a sum.  Warp w folds fields w, w + NT/32, ...:
-// each lane combines the NT/32 values of its column in a fixed order, then a
-// five-level shuffle tree.  The result is valid in thread 0.  This takes far
-// fewer float64 operations than a shuffle tree per warp and field.
-template <int NF, int NT>
-__device__ __forceinline__ void block_reduce_smem(double (&v)[NF], unsigned max_mask, double* sh) {
+// a max (bit f of MAXMASK) or a sum, fixed at compile time, so that a max
+// field costs no float64 instruction (GB300's float64 pipes retire about two
+// lanes per clock per SM).  Stage 1: warp w folds fields w, w + NT/32, ...:
+// each lane combines the NT/32 values of its column in a fixed order.  Stage
+// 2: four lanes per field, eight of its 32 column values each in a fixed
+// order, then two shuffle levels.  The result is valid in thread 0.
+template <int NF, int NT, unsigned MAXMASK>
+__device__ __forceinline__ void block_reduce_smem(double (&v)[NF], double* sh) {
+  static_assert(NT % 32 == 0 && 4 * NF <= NT, "block_reduce_smem: NT must be a multiple of 32, >= 4 NF");
+  constexpr int NW = NT / 32;
+  constexpr int NW2 = (4 * NF + 31) / 32;          // warps of stage 2
   __syncthreads();
 #pragma unroll
   for (int f = 0; f < NF; ++f) sh[f * NT + threadIdx.x] = v[f];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (int f = threadIdx.x >> 5; f < NF; f += NT / 32) {
-    const bool mx = (max_mask >> f) & 1u;
-    double t = sh[f * NT + lane];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 1; k < NT / 32; ++k) {
-      const double x = sh[f * NT + lane + 32 * k];
+  for (int f = 0; f < NF; ++f) {
+    if (f % NW == w) {                             // warp-uniform; the operation is known here
+      constexpr unsigned one = 1u;
+      const bool mx = (MAXMASK >> f) & one;
+      double t = sh[f * NT + lane];
+#pragma unroll
+      for (int k = 1; k < NW; ++k) {
+        const double x = sh[f * NT + lane + 32 * k];
+        t = mx ? nmax(t, x) : t + x;
+      }
+      sh[f * NT + lane] = t;                       // the column's total (this warp owns field f)
+    }
+  }
+  __syncthreads();
+  if (w < NW2) {                                   // whole warps: every lane reaches the shuffles
+    const int g = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const bool on = g < NF;
+    const bool mx = on && ((MAXMASK >> g) & 1u);
+    double t = on ? sh[g * NT + 8 * q] : 0.0;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      const double x = on ? sh[g * NT + 8 * q + k] : 0.0;
       t = mx ? nmax(t, x) : t + x;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 1; o < 4; o <<= 1) {
       const double x = __shfl_xor_sync(0xffffffffu, t, o);
       t = mx ? nmax(t, x) : t + x;
     }
-    if (lane == 0) sh[f * NT] = t;
+    __syncwarp();
+    if (on && q == 0) sh[g * NT] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
       if (NIT > 1) kkt_m_row<NIT - 1>(a, f, r0, s[NIT - 1]);
     }
   }
-  block_reduce_smem<9, BNT>(f, 0x133u, kkt_sm);
+  block_reduce_smem<9, BNT, 0x133u>(f, kkt_sm);
   if (tid == 0)
     for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
 }
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
       if (NIT > 1) kkt_n_row<NIT - 1, LR>(a, f, r0, sq[NIT - 1], sa[NIT - 1]);
     }
   }
-  block_reduce_smem<15, BNT>(f, 0x4387u, kkt_sm);
+  block_reduce_smem<15, BNT, 0x4387u>(f, kkt_sm);
   if (tid == 0)
     for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
 }
@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_m_sums(KktB a, const double* __rest
     if (it == 0) kkt_m_row<0>(a, f, r0 + t, s0[r0 + t]);
     else kkt_m_row<1>(a, f, r0 + t, s1[r0 + t]);
   }
-  block_reduce_smem<9, BNT>(f, 0x133u, sh);
+  block_reduce_smem<9, BNT, 0x133u>(f, sh);
   if (tid == 0)
     for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
 }
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(BNT) k_kkt_n_sums(KktB a, const double* __rest
     if (it == 0) kkt_n_row<0, false>(a, f, r0 + t, q0[r0 + t], t0[r0 + t]);
     else kkt_n_row<1, false>(a, f, r0 + t, q1[r0 + t], t1[r0 + t]);
   }
-  block_reduce_smem<15, BNT>(f, 0x4387u, sh);
+  block_reduce_smem<15, BNT, 0x4387u>(f, sh);
   if (tid == 0)
     for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
 }
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
     if (tid == 0) row(r0, q, w);
   }
   static_assert(sizeof(V) * BNNZ >= 2 * NT * sizeof(double), "staging buffer too small for the reduction");
-  block_reduce_smem<2, NT>(f, 0u, reinterpret_cast<double*>(prod));
+  block_reduce_smem<2, NT, 0u>(f, reinterpret_cast<double*>(prod));
   if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)la.nblkP + blockIdx.x] = f[1]; }
 }
 
