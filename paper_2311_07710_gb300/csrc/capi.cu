@@ -1116,6 +1116,8 @@ void alloc_work(pdqp_problem* h, cudaStream_t s) {
   w.act_P = dalloc<int>(h, (size_t)std::max(w.P.nblk, 1));
   w.cpart_m = dalloc<double>(h, (size_t)9 * std::max(w.nchunk_m, 1));
   w.cpart_n = dalloc<double>(h, (size_t)15 * std::max(w.nchunk_n, 1));
+  w.lz_ticket = dalloc<unsigned>(h, (size_t)std::max(w.nchunk_n, 1));
+  CK(cudaMemsetAsync(w.lz_ticket, 0, sizeof(unsigned) * std::max(w.nchunk_n, 1), s));
   w.st = dalloc<DevState>(h, count);
   w.bst = dalloc<BatchState>(h, 1);
   w.stage_n = dalloc<double>(h, n); w.stage_m = dalloc<double>(h, m);

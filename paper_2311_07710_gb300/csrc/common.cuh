@@ -105,6 +105,27 @@ __device__ __forceinline__ double nmax(double a, double b) {
   return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
 }
 
+// float -> double built from the IEEE bit fields with integer instructions
+// (the conversion instruction issues on GB300's slow float64 pipe): exponent
+// rebiased by 1023 - 127, fraction moved up 29 bits; a subnormal normalised at
+// its leading one; zeros, infinities and NaNs keep their class.  The same
+// value as the conversion for every float (NaN payloads aside).
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  unsigned long long b = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 255u) {
+    b |= (0x7FFULL << 52) | ((unsigned long long)m << 29);
+  } else if (e != 0u) {
+    b |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m != 0u) {
+    const int p = 31 - __clz(m);                  // leading one of the subnormal fraction
+    b |= ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFULL);
+  }
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double f2d(double x) { return x; }
+
 // Block reduction of NF per-thread fields through shared-memory scratch `sh`
 // (NF * NT doubles; it may alias data the block no longer reads).  Field f is
 // a max (bit f of MAXMASK) or a sum, fixed at compile time, so that a max

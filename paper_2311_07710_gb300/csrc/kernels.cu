@@ -868,7 +868,37 @@ struct LzArgs {
   // (its readers multiply by pi_inv_norm, k_lz_orth writes v = r / beta back);
   // 0: k_lz_norm normalises it in place (a low-rank term reads it as well)
   int lazy;
+  double* cpart;                   // [2][nchunk] chunk sums of the row-block partials
+  unsigned* ticket;                // [nchunk] zero between launches
+  int nchunk;
 };
+
+// After row block b of instance i wrote its two partials (part[b],
+// part[nblkP + b]; one thread): the last of its chunk's blocks to finish -- a
+// ticket taken after a fence -- sums the chunk's partials in block order into
+// the chunk sums and resets the ticket.  Chunks are KKT_CHUNK consecutive row
+// blocks from the instance's first, so a batch, a family member and a
+// standalone solve sum alike, and the per-instance reductions (one CUDA block
+// each) read tens of chunk sums instead of thousands of partials.  No waits:
+// every block of a chunk runs the kernel to this point or none does (the
+// early exits test the instance's state only).
+__device__ __forceinline__ void lz_chunk_close(const LzArgs& a, const double* part, int b, int i) {
+  const Inst in = a.inst[i];
+  const int c = (b - in.bP0) / KKT_CHUNK;
+  const int c0 = in.bP0 + c * KKT_CHUNK, c1 = min(c0 + KKT_CHUNK, in.bP1);
+  const int g = in.cP0 + c;
+  __threadfence();
+  if (atomicAdd(a.ticket + g, 1u) != (unsigned)(c1 - c0 - 1)) return;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = c0; k < c1; ++k) {
+    s0 += __ldcg(part + k);
+    s1 += __ldcg(part + (size_t)a.nblkP + k);
+  }
+  a.cpart[g] = s0;
+  a.cpart[(size_t)a.nchunk + g] = s1;
+  a.ticket[g] = 0u;
+}
 
 // the factor that normalises operator o's stored vector (1 when it is stored
 // normalised), in the vectors' precision
@@ -931,11 +961,11 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
   const int e0 = P.rp[r0];
   const int ne = P.rp[r1] - e0;
   auto row = [&](int r, V sQ, V sA) {
-    if (doA) { const V u = -sA; wA[r] = u; f[0] += (double)r_mul(vA[r], gA) * (double)u; }
+    if (doA) { const V u = -sA; wA[r] = u; f[0] = fma(f2d(r_mul(vA[r], gA)), f2d(u), f[0]); }
     if (doQ) {
       if (LR) sQ += lr_row<V, V, V>(F, wlr, rk, r);
       wQ[r] = sQ;
-      f[1] += (double)r_mul(zin[r], gQ) * (double)sQ;
+      f[1] = fma(f2d(r_mul(zin[r], gQ)), f2d(sQ), f[1]);
     }
   };
   if (ne <= BNNZ) {
@@ -964,11 +994,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
   }
   static_assert(sizeof(V) * BNNZ >= 2 * NT * sizeof(double), "staging buffer too small for the reduction");
   block_reduce_smem<2, NT, 0u>(f, reinterpret_cast<double*>(prod));
-  if (tid == 0) { part[blockIdx.x] = f[0]; part[(size_t)la.nblkP + blockIdx.x] = f[1]; }
+  if (tid == 0) {
+    part[blockIdx.x] = f[0];
+    part[(size_t)la.nblkP + blockIdx.x] = f[1];
+    lz_chunk_close(la, part, blockIdx.x, la.blk_inst_P[blockIdx.x]);
+  }
 }
 
-// Per-thread sums of the two fields of row blocks [b0, b1) (stride blockDim):
-// four independent accumulators, combined in a fixed order.
+// Per-thread sums of the two fields (part[b], part[stride + b]) over [b0, b1)
+// (stride blockDim): four independent accumulators, combined in a fixed order.
 __device__ __forceinline__ void lz_block_sums(const double* __restrict__ part, int nblkP, int b0, int b1,
                                               double (&f)[2]) {
   double acc[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
@@ -989,15 +1023,15 @@ __device__ __forceinline__ void lz_block_sums(const double* __restrict__ part, i
   f[1] = (acc[1][0] + acc[1][1]) + (acc[1][2] + acc[1][3]);
 }
 
-// one CUDA block per instance: alpha_k = sum of its row blocks' partials
+// one CUDA block per instance: alpha_k = sum of its chunk sums
 template <int NT>
-__global__ void __launch_bounds__(NT) k_lz_alpha(LzArgs a, const double* __restrict__ part) {
+__global__ void __launch_bounds__(NT) k_lz_alpha(LzArgs a) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;
   const Inst in = a.inst[i];
   double f[2] = {0.0, 0.0};
-  lz_block_sums(part, a.nblkP, in.bP0, in.bP1, f);
+  lz_block_sums(a.cpart, a.nchunk, in.cP0, in.cP0 + kkt_chunks(in.bP0, in.bP1), f);
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   if (threadIdx.x == 0) {
@@ -1053,14 +1087,14 @@ __global__ void __launch_bounds__(256) k_lz_orth(LzArgs a, BCsr<V> P, const V* _
           if (a.lazy) vA[rr] = x;
           const V t = fma(-bpA, vp[0][u], fma(-alA, x, w[0][u]));
           vA_prev[rr] = t;
-          f[0] = fma((double)t, (double)t, f[0]);
+          f[0] = fma(f2d(t), f2d(t), f[0]);
         }
         if (doQ) {
           const V x = r_mul(v[1][u], gQ);
           if (a.lazy) vQ[rr] = x;
           const V t = fma(-bpQ, vp[1][u], fma(-alQ, x, w[1][u]));
           vQ_prev[rr] = t;
-          f[1] = fma((double)t, (double)t, f[1]);
+          f[1] = fma(f2d(t), f2d(t), f[1]);
         }
       }
     }
@@ -1070,7 +1104,11 @@ __global__ void __launch_bounds__(256) k_lz_orth(LzArgs a, BCsr<V> P, const V* _
     f[0] += __shfl_xor_sync(0xffffffffu, f[0], o);
     f[1] += __shfl_xor_sync(0xffffffffu, f[1], o);
   }
-  if (lane == 0) { part[b] = f[0]; part[(size_t)a.nblkP + b] = f[1]; }
+  if (lane == 0) {
+    part[b] = f[0];
+    part[(size_t)a.nblkP + b] = f[1];
+    lz_chunk_close(a, part, b, i);
+  }
 }
 
 // Number of eigenvalues of the k x k tridiagonal (al, be2 = squared betas)
@@ -1237,14 +1275,14 @@ __device__ void bracket_max_eig_warp(const double* __restrict__ al, const double
 // refines theta_k and the second theta_{k-1} from their brackets, and the
 // outcome is the one the precise values give at every step.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, const double* __restrict__ part, double tol,
+__global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol,
                                                int max_steps) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
   const Inst in = a.inst[i];
   double f[2] = {0.0, 0.0};
-  lz_block_sums(part, a.nblkP, in.bP0, in.bP1, f);
+  lz_block_sums(a.cpart, a.nchunk, in.cP0, in.cP0 + kkt_chunks(in.bP0, in.bP1), f);
   const bool is_max[2] = {false, false};
   block_reduce<2>(f, is_max);
   __shared__ double beta[2], s_lo[2], s_hi[2], s_theta[2][2];
@@ -1832,6 +1870,7 @@ static LzArgs lz_args(Work& w) {
   la.blk_inst_P = w.blk_inst_P; la.blk_inst_A = w.blk_inst_A; la.row_inst_n = w.row_inst_n;
   la.nblkP = w.P.nblk;
   la.lazy = w.r == 0 ? 1 : 0;
+  la.cpart = w.cpart_n; la.ticket = w.lz_ticket; la.nchunk = w.nchunk_n;
   return la;
 }
 
@@ -1842,8 +1881,6 @@ static void lanczos_init_t(Work& w, V* const* pu, V* const* pz, cudaStream_t s) 
 }
 
 void lanczos_init(Work& w, bool mixed, cudaStream_t s) {
-  w.max_inst_blkP = 0;
-  for (const Inst& in : w.inst_host) w.max_inst_blkP = std::max(w.max_inst_blkP, in.bP1 - in.bP0);
   if (mixed) lanczos_init_t<float>(w, w.fpu, w.fpz, s);
   else lanczos_init_t<double>(w, w.pu, w.pz, s);
 }
@@ -1865,17 +1902,12 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   else
     launch(k_lz_n<V, NT, false>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
            w.part_n, F, lr_weights<V>(w), w.r);
-  // a single large instance sums thousands of block partials: more threads
-  // keep more of its loads in flight; batches of small instances keep 128
-  const bool wide = w.max_inst_blkP > 2048;
-  if (wide) launch(k_lz_alpha<512>, w.count, 512, 0, s, la, (const double*)w.part_n);
-  else launch(k_lz_alpha<128>, w.count, 128, 0, s, la, (const double*)w.part_n);
+  // the per-instance reductions read the chunk sums (a few hundred for the
+  // largest instance), so 128 threads each suffice
+  launch(k_lz_alpha<128>, w.count, 128, 0, s, la);
   launch(k_lz_orth<V>, cdiv(w.P.nblk, 8), 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], pu[cur], pu[prv],
          pz[cur], pz[prv], w.part_n);
-  if (wide) launch(k_lz_beta<512>, w.count, 512, 0, s, la, (const double*)w.part_n, p.norm_tol,
-         p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
-  else launch(k_lz_beta<128>, w.count, 128, 0, s, la, (const double*)w.part_n, p.norm_tol,
-         p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
+  launch(k_lz_beta<128>, w.count, 128, 0, s, la, p.norm_tol, p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
   if (!la.lazy) launch(k_lz_norm<V>, std::min(cdiv(w.n, 256), 4 * w.num_sms), 256, 0, s, la, pu[prv], pz[prv]);
 }
 

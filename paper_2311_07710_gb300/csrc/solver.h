@@ -140,6 +140,7 @@ struct Work {
   double *lw[2] = {nullptr, nullptr};    // Lanczos products A~'A~v and Q~v [n]
   float *flw[2] = {nullptr, nullptr};
   double *lz_al = nullptr, *lz_be = nullptr;   // [count][2][512] Lanczos coefficients
+  unsigned* lz_ticket = nullptr;   // [nchunk_n] Lanczos chunk tickets (0 between launches)
   // reductions
   double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
   double *part_m = nullptr;  // [9][A.nblk]  field-major partial sums of the row-block kernels
@@ -147,7 +148,6 @@ struct Work {
   double *cpart_m = nullptr; // [9][nchunk_m]  chunk sums of part_m (KKT_CHUNK blocks each)
   double *cpart_n = nullptr; // [15][nchunk_n]
   int nchunk_m = 0, nchunk_n = 0, maxchunk_m = 0, maxchunk_n = 0;
-  int max_inst_blkP = 0;     // most row blocks of P held by one instance
   int* act_A = nullptr;      // batches: [A.nblk] row blocks of the running instances (count in bst)
   int* act_P = nullptr;      // [P.nblk]
   StepEntry* tab = nullptr;  // [count][tab_stride]
