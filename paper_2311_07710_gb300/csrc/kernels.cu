@@ -1274,9 +1274,11 @@ __device__ void bracket_max_eig_warp(const double* __restrict__ al, const double
 // theta_k and theta_{k-1} cannot decide it: then the first warp of the pair
 // refines theta_k and the second theta_{k-1} from their brackets, and the
 // outcome is the one the precise values give at every step.
+// kcap: the tridiagonals' capacity in the dynamic shared memory, at least the
+// step's k = pi_iters + 1 of every instance still running (2 kcap (3 doubles +
+// 2 floats) bytes).
 template <int NT>
-__global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol,
-                                               int max_steps) {
+__global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol, int max_steps, int kcap) {
   const int i = blockIdx.x;
   DevState& st = a.st[i];
   if (st.pi_done[0] && st.pi_done[1]) return;     // uniform: nothing left to do
@@ -1287,8 +1289,19 @@ __global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol,
   block_reduce<2>(f, is_max);
   __shared__ double beta[2], s_lo[2], s_hi[2], s_theta[2][2];
   __shared__ int done_in[2], s_precise[2];
-  __shared__ double s_al[2][LZ_MAX], s_be[2][LZ_MAX], s_be2[2][LZ_MAX];
-  __shared__ float s_alf[2][LZ_MAX], s_be2f[2][LZ_MAX];
+  // [2][kcap] each: alphas, |betas|, squared betas (float64), then the scaled
+  // float32 copies of the alphas and squared betas
+  extern __shared__ __align__(16) double lz_sm[];
+  double* const s_al_ = lz_sm;
+  double* const s_be_ = lz_sm + 2 * kcap;
+  double* const s_be2_ = lz_sm + 4 * kcap;
+  float* const s_alf_ = reinterpret_cast<float*>(lz_sm + 6 * kcap);
+  float* const s_be2f_ = s_alf_ + 2 * kcap;
+  auto s_al = [&](int o) { return s_al_ + o * kcap; };
+  auto s_be = [&](int o) { return s_be_ + o * kcap; };
+  auto s_be2 = [&](int o) { return s_be2_ + o * kcap; };
+  auto s_alf = [&](int o) { return s_alf_ + o * kcap; };
+  auto s_be2f = [&](int o) { return s_be2f_ + o * kcap; };
   const int k = st.pi_iters + 1;                  // alphas 0..k-1, betas 0..k-2 form T_k
   if (threadIdx.x == 0) {
     beta[0] = sqrt(f[0]); beta[1] = sqrt(f[1]);
@@ -1296,11 +1309,11 @@ __global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol,
   }
   for (int o = 0; o < 2; ++o)
     for (int t = threadIdx.x; t < k; t += blockDim.x) {
-      s_al[o][t] = lz_al(a, i, o)[t];
+      s_al(o)[t] = lz_al(a, i, o)[t];
       if (t < k - 1) {
         const double bb = lz_be(a, i, o)[t];
-        s_be[o][t] = fabs(bb);
-        s_be2[o][t] = bb * bb;
+        s_be(o)[t] = fabs(bb);
+        s_be2(o)[t] = bb * bb;
       }
     }
   __syncthreads();
@@ -1309,7 +1322,7 @@ __global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol,
   const double plo = st.pi_lam_prev[o], phi = st.pi_hi_prev[o];   // bracket of theta_{k-1}
   if (ritz && !done_in[o] && !second) {           // warp-uniform
     double lo, hi;
-    bracket_max_eig_warp(s_al[o], s_be[o], s_be2[o], s_alf[o], s_be2f[o], k, lo, hi);
+    bracket_max_eig_warp(s_al(o), s_be(o), s_be2(o), s_alf(o), s_be2f(o), k, lo, hi);
     const double mag = fmax(fabs(lo), fabs(hi));
     const double gap = fmax(fmax(lo - phi, plo - hi), 0.0);   // least |theta_k - theta_{k-1}|
     const bool go_on = k < max_steps && beta[o] > 1e-12 * mag && gap > tol * mag;
@@ -1322,9 +1335,9 @@ __global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol,
   __syncthreads();
   if (ritz && !done_in[o] && s_precise[o]) {
     if (!second)
-      s_theta[o][0] = refine_max_eig_warp(s_al[o], s_be2[o], k, s_lo[o], s_hi[o]);
+      s_theta[o][0] = refine_max_eig_warp(s_al(o), s_be2(o), k, s_lo[o], s_hi[o]);
     else if (plo != phi)
-      s_theta[o][1] = refine_max_eig_warp(s_al[o], s_be2[o], k - 1, plo, phi);
+      s_theta[o][1] = refine_max_eig_warp(s_al(o), s_be2(o), k - 1, plo, phi);
     else if (lane == 0)
       s_theta[o][1] = plo;
   }
@@ -1907,7 +1920,11 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
   launch(k_lz_alpha<128>, w.count, 128, 0, s, la);
   launch(k_lz_orth<V>, cdiv(w.P.nblk, 8), 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], pu[cur], pu[prv],
          pz[cur], pz[prv], w.part_n);
-  launch(k_lz_beta<128>, w.count, 128, 0, s, la, p.norm_tol, p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX);
+  // the tridiagonals have t + 1 rows at step t: shared memory for that many
+  // (the blocks per SM grow as the arrays shrink)
+  const int kcap = (t + 1 + 3) & ~3;
+  launch(k_lz_beta<128>, w.count, 128, (size_t)kcap * 2 * (3 * sizeof(double) + 2 * sizeof(float)), s, la,
+         p.norm_tol, p.norm_iters < LZ_MAX ? p.norm_iters : LZ_MAX, kcap);
   if (!la.lazy) launch(k_lz_norm<V>, std::min(cdiv(w.n, 256), 4 * w.num_sms), 256, 0, s, la, pu[prv], pz[prv]);
 }
 
