@@ -556,6 +556,10 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   if (mixed) alloc_mixed(h);
   if (use_il) alloc_il(h, mixed);
   w.il_active = use_il;
+  if (!use_il && !w.kkt_xx) {   // the row-block checks gather both iterates of a column at once
+    w.kkt_xx = dalloc<double2>(h, std::max(w.n, 1));
+    w.kkt_yy = dalloc<double2>(h, std::max(w.m, 1));
+  }
   w.detect = o.detect_infeasibility ? 1 : 0;
   w.eps_inf = o.eps_infeasible;
   if (w.detect) alloc_infeas(h, s);

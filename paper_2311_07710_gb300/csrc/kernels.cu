@@ -315,6 +315,8 @@ struct KktB {
   BCsr<double> A, P;                    // scaled (or original with D = null)
   const double* x[2];                   // iterates (scaled space), x: [n], y: [m]
   const double* y[2];
+  const double2* xx;                    // optional: (x[0], x[1]) and (y[0], y[1]) as pairs, so
+  const double2* yy;                    //   that one 16-byte gather fetches both (null: x[], y[])
   const double* ax;                     // anchors for the restart distances (null: none)
   const double* ay;
   const double *D1, *D2, *iD1, *iD2;    // null = 1
@@ -373,6 +375,30 @@ __device__ __forceinline__ void kkt_stage(const BCsr<double>& M, int e0, int ne,
     if (e < ne)
 #pragma unroll
       for (int it = 0; it < NIT; ++it) sx[it * BNNZ + e] = gather(it, ci[k]);
+  }
+}
+
+// kkt_stage for two iterates from a pair array: one 16-byte gather
+// (gather2(c), a double2) fills both iterates' entries of a nonzero.
+template <typename G2>
+__device__ __forceinline__ void kkt_stage_pairs(const BCsr<double>& M, int e0, int ne, int r0, int nr, double* sval,
+                                                double* sx, int* srp, G2 gather2) {
+  const int tid = threadIdx.x;
+  int ci[BEPT];
+#pragma unroll
+  for (int k = 0; k < BEPT; ++k) {
+    const int e = tid + k * BNT;
+    if (e < ne) { ci[k] = M.col[e0 + e]; sval[e] = M.val[e0 + e]; }
+  }
+  for (int t = tid; t <= nr; t += BNT) srp[t] = M.rp[r0 + t] - e0;
+#pragma unroll
+  for (int k = 0; k < BEPT; ++k) {
+    const int e = tid + k * BNT;
+    if (e < ne) {
+      const double2 v = gather2(ci[k]);
+      sx[e] = v.x;
+      sx[BNNZ + e] = v.y;
+    }
   }
 }
 
@@ -442,7 +468,10 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
   const int e0 = a.A.rp[r0];
   const int ne = a.A.rp[r1] - e0;
   if (ne <= BNNZ) {
-    kkt_stage<NIT>(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) { return __ldg(a.x[it] + c); });
+    if (NIT == 2 && a.xx)
+      kkt_stage_pairs(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int c) { return __ldg(a.xx + c); });
+    else
+      kkt_stage<NIT>(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) { return __ldg(a.x[it] + c); });
     __syncthreads();
     for (int q = tid; q < nr * NIT; q += BNT) {
       const int it = q >= nr ? 1 : 0, t = q - it * nr;
@@ -492,9 +521,13 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
   const int ne = a.P.rp[r1] - e0;
   const int n = a.n;
   if (ne <= BNNZ) {
-    kkt_stage<NIT>(a.P, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) {
-      return c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n));
-    });
+    if (NIT == 2 && a.xx)
+      kkt_stage_pairs(a.P, e0, ne, r0, nr, sval, sx, srp,
+                      [&](int c) { return c < n ? __ldg(a.xx + c) : __ldg(a.yy + (c - n)); });
+    else
+      kkt_stage<NIT>(a.P, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) {
+        return c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n));
+      });
     for (int t = tid; t < nr; t += BNT) ssp[t] = a.P.split[r0 + t] - e0;
     __syncthreads();
     for (int q = tid; q < nr * NIT; q += BNT) {
@@ -1754,6 +1787,7 @@ struct MixedArgs {
   float *fx, *fxbar, *fxt, *fxmd0, *fy, *fybar;
   float *fc, *fl, *fu, *fb, *fylo;
   double *x64[2], *y64[2];               // materialised iterates (current, average)
+  double2 *xx, *yy;                      // the same as pairs for the relKKT gathers (null: not written)
   const double *prodAx, *prodQx, *prodATy;   // [2][m], [2][n], [2][n]
 };
 
@@ -1772,12 +1806,24 @@ __global__ void k_init_mixed(MixedArgs a, const double* __restrict__ x0, const d
   }
 }
 
+// (x, x_bar) and (y, y_bar) as pairs for the relKKT gathers (float64 mode)
+__global__ void k_pair_iterates(int n, int m, const double* __restrict__ x, const double* __restrict__ xbar,
+                                const double* __restrict__ y, const double* __restrict__ ybar,
+                                double2* __restrict__ xx, double2* __restrict__ yy) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(n, m); i += gridDim.x * blockDim.x) {
+    if (i < n) xx[i] = make_double2(x[i], xbar[i]);
+    if (i < m) yy[i] = make_double2(y[i], ybar[i]);
+  }
+}
+
 __global__ void k_materialize(MixedArgs a) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(a.n, a.m); i += gridDim.x * blockDim.x) {
     if (i < a.n) {
       const double h = a.xhi[i], lo = a.ls[i], hi = a.us[i];
-      a.x64[0][i] = fmin(fmax(h + (double)a.fx[i], lo), hi);
-      a.x64[1][i] = fmin(fmax(h + (double)a.fxbar[i], lo), hi);
+      const double v0 = fmin(fmax(h + (double)a.fx[i], lo), hi), v1 = fmin(fmax(h + (double)a.fxbar[i], lo), hi);
+      a.x64[0][i] = v0;
+      a.x64[1][i] = v1;
+      if (a.xx) a.xx[i] = make_double2(v0, v1);
     }
     if (i < a.m) {
       const double h = a.yhi[i];
@@ -1785,6 +1831,7 @@ __global__ void k_materialize(MixedArgs a) {
       if (a.ineq[i]) { v0 = fmax(v0, 0.0); v1 = fmax(v1, 0.0); }
       a.y64[0][i] = v0;
       a.y64[1][i] = v1;
+      if (a.yy) a.yy[i] = make_double2(v0, v1);
     }
   }
 }
@@ -2204,11 +2251,17 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
   if (w.prof.on) w.prof.begin(2, s);
   const int NN = w.n > w.m ? w.n : w.m;
   const int grid_v = cdiv(NN, 256) < 4 * w.num_sms ? cdiv(NN, 256) : 4 * w.num_sms;
+  const bool pairs = !w.il_active && w.kkt_xx;
   if (mixed) {
     MixedArgs ma = mixed_args(w);
+    if (pairs) { ma.xx = w.kkt_xx; ma.yy = w.kkt_yy; }
     launch(k_materialize, grid_v, 256, 0, s, ma);
+  } else if (pairs) {
+    launch(k_pair_iterates, grid_v, 256, 0, s, w.n, w.m, (const double*)w.x, (const double*)w.xbar,
+           (const double*)w.y, (const double*)w.ybar, w.kkt_xx, w.kkt_yy);
   }
   KktB a = kkt_args(w, true);
+  if (pairs) { a.xx = w.kkt_xx; a.yy = w.kkt_yy; }
   if (mixed) {
     a.ax = w.xhi; a.ay = w.yhi;
     for (int it = 0; it < 2; ++it) {

@@ -141,6 +141,7 @@ struct Work {
   float *flw[2] = {nullptr, nullptr};
   double *lz_al = nullptr, *lz_be = nullptr;   // [count][2][512] Lanczos coefficients
   unsigned* lz_ticket = nullptr;   // [nchunk_n] Lanczos chunk tickets (0 between launches)
+  double2 *kkt_xx = nullptr, *kkt_yy = nullptr;   // [n], [m]: (x, x_bar), (y, y_bar) pairs the relKKT kernels gather
   // reductions
   double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
   double *part_m = nullptr;  // [9][A.nblk]  field-major partial sums of the row-block kernels
