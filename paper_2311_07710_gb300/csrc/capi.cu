@@ -25,6 +25,7 @@ struct ChunkGraph {
   double key_eps_inf = 0.0;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;       // kernel nodes in the graph (counted per replay)
+  int gA = 0, gP = 0;          // compacted chunks: the grids over the running row blocks
 };
 
 struct pdqp_problem {
@@ -36,6 +37,7 @@ struct pdqp_problem {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // solve start, setup done, loop done
   cudaStream_t cap = nullptr;                         // private stream for graph capture
   ChunkGraph graph;
+  std::vector<ChunkGraph> cgraphs;                    // compacted chunks, by padded grids (ChunkGraph::gA, gP)
   std::vector<pdqp_info> infos;                       // per instance, from the last solve
   std::vector<void*> allocs;
   int tuned_nt[2] = {0, 0};                           // autotuned variant per precision (0: not yet)
@@ -490,6 +492,66 @@ void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaS
   pdqp::g_launches += g.kernels;
 }
 
+// Drop every captured chunk graph (a buffer they point into was replaced).
+void drop_graphs(pdqp_problem* h) {
+  if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
+  h->graph.valid = false;
+  for (auto& c : h->cgraphs)
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+  h->cgraphs.clear();
+}
+
+// A compacted chunk (a batch whose running instances hold less than half of
+// the row blocks) through a graph captured at grids padded to powers of two:
+// the block lists are device data that each check rewrites (-1 past the
+// count), so one graph serves until the padded size changes -- a few graphs
+// per solve, against two direct launches per iteration in the batch's tail.
+static int pad_grid(int c, int cap) {
+  if (c <= 0) return 0;
+  int g = 1;
+  while (g < c) g <<= 1;
+  return std::min(g, cap);
+}
+
+void launch_compact_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
+  Work& w = h->w;
+  const int gA = pad_grid(w.bst_host->act_A, w.A.nblk), gP = pad_grid(w.bst_host->act_P, w.P.nblk);
+  ChunkGraph* g = nullptr;
+  for (ChunkGraph& c : h->cgraphs)
+    if (c.gA == gA && c.gP == gP && std::memcmp(&c.key, &p, sizeof(SolveParams)) == 0 &&
+        c.key_detect == w.detect && c.key_eps_inf == w.eps_inf)
+      g = &c;
+  if (!g) {
+    ChunkGraph c;
+    if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    pdqp::t_capturing = true;
+    pdqp::t_captured = 0;
+    w.act_grid_A = std::max(gA, 1);
+    w.act_grid_P = std::max(gP, 1);
+    pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap, 0, true);
+    w.act_grid_A = w.act_grid_P = 0;
+    pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
+    pdqp::t_capturing = false;
+    c.kernels = pdqp::t_captured;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(h->cap, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&c.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c.key = p;
+    c.key_detect = w.detect;
+    c.key_eps_inf = w.eps_inf;
+    c.valid = true;
+    c.gA = gA;
+    c.gP = gP;
+    h->cgraphs.push_back(c);
+    g = &h->cgraphs.back();
+  }
+  CK(cudaGraphLaunch(g->exec, s));
+  pdqp::g_launches += g->kernels;
+}
+
 pdqp_status finish_status(int st) {
   switch (st) {
     case ST_OPTIMAL: return PDQP_OK;
@@ -596,8 +658,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   if (w.tab_stride < o.check_period) {
     w.tab = dalloc<StepEntry>(h, (size_t)w.count * o.check_period);
     w.tab_stride = o.check_period;
-    if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
-    h->graph.valid = false;
+    drop_graphs(h);
   }
   CK(cudaEventRecord(h->ev[0], s));
   // preprocessing (Section 5): 10 Ruiz passes, l2, Pock-Chambolle (a resumed
@@ -736,8 +797,9 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       p.spmv_threads = tuned;
       pdqp::iterate_chunk(w, (int)len - j, mixed, p.spmv_threads, s, j);
       pdqp::check(w, p, 1, len, mixed, s);
-    } else if (len == o.check_period && !o.no_graphs && !w.prof.on && !compact_now(w, p)) {
-      launch_chunk_graph(h, p, mixed, s);
+    } else if (len == o.check_period && !o.no_graphs && !w.prof.on) {
+      if (compact_now(w, p)) launch_compact_graph(h, p, mixed, s);
+      else launch_chunk_graph(h, p, mixed, s);
     } else {
       pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s, 0, compact_now(w, p));
       pdqp::check(w, p, 1, len, mixed, s);
@@ -2105,8 +2167,7 @@ pdqp_status pdqp_set_lowrank_Q(pdqp_handle h, int32_t r, const float* F, int32_t
     to_device(w.Fo, hd.data(), N, s);
     CK(cudaStreamSynchronize(s));
     w.r = r;
-    if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
-    h->graph.valid = false;
+    drop_graphs(h);
     return PDQP_OK;
   } catch (const Fail& f) {
     h->err = f.msg;
@@ -2245,8 +2306,7 @@ pdqp_status pdqp_set_state(pdqp_handle h, const void* buf, size_t bytes, void* s
     if (w.tab_stride < C) {
       w.tab = dalloc<StepEntry>(h, (size_t)w.count * C);
       w.tab_stride = C;
-      if (h->graph.exec) { cudaGraphExecDestroy(h->graph.exec); h->graph.exec = nullptr; }
-      h->graph.valid = false;
+      drop_graphs(h);
     }
     const unsigned char* in = static_cast<const unsigned char*>(buf);
     size_t off = sizeof hd;
@@ -2343,6 +2403,8 @@ void pdqp_destroy(pdqp_handle h) {
   for (auto& e : h->tune_ev)
     if (e) cudaEventDestroy(e);
   if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+  for (auto& c : h->cgraphs)
+    if (c.exec) cudaGraphExecDestroy(c.exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->tmpl) pdqp_destroy(h->tmpl);
   delete h;

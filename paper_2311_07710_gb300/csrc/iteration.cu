@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_dual(DualB<V> a
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;   // compacted batches: running blocks only
+  if (bk < 0) return;                                             // padding of a compacted grid
   dual_block<V, NT, GATHER_LDG>(a, bk, j, prod, srp);
 }
 
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(Prim
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
+  if (bk < 0) return;
   primal_block<V, NT, LR, GATHER_LDG>(a, bk, j, prod, srp);
 }
 
@@ -600,8 +602,10 @@ static void run_chunk(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V* xt, V* 
   if (compact) {   // only the running instances' row blocks (counts of the last check)
     da.act = w.act_A;
     pa.act = w.act_P;
-    gA = w.bst_host->act_A;
-    gP = w.bst_host->act_P;
+    // a grid padded for a replayed graph (entries past the count are -1), or
+    // the counts themselves
+    gA = w.act_grid_A > 0 ? w.act_grid_A : w.bst_host->act_A;
+    gP = w.act_grid_P > 0 ? w.act_grid_P : w.bst_host->act_P;
   }
   for (int j = j0; j < j0 + len; ++j) {
     if (w.r > 0) lowrank_ft1(w, pa.F, (const V*)Z[j & 1], s);

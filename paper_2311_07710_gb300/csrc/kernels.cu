@@ -2296,6 +2296,9 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
          (const int*)w.P.rp, w.count, w.bst);
   if (w.count > 1) {   // the running instances' row blocks, for compacted launches
     cudaMemsetAsync(&w.bst->act_A, 0, 2 * sizeof(int), s);
+    // -1 past the count: the padding blocks of a replayed compacted grid skip
+    if (w.A.nblk > 0) cudaMemsetAsync(w.act_A, 0xFF, (size_t)w.A.nblk * sizeof(int), s);
+    cudaMemsetAsync(w.act_P, 0xFF, (size_t)w.P.nblk * sizeof(int), s);
     if (w.A.nblk > 0)
       launch(k_compact_blocks, std::min(cdiv(w.A.nblk, 256), 4 * w.num_sms), 256, 0, s, (const int*)w.blk_inst_A,
              w.A.nblk, (const DevState*)w.st, w.act_A, &w.bst->act_A);

@@ -150,7 +150,8 @@ struct Work {
   double *cpart_n = nullptr; // [15][nchunk_n]
   int nchunk_m = 0, nchunk_n = 0, maxchunk_m = 0, maxchunk_n = 0;
   int* act_A = nullptr;      // batches: [A.nblk] row blocks of the running instances (count in bst)
-  int* act_P = nullptr;      // [P.nblk]
+  int* act_P = nullptr;      // [P.nblk]; -1 past the count
+  int act_grid_A = 0, act_grid_P = 0;   // > 0: the grids of compacted launches (padded, for a captured graph)
   StepEntry* tab = nullptr;  // [count][tab_stride]
   DevState* st = nullptr;    // [count]
   DevState* st_host = nullptr;   // pinned mirror [count]
