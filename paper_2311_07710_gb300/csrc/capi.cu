@@ -522,6 +522,11 @@ void launch_compact_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cud
         c.key_detect == w.detect && c.key_eps_inf == w.eps_inf)
       g = &c;
   if (!g) {
+    if (h->cgraphs.size() >= 32) {   // many option sets on one handle: start the cache over
+      for (auto& c : h->cgraphs)
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+      h->cgraphs.clear();
+    }
     ChunkGraph c;
     if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
