@@ -1299,8 +1299,8 @@ __device__ void bracket_max_eig_warp(const double* __restrict__ al, const double
   }
 }
 
-// one CUDA block of NT >= 128 threads per instance (all of them sum the block
-// partials): beta, theta = lambda_max(T_k) and the stop test for both
+// one CUDA block of NT >= 128 threads per instance (all of them sum the
+// instance's chunk sums of |r|^2): beta, theta = lambda_max(T_k) and the stop test for both
 // operators (warps 0, 1: A'A; warps 2, 3: Q).  The stop
 // test |theta_k - theta_{k-1}| <= tol theta_k (or beta_k <= 1e-12 theta_k, or the
 // step limit) needs the precise Ritz values only where the brackets of
