@@ -1187,6 +1187,31 @@ void alloc_work(pdqp_problem* h, cudaStream_t s) {
   w.act_P = dalloc<int>(h, (size_t)std::max(w.P.nblk, 1));
   w.cpart_m = dalloc<double>(h, (size_t)9 * std::max(w.nchunk_m, 1));
   w.cpart_n = dalloc<double>(h, (size_t)15 * std::max(w.nchunk_n, 1));
+  {  // relKKT groups: KKT_GROUP consecutive row blocks of one instance each
+    const int count = (int)w.inst_host.size();
+    std::vector<int> gi[2], gf[2];
+    for (int side = 0; side < 2; ++side) {
+      gf[side].assign((size_t)count + 1, 0);
+      for (int i = 0; i < count; ++i) {
+        const Inst& I = w.inst_host[i];
+        const int nb = side ? I.bP1 - I.bP0 : I.bA1 - I.bA0;
+        gf[side][i] = (int)gi[side].size();
+        gi[side].insert(gi[side].end(), (size_t)((nb + KKT_GROUP - 1) / KKT_GROUP), i);
+      }
+      gf[side][count] = (int)gi[side].size();
+    }
+    w.ngrp_A = (int)gi[0].size();
+    w.ngrp_P = (int)gi[1].size();
+    w.grp_inst_A = dalloc<int>(h, std::max<size_t>(gi[0].size(), 1));
+    w.grp_inst_P = dalloc<int>(h, std::max<size_t>(gi[1].size(), 1));
+    w.grp_first_A = dalloc<int>(h, gf[0].size());
+    w.grp_first_P = dalloc<int>(h, gf[1].size());
+    if (!gi[0].empty()) to_device(w.grp_inst_A, gi[0].data(), gi[0].size(), s);
+    if (!gi[1].empty()) to_device(w.grp_inst_P, gi[1].data(), gi[1].size(), s);
+    to_device(w.grp_first_A, gf[0].data(), gf[0].size(), s);
+    to_device(w.grp_first_P, gf[1].data(), gf[1].size(), s);
+    CK(cudaStreamSynchronize(s));   // the host vectors go out of scope
+  }
   w.lz_ticket = dalloc<unsigned>(h, (size_t)std::max(w.nchunk_n, 1));
   CK(cudaMemsetAsync(w.lz_ticket, 0, sizeof(unsigned) * std::max(w.nchunk_n, 1), s));
   w.st = dalloc<DevState>(h, count);

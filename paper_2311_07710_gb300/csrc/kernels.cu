@@ -324,18 +324,34 @@ struct KktB {
   double* prodAx[2];                    // optional: A~x~, Q~x~, A~'y~ per iterate
   double* prodQx[2];
   double* prodATy[2];
-  double* part_m;                       // [9][nblk_m]
-  double* part_n;                       // [15][nblk_n]
-  int nblk_m, nblk_n;
+  double* part_m;                       // [9][ngrp_m] one partial per relKKT group
+  double* part_n;                       // [15][ngrp_n]
+  int ngrp_m, ngrp_n;
   int n, m;
   const unsigned char* ineq;            // per row of A: inequality
-  const int* blk_inst_A;                // instance of each row block (null: no status test)
-  const int* blk_inst_P;
-  const DevState* st;
+  const Inst* inst;
+  const int *grp_inst_A, *grp_first_A;  // relKKT groups (KKT_GROUP row blocks of one instance)
+  const int *grp_inst_P, *grp_first_P;
+  const DevState* st;                   // null: no status test
   const double* F;                      // low-rank factor F~ (null: none)
   const double* wlr;                    // [2][r]: F~' x per iterate
   int r;
 };
+
+// The row blocks [b0, b1) of relKKT group g and its instance: groups are
+// KKT_GROUP consecutive row blocks from the instance's first (of P: side 1,
+// of A: side 0), so a batch and a standalone solve form the same groups.
+struct KktGroup { int inst, b0, b1; };
+__device__ __forceinline__ KktGroup kkt_group(const KktB& a, int side, int g) {
+  KktGroup r;
+  r.inst = side ? a.grp_inst_P[g] : a.grp_inst_A[g];
+  const Inst in = a.inst[r.inst];
+  const int first = side ? a.grp_first_P[r.inst] : a.grp_first_A[r.inst];
+  const int bb = side ? in.bP0 : in.bA0, be = side ? in.bP1 : in.bA1;
+  r.b0 = bb + (g - first) * KKT_GROUP;
+  r.b1 = min(r.b0 + KKT_GROUP, be);
+  return r;
+}
 
 // Sign and class tests on the bits (integer instructions: GB300's float64
 // pipe is the bound of these kernels): v > 0, v < 0, v finite.
@@ -462,47 +478,53 @@ __global__ void __launch_bounds__(BNT) k_kkt_m(KktB a) {
   int* srp = reinterpret_cast<int*>(kkt_sm + (NIT + 1) * BNNZ);
   double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int tid = threadIdx.x;
-  if (a.st && a.st[a.blk_inst_A[blockIdx.x]].status != ST_RUNNING) return;
-  const int r0 = a.A.blk[blockIdx.x], r1 = a.A.blk[blockIdx.x + 1];
-  const int nr = r1 - r0;
-  const int e0 = a.A.rp[r0];
-  const int ne = a.A.rp[r1] - e0;
-  if (ne <= BNNZ) {
-    if (NIT == 2 && a.xx)
-      kkt_stage_pairs(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int c) { return __ldg(a.xx + c); });
-    else
-      kkt_stage<NIT>(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) { return __ldg(a.x[it] + c); });
-    __syncthreads();
-    for (int q = tid; q < nr * NIT; q += BNT) {
-      const int it = q >= nr ? 1 : 0, t = q - it * nr;
-      const double* xv = sx + it * BNNZ;
-      double s = 0.0;
-      for (int e = srp[t]; e < srp[t + 1]; ++e) s = fma(sval[e], xv[e], s);
-      if (it == 0) kkt_m_row<0>(a, f, r0 + t, s);
-      else kkt_m_row<NIT - 1>(a, f, r0 + t, s);
-    }
-  } else {
-    double s[NIT];
+  const KktGroup G = kkt_group(a, 0, blockIdx.x);
+  if (a.st && a.st[G.inst].status != ST_RUNNING) return;
+  for (int bk = G.b0; bk < G.b1; ++bk) {   // the group's row blocks, one after another
+    if (bk > G.b0) __syncthreads();          // the staging buffers are read up to here
+    const int r0 = a.A.blk[bk], r1 = a.A.blk[bk + 1];
+    const int nr = r1 - r0;
+    const int e0 = a.A.rp[r0];
+    const int ne = a.A.rp[r1] - e0;
+    if (ne <= BNNZ) {
+      if (NIT == 2 && a.xx)
+        kkt_stage_pairs(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int c) { return __ldg(a.xx + c); });
+      else
+        kkt_stage<NIT>(a.A, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) { return __ldg(a.x[it] + c); });
+      __syncthreads();
+      for (int q = tid; q < nr * NIT; q += BNT) {
+        const int it = q >= nr ? 1 : 0, t = q - it * nr;
+        const double* xv = sx + it * BNNZ;
+        double s = 0.0;
+        for (int e = srp[t]; e < srp[t + 1]; ++e) s = fma(sval[e], xv[e], s);
+        if (it == 0) kkt_m_row<0>(a, f, r0 + t, s);
+        else kkt_m_row<NIT - 1>(a, f, r0 + t, s);
+      }
+    } else {
+      double s[NIT];
 #pragma unroll
-    for (int it = 0; it < NIT; ++it) s[it] = 0.0;
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) {
-      const double v = a.A.val[e];
-      const int c = a.A.col[e];
+      for (int it = 0; it < NIT; ++it) s[it] = 0.0;
+      for (int e = e0 + tid; e < e0 + ne; e += BNT) {
+        const double v = a.A.val[e];
+        const int c = a.A.col[e];
 #pragma unroll
-      for (int it = 0; it < NIT; ++it) s[it] = fma(v, __ldg(a.x[it] + c), s[it]);
-    }
+        for (int it = 0; it < NIT; ++it) s[it] = fma(v, __ldg(a.x[it] + c), s[it]);
+      }
 #pragma unroll
-    for (int it = 0; it < NIT; ++it) s[it] = block_sum(s[it]);
-    if (tid == 0) {
-      kkt_m_row<0>(a, f, r0, s[0]);
-      if (NIT > 1) kkt_m_row<NIT - 1>(a, f, r0, s[NIT - 1]);
+      for (int it = 0; it < NIT; ++it) s[it] = block_sum(s[it]);
+      if (tid == 0) {
+        kkt_m_row<0>(a, f, r0, s[0]);
+        if (NIT > 1) kkt_m_row<NIT - 1>(a, f, r0, s[NIT - 1]);
+      }
     }
   }
   block_reduce_smem<9, BNT, 0x133u>(f, kkt_sm);
   if (tid == 0)
-    for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
+    for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.ngrp_m + blockIdx.x] = f[k];
 }
 
+// 80 registers (3 blocks per SM): capped at 64 for 4 blocks it spills and is
+// slower (n=1e6 checks 4.67 -> 5.15 ms per solve)
 template <int NIT, bool LR>
 __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
   extern __shared__ __align__(16) double kkt_sm[];
@@ -514,55 +536,59 @@ __global__ void __launch_bounds__(BNT) k_kkt_n(KktB a) {
 #pragma unroll
   for (int k = 0; k < 15; ++k) f[k] = 0.0;
   const int tid = threadIdx.x;
-  if (a.st && a.st[a.blk_inst_P[blockIdx.x]].status != ST_RUNNING) return;
-  const int r0 = a.P.blk[blockIdx.x], r1 = a.P.blk[blockIdx.x + 1];
-  const int nr = r1 - r0;
-  const int e0 = a.P.rp[r0];
-  const int ne = a.P.rp[r1] - e0;
+  const KktGroup G = kkt_group(a, 1, blockIdx.x);
+  if (a.st && a.st[G.inst].status != ST_RUNNING) return;
   const int n = a.n;
-  if (ne <= BNNZ) {
-    if (NIT == 2 && a.xx)
-      kkt_stage_pairs(a.P, e0, ne, r0, nr, sval, sx, srp,
-                      [&](int c) { return c < n ? __ldg(a.xx + c) : __ldg(a.yy + (c - n)); });
-    else
-      kkt_stage<NIT>(a.P, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) {
-        return c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n));
-      });
-    for (int t = tid; t < nr; t += BNT) ssp[t] = a.P.split[r0 + t] - e0;
-    __syncthreads();
-    for (int q = tid; q < nr * NIT; q += BNT) {
-      const int it = q >= nr ? 1 : 0, t = q - it * nr;
-      const double* xv = sx + it * BNNZ;
-      double sq = 0.0, sa = 0.0;
-      for (int e = srp[t]; e < ssp[t]; ++e) sq = fma(sval[e], xv[e], sq);
-      for (int e = ssp[t]; e < srp[t + 1]; ++e) sa = fma(sval[e], xv[e], sa);
-      if (it == 0) kkt_n_row<0, LR>(a, f, r0 + t, sq, sa);
-      else kkt_n_row<NIT - 1, LR>(a, f, r0 + t, sq, sa);
-    }
-  } else {
-    const int sp = a.P.split[r0];
-    double sq[NIT], sa[NIT];
-#pragma unroll
-    for (int it = 0; it < NIT; ++it) { sq[it] = 0.0; sa[it] = 0.0; }
-    for (int e = e0 + tid; e < e0 + ne; e += BNT) {
-      const double v = a.P.val[e];
-      const int c = a.P.col[e];
-#pragma unroll
-      for (int it = 0; it < NIT; ++it) {
-        if (e < sp) sq[it] = fma(v, __ldg(a.x[it] + c), sq[it]);
-        else sa[it] = fma(v, __ldg(a.y[it] + (c - n)), sa[it]);
+  for (int bk = G.b0; bk < G.b1; ++bk) {   // the group's row blocks, one after another
+    if (bk > G.b0) __syncthreads();          // the staging buffers are read up to here
+    const int r0 = a.P.blk[bk], r1 = a.P.blk[bk + 1];
+    const int nr = r1 - r0;
+    const int e0 = a.P.rp[r0];
+    const int ne = a.P.rp[r1] - e0;
+    if (ne <= BNNZ) {
+      if (NIT == 2 && a.xx)
+        kkt_stage_pairs(a.P, e0, ne, r0, nr, sval, sx, srp,
+                        [&](int c) { return c < n ? __ldg(a.xx + c) : __ldg(a.yy + (c - n)); });
+      else
+        kkt_stage<NIT>(a.P, e0, ne, r0, nr, sval, sx, srp, [&](int it, int c) {
+          return c < n ? __ldg(a.x[it] + c) : __ldg(a.y[it] + (c - n));
+        });
+      for (int t = tid; t < nr; t += BNT) ssp[t] = a.P.split[r0 + t] - e0;
+      __syncthreads();
+      for (int q = tid; q < nr * NIT; q += BNT) {
+        const int it = q >= nr ? 1 : 0, t = q - it * nr;
+        const double* xv = sx + it * BNNZ;
+        double sq = 0.0, sa = 0.0;
+        for (int e = srp[t]; e < ssp[t]; ++e) sq = fma(sval[e], xv[e], sq);
+        for (int e = ssp[t]; e < srp[t + 1]; ++e) sa = fma(sval[e], xv[e], sa);
+        if (it == 0) kkt_n_row<0, LR>(a, f, r0 + t, sq, sa);
+        else kkt_n_row<NIT - 1, LR>(a, f, r0 + t, sq, sa);
       }
-    }
+    } else {
+      const int sp = a.P.split[r0];
+      double sq[NIT], sa[NIT];
 #pragma unroll
-    for (int it = 0; it < NIT; ++it) { sq[it] = block_sum(sq[it]); sa[it] = block_sum(sa[it]); }
-    if (tid == 0) {
-      kkt_n_row<0, LR>(a, f, r0, sq[0], sa[0]);
-      if (NIT > 1) kkt_n_row<NIT - 1, LR>(a, f, r0, sq[NIT - 1], sa[NIT - 1]);
+      for (int it = 0; it < NIT; ++it) { sq[it] = 0.0; sa[it] = 0.0; }
+      for (int e = e0 + tid; e < e0 + ne; e += BNT) {
+        const double v = a.P.val[e];
+        const int c = a.P.col[e];
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+          if (e < sp) sq[it] = fma(v, __ldg(a.x[it] + c), sq[it]);
+          else sa[it] = fma(v, __ldg(a.y[it] + (c - n)), sa[it]);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) { sq[it] = block_sum(sq[it]); sa[it] = block_sum(sa[it]); }
+      if (tid == 0) {
+        kkt_n_row<0, LR>(a, f, r0, sq[0], sa[0]);
+        if (NIT > 1) kkt_n_row<NIT - 1, LR>(a, f, r0, sq[NIT - 1], sa[NIT - 1]);
+      }
     }
   }
   block_reduce_smem<15, BNT, 0x4387u>(f, kkt_sm);
   if (tid == 0)
-    for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
+    for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.ngrp_n + blockIdx.x] = f[k];
 }
 
 // launch both relKKT kernels with their dynamic shared memory
@@ -574,9 +600,9 @@ static void launch_kkt(const Work& w, const KktB& a, cudaStream_t s) {
     cudaFuncSetAttribute(k_kkt_n<NIT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
     cudaFuncSetAttribute(k_kkt_n<NIT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kkt_smem_bytes<NIT>());
   });
-  if (w.m > 0) launch(k_kkt_m<NIT>, w.A.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
-  if (a.F) launch(k_kkt_n<NIT, true>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
-  else launch(k_kkt_n<NIT, false>, w.P.nblk, BNT, kkt_smem_bytes<NIT>(), s, a);
+  if (w.m > 0) launch(k_kkt_m<NIT>, w.ngrp_A, BNT, kkt_smem_bytes<NIT>(), s, a);
+  if (a.F) launch(k_kkt_n<NIT, true>, w.ngrp_P, BNT, kkt_smem_bytes<NIT>(), s, a);
+  else launch(k_kkt_n<NIT, false>, w.ngrp_P, BNT, kkt_smem_bytes<NIT>(), s, a);
 }
 
 // --------------------------------------------------------------------------
@@ -663,16 +689,19 @@ __global__ void __launch_bounds__(BNT) k_kkt_m_sums(KktB a, const double* __rest
   __shared__ double sh[9 * BNT];
   double f[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int tid = threadIdx.x;
-  if (a.st && a.st[a.blk_inst_A[blockIdx.x]].status != ST_RUNNING) return;
-  const int r0 = a.A.blk[blockIdx.x], nr = a.A.blk[blockIdx.x + 1] - r0;
-  for (int q = tid; q < nr * 2; q += BNT) {
-    const int it = q >= nr ? 1 : 0, t = q - it * nr;
-    if (it == 0) kkt_m_row<0>(a, f, r0 + t, s0[r0 + t]);
-    else kkt_m_row<1>(a, f, r0 + t, s1[r0 + t]);
+  const KktGroup G = kkt_group(a, 0, blockIdx.x);
+  if (a.st && a.st[G.inst].status != ST_RUNNING) return;
+  for (int bk = G.b0; bk < G.b1; ++bk) {
+    const int r0 = a.A.blk[bk], nr = a.A.blk[bk + 1] - r0;
+    for (int q = tid; q < nr * 2; q += BNT) {
+      const int it = q >= nr ? 1 : 0, t = q - it * nr;
+      if (it == 0) kkt_m_row<0>(a, f, r0 + t, s0[r0 + t]);
+      else kkt_m_row<1>(a, f, r0 + t, s1[r0 + t]);
+    }
   }
   block_reduce_smem<9, BNT, 0x133u>(f, sh);
   if (tid == 0)
-    for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.nblk_m + blockIdx.x] = f[k];
+    for (int k = 0; k < 9; ++k) a.part_m[(size_t)k * a.ngrp_m + blockIdx.x] = f[k];
 }
 
 __global__ void __launch_bounds__(BNT) k_kkt_n_sums(KktB a, const double* __restrict__ q0,
@@ -683,16 +712,19 @@ __global__ void __launch_bounds__(BNT) k_kkt_n_sums(KktB a, const double* __rest
 #pragma unroll
   for (int k = 0; k < 15; ++k) f[k] = 0.0;
   const int tid = threadIdx.x;
-  if (a.st && a.st[a.blk_inst_P[blockIdx.x]].status != ST_RUNNING) return;
-  const int r0 = a.P.blk[blockIdx.x], nr = a.P.blk[blockIdx.x + 1] - r0;
-  for (int q = tid; q < nr * 2; q += BNT) {
-    const int it = q >= nr ? 1 : 0, t = q - it * nr;
-    if (it == 0) kkt_n_row<0, false>(a, f, r0 + t, q0[r0 + t], t0[r0 + t]);
-    else kkt_n_row<1, false>(a, f, r0 + t, q1[r0 + t], t1[r0 + t]);
+  const KktGroup G = kkt_group(a, 1, blockIdx.x);
+  if (a.st && a.st[G.inst].status != ST_RUNNING) return;
+  for (int bk = G.b0; bk < G.b1; ++bk) {
+    const int r0 = a.P.blk[bk], nr = a.P.blk[bk + 1] - r0;
+    for (int q = tid; q < nr * 2; q += BNT) {
+      const int it = q >= nr ? 1 : 0, t = q - it * nr;
+      if (it == 0) kkt_n_row<0, false>(a, f, r0 + t, q0[r0 + t], t0[r0 + t]);
+      else kkt_n_row<1, false>(a, f, r0 + t, q1[r0 + t], t1[r0 + t]);
+    }
   }
   block_reduce_smem<15, BNT, 0x4387u>(f, sh);
   if (tid == 0)
-    for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.nblk_n + blockIdx.x] = f[k];
+    for (int k = 0; k < 15; ++k) a.part_n[(size_t)k * a.ngrp_n + blockIdx.x] = f[k];
 }
 
 // the check's relKKT partials of a family handle through the interleaved sums
@@ -719,8 +751,8 @@ static void launch_kkt_il(Work& w, const KktB& a, cudaStream_t s) {
   from_il<double>(I[ILK_SQ1], ld, n, cnt, S[3], n, s);
   from_il<double>(I[ILK_ST0], ld, n, cnt, S[4], n, s);
   from_il<double>(I[ILK_ST1], ld, n, cnt, S[5], n, s);
-  if (w.m > 0) launch(k_kkt_m_sums, w.A.nblk, BNT, 0, s, a, (const double*)S[0], (const double*)S[1]);
-  launch(k_kkt_n_sums, w.P.nblk, BNT, 0, s, a, (const double*)S[2], (const double*)S[3], (const double*)S[4],
+  if (w.m > 0) launch(k_kkt_m_sums, w.ngrp_A, BNT, 0, s, a, (const double*)S[0], (const double*)S[1]);
+  launch(k_kkt_n_sums, w.ngrp_P, BNT, 0, s, a, (const double*)S[2], (const double*)S[3], (const double*)S[4],
          (const double*)S[5]);
 }
 
@@ -1565,41 +1597,46 @@ __device__ void fill_steps_block(const DevState& S, const SolveParams& p, StepEn
 __device__ void decide_thread0(DevState* __restrict__ st, const double* F, const SolveParams& p, int mode,
                                long long chunk_len, int inf_status);
 
-// Chunk sums of the relKKT block partials: CUDA block (i, c) reduces chunk c
-// of instance i -- KKT_CHUNK consecutive row blocks from the instance's first
-// -- for every field in a fixed order, so that a batch and a standalone solve
-// sum identically and the decision kernel reads tens of values, not thousands.
-__global__ void __launch_bounds__(32) k_kkt_chunks(const Inst* __restrict__ insts, const double* __restrict__ pm,
-                                                   int nbm, const double* __restrict__ pn, int nbn,
-                                                   double* __restrict__ cm, int ncm, double* __restrict__ cn,
-                                                   int ncn) {
-  const Inst in = insts[blockIdx.x];
+// Chunk sums of the relKKT group partials: CUDA block (i, c) reduces chunk c
+// of instance i -- its KKT_CHUNK / KKT_GROUP consecutive groups from the
+// instance's first (KKT_CHUNK row blocks) -- for every field in a fixed order,
+// so that a batch and a standalone solve sum identically and the decision
+// kernel reads tens of values, not thousands.  gfm, gfn: first group of each
+// instance (A, P).
+constexpr int KKT_GPC = KKT_CHUNK / KKT_GROUP;   // groups per chunk (8: lanes 0..7)
+__global__ void __launch_bounds__(32) k_kkt_chunks(const Inst* __restrict__ insts, const int* __restrict__ gfm,
+                                                   const double* __restrict__ pm, int ngm,
+                                                   const int* __restrict__ gfn, const double* __restrict__ pn,
+                                                   int ngn, double* __restrict__ cm, int ncm,
+                                                   double* __restrict__ cn, int ncn) {
+  const int i = blockIdx.x;
+  const Inst in = insts[i];
   const int lane = threadIdx.x, c = blockIdx.y;
-  const int bp = in.bP0 + c * KKT_CHUNK;
-  if (bp < in.bP1) {
+  if (in.bP0 + c * KKT_CHUNK < in.bP1) {
     const bool is_max[15] = {true, true, true, false, false, false, false,
                              true, true, true, false, false, false, false, true};
-    const int b = bp + lane;
+    const int g = gfn[i] + c * KKT_GPC + lane;
+    const bool on = lane < KKT_GPC && g < gfn[i + 1];
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
-      double v = b < in.bP1 ? pn[(size_t)k * nbn + b] : 0.0;
+      double v = on ? pn[(size_t)k * ngn + g] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = KKT_GPC / 2; o > 0; o >>= 1) {
         const double t = __shfl_xor_sync(0xffffffffu, v, o);
         v = is_max[k] ? nmax(v, t) : v + t;
       }
       if (lane == 0) cn[(size_t)k * ncn + in.cP0 + c] = v;
     }
   }
-  const int ba = in.bA0 + c * KKT_CHUNK;
-  if (in.m > 0 && ba < in.bA1) {
+  if (in.m > 0 && in.bA0 + c * KKT_CHUNK < in.bA1) {
     const bool is_max[9] = {true, true, false, false, true, true, false, false, true};
-    const int b = ba + lane;
+    const int g = gfm[i] + c * KKT_GPC + lane;
+    const bool on = lane < KKT_GPC && g < gfm[i + 1];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      double v = b < in.bA1 ? pm[(size_t)k * nbm + b] : 0.0;
+      double v = on ? pm[(size_t)k * ngm + g] : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = KKT_GPC / 2; o > 0; o >>= 1) {
         const double t = __shfl_xor_sync(0xffffffffu, v, o);
         v = is_max[k] ? nmax(v, t) : v + t;
       }
@@ -2063,10 +2100,12 @@ static KktB kkt_args(Work& w, bool scaled) {
   if (scaled) { a.D1 = w.D1; a.D2 = w.D2; a.iD1 = w.iD1; a.iD2 = w.iD2; }
   a.b = w.b; a.c = w.c; a.l = w.l; a.u = w.u;
   a.part_m = w.part_m; a.part_n = w.part_n;
-  a.nblk_m = w.A.nblk; a.nblk_n = w.P.nblk;
+  a.ngrp_m = w.ngrp_A; a.ngrp_n = w.ngrp_P;
+  a.inst = w.inst;
+  a.grp_inst_A = w.grp_inst_A; a.grp_first_A = w.grp_first_A;
+  a.grp_inst_P = w.grp_inst_P; a.grp_first_P = w.grp_first_P;
   a.n = w.n; a.m = w.m;
   a.ineq = w.row_ineq;
-  a.blk_inst_A = w.blk_inst_A; a.blk_inst_P = w.blk_inst_P;
   a.st = w.st;
   return a;
 }
@@ -2219,9 +2258,9 @@ static void infeas_check(Work& w, const KktB& main, cudaStream_t s) {
       a.c = w.inf_zn;
     }
     launch_kkt<2>(w, a, s);
-    launch(k_kkt_chunks, cgrid, 32, 0, s, (const Inst*)w.inst, (const double*)w.inf_part_m, w.A.nblk,
-           (const double*)w.inf_part_n, w.P.nblk, w.inf_cpart_m, std::max(w.nchunk_m, 1), w.inf_cpart_n,
-           std::max(w.nchunk_n, 1));
+    launch(k_kkt_chunks, cgrid, 32, 0, s, (const Inst*)w.inst, (const int*)w.grp_first_A,
+           (const double*)w.inf_part_m, w.ngrp_A, (const int*)w.grp_first_P, (const double*)w.inf_part_n,
+           w.ngrp_P, w.inf_cpart_m, std::max(w.nchunk_m, 1), w.inf_cpart_n, std::max(w.nchunk_n, 1));
     if (pass == 0)
       launch(k_infeas<0>, w.count, 64, 0, s, w.inf, (const DevState*)w.st, (const Inst*)w.inst,
              (const double*)w.inf_cpart_m, std::max(w.nchunk_m, 1), (const double*)w.inf_cpart_n,
@@ -2278,8 +2317,9 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
   else launch_kkt<2>(w, a, s);
   {
     const dim3 grid(w.count, std::max(w.maxchunk_n, w.maxchunk_m));
-    launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const double*)w.part_m, w.A.nblk,
-           (const double*)w.part_n, w.P.nblk, w.cpart_m, std::max(w.nchunk_m, 1), w.cpart_n, std::max(w.nchunk_n, 1));
+    launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const int*)w.grp_first_A, (const double*)w.part_m,
+           w.ngrp_A, (const int*)w.grp_first_P, (const double*)w.part_n, w.ngrp_P, w.cpart_m,
+           std::max(w.nchunk_m, 1), w.cpart_n, std::max(w.nchunk_n, 1));
   }
   const bool certify = w.detect && w.inf && mode == 1;
   if (certify) infeas_check(w, a, s);
@@ -2343,8 +2383,8 @@ void eval_kkt_user(Work& w, const double* x, const double* y, cudaStream_t s) {
     a.F = w.Fo; a.wlr = w.wlr; a.r = w.r;
   }
   launch_kkt<1>(w, a, s);
-  launch(k_kkt_finish_user, 1, 1024, 0, s, (const double*)w.part_m, w.m > 0 ? w.A.nblk : 0,
-         (const double*)w.part_n, w.P.nblk, w.st);
+  launch(k_kkt_finish_user, 1, 1024, 0, s, (const double*)w.part_m, w.m > 0 ? w.ngrp_A : 0,
+         (const double*)w.part_n, w.ngrp_P, w.st);
 }
 
 }  // namespace pdqp

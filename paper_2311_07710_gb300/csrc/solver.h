@@ -91,6 +91,11 @@ struct InfState {
   double scale, dual_scale;
 };
 
+// Row blocks per CUDA block of the relKKT kernels; a chunk of KKT_CHUNK row
+// blocks is KKT_CHUNK / KKT_GROUP groups.
+constexpr int KKT_GROUP = 4;
+static_assert(KKT_CHUNK % KKT_GROUP == 0, "a relKKT chunk holds whole groups");
+
 struct Work {
   int n = 0, m = 0, m_eq = 0;   // totals over the batch (m_eq: single-instance value)
   int count = 1;                // instances stacked block-diagonally
@@ -141,6 +146,11 @@ struct Work {
   float *flw[2] = {nullptr, nullptr};
   double *lz_al = nullptr, *lz_be = nullptr;   // [count][2][512] Lanczos coefficients
   unsigned* lz_ticket = nullptr;   // [nchunk_n] Lanczos chunk tickets (0 between launches)
+  // relKKT groups: KKT_GROUP consecutive row blocks of one instance per CUDA
+  // block of the check kernels (one field reduction per group)
+  int ngrp_P = 0, ngrp_A = 0;
+  int *grp_inst_P = nullptr, *grp_inst_A = nullptr;     // [ngrp] instance of each group
+  int *grp_first_P = nullptr, *grp_first_A = nullptr;   // [count + 1] first group of each instance
   double2 *kkt_xx = nullptr, *kkt_yy = nullptr;   // [n], [m]: (x, x_bar), (y, y_bar) pairs the relKKT kernels gather
   // reductions
   double *part = nullptr;    // [PDQP_RED_BLOCKS][32] (legacy layout, pdqp_kkt_noalloc kernels)
