@@ -699,14 +699,20 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       pdqp::scale_apply(lw, mixed, s);
     }
     pdqp::lanczos_init(lw, mixed, s);
+    lw.lz_compact = 0;
     for (int t = 0; t < o.norm_iters; ++t) {
       pdqp::lanczos_step(lw, t, p, mixed, s);
       if ((t & 7) == 7) {
         pdqp::count_running(lw, s);
+        if (lw.count > 1) pdqp::lanczos_compact(lw, s);
         sync_batch(lh, s);
         if (lw.bst_host->lz_running == 0) break;
+        // once the instances still estimating hold less than half of the row
+        // blocks, the next steps launch over theirs only
+        lw.lz_compact = lw.count > 1 && 2LL * lw.bst_host->act_P < (long long)lw.P.nblk ? 1 : 0;
       }
     }
+    lw.lz_compact = 0;
   }
   if (!resuming) {
     pdqp::norms_finish(lw, o.norm_A, o.norm_Q, s);

@@ -936,6 +936,10 @@ struct LzArgs {
   double* cpart;                   // [2][nchunk] chunk sums of the row-block partials
   unsigned* ticket;                // [nchunk] zero between launches
   int nchunk;
+  // batches late in the estimates: the row blocks of the instances still
+  // estimating (null: every row block); nactP entries of actP
+  const int *actA, *actP;
+  int nactP;
 };
 
 // After row block b of instance i wrote its two partials (part[b],
@@ -978,13 +982,14 @@ __device__ __forceinline__ double* lz_be(const LzArgs& a, int i, int o) { return
 template <typename V, int NT>
 __global__ void __launch_bounds__(NT, MinBlocks<V, NT>::value) k_lz_m(BCsr<V> A, LzArgs la, const V* __restrict__ vA,
                                                                    V* __restrict__ wm) {
-  const DevState& st = la.st[la.blk_inst_A[blockIdx.x]];
+  const int bk = la.actA ? la.actA[blockIdx.x] : (int)blockIdx.x;
+  const DevState& st = la.st[la.blk_inst_A[bk]];
   if (st.pi_done[0]) return;
   __shared__ V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   const int tid = threadIdx.x;
   const V gA = lz_scale<V>(la, st, 0);
-  const int r0 = A.blk[blockIdx.x], r1 = A.blk[blockIdx.x + 1];
+  const int r0 = A.blk[bk], r1 = A.blk[bk + 1];
   const int nr = r1 - r0;
   const int e0 = A.rp[r0];
   const int ne = A.rp[r1] - e0;
@@ -1014,14 +1019,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
   __shared__ __align__(16) V prod[BNNZ];
   __shared__ int srp[BROWS + 1];
   __shared__ int ssp[BROWS];
-  const DevState& st = la.st[la.blk_inst_P[blockIdx.x]];
+  const int bk = la.actP ? la.actP[blockIdx.x] : (int)blockIdx.x;
+  const DevState& st = la.st[la.blk_inst_P[bk]];
   const bool doA = !st.pi_done[0];
   const bool doQ = !st.pi_done[1];
   if (!doA && !doQ) return;                    // its instance's alpha reduction skips it
   double f[2] = {0.0, 0.0};
   const int tid = threadIdx.x;
   const V gA = lz_scale<V>(la, st, 0), gQ = lz_scale<V>(la, st, 1);   // v_A, v_Q normalisation
-  const int r0 = P.blk[blockIdx.x], r1 = P.blk[blockIdx.x + 1];
+  const int r0 = P.blk[bk], r1 = P.blk[bk + 1];
   const int nr = r1 - r0;
   const int e0 = P.rp[r0];
   const int ne = P.rp[r1] - e0;
@@ -1060,9 +1066,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_lz_n(BCsr<V
   static_assert(sizeof(V) * BNNZ >= 2 * NT * sizeof(double), "staging buffer too small for the reduction");
   block_reduce_smem<2, NT, 0u>(f, reinterpret_cast<double*>(prod));
   if (tid == 0) {
-    part[blockIdx.x] = f[0];
-    part[(size_t)la.nblkP + blockIdx.x] = f[1];
-    lz_chunk_close(la, part, blockIdx.x, la.blk_inst_P[blockIdx.x]);
+    part[bk] = f[0];
+    part[(size_t)la.nblkP + bk] = f[1];
+    lz_chunk_close(la, part, bk, la.blk_inst_P[bk]);
   }
 }
 
@@ -1117,8 +1123,9 @@ __global__ void __launch_bounds__(256) k_lz_orth(LzArgs a, BCsr<V> P, const V* _
                                                  const V* __restrict__ wQ, V* __restrict__ vA,
                                                  V* __restrict__ vA_prev, V* __restrict__ vQ,
                                                  V* __restrict__ vQ_prev, double* __restrict__ part) {
-  const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (b >= a.nblkP) return;                      // warp-uniform
+  const int q = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (q >= (a.actP ? a.nactP : a.nblkP)) return;   // warp-uniform
+  const int b = a.actP ? a.actP[q] : q;
   const int i = a.blk_inst_P[b];
   const DevState& st = a.st[i];
   const bool doA = !st.pi_done[0], doQ = !st.pi_done[1];
@@ -1968,6 +1975,7 @@ static LzArgs lz_args(Work& w) {
   la.nblkP = w.P.nblk;
   la.lazy = w.r == 0 ? 1 : 0;
   la.cpart = w.cpart_n; la.ticket = w.lz_ticket; la.nchunk = w.nchunk_n;
+  if (w.lz_compact) { la.actA = w.act_A; la.actP = w.act_P; la.nactP = w.bst_host->act_P; }
   return la;
 }
 
@@ -1987,22 +1995,24 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
                            V* const* lw, cudaStream_t s) {
   const int cur = t & 1, prv = cur ^ 1;
   const LzArgs la = lz_args(w);
-  if (w.m > 0) launch(k_lz_m<V, NT>, w.A.nblk, NT, 0, s, A, la, (const V*)pu[cur], pz[cur] + w.n);
+  // all row blocks, or late in a batch's estimates those of the instances still running
+  const int gA = w.lz_compact ? w.bst_host->act_A : w.A.nblk, gP = w.lz_compact ? w.bst_host->act_P : w.P.nblk;
+  if (w.m > 0) launch(k_lz_m<V, NT>, gA, NT, 0, s, A, la, (const V*)pu[cur], pz[cur] + w.n);
   const V* F = nullptr;
   if (w.r > 0) {
     F = lr_factor<V>(w);
     lowrank_ft<V, V>(w, F, (const V*)pz[cur], (const V*)nullptr, s);
   }
   if (F)
-    launch(k_lz_n<V, NT, true>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
+    launch(k_lz_n<V, NT, true>, gP, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
            w.part_n, F, lr_weights<V>(w), w.r);
   else
-    launch(k_lz_n<V, NT, false>, w.P.nblk, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
+    launch(k_lz_n<V, NT, false>, gP, NT, 0, s, P, la, (const V*)pz[cur], (const V*)pu[cur], lw[0], lw[1],
            w.part_n, F, lr_weights<V>(w), w.r);
   // the per-instance reductions read the chunk sums (a few hundred for the
   // largest instance), so 128 threads each suffice
   launch(k_lz_alpha<128>, w.count, 128, 0, s, la);
-  launch(k_lz_orth<V>, cdiv(w.P.nblk, 8), 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], pu[cur], pu[prv],
+  launch(k_lz_orth<V>, cdiv(gP, 8), 256, 0, s, la, P, (const V*)lw[0], (const V*)lw[1], pu[cur], pu[prv],
          pz[cur], pz[prv], w.part_n);
   // the tridiagonals have t + 1 rows at step t: shared memory for that many
   // (the blocks per SM grow as the arrays shrink)
@@ -2018,6 +2028,27 @@ static void lanczos_step_t(Work& w, int t, const SolveParams& p, BCsr<V> A, BCsr
 void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s) {
   if (mixed) lanczos_step_t<float, 256>(w, t, p, w.A.bscaled_f(), w.P.bscaled_f(), w.fpu, w.fpz, w.flw, s);
   else lanczos_step_t<double, 256>(w, t, p, w.A.bscaled(), w.P.bscaled(), w.pu, w.pz, w.lw, s);
+}
+
+// the row blocks of the instances whose estimates are still running: of A
+// where ||A|| is, of P where either is (the counts go to bst, read by the
+// host at its next synchronisation)
+__global__ void k_compact_lz(const int* __restrict__ blk_inst, int nblk, const DevState* __restrict__ st, int side,
+                             int* __restrict__ act, int* __restrict__ n) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+    const DevState& S = st[blk_inst[b]];
+    const bool run = side ? !(S.pi_done[0] && S.pi_done[1]) : !S.pi_done[0];
+    if (run) act[atomicAdd(n, 1)] = b;
+  }
+}
+
+void lanczos_compact(Work& w, cudaStream_t s) {
+  cudaMemsetAsync(&w.bst->act_A, 0, 2 * sizeof(int), s);
+  if (w.A.nblk > 0)
+    launch(k_compact_lz, std::min(cdiv(w.A.nblk, 256), 4 * w.num_sms), 256, 0, s, (const int*)w.blk_inst_A, w.A.nblk,
+           (const DevState*)w.st, 0, w.act_A, &w.bst->act_A);
+  launch(k_compact_lz, std::min(cdiv(w.P.nblk, 256), 4 * w.num_sms), 256, 0, s, (const int*)w.blk_inst_P, w.P.nblk,
+         (const DevState*)w.st, 1, w.act_P, &w.bst->act_P);
 }
 
 void count_running(Work& w, cudaStream_t s) {

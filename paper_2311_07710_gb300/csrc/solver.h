@@ -161,6 +161,7 @@ struct Work {
   int nchunk_m = 0, nchunk_n = 0, maxchunk_m = 0, maxchunk_n = 0;
   int* act_A = nullptr;      // batches: [A.nblk] row blocks of the running instances (count in bst)
   int* act_P = nullptr;      // [P.nblk]; -1 past the count
+  int lz_compact = 0;          // Lanczos steps over the lists of w.act_A / w.act_P (counts in bst_host)
   int act_grid_A = 0, act_grid_P = 0;   // > 0: the grids of compacted launches (padded, for a captured graph)
   StepEntry* tab = nullptr;  // [count][tab_stride]
   DevState* st = nullptr;    // [count]
@@ -218,6 +219,9 @@ void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
 void family_scaling(Work& w, const Work& t, cudaStream_t s);
 void family_norms(Work& w, const Work& t, cudaStream_t s);
 void count_running(Work& w, cudaStream_t s);
+// batches: list the row blocks of the instances whose norm estimates still
+// run (w.act_A / w.act_P, counts in w.bst) for compacted Lanczos steps
+void lanczos_compact(Work& w, cudaStream_t s);
 void init_iterates(Work& w, const double* x0, const double* y0, const SolveParams& p, cudaStream_t s);
 
 // iteration

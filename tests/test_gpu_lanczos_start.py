@@ -63,3 +63,30 @@ def test_norms_repeat_and_match_in_a_batch(pdqp, precision):
     finally:
         P.pdqp_destroy(hb)
     assert [(i.norm_A, i.norm_Q, i.norm_iters) for i in infos] == [keys[0], keys[0]]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_batch_norms_match_standalone_when_estimates_finish_apart(pdqp, precision):
+    """Late in a batch's estimates the Lanczos steps run over the row blocks of
+    the instances still estimating only; the norms stay bitwise those of the
+    standalone solves: control QPs whose estimates stop many steps apart."""
+    import qpgen
+    from paper_2311_07710_gb300 import pdqp as P
+    insts = qpgen.mpc_batch(48, seed=qpgen.SEED_BASE + 7411)
+    o = P.pdqp_default_options(precision=precision, max_iter=64, eps=0.0)
+    hb = P.batch_from_instances(insts)
+    try:
+        P.pdqp_solve(hb, o)
+        infos = P.pdqp_batch_info(hb)
+    finally:
+        P.pdqp_destroy(hb)
+    steps = [i.norm_iters for i in infos]
+    assert max(steps) - min(steps) >= 24          # the batch runs compacted steps at its end
+    order = sorted(range(len(insts)), key=lambda k: steps[k])
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        h = G.handle(insts[k])
+        try:
+            info = P.pdqp_solve(h, o)[1]
+        finally:
+            P.pdqp_destroy(h)
+        assert (info.norm_A, info.norm_Q, info.norm_iters) == (infos[k].norm_A, infos[k].norm_Q, infos[k].norm_iters)
