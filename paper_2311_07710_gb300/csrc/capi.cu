@@ -1193,6 +1193,11 @@ void alloc_work(pdqp_problem* h, cudaStream_t s) {
   w.act_P = dalloc<int>(h, (size_t)std::max(w.P.nblk, 1));
   w.cpart_m = dalloc<double>(h, (size_t)9 * std::max(w.nchunk_m, 1));
   w.cpart_n = dalloc<double>(h, (size_t)15 * std::max(w.nchunk_n, 1));
+  {  // the L2 prefetch of the row blocks' streams pays where every instance is small
+    long long big = 0;
+    for (const Inst& I : w.inst_host) big = std::max(big, (long long)I.n + I.m);
+    w.P.pf = w.A.pf = big <= 32768 ? 1 : 0;
+  }
   {  // relKKT groups: KKT_GROUP consecutive row blocks of one instance each
     const int count = (int)w.inst_host.size();
     std::vector<int> gi[2], gf[2];

@@ -95,6 +95,17 @@ __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __rest
   const int tid = threadIdx.x;
   const int a0 = e0 & ~3, o = e0 - a0;
   const int nq = (o + ne + 3) >> 2;
+  // matrices of small instances (M.pf): the block's index and value quads
+  // towards L2 at once (a bulk prefetch, a hint with no completion to wait
+  // for), so that the later phases' loads find them there instead of waiting
+  // for DRAM behind the earlier phases' gathers; both ranges start on a quad
+  // (16 bytes) and span whole quads
+  if (M.pf && tid == 0 && nq > 0) {
+    const unsigned long long gc = (unsigned long long)__cvta_generic_to_global(M.col + a0);
+    const unsigned long long gv = (unsigned long long)__cvta_generic_to_global(M.val + a0);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gc), "r"(nq * 16) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gv), "r"(nq * 4 * (int)sizeof(V)) : "memory");
+  }
   for (int t = tid; t <= nr; t += NT) srp[t] = M.rp[r0 + t] - e0;
 #pragma unroll
   for (int h = 0; h < QPT; h += QPP) {
