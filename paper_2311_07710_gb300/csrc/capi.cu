@@ -463,30 +463,49 @@ cudaGraphExec_t capture_iterations(pdqp_problem* h, int len, bool mixed, int nt,
   return exec;
 }
 
-void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
+// Capture one chunk (check_period iterations and the check) into c: over all
+// row blocks, or (compact) over the compacted lists of the running instances'
+// row blocks at the grids gA, gP.
+void capture_chunk(pdqp_problem* h, const SolveParams& p, bool mixed, bool compact, int gA, int gP,
+                   ChunkGraph& c) {
   Work& w = h->w;
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  pdqp::t_capturing = true;    // captured, not launched
+  pdqp::t_captured = 0;
+  w.act_grid_A = compact ? std::max(gA, 1) : 0;
+  w.act_grid_P = compact ? std::max(gP, 1) : 0;
+  pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap, 0, compact);
+  w.act_grid_A = w.act_grid_P = 0;
+  pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
+  pdqp::t_capturing = false;
+  c.kernels = pdqp::t_captured;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamEndCapture(h->cap, &graph));
+  const cudaError_t e = cudaGraphInstantiate(&c.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  c.key = p;
+  c.key_detect = w.detect;
+  c.key_eps_inf = w.eps_inf;
+  c.valid = true;
+  c.gA = gA;
+  c.gP = gP;
+}
+
+// a captured chunk is valid for the solve parameters and certificate options
+// it was captured with
+bool graph_matches(const ChunkGraph& c, const Work& w, const SolveParams& p) {
+  return c.valid && std::memcmp(&c.key, &p, sizeof(SolveParams)) == 0 && c.key_detect == w.detect &&
+         c.key_eps_inf == w.eps_inf;
+}
+
+void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
   ChunkGraph& g = h->graph;
-  if (!g.valid || std::memcmp(&g.key, &p, sizeof(SolveParams)) != 0 || g.key_detect != w.detect ||
-      g.key_eps_inf != w.eps_inf) {
+  if (!graph_matches(g, h->w, p)) {
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
     g.valid = false;
-    if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    pdqp::t_capturing = true;    // captured, not launched
-    pdqp::t_captured = 0;
-    pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap);
-    pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
-    pdqp::t_capturing = false;
-    g.kernels = pdqp::t_captured;
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamEndCapture(h->cap, &graph));
-    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(e);
-    g.key = p;
-    g.key_detect = w.detect;
-    g.key_eps_inf = w.eps_inf;
-    g.valid = true;
+    capture_chunk(h, p, mixed, false, 0, 0, g);
   }
   CK(cudaGraphLaunch(g.exec, s));
   pdqp::g_launches += g.kernels;
@@ -518,9 +537,7 @@ void launch_compact_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cud
   const int gA = pad_grid(w.bst_host->act_A, w.A.nblk), gP = pad_grid(w.bst_host->act_P, w.P.nblk);
   ChunkGraph* g = nullptr;
   for (ChunkGraph& c : h->cgraphs)
-    if (c.gA == gA && c.gP == gP && std::memcmp(&c.key, &p, sizeof(SolveParams)) == 0 &&
-        c.key_detect == w.detect && c.key_eps_inf == w.eps_inf)
-      g = &c;
+    if (c.gA == gA && c.gP == gP && graph_matches(c, w, p)) g = &c;
   if (!g) {
     if (h->cgraphs.size() >= 32) {   // many option sets on one handle: start the cache over
       for (auto& c : h->cgraphs)
@@ -528,28 +545,7 @@ void launch_compact_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cud
       h->cgraphs.clear();
     }
     ChunkGraph c;
-    if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
-    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    pdqp::t_capturing = true;
-    pdqp::t_captured = 0;
-    w.act_grid_A = std::max(gA, 1);
-    w.act_grid_P = std::max(gP, 1);
-    pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap, 0, true);
-    w.act_grid_A = w.act_grid_P = 0;
-    pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
-    pdqp::t_capturing = false;
-    c.kernels = pdqp::t_captured;
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamEndCapture(h->cap, &graph));
-    const cudaError_t e = cudaGraphInstantiate(&c.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(e);
-    c.key = p;
-    c.key_detect = w.detect;
-    c.key_eps_inf = w.eps_inf;
-    c.valid = true;
-    c.gA = gA;
-    c.gP = gP;
+    capture_chunk(h, p, mixed, true, gA, gP, c);
     h->cgraphs.push_back(c);
     g = &h->cgraphs.back();
   }
