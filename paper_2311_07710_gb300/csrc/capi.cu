@@ -81,6 +81,10 @@ struct Fail {
 // of freed blocks (the rest goes back to the device at synchronisation points),
 // so handles of similar sizes reuse memory instead of paying cudaMalloc /
 // cudaFree, which synchronise the device.
+// The pool keeps a quarter of the device's memory (at least POOL_KEEP): a
+// family handle holds tens of GB (its members' copies of the shared matrix),
+// and mapping that much afresh for every handle, then unmapping it at its
+// destruction, took ~30 ms each way.
 constexpr uint64_t POOL_KEEP = 8ULL << 30;
 cudaMemPool_t lib_pool() {
   static std::mutex mu;
@@ -96,7 +100,9 @@ cudaMemPool_t lib_pool() {
   props.location.id = dev;
   cudaMemPool_t pool = nullptr;
   CK(cudaMemPoolCreate(&pool, &props));
-  uint64_t keep = POOL_KEEP;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  uint64_t keep = std::max<uint64_t>(POOL_KEEP, (uint64_t)total_b / 4);
   CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
   pools[dev] = pool;
   return pool;
@@ -1330,9 +1336,11 @@ void replicate_csr(pdqp_problem* h, DCsr& M, const DCsr& T, int count, int n_t, 
   M.col = dalloc<int>(h, nnz + 8);
   M.val = dalloc<double>(h, nnz + 8);
   M.sval = dalloc<double>(h, nnz + 8);
+  // k_rep_cols writes every index and value: only the padding past the end
+  // needs zeros (the row pointers are small and cleared whole: no rows, no launch)
   CK(cudaMemsetAsync(M.rp, 0, (rows + 1 + 8) * sizeof(int), s));
-  CK(cudaMemsetAsync(M.col, 0, (nnz + 8) * sizeof(int), s));
-  CK(cudaMemsetAsync(M.val, 0, (nnz + 8) * sizeof(double), s));
+  CK(cudaMemsetAsync(M.col + nnz, 0, 8 * sizeof(int), s));
+  CK(cudaMemsetAsync(M.val + nnz, 0, 8 * sizeof(double), s));
   CK(cudaMemsetAsync(M.sval, 0, (nnz + 8) * sizeof(double), s));
   if (T.rows > 0) k_rep_rowptr<<<rep_grid(rows + 1), 256, 0, s>>>(T.rp, T.rows, T.nnz, count, M.rp);
   if (T.nnz > 0)
