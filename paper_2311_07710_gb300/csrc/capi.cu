@@ -689,14 +689,21 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     }
     if (ft) pdqp::family_scaling(w, sw, s);
   }
-  pdqp::scale_apply(w, mixed, s);
+  // a fresh family solve scales the template and copies its values to the
+  // members; a resumed one scales its own (its factors come from the state)
+  const bool rep_vals = ft && !resuming;
+  if (rep_vals) {
+    if (mixed) alloc_mixed(ft);
+    pdqp::scale_apply(sw, mixed, s);
+  }
+  pdqp::scale_apply(w, mixed, s, rep_vals ? &sw : nullptr);
 
   // spectral norms of the scaled matrices (a resumed solve keeps its own)
   const bool run_lanczos = !resuming && !(o.norm_A > 0.0 && o.norm_Q > 0.0);
   pdqp_problem* const lh = ft && w.r == 0 ? ft : h;
   Work& lw = lh->w;
   if (run_lanczos) {
-    if (lh != h) {
+    if (lh != h && !rep_vals) {   // the template scaled above otherwise
       if (mixed) alloc_mixed(lh);
       pdqp::scale_apply(lw, mixed, s);
     }

@@ -1934,13 +1934,42 @@ void scale_pass(Work& w, int kind, int pass, cudaStream_t s) {
   else scale_pass_t<2>(w, d, dn, s);
 }
 
-void scale_apply(Work& w, bool mixed, cudaStream_t s) {
+// every member's copy of the template's nnz_t values (members strided over grid.y)
+template <typename T>
+__global__ void k_rep_scaled(const T* __restrict__ t, long long nnz_t, int count, T* __restrict__ out) {
+  for (int q = blockIdx.y; q < count; q += gridDim.y) {
+    T* o = out + (long long)q * nnz_t;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz_t;
+         e += (long long)gridDim.x * blockDim.x)
+      o[e] = t[e];
+  }
+}
+
+template <typename T>
+static void rep_scaled(const T* t, long long nnz_t, int count, T* out, int num_sms, cudaStream_t s) {
+  if (nnz_t <= 0 || count <= 0 || !t || !out) return;
+  const int gx = (int)std::min<long long>(cdiv(nnz_t, 256), std::max(1, 4 * num_sms / std::max(count, 1) + 1));
+  launch(k_rep_scaled<T>, dim3(gx, std::min(count, 65535)), 256, 0, s, t, nnz_t, count, out);
+}
+
+void scale_apply(Work& w, bool mixed, cudaStream_t s, const Work* tmpl) {
   const int N = w.n + w.m;
   launch(k_inverse, cdiv(N, 256), 256, 0, s, (const double*)w.dsc, w.idsc, N);
-  launch(k_scale_vals, w.P.nblk, BNT, 0, s, w.P.borig(), (const double*)w.dsc, 0, 0, w.P.sval,
-         mixed ? w.P.sval_f : (float*)nullptr);
-  launch(k_scale_vals, w.A.nblk, BNT, 0, s, w.A.borig(), (const double*)w.dsc, w.n, 0, w.A.sval,
-         mixed ? w.A.sval_f : (float*)nullptr);
+  if (tmpl) {
+    // a family handle: every member's scaled values are the template's (the
+    // same factors and values, the same formula), copied instead of scaled
+    rep_scaled<double>(tmpl->P.sval, tmpl->P.nnz, w.count, w.P.sval, w.num_sms, s);
+    rep_scaled<double>(tmpl->A.sval, tmpl->A.nnz, w.count, w.A.sval, w.num_sms, s);
+    if (mixed) {
+      rep_scaled<float>(tmpl->P.sval_f, tmpl->P.nnz, w.count, w.P.sval_f, w.num_sms, s);
+      rep_scaled<float>(tmpl->A.sval_f, tmpl->A.nnz, w.count, w.A.sval_f, w.num_sms, s);
+    }
+  } else {
+    launch(k_scale_vals, w.P.nblk, BNT, 0, s, w.P.borig(), (const double*)w.dsc, 0, 0, w.P.sval,
+           mixed ? w.P.sval_f : (float*)nullptr);
+    launch(k_scale_vals, w.A.nblk, BNT, 0, s, w.A.borig(), (const double*)w.dsc, w.n, 0, w.A.sval,
+           mixed ? w.A.sval_f : (float*)nullptr);
+  }
   const int NN = w.n > w.m ? w.n : w.m;
   if (w.r > 0)
     launch(k_lr_scale, std::min(cdiv((long long)w.n * w.r, 256), 8 * w.num_sms), 256, 0, s, (const float*)w.F,

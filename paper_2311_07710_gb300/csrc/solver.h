@@ -217,7 +217,9 @@ inline void count_launch() {
 // from w.dsc (even pass) or w.nu (odd), writes them to the other buffer
 void scale_pass(Work& w, int kind, int pass, cudaStream_t s);
 void scale_reset(Work& w, cudaStream_t s);
-void scale_apply(Work& w, bool mixed, cudaStream_t s);
+// tmpl: a family handle's template, already scaled with the same factors:
+// its scaled values are copied to every member
+void scale_apply(Work& w, bool mixed, cudaStream_t s, const Work* tmpl = nullptr);
 void lanczos_init(Work& w, bool mixed, cudaStream_t s);
 void lanczos_step(Work& w, int t, const SolveParams& p, bool mixed, cudaStream_t s);
 void norms_finish(Work& w, double normA_opt, double normQ_opt, cudaStream_t s);
