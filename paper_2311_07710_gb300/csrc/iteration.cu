@@ -235,6 +235,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<V, NT, LR>::value) k_primal(Prim
   __shared__ int srp[BROWS + 1];
   const int bk = a.act ? a.act[blockIdx.x] : (int)blockIdx.x;
   if (bk < 0) return;
+  // (the dual half-step measured no gain from it: 202.6 -> 203.9 ms of a control-QP
+  // batch solve, against 225.4 -> 219.9 here)
+  prefetch_ahead(a.P, a.act, (int)blockIdx.x, (int)gridDim.x);
   primal_block<V, NT, LR, GATHER_LDG>(a, bk, j, prod, srp);
 }
 

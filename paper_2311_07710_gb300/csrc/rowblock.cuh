@@ -145,6 +145,33 @@ __device__ __forceinline__ void stage_products(const BCsr<V>& M, const X* __rest
   }
 }
 
+// The index and value quads of row block b towards L2 (a bulk prefetch, a
+// hint; blocks of one long row are skipped): one thread.  The range starts on a
+// quad and spans whole quads, inside the arrays' 8 entries of padding.
+template <typename V>
+__device__ __forceinline__ void prefetch_rowblock(const BCsr<V>& M, int b) {
+  const int e0 = M.rp[M.blk[b]], e1 = M.rp[M.blk[b + 1]];
+  if (e1 <= e0 || e1 - e0 > BNNZ) return;
+  const int a0 = e0 & ~3, nq = (e1 - a0 + 3) >> 2;
+  const unsigned long long gc = (unsigned long long)__cvta_generic_to_global(M.col + a0);
+  const unsigned long long gv = (unsigned long long)__cvta_generic_to_global(M.val + a0);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gc), "r"(nq * 16) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gv), "r"(nq * 4 * (int)sizeof(V)) : "memory");
+}
+
+// Matrices of small instances (M.pf): thread 0 of the CUDA block at position q
+// of a launch also prefetches the row block that the CUDA block one wave later
+// (q + PF_AHEAD: 8 resident blocks on each of 152 SMs) will stage, so that its
+// first phase, too, finds its quads in L2.
+constexpr int PF_AHEAD = 1216;
+template <typename V>
+__device__ __forceinline__ void prefetch_ahead(const BCsr<V>& M, const int* act, int q, int grid) {
+  const int q2 = q + PF_AHEAD;
+  if (!M.pf || threadIdx.x != 0 || q2 >= grid) return;
+  const int b2 = act ? act[q2] : q2;
+  if (b2 >= 0) prefetch_rowblock(M, b2);
+}
+
 // Occupancy target of the row-block kernels (blocks per SM).  They wait on
 // dependent gathers, so more resident warps hide more latency: with the
 // two-phase staging above, 256 threads of float data fit 32 registers without
