@@ -702,11 +702,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   const bool run_lanczos = !resuming && !(o.norm_A > 0.0 && o.norm_Q > 0.0);
   pdqp_problem* const lh = ft && w.r == 0 ? ft : h;
   Work& lw = lh->w;
-  if (run_lanczos) {
-    if (lh != h && !rep_vals) {   // the template scaled above otherwise
-      if (mixed) alloc_mixed(lh);
-      pdqp::scale_apply(lw, mixed, s);
-    }
+  if (run_lanczos) {   // (on the template: a fresh solve, so it was scaled above)
     pdqp::lanczos_init(lw, mixed, s);
     lw.lz_compact = 0;
     for (int t = 0; t < o.norm_iters; ++t) {
