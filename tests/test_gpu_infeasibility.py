@@ -4,7 +4,9 @@ same status at the same iteration and the same certificate to 1e-10; in mixed
 precision the status, with the certificate checked against its defining
 inequalities (support function by brute force); feasible solves unchanged;
 a batch mixing feasible and infeasible instances ends each one as its
-standalone solve does, bit for bit."""
+standalone solve does, bit for bit; so does a family handle (the certificate
+passes on its replicated matrix, whose scaled values are copied from its
+one-member template) against a batch of its members."""
 import numpy as np
 import pytest
 
@@ -91,6 +93,32 @@ def test_batch_ends_each_instance_as_alone(pdqp, precision):
         oy += inst.m
     assert [i.status for i in infos] == [pdqp.PDQP_OK, pdqp.PDQP_PRIMAL_INFEASIBLE, pdqp.PDQP_DUAL_INFEASIBLE,
                                         pdqp.PDQP_OK, pdqp.PDQP_PRIMAL_INFEASIBLE, pdqp.PDQP_OK]
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_family_handle_with_certificates_reproduces_batch(pdqp, precision):
+    fam = qpgen.family_qp(n=300, m=150)
+    C, B = fam.params(0, 5)
+    B[2, 0] = 1e4              # an equality row that no point of the box [-10, 10] meets
+    insts = [qpgen.QPInstance("member", fam.base.n, fam.base.m, fam.base.m_eq, fam.base.Q, fam.base.A, C[k], B[k],
+                              fam.base.l, fam.base.u) for k in range(5)]
+    N, M = 5 * fam.base.n, 5 * fam.base.m
+    o = pdqp.pdqp_default_options(precision=precision, detect_infeasibility=1, max_iter=5000)
+    out = []
+    for make in (lambda: pdqp.batch_from_instances(insts), lambda: pdqp.family_from_base(fam.base, C, B)):
+        h = make()
+        try:
+            x, y = np.zeros(N), np.zeros(M)
+            st, _ = pdqp.pdqp_solve(h, o, x_out=x, y_out=y)
+            out.append((st, [(i.status, i.iterations) for i in pdqp.pdqp_batch_info(h)], x, y))
+        finally:
+            pdqp.pdqp_destroy(h)
+    assert out[0][0] == out[1][0] == pdqp.PDQP_PRIMAL_INFEASIBLE
+    assert [s for s, _ in out[1][1]] == [pdqp.PDQP_OK, pdqp.PDQP_OK, pdqp.PDQP_PRIMAL_INFEASIBLE, pdqp.PDQP_OK,
+                                         pdqp.PDQP_OK]
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_array_equal(out[0][3], out[1][3])
 
 
 def test_graph_replay_matches_direct_launches(pdqp):
