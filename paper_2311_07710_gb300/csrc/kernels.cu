@@ -1271,22 +1271,33 @@ __device__ __forceinline__ void gershgorin_warp(const double* __restrict__ al, c
 
 // 32-point multisection of a bracket [lo, hi) of lambda_max in one warp, down
 // to 4e-15 relative; returns its midpoint
-__device__ double refine_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be2, int k,
-                                      double lo, double hi) {
+// the multisection's rounds: at most LZ_ROUNDS per bracket, and none once it
+// is 4e-15 relative
+constexpr int LZ_ROUNDS = 16;
+__device__ __forceinline__ bool lz_bracket_open(double lo, double hi, int rounds) {
+  return rounds < LZ_ROUNDS && hi - lo > 4e-15 * fabs(hi);
+}
+
+// one round of the 32-point multisection of [lo, hi) (in every lane of the warp)
+__device__ __forceinline__ void refine_round_warp(const double* __restrict__ al, const double* __restrict__ be2,
+                                                  int k, double& lo, double& hi) {
   const int lane = threadIdx.x & 31;
-  for (int round = 0; round < 16 && hi - lo > 4e-15 * fabs(hi); ++round) {
-    const double step = (hi - lo) * (1.0 / 33.0);
-    const double x = lo + step * (double)(lane + 1);
-    const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be2, k, x) < k);   // lambda_max >= x
-    if (ge == 0u) {
-      hi = lo + step;
-    } else {
-      const int t = 31 - __clz(ge);
-      const double nlo = lo + step * (double)(t + 1);
-      hi = t == 31 ? hi : lo + step * (double)(t + 2);
-      lo = nlo;
-    }
+  const double step = (hi - lo) * (1.0 / 33.0);
+  const double x = lo + step * (double)(lane + 1);
+  const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(al, be2, k, x) < k);   // lambda_max >= x
+  if (ge == 0u) {
+    hi = lo + step;
+  } else {
+    const int t = 31 - __clz(ge);
+    const double nlo = lo + step * (double)(t + 1);
+    hi = t == 31 ? hi : lo + step * (double)(t + 2);
+    lo = nlo;
   }
+}
+
+__device__ double refine_max_eig_warp(const double* __restrict__ al, const double* __restrict__ be2, int k,
+                                      double lo, double hi, int rounds = 0) {
+  for (; lz_bracket_open(lo, hi, rounds); ++rounds) refine_round_warp(al, be2, k, lo, hi);
   return 0.5 * (lo + hi);
 }
 
@@ -1404,35 +1415,79 @@ __global__ void __launch_bounds__(NT) k_lz_beta(LzArgs a, double tol, int max_st
       s_precise[o] = !go_on;
     }
   }
+  // Where the brackets leave the stop test open: refine theta_k's bracket and
+  // theta_{k-1}'s (when it is not exact), one round each at a time, until the
+  // brackets decide the test for certain (every value in them gives the same
+  // outcome) or both are at full precision (then their midpoints decide, as
+  // the precise values do).  Most steps near convergence go on, and learn it
+  // in a round or two; a stop needs theta_k in full and refines it the rest
+  // of the way, through the same rounds as a single refinement would take.
+  __shared__ double s_plo[2], s_phi[2];
+  __shared__ int s_rk[2], s_rp[2], s_dec[2];       // rounds done; decision: 0 open, 1 go on, 2 stop
+  __syncthreads();                                 // s_lo, s_hi, s_precise written above
+  if (threadIdx.x < 2) {
+    const int q = threadIdx.x;
+    s_plo[q] = st.pi_lam_prev[q];
+    s_phi[q] = st.pi_hi_prev[q];
+    s_rk[q] = 0;
+    s_rp[q] = 0;
+    s_dec[q] = (!done_in[q] && s_precise[q]) ? 0 : 1;
+  }
   __syncthreads();
-  if (ritz && !done_in[o] && s_precise[o]) {
-    if (!second)
-      s_theta[o][0] = refine_max_eig_warp(s_al(o), s_be2(o), k, s_lo[o], s_hi[o]);
-    else if (plo != phi)
-      s_theta[o][1] = refine_max_eig_warp(s_al(o), s_be2(o), k - 1, plo, phi);
-    else if (lane == 0)
-      s_theta[o][1] = plo;
+  for (int pass = 0; pass <= 2 * LZ_ROUNDS + 1; ++pass) {    // every thread takes the same passes
+    if (ritz && !second && lane == 0 && s_dec[o] == 0) {
+      const double lk = s_lo[o], hk = s_hi[o], lp = s_plo[o], hp = s_phi[o], b = beta[o];
+      const bool open_k = lz_bracket_open(lk, hk, s_rk[o]);
+      const bool open_p = lp != hp && lz_bracket_open(lp, hp, s_rp[o]);
+      int dec = 0;
+      if (k >= max_steps) {
+        dec = 2;
+      } else if (!open_k && !open_p) {                        // full precision: the midpoints decide
+        const double th = 0.5 * (lk + hk), tp = lp == hp ? lp : 0.5 * (lp + hp);
+        dec = (fabs(th - tp) <= tol * fabs(th) || b <= 1e-12 * fabs(th)) ? 2 : 1;
+      } else {   // certain outcomes: the tests hold for every value in the brackets
+        const double dmax = fmax(hk - lp, hp - lk), dmin = fmax(fmax(lk - hp, lp - hk), 0.0);
+        const double amax = fmax(fabs(lk), fabs(hk));                      // largest |theta_k|
+        const double amin = (lk <= 0.0 && hk >= 0.0) ? 0.0 : fmin(fabs(lk), fabs(hk));   // least
+        if (dmax <= tol * amin || b <= 1e-12 * amin) dec = 2;
+        else if (dmin > tol * amax && b > 1e-12 * amax) dec = 1;
+      }
+      s_dec[o] = dec;
+    }
+    __syncthreads();
+    if (s_dec[0] != 0 && s_dec[1] != 0) break;               // uniform: shared values after the barrier
+    if (ritz && s_dec[o] == 0) {                              // warp-uniform
+      if (!second && lz_bracket_open(s_lo[o], s_hi[o], s_rk[o])) {
+        double lo = s_lo[o], hi = s_hi[o];
+        refine_round_warp(s_al(o), s_be2(o), k, lo, hi);
+        __syncwarp();
+        if (lane == 0) { s_lo[o] = lo; s_hi[o] = hi; ++s_rk[o]; }
+      } else if (second && s_plo[o] != s_phi[o] && lz_bracket_open(s_plo[o], s_phi[o], s_rp[o])) {
+        double lo = s_plo[o], hi = s_phi[o];
+        refine_round_warp(s_al(o), s_be2(o), k - 1, lo, hi);
+        __syncwarp();
+        if (lane == 0) { s_plo[o] = lo; s_phi[o] = hi; ++s_rp[o]; }
+      }
+    }
+    __syncthreads();
+  }
+  // a stop needs theta_k in full (the rest of its refinement)
+  if (ritz && !second && !done_in[o] && s_precise[o] && s_dec[o] == 2) {
+    const double th = refine_max_eig_warp(s_al(o), s_be2(o), k, s_lo[o], s_hi[o], s_rk[o]);
+    if (lane == 0) s_theta[o][0] = th;
   }
   __syncthreads();
   if (ritz && !done_in[o] && !second && lane == 0) {
     const double b = beta[o];
-    if (!s_precise[o]) {                          // continues: keep the bracket
+    if (!s_precise[o] || s_dec[o] == 1) {        // goes on: keep the (refined) bracket
       st.pi_lam[o] = 0.5 * (s_lo[o] + s_hi[o]);
       st.pi_lam_prev[o] = s_lo[o];
       st.pi_hi_prev[o] = s_hi[o];
       lz_be(a, i, o)[k - 1] = b;
       st.pi_inv_norm[o] = 1.0 / b;
-    } else {
-      const double theta = s_theta[o][0], theta_prev = s_theta[o][1];
-      st.pi_lam[o] = theta;
-      if (fabs(theta - theta_prev) <= tol * fabs(theta) || b <= 1e-12 * fabs(theta) || k >= max_steps) {
-        st.pi_done[o] = 1;
-      } else {
-        lz_be(a, i, o)[k - 1] = b;
-        st.pi_lam_prev[o] = theta;
-        st.pi_hi_prev[o] = theta;
-        st.pi_inv_norm[o] = 1.0 / b;
-      }
+    } else {                                      // stops with theta_k in full
+      st.pi_lam[o] = s_theta[o][0];
+      st.pi_done[o] = 1;
     }
   }
   __syncthreads();
