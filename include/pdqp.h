@@ -145,6 +145,22 @@ typedef struct {
    * without it (iteration limit or numerical error). */
   int32_t detect_infeasibility;
   double eps_infeasible;     /* 1e-8 */
+  /* 1: maintained products (Section 2: the updates of Algorithm 1 are
+   * linear).  The iteration carries A x and A x_bar of the primal iterate and
+   * Q x_bar, A'y and A'y_bar along with the iterates: the dual half-step
+   * gathers x^k and forms A x_tilde^k = A x^k + theta_k (A x^k - A x^{k-1}),
+   * the primal half-step gathers x^k and y^{k+1} and forms
+   * Q x_md^k = (1 - 1/beta_k) Q x_bar^k + Q x^k / beta_k, and a check needs one
+   * gather of x for A x and one for Q x (the next iteration starts from those
+   * two products) instead of the products of both iterates with A, Q and A'.
+   * The iterates equal the default's in exact arithmetic; their rounding
+   * differs.  Needs precision PDQP_PREC_FP64, spmv_threads 0 or 256 (the
+   * 256-thread row-block kernels run), no low-rank term and no row longer
+   * than a row block, and no state loaded by pdqp_set_state: else the solve
+   * returns PDQP_ERR_INVALID.  A family handle runs the row-block kernels.
+   * pdqp_get_state after such a solve returns PDQP_ERR_INVALID (the state
+   * holds no x_md, x_tilde).  Not in the paper; default 0. */
+  int32_t maintained_products;
 } pdqp_options;
 
 typedef struct {
@@ -302,8 +318,9 @@ pdqp_status pdqp_get_iterates(pdqp_handle h, double *x, double *y, double *xbar,
  * buf (HOST memory, caller-owned) receives an opaque blob of this library
  * version; with buf = NULL only *bytes is set to the size needed.  On entry
  * *bytes is the capacity of buf, on return the size written.  Needs a solve
- * on the handle first (else PDQP_ERR_INVALID); synchronises `stream`.  The
- * blob of a batch handle holds every instance. */
+ * on the handle first, one without options.maintained_products (else
+ * PDQP_ERR_INVALID); synchronises `stream`.  The blob of a batch handle holds
+ * every instance. */
 pdqp_status pdqp_get_state(pdqp_handle h, void *buf, size_t *bytes, void *stream);
 
 /* Load a state from pdqp_get_state into a handle of the same problem (the

@@ -22,6 +22,7 @@ struct ChunkGraph {
   bool valid = false;
   SolveParams key{};
   int key_detect = 0;          // the certificate tests are part of the captured check
+  int key_mp = 0;              // maintained products (their own iteration and check kernels)
   double key_eps_inf = 0.0;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;       // kernel nodes in the graph (counted per replay)
@@ -49,6 +50,7 @@ struct pdqp_problem {
   SolveParams end_p{};
   int end_pos = 0;
   long long end_k_total = 0;
+  bool end_mp = false;         // the last solve maintained its products (no resumable state)
   // A state loaded by pdqp_set_state: the next solve continues from it.
   bool resume = false;
   SolveParams resume_p{};
@@ -364,6 +366,22 @@ void alloc_il(pdqp_problem* h, bool mixed) {
     if (!w.kks[k]) w.kks[k] = dalloc<double>(h, slen[k] * cnt);
 }
 
+// the maintained products' vectors (first solve with options.maintained_products)
+void alloc_mp(pdqp_problem* h) {
+  Work& w = h->w;
+  if (w.mp_ax) return;
+  const size_t n = std::max(w.n, 1), m = std::max(w.m, 1);
+  w.mp_ax = dalloc<double>(h, m);
+  w.mp_axb = dalloc<double>(h, m);
+  w.mp_qxb = dalloc<double>(h, n);
+  w.mp_aty = dalloc<double>(h, n);
+  w.mp_atyb = dalloc<double>(h, n);
+  for (int k = 0; k < 2; ++k) {
+    w.mp_sA[k] = dalloc<double>(h, m);
+    w.mp_sQ[k] = dalloc<double>(h, n);
+  }
+}
+
 SolveParams make_params(const pdqp_options& o) {
   SolveParams p{};
   p.step_rule = o.step_rule;
@@ -403,6 +421,11 @@ void validate_options(const pdqp_options& o) {
   if (o.detect_infeasibility != 0 && o.detect_infeasibility != 1) bad("options.detect_infeasibility must be 0 or 1");
   if (o.detect_infeasibility && !(o.eps_infeasible > 0.0 && o.eps_infeasible < 1.0))
     bad("options.eps_infeasible must be in (0, 1)");
+  if (o.maintained_products != 0 && o.maintained_products != 1) bad("options.maintained_products must be 0 or 1");
+  if (o.maintained_products && o.precision != PDQP_PREC_FP64)
+    bad("options.maintained_products needs precision PDQP_PREC_FP64 (the check's products must be float64)");
+  if (o.maintained_products && o.spmv_threads != 0 && o.spmv_threads != 256)
+    bad("options.maintained_products runs the 256-thread row-block kernels: spmv_threads must be 0 or 256");
 }
 
 double now_s() {
@@ -457,7 +480,7 @@ cudaGraphExec_t capture_iterations(pdqp_problem* h, int len, bool mixed, int nt,
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   pdqp::t_capturing = true;    // captured, not launched
   pdqp::t_captured = 0;
-  pdqp::iterate_chunk(w, len, mixed, nt, h->cap, j0);
+  pdqp::iterate(w, len, mixed, nt, h->cap, j0);
   pdqp::t_capturing = false;
   *kernels = pdqp::t_captured;
   cudaGraph_t graph = nullptr;
@@ -481,7 +504,7 @@ void capture_chunk(pdqp_problem* h, const SolveParams& p, bool mixed, bool compa
   pdqp::t_captured = 0;
   w.act_grid_A = compact ? std::max(gA, 1) : 0;
   w.act_grid_P = compact ? std::max(gP, 1) : 0;
-  pdqp::iterate_chunk(w, p.check_period, mixed, p.spmv_threads, h->cap, 0, compact);
+  pdqp::iterate(w, p.check_period, mixed, p.spmv_threads, h->cap, 0, compact);
   w.act_grid_A = w.act_grid_P = 0;
   pdqp::check(w, p, 1, p.check_period, mixed, h->cap);
   pdqp::t_capturing = false;
@@ -494,6 +517,7 @@ void capture_chunk(pdqp_problem* h, const SolveParams& p, bool mixed, bool compa
   c.key = p;
   c.key_detect = w.detect;
   c.key_eps_inf = w.eps_inf;
+  c.key_mp = w.mp;
   c.valid = true;
   c.gA = gA;
   c.gP = gP;
@@ -503,7 +527,7 @@ void capture_chunk(pdqp_problem* h, const SolveParams& p, bool mixed, bool compa
 // it was captured with
 bool graph_matches(const ChunkGraph& c, const Work& w, const SolveParams& p) {
   return c.valid && std::memcmp(&c.key, &p, sizeof(SolveParams)) == 0 && c.key_detect == w.detect &&
-         c.key_eps_inf == w.eps_inf;
+         c.key_eps_inf == w.eps_inf && c.key_mp == w.mp;
 }
 
 void launch_chunk_graph(pdqp_problem* h, const SolveParams& p, bool mixed, cudaStream_t s) {
@@ -621,7 +645,14 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   const bool il_ok = w.fam_il && w.r == 0;
   if (o.spmv_threads == 3 && !il_ok)
     throw Fail{PDQP_ERR_INVALID, "options.spmv_threads = 3 needs a family handle without long rows or low-rank term"};
-  const bool use_il = il_ok && (o.spmv_threads == 0 || o.spmv_threads == 3);
+  // maintained products: float64 row-block kernels over the whole handle
+  const bool mp = o.maintained_products != 0;
+  if (mp && w.r > 0) throw Fail{PDQP_ERR_INVALID, "options.maintained_products: the problem has a low-rank term"};
+  if (mp && (w.A.nlseg > 0 || w.P.nlseg > 0))
+    throw Fail{PDQP_ERR_INVALID, "options.maintained_products: a row of A or P holds more nonzeros than a row block"};
+  if (mp && h->resume)
+    throw Fail{PDQP_ERR_INVALID, "options.maintained_products: a solve resumed from pdqp_set_state is not supported"};
+  const bool use_il = il_ok && !mp && (o.spmv_threads == 0 || o.spmv_threads == 3);
   if (mixed) alloc_mixed(h);
   if (use_il) alloc_il(h, mixed);
   w.il_active = use_il;
@@ -634,6 +665,12 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   if (w.detect) alloc_infeas(h, s);
   SolveParams p = make_params(o);
   if (use_il) p.spmv_threads = 3;
+  w.mp = mp ? 1 : 0;
+  w.mp_accelerate = p.accelerate;
+  if (mp) {
+    alloc_mp(h);
+    p.spmv_threads = 256;
+  }
 
   // a state loaded by pdqp_set_state: the solve continues from it, so the
   // parameters that shape the trajectory must be the saved solve's
@@ -738,7 +775,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     pos = h->resume_pos;
     if (pos > 0) {
       const int len = (int)std::min<long long>(o.check_period - pos, o.max_iter - k_total);
-      pdqp::iterate_chunk(w, len, mixed, p.spmv_threads, s, pos);
+      pdqp::iterate(w, len, mixed, p.spmv_threads, s, pos);
       pdqp::check(w, p, 1, len, mixed, s);
       k_total += len;
       pos = (pos + len) % o.check_period;
@@ -764,7 +801,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
   static const int kCand[4] = {256, 512, 1, 2};
   const int ncand = cluster_ok ? 4 : 3;
   constexpr int TUNE = 4, ROUNDS = 2;
-  const bool autotune = o.spmv_threads == 0 && !use_il;
+  const bool autotune = o.spmv_threads == 0 && !use_il && !mp;
   int& tuned = h->tuned_nt[mixed ? 1 : 0];
   if (autotune && !tuned) tuned = tuned_lookup(w, mixed);   // a handle of the same shape tuned before
   if (autotune && tuned) p.spmv_threads = tuned;
@@ -779,7 +816,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       float best_ms[4] = {0.f, 0.f, 0.f, 0.f};
       int j = 0;
       const bool replay = !w.prof.on && !o.no_graphs;
-      if (replay) pdqp::iterate_chunk(w, 0, mixed, 1, s, 0);   // one-time setup of the pipelined variant
+      if (replay) pdqp::iterate(w, 0, mixed, 1, s, 0);   // one-time setup of the pipelined variant
       for (int r = 0; r < ROUNDS; ++r) {
         cudaGraphExec_t ex[4] = {nullptr, nullptr, nullptr, nullptr};
         long long kern[4] = {0, 0, 0, 0};
@@ -791,7 +828,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
             CK(cudaGraphLaunch(ex[c], s));
             pdqp::g_launches += kern[c];
           } else {
-            pdqp::iterate_chunk(w, TUNE, mixed, kCand[c], s, j);
+            pdqp::iterate(w, TUNE, mixed, kCand[c], s, j);
           }
           j += TUNE;
           CK(cudaEventRecord(h->tune_ev[c + 1], s));
@@ -811,13 +848,13 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
       tuned = kCand[bc];
       tuned_store(w, mixed, tuned);
       p.spmv_threads = tuned;
-      pdqp::iterate_chunk(w, (int)len - j, mixed, p.spmv_threads, s, j);
+      pdqp::iterate(w, (int)len - j, mixed, p.spmv_threads, s, j);
       pdqp::check(w, p, 1, len, mixed, s);
     } else if (len == o.check_period && !o.no_graphs && !w.prof.on) {
       if (compact_now(w, p)) launch_compact_graph(h, p, mixed, s);
       else launch_chunk_graph(h, p, mixed, s);
     } else {
-      pdqp::iterate_chunk(w, (int)len, mixed, p.spmv_threads, s, 0, compact_now(w, p));
+      pdqp::iterate(w, (int)len, mixed, p.spmv_threads, s, 0, compact_now(w, p));
       pdqp::check(w, p, 1, len, mixed, s);
     }
     CK(cudaGetLastError());
@@ -865,6 +902,7 @@ pdqp_status solve_impl(pdqp_problem* h, const pdqp_options& o, const double* x0,
     for (int i = 1; i < w.count; ++i) info->iterations = std::max(info->iterations, h->infos[i].iterations);
   }
   h->solved = true;
+  h->end_mp = mp;
   h->end_p = p;
   h->end_pos = pos;
   h->end_k_total = k_total;
@@ -2108,6 +2146,7 @@ void pdqp_default_options(pdqp_options* o) {
   o->no_graphs = 0;
   o->detect_infeasibility = 0;
   o->eps_infeasible = 1e-8;
+  o->maintained_products = 0;
 }
 
 const char* pdqp_status_string(int32_t st) {
@@ -2288,6 +2327,8 @@ pdqp_status pdqp_get_state(pdqp_handle h, void* buf, size_t* bytes, void* stream
   try {
     h->err.clear();
     if (!h->solved) throw Fail{PDQP_ERR_INVALID, "pdqp_get_state: no solve has run on this handle"};
+    if (h->end_mp)
+      throw Fail{PDQP_ERR_INVALID, "pdqp_get_state: the last solve maintained its products (no resumable state)"};
     Work& w = h->w;
     const bool mixed = h->end_p.mixed != 0;
     const int C = h->end_p.check_period;

@@ -2405,7 +2405,8 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
   if (w.prof.on) w.prof.begin(2, s);
   const int NN = w.n > w.m ? w.n : w.m;
   const int grid_v = cdiv(NN, 256) < 4 * w.num_sms ? cdiv(NN, 256) : 4 * w.num_sms;
-  const bool pairs = !w.il_active && w.kkt_xx;
+  const bool mp = w.mp && !mixed && !w.il_active;   // products maintained by the iteration
+  const bool pairs = !w.il_active && w.kkt_xx && !mp;
   if (mixed) {
     MixedArgs ma = mixed_args(w);
     if (pairs) { ma.xx = w.kkt_xx; ma.yy = w.kkt_yy; }
@@ -2428,8 +2429,16 @@ void check(Work& w, const SolveParams& p, int mode, long long chunk_len, bool mi
     lowrank_ft<double, double>(w, w.Fd, a.x[0], a.x[1], s);
     a.F = w.Fd; a.wlr = w.wlr; a.r = w.r;
   }
-  if (w.il_active) launch_kkt_il(w, a, s);   // a family handle on interleaved vectors (no low-rank term)
-  else launch_kkt<2>(w, a, s);
+  if (w.il_active) {
+    launch_kkt_il(w, a, s);   // a family handle on interleaved vectors (no low-rank term)
+  } else if (mp) {            // row sums from the maintained products and one gather of x each for A x, Q x
+    mp_check_products(w, mode, chunk_len, s);
+    if (w.m > 0) launch(k_kkt_m_sums, w.ngrp_A, BNT, 0, s, a, (const double*)w.mp_sA[0], (const double*)w.mp_sA[1]);
+    launch(k_kkt_n_sums, w.ngrp_P, BNT, 0, s, a, (const double*)w.mp_sQ[0], (const double*)w.mp_sQ[1],
+           (const double*)w.mp_aty, (const double*)w.mp_atyb);
+  } else {
+    launch_kkt<2>(w, a, s);
+  }
   {
     const dim3 grid(w.count, std::max(w.maxchunk_n, w.maxchunk_m));
     launch(k_kkt_chunks, grid, 32, 0, s, (const Inst*)w.inst, (const int*)w.grp_first_A, (const double*)w.part_m,

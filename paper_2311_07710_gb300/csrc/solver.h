@@ -197,6 +197,14 @@ struct Work {
   double *inf_zn = nullptr, *inf_zm = nullptr;       // zeros [n], [m]
   double *inf_lrec = nullptr, *inf_urec = nullptr;   // the box's recession cone: 0 / -inf / +inf [n]
   double *inf_part_m = nullptr, *inf_part_n = nullptr, *inf_cpart_m = nullptr, *inf_cpart_n = nullptr;
+  // maintained products (float64 solves with options.maintained_products):
+  // A~x^k, A~x_bar^k [m] of the last dual half-step; Q~x_bar^k and P's -A~'
+  // part of y^{k+1}, y_bar^{k+1} [n] of the last primal half-step; the
+  // check's A~x, A~x_bar [m] and Q~x, Q~x_bar [n] of its two iterates
+  int mp = 0;                                // this solve maintains them
+  int mp_accelerate = 0;                     // its options.accelerate
+  double *mp_ax = nullptr, *mp_axb = nullptr, *mp_qxb = nullptr, *mp_aty = nullptr, *mp_atyb = nullptr;
+  double *mp_sA[2] = {nullptr, nullptr}, *mp_sQ[2] = {nullptr, nullptr};
   Profiler prof;
 };
 
@@ -241,6 +249,14 @@ void init_iterates(Work& w, const double* x0, const double* y0, const SolveParam
 // the whole chunk in one cluster launch (only where chunk_cluster_ok), 3 the
 // member-interleaved family kernels (only where w.fam_il, buffers allocated).
 void iterate_chunk(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0, bool compact = false);
+// iterate_chunk, or with w.mp the maintained-products kernels (float64, 256
+// threads per row block; nt is not used; the chunk starts at j0 = 0 right
+// after a check, whose products of the iterate it starts from)
+void iterate(Work& w, int len, bool mixed, int nt, cudaStream_t s, int j0 = 0, bool compact = false);
+// with w.mp: the check's products A~x, A~x_bar, Q~x, Q~x_bar of (x, x_bar)
+// after chunk_len iterations (mode 1), or of the start point (mode 0, which
+// also forms the A~' products of y)
+void mp_check_products(Work& w, int mode, long long chunk_len, cudaStream_t s);
 // few row blocks, no long rows, no low-rank term, the vector copies fit in shared memory
 bool chunk_cluster_ok(const Work& w, bool mixed);
 void prepare_chunk_cluster();           // once, outside any stream capture

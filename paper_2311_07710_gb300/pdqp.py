@@ -36,6 +36,7 @@ class pdqp_options(ctypes.Structure):
         ("norm_A", ctypes.c_double), ("norm_Q", ctypes.c_double), ("norm_iters", ctypes.c_int32),
         ("norm_tol", ctypes.c_double), ("spmv_threads", ctypes.c_int32), ("no_graphs", ctypes.c_int32),
         ("detect_infeasibility", ctypes.c_int32), ("eps_infeasible", ctypes.c_double),
+        ("maintained_products", ctypes.c_int32),
     ]
 
 
