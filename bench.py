@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload: skip the sub-records of the MPC batch and the learned warm start")
     ap.add_argument("--epochs", type=int, default=20, help="family_ws: training epochs")
+    ap.add_argument("--maintained-products", action="store_true",
+                    help="the main leg with options.maintained_products (needs --precision fp64)")
     ap.add_argument("--n", type=int, default=1_000_000,
                     help="variables of the workload (m = n/2); smaller only for profiler captures")
     return ap.parse_args()
@@ -338,7 +340,8 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
-    opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=args.spmv_threads)
+    opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=args.spmv_threads,
+                                     maintained_products=1 if args.maintained_products else 0)
     if args.workload == "mpc_batch":
         insts = qpgen.mpc_batch(args.batch or 4096, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
     elif args.workload == "random_sparse_qp":
@@ -480,6 +483,8 @@ def run_ours(args, world, rank, local):
     avg_s = d["ms"] / d["launches"] / 1e3
     achieved_gbs = d["bytes"] / avg_s / 1e9
     kname = {"dual": "k_dual", "primal": "k_primal", "other": "k_chunk_cluster"}[dom]
+    if args.maintained_products:
+        kname += "_mp"
     nnz_rows = (nnz_A, M, 8) if dom == "dual" else (nnz_P, N, 15)
     flops = 2.0 * nnz_rows[0] + nnz_rows[2] * nnz_rows[1]
     if args.precision == "fp64" and dom != "other":
@@ -518,6 +523,7 @@ def run_ours(args, world, rank, local):
                        (f"mpc_batch: {per_step} control QPs, 12 states, 4 inputs, horizon 10..100, one batched handle"
                         if args.workload == "mpc_batch" else "random_sparse_qp n=1000 m=500"),
                        "precision": args.precision, "eps": 1e-6,
+                       "maintained_products": bool(args.maintained_products),
                        "l2": "inputs larger than L2 (matrices >= 200 MB), no flush",
                        "parallelism": f"replicas x{world}"},
             "iterations_per_solve": iters if per_step == 1 else
@@ -1135,6 +1141,8 @@ def run_algorithms(args, world, rank, local):
 
 def main():
     args = parse()
+    if args.maintained_products and args.precision != "fp64":
+        raise SystemExit("--maintained-products needs --precision fp64")
     world, rank, local = dist_setup(args)
     args.gpus = world if world > 1 else args.gpus
     if args.impl == "reference":
