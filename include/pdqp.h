@@ -181,13 +181,16 @@ typedef struct {
 /* Per-kernel device time of the solver's hot loop, measured with CUDA events
  * recorded on the solve's stream around every launch while profiling is on.
  * kind 0 = dual half-step, 1 = primal half-step, 2 = relKKT check + restart,
- * 3 = everything else (scaling, norms, start point, output). */
+ * 3 = the one-launch cluster chunk (spmv_threads 2: both half-steps of a
+ * chunk's iterations per launch).  Scaling, norms, start point and output are
+ * not timed. */
 typedef struct {
   int64_t launches[4];
   double ms[4];              /* summed device milliseconds */
-  double bytes[4];           /* algorithmic DRAM bytes of one launch (kinds 0, 1): the mean
-                                over the timed launches of the bytes of the instances that
-                                were running at each launch */
+  double bytes[4];           /* algorithmic DRAM bytes of one launch (kinds 0, 1, 3): the
+                                mean over the timed launches of the bytes of the instances
+                                that were running at each launch (kind 3: both half-steps
+                                of every iteration in the launch) */
 } pdqp_profile;
 
 /* Fill *opt with the defaults listed above. */

@@ -2524,6 +2524,7 @@ pdqp_status pdqp_profile_read(pdqp_handle h, pdqp_profile* out) {
                           (double)w.P.nnz * (sv + 4.0) + 4.0 * (n + 1) + sv * (10.0 * n + m)};
   for (int k = 0; k < 2; ++k)
     out->bytes[k] = w.prof.launches[k] > 0 ? w.prof.bytes[k] / (double)w.prof.launches[k] : full[k];
+  if (w.prof.launches[3] > 0) out->bytes[3] = w.prof.bytes[3] / (double)w.prof.launches[3];
   return PDQP_OK;
 }
 
