@@ -281,10 +281,100 @@ __device__ __forceinline__ void broadcast(cg::cluster_group& cl, int ctas, V* p,
   for (int q = 0; q < ctas; ++q) *cl.map_shared_rank(p, q) = v;
 }
 
+// Resident row blocks: where every CTA takes at most one row block of A and
+// one of P, each CTA copies its blocks' row offsets, column indices and
+// values to shared memory once per launch, so that a half-step's dependent
+// chain starts at the gathers from the shared-memory vector copies instead of
+// behind two or three global round trips (block start, row pointers, index and
+// value quads).  The products val[e] * v[col[e]] and the row sums in order are
+// those of dual_block / primal_block, so the iterates stay theirs.
+template <typename V>
+struct ResBlock {
+  int r0, nr, ne;
+  int* srp;          // [BROWS + 1]
+  int* col;          // [BNNZ]
+  V* val;            // [BNNZ]
+};
+template <typename V>
+__host__ __device__ inline size_t chunk_res_offset(int n, int m) {   // behind the vector copies, 16-byte aligned
+  return (chunk_head_bytes<V>() + (size_t)(3 * (size_t)n + 2 * (size_t)m) * sizeof(V) + 15) / 16 * 16;
+}
+template <typename V>
+constexpr size_t chunk_res_bytes() {   // both resident blocks, rounded to 16 bytes each
+  return 2 * (((size_t)BNNZ * sizeof(V) + (size_t)BNNZ * sizeof(int) + (BROWS + 1) * sizeof(int) + 15) / 16 * 16);
+}
+template <typename V>
+__device__ __forceinline__ ResBlock<V> res_view(unsigned char* base) {
+  ResBlock<V> rb;
+  rb.val = reinterpret_cast<V*>(base);
+  rb.col = reinterpret_cast<int*>(rb.val + BNNZ);
+  rb.srp = rb.col + BNNZ;
+  rb.r0 = rb.nr = rb.ne = 0;
+  return rb;
+}
+template <typename V>
+__device__ __forceinline__ void res_load(const BCsr<V>& M, int b, ResBlock<V>& rb) {
+  const int r0 = M.blk[b], r1 = M.blk[b + 1];
+  const int e0 = M.rp[r0];
+  rb.r0 = r0;
+  rb.nr = r1 - r0;
+  rb.ne = M.rp[r1] - e0;   // <= BNNZ: no long rows in the cluster chunk
+  for (int t = threadIdx.x; t <= rb.nr; t += CHUNK_NT) rb.srp[t] = M.rp[r0 + t] - e0;
+  for (int e = threadIdx.x; e < rb.ne; e += CHUNK_NT) {
+    rb.col[e] = M.col[e0 + e];
+    rb.val[e] = M.val[e0 + e];
+  }
+}
+
+static_assert(BROWS <= CHUNK_NT, "a resident block's rows take one thread each");
+
+// dual_block on a resident block (rows <= BROWS <= CHUNK_NT: one row per thread)
+template <typename V>
+__device__ __forceinline__ void dual_block_res(const DualB<V>& a, int bk, int j, V* prod, const ResBlock<V>& rb) {
+  const int tid = threadIdx.x;
+  const int inst = a.blk_inst[bk];
+  if (a.st[inst].status != ST_RUNNING) return;    // uniform over the block
+  V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
+  if (tid < rb.nr) {
+    const int r = rb.r0 + tid;
+    yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
+    if (a.ylo) lo = a.ylo[r];
+  }
+  const StepEntry& es = a.tab[inst * a.C + j];
+  for (int e = tid; e < rb.ne; e += CHUNK_NT) prod[e] = rb.val[e] * a.xt[rb.col[e]];
+  __syncthreads();
+  if (tid < rb.nr) {
+    V s = V(0);
+    for (int e = rb.srp[tid]; e < rb.srp[tid + 1]; ++e) s += prod[e];
+    dual_row(a, es, rb.r0 + tid, s, yo, bi, yb, lo);
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void primal_block_res(const PrimalB<V>& a, int bk, int j, V* prod,
+                                                 const ResBlock<V>& rb) {
+  const int tid = threadIdx.x;
+  const int inst = a.blk_inst[bk];
+  if (a.st[inst].status != ST_RUNNING) return;
+  V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
+  if (tid < rb.nr) {
+    const int r = rb.r0 + tid;
+    xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
+  }
+  const StepEntry& es = a.tab[inst * a.C + j];
+  for (int e = tid; e < rb.ne; e += CHUNK_NT) prod[e] = rb.val[e] * a.zin[rb.col[e]];
+  __syncthreads();
+  if (tid < rb.nr) {
+    V s = V(0);
+    for (int e = rb.srp[tid]; e < rb.srp[tid + 1]; ++e) s += prod[e];
+    primal_row<V, false>(a, es, rb.r0 + tid, s, xo, xb, cr, lr, ur);
+  }
+}
+
 template <typename V>
 __global__ void __launch_bounds__(CHUNK_NT)
     k_chunk_cluster(DualB<V> da, PrimalB<V> pa, int nblkA, int nblkP, V* z0, V* z1, int n, int m, int j0,
-                    int len) {
+                    int len, int resident) {
   extern __shared__ __align__(16) unsigned char chunk_sm[];
   V* prod = reinterpret_cast<V*>(chunk_sm);
   int* srp = reinterpret_cast<int*>(prod + BNNZ);
@@ -297,6 +387,14 @@ __global__ void __launch_bounds__(CHUNK_NT)
   for (int i = tid; i < n + m; i += CHUNK_NT) {
     zs[0][i] = __ldcg(z0 + i);
     zs[1][i] = __ldcg(z1 + i);
+  }
+  // resident blocks (the host passes resident = 1 only where nblkA, nblkP <=
+  // ctas and their copies fit behind the vectors)
+  unsigned char* rbase = chunk_sm + chunk_res_offset<V>(n, m);
+  ResBlock<V> rA = res_view<V>(rbase), rP = res_view<V>(rbase + chunk_res_bytes<V>() / 2);
+  if (resident) {
+    if (cta < nblkA) res_load(da.A, cta, rA);
+    if (cta < nblkP) res_load(pa.P, cta, rP);
   }
   cluster_barrier();                              // every copy is whole before anyone writes into it
   DualB<V> dl = da;
@@ -311,7 +409,8 @@ __global__ void __launch_bounds__(CHUNK_NT)
     dl.ynew = zj + n;
     for (int bk = cta; bk < nblkA; bk += ctas) {
       __syncthreads();                            // the previous block's rows are done with prod
-      dual_block<V, CHUNK_NT, GATHER_PLAIN>(dl, bk, j, prod, srp);
+      if (resident) dual_block_res<V>(dl, bk, j, prod, rA);
+      else dual_block<V, CHUNK_NT, GATHER_PLAIN>(dl, bk, j, prod, srp);
       if (da.st[da.blk_inst[bk]].status == ST_RUNNING) {
         const int r0 = da.A.blk[bk], nr = da.A.blk[bk + 1] - r0;
         for (int t = tid; t < nr; t += CHUNK_NT) broadcast(cl, ctas, zsj + n + r0 + t, dl.ynew[r0 + t]);
@@ -322,7 +421,8 @@ __global__ void __launch_bounds__(CHUNK_NT)
     pl.zout = zn;
     for (int bk = cta; bk < nblkP; bk += ctas) {
       __syncthreads();
-      primal_block<V, CHUNK_NT, false, GATHER_PLAIN>(pl, bk, j, prod, srp);
+      if (resident) primal_block_res<V>(pl, bk, j, prod, rP);
+      else primal_block<V, CHUNK_NT, false, GATHER_PLAIN>(pl, bk, j, prod, srp);
       if (pa.st[pa.blk_inst[bk]].status == ST_RUNNING) {
         const int r0 = pa.P.blk[bk], nr = pa.P.blk[bk + 1] - r0;
         for (int t = tid; t < nr; t += CHUNK_NT) {
@@ -947,12 +1047,14 @@ static void run_chunk_cluster(Work& w, int j0, int len, BCsr<V> A, BCsr<V> P, V*
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(g_chunk_ctas);               // one cluster
   cfg.blockDim = dim3(CHUNK_NT);
-  cfg.dynamicSmemBytes = chunk_smem_bytes<V>(w.n, w.m);
+  const int nblkA = w.m > 0 ? w.A.nblk : 0;
+  const size_t res_end = chunk_res_offset<V>(w.n, w.m) + chunk_res_bytes<V>();
+  const int resident = nblkA <= g_chunk_ctas && w.P.nblk <= g_chunk_ctas && res_end <= (size_t)CHUNK_SMEM_MAX;
+  cfg.dynamicSmemBytes = resident ? res_end : chunk_smem_bytes<V>(w.n, w.m);
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_chunk_cluster<V>, da, pa, w.m > 0 ? w.A.nblk : 0, w.P.nblk, Z[0], Z[1], w.n, w.m, j0,
-                     len);
+  cudaLaunchKernelEx(&cfg, k_chunk_cluster<V>, da, pa, nblkA, w.P.nblk, Z[0], Z[1], w.n, w.m, j0, len, resident);
   count_launch();
   if (Pr.on) Pr.end(s);
 }
