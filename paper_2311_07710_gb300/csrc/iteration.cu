@@ -282,38 +282,48 @@ __device__ __forceinline__ void broadcast(cg::cluster_group& cl, int ctas, V* p,
 }
 
 // Resident row blocks: where every CTA takes at most one row block of A and
-// one of P, each CTA copies its blocks' row offsets, column indices and
-// values to shared memory once per launch, so that a half-step's dependent
-// chain starts at the gathers from the shared-memory vector copies instead of
-// behind two or three global round trips (block start, row pointers, index and
-// value quads).  The products val[e] * v[col[e]] and the row sums in order are
-// those of dual_block / primal_block, so the iterates stay theirs.
+// one of P, each CTA keeps its blocks in shared memory for the launch: the
+// row offsets, column indices and values, and the rows' own operands (of A:
+// b, y_bar, the inequality flag and the mixed-precision lower bound; of P: x,
+// x_bar, c, l, u), which only this CTA updates.  A half-step's dependent chain
+// then runs from the gathers out of the shared-memory vector copies to the
+// writes into every CTA's copies, straight from registers, with no global
+// round trip on it (the results still go to global memory for the checks).
+// The products val[e] * v[col[e]], the row sums in order and the row updates
+// are dual_block / primal_block's, so the iterates stay theirs.
+constexpr int RES_ROWS = 5;   // operand rows per resident block
 template <typename V>
 struct ResBlock {
   int r0, nr, ne;
-  int* srp;          // [BROWS + 1]
-  int* col;          // [BNNZ]
   V* val;            // [BNNZ]
+  V* row[RES_ROWS];  // [BROWS] each
+  int* col;          // [BNNZ]
+  int* srp;          // [BROWS + 1]
 };
 template <typename V>
 __host__ __device__ inline size_t chunk_res_offset(int n, int m) {   // behind the vector copies, 16-byte aligned
   return (chunk_head_bytes<V>() + (size_t)(3 * (size_t)n + 2 * (size_t)m) * sizeof(V) + 15) / 16 * 16;
 }
 template <typename V>
-constexpr size_t chunk_res_bytes() {   // both resident blocks, rounded to 16 bytes each
-  return 2 * (((size_t)BNNZ * sizeof(V) + (size_t)BNNZ * sizeof(int) + (BROWS + 1) * sizeof(int) + 15) / 16 * 16);
+constexpr size_t chunk_res_block_bytes() {   // one resident block, a multiple of 16 bytes
+  return ((size_t)(BNNZ + RES_ROWS * BROWS) * sizeof(V) + (size_t)BNNZ * sizeof(int) + (BROWS + 1) * sizeof(int) +
+          15) / 16 * 16;
 }
+template <typename V>
+constexpr size_t chunk_res_bytes() { return 2 * chunk_res_block_bytes<V>(); }
 template <typename V>
 __device__ __forceinline__ ResBlock<V> res_view(unsigned char* base) {
   ResBlock<V> rb;
   rb.val = reinterpret_cast<V*>(base);
-  rb.col = reinterpret_cast<int*>(rb.val + BNNZ);
+  for (int k = 0; k < RES_ROWS; ++k) rb.row[k] = rb.val + BNNZ + k * BROWS;
+  rb.col = reinterpret_cast<int*>(rb.val + BNNZ + RES_ROWS * BROWS);
   rb.srp = rb.col + BNNZ;
   rb.r0 = rb.nr = rb.ne = 0;
   return rb;
 }
 template <typename V>
-__device__ __forceinline__ void res_load(const BCsr<V>& M, int b, ResBlock<V>& rb) {
+__device__ __forceinline__ void res_load(const BCsr<V>& M, int b, ResBlock<V>& rb, const V* o0, const V* o1,
+                                         const V* o2, const V* o3, const V* o4) {
   const int r0 = M.blk[b], r1 = M.blk[b + 1];
   const int e0 = M.rp[r0];
   rb.r0 = r0;
@@ -324,50 +334,65 @@ __device__ __forceinline__ void res_load(const BCsr<V>& M, int b, ResBlock<V>& r
     rb.col[e] = M.col[e0 + e];
     rb.val[e] = M.val[e0 + e];
   }
+  const V* src[RES_ROWS] = {o0, o1, o2, o3, o4};
+  for (int t = threadIdx.x; t < rb.nr; t += CHUNK_NT)
+#pragma unroll
+    for (int k = 0; k < RES_ROWS; ++k) rb.row[k][t] = src[k] ? src[k][r0 + t] : V(0);
 }
 
 static_assert(BROWS <= CHUNK_NT, "a resident block's rows take one thread each");
 
-// dual_block on a resident block (rows <= BROWS <= CHUNK_NT: one row per thread)
+// dual_block on a resident block: rows[0] b, [1] y_bar, [2] 1 for an
+// inequality row, [3] the lower bound; y^k from the shared-memory copy yk, y+
+// into every CTA's copy at ycopy
 template <typename V>
-__device__ __forceinline__ void dual_block_res(const DualB<V>& a, int bk, int j, V* prod, const ResBlock<V>& rb) {
+__device__ __forceinline__ void dual_block_res(const DualB<V>& a, int bk, int j, V* prod, ResBlock<V>& rb,
+                                               cg::cluster_group& cl, int ctas, const V* yk, V* ycopy) {
   const int tid = threadIdx.x;
   const int inst = a.blk_inst[bk];
   if (a.st[inst].status != ST_RUNNING) return;    // uniform over the block
-  V yo = V(0), bi = V(0), yb = V(0), lo = V(0);
-  if (tid < rb.nr) {
-    const int r = rb.r0 + tid;
-    yo = a.yold[r]; bi = a.b[r]; yb = a.ybar[r];
-    if (a.ylo) lo = a.ylo[r];
-  }
   const StepEntry& es = a.tab[inst * a.C + j];
   for (int e = tid; e < rb.ne; e += CHUNK_NT) prod[e] = rb.val[e] * a.xt[rb.col[e]];
   __syncthreads();
   if (tid < rb.nr) {
     V s = V(0);
     for (int e = rb.srp[tid]; e < rb.srp[tid + 1]; ++e) s += prod[e];
-    dual_row(a, es, rb.r0 + tid, s, yo, bi, yb, lo);
+    const int r = rb.r0 + tid;
+    V yn, ybn;
+    dual_update<V>(es, s, yk[r], rb.row[0][tid], rb.row[1][tid], rb.row[3][tid], rb.row[2][tid] != V(0), yn, ybn);
+    rb.row[1][tid] = ybn;
+    a.ybar[r] = ybn;
+    a.ynew[r] = yn;
+    broadcast(cl, ctas, ycopy + r, yn);
   }
 }
 
+// primal_block on a resident block: rows[0] x, [1] x_bar, [2] c, [3] l, [4] u;
+// the next x_md into every CTA's copy at zcopy, the next x_tilde at xcopy
 template <typename V>
-__device__ __forceinline__ void primal_block_res(const PrimalB<V>& a, int bk, int j, V* prod,
-                                                 const ResBlock<V>& rb) {
+__device__ __forceinline__ void primal_block_res(const PrimalB<V>& a, int bk, int j, V* prod, ResBlock<V>& rb,
+                                                 cg::cluster_group& cl, int ctas, V* zcopy, V* xcopy) {
   const int tid = threadIdx.x;
   const int inst = a.blk_inst[bk];
   if (a.st[inst].status != ST_RUNNING) return;
-  V xo = V(0), xb = V(0), cr = V(0), lr = V(0), ur = V(0);
-  if (tid < rb.nr) {
-    const int r = rb.r0 + tid;
-    xo = a.x[r]; xb = a.xbar[r]; cr = a.c[r]; lr = a.l[r]; ur = a.u[r];
-  }
   const StepEntry& es = a.tab[inst * a.C + j];
   for (int e = tid; e < rb.ne; e += CHUNK_NT) prod[e] = rb.val[e] * a.zin[rb.col[e]];
   __syncthreads();
   if (tid < rb.nr) {
     V s = V(0);
     for (int e = rb.srp[tid]; e < rb.srp[tid + 1]; ++e) s += prod[e];
-    primal_row<V, false>(a, es, rb.r0 + tid, s, xo, xb, cr, lr, ur);
+    const int r = rb.r0 + tid;
+    const V g = r_add(s, rb.row[2][tid]);
+    V xn, xb, zo, xtn;
+    primal_update<V>(es, g, rb.row[0][tid], rb.row[1][tid], rb.row[3][tid], rb.row[4][tid], xn, xb, zo, xtn);
+    rb.row[0][tid] = xn;
+    rb.row[1][tid] = xb;
+    a.xbar[r] = xb;
+    a.zout[r] = zo;
+    a.xt[r] = xtn;
+    a.x[r] = xn;
+    broadcast(cl, ctas, zcopy + r, zo);
+    broadcast(cl, ctas, xcopy + r, xtn);
   }
 }
 
@@ -393,8 +418,12 @@ __global__ void __launch_bounds__(CHUNK_NT)
   unsigned char* rbase = chunk_sm + chunk_res_offset<V>(n, m);
   ResBlock<V> rA = res_view<V>(rbase), rP = res_view<V>(rbase + chunk_res_bytes<V>() / 2);
   if (resident) {
-    if (cta < nblkA) res_load(da.A, cta, rA);
-    if (cta < nblkP) res_load(pa.P, cta, rP);
+    // the inequality flags as values of V (1 or 0) in a scratch slot first
+    if (cta < nblkA) {
+      res_load(da.A, cta, rA, da.b, da.ybar, (const V*)nullptr, da.ylo, (const V*)nullptr);
+      for (int t = tid; t < rA.nr; t += CHUNK_NT) rA.row[2][t] = da.ineq[rA.r0 + t] ? V(1) : V(0);
+    }
+    if (cta < nblkP) res_load(pa.P, cta, rP, pa.x, pa.xbar, pa.c, pa.l, pa.u);
   }
   cluster_barrier();                              // every copy is whole before anyone writes into it
   DualB<V> dl = da;
@@ -409,8 +438,11 @@ __global__ void __launch_bounds__(CHUNK_NT)
     dl.ynew = zj + n;
     for (int bk = cta; bk < nblkA; bk += ctas) {
       __syncthreads();                            // the previous block's rows are done with prod
-      if (resident) dual_block_res<V>(dl, bk, j, prod, rA);
-      else dual_block<V, CHUNK_NT, GATHER_PLAIN>(dl, bk, j, prod, srp);
+      if (resident) {
+        dual_block_res<V>(dl, bk, j, prod, rA, cl, ctas, zsn + n, zsj + n);
+        continue;
+      }
+      dual_block<V, CHUNK_NT, GATHER_PLAIN>(dl, bk, j, prod, srp);
       if (da.st[da.blk_inst[bk]].status == ST_RUNNING) {
         const int r0 = da.A.blk[bk], nr = da.A.blk[bk + 1] - r0;
         for (int t = tid; t < nr; t += CHUNK_NT) broadcast(cl, ctas, zsj + n + r0 + t, dl.ynew[r0 + t]);
@@ -421,8 +453,11 @@ __global__ void __launch_bounds__(CHUNK_NT)
     pl.zout = zn;
     for (int bk = cta; bk < nblkP; bk += ctas) {
       __syncthreads();
-      if (resident) primal_block_res<V>(pl, bk, j, prod, rP);
-      else primal_block<V, CHUNK_NT, false, GATHER_PLAIN>(pl, bk, j, prod, srp);
+      if (resident) {
+        primal_block_res<V>(pl, bk, j, prod, rP, cl, ctas, zsn, xs);
+        continue;
+      }
+      primal_block<V, CHUNK_NT, false, GATHER_PLAIN>(pl, bk, j, prod, srp);
       if (pa.st[pa.blk_inst[bk]].status == ST_RUNNING) {
         const int r0 = pa.P.blk[bk], nr = pa.P.blk[bk + 1] - r0;
         for (int t = tid; t < nr; t += CHUNK_NT) {
