@@ -58,6 +58,15 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal float64 rate (no FP64 tensor path
 # an L2-resident vector, measured on GB300 through the SM's load path, the
 # fastest of the paths measured (profiles/gather_ceiling_gb300.md)
 GATHER_ROOF_PER_S = 2.6e11
+CHECK_PERIOD = None   # --check-period: the relKKT check period of every solver leg (None: the library's)
+
+
+def solver_options(pdqp, **kw):
+    """pdqp_default_options with the run's check period (when --check-period
+    gives one) unless the call sets its own."""
+    if CHECK_PERIOD is not None:
+        kw.setdefault("check_period", CHECK_PERIOD)
+    return pdqp.pdqp_default_options(**kw)
 
 
 def parse():
@@ -89,6 +98,9 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload: skip the sub-records of the MPC batch and the learned warm start")
     ap.add_argument("--epochs", type=int, default=20, help="family_ws: training epochs")
+    ap.add_argument("--check-period", type=int, default=None,
+                    help="relKKT check period of every solver leg (default: the library's, 64); the "
+                         "oracle legs and the stored oracle solve keep the oracle's own (64)")
     ap.add_argument("--maintained-products", action="store_true",
                     help="the main leg with options.maintained_products (needs --precision fp64)")
     ap.add_argument("--n", type=int, default=1_000_000,
@@ -340,7 +352,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     prec = pdqp.PDQP_PREC_MIXED if args.precision == "mixed" else pdqp.PDQP_PREC_FP64
-    opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=args.spmv_threads,
+    opts = solver_options(pdqp, precision=prec, spmv_threads=args.spmv_threads,
                                      maintained_products=1 if args.maintained_products else 0)
     if args.workload == "mpc_batch":
         insts = qpgen.mpc_batch(args.batch or 4096, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
@@ -400,7 +412,7 @@ def run_ours(args, world, rank, local):
     # ---- side measurement: plain float64 solves of the same problem ----
     fp64_side = None
     if args.precision == "mixed" and not args.no_fp64_side:
-        o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, spmv_threads=args.spmv_threads)
+        o64 = solver_options(pdqp, precision=pdqp.PDQP_PREC_FP64, spmv_threads=args.spmv_threads)
         pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
         torch.cuda.synchronize(dev)
         k64 = args.steps          # the same step count as the mixed-precision leg
@@ -424,7 +436,7 @@ def run_ours(args, world, rank, local):
         # carries A x, A x_bar, Q x_bar, A'y, A'y_bar, and a check gathers x
         # once for A x and once for Q x
         if args.spmv_threads in (0, 256):
-            omp = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, maintained_products=1)
+            omp = solver_options(pdqp, precision=pdqp.PDQP_PREC_FP64, maintained_products=1)
             pdqp.pdqp_solve(h, omp, x_out=x, y_out=y, stream=stream)
             torch.cuda.synchronize(dev)
             ev0.record(stream)
@@ -524,6 +536,7 @@ def run_ours(args, world, rank, local):
                         if args.workload == "mpc_batch" else "random_sparse_qp n=1000 m=500"),
                        "precision": args.precision, "eps": 1e-6,
                        "maintained_products": bool(args.maintained_products),
+                       "check_period": args.check_period or 64,
                        "l2": "inputs larger than L2 (matrices >= 200 MB), no flush",
                        "parallelism": f"replicas x{world}"},
             "iterations_per_solve": iters if per_step == 1 else
@@ -687,7 +700,7 @@ def plain_fp64_cold(pdqp, insts, stream, dev):
     problem per handle solved after another (each handle built and solved
     once before the timed region).  Solves per second over `insts`."""
     import torch
-    o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64)
+    o64 = solver_options(pdqp, precision=pdqp.PDQP_PREC_FP64)
     hs, outs = [], []
     for inst in insts:
         h = pdqp.create_from_csr(inst.n, inst.m, inst.m_eq, inst.Q, inst.A, inst.c, inst.b, inst.l, inst.u,
@@ -733,7 +746,7 @@ def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True, cpu_
     import qpgen
     insts = qpgen.mpc_batch(4096, seed=qpgen.SEED_BASE + 3 + 1000 * rank)
     N, M = sum(i.n for i in insts), sum(i.m for i in insts)
-    opts = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_MIXED)
+    opts = solver_options(pdqp, precision=pdqp.PDQP_PREC_MIXED)
     h = pdqp.batch_from_instances(insts, device=True)
     x = torch.zeros(N, dtype=torch.float64, device=dev)
     y = torch.zeros(M, dtype=torch.float64, device=dev)
@@ -746,7 +759,7 @@ def mpc_record(pdqp, rank, dev, stream, steps=2, plain_sample=32, e2e=True, cpu_
     x_mixed, y_mixed = x.clone(), y.clone()
     prof = profiled_pass(pdqp, h, lambda: pdqp.pdqp_solve(h, opts, x_out=x, y_out=y, stream=stream), 1, dev)
     # the same handle in plain float64 from the zero start (batched)
-    o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64)
+    o64 = solver_options(pdqp, precision=pdqp.PDQP_PREC_FP64)
     pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream)
     t64, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream))
     infos64 = pdqp.pdqp_batch_info(h)
@@ -814,7 +827,7 @@ def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, 
     import torch
     import qpgen
     prec = pdqp.PDQP_PREC_MIXED if precision == "mixed" else pdqp.PDQP_PREC_FP64
-    opts = pdqp.pdqp_default_options(precision=prec, spmv_threads=spmv_threads)
+    opts = solver_options(pdqp, precision=prec, spmv_threads=spmv_threads)
     fam = qpgen.family_qp(seed=qpgen.SEED_BASE + 4 + 1000 * rank)
     n, m = fam.base.n, fam.base.m
 
@@ -878,7 +891,7 @@ def family_record(pdqp, rank, dev, stream, train=50000, held=10000, chunk=2048, 
     t_mean, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, opts, x0=Xmean.repeat(k), y0=Ymean.repeat(k), x_out=x,
                                                         y_out=y, stream=stream))
     mean_infos = pdqp.pdqp_batch_info(h)
-    o64 = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, spmv_threads=spmv_threads)
+    o64 = solver_options(pdqp, precision=pdqp.PDQP_PREC_FP64, spmv_threads=spmv_threads)
     t64, _ = _timed(stream, lambda: pdqp.pdqp_solve(h, o64, x_out=x, y_out=y, stream=stream))
     infos64 = pdqp.pdqp_batch_info(h)
     rel = lambda P, Q: float(torch.linalg.norm(P - Q) / torch.linalg.norm(Q))
@@ -1105,7 +1118,7 @@ def run_algorithms(args, world, rank, local):
     for eps in (1e-3, 1e-6):
         per = {}
         for name, acc, rule, K in ALGORITHMS:
-            o = pdqp.pdqp_default_options(precision=pdqp.PDQP_PREC_FP64, eps=eps, max_iter=SGM_LIMIT,
+            o = solver_options(pdqp, precision=pdqp.PDQP_PREC_FP64, eps=eps, max_iter=SGM_LIMIT,
                                           accelerate=acc, restart_rule=rule, fixed_K=max(K, 1))
             pdqp.pdqp_solve(h, o, x_out=x, y_out=y)
             infos = pdqp.pdqp_batch_info(h)
@@ -1140,7 +1153,9 @@ def run_algorithms(args, world, rank, local):
 
 
 def main():
+    global CHECK_PERIOD
     args = parse()
+    CHECK_PERIOD = args.check_period
     if args.maintained_products and args.precision != "fp64":
         raise SystemExit("--maintained-products needs --precision fp64")
     world, rank, local = dist_setup(args)
